@@ -1,0 +1,193 @@
+/*
+ * bec.h -- C ABI of the GB300 (sm_103a) library for the block epsilon-circulant
+ * (BEC) all-at-once preconditioner of Lin & Ng, "An all-at-once preconditioner
+ * for evolutionary partial differential equations" (arXiv 2002.01108).
+ *
+ * Problem (Sec. 2, eqs. heateq/stepsystem/allatoncesystem): the heat equation
+ * u_t = div(a grad u) + f on (0,1)^dim, zero Dirichlet data, backward Euler with
+ * tau = T/N, finite differences in space (M = I, K = FD Laplacian times a), gives
+ *     L u = f,   L = block lower-bidiagonal(A_0 = I + tau K on the diagonal,
+ *                                          -I below it),
+ *     u = (u^1; ...; u^N),  f = (tau f^1 + u^0; tau f^2; ...; tau f^N).
+ * The preconditioner (start of Sec. 3) is P_eps = L - eps E_1 E_N^T, i.e. L with
+ * -eps I in block (1, N), eps in (0, 1] (Theorem pinvertibility).
+ *
+ * Layout of every space-time vector: N slices of J = nx * ny doubles, slice n
+ * (n = 1..N) at offset (n-1) J, and inside a slice x fastest ([N][ny][nx]).
+ * For dim = 1, J = nx.
+ *
+ * Conventions for every entry point:
+ *  - Vector arguments are DEVICE pointers owned by the caller (except where
+ *    marked host), 8-byte aligned, holding U = N * J doubles, on the device
+ *    the problem was allocated on.  The library never frees them.
+ *  - Work is enqueued on the problem's CUDA stream and is asynchronous, except
+ *    bec_gmres_solve / bec_gmres_solve_host / bec_true_relres, which
+ *    synchronise that stream to return scalars.
+ *  - The apply and solve paths allocate nothing; all workspace is made by
+ *    bec_allocate_problem and released by bec_free_problem.
+ *  - Invalid arguments return BEC_EINVAL and enqueue nothing.  A CUDA failure
+ *    returns BEC_ECUDA; bec_last_error() then describes it.
+ *  - A problem object must not be used from two host threads at once.
+ */
+#ifndef BEC_H
+#define BEC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bec_problem bec_problem;
+
+typedef enum {
+  BEC_OK = 0,
+  BEC_EINVAL = 1,      /* bad argument (size, pointer, eps outside (0,1], ...) */
+  BEC_ENOMEM = 2,      /* device or host allocation failed */
+  BEC_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  BEC_ENOTCONV = 4,    /* GMRES hit maxit; u and info still hold the best iterate */
+  BEC_ENUMERIC = 5,    /* NaN or Inf met in the Krylov recurrences */
+  BEC_ETIMEOUT = 6,    /* a bounded device wait ran out */
+  BEC_EUNSUPPORTED = 7 /* valid request that this build does not implement */
+} bec_status;
+
+/* How P_eps^{-1} solves the shifted spatial systems B_k z = y (Sec. 4, Step 2). */
+enum {
+  BEC_ROUTE_FST = 0    /* 2D/1D sine transform: exact for constant a (Sec. 4) */
+};
+
+/* Arithmetic of the preconditioner apply.  The operator L, the Krylov vectors,
+ * the Gram-Schmidt dots and the Hessenberg least squares are always FP64. */
+enum {
+  BEC_PC_FP64 = 0,     /* transforms and divide in double */
+  BEC_PC_FP32 = 1      /* transforms and divide in float / complex64; input and
+                          output stay double (an inexact preconditioner, use
+                          flexible GMRES) */
+};
+
+typedef struct {
+  int dim;             /* 1 or 2 */
+  int nx, ny;          /* interior points per side (h = 1/(nx+1)); ny must
+                          equal nx for dim 2 and is ignored for dim 1.
+                          nx + 1 must be a power of two in [4, 1024]. */
+  int N;               /* time steps; a power of two in [2, 1024] */
+  double T;            /* final time, tau = T / N */
+  double a;            /* constant diffusion coefficient a > 0 */
+  int route;           /* BEC_ROUTE_FST */
+  int precision;       /* BEC_PC_FP64 or BEC_PC_FP32 */
+  int max_restart;     /* largest GMRES restart length a solve may ask for
+                          (0 selects 30); sizes the Krylov basis */
+  int flexible;        /* nonzero: also allocate the FGMRES basis Z */
+  int host_io;         /* nonzero: also allocate the staging vectors used by
+                          bec_gmres_solve_host */
+} bec_problem_desc;
+
+/* Validates desc, allocates the workspace (Krylov basis (max_restart+1) x U
+ * doubles, Z when flexible, one U-vector of preconditioner scratch, tables)
+ * and returns a problem bound to `stream` (a cudaStream_t; NULL = the legacy
+ * default stream) on the current device.  eps starts unset. */
+bec_status bec_allocate_problem(const bec_problem_desc* desc, void* stream,
+                                bec_problem** out);
+
+/* Sets eps in (0, 1] (Theorem pinvertibility) and recomputes the tables of
+ * Sec. 4: D_eps = diag(eps^{(k-1)/N}) and lambda_k = 1 - eps^{1/N} theta^k
+ * (eq. repsdiagform with r = (1, -1)).  eps = 1 is the block circulant
+ * preconditioner of McDonald, Pestana and Wathen.  Else BEC_EINVAL. */
+bec_status bec_set_eps(bec_problem* p, double eps);
+
+/* y = L v (Sec. 2, eq. allatoncesystem): y^n = (I + tau K) v^n - v^{n-1},
+ * with no v^0 term.  v and y must not overlap. */
+bec_status bec_apply_A(bec_problem* p, const double* v, double* y);
+
+/* y = P_eps v (start of Sec. 3); as bec_apply_A plus -eps v^N into slice 1.
+ * A check of bec_apply_Pinv, not part of the solve.  v, y must not overlap. */
+bec_status bec_apply_P(bec_problem* p, const double* v, double* y);
+
+/* z = P_eps^{-1} y by the three steps of Sec. 4 (eqs. ytild, blockdiaginv,
+ * zcompt): scale slice k by eps^{(k-1)/N}, FFT along time, solve the N shifted
+ * systems (lambda_k I + tau K) z~ = y~ by the 2D sine transform, of which only
+ * ceil((N+1)/2) are distinct (half-spectrum remark of Sec. 4), inverse FFT and
+ * unscale.  y == z (in place) is allowed; partial overlap is not.  Needs
+ * bec_set_eps first (else BEC_EINVAL). */
+bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z);
+
+/* f = (tau f^1 + u^0; tau f^2; ...; tau f^N) (Sec. 2).  u0: J doubles,
+ * fsrc: U doubles (the source at t_1..t_N), f: U doubles. */
+bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc,
+                         double* f);
+
+typedef struct {
+  int restart;         /* GMRES(restart); 1 <= restart <= max_restart */
+  int maxit;           /* cap on total inner iterations */
+  double rtol;         /* stop when the monitored residual <= rtol * reference */
+  int flexible;        /* right preconditioning with stored Z (FGMRES); needs
+                          desc.flexible.  Required for BEC_PC_FP32. */
+  int left_pc;         /* left preconditioning as in Sec. 5 (monitors the
+                          preconditioned residual, reference ||P^{-1} f||).
+                          0 = right preconditioning (monitors ||f - L u||,
+                          reference ||f||). */
+  int use_x0;          /* nonzero: u holds the initial guess; else x0 = 0 */
+} bec_gmres_opts;
+
+typedef struct {
+  int iters;           /* total inner iterations */
+  int restarts;        /* completed restart cycles beyond the first */
+  int converged;       /* 1 if the monitored residual met rtol */
+  double prec_relres;  /* final monitored residual / reference */
+  double true_relres;  /* RES = ||f - L u|| / ||f|| (Sec. 5), recomputed */
+} bec_gmres_info;
+
+/* Solves L u = f by restarted GMRES preconditioned with P_eps (Sec. 5:
+ * zero initial guess unless use_x0, modified stopping rule rtol).  The Arnoldi
+ * basis is built with classical Gram-Schmidt applied twice, the least squares
+ * by Givens rotations, all in FP64 on the device; the host reads one scalar
+ * per iteration.  f and u are device vectors that must not overlap.  Returns
+ * BEC_ENOTCONV when maxit is reached (u and info are still written). */
+bec_status bec_gmres_solve(bec_problem* p, const double* f, double* u,
+                           const bec_gmres_opts* opts, bec_gmres_info* info);
+
+/* As bec_gmres_solve, but f and u are HOST pointers (pinned memory gives the
+ * fastest copies); copies in, solves, copies out, synchronises.  Needs
+ * desc.host_io. */
+bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host,
+                                double* u_host, const bec_gmres_opts* opts,
+                                bec_gmres_info* info);
+
+/* RES = ||f - L u||_2 / ||f||_2 (Sec. 5) computed on the device; writes the
+ * value to *out (host) after synchronising the stream. */
+bec_status bec_true_relres(bec_problem* p, const double* f, const double* u,
+                           double* out);
+
+/* Releases the workspace; p may be NULL. */
+bec_status bec_free_problem(bec_problem* p);
+
+/* Number of space-time unknowns U = N * J of the problem (0 if p is NULL). */
+long long bec_problem_size(const bec_problem* p);
+
+/* Number of kernels the library launched on this problem since allocation. */
+long long bec_kernel_launches(const bec_problem* p);
+
+/* Per-kernel timing (not part of the method): while profiling is on, every
+ * kernel launch of this problem is bracketed by two CUDA events on the
+ * problem's stream.  bec_profile_start creates `capacity` event pairs and
+ * clears earlier records (launches beyond capacity are counted but not
+ * timed); bec_profile_stop synchronises the stream, sums the event intervals
+ * per kernel name into out[0 .. *count-1] (at most `cap` entries, names are
+ * static strings owned by the library), destroys the events and turns
+ * profiling off. */
+typedef struct {
+  const char* name;
+  long long launches;    /* launches recorded with timing */
+  double ms;             /* summed event time of those launches */
+} bec_kernel_time;
+bec_status bec_profile_start(bec_problem* p, int capacity);
+bec_status bec_profile_stop(bec_problem* p, bec_kernel_time* out, int cap,
+                            int* count);
+
+const char* bec_status_string(bec_status s);
+
+/* Text of the last error met by the calling thread ("" if none). */
+const char* bec_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEC_H */

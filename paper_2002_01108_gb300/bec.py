@@ -1,0 +1,268 @@
+"""ctypes binding of libbec (include/bec.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of libbec.so; this module only
+checks tensor shapes/dtypes/devices and passes raw pointers and the current
+CUDA stream.  If the library is missing it raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbec.so")
+
+BEC_OK, BEC_EINVAL, BEC_ENOMEM, BEC_ECUDA, BEC_ENOTCONV, BEC_ENUMERIC, BEC_ETIMEOUT, \
+    BEC_EUNSUPPORTED = range(8)
+BEC_ROUTE_FST = 0
+BEC_PC_FP64, BEC_PC_FP32 = 0, 1
+
+#: every symbol include/bec.h declares
+EXPORTED = (
+    "bec_allocate_problem", "bec_set_eps", "bec_apply_A", "bec_apply_P", "bec_apply_Pinv",
+    "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_true_relres",
+    "bec_free_problem", "bec_problem_size", "bec_kernel_launches", "bec_status_string",
+    "bec_last_error", "bec_profile_start", "bec_profile_stop",
+)
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("N", ctypes.c_int), ("T", ctypes.c_double), ("a", ctypes.c_double),
+                ("route", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_restart", ctypes.c_int), ("flexible", ctypes.c_int),
+                ("host_io", ctypes.c_int)]
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("flexible", ctypes.c_int), ("left_pc", ctypes.c_int), ("use_x0", ctypes.c_int)]
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("prec_relres", ctypes.c_double), ("true_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
+class BecError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {_lib().bec_status_string(status).decode()} ({detail})")
+        self.status = status
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2002_01108_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    D = ctypes.c_void_p
+    sig = {
+        "bec_allocate_problem": ([ctypes.POINTER(ProblemDesc), P, ctypes.POINTER(P)], ctypes.c_int),
+        "bec_set_eps": ([P, ctypes.c_double], ctypes.c_int),
+        "bec_apply_A": ([P, D, D], ctypes.c_int),
+        "bec_apply_P": ([P, D, D], ctypes.c_int),
+        "bec_apply_Pinv": ([P, D, D], ctypes.c_int),
+        "bec_build_rhs": ([P, D, D, D], ctypes.c_int),
+        "bec_gmres_solve": ([P, D, D, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+                            ctypes.c_int),
+        "bec_gmres_solve_host": ([P, D, D, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+                                 ctypes.c_int),
+        "bec_true_relres": ([P, D, D, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bec_free_problem": ([P], ctypes.c_int),
+        "bec_problem_size": ([P], ctypes.c_longlong),
+        "bec_kernel_launches": ([P], ctypes.c_longlong),
+        "bec_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "bec_last_error": ([], ctypes.c_char_p),
+        "bec_profile_start": ([P, ctypes.c_int], ctypes.c_int),
+        "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def load():
+    """Load libbec.so (raises if it is not built)."""
+    return _lib()
+
+
+def _check(status: int, where: str, allow=(BEC_OK,)):
+    if status not in allow:
+        raise BecError(status, where, _lib().bec_last_error().decode())
+    return status
+
+
+def _dptr(t, U: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != U:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {U}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """One all-at-once heat problem bound to a CUDA stream (include/bec.h)."""
+
+    def __init__(self, dim: int, nx: int, N: int, T: float = 1.0, a: float = 1.0,
+                 precision: str = "fp64", max_restart: int = 30, flexible: bool = False,
+                 host_io: bool = False, stream=None):
+        import torch
+        self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
+        self.precision = precision
+        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a, BEC_ROUTE_FST,
+                           BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
+                           max_restart, int(flexible), int(host_io))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = ctypes.c_void_p(stream.cuda_stream)
+        out = ctypes.c_void_p()
+        _check(_lib().bec_allocate_problem(ctypes.byref(desc), handle, ctypes.byref(out)),
+               "bec_allocate_problem")
+        self._p = out
+        self.U = int(_lib().bec_problem_size(self._p))
+        self.J = self.U // N
+        self.shape = (N, nx, nx) if dim == 2 else (N, nx)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_p", None):
+            _lib().bec_free_problem(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def launches(self) -> int:
+        return int(_lib().bec_kernel_launches(self._p))
+
+    def _new(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    # -- entry points
+    def set_eps(self, eps: float):
+        _check(_lib().bec_set_eps(self._p, float(eps)), "bec_set_eps")
+        self.eps = float(eps)
+
+    def apply_A(self, v, y=None):
+        y = self._new() if y is None else y
+        _check(_lib().bec_apply_A(self._p, _dptr(v, self.U, "v"), _dptr(y, self.U, "y")), "bec_apply_A")
+        return y
+
+    def apply_P(self, v, y=None):
+        y = self._new() if y is None else y
+        _check(_lib().bec_apply_P(self._p, _dptr(v, self.U, "v"), _dptr(y, self.U, "y")), "bec_apply_P")
+        return y
+
+    def apply_Pinv(self, y, z=None):
+        z = self._new() if z is None else z
+        _check(_lib().bec_apply_Pinv(self._p, _dptr(y, self.U, "y"), _dptr(z, self.U, "z")),
+               "bec_apply_Pinv")
+        return z
+
+    def build_rhs(self, u0, fsrc, f=None):
+        f = self._new() if f is None else f
+        _check(_lib().bec_build_rhs(self._p, _dptr(u0, self.J, "u0"), _dptr(fsrc, self.U, "fsrc"),
+                                    _dptr(f, self.U, "f")), "bec_build_rhs")
+        return f
+
+    @staticmethod
+    def _opts(restart, maxit, rtol, flexible, left_pc, use_x0):
+        return GmresOpts(int(restart), int(maxit), float(rtol), int(flexible), int(left_pc), int(use_x0))
+
+    def gmres_solve(self, f, u=None, restart: int = 30, maxit: int = 300, rtol: float = 1e-8,
+                    flexible: bool = False, left_pc: bool = False, use_x0: bool = False):
+        """Returns (u, info dict).  Raises BecError except on convergence or maxit."""
+        u = self._new() if u is None else u
+        opts = self._opts(restart, maxit, rtol, flexible, left_pc, use_x0)
+        info = GmresInfo()
+        _check(_lib().bec_gmres_solve(self._p, _dptr(f, self.U, "f"), _dptr(u, self.U, "u"),
+                                      ctypes.byref(opts), ctypes.byref(info)),
+               "bec_gmres_solve", allow=(BEC_OK, BEC_ENOTCONV))
+        return u, info.as_dict()
+
+    def gmres_solve_host(self, f_host, u_host=None, restart: int = 30, maxit: int = 300,
+                         rtol: float = 1e-8, flexible: bool = False, left_pc: bool = False,
+                         use_x0: bool = False):
+        """Host-buffer solve: f_host/u_host are float64 CPU tensors or arrays of U
+        elements (pinned CPU tensors give the fastest copies)."""
+        f_ptr, u_ptr, u_out = self._host_ptrs(f_host, u_host)
+        opts = self._opts(restart, maxit, rtol, flexible, left_pc, use_x0)
+        info = GmresInfo()
+        _check(_lib().bec_gmres_solve_host(self._p, f_ptr, u_ptr, ctypes.byref(opts),
+                                           ctypes.byref(info)),
+               "bec_gmres_solve_host", allow=(BEC_OK, BEC_ENOTCONV))
+        return u_out, info.as_dict()
+
+    def _host_ptrs(self, f_host, u_host):
+        import torch
+
+        def ptr(x, name):
+            if isinstance(x, torch.Tensor):
+                if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != self.U:
+                    raise ValueError(f"{name} must be a contiguous float64 CPU tensor of U elements")
+                return ctypes.c_void_p(x.data_ptr())
+            if isinstance(x, np.ndarray):
+                if x.dtype != np.float64 or not x.flags.c_contiguous or x.size != self.U:
+                    raise ValueError(f"{name} must be a contiguous float64 array of U elements")
+                return ctypes.c_void_p(x.ctypes.data)
+            raise TypeError(f"{name} must be a torch CPU tensor or a numpy array")
+
+        if u_host is None:
+            u_host = (torch.empty(self.shape, dtype=torch.float64) if isinstance(f_host, torch.Tensor)
+                      else np.empty(self.shape))
+        return ptr(f_host, "f_host"), ptr(u_host, "u_host"), u_host
+
+    def profile_start(self, capacity: int = 65536):
+        """Bracket every kernel launch with CUDA events (include/bec.h)."""
+        _check(_lib().bec_profile_start(self._p, int(capacity)), "bec_profile_start")
+
+    def profile_stop(self) -> dict:
+        """Synchronise and return {kernel name: (launches, total ms)}."""
+        cap = 64
+        buf = (KernelTime * cap)()
+        n = ctypes.c_int()
+        _check(_lib().bec_profile_stop(self._p, buf, cap, ctypes.byref(n)), "bec_profile_stop")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms))
+                for i in range(min(n.value, cap))}
+
+    def true_relres(self, f, u) -> float:
+        out = ctypes.c_double()
+        _check(_lib().bec_true_relres(self._p, _dptr(f, self.U, "f"), _dptr(u, self.U, "u"),
+                                      ctypes.byref(out)), "bec_true_relres")
+        return out.value

@@ -1,0 +1,629 @@
+// C ABI of libbec: problem set-up, the preconditioner apply of Sec. 4, the
+// all-at-once operator of Sec. 2 and restarted (F)GMRES of Sec. 5.  Host code
+// only: every arithmetic step runs in the kernels of the other units.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bec_internal.h"
+
+namespace bec {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bec_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return BEC_ECUDA;
+}
+
+void prof_begin(bec_problem* p) {
+  Profiler& f = p->prof;
+  if (!f.on) return;
+  if ((size_t)(2 * f.used + 2) > f.ev.size()) {
+    f.overflow++;
+    f.pending = -1;
+    return;
+  }
+  cudaEventRecord(f.ev[2 * f.used], p->stream);
+  f.pending = f.used;
+}
+
+void prof_end(bec_problem* p, const char* name) {
+  Profiler& f = p->prof;
+  if (!f.on || f.pending < 0) return;
+  cudaEventRecord(f.ev[2 * f.pending + 1], p->stream);
+  f.names[f.pending] = name;
+  f.used++;
+  f.pending = -1;
+}
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// device scalar slots
+constexpr int S_REF = 0, S_BETA = 1, S_W = 2, S_RES = 3, S_TRUE = 4, S_ONE = 15;
+
+bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(long long x) {
+  int l = 0;
+  while ((1LL << l) < x) ++l;
+  return l;
+}
+
+bec_status einval(const char* msg) {
+  set_error(msg);
+  return BEC_EINVAL;
+}
+
+template <typename T>
+bec_status dmalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return BEC_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return BEC_ENOMEM;
+  }
+  return BEC_OK;
+}
+
+template <typename T>
+bec_status upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  BEC_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return BEC_OK;
+}
+
+void destroy_profiler(bec_problem* p) {
+  for (cudaEvent_t e : p->prof.ev) cudaEventDestroy(e);
+  p->prof.ev.clear();
+  p->prof.names.clear();
+  p->prof.used = 0;
+  p->prof.pending = -1;
+  p->prof.on = false;
+}
+
+void free_all(bec_problem* p) {
+  destroy_profiler(p);
+  PcTables& t = p->tab;
+  void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
+                  t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
+                  p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
+                  p->sn, p->g, p->ycoef, p->scal, p->io_f, p->io_u};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->host_scal) cudaFreeHost(p->host_scal);
+}
+
+// e^{-2 pi i j / n}, j < n
+void twiddles(int n, std::vector<double2>& t64, std::vector<float2>& t32) {
+  t64.resize(n);
+  t32.resize(n);
+  for (int j = 0; j < n; ++j) {
+    const double a = -2.0 * kPi * j / n;
+    t64[j] = make_double2(std::cos(a), std::sin(a));
+    t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+  }
+}
+
+bec_status read_scalars(bec_problem* p) {
+  BEC_CUDA_TRY(cudaMemcpyAsync(p->host_scal, p->scal, kScalSlots * sizeof(double),
+                               cudaMemcpyDeviceToHost, p->stream));
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return BEC_OK;
+}
+
+#define BEC_TRY(expr)                  \
+  do {                                 \
+    bec_status _s = (expr);            \
+    if (_s != BEC_OK) return _s;       \
+  } while (0)
+
+// z = P_eps^{-1} y (no argument checks)
+bec_status apply_pinv(bec_problem* p, const double* y, double* z) {
+  const int fp64 = p->desc.precision == BEC_PC_FP64;
+  const double n = (double)(p->m + 1);
+  const double per_axis = (2.0 / n) / 16.0;   // (orthonormal / raw)^2 for one forward+inverse pair
+  const double scale = 0.5 / p->N * (p->dim == 2 ? per_axis * per_axis : per_axis);
+  const long long rows = p->dim == 2 ? (long long)p->N * p->m : p->N;
+  if (fp64) {
+    BEC_TRY(launch_dst_rows(p, y, 1, z, 1, rows, 1));
+    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
+    BEC_TRY(launch_time_pass(p, z, 1, scale));
+    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
+    BEC_TRY(launch_dst_rows(p, z, 1, z, 1, rows, 1));
+  } else {
+    void* s = p->pc_scratch;
+    BEC_TRY(launch_dst_rows(p, y, 1, s, 0, rows, 0));
+    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
+    BEC_TRY(launch_time_pass(p, s, 0, scale));
+    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
+    BEC_TRY(launch_dst_rows(p, s, 0, z, 1, rows, 0));
+  }
+  return BEC_OK;
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+bool aligned8(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; }
+
+bec_status check_vec(const void* q) {
+  if (q == nullptr) return einval("null vector pointer");
+  if (!aligned8(q)) return einval("vector pointer not 8-byte aligned");
+  return BEC_OK;
+}
+
+bool overlap(const bec_problem* p, const double* a, const double* b) {
+  return a < b + p->U && b < a + p->U;
+}
+
+bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmres_opts* o,
+                      bec_gmres_info* info) {
+  const long long U = p->U;
+  const int R = o->restart;
+  const bool left = o->left_pc != 0;
+  const bool flex = o->flexible != 0;
+  double* V = p->V;
+
+  // reference norm: ||f|| (right) or ||P^{-1} f|| (left)
+  if (left) {
+    BEC_TRY(apply_pinv(p, f, p->t));
+    BEC_TRY(launch_norm(p, p->t, S_REF));
+  } else {
+    BEC_TRY(launch_norm(p, f, S_REF));
+  }
+  if (!o->use_x0) BEC_TRY(launch_zero(p, u));
+  BEC_TRY(read_scalars(p));
+  const double ref = p->host_scal[S_REF];
+  bec_gmres_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  if (!std::isfinite(ref)) {
+    set_error("right-hand side contains NaN or Inf");
+    return BEC_ENUMERIC;
+  }
+  if (ref == 0.0) {
+    BEC_TRY(launch_zero(p, u));
+    inf.converged = 1;
+    if (info) *info = inf;
+    return BEC_OK;
+  }
+
+  int iters = 0, restarts = 0;
+  bool converged = false, x_nonzero = o->use_x0 != 0;
+  double monitored = 1.0;
+  while (true) {
+    if (x_nonzero)
+      BEC_TRY(launch_residual(p, f, u, V));
+    else
+      BEC_TRY(launch_copy(p, f, V));
+    if (left) BEC_TRY(apply_pinv(p, V, V));
+    BEC_TRY(launch_norm(p, V, S_BETA));
+    BEC_TRY(read_scalars(p));
+    const double beta = p->host_scal[S_BETA];
+    if (!std::isfinite(beta)) {
+      set_error("NaN or Inf in the GMRES residual");
+      return BEC_ENUMERIC;
+    }
+    monitored = beta / ref;
+    if (beta <= o->rtol * ref) {
+      converged = true;
+      break;
+    }
+    if (iters >= o->maxit) break;
+    BEC_TRY(launch_scale_by_inv(p, V, V, S_BETA));
+    BEC_TRY(launch_gmres_start(p, S_BETA));
+    int k = 0;
+    double* h1 = p->hcol;
+    double* h2 = p->hcol + (p->max_restart + 2);
+    for (int j = 0; j < R; ++j) {
+      const double* vj = V + (long long)j * U;
+      if (left) {
+        BEC_TRY(launch_apply_L(p, vj, p->t, 0.0));
+        BEC_TRY(apply_pinv(p, p->t, p->w));
+      } else {
+        double* z = flex ? p->Z + (long long)j * U : p->t;
+        BEC_TRY(apply_pinv(p, vj, z));
+        BEC_TRY(launch_apply_L(p, z, p->w, 0.0));
+      }
+      // classical Gram-Schmidt, twice
+      BEC_TRY(launch_mdot(p, V, j + 1, p->w, h1));
+      BEC_TRY(launch_maxpy(p, p->w, V, j + 1, h1, -1.0, -1));
+      BEC_TRY(launch_mdot(p, V, j + 1, p->w, h2));
+      BEC_TRY(launch_maxpy(p, p->w, V, j + 1, h2, -1.0, S_W));
+      BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES));
+      BEC_TRY(launch_scale_by_inv(p, p->w, V + (long long)(j + 1) * U, S_W));
+      ++iters;
+      k = j + 1;
+      BEC_TRY(read_scalars(p));
+      const double res = p->host_scal[S_RES];
+      if (!std::isfinite(res)) {
+        set_error("NaN or Inf in the GMRES recurrences");
+        return BEC_ENUMERIC;
+      }
+      monitored = res / ref;
+      if (res <= o->rtol * ref) {
+        converged = true;
+        break;
+      }
+      if (iters >= o->maxit) break;
+    }
+    BEC_TRY(launch_least_squares(p, k));
+    if (left) {
+      BEC_TRY(launch_maxpy(p, u, V, k, p->ycoef, 1.0, -1));
+    } else if (flex) {
+      BEC_TRY(launch_maxpy(p, u, p->Z, k, p->ycoef, 1.0, -1));
+    } else {
+      BEC_TRY(launch_zero(p, p->t));
+      BEC_TRY(launch_maxpy(p, p->t, V, k, p->ycoef, 1.0, -1));
+      BEC_TRY(apply_pinv(p, p->t, p->w));
+      BEC_TRY(launch_maxpy(p, u, p->w, 1, p->scal + S_ONE, 1.0, -1));
+    }
+    x_nonzero = true;
+    if (converged || iters >= o->maxit) break;
+    ++restarts;
+  }
+  BEC_TRY(launch_residual_norms(p, f, u, S_TRUE));
+  BEC_TRY(read_scalars(p));
+  inf.iters = iters;
+  inf.restarts = restarts;
+  inf.converged = converged ? 1 : 0;
+  inf.prec_relres = monitored;
+  inf.true_relres = p->host_scal[S_TRUE] / p->host_scal[S_TRUE + 1];
+  if (info) *info = inf;
+  return converged ? BEC_OK : BEC_ENOTCONV;
+}
+
+bec_status check_opts(const bec_problem* p, const bec_gmres_opts* o) {
+  if (o == nullptr) return einval("null options");
+  if (o->restart < 1 || o->restart > p->max_restart)
+    return einval("restart must be in [1, max_restart]");
+  if (o->maxit < 1) return einval("maxit must be >= 1");
+  if (!(o->rtol >= 0.0) || !std::isfinite(o->rtol)) return einval("rtol must be finite and >= 0");
+  if (o->flexible && p->Z == nullptr) return einval("flexible GMRES needs desc.flexible");
+  if (o->flexible && o->left_pc) return einval("flexible GMRES is right-preconditioned");
+  if (p->desc.precision == BEC_PC_FP32 && !o->flexible)
+    return einval("the FP32 preconditioner is inexact: use flexible GMRES");
+  if (p->eps <= 0.0) return einval("call bec_set_eps first");
+  return BEC_OK;
+}
+
+}  // namespace
+}  // namespace bec
+
+using namespace bec;
+
+extern "C" {
+
+bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_problem** out) {
+  if (d == nullptr || out == nullptr) return einval("null argument");
+  *out = nullptr;
+  if (d->dim != 1 && d->dim != 2) return einval("dim must be 1 or 2");
+  if (!is_pow2((long long)d->nx + 1) || d->nx + 1 < 4 || d->nx + 1 > 1024)
+    return einval("nx + 1 must be a power of two in [4, 1024]");
+  if (d->dim == 2 && d->ny != d->nx) return einval("dim 2 needs ny == nx");
+  if (!is_pow2(d->N) || d->N < 2 || d->N > 1024)
+    return einval("N must be a power of two in [2, 1024]");
+  if (!(d->T > 0.0) || !std::isfinite(d->T)) return einval("T must be finite and > 0");
+  if (!(d->a > 0.0) || !std::isfinite(d->a)) return einval("a must be finite and > 0");
+  if (d->route != BEC_ROUTE_FST) {
+    set_error("only the sine-transform route is built");
+    return BEC_EUNSUPPORTED;
+  }
+  if (d->precision != BEC_PC_FP64 && d->precision != BEC_PC_FP32)
+    return einval("precision must be BEC_PC_FP64 or BEC_PC_FP32");
+  if (d->max_restart < 0 || d->max_restart > kMaxRestart)
+    return einval("max_restart must be in [0, 60]");
+
+  bec_problem* p = new (std::nothrow) bec_problem();
+  if (p == nullptr) return BEC_ENOMEM;
+  p->desc = *d;
+  p->dim = d->dim;
+  p->m = d->nx;
+  p->N = d->N;
+  p->J = d->dim == 2 ? (long long)d->nx * d->nx : d->nx;
+  p->U = p->J * d->N;
+  p->tau = d->T / d->N;
+  p->h = 1.0 / (d->nx + 1);
+  p->a = d->a;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->max_restart = d->max_restart == 0 ? 30 : d->max_restart;
+  cudaGetDevice(&p->device);
+
+  const int n = p->m + 1, N = p->N, R = p->max_restart;
+  PcTables& t = p->tab;
+  t.space.n = n;
+  t.space.logn = ilog2(n);
+  t.time.n = N;
+  t.time.logn = ilog2(N);
+  const long long U = p->U;
+  const long long parts = std::max<long long>(32LL * kReduceBlocks, 2 * stencil_blocks(p));
+  bec_status s = BEC_OK;
+  auto chain = [&](bec_status r) {
+    if (s == BEC_OK) s = r;
+  };
+  chain(dmalloc(&t.space.tw64, n));
+  chain(dmalloc(&t.space.tw32, n));
+  chain(dmalloc(&t.time.tw64, N));
+  chain(dmalloc(&t.time.tw32, N));
+  chain(dmalloc(&t.sin2_64, n));
+  chain(dmalloc(&t.sin2_32, n));
+  chain(dmalloc(&t.mu64, p->m));
+  chain(dmalloc(&t.mu32, p->m));
+  chain(dmalloc(&t.es64, N));
+  chain(dmalloc(&t.eis64, N));
+  chain(dmalloc(&t.es32, N));
+  chain(dmalloc(&t.eis32, N));
+  chain(dmalloc(&t.lamf64, N / 2 + 1));
+  chain(dmalloc(&t.lamf32, N / 2 + 1));
+  if (d->precision == BEC_PC_FP32) {
+    float* sc = nullptr;
+    chain(dmalloc(&sc, (size_t)U));
+    p->pc_scratch = sc;
+  }
+  chain(dmalloc(&p->V, (size_t)(R + 1) * U));
+  if (d->flexible) chain(dmalloc(&p->Z, (size_t)R * U));
+  chain(dmalloc(&p->w, (size_t)U));
+  chain(dmalloc(&p->t, (size_t)U));
+  chain(dmalloc(&p->partials, (size_t)parts));
+  chain(dmalloc(&p->hcol, (size_t)2 * (R + 2)));
+  chain(dmalloc(&p->H, (size_t)(R + 1) * R));
+  chain(dmalloc(&p->cs, (size_t)R));
+  chain(dmalloc(&p->sn, (size_t)R));
+  chain(dmalloc(&p->g, (size_t)R + 1));
+  chain(dmalloc(&p->ycoef, (size_t)R));
+  chain(dmalloc(&p->scal, (size_t)kScalSlots));
+  if (d->host_io) {
+    chain(dmalloc(&p->io_f, (size_t)U));
+    chain(dmalloc(&p->io_u, (size_t)U));
+  }
+  if (s == BEC_OK) {
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&p->host_scal),
+                                   kScalSlots * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->host_scal = nullptr;
+      set_error("cudaMallocHost failed");
+      s = BEC_ENOMEM;
+    }
+  }
+  if (s != BEC_OK) {
+    free_all(p);
+    delete p;
+    return s;
+  }
+
+  // tables that do not depend on eps
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  twiddles(n, tw64, tw32);
+  chain(upload(t.space.tw64, tw64, p->stream));
+  chain(upload(t.space.tw32, tw32, p->stream));
+  std::vector<double2> ttw64;
+  std::vector<float2> ttw32;
+  twiddles(N, ttw64, ttw32);
+  chain(upload(t.time.tw64, ttw64, p->stream));
+  chain(upload(t.time.tw32, ttw32, p->stream));
+  std::vector<double> s64(n), mu64(p->m);
+  std::vector<float> s32(n), mu32(p->m);
+  for (int j = 0; j < n; ++j) {
+    s64[j] = 2.0 * std::sin(j * kPi / n);
+    s32[j] = (float)s64[j];
+  }
+  // 1D FD eigenvalues (4a/h^2) sin^2(k pi h / 2), k = 1..m
+  for (int k = 1; k <= p->m; ++k) {
+    const double sk = std::sin(k * kPi * p->h / 2.0);
+    mu64[k - 1] = 4.0 * p->a / (p->h * p->h) * sk * sk;
+    mu32[k - 1] = (float)mu64[k - 1];
+  }
+  chain(upload(t.sin2_64, s64, p->stream));
+  chain(upload(t.sin2_32, s32, p->stream));
+  chain(upload(t.mu64, mu64, p->stream));
+  chain(upload(t.mu32, mu32, p->stream));
+  std::vector<double> scal0(kScalSlots, 0.0);
+  scal0[S_ONE] = 1.0;
+  chain(upload(p->scal, scal0, p->stream));
+  if (s == BEC_OK) {
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (s != BEC_OK) {
+    free_all(p);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return BEC_OK;
+}
+
+bec_status bec_set_eps(bec_problem* p, double eps) {
+  if (p == nullptr) return einval("null problem");
+  if (!(eps > 0.0 && eps <= 1.0)) return einval("eps must lie in (0, 1]");
+  const int N = p->N;
+  std::vector<double> es(N), eis(N);
+  std::vector<float> es32(N), eis32(N);
+  const double le = std::log(eps);
+  for (int j = 0; j < N; ++j) {
+    es[j] = std::exp(le * j / N);
+    eis[j] = std::exp(-le * j / N);
+    es32[j] = (float)es[j];
+    eis32[j] = (float)eis[j];
+  }
+  // lambda'_k = 1 - eps^{1/N} e^{-2 pi i k / N}, the eigenvalue that pairs with
+  // the forward-sign FFT (lambda_{N-k} of eq. repsdiagform, r = (1, -1))
+  const double e1 = std::exp(le / N);
+  std::vector<double2> lam(N / 2 + 1);
+  std::vector<float2> lam32(N / 2 + 1);
+  for (int k = 0; k <= N / 2; ++k) {
+    const double a = 2.0 * kPi * k / N;
+    double re = 1.0 - e1 * std::cos(a), im = e1 * std::sin(a);
+    if (k == 0) re = 1.0 - e1, im = 0.0;
+    if (2 * k == N) re = 1.0 + e1, im = 0.0;
+    lam[k] = make_double2(re, im);
+    lam32[k] = make_float2((float)re, (float)im);
+  }
+  const PcTables& t = p->tab;
+  BEC_TRY(upload(t.es64, es, p->stream));
+  BEC_TRY(upload(t.eis64, eis, p->stream));
+  BEC_TRY(upload(t.es32, es32, p->stream));
+  BEC_TRY(upload(t.eis32, eis32, p->stream));
+  BEC_TRY(upload(t.lamf64, lam, p->stream));
+  BEC_TRY(upload(t.lamf32, lam32, p->stream));
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  p->eps = eps;
+  return BEC_OK;
+}
+
+bec_status bec_apply_A(bec_problem* p, const double* v, double* y) {
+  if (p == nullptr) return einval("null problem");
+  BEC_TRY(check_vec(v));
+  BEC_TRY(check_vec(y));
+  if (overlap(p, v, y)) return einval("v and y must not overlap");
+  return launch_apply_L(p, v, y, 0.0);
+}
+
+bec_status bec_apply_P(bec_problem* p, const double* v, double* y) {
+  if (p == nullptr) return einval("null problem");
+  if (p->eps <= 0.0) return einval("call bec_set_eps first");
+  BEC_TRY(check_vec(v));
+  BEC_TRY(check_vec(y));
+  if (overlap(p, v, y)) return einval("v and y must not overlap");
+  return launch_apply_L(p, v, y, p->eps);
+}
+
+bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z) {
+  if (p == nullptr) return einval("null problem");
+  if (p->eps <= 0.0) return einval("call bec_set_eps first");
+  BEC_TRY(check_vec(y));
+  BEC_TRY(check_vec(z));
+  if (y != z && overlap(p, y, z)) return einval("y and z must be equal or disjoint");
+  return apply_pinv(p, y, z);
+}
+
+bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc, double* f) {
+  if (p == nullptr) return einval("null problem");
+  BEC_TRY(check_vec(u0));
+  BEC_TRY(check_vec(fsrc));
+  BEC_TRY(check_vec(f));
+  return launch_build_rhs(p, u0, fsrc, f);
+}
+
+bec_status bec_gmres_solve(bec_problem* p, const double* f, double* u, const bec_gmres_opts* opts,
+                           bec_gmres_info* info) {
+  if (p == nullptr) return einval("null problem");
+  BEC_TRY(check_opts(p, opts));
+  if (f == nullptr || u == nullptr) return einval("null vector pointer");
+  if (!aligned16(f) || !aligned16(u)) return einval("f and u must be 16-byte aligned");
+  if (overlap(p, f, u)) return einval("f and u must not overlap");
+  return gmres_impl(p, f, u, opts, info);
+}
+
+bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host, double* u_host,
+                                const bec_gmres_opts* opts, bec_gmres_info* info) {
+  if (p == nullptr) return einval("null problem");
+  if (p->io_f == nullptr) return einval("bec_gmres_solve_host needs desc.host_io");
+  BEC_TRY(check_opts(p, opts));
+  if (f_host == nullptr || u_host == nullptr) return einval("null host pointer");
+  const size_t bytes = (size_t)p->U * sizeof(double);
+  BEC_CUDA_TRY(cudaMemcpyAsync(p->io_f, f_host, bytes, cudaMemcpyHostToDevice, p->stream));
+  if (opts->use_x0)
+    BEC_CUDA_TRY(cudaMemcpyAsync(p->io_u, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
+  const bec_status s = gmres_impl(p, p->io_f, p->io_u, opts, info);
+  if (s != BEC_OK && s != BEC_ENOTCONV) return s;
+  BEC_CUDA_TRY(cudaMemcpyAsync(u_host, p->io_u, bytes, cudaMemcpyDeviceToHost, p->stream));
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return s;
+}
+
+bec_status bec_true_relres(bec_problem* p, const double* f, const double* u, double* out) {
+  if (p == nullptr || out == nullptr) return einval("null argument");
+  BEC_TRY(check_vec(f));
+  BEC_TRY(check_vec(u));
+  BEC_TRY(launch_residual_norms(p, f, u, S_TRUE));
+  BEC_TRY(read_scalars(p));
+  *out = p->host_scal[S_TRUE] / p->host_scal[S_TRUE + 1];
+  return BEC_OK;
+}
+
+bec_status bec_free_problem(bec_problem* p) {
+  if (p == nullptr) return BEC_OK;
+  cudaStreamSynchronize(p->stream);
+  free_all(p);
+  delete p;
+  return BEC_OK;
+}
+
+long long bec_problem_size(const bec_problem* p) { return p ? p->U : 0; }
+
+long long bec_kernel_launches(const bec_problem* p) { return p ? p->launches : 0; }
+
+bec_status bec_profile_start(bec_problem* p, int capacity) {
+  if (p == nullptr || capacity < 1) return einval("null problem or capacity < 1");
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  destroy_profiler(p);
+  p->prof.ev.resize((size_t)2 * capacity);
+  for (auto& e : p->prof.ev) {
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) {
+      e = nullptr;
+      p->prof.ev.clear();
+      return cuda_fail(err, "cudaEventCreate");
+    }
+  }
+  p->prof.names.assign((size_t)capacity, nullptr);
+  p->prof.overflow = 0;
+  p->prof.on = true;
+  return BEC_OK;
+}
+
+bec_status bec_profile_stop(bec_problem* p, bec_kernel_time* out, int cap, int* count) {
+  if (p == nullptr || count == nullptr || (out == nullptr && cap > 0))
+    return einval("null argument");
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  std::vector<bec_kernel_time> agg;
+  for (int i = 0; i < p->prof.used; ++i) {
+    float ms = 0.f;
+    BEC_CUDA_TRY(cudaEventElapsedTime(&ms, p->prof.ev[2 * i], p->prof.ev[2 * i + 1]));
+    const char* nm = p->prof.names[i];
+    auto it = std::find_if(agg.begin(), agg.end(),
+                           [nm](const bec_kernel_time& k) { return std::strcmp(k.name, nm) == 0; });
+    if (it == agg.end()) {
+      agg.push_back(bec_kernel_time{nm, 1, (double)ms});
+    } else {
+      it->launches++;
+      it->ms += ms;
+    }
+  }
+  destroy_profiler(p);
+  *count = (int)agg.size();
+  for (int i = 0; i < (int)agg.size() && i < cap; ++i) out[i] = agg[i];
+  return BEC_OK;
+}
+
+const char* bec_status_string(bec_status s) {
+  switch (s) {
+    case BEC_OK: return "BEC_OK";
+    case BEC_EINVAL: return "BEC_EINVAL";
+    case BEC_ENOMEM: return "BEC_ENOMEM";
+    case BEC_ECUDA: return "BEC_ECUDA";
+    case BEC_ENOTCONV: return "BEC_ENOTCONV";
+    case BEC_ENUMERIC: return "BEC_ENUMERIC";
+    case BEC_ETIMEOUT: return "BEC_ETIMEOUT";
+    case BEC_EUNSUPPORTED: return "BEC_EUNSUPPORTED";
+  }
+  return "BEC_UNKNOWN";
+}
+
+const char* bec_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// Internal declarations shared by the translation units of libbec.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bec.h"
+
+namespace bec {
+
+// Tables for one transform length n: twiddles e^{-2 pi i j / n}, j < n.
+struct FftTables {
+  int n = 0, logn = 0;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+};
+
+// Everything the preconditioner kernels read besides the vectors.
+struct PcTables {
+  FftTables space;           // n = nx + 1
+  FftTables time;            // n = N
+  double* sin2_64 = nullptr; // 2 sin(j pi / n), j < n   (DST-I pre-pass)
+  float* sin2_32 = nullptr;
+  double* mu64 = nullptr;    // 1D FD eigenvalues mu_i, i = 1..m
+  float* mu32 = nullptr;
+  double* es64 = nullptr;    // eps^{j/N}, j < N
+  double* eis64 = nullptr;   // eps^{-j/N}
+  float* es32 = nullptr;
+  float* eis32 = nullptr;
+  double2* lamf64 = nullptr; // 1 - eps^{1/N} e^{-2 pi i k / N}, k = 0..N/2
+  float2* lamf32 = nullptr;
+};
+
+// Event pairs around kernel launches (bec_profile_start / bec_profile_stop).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;       // 2 per record
+  std::vector<const char*> names;    // 1 per record
+  int used = 0;                      // records completed
+  int pending = -1;                  // record whose start event is in flight
+  long long overflow = 0;
+};
+
+}  // namespace bec
+
+struct bec_problem {
+  bec_problem_desc desc;
+  int dim = 0, m = 0, N = 0;
+  long long J = 0, U = 0;
+  double tau = 0.0, h = 0.0, a = 1.0;
+  double eps = -1.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int max_restart = 30;
+  long long launches = 0;
+
+  bec::PcTables tab;
+  void* pc_scratch = nullptr;   // U elements of the preconditioner's type
+
+  // Krylov workspace (FP64)
+  double* V = nullptr;          // (max_restart + 1) x U
+  double* Z = nullptr;          // max_restart x U (flexible only)
+  double* w = nullptr;          // U
+  double* t = nullptr;          // U
+  double* partials = nullptr;   // reduction partials
+  double* hcol = nullptr;       // two Gram-Schmidt coefficient columns, 2 x (max_restart + 2)
+  double* H = nullptr;          // (max_restart + 1) x max_restart, column-major
+  double* cs = nullptr;         // Givens cosines
+  double* sn = nullptr;         // Givens sines
+  double* g = nullptr;          // rotated right-hand side (max_restart + 1)
+  double* ycoef = nullptr;      // least-squares solution (max_restart)
+  double* scal = nullptr;       // device scalars (norms, residual estimate)
+  double* host_scal = nullptr;  // pinned mirror of scal
+  double* io_f = nullptr;       // host_io staging
+  double* io_u = nullptr;
+  bec::Profiler prof;
+};
+
+namespace bec {
+
+constexpr int kReduceBlocks = 608;   // 4 x 152 SMs: fixed => deterministic sums
+constexpr int kScalSlots = 16;
+constexpr int kMaxRestart = 60;
+
+// ---- error plumbing
+void set_error(const std::string& msg);
+bec_status cuda_fail(cudaError_t e, const char* where);
+#define BEC_CUDA_TRY(expr)                                            \
+  do {                                                                \
+    cudaError_t _e = (expr);                                          \
+    if (_e != cudaSuccess) return ::bec::cuda_fail(_e, #expr);        \
+  } while (0)
+void prof_begin(bec_problem* p);
+void prof_end(bec_problem* p, const char* name);
+// Call BEC_LAUNCH_BEGIN(p) right before a kernel launch and
+// BEC_LAUNCH_CHECK(p, name) right after it.
+#define BEC_LAUNCH_BEGIN(p) ::bec::prof_begin(p)
+#define BEC_LAUNCH_CHECK(p, where)                                    \
+  do {                                                                \
+    (p)->launches++;                                                  \
+    cudaError_t _e = cudaGetLastError();                              \
+    if (_e != cudaSuccess) return ::bec::cuda_fail(_e, where);        \
+    ::bec::prof_end(p, where);                                        \
+  } while (0)
+
+// ---- preconditioner passes (bec_dst.cu, bec_time.cu)
+// DST-I (unnormalised, times 4) along x of `rows` contiguous rows of length m.
+bec_status launch_dst_rows(bec_problem* p, const void* in, int in_fp64,
+                           void* out, int out_fp64, long long rows, int fp64);
+// DST-I (same scaling) along y of every [ny][nx] slice, in place.
+bec_status launch_dst_cols(bec_problem* p, void* data, int fp64);
+// Time pass: scale, FFT over N, divide by the shifted eigenvalues, inverse
+// FFT, unscale, for every spatial mode, in place.
+bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale);
+
+// ---- stencils (bec_stencil.cu)
+// number of blocks (partial sums) the residual-norm kernel writes
+long long stencil_blocks(const bec_problem* p);
+// y = L v; with corner != 0, y = P_eps v (adds -corner * v^N to slice 1).
+bec_status launch_apply_L(bec_problem* p, const double* v, double* y,
+                          double corner);
+bec_status launch_build_rhs(bec_problem* p, const double* u0,
+                            const double* fsrc, double* f);
+// partials[b] = sum over block b of (f - L u)^2, partials[B + b] = sum f^2;
+// then scal[slot] = sqrt(sum r^2), scal[slot+1] = sqrt(sum f^2).
+bec_status launch_residual_norms(bec_problem* p, const double* f,
+                                 const double* u, int slot);
+// r = f - L u (u may be null: r = f)
+bec_status launch_residual(bec_problem* p, const double* f, const double* u,
+                           double* r);
+
+// ---- Krylov BLAS (bec_krylov.cu)
+// hcol[i] = <V_i, w>, i < nv, V_i = Vb + i U.
+bec_status launch_mdot(bec_problem* p, const double* Vb, int nv,
+                       const double* w, double* hcol);
+// w -= sum_i hcol[i] V_i (i < nv); if norm_slot >= 0 also scal[slot] = ||w||.
+bec_status launch_maxpy(bec_problem* p, double* w, const double* Vb, int nv,
+                        const double* coef, double sign, int norm_slot);
+// scal[slot] = ||x||
+bec_status launch_norm(bec_problem* p, const double* x, int slot);
+// y = x * (1 / scal[slot])  (scal read on the device)
+bec_status launch_scale_by_inv(bec_problem* p, const double* x, double* y,
+                               int slot);
+// Hessenberg column j: H(0:j, j) = h1 + h2 (the two Gram-Schmidt passes),
+// H(j+1, j) = scal[norm_slot]; applies the previous rotations, makes
+// rotation j, updates g and writes |g[j+1]| to scal[res_slot].
+bec_status launch_hessenberg(bec_problem* p, int j, const double* h1,
+                             const double* h2, int norm_slot, int res_slot);
+// g[0] = scal[slot]; clears rotations.
+bec_status launch_gmres_start(bec_problem* p, int slot);
+// ycoef = H(0:k,0:k)^{-1} g(0:k)
+bec_status launch_least_squares(bec_problem* p, int k);
+bec_status launch_copy(bec_problem* p, const double* x, double* y);
+bec_status launch_zero(bec_problem* p, double* x);
+
+}  // namespace bec

@@ -1,0 +1,214 @@
+// All-at-once stencil kernels (Sec. 2, eq. allatoncesystem): L v, P_eps v,
+// the right-hand side f and the true residual RES of Sec. 5.
+//
+// With M = I and K = (a/h^2) x (3- or 5-point Laplacian), block row n of L is
+//     (L v)^n = (1 + 2 dim c) v^n - c (sum of the 2 dim neighbours of v^n) - v^{n-1},
+// c = tau a / h^2, with no v^0 term; P_eps adds -eps v^N to block row 1.
+// A thread owns one spatial point and walks a chunk of time slices, keeping
+// v^{n-1} in a register, so v is read from memory once.
+#include <cuda_runtime.h>
+
+#include "bec_internal.h"
+
+namespace bec {
+namespace {
+
+constexpr int kStencilThreads = 256;
+constexpr int kTimeChunk = 8;
+
+struct StencilGeom {
+  long long J;
+  int m, N, dim;
+  double cdiag, c;
+};
+
+__device__ __forceinline__ double apply_row(const double* __restrict__ vs, long long q, int ix,
+                                            int iy, const StencilGeom& g, double center) {
+  double nb = (ix > 0 ? vs[q - 1] : 0.0) + (ix < g.m - 1 ? vs[q + 1] : 0.0);
+  if (g.dim == 2) nb += (iy > 0 ? vs[q - g.m] : 0.0) + (iy < g.m - 1 ? vs[q + g.m] : 0.0);
+  return g.cdiag * center - g.c * nb;
+}
+
+// y = L v (corner = 0) or y = P_eps v (corner = eps).
+__global__ void __launch_bounds__(kStencilThreads)
+apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom g,
+               double corner) {
+  const long long q = (long long)blockIdx.x * kStencilThreads + threadIdx.x;
+  if (q >= g.J) return;
+  const int n0 = blockIdx.y * kTimeChunk;
+  const int n1 = min(g.N, n0 + kTimeChunk);
+  const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
+  const int ix = (int)(q - (long long)iy * g.m);
+  double prev = n0 > 0 ? v[(long long)(n0 - 1) * g.J + q]
+                       : (corner != 0.0 ? corner * v[(long long)(g.N - 1) * g.J + q] : 0.0);
+  for (int n = n0; n < n1; ++n) {
+    const double* vs = v + (long long)n * g.J;
+    const double center = vs[q];
+    y[(long long)n * g.J + q] = apply_row(vs, q, ix, iy, g, center) - prev;
+    prev = center;
+  }
+}
+
+// r = f - L u (u == nullptr: r = f)
+__global__ void __launch_bounds__(kStencilThreads)
+residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
+                double* __restrict__ r, StencilGeom g) {
+  const long long q = (long long)blockIdx.x * kStencilThreads + threadIdx.x;
+  if (q >= g.J) return;
+  const int n0 = blockIdx.y * kTimeChunk;
+  const int n1 = min(g.N, n0 + kTimeChunk);
+  const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
+  const int ix = (int)(q - (long long)iy * g.m);
+  if (u == nullptr) {
+    for (int n = n0; n < n1; ++n) r[(long long)n * g.J + q] = f[(long long)n * g.J + q];
+    return;
+  }
+  double prev = n0 > 0 ? u[(long long)(n0 - 1) * g.J + q] : 0.0;
+  for (int n = n0; n < n1; ++n) {
+    const double* us = u + (long long)n * g.J;
+    const double center = us[q];
+    const long long o = (long long)n * g.J + q;
+    r[o] = f[o] - (apply_row(us, q, ix, iy, g, center) - prev);
+    prev = center;
+  }
+}
+
+// Block sums of (f - L u)^2 and f^2 for RES (Sec. 5).  One partial pair per
+// block, reduced in a fixed order by finish_norms_kernel: deterministic.
+__global__ void __launch_bounds__(kStencilThreads)
+residual_norms_kernel(const double* __restrict__ f, const double* __restrict__ u,
+                      double* __restrict__ partials, StencilGeom g) {
+  const long long q = (long long)blockIdx.x * kStencilThreads + threadIdx.x;
+  double rr = 0.0, ff = 0.0;
+  if (q < g.J) {
+    const int n0 = blockIdx.y * kTimeChunk;
+    const int n1 = min(g.N, n0 + kTimeChunk);
+    const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
+    const int ix = (int)(q - (long long)iy * g.m);
+    double prev = n0 > 0 ? u[(long long)(n0 - 1) * g.J + q] : 0.0;
+    for (int n = n0; n < n1; ++n) {
+      const double* us = u + (long long)n * g.J;
+      const double center = us[q];
+      const long long o = (long long)n * g.J + q;
+      const double fo = f[o];
+      const double r = fo - (apply_row(us, q, ix, iy, g, center) - prev);
+      rr += r * r;
+      ff += fo * fo;
+      prev = center;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ff += __shfl_down_sync(0xffffffffu, ff, off);
+  }
+  __shared__ double s_rr[kStencilThreads / 32], s_ff[kStencilThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_rr[warp] = rr;
+    s_ff[warp] = ff;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kStencilThreads / 32; ++w) {
+      a += s_rr[w];
+      b += s_ff[w];
+    }
+    const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    partials[2 * blk] = a;
+    partials[2 * blk + 1] = b;
+  }
+}
+
+__global__ void finish_norms_kernel(const double* __restrict__ partials, long long nblk,
+                                    double* __restrict__ scal, int slot) {
+  __shared__ double s_a[256], s_b[256];
+  double a = 0.0, b = 0.0;
+  for (long long i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  s_a[threadIdx.x] = a;
+  s_b[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + s];
+      s_b[threadIdx.x] += s_b[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scal[slot] = sqrt(s_a[0]);
+    scal[slot + 1] = sqrt(s_b[0]);
+  }
+}
+
+// f = tau fsrc, plus u0 in slice 1 (Sec. 2).
+__global__ void build_rhs_kernel(const double* __restrict__ u0, const double* __restrict__ fsrc,
+                                 double* __restrict__ f, long long J, long long U, double tau) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < U;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = tau * fsrc[i];
+    if (i < J) v += u0[i];
+    f[i] = v;
+  }
+}
+
+StencilGeom geom(const bec_problem* p) {
+  StencilGeom g;
+  g.J = p->J;
+  g.m = p->m;
+  g.N = p->N;
+  g.dim = p->dim;
+  g.c = p->tau * p->a / (p->h * p->h);
+  g.cdiag = 1.0 + 2.0 * p->dim * g.c;
+  return g;
+}
+
+dim3 stencil_grid(const bec_problem* p) {
+  return dim3((unsigned)((p->J + kStencilThreads - 1) / kStencilThreads),
+              (unsigned)((p->N + kTimeChunk - 1) / kTimeChunk));
+}
+
+}  // namespace
+
+long long stencil_blocks(const bec_problem* p) {
+  const dim3 g = stencil_grid(p);
+  return (long long)g.x * g.y;
+}
+
+bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double corner) {
+  BEC_LAUNCH_BEGIN(p);
+  apply_L_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner);
+  BEC_LAUNCH_CHECK(p, "apply_L_kernel");
+  return BEC_OK;
+}
+
+bec_status launch_residual(bec_problem* p, const double* f, const double* u, double* r) {
+  BEC_LAUNCH_BEGIN(p);
+  residual_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
+  BEC_LAUNCH_CHECK(p, "residual_kernel");
+  return BEC_OK;
+}
+
+bec_status launch_residual_norms(bec_problem* p, const double* f, const double* u, int slot) {
+  const dim3 grid = stencil_grid(p);
+  BEC_LAUNCH_BEGIN(p);
+  residual_norms_kernel<<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
+  BEC_LAUNCH_CHECK(p, "residual_norms_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  finish_norms_kernel<<<1, 256, 0, p->stream>>>(p->partials, (long long)grid.x * grid.y, p->scal,
+                                                 slot);
+  BEC_LAUNCH_CHECK(p, "finish_norms_kernel");
+  return BEC_OK;
+}
+
+bec_status launch_build_rhs(bec_problem* p, const double* u0, const double* fsrc, double* f) {
+  BEC_LAUNCH_BEGIN(p);
+  build_rhs_kernel<<<4 * 152, 256, 0, p->stream>>>(u0, fsrc, f, p->J, p->U, p->tau);
+  BEC_LAUNCH_CHECK(p, "build_rhs_kernel");
+  return BEC_OK;
+}
+
+}  // namespace bec

@@ -1,0 +1,140 @@
+// Time pass of P_eps^{-1} (Sec. 4, eqs. ytild, blockdiaginv, zcompt), run in
+// the sine basis where every B_k = lambda_k I + tau K is diagonal:
+//   for each spatial mode q with FD eigenvalue mu_q, and its column w_j (j < N),
+//     a_j = eps^{j/N} w_j                       (D_eps, Step 1)
+//     A_k = sum_j a_j e^{-2 pi i jk/N}          (FFT along time, Step 1)
+//     B_k = A_k / (lambda'_k + tau mu_q)        (Step 2; lambda'_k = 1 - eps^{1/N}
+//                                                e^{-2 pi i k/N} is the eigenvalue that
+//                                                pairs with this FFT sign)
+//     z_j = eps^{-j/N} N^{-1} sum_k B_k e^{+2 pi i jk/N}   (Step 3)
+// Two real modes share one complex FFT; their spectra are separated, divided
+// and recombined for the pairs (k, N-k), k = 0..N/2, so only ceil((N+1)/2)
+// distinct shifted solves are done (half-spectrum remark of Sec. 4).
+#include <cuda_runtime.h>
+
+#include "bec_fft.cuh"
+#include "bec_internal.h"
+
+namespace bec {
+namespace {
+
+template <typename T>
+constexpr int time_warps() { return sizeof(T) == 8 ? 8 : 16; }
+
+template <typename T>
+__device__ __forceinline__ T mode_mu(long long q, long long J, int m, int dim,
+                                     const T* __restrict__ mu1) {
+  if (q >= J) return T(1);                     // padding column: any positive value
+  if (dim == 1) return mu1[q];
+  const int l = (int)(q / m), i = (int)(q - (long long)l * m);
+  return mu1[i] + mu1[l];
+}
+
+// data: [N][J] in place.  A block owns W = 2 x warps adjacent modes; warp w
+// transforms modes (q0 + 2w, q0 + 2w + 1) packed as real + i imaginary.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(time_warps<T>() * 32)
+time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
+                 const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
+                 const T* __restrict__ mu1, T tau, T scale, const v2_t<T>* __restrict__ tw) {
+  using V = v2_t<T>;
+  constexpr int N = 1 << LOGN;
+  constexpr int LSC = N + 1;
+  constexpr int WARPS = time_warps<T>();
+  constexpr int W = 2 * WARPS;
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  T* sm = reinterpret_cast<T*>(smem_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q0 = (long long)blockIdx.x * W;
+
+  // load + D_eps scaling: mode c of the tile -> line c/2, real (c even) or imaginary part
+  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
+    const int j = e / W, c = e % W;
+    const long long q = q0 + c;
+    const T v = q < J ? data[(long long)j * J + q] * es[j] : T(0);
+    sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] = v;
+  }
+  __syncthreads();
+
+  V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
+  warp_fft<T, -1, LOGN>(line, tw, lane);
+
+  const long long qa = q0 + 2 * warp;
+  const T mua = mode_mu(qa, J, m, dim, mu1);
+  const T mub = qa + 1 < J ? mode_mu(qa + 1, J, m, dim, mu1) : mua;
+  constexpr int NK = N / 2 + 1;
+  constexpr int PERK = (NK + 31) / 32;
+#pragma unroll
+  for (int t = 0; t < PERK; ++t) {
+    const int k = lane + 32 * t;
+    if (k < NK) {
+      const int kk = (N - k) & (N - 1);
+      const V C = line[k], Cn = line[kk];
+      // A1 = spectrum of mode a, A2 = spectrum of mode b (each times 2)
+      const V A1 = {C.x + Cn.x, C.y - Cn.y};
+      const V A2 = {C.y + Cn.y, Cn.x - C.x};
+      const V L = lamf[k];
+      const T d1r = L.x + tau * mua, d2r = L.x + tau * mub;
+      const T s1 = scale / (d1r * d1r + L.y * L.y);
+      const T s2 = scale / (d2r * d2r + L.y * L.y);
+      const V q1 = {d1r * s1, -L.y * s1};           // scale / d1
+      const V q2 = {d2r * s2, -L.y * s2};
+      const V B1 = cmul(A1, q1), B2 = cmul(A2, q2);
+      line[k] = {B1.x - B2.y, B1.y + B2.x};         // B1 + i B2
+      line[kk] = {B1.x + B2.y, B2.x - B1.y};        // conj(B1) + i conj(B2)
+    }
+  }
+  __syncwarp();
+  warp_fft<T, +1, LOGN>(line, tw, lane);
+  __syncthreads();
+
+  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
+    const int j = e / W, c = e % W;
+    const long long q = q0 + c;
+    if (q < J) data[(long long)j * J + q] = sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] * eis[j];
+  }
+}
+
+template <typename T, int LOGN>
+bec_status time_launch(bec_problem* p, void* data, double scale, const T* es, const T* eis,
+                       const v2_t<T>* lamf, const T* mu1, const v2_t<T>* tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int warps = time_warps<T>();
+  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T);
+  auto k = time_pass_kernel<T, LOGN>;
+  if (smem > 48 * 1024)
+    BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long W = 2 * warps;
+  const unsigned grid = (unsigned)((p->J + W - 1) / W);
+  BEC_LAUNCH_BEGIN(p);
+  k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->J, p->m, p->dim, es, eis,
+                                           lamf, mu1, (T)p->tau, (T)scale, tw);
+  BEC_LAUNCH_CHECK(p, "time_pass_kernel");
+  return BEC_OK;
+}
+
+template <typename T>
+bec_status time_dispatch(bec_problem* p, void* data, double scale, const T* es, const T* eis,
+                         const v2_t<T>* lamf, const T* mu1, const v2_t<T>* tw) {
+  switch (p->tab.time.logn) {
+#define BEC_TIME_CASE(L) \
+  case L: return time_launch<T, L>(p, data, scale, es, eis, lamf, mu1, tw);
+    BEC_TIME_CASE(1) BEC_TIME_CASE(2) BEC_TIME_CASE(3) BEC_TIME_CASE(4) BEC_TIME_CASE(5)
+    BEC_TIME_CASE(6) BEC_TIME_CASE(7) BEC_TIME_CASE(8) BEC_TIME_CASE(9) BEC_TIME_CASE(10)
+#undef BEC_TIME_CASE
+    default: break;
+  }
+  set_error("unsupported number of time steps");
+  return BEC_EUNSUPPORTED;
+}
+
+}  // namespace
+
+bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale) {
+  const PcTables& t = p->tab;
+  if (fp64)
+    return time_dispatch<double>(p, data, scale, t.es64, t.eis64, t.lamf64, t.mu64, t.time.tw64);
+  return time_dispatch<float>(p, data, scale, t.es32, t.eis32, t.lamf32, t.mu32, t.time.tw32);
+}
+
+}  // namespace bec

@@ -1,0 +1,208 @@
+"""Parity of the CUDA kernels (through the C ABI) with the FP64 CPU oracle, on
+the same seeded inputs, element by element.
+
+Tolerances follow from the arithmetic:
+* the stencil sums 2 dim + 2 terms of size <= (1 + 4c) max|v|, c = tau a/h^2,
+  so |y - y_ref| <= 8 u (1 + 2 dim c) max|v| with u the unit roundoff;
+* P_eps^{-1} is a chain of O(log2(N n^dim)) transform stages followed by the
+  unscaling eps^{-j/N} <= 1/eps, so its max-norm error relative to max|z| is
+  bounded by 16 u log2(N n^dim) / eps (u = 2^-53 for FP64, 2^-24 for FP32);
+* the oracle's banded-LU route solves each B_k = lambda_k I + tau K with a
+  forward error of order u kappa(B_k), kappa from the closed-form eigenvalues
+  lambda_k + tau mu, so comparisons with it add 16 u max_k kappa(B_k).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from workloads import heat_case_1d, heat_case_2d
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2002_01108_gb300 import build
+    build.build()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dev(a):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    _torch().cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def mats(dim, m, a=1.0):
+    K = O.fd_stiffness(dim, m, a)
+    return sp.identity(K.shape[0], format="csr"), K
+
+
+def problem(dim, m, N, **kw):
+    from paper_2002_01108_gb300 import Problem
+    return Problem(dim, m, N, **kw)
+
+
+def pinv_tol(eps, N, m, dim, unit):
+    return 16 * unit * math.log2(N * (m + 1) ** dim) / eps
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def kappa_shifted(dim, m, N, eps):
+    """max_k cond(lambda_k I + tau K) from the closed-form eigenvalues."""
+    mu1 = O.fd_dst_eigs(m)
+    mu = mu1 if dim == 1 else (mu1[:, None] + mu1[None, :]).reshape(-1)
+    lam = O.eps_circulant_eigs(N, eps)
+    d = np.abs(lam[:, None] + mu[None, :] / N)
+    return float(np.max(d.max(axis=1) / d.min(axis=1)))
+
+
+def check_pinv(z, y, dim, m, N, eps, unit):
+    """z against the oracle's sine-transform route (all sizes) and against the
+    plain per-frequency banded LU (when small enough)."""
+    tol = pinv_tol(eps, N, m, dim, unit)
+    assert max_rel(z, O.apply_Pinv_fst(y, dim, 1.0, 1.0 / N, eps)) <= tol
+    if m ** dim <= 4096:
+        M, K = mats(dim, m)
+        ref = O.apply_Pinv_lu(y, M, K, 1.0 / N, eps)
+        assert max_rel(z, ref) <= tol + 16 * U64 * kappa_shifted(dim, m, N, eps)
+    return tol
+
+
+# ------------------------------------------------------------------ L and P_eps
+@pytest.mark.parametrize("dim,m,N", [(1, 63, 64), (1, 3, 2), (2, 3, 2), (2, 7, 4), (2, 31, 16),
+                                     (2, 63, 32)])
+def test_apply_A_matches_assembled_L(dim, m, N):
+    M, K = mats(dim, m)
+    tau = 1.0 / N
+    v = np.random.default_rng(100 + m).uniform(-1, 1, (N,) + (m,) * dim)
+    with problem(dim, m, N) as p:
+        y = host(p.apply_A(dev(v)))
+    ref = (O.assemble_L(N, M, K, tau) @ v.reshape(-1)).reshape(v.shape)
+    c = tau * (m + 1) ** 2
+    assert np.max(np.abs(y - ref)) <= 8 * U64 * (1 + 2 * dim * c) * np.max(np.abs(v))
+
+
+@pytest.mark.parametrize("dim,m,N,eps", [(1, 15, 8, 0.3), (2, 7, 4, 1.0), (2, 31, 16, 1e-4)])
+def test_apply_P_matches_assembled_P(dim, m, N, eps):
+    M, K = mats(dim, m)
+    tau = 1.0 / N
+    v = np.random.default_rng(7).uniform(-1, 1, (N,) + (m,) * dim)
+    with problem(dim, m, N) as p:
+        p.set_eps(eps)
+        y = host(p.apply_P(dev(v)))
+    ref = (O.assemble_P(N, M, K, tau, eps) @ v.reshape(-1)).reshape(v.shape)
+    c = tau * (m + 1) ** 2
+    assert np.max(np.abs(y - ref)) <= 8 * U64 * (1 + 2 * dim * c) * np.max(np.abs(v))
+
+
+def test_build_rhs_matches_oracle():
+    case = heat_case_2d(seed=2, m=31, N=16)
+    with problem(2, 31, 16) as p:
+        f = host(p.build_rhs(dev(case.u0), dev(case.fsrc)))
+    ref = O.build_rhs(case.u0, case.fsrc, case.tau)
+    assert np.max(np.abs(f - ref)) <= 2 * U64 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------------------ P_eps^{-1}
+_PINV = [
+    (1, 3, 2, 1.0), (1, 63, 64, 0.0625), (1, 1023, 4, 0.5), (1, 7, 1024, 0.01),
+    (2, 3, 2, 0.5), (2, 7, 4, 1e-4), (2, 15, 16, 0.25), (2, 31, 8, 1.0), (2, 63, 64, 0.0625),
+    (2, 127, 32, 1e-2), (2, 255, 8, 0.1), (2, 511, 2, 0.7), (2, 15, 512, 0.05),
+]
+
+
+@pytest.mark.parametrize("dim,m,N,eps", _PINV)
+def test_apply_Pinv_fp64_matches_oracle(dim, m, N, eps):
+    y = np.random.default_rng(1000 + N + m).uniform(-1, 1, (N,) + (m,) * dim)
+    with problem(dim, m, N) as p:
+        p.set_eps(eps)
+        z = host(p.apply_Pinv(dev(y)))
+    check_pinv(z, y, dim, m, N, eps, U64)
+
+
+@pytest.mark.parametrize("dim,m,N,eps", [(1, 63, 64, 0.0625), (2, 15, 16, 0.25), (2, 63, 64, 0.0625),
+                                         (2, 127, 32, 1e-2), (2, 7, 4, 1e-4)])
+def test_apply_Pinv_fp32_within_single_precision_bound(dim, m, N, eps):
+    y = np.random.default_rng(2000 + N + m).uniform(-1, 1, (N,) + (m,) * dim)
+    with problem(dim, m, N, precision="fp32") as p:
+        p.set_eps(eps)
+        z = host(p.apply_Pinv(dev(y)))
+    check_pinv(z, y, dim, m, N, eps, U32)
+    assert max_rel(z, O.apply_Pinv_fst(y, dim, 1.0, 1.0 / N, eps)) > 1e-12   # really single precision
+
+
+def test_apply_Pinv_in_place_equals_out_of_place():
+    y = np.random.default_rng(3).uniform(-1, 1, (16, 31, 31))
+    with problem(2, 31, 16) as p:
+        p.set_eps(0.1)
+        yd = dev(y)
+        z = host(p.apply_Pinv(yd))
+        p.apply_Pinv(yd, yd)
+        assert np.array_equal(host(yd), z)
+
+
+def test_apply_Pinv_eps_one_is_block_circulant():
+    """eps = 1 gives the block circulant preconditioner (Sec. 3)."""
+    dim, m, N = 2, 7, 8
+    y = np.random.default_rng(4).uniform(-1, 1, (N, m, m))
+    M, K = mats(dim, m)
+    with problem(dim, m, N) as p:
+        p.set_eps(1.0)
+        z = host(p.apply_Pinv(dev(y)))
+    P = O.assemble_P(N, M, K, 1.0 / N, 1.0).toarray()
+    ref = np.linalg.solve(P, y.reshape(-1)).reshape(y.shape)
+    assert max_rel(z, ref) <= pinv_tol(1.0, N, m, dim, U64)
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.0625, 1e-4])
+def test_apply_Pinv_full_size_2d_255_N256(eps):
+    """The benchmark size (255 x 255 x 256 = 16.6M unknowns): full element-wise
+    comparison with the oracle's sine-transform route, and the residual
+    ||P_eps z - y|| / ||y|| through the GPU's own P_eps stencil."""
+    case = heat_case_2d(seed=2, m=255, N=256, eps=eps)
+    y = case.fsrc
+    with problem(2, 255, 256) as p:
+        p.set_eps(eps)
+        yd = dev(y)
+        zd = p.apply_Pinv(yd)
+        r = p.apply_P(zd)
+        z = host(zd)
+        res = float(np.linalg.norm(host(r) - y) / np.linalg.norm(y))
+    tol = pinv_tol(eps, 256, 255, 2, U64)
+    assert res <= tol
+    ref = O.apply_Pinv_fst(y, 2, 1.0, case.tau, eps)
+    assert max_rel(z, ref) <= tol
+
+
+def test_invalid_calls_return_einval():
+    from paper_2002_01108_gb300 import BecError
+    torch = _torch()
+    with problem(2, 7, 4) as p:
+        y = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+        with pytest.raises(BecError) as e:
+            p.apply_Pinv(y)              # eps not set
+        assert e.value.status == 1
+        for bad in (0.0, -0.5, 1.5, float("nan")):
+            with pytest.raises(BecError):
+                p.set_eps(bad)
+        p.set_eps(0.5)
+        with pytest.raises(BecError):
+            p.apply_A(y, y)              # overlapping

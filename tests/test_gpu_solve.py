@@ -1,0 +1,169 @@
+"""GMRES / FGMRES on the GPU (through the C ABI) against the oracle: the
+all-at-once solution must equal sequential backward-Euler stepping (Sec. 2),
+the stopping rules of Sec. 5 must hold, and the iteration counts of left
+preconditioned GMRES must equal the oracle's."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from workloads import heat_case_1d, heat_case_2d
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2002_01108_gb300 import build
+    build.build()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def problem(case, **kw):
+    from paper_2002_01108_gb300 import Problem
+    p = Problem(case.dim, case.m, case.N, T=case.T, **kw)
+    p.set_eps(case.eps)
+    return p
+
+
+def oracle_solution(case):
+    K = O.fd_stiffness(case.dim, case.m, case.a)
+    M = sp.identity(K.shape[0], format="csr")
+    f = O.build_rhs(case.u0, case.fsrc, case.tau)
+    return f, O.timestep_solve(f, M, K, case.tau), M, K
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_gmres_1d_m63_N64_matches_time_stepping():
+    """1D heat, m = 63, N = 64, eps = sqrt(tau)/2, GMRES(30), tol 1e-10."""
+    case = heat_case_1d(seed=1)
+    f, u_ref, _, _ = oracle_solution(case)
+    with problem(case) as p:
+        fd = dev(f)
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-10)
+        assert info["converged"] == 1 and info["true_relres"] <= 1e-10 * (1 + 1e-6)
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-13)
+        assert rel2(host(u), u_ref) <= 1e-10
+
+
+def test_gmres_left_preconditioned_iterations_equal_oracle():
+    """Left preconditioning and the stopping rule of Sec. 5 (tol 1e-7 on the
+    preconditioned residual): the GPU takes as many iterations as the oracle."""
+    case = heat_case_2d(seed=9, m=31, N=32, eps=0.05)
+    f, u_ref, M, K = oracle_solution(case)
+    L = O.assemble_L(case.N, M, K, case.tau)
+    for eps_case, tol in ((case.eps, 1e-7), (1.0, 1e-7), (case.eps, 1e-12)):
+        Minv = lambda v, e=eps_case: O.apply_Pinv_fst(v.reshape(f.shape), 2, 1.0, case.tau, e).reshape(-1)
+        _, oinfo = O.gmres(lambda v: L @ v, f.reshape(-1), Minv, restart=50, tol=tol)
+        with problem(case, max_restart=50) as p:
+            p.set_eps(eps_case)
+            u, info = p.gmres_solve(dev(f), restart=50, rtol=tol, left_pc=True)
+        assert info["iters"] == oinfo["iters"], (eps_case, tol, info, oinfo["iters"])
+
+
+def test_fgmres_fp32_preconditioner_reaches_fp64_accuracy():
+    """FP32 P_eps^{-1} inside FP64 flexible GMRES reaches the FP64 tolerance."""
+    case = heat_case_2d(seed=3, m=63, N=64)
+    f, u_ref, _, _ = oracle_solution(case)
+    with problem(case, precision="fp32", flexible=True, max_restart=20) as p:
+        u, info = p.gmres_solve(dev(f), restart=20, rtol=1e-8, flexible=True)
+        assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8
+        u, info = p.gmres_solve(dev(f), restart=20, rtol=1e-13, flexible=True)
+        assert rel2(host(u), u_ref) <= 1e-9
+
+
+def test_gmres_2d_255_N256_benchmark_size():
+    """The benchmark workload (255^2 x 256, eps = sqrt(tau)): RES <= 1e-8 at the
+    benchmark tolerance, and the solution equals sequential stepping to 1e-8
+    when solved to 1e-13."""
+    case = heat_case_2d(seed=2, m=255, N=256, eps=1.0 / 16)
+    f, u_ref, _, _ = oracle_solution(case)
+    with problem(case) as p:
+        fd = dev(f)
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-8)
+        assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-13)
+        assert rel2(host(u), u_ref) <= 1e-8
+
+
+def test_fgmres_fp32_benchmark_size():
+    case = heat_case_2d(seed=2, m=255, N=256, eps=1.0 / 16)
+    f, u_ref, _, _ = oracle_solution(case)
+    with problem(case, precision="fp32", flexible=True, max_restart=20) as p:
+        u, info = p.gmres_solve(dev(f), restart=20, rtol=1e-8, flexible=True)
+        assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8
+        assert rel2(host(u), u_ref) <= 1e-6
+
+
+def test_solve_is_bitwise_reproducible():
+    case = heat_case_2d(seed=5, m=63, N=32, eps=0.1)
+    f, _, _, _ = oracle_solution(case)
+    with problem(case) as p:
+        fd = dev(f)
+        a, ia = p.gmres_solve(fd, rtol=1e-12)
+        b, ib = p.gmres_solve(fd, rtol=1e-12)
+        assert np.array_equal(host(a), host(b)) and ia == ib
+
+
+def test_host_buffer_solve_equals_device_solve():
+    import torch
+    case = heat_case_2d(seed=6, m=63, N=32, eps=0.1)
+    f, _, _, _ = oracle_solution(case)
+    with problem(case, host_io=True) as p:
+        ud, _ = p.gmres_solve(dev(f), rtol=1e-10)
+        fh = torch.from_numpy(f.copy()).pin_memory()
+        uh, info = p.gmres_solve_host(fh, rtol=1e-10)
+        assert np.array_equal(uh.numpy(), host(ud))
+
+
+def test_restarts_maxit_and_initial_guess():
+    case = heat_case_2d(seed=7, m=31, N=16, eps=0.5)
+    f, u_ref, _, _ = oracle_solution(case)
+    with problem(case, max_restart=4) as p:
+        fd = dev(f)
+        u, info = p.gmres_solve(fd, restart=2, rtol=1e-12, maxit=200)
+        assert info["converged"] == 1 and info["restarts"] >= 1
+        assert rel2(host(u), u_ref) <= 1e-9
+        u2, info2 = p.gmres_solve(fd, restart=2, rtol=1e-14, maxit=1)
+        assert info2["converged"] == 0 and info2["iters"] == 1
+        u3, info3 = p.gmres_solve(fd, u=dev(u_ref), restart=2, rtol=1e-8, use_x0=True)
+        assert info3["iters"] == 0 and info3["converged"] == 1
+
+
+def test_zero_and_nonfinite_right_hand_sides():
+    import torch
+    from paper_2002_01108_gb300 import BecError
+    case = heat_case_2d(seed=8, m=15, N=8, eps=0.5)
+    with problem(case) as p:
+        z = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+        u, info = p.gmres_solve(z)
+        assert info["converged"] == 1 and float(u.abs().max()) == 0.0
+        bad = torch.ones(p.shape, dtype=torch.float64, device="cuda")
+        bad[0, 0, 0] = float("nan")
+        with pytest.raises(BecError) as e:
+            p.gmres_solve(bad)
+        assert e.value.status == 5
+
+
+def test_kernel_launches_are_counted():
+    case = heat_case_2d(seed=8, m=15, N=8, eps=0.5)
+    f, _, _, _ = oracle_solution(case)
+    with problem(case) as p:
+        before = p.launches
+        p.gmres_solve(dev(f), rtol=1e-8)
+        assert p.launches > before
