@@ -156,6 +156,33 @@ bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host,
 bec_status bec_true_relres(bec_problem* p, const double* f, const double* u,
                            double* out);
 
+/* RES = ||f - L u||_2 / ||f||_2 for the problem (dim, nx, N, T, a) of
+ * bec_allocate_problem, WITHOUT allocating anything and without a problem
+ * object.  The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory at the point where they check a solution -- device
+ * memory owned by another allocator (a framework's caching pool), a memory
+ * budget fixed at start-up, a no-allocation-after-initialisation policy, or
+ * a device that is nearly full.
+ *  - f, u: device vectors of U = N * J doubles ([N][ny][nx]); res_out: one
+ *    device double that receives RES.  All owned by the caller; the result
+ *    is written asynchronously on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream), so synchronise before reading it.
+ *  - Scratch: the block partial sums live in a file-scope device array of
+ *    16384 pairs of doubles (256 KiB) that every GPU which loads the library
+ *    holds until the process exits.  Sizes with ceil(J/256) * ceil(N/8) >
+ *    16384 (about 33.5M unknowns) are rejected with BEC_EINVAL and a message
+ *    in bec_last_error(); so are the size rules of bec_allocate_problem.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  No cudaMalloc, cudaFree or allocating
+ *    library routine is called.
+ *  - Every call shares the array and leaves its partial sums there; each
+ *    call writes every slot it reads, so nothing needs clearing, but calls
+ *    that overlap on the GPU (e.g. on two streams at once) race on it. */
+bec_status bec_relres_noalloc(int dim, int nx, int N, double T, double a,
+                              const double* f, const double* u, double* res_out,
+                              void* stream);
+
 /* Releases the workspace; p may be NULL. */
 bec_status bec_free_problem(bec_problem* p);
 

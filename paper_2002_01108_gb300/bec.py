@@ -24,7 +24,7 @@ EXPORTED = (
     "bec_allocate_problem", "bec_set_eps", "bec_apply_A", "bec_apply_P", "bec_apply_Pinv",
     "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_true_relres",
     "bec_free_problem", "bec_problem_size", "bec_kernel_launches", "bec_status_string",
-    "bec_last_error", "bec_profile_start", "bec_profile_stop",
+    "bec_last_error", "bec_profile_start", "bec_profile_stop", "bec_relres_noalloc",
 )
 
 
@@ -89,6 +89,8 @@ def _lib():
         "bec_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "bec_last_error": ([], ctypes.c_char_p),
         "bec_profile_start": ([P, ctypes.c_int], ctypes.c_int),
+        "bec_relres_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, D, D, D, P], ctypes.c_int),
         "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     }
