@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--form", choices=("fp64", "fp32"), default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32"), default=None,
+                    help="run a small bounded case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -352,8 +354,39 @@ def run_gpu(args):
     return 0
 
 
+def run_ncu_case(which: str):
+    """A bounded workload for profiler captures: the benchmark problem with a
+    two-vector Krylov basis (under 1 GB on the device), three P_eps^{-1}
+    applies and two stencil applies, or one short FGMRES solve."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2002_01108_gb300 import Problem
+    from paper_2002_01108_gb300 import build as bec_build
+    from workloads import heat_case_2d
+    bec_build.build()
+    case = heat_case_2d(seed=2, m=M_SIDE, N=N_STEPS, eps=EPS)
+    form = "fp64" if which == "pinv_fp64" else "fp32"
+    with Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=2, flexible=form == "fp32") as p:
+        p.set_eps(EPS)
+        f = p.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
+        if which == "solve_fp32":
+            p.gmres_solve(f, restart=2, maxit=2, rtol=RTOL, flexible=True)
+        else:
+            z = torch.empty_like(f)
+            for _ in range(3):
+                p.apply_Pinv(f, z)
+            y = torch.empty_like(f)
+            for _ in range(2):
+                p.apply_A(z, y)
+        torch.cuda.synchronize()
+    print(f"ncu case {which} done")
+    return 0
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        return run_ncu_case(args.ncu_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
