@@ -101,7 +101,7 @@ void free_all(bec_problem* p) {
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
                   p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
-                  p->sn, p->g, p->ycoef, p->scal, p->io_f, p->io_u};
+                  p->sn, p->g, p->ycoef, p->sigma, p->scal, p->io_f, p->io_u};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->host_scal) cudaFreeHost(p->host_scal);
@@ -131,8 +131,9 @@ bec_status read_scalars(bec_problem* p) {
     if (_s != BEC_OK) return _s;       \
   } while (0)
 
-// z = P_eps^{-1} y (no argument checks)
-bec_status apply_pinv(bec_problem* p, const double* y, double* z) {
+// z = P_eps^{-1} (s y) with s = *scale_dev (1 if null); no argument checks
+bec_status apply_pinv(bec_problem* p, const double* y, double* z,
+                      const double* scale_dev = nullptr) {
   const int fp64 = p->desc.precision == BEC_PC_FP64;
   const double n = (double)(p->m + 1);
   const double per_axis = (2.0 / n) / 16.0;   // (orthonormal / raw)^2 for one forward+inverse pair
@@ -141,14 +142,14 @@ bec_status apply_pinv(bec_problem* p, const double* y, double* z) {
   if (fp64) {
     BEC_TRY(launch_dst_rows(p, y, 1, z, 1, rows, 1));
     if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
-    BEC_TRY(launch_time_pass(p, z, 1, scale));
+    BEC_TRY(launch_time_pass(p, z, 1, scale, scale_dev));
     if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
     BEC_TRY(launch_dst_rows(p, z, 1, z, 1, rows, 1));
   } else {
     void* s = p->pc_scratch;
     BEC_TRY(launch_dst_rows(p, y, 1, s, 0, rows, 0));
     if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
-    BEC_TRY(launch_time_pass(p, s, 0, scale));
+    BEC_TRY(launch_time_pass(p, s, 0, scale, scale_dev));
     if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
     BEC_TRY(launch_dst_rows(p, s, 0, z, 1, rows, 0));
   }
@@ -174,7 +175,12 @@ bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmre
   const int R = o->restart;
   const bool left = o->left_pc != 0;
   const bool flex = o->flexible != 0;
-  double* V = p->V;
+  // Basis vectors are addressed through a pointer list: with x0 = 0 and right
+  // preconditioning the first one is the caller's f itself (read only).
+  std::vector<const double*> Vp(R + 1), Zp(R);
+  for (int i = 0; i <= R; ++i) Vp[i] = p->V + (long long)i * U;
+  for (int i = 0; i < R && flex; ++i) Zp[i] = p->Z + (long long)i * U;
+  double* sigma = p->sigma;
 
   // reference norm: ||f|| (right) or ||P^{-1} f|| (left)
   if (left) {
@@ -202,15 +208,27 @@ bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmre
   int iters = 0, restarts = 0;
   bool converged = false, x_nonzero = o->use_x0 != 0;
   double monitored = 1.0;
+  double* h1 = p->hcol;
+  double* h2 = p->hcol + (p->max_restart + 2);
   while (true) {
-    if (x_nonzero)
-      BEC_TRY(launch_residual(p, f, u, V));
-    else
-      BEC_TRY(launch_copy(p, f, V));
-    if (left) BEC_TRY(apply_pinv(p, V, V));
-    BEC_TRY(launch_norm(p, V, S_BETA));
-    BEC_TRY(read_scalars(p));
-    const double beta = p->host_scal[S_BETA];
+    // r0, stored unnormalised in V_0 (sigma_0 = 1 / ||r0|| set by gmres_start)
+    int beta_slot = S_BETA;
+    if (x_nonzero) {
+      BEC_TRY(launch_residual(p, f, u, p->V));
+      Vp[0] = p->V;
+    } else if (!left) {
+      Vp[0] = f;
+      beta_slot = S_REF;
+    } else {
+      Vp[0] = p->V;
+    }
+    if (left) BEC_TRY(apply_pinv(p, x_nonzero ? p->V : f, p->V));
+    double beta = ref;
+    if (beta_slot == S_BETA) {
+      BEC_TRY(launch_norm(p, Vp[0], S_BETA));
+      BEC_TRY(read_scalars(p));
+      beta = p->host_scal[S_BETA];
+    }
     if (!std::isfinite(beta)) {
       set_error("NaN or Inf in the GMRES residual");
       return BEC_ENUMERIC;
@@ -221,28 +239,24 @@ bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmre
       break;
     }
     if (iters >= o->maxit) break;
-    BEC_TRY(launch_scale_by_inv(p, V, V, S_BETA));
-    BEC_TRY(launch_gmres_start(p, S_BETA));
+    BEC_TRY(launch_gmres_start(p, beta_slot));
     int k = 0;
-    double* h1 = p->hcol;
-    double* h2 = p->hcol + (p->max_restart + 2);
     for (int j = 0; j < R; ++j) {
-      const double* vj = V + (long long)j * U;
       if (left) {
-        BEC_TRY(launch_apply_L(p, vj, p->t, 0.0));
+        BEC_TRY(launch_apply_L(p, Vp[j], p->t, 0.0, sigma + j));
         BEC_TRY(apply_pinv(p, p->t, p->w));
+        BEC_TRY(launch_dots(p, p->w, Vp.data(), j + 1, sigma, h1));
       } else {
         double* z = flex ? p->Z + (long long)j * U : p->t;
-        BEC_TRY(apply_pinv(p, vj, z));
-        BEC_TRY(launch_apply_L(p, z, p->w, 0.0));
+        BEC_TRY(apply_pinv(p, Vp[j], z, sigma + j));
+        BEC_TRY(launch_stencil_dots(p, z, p->w, Vp.data(), j + 1, sigma, h1));
       }
-      // classical Gram-Schmidt, twice
-      BEC_TRY(launch_mdot(p, V, j + 1, p->w, h1));
-      BEC_TRY(launch_maxpy(p, p->w, V, j + 1, h1, -1.0, -1));
-      BEC_TRY(launch_mdot(p, V, j + 1, p->w, h2));
-      BEC_TRY(launch_maxpy(p, p->w, V, j + 1, h2, -1.0, S_W));
+      // classical Gram-Schmidt, second pass fused with the first update
+      BEC_TRY(launch_update_dots(p, p->w, Vp.data(), j + 1, sigma, h1, h2));
+      double* vnext = p->V + (long long)(j + 1) * U;
+      BEC_TRY(launch_combine(p, vnext, p->w, Vp.data(), j + 1, sigma, h2, -1.0, S_W));
+      Vp[j + 1] = vnext;
       BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES));
-      BEC_TRY(launch_scale_by_inv(p, p->w, V + (long long)(j + 1) * U, S_W));
       ++iters;
       k = j + 1;
       BEC_TRY(read_scalars(p));
@@ -260,14 +274,14 @@ bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmre
     }
     BEC_TRY(launch_least_squares(p, k));
     if (left) {
-      BEC_TRY(launch_maxpy(p, u, V, k, p->ycoef, 1.0, -1));
+      BEC_TRY(launch_combine(p, u, u, Vp.data(), k, sigma, p->ycoef, 1.0, -1));
     } else if (flex) {
-      BEC_TRY(launch_maxpy(p, u, p->Z, k, p->ycoef, 1.0, -1));
+      BEC_TRY(launch_combine(p, u, u, Zp.data(), k, nullptr, p->ycoef, 1.0, -1));
     } else {
-      BEC_TRY(launch_zero(p, p->t));
-      BEC_TRY(launch_maxpy(p, p->t, V, k, p->ycoef, 1.0, -1));
+      BEC_TRY(launch_combine(p, p->t, nullptr, Vp.data(), k, sigma, p->ycoef, 1.0, -1));
       BEC_TRY(apply_pinv(p, p->t, p->w));
-      BEC_TRY(launch_maxpy(p, u, p->w, 1, p->scal + S_ONE, 1.0, -1));
+      const double* wl[1] = {p->w};
+      BEC_TRY(launch_combine(p, u, u, wl, 1, nullptr, p->scal + S_ONE, 1.0, -1));
     }
     x_nonzero = true;
     if (converged || iters >= o->maxit) break;
@@ -347,7 +361,9 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   t.time.n = N;
   t.time.logn = ilog2(N);
   const long long U = p->U;
-  const long long parts = std::max<long long>(32LL * kReduceBlocks, 2 * stencil_blocks(p));
+  const long long parts = std::max<long long>(
+      std::max<long long>((long long)kMaxVec * kReduceBlocks, (long long)kMaxVec * kStencilDotBlocks),
+      2 * stencil_blocks(p));
   bec_status s = BEC_OK;
   auto chain = [&](bec_status r) {
     if (s == BEC_OK) s = r;
@@ -382,6 +398,7 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&p->sn, (size_t)R));
   chain(dmalloc(&p->g, (size_t)R + 1));
   chain(dmalloc(&p->ycoef, (size_t)R));
+  chain(dmalloc(&p->sigma, (size_t)R + 1));
   chain(dmalloc(&p->scal, (size_t)kScalSlots));
   if (d->host_io) {
     chain(dmalloc(&p->io_f, (size_t)U));

@@ -72,6 +72,7 @@ struct bec_problem {
   double* sn = nullptr;         // Givens sines
   double* g = nullptr;          // rotated right-hand side (max_restart + 1)
   double* ycoef = nullptr;      // least-squares solution (max_restart)
+  double* sigma = nullptr;      // 1 / ||stored V_i||: V_i is kept unnormalised (max_restart + 1)
   double* scal = nullptr;       // device scalars (norms, residual estimate)
   double* host_scal = nullptr;  // pinned mirror of scal
   double* io_f = nullptr;       // host_io staging
@@ -82,8 +83,15 @@ struct bec_problem {
 namespace bec {
 
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs: fixed => deterministic sums
+constexpr int kStencilDotBlocks = 1216;  // 8 x 152: fused stencil + dots grid
 constexpr int kScalSlots = 16;
 constexpr int kMaxRestart = 60;
+constexpr int kMaxVec = 32;          // vectors one fused Krylov launch handles
+
+// Krylov basis vectors handed to a kernel by value.
+struct VecList {
+  const double* v[kMaxVec];
+};
 
 // ---- error plumbing
 void set_error(const std::string& msg);
@@ -113,15 +121,22 @@ bec_status launch_dst_rows(bec_problem* p, const void* in, int in_fp64,
 // DST-I (same scaling) along y of every [ny][nx] slice, in place.
 bec_status launch_dst_cols(bec_problem* p, void* data, int fp64);
 // Time pass: scale, FFT over N, divide by the shifted eigenvalues, inverse
-// FFT, unscale, for every spatial mode, in place.
-bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale);
+// FFT, unscale, for every spatial mode, in place.  The divide is multiplied by
+// `scale` and, when scale_dev is not null, by the device scalar *scale_dev.
+bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
+                            const double* scale_dev);
 
 // ---- stencils (bec_stencil.cu)
 // number of blocks (partial sums) the residual-norm kernel writes
 long long stencil_blocks(const bec_problem* p);
-// y = L v; with corner != 0, y = P_eps v (adds -corner * v^N to slice 1).
+// y = L v; with corner != 0, y = P_eps v (adds -corner * v^N to slice 1);
+// with out_scale != null the result is multiplied by the device scalar.
 bec_status launch_apply_L(bec_problem* p, const double* v, double* y,
-                          double corner);
+                          double corner, const double* out_scale = nullptr);
+// w = L z and hout[i] = sigma_i <V_i, w> for i < nv in one pass over z, w, V.
+bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
+                               const double* const* V, int nv,
+                               const double* sigma, double* hout);
 bec_status launch_build_rhs(bec_problem* p, const double* u0,
                             const double* fsrc, double* f);
 // partials[b] = sum over block b of (f - L u)^2, partials[B + b] = sum f^2;
@@ -132,24 +147,33 @@ bec_status launch_residual_norms(bec_problem* p, const double* f,
 bec_status launch_residual(bec_problem* p, const double* f, const double* u,
                            double* r);
 
-// ---- Krylov BLAS (bec_krylov.cu)
-// hcol[i] = <V_i, w>, i < nv, V_i = Vb + i U.
-bec_status launch_mdot(bec_problem* p, const double* Vb, int nv,
-                       const double* w, double* hcol);
-// w -= sum_i hcol[i] V_i (i < nv); if norm_slot >= 0 also scal[slot] = ||w||.
-bec_status launch_maxpy(bec_problem* p, double* w, const double* Vb, int nv,
-                        const double* coef, double sign, int norm_slot);
+// ---- Krylov BLAS (bec_krylov.cu).  V is a host array of nv device
+// pointers; sigma (device, may be null = all ones) scales V_i.
+// hout[i] = sigma_i <V_i, w>
+bec_status launch_dots(bec_problem* p, const double* w, const double* const* V,
+                       int nv, const double* sigma, double* hout);
+// w -= sum_i coef_i sigma_i V_i, then hout[i] = sigma_i <V_i, w>
+bec_status launch_update_dots(bec_problem* p, double* w,
+                              const double* const* V, int nv,
+                              const double* sigma, const double* coef,
+                              double* hout);
+// out = w + sign sum_i coef_i sigma_i V_i (w may be null = 0, out may be w);
+// if norm_slot >= 0 also scal[norm_slot] = ||out||.
+bec_status launch_combine(bec_problem* p, double* out, const double* w,
+                          const double* const* V, int nv, const double* sigma,
+                          const double* coef, double sign, int norm_slot);
+// dots of a finished partial array: hout[i] = sigma_i sum_b partials[i nb + b]
+bec_status launch_finish_dots(bec_problem* p, int nv, int nb,
+                              const double* sigma, double* hout);
 // scal[slot] = ||x||
 bec_status launch_norm(bec_problem* p, const double* x, int slot);
-// y = x * (1 / scal[slot])  (scal read on the device)
-bec_status launch_scale_by_inv(bec_problem* p, const double* x, double* y,
-                               int slot);
 // Hessenberg column j: H(0:j, j) = h1 + h2 (the two Gram-Schmidt passes),
-// H(j+1, j) = scal[norm_slot]; applies the previous rotations, makes
-// rotation j, updates g and writes |g[j+1]| to scal[res_slot].
+// H(j+1, j) = scal[norm_slot] and sigma[j+1] = 1 / H(j+1, j); applies the
+// previous rotations, makes rotation j, updates g and writes |g[j+1]| to
+// scal[res_slot].
 bec_status launch_hessenberg(bec_problem* p, int j, const double* h1,
                              const double* h2, int norm_slot, int res_slot);
-// g[0] = scal[slot]; clears rotations.
+// g = (scal[slot], 0, ...), sigma[0] = 1 / scal[slot].
 bec_status launch_gmres_start(bec_problem* p, int slot);
 // ycoef = H(0:k,0:k)^{-1} g(0:k)
 bec_status launch_least_squares(bec_problem* p, int k);

@@ -29,10 +29,10 @@ __device__ __forceinline__ double apply_row(const double* __restrict__ vs, long 
   return g.cdiag * center - g.c * nb;
 }
 
-// y = L v (corner = 0) or y = P_eps v (corner = eps).
+// y = L v (corner = 0) or y = P_eps v (corner = eps), times *out_scale if given.
 __global__ void __launch_bounds__(kStencilThreads)
 apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom g,
-               double corner) {
+               double corner, const double* __restrict__ out_scale) {
   const long long q = (long long)blockIdx.x * kStencilThreads + threadIdx.x;
   if (q >= g.J) return;
   const int n0 = blockIdx.y * kTimeChunk;
@@ -41,11 +41,61 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
   const int ix = (int)(q - (long long)iy * g.m);
   double prev = n0 > 0 ? v[(long long)(n0 - 1) * g.J + q]
                        : (corner != 0.0 ? corner * v[(long long)(g.N - 1) * g.J + q] : 0.0);
+  const double sc = out_scale ? out_scale[0] : 1.0;
   for (int n = n0; n < n1; ++n) {
     const double* vs = v + (long long)n * g.J;
     const double center = vs[q];
-    y[(long long)n * g.J + q] = apply_row(vs, q, ix, iy, g, center) - prev;
+    const double r = apply_row(vs, q, ix, iy, g, center) - prev;
+    y[(long long)n * g.J + q] = out_scale ? sc * r : r;
     prev = center;
+  }
+}
+
+// w = L z and, for v < NV, the block sums of V_v . w: the first Gram-Schmidt
+// pass fused with the operator.  A fixed grid walks the (256-point tile, time
+// chunk) pairs in a fixed order, so the partial sums are reproducible.
+template <int NV>
+__global__ void __launch_bounds__(kStencilThreads)
+stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, StencilGeom g, VecList V,
+                    double* __restrict__ partials) {
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  const long long jt = (g.J + kStencilThreads - 1) / kStencilThreads;
+  const long long tiles = jt * ((g.N + kTimeChunk - 1) / kTimeChunk);
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const long long q = (t % jt) * kStencilThreads + threadIdx.x;
+    if (q >= g.J) continue;
+    const int n0 = (int)(t / jt) * kTimeChunk;
+    const int n1 = min(g.N, n0 + kTimeChunk);
+    const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
+    const int ix = (int)(q - (long long)iy * g.m);
+    double prev = n0 > 0 ? z[(long long)(n0 - 1) * g.J + q] : 0.0;
+    for (int n = n0; n < n1; ++n) {
+      const double* zs = z + (long long)n * g.J;
+      const double center = zs[q];
+      const long long o = (long long)n * g.J + q;
+      const double y = apply_row(zs, q, ix, iy, g, center) - prev;
+      w[o] = y;
+      prev = center;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fma(V.v[v][o], y, acc[v]);
+    }
+  }
+  __shared__ double red[kStencilThreads / 32][NV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = acc[v];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) red[warp][v] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < kStencilThreads / 32; ++wi) s += red[wi][threadIdx.x];
+    partials[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -178,11 +228,43 @@ long long stencil_blocks(const bec_problem* p) {
   return (long long)g.x * g.y;
 }
 
-bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double corner) {
+bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double corner,
+                          const double* out_scale) {
   BEC_LAUNCH_BEGIN(p);
-  apply_L_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner);
+  apply_L_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
+                                                                     out_scale);
   BEC_LAUNCH_CHECK(p, "apply_L_kernel");
   return BEC_OK;
+}
+
+bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
+                               const double* const* V, int nv, const double* sigma,
+                               double* hout) {
+  const int n = nv < kMaxVec ? nv : kMaxVec;
+  VecList L;
+  for (int i = 0; i < kMaxVec; ++i) L.v[i] = i < n ? V[i] : V[0];
+  BEC_LAUNCH_BEGIN(p);
+  switch (n) {
+#define BEC_SD_CASE(NV)                                                                     \
+  case NV:                                                                                  \
+    stencil_dots_kernel<NV><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(          \
+        z, w, geom(p), L, p->partials);                                                     \
+    break;
+    BEC_SD_CASE(1) BEC_SD_CASE(2) BEC_SD_CASE(3) BEC_SD_CASE(4) BEC_SD_CASE(5) BEC_SD_CASE(6)
+    BEC_SD_CASE(7) BEC_SD_CASE(8) BEC_SD_CASE(9) BEC_SD_CASE(10) BEC_SD_CASE(11) BEC_SD_CASE(12)
+    BEC_SD_CASE(13) BEC_SD_CASE(14) BEC_SD_CASE(15) BEC_SD_CASE(16) BEC_SD_CASE(17)
+    BEC_SD_CASE(18) BEC_SD_CASE(19) BEC_SD_CASE(20) BEC_SD_CASE(21) BEC_SD_CASE(22)
+    BEC_SD_CASE(23) BEC_SD_CASE(24) BEC_SD_CASE(25) BEC_SD_CASE(26) BEC_SD_CASE(27)
+    BEC_SD_CASE(28) BEC_SD_CASE(29) BEC_SD_CASE(30) BEC_SD_CASE(31) BEC_SD_CASE(32)
+#undef BEC_SD_CASE
+    default: return BEC_EINVAL;
+  }
+  BEC_LAUNCH_CHECK(p, "stencil_dots_kernel");
+  bec_status s = launch_finish_dots(p, n, kStencilDotBlocks, sigma, hout);
+  if (s != BEC_OK || nv <= kMaxVec) return s;
+  // more vectors than one fused launch holds: the rest as plain dots
+  return launch_dots(p, w, V + kMaxVec, nv - kMaxVec, sigma ? sigma + kMaxVec : nullptr,
+                     hout + kMaxVec);
 }
 
 bec_status launch_residual(bec_problem* p, const double* f, const double* u, double* r) {

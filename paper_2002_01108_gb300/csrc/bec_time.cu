@@ -36,8 +36,10 @@ template <typename T, int LOGN>
 __global__ void __launch_bounds__(time_warps<T>() * 32)
 time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
-                 const T* __restrict__ mu1, T tau, T scale, const v2_t<T>* __restrict__ tw) {
+                 const T* __restrict__ mu1, T tau, T scale_h, const double* __restrict__ scale_dev,
+                 const v2_t<T>* __restrict__ tw) {
   using V = v2_t<T>;
+  const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
   constexpr int N = 1 << LOGN;
   constexpr int LSC = N + 1;
   constexpr int WARPS = time_warps<T>();
@@ -96,8 +98,9 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
 }
 
 template <typename T, int LOGN>
-bec_status time_launch(bec_problem* p, void* data, double scale, const T* es, const T* eis,
-                       const v2_t<T>* lamf, const T* mu1, const v2_t<T>* tw) {
+bec_status time_launch(bec_problem* p, void* data, double scale, const double* scale_dev,
+                       const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                       const v2_t<T>* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int warps = time_warps<T>();
   const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T);
@@ -108,17 +111,18 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const T* es, co
   const unsigned grid = (unsigned)((p->J + W - 1) / W);
   BEC_LAUNCH_BEGIN(p);
   k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->J, p->m, p->dim, es, eis,
-                                           lamf, mu1, (T)p->tau, (T)scale, tw);
+                                           lamf, mu1, (T)p->tau, (T)scale, scale_dev, tw);
   BEC_LAUNCH_CHECK(p, "time_pass_kernel");
   return BEC_OK;
 }
 
 template <typename T>
-bec_status time_dispatch(bec_problem* p, void* data, double scale, const T* es, const T* eis,
-                         const v2_t<T>* lamf, const T* mu1, const v2_t<T>* tw) {
+bec_status time_dispatch(bec_problem* p, void* data, double scale, const double* scale_dev,
+                         const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                         const v2_t<T>* tw) {
   switch (p->tab.time.logn) {
 #define BEC_TIME_CASE(L) \
-  case L: return time_launch<T, L>(p, data, scale, es, eis, lamf, mu1, tw);
+  case L: return time_launch<T, L>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw);
     BEC_TIME_CASE(1) BEC_TIME_CASE(2) BEC_TIME_CASE(3) BEC_TIME_CASE(4) BEC_TIME_CASE(5)
     BEC_TIME_CASE(6) BEC_TIME_CASE(7) BEC_TIME_CASE(8) BEC_TIME_CASE(9) BEC_TIME_CASE(10)
 #undef BEC_TIME_CASE
@@ -130,11 +134,14 @@ bec_status time_dispatch(bec_problem* p, void* data, double scale, const T* es, 
 
 }  // namespace
 
-bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale) {
+bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
+                            const double* scale_dev) {
   const PcTables& t = p->tab;
   if (fp64)
-    return time_dispatch<double>(p, data, scale, t.es64, t.eis64, t.lamf64, t.mu64, t.time.tw64);
-  return time_dispatch<float>(p, data, scale, t.es32, t.eis32, t.lamf32, t.mu32, t.time.tw32);
+    return time_dispatch<double>(p, data, scale, scale_dev, t.es64, t.eis64, t.lamf64, t.mu64,
+                                 t.time.tw64);
+  return time_dispatch<float>(p, data, scale, scale_dev, t.es32, t.eis32, t.lamf32, t.mu32,
+                              t.time.tw32);
 }
 
 }  // namespace bec
