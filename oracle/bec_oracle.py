@@ -34,6 +34,7 @@ __all__ = [
     "fourier_matrix", "eps_scaling", "eps_circulant_eigs", "dst_matrix", "fd_dst_eigs",
     "apply_Pinv_dense", "apply_Pinv_lu", "apply_Pinv_woodbury", "apply_Pinv_fst",
     "gmres", "fgmres", "relative_residual",
+    "mg_prolongation", "MGHierarchy", "mg_vcycle", "apply_Pinv_mg", "node_coefficient",
 ]
 
 #: backward Euler, r_0 = 1, r_1 = -1 (Sec. 4, remark after eq. pstepscheme)
@@ -476,3 +477,87 @@ def relative_residual(L, u: np.ndarray, f: np.ndarray) -> float:
     """RES = ||f - L u||_2 / ||f||_2 (Sec. 5)."""
     fv = f.reshape(-1)
     return float(np.linalg.norm(fv - L @ u.reshape(-1)) / np.linalg.norm(fv))
+
+
+# --------------------------------------------------------------------------
+# Multigrid route for variable coefficients (Sec. 4: "a multigrid method as
+# inner spatial solver"; Sec. 5, Example 2: one V-cycle per shifted system,
+# one pre- and one post-smoothing step, piecewise-linear interpolation and its
+# transpose).  Readings: bilinear prolongation P, restriction R = P^T / 4,
+# Galerkin coarse operators, damped Jacobi (omega = 0.8) in place of ILU.
+# --------------------------------------------------------------------------
+def mg_prolongation(mc: int) -> sp.csr_matrix:
+    """Bilinear interpolation from the (mc x mc) interior grid of spacing 2h to
+    the (2mc+1)^2 fine interior grid, zero Dirichlet data.  1D factor:
+    fine 2i+1 <- coarse i (weight 1), fine 2i <- coarse i-1, i (weights 1/2)."""
+    mf = 2 * mc + 1
+    P1 = sp.lil_matrix((mf, mc))
+    for i in range(mc):
+        P1[2 * i + 1, i] = 1.0
+        P1[2 * i, i] += 0.5
+        P1[2 * i + 2, i] += 0.5
+    P1 = P1.tocsr()
+    return sp.kron(P1, P1).tocsr()
+
+
+class MGHierarchy:
+    """Grids m_0 = m > m_1 = (m-1)/2 > ... > 1, with P_l, R_l = P_l^T/4 and the
+    Galerkin pairs (M_l, K_l): M_0 = I, K_0 = K, M_{l+1} = R_l M_l P_l,
+    K_{l+1} = R_l K_l P_l.  B_k on level l is lambda M_l + tau K_l."""
+
+    def __init__(self, K: sp.spmatrix, m: int):
+        self.sizes = [m]
+        while self.sizes[-1] > 1:
+            self.sizes.append((self.sizes[-1] - 1) // 2)
+        self.P, self.R, self.M, self.K = [], [], [sp.identity(m * m, format="csr")], [K.tocsr()]
+        for l in range(len(self.sizes) - 1):
+            P = mg_prolongation(self.sizes[l + 1])
+            R = (P.T / 4.0).tocsr()
+            self.P.append(P)
+            self.R.append(R)
+            self.M.append((R @ self.M[l] @ P).tocsr())
+            self.K.append((R @ self.K[l] @ P).tocsr())
+
+    def op(self, l: int, lam: complex, tau: float):
+        return (lam * self.M[l] + tau * self.K[l]).tocsr()
+
+
+def mg_vcycle(h: MGHierarchy, lam: complex, tau: float, b: np.ndarray, omega: float = 0.8,
+              nu1: int = 1, nu2: int = 1, l: int = 0, x0=None) -> np.ndarray:
+    """One V-cycle for (lam M_l + tau K_l) x = b from x0 (zero if None): nu1
+    damped-Jacobi sweeps, residual, restriction, recursive coarse correction,
+    prolongation, nu2 sweeps.  The 1 x 1 coarsest grid is solved exactly."""
+    A = h.op(l, lam, tau)
+    if h.sizes[l] == 1:
+        return b / A.toarray()[0, 0]
+    dinv = 1.0 / A.diagonal()
+    x = np.zeros_like(b, dtype=np.complex128) if x0 is None else x0.astype(np.complex128)
+    for _ in range(nu1):
+        x = x + omega * dinv * (b - A @ x)
+    r = b - A @ x
+    ec = mg_vcycle(h, lam, tau, h.R[l] @ r, omega, nu1, nu2, l + 1)
+    x = x + h.P[l] @ ec
+    for _ in range(nu2):
+        x = x + omega * dinv * (b - A @ x)
+    return x
+
+
+def apply_Pinv_mg(y: np.ndarray, h: MGHierarchy, tau: float, eps: float, r=BDF1,
+                  omega: float = 0.8, nu1: int = 1, nu2: int = 1) -> np.ndarray:
+    """Approximate P_eps^{-1} y by the three steps of Sec. 4 with Step 2 done
+    by one V-cycle per shifted system (all N frequencies)."""
+    N = y.shape[0]
+    Y = y.reshape(N, -1).astype(np.float64)
+    d = eps_scaling(N, eps)
+    yt = math.sqrt(N) * np.fft.ifft(d[:, None] * Y, axis=0)          # Step 1
+    lam = eps_circulant_eigs(N, eps, r)
+    zt = np.empty_like(yt)
+    for k in range(N):                                                # Step 2
+        zt[k] = mg_vcycle(h, lam[k], tau, yt[k], omega, nu1, nu2)
+    z = (np.fft.fft(zt, axis=0) / math.sqrt(N)) / d[:, None]           # Step 3
+    return z.real.reshape(y.shape)
+
+
+def node_coefficient(g: np.ndarray) -> np.ndarray:
+    """a = exp(g) on all (m+2)^2 nodes (the variable diffusion coefficient)."""
+    return np.exp(g)
