@@ -74,7 +74,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--form", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--form", choices=("fp64", "fp32"), default="fp64",
+                    help="preconditioner arithmetic of the headline number")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip measuring the other preconditioner form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32"), default=None,
                     help="run a small bounded case for an ncu capture and exit (no JSON line)")
@@ -223,40 +226,21 @@ def run_reference(args):
     return 0
 
 
-def run_gpu(args):
-    import numpy as np
+def measure_form(form, case, args, ws, local, dist):
+    """Time K solves of the workload with one preconditioner form.  Returns the
+    per-step time (max over ranks), the live per-kernel event times, the
+    launch count, the clocks seen and the host-buffer (end-to-end) time."""
     import torch
-
-    ws, rank, local = dist_setup()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    from paper_2002_01108_gb300 import build as bec_build
-    if rank == 0:
-        bec_build.build()
-    if ws > 1:
-        dist.barrier()
     from paper_2002_01108_gb300 import Problem
-    from workloads import heat_case_2d
 
-    form = args.form
-    case = heat_case_2d(seed=2, m=M_SIDE, N=N_STEPS, eps=EPS)
     # Z is stored in both forms: with a fixed preconditioner FGMRES gives the
     # same iterates as right-preconditioned GMRES and saves the final apply.
-    flexible = True
-    prob = Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=RESTART, flexible=flexible,
+    prob = Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=RESTART, flexible=True,
                    host_io=True)
     prob.set_eps(EPS)
-    u0 = torch.from_numpy(case.u0).cuda()
-    fsrc = torch.from_numpy(case.fsrc).cuda()
-    f = prob.build_rhs(u0, fsrc)
-    del fsrc
+    f = prob.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
     u = torch.empty_like(f)
-    solve_kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=flexible)
-
+    solve_kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=True)
     for _ in range(args.warmup):
         prob.gmres_solve(f, u, **solve_kw)
     torch.cuda.synchronize()
@@ -281,11 +265,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    ms_total = ev0.elapsed_time(ev1)
+    ms_step = ev0.elapsed_time(ev1) / args.steps
     kernels = prob.profile_stop()
     launches = prob.launches - launches0
     clocks = sampler.stop()
-    ms_step = ms_total / args.steps
     if ws > 1:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -295,22 +278,24 @@ def run_gpu(args):
     f_host = f.cpu().pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
     prob.gmres_solve_host(f_host, u_host, **solve_kw)
-    e2e_times = []
+    e2e = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         prob.gmres_solve_host(f_host, u_host, **solve_kw)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times) / len(e2e_times)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e) / len(e2e)
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-
     U = prob.U
-    value = ws * U / (ms_step / 1e3)
-    total_ms = sum(ms for _, ms in kernels.values())
-    kern = {name: {"launches": n, "ms": round(ms, 4), "share": round(ms / total_ms, 4) if total_ms else None}
-            for name, (n, ms) in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
+    prob.close()
+    return {"U": U, "ms_step": ms_step, "kernels": kernels, "launches": launches,
+            "clocks": clocks, "info": infos[-1], "e2e_s": e2e_s,
+            "e2e_samples_ms": [round(x * 1e3, 3) for x in e2e]}
+
+
+def roofline(form, kernels, U):
     dom = max(kernels.items(), key=lambda kv: kv[1][1])[0]
     dom_n, dom_ms = kernels[dom]
     avg_ms = dom_ms / max(dom_n, 1)
@@ -329,24 +314,66 @@ def run_gpu(args):
                 "algorithmic_per_unit": f"{bpu:.0f} B", "units_per_launch": U}
     roof["avg_launch_ms"] = avg_ms
     roof["traffic"] = NCU_TRAFFIC.get((dom, form))
+    return roof
 
+
+def kernel_table(kernels):
+    total_ms = sum(ms for _, ms in kernels.values())
+    return {name: {"launches": n, "ms": round(ms, 4),
+                   "share": round(ms / total_ms, 4) if total_ms else None}
+            for name, (n, ms) in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2002_01108_gb300 import build as bec_build
+    if rank == 0:
+        bec_build.build()
+    if ws > 1:
+        dist.barrier()
+    from workloads import heat_case_2d
+
+    case = heat_case_2d(seed=2, m=M_SIDE, N=N_STEPS, eps=EPS)
+    form = args.form
+    r = measure_form(form, case, args, ws, local, dist)
+    U = r["U"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64",
+        "metric": METRIC, "value": ws * U / (r["ms_step"] / 1e3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded U[-1,1] source, 8x8 random sine-series u0)",
-        "config": dict(workload_config(form), iterations=infos[-1]["iters"],
-                       true_relres=infos[-1]["true_relres"], parallelism=f"{ws} independent replicas"),
-        "roofline": roof,
-        "e2e": {"value": ws * U / e2e_s, "unit": UNIT, "h2d_bytes_per_step": U * 8,
-                "d2h_bytes_per_step": U * 8, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "kernels": kern,
+        "config": dict(workload_config(form), iterations=r["info"]["iters"],
+                       true_relres=r["info"]["true_relres"],
+                       parallelism=f"{ws} independent replicas"),
+        "roofline": roofline(form, r["kernels"], U),
+        "e2e": {"value": ws * U / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": U * 8,
+                "d2h_bytes_per_step": U * 8, "ms_per_step": r["e2e_s"] * 1e3,
+                "samples_ms": r["e2e_samples_ms"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "kernels": kernel_table(r["kernels"]),
         "paper_context": "Table table1 (N=256, 255^2, Q1, a=1e-5): 12.54 s MATLAB on 2x Xeon E5-2690 v4 "
                          "= 1.33e6 unknowns/s (different discretisation and tolerance)",
     }
-    prob.close()
+    if not args.no_other_form:
+        other = "fp32" if form == "fp64" else "fp64"
+        o = measure_form(other, case, args, ws, local, dist)
+        line["forms"] = {other + "_preconditioner": {
+            "value": ws * U / (o["ms_step"] / 1e3), "unit": UNIT, "ms_per_step": o["ms_step"],
+            "iterations": o["info"]["iters"], "true_relres": o["info"]["true_relres"],
+            "e2e_value": ws * U / o["e2e_s"], "gpu_launches": o["launches"], "clocks": o["clocks"],
+            "roofline": roofline(other, o["kernels"], U), "kernels": kernel_table(o["kernels"]),
+            "note": "same workload and tolerance; FP32/complex64 P_eps^-1 inside FP64 FGMRES"
+                    if other == "fp32" else "same workload; plain FP64 form"}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(case)
     if rank == 0:
