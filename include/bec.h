@@ -51,7 +51,13 @@ typedef enum {
 
 /* How P_eps^{-1} solves the shifted spatial systems B_k z = y (Sec. 4, Step 2). */
 enum {
-  BEC_ROUTE_FST = 0    /* 2D/1D sine transform: exact for constant a (Sec. 4) */
+  BEC_ROUTE_FST = 0,   /* 2D/1D sine transform: exact for constant a (Sec. 4) */
+  BEC_ROUTE_MG = 1     /* one geometric multigrid V-cycle per shifted system,
+                          any positive a (Sec. 4; Example 2 of Sec. 5): bilinear
+                          prolongation, full-weighting restriction, Galerkin
+                          coarse operators, damped Jacobi smoothing; 2D only.
+                          An inexact preconditioner: use flexible GMRES or
+                          accept that GMRES sees a fixed linear operator. */
 };
 
 /* Arithmetic of the preconditioner apply.  The operator L, the Krylov vectors,
@@ -78,6 +84,14 @@ typedef struct {
   int flexible;        /* nonzero: also allocate the FGMRES basis Z */
   int host_io;         /* nonzero: also allocate the staging vectors used by
                           bec_gmres_solve_host */
+  const double* a_nodes; /* HOST array of (nx+2)*(nx+2) values of a(x) > 0 on
+                          all grid nodes, boundary included, [iy][ix]; copied.
+                          NULL: a is the constant `a`.  The face coefficient
+                          between two nodes is the mean of their values
+                          (conservative 5-point scheme).  Needs BEC_ROUTE_MG. */
+  int mg_pre, mg_post;   /* damped-Jacobi sweeps before / after the coarse
+                          correction (0, 0 select 1, 1: the paper's counts) */
+  double mg_omega;       /* Jacobi damping (0 selects 0.8) */
 } bec_problem_desc;
 
 /* Validates desc, allocates the workspace (Krylov basis (max_restart+1) x U
@@ -103,10 +117,12 @@ bec_status bec_apply_P(bec_problem* p, const double* v, double* y);
 
 /* z = P_eps^{-1} y by the three steps of Sec. 4 (eqs. ytild, blockdiaginv,
  * zcompt): scale slice k by eps^{(k-1)/N}, FFT along time, solve the N shifted
- * systems (lambda_k I + tau K) z~ = y~ by the 2D sine transform, of which only
- * ceil((N+1)/2) are distinct (half-spectrum remark of Sec. 4), inverse FFT and
- * unscale.  y == z (in place) is allowed; partial overlap is not.  Needs
- * bec_set_eps first (else BEC_EINVAL). */
+ * systems (lambda_k I + tau K) z~ = y~, of which only ceil((N+1)/2) are
+ * distinct (half-spectrum remark of Sec. 4), inverse FFT and unscale.  The
+ * shifted systems are solved exactly by the 2D sine transform
+ * (BEC_ROUTE_FST), or approximately by one multigrid V-cycle each
+ * (BEC_ROUTE_MG).  y == z (in place) is allowed; partial overlap is not.
+ * Needs bec_set_eps first (else BEC_EINVAL). */
 bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z);
 
 /* f = (tau f^1 + u^0; tau f^2; ...; tau f^N) (Sec. 2).  u0: J doubles,

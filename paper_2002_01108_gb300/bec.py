@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libbec.so")
 
 BEC_OK, BEC_EINVAL, BEC_ENOMEM, BEC_ECUDA, BEC_ENOTCONV, BEC_ENUMERIC, BEC_ETIMEOUT, \
     BEC_EUNSUPPORTED = range(8)
-BEC_ROUTE_FST = 0
+BEC_ROUTE_FST, BEC_ROUTE_MG = 0, 1
 BEC_PC_FP64, BEC_PC_FP32 = 0, 1
 
 #: every symbol include/bec.h declares
@@ -33,7 +33,8 @@ class ProblemDesc(ctypes.Structure):
                 ("N", ctypes.c_int), ("T", ctypes.c_double), ("a", ctypes.c_double),
                 ("route", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_restart", ctypes.c_int), ("flexible", ctypes.c_int),
-                ("host_io", ctypes.c_int)]
+                ("host_io", ctypes.c_int), ("a_nodes", ctypes.c_void_p),
+                ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -131,13 +132,23 @@ class Problem:
 
     def __init__(self, dim: int, nx: int, N: int, T: float = 1.0, a: float = 1.0,
                  precision: str = "fp64", max_restart: int = 30, flexible: bool = False,
-                 host_io: bool = False, stream=None):
+                 host_io: bool = False, stream=None, route: str = "fst", a_nodes=None,
+                 mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0):
         import torch
         self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
         self.precision = precision
-        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a, BEC_ROUTE_FST,
+        self._a_nodes = None
+        a_ptr = None
+        if a_nodes is not None:
+            self._a_nodes = np.ascontiguousarray(a_nodes, dtype=np.float64)
+            if self._a_nodes.size != (nx + 2) ** 2:
+                raise ValueError("a_nodes must hold (nx+2)^2 values")
+            a_ptr = self._a_nodes.ctypes.data
+        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a,
+                           BEC_ROUTE_MG if route == "mg" else BEC_ROUTE_FST,
                            BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
-                           max_restart, int(flexible), int(host_io))
+                           max_restart, int(flexible), int(host_io), a_ptr,
+                           int(mg_pre), int(mg_post), float(mg_omega))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -97,6 +97,7 @@ void destroy_profiler(bec_problem* p) {
 
 void free_all(bec_problem* p) {
   destroy_profiler(p);
+  mg_free(p);
   PcTables& t = p->tab;
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
@@ -135,6 +136,11 @@ bec_status read_scalars(bec_problem* p) {
 bec_status apply_pinv(bec_problem* p, const double* y, double* z,
                       const double* scale_dev = nullptr) {
   const int fp64 = p->desc.precision == BEC_PC_FP64;
+  if (p->desc.route == BEC_ROUTE_MG) {
+    BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));
+    BEC_TRY(mg_vcycle(p));
+    return launch_time_inv(p, p->mg.lv[0].x, z, fp64);
+  }
   const double n = (double)(p->m + 1);
   const double per_axis = (2.0 / n) / 16.0;   // (orthonormal / raw)^2 for one forward+inverse pair
   const double scale = 0.5 / p->N * (p->dim == 2 ? per_axis * per_axis : per_axis);
@@ -330,10 +336,15 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     return einval("N must be a power of two in [2, 1024]");
   if (!(d->T > 0.0) || !std::isfinite(d->T)) return einval("T must be finite and > 0");
   if (!(d->a > 0.0) || !std::isfinite(d->a)) return einval("a must be finite and > 0");
-  if (d->route != BEC_ROUTE_FST) {
-    set_error("only the sine-transform route is built");
-    return BEC_EUNSUPPORTED;
-  }
+  if (d->route != BEC_ROUTE_FST && d->route != BEC_ROUTE_MG)
+    return einval("route must be BEC_ROUTE_FST or BEC_ROUTE_MG");
+  if (d->route == BEC_ROUTE_FST && d->a_nodes != nullptr)
+    return einval("a variable coefficient (a_nodes) needs BEC_ROUTE_MG");
+  if (d->route == BEC_ROUTE_MG && d->dim != 2) return einval("the multigrid route is 2D");
+  if (d->route == BEC_ROUTE_MG && d->N > 512) return einval("the multigrid route needs N <= 512");
+  if (d->mg_pre < 0 || d->mg_post < 0 || d->mg_pre > 8 || d->mg_post > 8)
+    return einval("mg_pre and mg_post must lie in [0, 8]");
+  if (!(d->mg_omega >= 0.0) || d->mg_omega >= 2.0) return einval("mg_omega must lie in [0, 2)");
   if (d->precision != BEC_PC_FP64 && d->precision != BEC_PC_FP32)
     return einval("precision must be BEC_PC_FP64 or BEC_PC_FP32");
   if (d->max_restart < 0 || d->max_restart > kMaxRestart)
@@ -382,7 +393,14 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&t.eis32, N));
   chain(dmalloc(&t.lamf64, N / 2 + 1));
   chain(dmalloc(&t.lamf32, N / 2 + 1));
-  if (d->precision == BEC_PC_FP32) {
+  if (d->route == BEC_ROUTE_MG && s == BEC_OK) {
+    p->mg.pre = d->mg_pre == 0 ? 1 : d->mg_pre;
+    p->mg.post = (d->mg_pre == 0 && d->mg_post == 0) ? 1 : d->mg_post;
+    p->mg.omega = d->mg_omega == 0.0 ? 0.8 : d->mg_omega;
+    chain(mg_setup(p, d->a_nodes));
+  }
+  p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
+  if (d->precision == BEC_PC_FP32 && d->route == BEC_ROUTE_FST) {
     float* sc = nullptr;
     chain(dmalloc(&sc, (size_t)U));
     p->pc_scratch = sc;

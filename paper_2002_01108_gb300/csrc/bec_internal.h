@@ -44,6 +44,25 @@ struct Profiler {
   long long overflow = 0;
 };
 
+// One multigrid level: real Galerkin stencils and complex work arrays for
+// all N/2+1 frequencies, in the preconditioner's precision.
+struct MgLevel {
+  int m = 0;
+  long long J = 0;
+  void* SM = nullptr;   // [9][J] mass stencil (level 0: identity)
+  void* SK = nullptr;   // [9][J] stiffness stencil
+  void* x = nullptr;    // [K][J] complex
+  void* b = nullptr;
+  void* r = nullptr;
+};
+
+struct MgState {
+  int pre = 1, post = 1;
+  double omega = 0.8;
+  int K = 0;            // N/2 + 1 frequencies
+  std::vector<MgLevel> lv;
+};
+
 }  // namespace bec
 
 struct bec_problem {
@@ -78,6 +97,8 @@ struct bec_problem {
   double* io_f = nullptr;       // host_io staging
   double* io_u = nullptr;
   bec::Profiler prof;
+  double* kcoef = nullptr;      // variable a: tau K row [centre, W, E, S, N] x J
+  bec::MgState mg;              // BEC_ROUTE_MG hierarchy
 };
 
 namespace bec {
@@ -125,6 +146,18 @@ bec_status launch_dst_cols(bec_problem* p, void* data, int fp64);
 // `scale` and, when scale_dev is not null, by the device scalar *scale_dev.
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
                             const double* scale_dev);
+
+// ---- multigrid route (bec_mg.cu, bec_time.cu)
+// Builds the coefficient rows, the Galerkin hierarchy and its buffers.
+bec_status mg_setup(bec_problem* p, const double* a_nodes);
+void mg_free(bec_problem* p);
+// One V-cycle for every frequency: level-0 b -> level-0 x.
+bec_status mg_vcycle(bec_problem* p);
+// spec[k][q] = sum_j e^{-2 pi i jk/N} eps^{j/N} (s y)[j][q], k <= N/2 (s = *scale_dev or 1)
+bec_status launch_time_fwd(bec_problem* p, const double* y, void* spec, int fp64,
+                           const double* scale_dev);
+// z[j][q] = eps^{-j/N} N^{-1} sum_k spec_k e^{2 pi i jk/N} (Hermitian extension)
+bec_status launch_time_inv(bec_problem* p, const void* spec, double* z, int fp64);
 
 // ---- stencils (bec_stencil.cu)
 // number of blocks (partial sums) the residual-norm kernel writes

@@ -19,8 +19,9 @@ constexpr int kTimeChunk = 8;
 struct StencilGeom {
   long long J;
   int m, N, dim;
-  double c;       // tau a / h^2
+  double c;       // tau a / h^2 (constant a)
   double alpha;   // (1 + 2 dim c) / c
+  const double* __restrict__ kc;   // variable a: tau K row [centre, W, E, S, N] x J, or null
 };
 
 // (L v)^n at one point: c (alpha v - sum of neighbours) - v^{n-1}, which is
@@ -28,6 +29,15 @@ struct StencilGeom {
 __device__ __forceinline__ double apply_row(const double* __restrict__ vs, long long q, int ix,
                                             int iy, const StencilGeom& g, double center,
                                             double prev) {
+  if (g.kc != nullptr) {   // variable coefficient: v + tau K v - v^{n-1}
+    const long long J = g.J;
+    double t = fma(g.kc[q], center, center - prev);
+    if (ix > 0) t = fma(-g.kc[J + q], vs[q - 1], t);
+    if (ix < g.m - 1) t = fma(-g.kc[2 * J + q], vs[q + 1], t);
+    if (iy > 0) t = fma(-g.kc[3 * J + q], vs[q - g.m], t);
+    if (iy < g.m - 1) t = fma(-g.kc[4 * J + q], vs[q + g.m], t);
+    return t;
+  }
   double nb = (ix > 0 ? vs[q - 1] : 0.0) + (ix < g.m - 1 ? vs[q + 1] : 0.0);
   if (g.dim == 2) nb += (iy > 0 ? vs[q - g.m] : 0.0) + (iy < g.m - 1 ? vs[q + g.m] : 0.0);
   return fma(g.c, fma(g.alpha, center, -nb), -prev);
@@ -217,6 +227,7 @@ StencilGeom geom(const bec_problem* p) {
   g.dim = p->dim;
   g.c = p->tau * p->a / (p->h * p->h);
   g.alpha = (1.0 + 2.0 * p->dim * g.c) / g.c;
+  g.kc = p->kcoef;
   return g;
 }
 

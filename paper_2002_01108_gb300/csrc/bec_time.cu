@@ -132,7 +132,173 @@ bec_status time_dispatch(bec_problem* p, void* data, double scale, const double*
   return BEC_EUNSUPPORTED;
 }
 
+// Step 1 alone (multigrid route): for every spatial point q the half
+// spectrum  S[k][q] = scale sum_j e^{-2 pi i jk/N} eps^{j/N} y[j][q],
+// k = 0..N/2, written to HBM as [N/2+1][J] complex.  Two points share one
+// complex FFT and are separated as (C_k + conj C_{N-k}) / 2 and
+// (C_k - conj C_{N-k}) / (2i).
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(time_warps<T>() * 32)
+time_fwd_kernel(const double* __restrict__ y, v2_t<T>* __restrict__ spec, long long J,
+                const T* __restrict__ es, T scale_h, const double* __restrict__ scale_dev,
+                const v2_t<T>* __restrict__ tw) {
+  using V = v2_t<T>;
+  constexpr int N = 1 << LOGN;
+  constexpr int LSC = N + 1;
+  constexpr int WARPS = time_warps<T>();
+  constexpr int W = 2 * WARPS;
+  constexpr int NK = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  T* sm = reinterpret_cast<T*>(smem_bytes);
+  V* out = reinterpret_cast<V*>(sm + (size_t)WARPS * 2 * LSC);   // [NK][W]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q0 = (long long)blockIdx.x * W;
+  const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
+  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
+    const int j = e / W, c = e % W;
+    const long long q = q0 + c;
+    sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] = q < J ? (T)y[(long long)j * J + q] * es[j] : T(0);
+  }
+  __syncthreads();
+  V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
+  warp_fft<T, -1, LOGN>(line, tw, lane);
+  const T half = scale * T(0.5);
+  for (int k = lane; k < NK; k += 32) {
+    const V C = line[k], Cn = line[(N - k) & (N - 1)];
+    out[k * W + 2 * warp] = {(C.x + Cn.x) * half, (C.y - Cn.y) * half};
+    out[k * W + 2 * warp + 1] = {(C.y + Cn.y) * half, (Cn.x - C.x) * half};
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NK * W; e += WARPS * 32) {
+    const int k = e / W, c = e % W;
+    const long long q = q0 + c;
+    if (q < J) spec[(long long)k * J + q] = out[e];
+  }
+}
+
+// Step 3 alone (multigrid route): z[j][q] = scale eps^{-j/N} sum_k Z_k
+// e^{+2 pi i jk/N} with Z_{N-k} = conj(Z_k), from the half spectrum.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(time_warps<T>() * 32)
+time_inv_kernel(const v2_t<T>* __restrict__ spec, double* __restrict__ z, long long J,
+                const T* __restrict__ eis, T scale, const v2_t<T>* __restrict__ tw) {
+  using V = v2_t<T>;
+  constexpr int N = 1 << LOGN;
+  constexpr int LSC = N + 1;
+  constexpr int WARPS = time_warps<T>();
+  constexpr int W = 2 * WARPS;
+  constexpr int NK = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  T* sm = reinterpret_cast<T*>(smem_bytes);
+  V* in = reinterpret_cast<V*>(sm + (size_t)WARPS * 2 * LSC);    // [NK][W]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q0 = (long long)blockIdx.x * W;
+  for (int e = threadIdx.x; e < NK * W; e += WARPS * 32) {
+    const int k = e / W, c = e % W;
+    const long long q = q0 + c;
+    in[e] = q < J ? spec[(long long)k * J + q] : V{0, 0};
+  }
+  __syncthreads();
+  V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
+  for (int k = lane; k < NK; k += 32) {
+    const V A = in[k * W + 2 * warp], B = in[k * W + 2 * warp + 1];
+    line[k] = {A.x - B.y, A.y + B.x};                    // A + i B
+    if (k > 0 && k < N / 2) line[N - k] = {A.x + B.y, B.x - A.y};   // conj(A) + i conj(B)
+  }
+  __syncwarp();
+  warp_fft<T, +1, LOGN>(line, tw, lane);
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
+    const int j = e / W, c = e % W;
+    const long long q = q0 + c;
+    if (q < J)
+      z[(long long)j * J + q] = (double)(sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] * eis[j] * scale);
+  }
+}
+
+template <typename T, int LOGN>
+bec_status time_fwd_launch(bec_problem* p, const double* y, void* spec, double scale,
+                           const double* scale_dev, const T* es, const v2_t<T>* tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int warps = time_warps<T>();
+  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T) +
+                      (size_t)(N / 2 + 1) * 2 * warps * sizeof(v2_t<T>);
+  auto k = time_fwd_kernel<T, LOGN>;
+  if (smem > 48 * 1024)
+    BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long W = 2 * warps;
+  BEC_LAUNCH_BEGIN(p);
+  k<<<(unsigned)((p->J + W - 1) / W), warps * 32, smem, p->stream>>>(
+      y, static_cast<v2_t<T>*>(spec), p->J, es, (T)scale, scale_dev, tw);
+  BEC_LAUNCH_CHECK(p, "time_fwd_kernel");
+  return BEC_OK;
+}
+
+template <typename T, int LOGN>
+bec_status time_inv_launch(bec_problem* p, const void* spec, double* z, double scale,
+                           const T* eis, const v2_t<T>* tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int warps = time_warps<T>();
+  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T) +
+                      (size_t)(N / 2 + 1) * 2 * warps * sizeof(v2_t<T>);
+  auto k = time_inv_kernel<T, LOGN>;
+  if (smem > 48 * 1024)
+    BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long W = 2 * warps;
+  BEC_LAUNCH_BEGIN(p);
+  k<<<(unsigned)((p->J + W - 1) / W), warps * 32, smem, p->stream>>>(
+      static_cast<const v2_t<T>*>(spec), z, p->J, eis, (T)scale, tw);
+  BEC_LAUNCH_CHECK(p, "time_inv_kernel");
+  return BEC_OK;
+}
+
+#define BEC_TIME_SWITCH(logn, CALL)                                                    \
+  switch (logn) {                                                                     \
+    case 1: return CALL(1);                                                           \
+    case 2: return CALL(2);                                                           \
+    case 3: return CALL(3);                                                           \
+    case 4: return CALL(4);                                                           \
+    case 5: return CALL(5);                                                           \
+    case 6: return CALL(6);                                                           \
+    case 7: return CALL(7);                                                           \
+    case 8: return CALL(8);                                                           \
+    case 9: return CALL(9);                                                           \
+    default: break;                                                                   \
+  }
+
 }  // namespace
+
+bec_status launch_time_fwd(bec_problem* p, const double* y, void* spec, int fp64,
+                           const double* scale_dev) {
+  const PcTables& t = p->tab;
+  if (fp64) {
+#define BEC_FWD64(L) time_fwd_launch<double, L>(p, y, spec, 1.0, scale_dev, t.es64, t.time.tw64)
+    BEC_TIME_SWITCH(t.time.logn, BEC_FWD64)
+#undef BEC_FWD64
+  } else {
+#define BEC_FWD32(L) time_fwd_launch<float, L>(p, y, spec, 1.0, scale_dev, t.es32, t.time.tw32)
+    BEC_TIME_SWITCH(t.time.logn, BEC_FWD32)
+#undef BEC_FWD32
+  }
+  set_error("the multigrid route supports N <= 512");
+  return BEC_EUNSUPPORTED;
+}
+
+bec_status launch_time_inv(bec_problem* p, const void* spec, double* z, int fp64) {
+  const PcTables& t = p->tab;
+  const double scale = 1.0 / p->N;
+  if (fp64) {
+#define BEC_INV64(L) time_inv_launch<double, L>(p, spec, z, scale, t.eis64, t.time.tw64)
+    BEC_TIME_SWITCH(t.time.logn, BEC_INV64)
+#undef BEC_INV64
+  } else {
+#define BEC_INV32(L) time_inv_launch<float, L>(p, spec, z, scale, t.eis32, t.time.tw32)
+    BEC_TIME_SWITCH(t.time.logn, BEC_INV32)
+#undef BEC_INV32
+  }
+  set_error("the multigrid route supports N <= 512");
+  return BEC_EUNSUPPORTED;
+}
 
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
                             const double* scale_dev) {

@@ -67,7 +67,21 @@ def test_allocate_rejects_mismatched_ny_and_unknown_route(lib):
     d = ProblemDesc(2, 63, 31, 64, 1.0, 1.0, 0, 0, 10, 0, 0)
     assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1
     d = ProblemDesc(2, 63, 63, 64, 1.0, 1.0, 5, 0, 10, 0, 0)
-    assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 7
+    assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1
+
+
+def test_allocate_rejects_invalid_multigrid_requests(lib):
+    import numpy as np
+    from paper_2002_01108_gb300.bec import ProblemDesc
+    out = ctypes.c_void_p()
+    a = np.ones(65 * 65)
+    # a variable coefficient needs the multigrid route
+    d = ProblemDesc(2, 63, 63, 64, 1.0, 1.0, 0, 0, 10, 0, 0, a.ctypes.data)
+    assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1
+    # the multigrid route is 2D, N <= 512, omega in [0, 2), sweeps in [0, 8]
+    for dim, N, pre, omega in ((1, 64, 0, 0.0), (2, 1024, 0, 0.0), (2, 64, 9, 0.0), (2, 64, 0, 2.5)):
+        d = ProblemDesc(dim, 63, 63, N, 1.0, 1.0, 1, 0, 10, 0, 0, None, pre, 0, omega)
+        assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (dim, N, pre, omega)
 
 
 def test_null_arguments_are_rejected(lib):
