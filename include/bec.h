@@ -52,6 +52,14 @@ typedef enum {
 /* How P_eps^{-1} solves the shifted spatial systems B_k z = y (Sec. 4, Step 2). */
 enum {
   BEC_ROUTE_FST = 0,   /* 2D/1D sine transform: exact for constant a (Sec. 4) */
+  BEC_ROUTE_LEARNED = 2, /* BEC_ROUTE_MG plus a learned correction of what each
+                          V-cycle leaves: a 4-level convolutional network on
+                          the grid of spacing 2h (BF16 activations, FP32
+                          accumulation), trained on the GPU by
+                          bec_learned_train on pairs the multigrid generates;
+                          per frequency, the correction is kept only if it
+                          lowers ||b - B x|| (the V-cycle is the fallback and
+                          the judge).  Needs BEC_PC_FP32 and nx >= 31. */
   BEC_ROUTE_MG = 1     /* one geometric multigrid V-cycle per shifted system,
                           any positive a (Sec. 4; Example 2 of Sec. 5): bilinear
                           prolongation, full-weighting restriction, Galerkin
@@ -92,6 +100,9 @@ typedef struct {
   int mg_pre, mg_post;   /* damped-Jacobi sweeps before / after the coarse
                           correction (0, 0 select 1, 1: the paper's counts) */
   double mg_omega;       /* Jacobi damping (0 selects 0.8) */
+  int net_channels;      /* BEC_ROUTE_LEARNED: channels (4 or 32; 0 selects 32) */
+  int net_fp32;          /* BEC_ROUTE_LEARNED: nonzero keeps activations in FP32
+                            (used to check gradients); default BF16 */
 } bec_problem_desc;
 
 /* Validates desc, allocates the workspace (Krylov basis (max_restart+1) x U
@@ -201,6 +212,73 @@ bec_status bec_relres_noalloc(int dim, int nx, int N, double T, double a,
 
 /* Releases the workspace; p may be NULL. */
 bec_status bec_free_problem(bec_problem* p);
+
+/* ---- Learned correction (BEC_ROUTE_LEARNED) -------------------------------
+ * The network's weights: 9 layers of 3 x 3 convolutions, layer i a FP32
+ * array [3][3][c_in][c_out] (c = 5 -> C, C -> C x 7, C -> 2), concatenated. */
+long long bec_learned_num_weights(const bec_problem* p);
+bec_status bec_learned_get_weights(bec_problem* p, float* host);
+bec_status bec_learned_set_weights(bec_problem* p, const float* host);
+
+/* Trains the network on the GPU: every ceil((N/2+1)/batch) steps a fresh set
+ * of pairs (r, B_k^{-1} r) is made for all frequencies (r = what one V-cycle
+ * leaves of a random right-hand side; B_k^{-1} r by 12 defect-correction
+ * V-cycles); each step draws `batch` frequencies, runs the forward and
+ * backward kernels on the relative error ||e - e*||^2 / ||e*||^2 and takes
+ * one Adam step with learning rate lr.  loss_history (host, `steps` doubles,
+ * may be NULL) receives the mean batch loss of every step.  Synchronises. */
+bec_status bec_learned_train(bec_problem* p, int steps, int batch, double lr,
+                             unsigned long long seed, double* loss_history);
+
+/* Loss and weight gradient for B given samples (a check of the kernels):
+ * lam_idx (host, B ints) the frequency index k of each sample, r and e_target
+ * DEVICE arrays of B fine-grid complex128 fields [B][ny][nx][2].  loss (host)
+ * receives the mean relative error, grad (host, may be NULL) the gradient of
+ * every weight.  Synchronises. */
+bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx,
+                                 const double* r, const double* e_target,
+                                 double* loss, float* grad);
+
+/* Frequencies at which the last bec_apply_Pinv kept the V-cycle result
+ * because the correction did not lower the residual (-1: not learned). */
+long long bec_learned_fallbacks(bec_problem* p);
+
+/* ---- Batches of independent problems of uneven size ---------------------
+ * Not a construct of the paper: many independent instances (different grid,
+ * N and eps) solved together.  Each instance is a bec_problem (own
+ * workspace, own tables) bound to one of `nstreams` CUDA streams the batch
+ * creates.  bec_batch_solve runs every instance's restarted GMRES in rounds:
+ * one Arnoldi iteration of every active instance is enqueued on its stream
+ * (replayed from a per-iteration CUDA graph when use_graphs != 0), then the
+ * host waits once per stream and every instance reads its residual.  Work of
+ * instances on different streams overlaps on the GPU. */
+typedef struct bec_batch bec_batch;
+
+/* descs[i] and eps[i] for i < count as in bec_allocate_problem/bec_set_eps;
+ * nstreams in [1, 64].  On failure nothing stays allocated and
+ * bec_last_error() names the failing instance. */
+bec_status bec_batch_create(const bec_problem_desc* descs, const double* eps,
+                            int count, int nstreams, int use_graphs,
+                            bec_batch** out);
+
+/* The problem object of instance i (for bec_build_rhs, bec_apply_*, ...);
+ * owned by the batch. */
+bec_status bec_batch_problem(bec_batch* b, int i, bec_problem** out);
+
+/* Solves every instance: f[i], u[i] are device vectors of instance i
+ * (16-byte aligned), opts apply to all, infos[i] (may be NULL) receives each
+ * instance's result.  Synchronises.  Returns the first error met, else
+ * BEC_ENOTCONV if some instance missed rtol within maxit, else BEC_OK. */
+bec_status bec_batch_solve(bec_batch* b, const double* const* f,
+                           double* const* u, const bec_gmres_opts* opts,
+                           bec_gmres_info* infos);
+
+/* Total space-time unknowns of the batch; kernels launched by all instances. */
+long long bec_batch_unknowns(const bec_batch* b);
+long long bec_batch_kernel_launches(const bec_batch* b);
+
+/* Releases every instance and the streams; b may be NULL. */
+bec_status bec_batch_free(bec_batch* b);
 
 /* Number of space-time unknowns U = N * J of the problem (0 if p is NULL). */
 long long bec_problem_size(const bec_problem* p);

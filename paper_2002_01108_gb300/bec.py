@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libbec.so")
 
 BEC_OK, BEC_EINVAL, BEC_ENOMEM, BEC_ECUDA, BEC_ENOTCONV, BEC_ENUMERIC, BEC_ETIMEOUT, \
     BEC_EUNSUPPORTED = range(8)
-BEC_ROUTE_FST, BEC_ROUTE_MG = 0, 1
+BEC_ROUTE_FST, BEC_ROUTE_MG, BEC_ROUTE_LEARNED = 0, 1, 2
 BEC_PC_FP64, BEC_PC_FP32 = 0, 1
 
 #: every symbol include/bec.h declares
@@ -25,6 +25,10 @@ EXPORTED = (
     "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_true_relres",
     "bec_free_problem", "bec_problem_size", "bec_kernel_launches", "bec_status_string",
     "bec_last_error", "bec_profile_start", "bec_profile_stop", "bec_relres_noalloc",
+    "bec_batch_create", "bec_batch_problem", "bec_batch_solve", "bec_batch_unknowns",
+    "bec_batch_kernel_launches", "bec_batch_free", "bec_learned_num_weights",
+    "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
+    "bec_learned_loss_grad", "bec_learned_fallbacks",
 )
 
 
@@ -34,7 +38,8 @@ class ProblemDesc(ctypes.Structure):
                 ("route", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_restart", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("host_io", ctypes.c_int), ("a_nodes", ctypes.c_void_p),
-                ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double)]
+                ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double),
+                ("net_channels", ctypes.c_int), ("net_fp32", ctypes.c_int)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -90,6 +95,24 @@ def _lib():
         "bec_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "bec_last_error": ([], ctypes.c_char_p),
         "bec_profile_start": ([P, ctypes.c_int], ctypes.c_int),
+        "bec_batch_create": ([ctypes.POINTER(ProblemDesc), ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)],
+                             ctypes.c_int),
+        "bec_batch_problem": ([P, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
+        "bec_batch_solve": ([P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(GmresOpts),
+                             ctypes.POINTER(GmresInfo)], ctypes.c_int),
+        "bec_batch_unknowns": ([P], ctypes.c_longlong),
+        "bec_batch_kernel_launches": ([P], ctypes.c_longlong),
+        "bec_batch_free": ([P], ctypes.c_int),
+        "bec_learned_num_weights": ([P], ctypes.c_longlong),
+        "bec_learned_get_weights": ([P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "bec_learned_set_weights": ([P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "bec_learned_train": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong,
+                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bec_learned_loss_grad": ([P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), D, D,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)],
+                                  ctypes.c_int),
+        "bec_learned_fallbacks": ([P], ctypes.c_longlong),
         "bec_relres_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, D, D, D, P], ctypes.c_int),
         "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
@@ -133,7 +156,8 @@ class Problem:
     def __init__(self, dim: int, nx: int, N: int, T: float = 1.0, a: float = 1.0,
                  precision: str = "fp64", max_restart: int = 30, flexible: bool = False,
                  host_io: bool = False, stream=None, route: str = "fst", a_nodes=None,
-                 mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0):
+                 mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0,
+                 net_channels: int = 0, net_fp32: bool = False):
         import torch
         self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
         self.precision = precision
@@ -144,11 +168,12 @@ class Problem:
             if self._a_nodes.size != (nx + 2) ** 2:
                 raise ValueError("a_nodes must hold (nx+2)^2 values")
             a_ptr = self._a_nodes.ctypes.data
-        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a,
-                           BEC_ROUTE_MG if route == "mg" else BEC_ROUTE_FST,
+        routes = {"fst": BEC_ROUTE_FST, "mg": BEC_ROUTE_MG, "learned": BEC_ROUTE_LEARNED}
+        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a, routes[route],
                            BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
                            max_restart, int(flexible), int(host_io), a_ptr,
-                           int(mg_pre), int(mg_post), float(mg_omega))
+                           int(mg_pre), int(mg_post), float(mg_omega), int(net_channels),
+                           int(net_fp32))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -274,8 +299,128 @@ class Problem:
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms))
                 for i in range(min(n.value, cap))}
 
+    # -- learned correction
+    def learned_weights(self):
+        n = int(_lib().bec_learned_num_weights(self._p))
+        w = np.empty(n, dtype=np.float32)
+        _check(_lib().bec_learned_get_weights(self._p, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "bec_learned_get_weights")
+        return w
+
+    def set_learned_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(_lib().bec_learned_set_weights(self._p, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "bec_learned_set_weights")
+
+    def learned_train(self, steps: int, batch: int = 16, lr: float = 1e-3, seed: int = 0):
+        hist = np.zeros(steps)
+        _check(_lib().bec_learned_train(self._p, int(steps), int(batch), float(lr), int(seed),
+                                        hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "bec_learned_train")
+        return hist
+
+    def learned_loss_grad(self, lam_idx, r, e_target):
+        """r, e_target: complex128 CUDA tensors [B][nx][nx] (view as float64 pairs)."""
+        import torch
+        B = len(lam_idx)
+        idx = (ctypes.c_int * B)(*[int(k) for k in lam_idx])
+        rr = torch.view_as_real(r).contiguous()
+        et = torch.view_as_real(e_target).contiguous()
+        loss = ctypes.c_double()
+        g = np.empty(int(_lib().bec_learned_num_weights(self._p)), dtype=np.float32)
+        _check(_lib().bec_learned_loss_grad(self._p, B, idx, ctypes.c_void_p(rr.data_ptr()),
+                                            ctypes.c_void_p(et.data_ptr()), ctypes.byref(loss),
+                                            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "bec_learned_loss_grad")
+        return loss.value, g
+
+    @property
+    def learned_fallbacks(self) -> int:
+        return int(_lib().bec_learned_fallbacks(self._p))
+
     def true_relres(self, f, u) -> float:
         out = ctypes.c_double()
         _check(_lib().bec_true_relres(self._p, _dptr(f, self.U, "f"), _dptr(u, self.U, "u"),
                                       ctypes.byref(out)), "bec_true_relres")
         return out.value
+
+
+class Batch:
+    """Independent problems of uneven size solved together (bec_batch_*).
+    `specs` is a list of dicts with keys dim, nx, N, eps and optionally T, a,
+    precision, max_restart, route, a_nodes."""
+
+    def __init__(self, specs, nstreams: int = 8, use_graphs: bool = True, flexible: bool = True):
+        n = len(specs)
+        descs = (ProblemDesc * n)()
+        eps = (ctypes.c_double * n)()
+        self._keep = []
+        self.shapes = []
+        for i, sp in enumerate(specs):
+            a_ptr = None
+            if sp.get("a_nodes") is not None:
+                arr = np.ascontiguousarray(sp["a_nodes"], dtype=np.float64)
+                self._keep.append(arr)
+                a_ptr = arr.ctypes.data
+            dim, nx, N = sp["dim"], sp["nx"], sp["N"]
+            descs[i] = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, sp.get("T", 1.0), sp.get("a", 1.0),
+                                   BEC_ROUTE_MG if sp.get("route") == "mg" else BEC_ROUTE_FST,
+                                   BEC_PC_FP32 if sp.get("precision", "fp32") == "fp32" else BEC_PC_FP64,
+                                   sp.get("max_restart", 10), int(flexible), 0, a_ptr, 0, 0, 0.0)
+            eps[i] = sp["eps"]
+            self.shapes.append((N, nx, nx) if dim == 2 else (N, nx))
+        out = ctypes.c_void_p()
+        _check(_lib().bec_batch_create(descs, eps, n, int(nstreams), int(use_graphs), ctypes.byref(out)),
+               "bec_batch_create")
+        self._b = out
+        self.count = n
+
+    @property
+    def unknowns(self) -> int:
+        return int(_lib().bec_batch_unknowns(self._b))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib().bec_batch_kernel_launches(self._b))
+
+    def problem_handle(self, i: int):
+        out = ctypes.c_void_p()
+        _check(_lib().bec_batch_problem(self._b, int(i), ctypes.byref(out)), "bec_batch_problem")
+        return out
+
+    def build_rhs(self, i: int, u0, fsrc, f):
+        U = f.numel()
+        _check(_lib().bec_build_rhs(self.problem_handle(i), _dptr(u0, U // self.shapes[i][0], "u0"),
+                                    _dptr(fsrc, U, "fsrc"), _dptr(f, U, "f")), "bec_build_rhs")
+        return f
+
+    def solve(self, fs, us, restart: int = 10, maxit: int = 300, rtol: float = 1e-8,
+              flexible: bool = True):
+        n = self.count
+        fp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(f.data_ptr()) for f in fs])
+        up = (ctypes.c_void_p * n)(*[ctypes.c_void_p(u.data_ptr()) for u in us])
+        for i in range(n):
+            _dptr(fs[i], fs[i].numel(), "f")
+            _dptr(us[i], us[i].numel(), "u")
+        opts = GmresOpts(int(restart), int(maxit), float(rtol), int(flexible), 0, 0)
+        infos = (GmresInfo * n)()
+        _check(_lib().bec_batch_solve(self._b, fp, up, ctypes.byref(opts), infos),
+               "bec_batch_solve", allow=(BEC_OK, BEC_ENOTCONV))
+        return [infos[i].as_dict() for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib().bec_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

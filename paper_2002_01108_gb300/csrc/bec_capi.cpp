@@ -97,7 +97,11 @@ void destroy_profiler(bec_problem* p) {
 
 void free_all(bec_problem* p) {
   destroy_profiler(p);
+  net_free(p);
   mg_free(p);
+  for (auto& g : p->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
   PcTables& t = p->tab;
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
@@ -132,36 +136,6 @@ bec_status read_scalars(bec_problem* p) {
     if (_s != BEC_OK) return _s;       \
   } while (0)
 
-// z = P_eps^{-1} (s y) with s = *scale_dev (1 if null); no argument checks
-bec_status apply_pinv(bec_problem* p, const double* y, double* z,
-                      const double* scale_dev = nullptr) {
-  const int fp64 = p->desc.precision == BEC_PC_FP64;
-  if (p->desc.route == BEC_ROUTE_MG) {
-    BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));
-    BEC_TRY(mg_vcycle(p));
-    return launch_time_inv(p, p->mg.lv[0].x, z, fp64);
-  }
-  const double n = (double)(p->m + 1);
-  const double per_axis = (2.0 / n) / 16.0;   // (orthonormal / raw)^2 for one forward+inverse pair
-  const double scale = 0.5 / p->N * (p->dim == 2 ? per_axis * per_axis : per_axis);
-  const long long rows = p->dim == 2 ? (long long)p->N * p->m : p->N;
-  if (fp64) {
-    BEC_TRY(launch_dst_rows(p, y, 1, z, 1, rows, 1));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
-    BEC_TRY(launch_time_pass(p, z, 1, scale, scale_dev));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
-    BEC_TRY(launch_dst_rows(p, z, 1, z, 1, rows, 1));
-  } else {
-    void* s = p->pc_scratch;
-    BEC_TRY(launch_dst_rows(p, y, 1, s, 0, rows, 0));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
-    BEC_TRY(launch_time_pass(p, s, 0, scale, scale_dev));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
-    BEC_TRY(launch_dst_rows(p, s, 0, z, 1, rows, 0));
-  }
-  return BEC_OK;
-}
-
 bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 bool aligned8(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; }
 
@@ -175,136 +149,9 @@ bool overlap(const bec_problem* p, const double* a, const double* b) {
   return a < b + p->U && b < a + p->U;
 }
 
-bec_status gmres_impl(bec_problem* p, const double* f, double* u, const bec_gmres_opts* o,
-                      bec_gmres_info* info) {
-  const long long U = p->U;
-  const int R = o->restart;
-  const bool left = o->left_pc != 0;
-  const bool flex = o->flexible != 0;
-  // Basis vectors are addressed through a pointer list: with x0 = 0 and right
-  // preconditioning the first one is the caller's f itself (read only).
-  std::vector<const double*> Vp(R + 1), Zp(R);
-  for (int i = 0; i <= R; ++i) Vp[i] = p->V + (long long)i * U;
-  for (int i = 0; i < R && flex; ++i) Zp[i] = p->Z + (long long)i * U;
-  double* sigma = p->sigma;
+}  // namespace
 
-  // reference norm: ||f|| (right) or ||P^{-1} f|| (left)
-  if (left) {
-    BEC_TRY(apply_pinv(p, f, p->t));
-    BEC_TRY(launch_norm(p, p->t, S_REF));
-  } else {
-    BEC_TRY(launch_norm(p, f, S_REF));
-  }
-  if (!o->use_x0) BEC_TRY(launch_zero(p, u));
-  BEC_TRY(read_scalars(p));
-  const double ref = p->host_scal[S_REF];
-  bec_gmres_info inf;
-  std::memset(&inf, 0, sizeof(inf));
-  if (!std::isfinite(ref)) {
-    set_error("right-hand side contains NaN or Inf");
-    return BEC_ENUMERIC;
-  }
-  if (ref == 0.0) {
-    BEC_TRY(launch_zero(p, u));
-    inf.converged = 1;
-    if (info) *info = inf;
-    return BEC_OK;
-  }
-
-  int iters = 0, restarts = 0;
-  bool converged = false, x_nonzero = o->use_x0 != 0;
-  double monitored = 1.0;
-  double* h1 = p->hcol;
-  double* h2 = p->hcol + (p->max_restart + 2);
-  while (true) {
-    // r0, stored unnormalised in V_0 (sigma_0 = 1 / ||r0|| set by gmres_start)
-    int beta_slot = S_BETA;
-    if (x_nonzero) {
-      BEC_TRY(launch_residual(p, f, u, p->V));
-      Vp[0] = p->V;
-    } else if (!left) {
-      Vp[0] = f;
-      beta_slot = S_REF;
-    } else {
-      Vp[0] = p->V;
-    }
-    if (left) BEC_TRY(apply_pinv(p, x_nonzero ? p->V : f, p->V));
-    double beta = ref;
-    if (beta_slot == S_BETA) {
-      BEC_TRY(launch_norm(p, Vp[0], S_BETA));
-      BEC_TRY(read_scalars(p));
-      beta = p->host_scal[S_BETA];
-    }
-    if (!std::isfinite(beta)) {
-      set_error("NaN or Inf in the GMRES residual");
-      return BEC_ENUMERIC;
-    }
-    monitored = beta / ref;
-    if (beta <= o->rtol * ref) {
-      converged = true;
-      break;
-    }
-    if (iters >= o->maxit) break;
-    BEC_TRY(launch_gmres_start(p, beta_slot));
-    int k = 0;
-    for (int j = 0; j < R; ++j) {
-      if (left) {
-        BEC_TRY(launch_apply_L(p, Vp[j], p->t, 0.0, sigma + j));
-        BEC_TRY(apply_pinv(p, p->t, p->w));
-        BEC_TRY(launch_dots(p, p->w, Vp.data(), j + 1, sigma, h1));
-      } else {
-        double* z = flex ? p->Z + (long long)j * U : p->t;
-        BEC_TRY(apply_pinv(p, Vp[j], z, sigma + j));
-        BEC_TRY(launch_stencil_dots(p, z, p->w, Vp.data(), j + 1, sigma, h1));
-      }
-      // classical Gram-Schmidt, second pass fused with the first update
-      BEC_TRY(launch_update_dots(p, p->w, Vp.data(), j + 1, sigma, h1, h2));
-      double* vnext = p->V + (long long)(j + 1) * U;
-      BEC_TRY(launch_combine(p, vnext, p->w, Vp.data(), j + 1, sigma, h2, -1.0, S_W));
-      Vp[j + 1] = vnext;
-      BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES));
-      ++iters;
-      k = j + 1;
-      BEC_TRY(read_scalars(p));
-      const double res = p->host_scal[S_RES];
-      if (!std::isfinite(res)) {
-        set_error("NaN or Inf in the GMRES recurrences");
-        return BEC_ENUMERIC;
-      }
-      monitored = res / ref;
-      if (res <= o->rtol * ref) {
-        converged = true;
-        break;
-      }
-      if (iters >= o->maxit) break;
-    }
-    BEC_TRY(launch_least_squares(p, k));
-    if (left) {
-      BEC_TRY(launch_combine(p, u, u, Vp.data(), k, sigma, p->ycoef, 1.0, -1));
-    } else if (flex) {
-      BEC_TRY(launch_combine(p, u, u, Zp.data(), k, nullptr, p->ycoef, 1.0, -1));
-    } else {
-      BEC_TRY(launch_combine(p, p->t, nullptr, Vp.data(), k, sigma, p->ycoef, 1.0, -1));
-      BEC_TRY(apply_pinv(p, p->t, p->w));
-      const double* wl[1] = {p->w};
-      BEC_TRY(launch_combine(p, u, u, wl, 1, nullptr, p->scal + S_ONE, 1.0, -1));
-    }
-    x_nonzero = true;
-    if (converged || iters >= o->maxit) break;
-    ++restarts;
-  }
-  BEC_TRY(launch_residual_norms(p, f, u, S_TRUE));
-  BEC_TRY(read_scalars(p));
-  inf.iters = iters;
-  inf.restarts = restarts;
-  inf.converged = converged ? 1 : 0;
-  inf.prec_relres = monitored;
-  inf.true_relres = p->host_scal[S_TRUE] / p->host_scal[S_TRUE + 1];
-  if (info) *info = inf;
-  return converged ? BEC_OK : BEC_ENOTCONV;
-}
-
-bec_status check_opts(const bec_problem* p, const bec_gmres_opts* o) {
+bec_status check_gmres_opts(const bec_problem* p, const bec_gmres_opts* o) {
   if (o == nullptr) return einval("null options");
   if (o->restart < 1 || o->restart > p->max_restart)
     return einval("restart must be in [1, max_restart]");
@@ -318,7 +165,6 @@ bec_status check_opts(const bec_problem* p, const bec_gmres_opts* o) {
   return BEC_OK;
 }
 
-}  // namespace
 }  // namespace bec
 
 using namespace bec;
@@ -336,12 +182,19 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     return einval("N must be a power of two in [2, 1024]");
   if (!(d->T > 0.0) || !std::isfinite(d->T)) return einval("T must be finite and > 0");
   if (!(d->a > 0.0) || !std::isfinite(d->a)) return einval("a must be finite and > 0");
-  if (d->route != BEC_ROUTE_FST && d->route != BEC_ROUTE_MG)
-    return einval("route must be BEC_ROUTE_FST or BEC_ROUTE_MG");
+  if (d->route != BEC_ROUTE_FST && d->route != BEC_ROUTE_MG && d->route != BEC_ROUTE_LEARNED)
+    return einval("route must be BEC_ROUTE_FST, BEC_ROUTE_MG or BEC_ROUTE_LEARNED");
+  const bool mgroute = d->route == BEC_ROUTE_MG || d->route == BEC_ROUTE_LEARNED;
   if (d->route == BEC_ROUTE_FST && d->a_nodes != nullptr)
-    return einval("a variable coefficient (a_nodes) needs BEC_ROUTE_MG");
-  if (d->route == BEC_ROUTE_MG && d->dim != 2) return einval("the multigrid route is 2D");
-  if (d->route == BEC_ROUTE_MG && d->N > 512) return einval("the multigrid route needs N <= 512");
+    return einval("a variable coefficient (a_nodes) needs BEC_ROUTE_MG or BEC_ROUTE_LEARNED");
+  if (mgroute && d->dim != 2) return einval("the multigrid route is 2D");
+  if (mgroute && d->N > 512) return einval("the multigrid route needs N <= 512");
+  if (d->route == BEC_ROUTE_LEARNED) {
+    if (d->precision != BEC_PC_FP32) return einval("the learned route needs BEC_PC_FP32");
+    if (d->nx < 31) return einval("the learned route needs nx >= 31");
+    if (d->net_channels != 0 && d->net_channels != 4 && d->net_channels != 32)
+      return einval("net_channels must be 0, 4 or 32");
+  }
   if (d->mg_pre < 0 || d->mg_post < 0 || d->mg_pre > 8 || d->mg_post > 8)
     return einval("mg_pre and mg_post must lie in [0, 8]");
   if (!(d->mg_omega >= 0.0) || d->mg_omega >= 2.0) return einval("mg_omega must lie in [0, 2)");
@@ -393,11 +246,13 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&t.eis32, N));
   chain(dmalloc(&t.lamf64, N / 2 + 1));
   chain(dmalloc(&t.lamf32, N / 2 + 1));
-  if (d->route == BEC_ROUTE_MG && s == BEC_OK) {
+  if (mgroute && s == BEC_OK) {
     p->mg.pre = d->mg_pre == 0 ? 1 : d->mg_pre;
     p->mg.post = (d->mg_pre == 0 && d->mg_post == 0) ? 1 : d->mg_post;
     p->mg.omega = d->mg_omega == 0.0 ? 0.8 : d->mg_omega;
     chain(mg_setup(p, d->a_nodes));
+    if (d->route == BEC_ROUTE_LEARNED && s == BEC_OK)
+      chain(net_setup(p, d->a_nodes, d->net_channels == 0 ? 32 : d->net_channels, d->net_fp32, 32));
   }
   p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
   if (d->precision == BEC_PC_FP32 && d->route == BEC_ROUTE_FST) {
@@ -542,7 +397,7 @@ bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z) {
   BEC_TRY(check_vec(y));
   BEC_TRY(check_vec(z));
   if (y != z && overlap(p, y, z)) return einval("y and z must be equal or disjoint");
-  return apply_pinv(p, y, z);
+  return apply_pinv(p, y, z, nullptr);
 }
 
 bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc, double* f) {
@@ -556,24 +411,24 @@ bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc, d
 bec_status bec_gmres_solve(bec_problem* p, const double* f, double* u, const bec_gmres_opts* opts,
                            bec_gmres_info* info) {
   if (p == nullptr) return einval("null problem");
-  BEC_TRY(check_opts(p, opts));
+  BEC_TRY(check_gmres_opts(p, opts));
   if (f == nullptr || u == nullptr) return einval("null vector pointer");
   if (!aligned16(f) || !aligned16(u)) return einval("f and u must be 16-byte aligned");
   if (overlap(p, f, u)) return einval("f and u must not overlap");
-  return gmres_impl(p, f, u, opts, info);
+  return gmres_solve_one(p, f, u, opts, info);
 }
 
 bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host, double* u_host,
                                 const bec_gmres_opts* opts, bec_gmres_info* info) {
   if (p == nullptr) return einval("null problem");
   if (p->io_f == nullptr) return einval("bec_gmres_solve_host needs desc.host_io");
-  BEC_TRY(check_opts(p, opts));
+  BEC_TRY(check_gmres_opts(p, opts));
   if (f_host == nullptr || u_host == nullptr) return einval("null host pointer");
   const size_t bytes = (size_t)p->U * sizeof(double);
   BEC_CUDA_TRY(cudaMemcpyAsync(p->io_f, f_host, bytes, cudaMemcpyHostToDevice, p->stream));
   if (opts->use_x0)
     BEC_CUDA_TRY(cudaMemcpyAsync(p->io_u, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
-  const bec_status s = gmres_impl(p, p->io_f, p->io_u, opts, info);
+  const bec_status s = gmres_solve_one(p, p->io_f, p->io_u, opts, info);
   if (s != BEC_OK && s != BEC_ENOTCONV) return s;
   BEC_CUDA_TRY(cudaMemcpyAsync(u_host, p->io_u, bytes, cudaMemcpyDeviceToHost, p->stream));
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -643,6 +498,50 @@ bec_status bec_profile_stop(bec_problem* p, bec_kernel_time* out, int cap, int* 
   *count = (int)agg.size();
   for (int i = 0; i < (int)agg.size() && i < cap; ++i) out[i] = agg[i];
   return BEC_OK;
+}
+
+long long bec_learned_num_weights(const bec_problem* p) { return p ? net_num_weights(p) : 0; }
+
+static bec_status need_net(const bec_problem* p) {
+  if (p == nullptr || p->net == nullptr) return einval("not a BEC_ROUTE_LEARNED problem");
+  return BEC_OK;
+}
+
+bec_status bec_learned_get_weights(bec_problem* p, float* host) {
+  BEC_TRY(need_net(p));
+  if (host == nullptr) return einval("null host pointer");
+  return net_get_weights(p, host);
+}
+
+bec_status bec_learned_set_weights(bec_problem* p, const float* host) {
+  BEC_TRY(need_net(p));
+  if (host == nullptr) return einval("null host pointer");
+  return net_set_weights(p, host);
+}
+
+bec_status bec_learned_train(bec_problem* p, int steps, int batch, double lr,
+                             unsigned long long seed, double* loss_history) {
+  BEC_TRY(need_net(p));
+  if (steps < 0 || batch < 1 || batch > 32 || !(lr > 0.0)) return einval("bad training arguments");
+  if (p->eps <= 0.0) return einval("call bec_set_eps first");
+  return net_train(p, steps, batch, (float)lr, seed, loss_history);
+}
+
+bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx, const double* r,
+                                 const double* e_target, double* loss, float* grad) {
+  BEC_TRY(need_net(p));
+  if (lam_idx == nullptr || r == nullptr || e_target == nullptr || loss == nullptr)
+    return einval("null argument");
+  if (B < 1 || B > 32) return einval("B must lie in [1, 32]");
+  for (int b = 0; b < B; ++b)
+    if (lam_idx[b] < 0 || lam_idx[b] > p->N / 2) return einval("frequency index out of range");
+  if (p->eps <= 0.0) return einval("call bec_set_eps first");
+  return net_loss_grad(p, B, lam_idx, r, e_target, loss, grad);
+}
+
+long long bec_learned_fallbacks(bec_problem* p) {
+  if (p == nullptr || p->net == nullptr) return -1;
+  return net_fallbacks(p);
 }
 
 const char* bec_status_string(bec_status s) {

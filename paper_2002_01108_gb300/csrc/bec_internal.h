@@ -63,6 +63,15 @@ struct MgState {
   std::vector<MgLevel> lv;
 };
 
+struct NetState;   // learned correction (bec_net.cu)
+
+// One Arnoldi iteration captured as a CUDA graph (batched solves).
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;   // kernel launches inside the graph
+  bool warm = false;       // ran eagerly once
+};
+
 }  // namespace bec
 
 struct bec_problem {
@@ -99,7 +108,40 @@ struct bec_problem {
   bec::Profiler prof;
   double* kcoef = nullptr;      // variable a: tau K row [centre, W, E, S, N] x J
   bec::MgState mg;              // BEC_ROUTE_MG hierarchy
+  bec::NetState* net = nullptr;  // BEC_ROUTE_LEARNED network
+  std::vector<bec::IterGraph> graphs;   // per Arnoldi index j (batched solves)
+  int graph_mode = -1;          // left / flexible flags the graphs were captured with
 };
+
+namespace bec {
+
+// Restarted (F)GMRES as a resumable state machine (bec_gmres.cpp).
+struct GmresRun {
+  enum State { BEGIN, AFTER_BEGIN, CYCLE, AFTER_CYCLE, ITER, AFTER_ITER, FINISH, AFTER_FINISH, DONE };
+  bec_problem* p = nullptr;
+  const double* f = nullptr;
+  double* u = nullptr;
+  bec_gmres_opts o{};
+  bool use_graphs = false;
+  State state = BEGIN;
+  bec_status status = BEC_OK;
+  double ref = 0.0, monitored = 1.0, true_relres = 0.0;
+  int iters = 0, restarts = 0, j = 0, k = 0, beta_slot = 1;
+  bool converged = false, x_nonzero = false, zero_rhs = false;
+  std::vector<const double*> Vp, Zp;
+};
+void gmres_run_init(GmresRun& r, bec_problem* p, const double* f, double* u,
+                    const bec_gmres_opts& o, bool use_graphs);
+bec_status gmres_run_step(GmresRun& r, bool* enqueued);
+void gmres_run_info(const GmresRun& r, bec_gmres_info* info);
+bec_status gmres_run_result(const GmresRun& r);
+bec_status gmres_solve_one(bec_problem* p, const double* f, double* u,
+                           const bec_gmres_opts* o, bec_gmres_info* info);
+bec_status check_gmres_opts(const bec_problem* p, const bec_gmres_opts* o);
+// z = P_eps^{-1} (s y), s = *scale_dev (1 if null)
+bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* scale_dev);
+
+}  // namespace bec
 
 namespace bec {
 
@@ -153,11 +195,26 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes);
 void mg_free(bec_problem* p);
 // One V-cycle for every frequency: level-0 b -> level-0 x.
 bec_status mg_vcycle(bec_problem* p);
+// r = b - B x on the finest level for every frequency ([K][J] complex arrays)
+bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void* b);
 // spec[k][q] = sum_j e^{-2 pi i jk/N} eps^{j/N} (s y)[j][q], k <= N/2 (s = *scale_dev or 1)
 bec_status launch_time_fwd(bec_problem* p, const double* y, void* spec, int fp64,
                            const double* scale_dev);
 // z[j][q] = eps^{-j/N} N^{-1} sum_k spec_k e^{2 pi i jk/N} (Hermitian extension)
 bec_status launch_time_inv(bec_problem* p, const void* spec, double* z, int fp64);
+
+// ---- learned correction (bec_net.cu)
+bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp32_acts, int bmax);
+void net_free(bec_problem* p);
+bec_status net_correct(bec_problem* p);   // after the V-cycle: x += judged correction
+bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
+                     double* loss_hist);
+long long net_num_weights(const bec_problem* p);
+bec_status net_get_weights(bec_problem* p, float* host);
+bec_status net_set_weights(bec_problem* p, const float* host);
+bec_status net_loss_grad(bec_problem* p, int B, const int* lams, const double* r, const double* et,
+                         double* loss_out, float* grad_host);
+long long net_fallbacks(bec_problem* p);
 
 // ---- stencils (bec_stencil.cu)
 // number of blocks (partial sums) the residual-norm kernel writes

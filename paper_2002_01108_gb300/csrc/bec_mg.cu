@@ -278,6 +278,17 @@ MgArgs<T> level_args(const bec_problem* p, const MgLevel& L) {
   return a;
 }
 
+// Profile names per level (level 0 is the finest grid).
+#define BEC_LV_NAMES(base)                                                                \
+  {base "[l0]", base "[l1]", base "[l2]", base "[l3]", base "[l4]", base "[l5]", base "[l6]", \
+   base "[l7]", base "[l8]", base "[l9]", base "[l10]"}
+const char* const kSmooth0Names[] = BEC_LV_NAMES("mg_smooth0_kernel");
+const char* const kSmoothNames[] = BEC_LV_NAMES("mg_smooth_kernel");
+const char* const kResidNames[] = BEC_LV_NAMES("mg_residual_kernel");
+const char* const kRestrictNames[] = BEC_LV_NAMES("mg_restrict_kernel");
+const char* const kProlongNames[] = BEC_LV_NAMES("mg_prolong_add_kernel");
+#undef BEC_LV_NAMES
+
 dim3 mg_grid(long long J, int K) {
   return dim3((unsigned)((J + kMgThreads - 1) / kMgThreads),
               (unsigned)((K + kFreqChunk - 1) / kFreqChunk));
@@ -296,23 +307,23 @@ bec_status vcycle_t(bec_problem* p) {
     BEC_LAUNCH_BEGIN(p);
     mg_smooth_kernel<T, true><<<g, kMgThreads, 0, p->stream>>>(
         static_cast<V*>(c.x), nullptr, static_cast<const V*>(c.b), a);
-    BEC_LAUNCH_CHECK(p, "mg_smooth_kernel");
+    BEC_LAUNCH_CHECK(p, kSmooth0Names[l]);
     for (int s = 1; s < p->mg.pre; ++s) {
       BEC_LAUNCH_BEGIN(p);
       mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
           static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
-      BEC_LAUNCH_CHECK(p, "mg_smooth_kernel");
+      BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
       std::swap(c.x, c.r);
     }
     BEC_LAUNCH_BEGIN(p);
     mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
         static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
-    BEC_LAUNCH_CHECK(p, "mg_residual_kernel");
+    BEC_LAUNCH_CHECK(p, kResidNames[l]);
     MgLevel& n = lv[l + 1];
     BEC_LAUNCH_BEGIN(p);
     mg_restrict_kernel<T><<<mg_grid(n.J, K), kMgThreads, 0, p->stream>>>(
         static_cast<V*>(n.b), static_cast<const V*>(c.r), n.m, c.m, K);
-    BEC_LAUNCH_CHECK(p, "mg_restrict_kernel");
+    BEC_LAUNCH_CHECK(p, kRestrictNames[l]);
   }
   {
     MgLevel& c = lv[L - 1];
@@ -328,13 +339,13 @@ bec_status vcycle_t(bec_problem* p) {
     BEC_LAUNCH_BEGIN(p);
     mg_prolong_add_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
         static_cast<V*>(c.x), static_cast<const V*>(n.x), c.m, n.m, K);
-    BEC_LAUNCH_CHECK(p, "mg_prolong_add_kernel");
+    BEC_LAUNCH_CHECK(p, kProlongNames[l]);
     const MgArgs<T> a = level_args<T>(p, c);
     for (int s = 0; s < p->mg.post; ++s) {
       BEC_LAUNCH_BEGIN(p);
       mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
           static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
-      BEC_LAUNCH_CHECK(p, "mg_smooth_kernel");
+      BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
       std::swap(c.x, c.r);
     }
   }
@@ -393,6 +404,7 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes) {
   const bool fp64 = p->desc.precision == BEC_PC_FP64;
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
   p->mg.K = p->N / 2 + 1;
+  if (m > 2047) return BEC_EINVAL;   // at most 11 levels (profile names)
   std::vector<double> SM = SM0, SK = SK0;
   int ml = m;
   while (true) {
@@ -436,6 +448,23 @@ void mg_free(bec_problem* p) {
   p->mg.lv.clear();
   if (p->kcoef) cudaFree(p->kcoef);
   p->kcoef = nullptr;
+}
+
+bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void* b) {
+  const MgLevel& L = p->mg.lv[0];
+  if (p->desc.precision == BEC_PC_FP64) {
+    BEC_LAUNCH_BEGIN(p);
+    mg_residual_kernel<double><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+        static_cast<double2*>(r), static_cast<const double2*>(x), static_cast<const double2*>(b),
+        level_args<double>(p, L));
+  } else {
+    BEC_LAUNCH_BEGIN(p);
+    mg_residual_kernel<float><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+        static_cast<float2*>(r), static_cast<const float2*>(x), static_cast<const float2*>(b),
+        level_args<float>(p, L));
+  }
+  BEC_LAUNCH_CHECK(p, "mg_residual_kernel[l0]");
+  return BEC_OK;
 }
 
 bec_status mg_vcycle(bec_problem* p) {

@@ -1,0 +1,885 @@
+// Learned route of P_eps^{-1} (BEC_ROUTE_LEARNED): one multigrid V-cycle per
+// shifted system, then a learned correction of what the V-cycle left,
+//     x_k <- x_k + P_0 (s c_k Net(R_0 (b_k - B_k x_k) / s, log a, lambda'_k)),
+// judged per frequency by the residual ||b_k - B_k x||: a frequency whose
+// residual the network does not reduce keeps the V-cycle result (the
+// multigrid is the fallback and the judge).  The network (see
+// bec_net_kernels.cuh) runs on the grid of spacing 2h with 4 levels and C
+// channels and is trained on the GPU, by these kernels, on pairs
+// (r, e* = B_k^{-1} r) that the multigrid itself generates: r is the residual
+// a V-cycle leaves for a random right-hand side, e* is obtained by repeated
+// V-cycles (defect correction).  Requires the FP32 preconditioner.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "bec_fft.cuh"
+#include "bec_internal.h"
+#include "bec_net_kernels.cuh"
+
+namespace bec {
+
+namespace {
+
+enum Act { A_X, A_H0, A_S0, A_R0, A_S1, A_R1, A_S2, A_R2, A_S3, A_P2, A_U2, A_P1, A_U1, A_P0,
+           A_U0, A_Y, NACT };
+
+int act_level(int a) {
+  switch (a) {
+    case A_X: case A_H0: case A_S0: case A_P0: case A_U0: case A_Y: return 0;
+    case A_R0: case A_S1: case A_P1: case A_U1: return 1;
+    case A_R1: case A_S2: case A_P2: case A_U2: return 2;
+    default: return 3;
+  }
+}
+
+constexpr int kT = 256;
+unsigned grid_for(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+}  // namespace
+
+struct NetState {
+  int C = 32;
+  bool fp32 = false;
+  int mf = 0;                    // fine grid
+  int sz[4] = {0, 0, 0, 0};      // network levels, sz[0] = (mf - 1) / 2
+  int Bmax = 0;
+  int cin[9], cout[9];
+  long long woff[10];
+  float* W = nullptr;            // FP32 master weights, all layers
+  float* G = nullptr;            // gradients
+  float* Mo = nullptr;           // Adam moments
+  float* Ve = nullptr;
+  float* wpart = nullptr;        // weight-gradient partials
+  long long wpart_n = 0;
+  void* act[NACT] = {};
+  void* grad[NACT] = {};
+  float* la_c = nullptr;         // coarse log a, centred
+  double a_mean = 1.0;
+  float* rc = nullptr;           // [Bmax][mc^2] complex
+  float* sinv = nullptr;         // per sample 1/s
+  float* cfac = nullptr;         // per sample s c_k
+  int* row = nullptr;            // per sample row of res / etgt (staged from the host)
+  int* lam = nullptr;            // per sample frequency index
+  int* iota = nullptr;           // 0, 1, ..., K-1 (rows = frequencies, no host staging)
+  const int* cur_row = nullptr;  // the index arrays the next features/loss calls use
+  const int* cur_lam = nullptr;
+  int* h_idx = nullptr;          // pinned staging of row/lam (2 Bmax)
+  float* efine = nullptr;        // [Bmax][J] complex: P_0 correction
+  float* res = nullptr;          // [K][J] complex residuals
+  float* etgt = nullptr;         // [K][J] complex targets
+  float* ework = nullptr;        // [K][J] complex defect-correction iterate
+  float* xnew = nullptr;         // [K][J] complex corrected iterate
+  double* part = nullptr;        // per-sample / per-frequency partial sums
+  double* h_part = nullptr;      // pinned mirror
+  int adam_t = 0;
+  long long fallbacks = 0;       // frequencies the judge kept at the V-cycle (last apply)
+  unsigned long long rng_ctr = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------ net kernels
+// rc[b][q] = R_0 res[row[b]] at coarse node q (complex = 2 channels)
+__global__ void feat_restrict_kernel(const float2* __restrict__ res, const int* __restrict__ row,
+                                     float2* __restrict__ rc, int mf, int mc, int B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mcc = (long long)mc * mc;
+  if (g >= B * mcc) return;
+  const int b = (int)(g / mcc), q = (int)(g - (long long)b * mcc);
+  const int cy = q / mc, cx = q % mc;
+  const float2* src = res + (long long)row[b] * mf * mf;
+  float2 acc = {0.f, 0.f};
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const float w = (dy == 0 ? 0.5f : 0.25f) * (dx == 0 ? 0.5f : 0.25f);
+      const float2 v = src[(long long)(2 * cy + 1 + dy) * mf + (2 * cx + 1 + dx)];
+      acc.x = fmaf(w, v.x, acc.x);
+      acc.y = fmaf(w, v.y, acc.y);
+    }
+  rc[g] = acc;
+}
+
+// one block per sample: s = rms(rc[b]); sinv = 1/s; cfac = s / |lambda'_k + tau a_mean 2 pi^2|
+__global__ void feat_scale_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
+                                  const float2* __restrict__ lamf, float* __restrict__ sinv,
+                                  float* __restrict__ cfac, long long mcc, float tau_a_2pi2) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < mcc; q += blockDim.x) {
+    const float2 v = rc[b * mcc + q];
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+    if ((int)threadIdx.x < st2) red[threadIdx.x] += red[threadIdx.x + st2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double rms = sqrt(red[0] / (double)mcc);
+    if (!(rms > 0.0)) rms = 1.0;
+    const float2 L = lamf[lam[b]];
+    const double mag = hypot((double)L.x + tau_a_2pi2, (double)L.y);
+    sinv[b] = (float)(1.0 / rms);
+    cfac[b] = (float)(rms / mag);
+  }
+}
+
+// X[b][q] = (Re rc / s, Im rc / s, log a, Re lambda', Im lambda')
+template <typename AT>
+__global__ void feat_fill_kernel(const float2* __restrict__ rc, const float* __restrict__ sinv,
+                                 const float* __restrict__ la_c, const int* __restrict__ lam,
+                                 const float2* __restrict__ lamf, AT* __restrict__ X, long long mcc,
+                                 int B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B * mcc) return;
+  const int b = (int)(g / mcc);
+  const long long q = g - (long long)b * mcc;
+  const float2 v = rc[g];
+  const float si = sinv[b];
+  const float2 L = lamf[lam[b]];
+  AT* d = X + g * 5;
+  d[0] = net::st<AT>(v.x * si);
+  d[1] = net::st<AT>(v.y * si);
+  d[2] = net::st<AT>(la_c[q]);
+  d[3] = net::st<AT>(L.x);
+  d[4] = net::st<AT>(L.y);
+}
+
+// efine[b][f] = P_0 (cfac_b (y0 + i y1)) at fine node f
+template <typename AT>
+__global__ void out_prolong_kernel(const AT* __restrict__ Y, const float* __restrict__ cfac,
+                                   float2* __restrict__ efine, int mc, int mf, int B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mff = (long long)mf * mf;
+  if (g >= B * mff) return;
+  const int b = (int)(g / mff), f = (int)(g - (long long)b * mff);
+  const int fy = f / mf, fx = f % mf;
+  const AT* src = Y + (long long)b * mc * mc * 2;
+  float ax = 0.f, ay = 0.f;
+  for (int a = 0; a < 2; ++a) {
+    int cy;
+    float wy;
+    if (fy & 1) { if (a) break; cy = (fy - 1) / 2; wy = 1.f; }
+    else { cy = fy / 2 - 1 + a; wy = 0.5f; }
+    if (cy < 0 || cy >= mc) continue;
+    for (int c2 = 0; c2 < 2; ++c2) {
+      int cx;
+      float wx;
+      if (fx & 1) { if (c2) break; cx = (fx - 1) / 2; wx = 1.f; }
+      else { cx = fx / 2 - 1 + c2; wx = 0.5f; }
+      if (cx < 0 || cx >= mc) continue;
+      const AT* v = src + ((long long)cy * mc + cx) * 2;
+      ax = fmaf(wy * wx, net::ld(v), ax);
+      ay = fmaf(wy * wx, net::ld(v + 1), ay);
+    }
+  }
+  const float c = cfac[b];
+  efine[g] = make_float2(c * ax, c * ay);
+}
+
+// one block per sample: part[2b] = ||efine - etgt[row]||^2, part[2b+1] = ||etgt[row]||^2
+__global__ void loss_parts_kernel(const float2* __restrict__ efine, const float2* __restrict__ etgt,
+                                  const int* __restrict__ row, double* __restrict__ part,
+                                  long long mff) {
+  __shared__ double rn[256], rd[256];
+  const int b = blockIdx.x;
+  const float2* t = etgt + (long long)row[b] * mff;
+  const float2* e = efine + (long long)b * mff;
+  double num = 0.0, den = 0.0;
+  for (long long f = threadIdx.x; f < mff; f += blockDim.x) {
+    const float2 tv = t[f], ev = e[f];
+    const double dx = (double)ev.x - tv.x, dy = (double)ev.y - tv.y;
+    num += dx * dx + dy * dy;
+    den += (double)tv.x * tv.x + (double)tv.y * tv.y;
+  }
+  rn[threadIdx.x] = num;
+  rd[threadIdx.x] = den;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      rn[threadIdx.x] += rn[threadIdx.x + s];
+      rd[threadIdx.x] += rd[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * b] = rn[0];
+    part[2 * b + 1] = rd[0];
+  }
+}
+
+// dL/dy: dy[b][q][c] = cfac_b * (P_0^T d)[q], d = 2 (efine - etgt) / (den_b B), P_0^T = 4 R_0
+template <typename AT>
+__global__ void loss_grad_kernel(const float2* __restrict__ efine, const float2* __restrict__ etgt,
+                                 const int* __restrict__ row, const double* __restrict__ part,
+                                 const float* __restrict__ cfac, AT* __restrict__ dY, int mf,
+                                 int mc, int B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mcc = (long long)mc * mc, mff = (long long)mf * mf;
+  if (g >= B * mcc) return;
+  const int b = (int)(g / mcc), q = (int)(g - (long long)b * mcc);
+  const int cy = q / mc, cx = q % mc;
+  const float2* e = efine + (long long)b * mff;
+  const float2* t = etgt + (long long)row[b] * mff;
+  const double k = 2.0 / (part[2 * b + 1] * B);
+  double ax = 0.0, ay = 0.0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const double w = (dy == 0 ? 0.5 : 0.25) * (dx == 0 ? 0.5 : 0.25);
+      const long long f = (long long)(2 * cy + 1 + dy) * mf + (2 * cx + 1 + dx);
+      ax += w * ((double)e[f].x - t[f].x);
+      ay += w * ((double)e[f].y - t[f].y);
+    }
+  const double c = 4.0 * k * cfac[b];
+  dY[g * 2] = net::st<AT>((float)(c * ax));
+  dY[g * 2 + 1] = net::st<AT>((float)(c * ay));
+}
+
+// counter-based standard normal pair (splitmix64 hash + Box-Muller)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void gauss_fill_kernel(float2* __restrict__ v, long long n, unsigned long long key) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const unsigned long long h = mix64(key ^ mix64((unsigned long long)g));
+  const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = ((float)((h >> 16) & 0xFFFFFF) + 0.5f) * (1.0f / 16777216.0f);
+  const float r = sqrtf(-2.f * logf(u1));
+  float sv, cv;
+  sincospif(2.f * u2, &sv, &cv);
+  v[g] = make_float2(r * cv, r * sv);
+}
+
+__global__ void axpy_c_kernel(float2* __restrict__ y, const float2* __restrict__ x, long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) {
+    const float2 a = y[g], b = x[g];
+    y[g] = make_float2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// out[k0 + b] = x[k0 + b] + efine[b]
+__global__ void add_corr_kernel(float2* __restrict__ out, const float2* __restrict__ x,
+                                const float2* __restrict__ efine, long long mff, int k0, int B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B * mff) return;
+  const long long o = (long long)k0 * mff + g;
+  const float2 a = x[o], e = efine[g];
+  out[o] = make_float2(a.x + e.x, a.y + e.y);
+}
+
+// one block per frequency: part[k] = ||r_k||^2
+__global__ void freq_sumsq_kernel(const float2* __restrict__ r, double* __restrict__ part,
+                                  long long mff) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (long long f = threadIdx.x; f < mff; f += blockDim.x) {
+    const float2 v = r[(long long)k * mff + f];
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+    if ((int)threadIdx.x < st2) red[threadIdx.x] += red[threadIdx.x + st2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[k] = red[0];
+}
+
+// keep the corrected iterate where it lowered the residual, else the V-cycle's
+__global__ void judge_select_kernel(float2* __restrict__ x, const float2* __restrict__ xnew,
+                                    const double* __restrict__ before, const double* __restrict__ after,
+                                    long long mff, int K, int* __restrict__ fallbacks) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)K * mff) return;
+  const int k = (int)(g / mff);
+  const bool take = after[k] < before[k];
+  if (take) x[g] = xnew[g];
+  if (g - (long long)k * mff == 0 && !take) atomicAdd(fallbacks, 1);
+}
+
+// ------------------------------------------------------------ dispatch helpers
+template <typename AT>
+bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m, int B, bool relu) {
+  NetState& n = *p->net;
+  const float* W = n.W + n.woff[layer];
+  const long long npix = (long long)B * m * m;
+  const unsigned g = (unsigned)((npix + net::kConvThreads - 1) / net::kConvThreads);
+  const int ci = n.cin[layer], co = n.cout[layer];
+  const AT* a = static_cast<const AT*>(in);
+  AT* o = static_cast<AT*>(out);
+  BEC_LAUNCH_BEGIN(p);
+#define BEC_CF(CI, CO)                                                                            \
+  if (ci == CI && co == CO) {                                                                     \
+    if (relu) net::conv3x3_fwd_kernel<AT, CI, CO, true><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
+    else net::conv3x3_fwd_kernel<AT, CI, CO, false><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
+  } else
+  BEC_CF(5, 4) BEC_CF(4, 4) BEC_CF(4, 2) BEC_CF(5, 32) BEC_CF(32, 32) BEC_CF(32, 2) {
+    set_error("unsupported network channel count");
+    return BEC_EUNSUPPORTED;
+  }
+#undef BEC_CF
+  BEC_LAUNCH_CHECK(p, "net_conv_fwd_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer, void* din, int m,
+                    int B) {
+  NetState& n = *p->net;
+  const float* W = n.W + n.woff[layer];
+  float* dW = n.G + n.woff[layer];
+  const long long npix = (long long)B * m * m;
+  const int ci = n.cin[layer], co = n.cout[layer];
+  const int nw = 9 * ci * co;
+  long long nblk = (npix + 255) / 256;
+  if (nblk > 512) nblk = 512;
+  const long long per = (npix + nblk - 1) / nblk;
+  const unsigned g = (unsigned)((npix + net::kConvThreads - 1) / net::kConvThreads);
+  const AT* a = static_cast<const AT*>(in);
+  const AT* d = static_cast<const AT*>(dout);
+  AT* di = static_cast<AT*>(din);
+#define BEC_CB(CI, CO)                                                                            \
+  if (ci == CI && co == CO) {                                                                     \
+    BEC_LAUNCH_BEGIN(p);                                                                          \
+    net::conv3x3_bwd_weight_kernel<AT, CI, CO><<<(unsigned)nblk, 256, 0, p->stream>>>(a, d, n.wpart, m, npix, per); \
+    BEC_LAUNCH_CHECK(p, "net_conv_wgrad_kernel");                                                 \
+    if (di) {                                                                                     \
+      BEC_LAUNCH_BEGIN(p);                                                                        \
+      net::conv3x3_bwd_data_kernel<AT, CI, CO><<<g, net::kConvThreads, 0, p->stream>>>(d, W, di, m, npix); \
+      BEC_LAUNCH_CHECK(p, "net_conv_dgrad_kernel");                                               \
+    }                                                                                             \
+  } else
+  BEC_CB(5, 4) BEC_CB(4, 4) BEC_CB(4, 2) BEC_CB(5, 32) BEC_CB(32, 32) BEC_CB(32, 2) {
+    set_error("unsupported network channel count");
+    return BEC_EUNSUPPORTED;
+  }
+#undef BEC_CB
+  BEC_LAUNCH_BEGIN(p);
+  net::reduce_parts_kernel<<<(nw + 255) / 256, 256, 0, p->stream>>>(n.wpart, (int)nblk, nw, dW);
+  BEC_LAUNCH_CHECK(p, "net_wgrad_reduce_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status restrict_ch(bec_problem* p, const void* in, void* out, int lf, int B, float scale,
+                       bool add) {
+  NetState& n = *p->net;
+  const int mf = n.sz[lf], mc = n.sz[lf + 1];
+  const long long cnt = (long long)B * mc * mc * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  if (add)
+    net::restrict_ch_kernel<AT, true><<<grid_for(cnt), kT, 0, p->stream>>>(
+        static_cast<const AT*>(in), static_cast<AT*>(out), mf, mc, n.C, cnt, scale);
+  else
+    net::restrict_ch_kernel<AT, false><<<grid_for(cnt), kT, 0, p->stream>>>(
+        static_cast<const AT*>(in), static_cast<AT*>(out), mf, mc, n.C, cnt, scale);
+  BEC_LAUNCH_CHECK(p, "net_restrict_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status prolong_ch(bec_problem* p, const void* in, const void* add_src, void* out, int lf, int B,
+                      float scale) {
+  NetState& n = *p->net;
+  const int mf = n.sz[lf], mc = n.sz[lf + 1];
+  const long long cnt = (long long)B * mf * mf * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  net::prolong_ch_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
+      static_cast<const AT*>(in), static_cast<const AT*>(add_src), static_cast<AT*>(out), mc, mf,
+      n.C, cnt, scale);
+  BEC_LAUNCH_CHECK(p, "net_prolong_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status relu_mask(bec_problem* p, void* d, const void* a, int level, int B) {
+  NetState& n = *p->net;
+  const long long cnt = (long long)B * n.sz[level] * n.sz[level] * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  net::relu_mask_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(static_cast<AT*>(d),
+                                                                 static_cast<const AT*>(a), cnt);
+  BEC_LAUNCH_CHECK(p, "net_relu_mask_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status add_into(bec_problem* p, void* d, const void* e, int level, int B) {
+  NetState& n = *p->net;
+  const long long cnt = (long long)B * n.sz[level] * n.sz[level] * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  net::add_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(static_cast<AT*>(d),
+                                                           static_cast<const AT*>(e), cnt);
+  BEC_LAUNCH_CHECK(p, "net_add_kernel");
+  return BEC_OK;
+}
+
+#define BEC_TRY(expr)            \
+  do {                           \
+    bec_status _s = (expr);      \
+    if (_s != BEC_OK) return _s; \
+  } while (0)
+
+// features of B samples (rows n.row, frequencies n.lam) from n.res into act[X]
+template <typename AT>
+bec_status features(bec_problem* p, int B) {
+  NetState& n = *p->net;
+  const int mc = n.sz[0];
+  const long long mcc = (long long)mc * mc;
+  const float2* lamf = p->tab.lamf32;
+  BEC_LAUNCH_BEGIN(p);
+  feat_restrict_kernel<<<grid_for(B * mcc), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.res), n.cur_row, reinterpret_cast<float2*>(n.rc), n.mf, mc, B);
+  BEC_LAUNCH_CHECK(p, "net_feat_restrict_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  feat_scale_kernel<<<B, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.rc), n.cur_lam, lamf,
+                                              n.sinv, n.cfac, mcc,
+                                              (float)(p->tau * n.a_mean * 2.0 * M_PI * M_PI));
+  BEC_LAUNCH_CHECK(p, "net_feat_scale_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  feat_fill_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.rc), n.sinv, n.la_c, n.cur_lam, lamf,
+      static_cast<AT*>(n.act[A_X]), mcc, B);
+  BEC_LAUNCH_CHECK(p, "net_feat_fill_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status forward(bec_problem* p, int B) {
+  NetState& n = *p->net;
+  void** a = n.act;
+  BEC_TRY(conv_fwd<AT>(p, a[A_X], 0, a[A_H0], n.sz[0], B, true));
+  BEC_TRY(conv_fwd<AT>(p, a[A_H0], 1, a[A_S0], n.sz[0], B, true));
+  BEC_TRY(restrict_ch<AT>(p, a[A_S0], a[A_R0], 0, B, 1.f, false));
+  BEC_TRY(conv_fwd<AT>(p, a[A_R0], 2, a[A_S1], n.sz[1], B, true));
+  BEC_TRY(restrict_ch<AT>(p, a[A_S1], a[A_R1], 1, B, 1.f, false));
+  BEC_TRY(conv_fwd<AT>(p, a[A_R1], 3, a[A_S2], n.sz[2], B, true));
+  BEC_TRY(restrict_ch<AT>(p, a[A_S2], a[A_R2], 2, B, 1.f, false));
+  BEC_TRY(conv_fwd<AT>(p, a[A_R2], 4, a[A_S3], n.sz[3], B, true));
+  BEC_TRY(prolong_ch<AT>(p, a[A_S3], a[A_S2], a[A_P2], 2, B, 1.f));
+  BEC_TRY(conv_fwd<AT>(p, a[A_P2], 5, a[A_U2], n.sz[2], B, true));
+  BEC_TRY(prolong_ch<AT>(p, a[A_U2], a[A_S1], a[A_P1], 1, B, 1.f));
+  BEC_TRY(conv_fwd<AT>(p, a[A_P1], 6, a[A_U1], n.sz[1], B, true));
+  BEC_TRY(prolong_ch<AT>(p, a[A_U1], a[A_S0], a[A_P0], 0, B, 1.f));
+  BEC_TRY(conv_fwd<AT>(p, a[A_P0], 7, a[A_U0], n.sz[0], B, true));
+  BEC_TRY(conv_fwd<AT>(p, a[A_U0], 8, a[A_Y], n.sz[0], B, false));
+  // the correction on the fine grid
+  const long long mff = (long long)n.mf * n.mf;
+  BEC_LAUNCH_BEGIN(p);
+  out_prolong_kernel<AT><<<grid_for(B * mff), kT, 0, p->stream>>>(
+      static_cast<const AT*>(a[A_Y]), n.cfac, reinterpret_cast<float2*>(n.efine), n.sz[0], n.mf, B);
+  BEC_LAUNCH_CHECK(p, "net_out_prolong_kernel");
+  return BEC_OK;
+}
+
+// gradients of every weight for the loss whose dL/dY is in grad[A_Y]
+template <typename AT>
+bec_status backward(bec_problem* p, int B) {
+  NetState& n = *p->net;
+  void** a = n.act;
+  void** d = n.grad;
+  BEC_TRY(conv_bwd<AT>(p, a[A_U0], d[A_Y], 8, d[A_U0], n.sz[0], B));
+  BEC_TRY(relu_mask<AT>(p, d[A_U0], a[A_U0], 0, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_P0], d[A_U0], 7, d[A_P0], n.sz[0], B));
+  // P0 = P U1 + S0:  dU1 = P^T dP0 = 4 R dP0,  dS0 = dP0 (+ more below)
+  BEC_TRY(restrict_ch<AT>(p, d[A_P0], d[A_U1], 0, B, 4.f, false));
+  BEC_TRY(relu_mask<AT>(p, d[A_U1], a[A_U1], 1, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_P1], d[A_U1], 6, d[A_P1], n.sz[1], B));
+  BEC_TRY(restrict_ch<AT>(p, d[A_P1], d[A_U2], 1, B, 4.f, false));
+  BEC_TRY(relu_mask<AT>(p, d[A_U2], a[A_U2], 2, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_P2], d[A_U2], 5, d[A_P2], n.sz[2], B));
+  BEC_TRY(restrict_ch<AT>(p, d[A_P2], d[A_S3], 2, B, 4.f, false));
+  BEC_TRY(relu_mask<AT>(p, d[A_S3], a[A_S3], 3, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_R2], d[A_S3], 4, d[A_R2], n.sz[3], B));
+  // S2 feeds R2 = R S2 and P2 = P S3 + S2:  dS2 = R^T dR2 + dP2 = P dR2 / 4 + dP2
+  BEC_TRY(prolong_ch<AT>(p, d[A_R2], d[A_P2], d[A_S2], 2, B, 0.25f));
+  BEC_TRY(relu_mask<AT>(p, d[A_S2], a[A_S2], 2, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_R1], d[A_S2], 3, d[A_R1], n.sz[2], B));
+  BEC_TRY(prolong_ch<AT>(p, d[A_R1], d[A_P1], d[A_S1], 1, B, 0.25f));
+  BEC_TRY(relu_mask<AT>(p, d[A_S1], a[A_S1], 1, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_R0], d[A_S1], 2, d[A_R0], n.sz[1], B));
+  BEC_TRY(prolong_ch<AT>(p, d[A_R0], d[A_P0], d[A_S0], 0, B, 0.25f));
+  BEC_TRY(relu_mask<AT>(p, d[A_S0], a[A_S0], 0, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_H0], d[A_S0], 1, d[A_H0], n.sz[0], B));
+  BEC_TRY(relu_mask<AT>(p, d[A_H0], a[A_H0], 0, B));
+  BEC_TRY(conv_bwd<AT>(p, a[A_X], d[A_H0], 0, nullptr, n.sz[0], B));
+  return BEC_OK;
+}
+
+// loss parts (per sample) and dL/dY for the samples in n.row against n.etgt
+template <typename AT>
+bec_status loss_and_dy(bec_problem* p, int B) {
+  NetState& n = *p->net;
+  const long long mff = (long long)n.mf * n.mf;
+  const long long mcc = (long long)n.sz[0] * n.sz[0];
+  BEC_LAUNCH_BEGIN(p);
+  loss_parts_kernel<<<B, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.efine),
+                                              reinterpret_cast<const float2*>(n.etgt), n.cur_row,
+                                              n.part, mff);
+  BEC_LAUNCH_CHECK(p, "net_loss_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  loss_grad_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.efine), reinterpret_cast<const float2*>(n.etgt), n.cur_row,
+      n.part, n.cfac, static_cast<AT*>(n.grad[A_Y]), n.mf, n.sz[0], B);
+  BEC_LAUNCH_CHECK(p, "net_loss_grad_kernel");
+  return BEC_OK;
+}
+
+bec_status set_samples(bec_problem* p, const int* rows, const int* lams, int B) {
+  NetState& n = *p->net;
+  for (int b = 0; b < B; ++b) {
+    n.h_idx[b] = rows[b];
+    n.h_idx[n.Bmax + b] = lams[b];
+  }
+  BEC_CUDA_TRY(cudaMemcpyAsync(n.row, n.h_idx, B * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  BEC_CUDA_TRY(cudaMemcpyAsync(n.lam, n.h_idx + n.Bmax, B * sizeof(int), cudaMemcpyHostToDevice,
+                               p->stream));
+  // the staging buffer is reused by the next call only after a stream sync
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  n.cur_row = n.row;
+  n.cur_lam = n.lam;
+  return BEC_OK;
+}
+
+bec_status adam_step(bec_problem* p, float lr) {
+  NetState& n = *p->net;
+  n.adam_t++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float lr_t = lr * sqrtf(1.f - powf(b2, (float)n.adam_t)) / (1.f - powf(b1, (float)n.adam_t));
+  const int nw = (int)n.woff[9];
+  BEC_LAUNCH_BEGIN(p);
+  net::adam_kernel<<<(nw + 255) / 256, 256, 0, p->stream>>>(n.W, n.Mo, n.Ve, n.G, nw, lr_t, b1, b2,
+                                                            1e-8f);
+  BEC_LAUNCH_CHECK(p, "net_adam_kernel");
+  return BEC_OK;
+}
+
+// Training pairs for every frequency: res = b - B V(b) for a random b, and
+// etgt = B^{-1} res by `sweeps` defect-correction V-cycles.
+bec_status make_pairs(bec_problem* p, int sweeps) {
+  NetState& n = *p->net;
+  MgLevel& L0 = p->mg.lv[0];
+  const long long tot = (long long)p->mg.K * L0.J;
+  BEC_LAUNCH_BEGIN(p);
+  gauss_fill_kernel<<<grid_for(tot), kT, 0, p->stream>>>(static_cast<float2*>(L0.b), tot,
+                                                         0xB5C0FFEEull + (n.rng_ctr++) * 0x100000001ull);
+  BEC_LAUNCH_CHECK(p, "net_gauss_fill_kernel");
+  // keep the right-hand side: res buffer first holds b
+  BEC_CUDA_TRY(cudaMemcpyAsync(n.ework, L0.b, tot * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
+  BEC_TRY(mg_vcycle(p));
+  BEC_TRY(mg_residual_level0(p, n.res, L0.x, n.ework));          // res = b - B V(b)
+  BEC_CUDA_TRY(cudaMemsetAsync(n.etgt, 0, tot * sizeof(float2), p->stream));
+  for (int it = 0; it < sweeps; ++it) {
+    BEC_TRY(mg_residual_level0(p, L0.b, n.etgt, n.res));          // b = res - B e
+    BEC_TRY(mg_vcycle(p));
+    BEC_LAUNCH_BEGIN(p);
+    axpy_c_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<float2*>(n.etgt),
+                                                       static_cast<const float2*>(p->mg.lv[0].x), tot);
+    BEC_LAUNCH_CHECK(p, "net_axpy_kernel");
+  }
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
+                   double* loss_hist) {
+  NetState& n = *p->net;
+  const int K = p->mg.K;
+  unsigned long long st = seed * 6364136223846793005ull + 1442695040888963407ull;
+  std::vector<int> rows(batch);
+  const int regen = (K + batch - 1) / batch;   // batches drawn from one set of pairs
+  for (int s = 0; s < steps; ++s) {
+    if (s % regen == 0) BEC_TRY(make_pairs(p, 12));
+    for (int b = 0; b < batch; ++b) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      rows[b] = (int)((st >> 33) % (unsigned long long)K);
+    }
+    BEC_TRY(set_samples(p, rows.data(), rows.data(), batch));
+    BEC_TRY(features<AT>(p, batch));
+    BEC_TRY(forward<AT>(p, batch));
+    BEC_TRY(loss_and_dy<AT>(p, batch));
+    BEC_TRY(backward<AT>(p, batch));
+    BEC_TRY(adam_step(p, lr));
+    if (loss_hist) {
+      BEC_CUDA_TRY(cudaMemcpyAsync(n.h_part, n.part, 2 * batch * sizeof(double),
+                                   cudaMemcpyDeviceToHost, p->stream));
+      BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+      double l = 0.0;
+      for (int b = 0; b < batch; ++b) l += n.h_part[2 * b] / n.h_part[2 * b + 1];
+      loss_hist[s] = l / batch;
+    }
+  }
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status correct_t(bec_problem* p) {
+  NetState& n = *p->net;
+  MgLevel& L0 = p->mg.lv[0];
+  const int K = p->mg.K;
+  const long long mff = (long long)n.mf * n.mf;
+  // residual the V-cycle left, and its norm per frequency
+  BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
+  BEC_LAUNCH_BEGIN(p);
+  freq_sumsq_kernel<<<K, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.res), n.part, mff);
+  BEC_LAUNCH_CHECK(p, "net_freq_norm_kernel");
+  for (int k0 = 0; k0 < K; k0 += n.Bmax) {
+    const int B = K - k0 < n.Bmax ? K - k0 : n.Bmax;
+    n.cur_row = n.iota + k0;
+    n.cur_lam = n.iota + k0;
+    BEC_TRY(features<AT>(p, B));
+    BEC_TRY(forward<AT>(p, B));
+    BEC_LAUNCH_BEGIN(p);
+    add_corr_kernel<<<grid_for(B * mff), kT, 0, p->stream>>>(
+        reinterpret_cast<float2*>(n.xnew), static_cast<const float2*>(L0.x),
+        reinterpret_cast<const float2*>(n.efine), mff, k0, B);
+    BEC_LAUNCH_CHECK(p, "net_add_correction_kernel");
+  }
+  // judge: keep the correction only where it lowered the residual
+  BEC_TRY(mg_residual_level0(p, L0.r, n.xnew, L0.b));
+  BEC_LAUNCH_BEGIN(p);
+  freq_sumsq_kernel<<<K, 256, 0, p->stream>>>(static_cast<const float2*>(L0.r), n.part + K, mff);
+  BEC_LAUNCH_CHECK(p, "net_freq_norm_kernel");
+  int* fb = reinterpret_cast<int*>(n.part + 2 * K);
+  BEC_CUDA_TRY(cudaMemsetAsync(fb, 0, sizeof(int), p->stream));
+  BEC_LAUNCH_BEGIN(p);
+  judge_select_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
+      static_cast<float2*>(L0.x), reinterpret_cast<const float2*>(n.xnew), n.part, n.part + K, mff,
+      K, fb);
+  BEC_LAUNCH_CHECK(p, "net_judge_kernel");
+  return BEC_OK;
+}
+
+bec_status dalloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc (learned correction)");
+    return BEC_ENOMEM;
+  }
+  return BEC_OK;
+}
+
+}  // namespace
+
+bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp32_acts, int bmax) {
+  if (p->desc.precision != BEC_PC_FP32) return BEC_EINVAL;
+  if (p->m < 31) {
+    set_error("the learned route needs nx >= 31 (4 network levels below the fine grid)");
+    return BEC_EINVAL;
+  }
+  NetState* n = new (std::nothrow) NetState();
+  if (n == nullptr) return BEC_ENOMEM;
+  p->net = n;
+  n->C = channels;
+  n->fp32 = fp32_acts != 0;
+  n->mf = p->m;
+  n->sz[0] = (p->m - 1) / 2;
+  for (int l = 1; l < 4; ++l) n->sz[l] = (n->sz[l - 1] - 1) / 2;
+  n->Bmax = bmax;
+  const int C = channels;
+  const int shapes[9][2] = {{5, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, 2}};
+  n->woff[0] = 0;
+  for (int i = 0; i < 9; ++i) {
+    n->cin[i] = shapes[i][0];
+    n->cout[i] = shapes[i][1];
+    n->woff[i + 1] = n->woff[i] + 9LL * shapes[i][0] * shapes[i][1];
+  }
+  const long long nw = n->woff[9];
+  bec_status s = BEC_OK;
+  auto chain = [&](bec_status r) { if (s == BEC_OK) s = r; };
+  chain(dalloc(reinterpret_cast<void**>(&n->W), nw * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->G), nw * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->Mo), nw * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->Ve), nw * sizeof(float)));
+  n->wpart_n = 512LL * 9 * 32 * 32;
+  chain(dalloc(reinterpret_cast<void**>(&n->wpart), n->wpart_n * sizeof(float)));
+  const size_t asz = n->fp32 ? sizeof(float) : sizeof(__nv_bfloat16);
+  for (int a = 0; a < NACT; ++a) {
+    const int l = act_level(a);
+    const int ch = a == A_X ? 5 : (a == A_Y ? 2 : C);
+    const size_t bytes = (size_t)bmax * n->sz[l] * n->sz[l] * ch * asz;
+    chain(dalloc(&n->act[a], bytes));
+    chain(dalloc(&n->grad[a], bytes));
+  }
+  const long long mcc = (long long)n->sz[0] * n->sz[0];
+  const long long mff = (long long)p->m * p->m;
+  const long long K = p->N / 2 + 1;
+  chain(dalloc(reinterpret_cast<void**>(&n->la_c), mcc * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->rc), (size_t)bmax * mcc * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->sinv), bmax * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->cfac), bmax * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->row), bmax * sizeof(int)));
+  chain(dalloc(reinterpret_cast<void**>(&n->lam), bmax * sizeof(int)));
+  chain(dalloc(reinterpret_cast<void**>(&n->iota), K * sizeof(int)));
+  chain(dalloc(reinterpret_cast<void**>(&n->efine), (size_t)bmax * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->res), (size_t)K * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->etgt), (size_t)K * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->ework), (size_t)K * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->xnew), (size_t)K * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(2 * K + 2 * bmax + 2) * sizeof(double)));
+  if (s == BEC_OK) {
+    if (cudaMallocHost(reinterpret_cast<void**>(&n->h_idx), 2 * bmax * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&n->h_part), (2 * K + 2 * bmax + 2) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      s = BEC_ENOMEM;
+    }
+  }
+  if (s != BEC_OK) return s;
+  // coarse log a (centred by the mean over all nodes) and the mean of a
+  const int m2 = p->m + 2;
+  std::vector<double> la((size_t)m2 * m2);
+  double mean_la = 0.0, mean_a = 0.0;
+  for (size_t i = 0; i < la.size(); ++i) {
+    const double a = a_nodes ? a_nodes[i] : p->a;
+    la[i] = std::log(a);
+    mean_la += la[i];
+    mean_a += a;
+  }
+  mean_la /= (double)la.size();
+  n->a_mean = mean_a / (double)la.size();
+  std::vector<float> lac(mcc);
+  for (int cy = 0; cy < n->sz[0]; ++cy)
+    for (int cx = 0; cx < n->sz[0]; ++cx)
+      lac[(size_t)cy * n->sz[0] + cx] = (float)(la[(size_t)(2 * cy + 2) * m2 + (2 * cx + 2)] - mean_la);
+  BEC_CUDA_TRY(cudaMemcpy(n->la_c, lac.data(), lac.size() * sizeof(float), cudaMemcpyHostToDevice));
+  std::vector<int> io(K);
+  for (long long k = 0; k < K; ++k) io[k] = (int)k;
+  BEC_CUDA_TRY(cudaMemcpy(n->iota, io.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+  // He-normal initial weights from a fixed counter-based sequence, last layer x 0.1
+  std::vector<float> w(nw);
+  unsigned long long z = 0x243F6A8885A308D3ull;
+  for (int i = 0; i < 9; ++i) {
+    const double sd = std::sqrt(2.0 / (9.0 * n->cin[i])) * (i == 8 ? 0.1 : 1.0);
+    for (long long j = n->woff[i]; j < n->woff[i + 1]; ++j) {
+      z = z * 6364136223846793005ull + 1442695040888963407ull;
+      const double u1 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+      z = z * 6364136223846793005ull + 1442695040888963407ull;
+      const double u2 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+      w[j] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
+    }
+  }
+  BEC_CUDA_TRY(cudaMemcpy(n->W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice));
+  BEC_CUDA_TRY(cudaMemset(n->Mo, 0, nw * sizeof(float)));
+  BEC_CUDA_TRY(cudaMemset(n->Ve, 0, nw * sizeof(float)));
+  return BEC_OK;
+}
+
+void net_free(bec_problem* p) {
+  NetState* n = p->net;
+  if (n == nullptr) return;
+  void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->la_c, n->rc, n->sinv, n->cfac, n->row,
+                  n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int a = 0; a < NACT; ++a) {
+    if (n->act[a]) cudaFree(n->act[a]);
+    if (n->grad[a]) cudaFree(n->grad[a]);
+  }
+  if (n->h_idx) cudaFreeHost(n->h_idx);
+  if (n->h_part) cudaFreeHost(n->h_part);
+  delete n;
+  p->net = nullptr;
+}
+
+bec_status net_correct(bec_problem* p) {
+  return p->net->fp32 ? correct_t<float>(p) : correct_t<__nv_bfloat16>(p);
+}
+
+bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
+                     double* loss_hist) {
+  if (batch < 1 || batch > p->net->Bmax) return BEC_EINVAL;
+  return p->net->fp32 ? train_t<float>(p, steps, batch, lr, seed, loss_hist)
+                      : train_t<__nv_bfloat16>(p, steps, batch, lr, seed, loss_hist);
+}
+
+long long net_num_weights(const bec_problem* p) { return p->net ? p->net->woff[9] : 0; }
+
+bec_status net_get_weights(bec_problem* p, float* host) {
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(host, p->net->W, p->net->woff[9] * sizeof(float), cudaMemcpyDeviceToHost));
+  return BEC_OK;
+}
+
+bec_status net_set_weights(bec_problem* p, const float* host) {
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(p->net->W, host, p->net->woff[9] * sizeof(float), cudaMemcpyHostToDevice));
+  p->net->adam_t = 0;
+  BEC_CUDA_TRY(cudaMemset(p->net->Mo, 0, p->net->woff[9] * sizeof(float)));
+  BEC_CUDA_TRY(cudaMemset(p->net->Ve, 0, p->net->woff[9] * sizeof(float)));
+  return BEC_OK;
+}
+
+namespace {
+__global__ void c128_to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b,
+                                   long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) b[g] = make_float2((float)a[g].x, (float)a[g].y);
+}
+
+template <typename AT>
+bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, const double* et,
+                       double* loss_out, float* grad_host) {
+  NetState& n = *p->net;
+  const long long mff = (long long)n.mf * n.mf;
+  const long long tot = (long long)B * mff;
+  BEC_LAUNCH_BEGIN(p);
+  c128_to_c64_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<const double2*>(r),
+                                                          reinterpret_cast<float2*>(n.res), tot);
+  BEC_LAUNCH_CHECK(p, "net_convert_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  c128_to_c64_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<const double2*>(et),
+                                                          reinterpret_cast<float2*>(n.etgt), tot);
+  BEC_LAUNCH_CHECK(p, "net_convert_kernel");
+  std::vector<int> rows(B);
+  for (int b = 0; b < B; ++b) rows[b] = b;
+  BEC_TRY(set_samples(p, rows.data(), lams, B));
+  BEC_TRY(features<AT>(p, B));
+  BEC_TRY(forward<AT>(p, B));
+  BEC_TRY(loss_and_dy<AT>(p, B));
+  BEC_TRY(backward<AT>(p, B));
+  BEC_CUDA_TRY(cudaMemcpyAsync(n.h_part, n.part, 2 * B * sizeof(double), cudaMemcpyDeviceToHost,
+                               p->stream));
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  double l = 0.0;
+  for (int b = 0; b < B; ++b) l += n.h_part[2 * b] / n.h_part[2 * b + 1];
+  *loss_out = l / B;
+  if (grad_host)
+    BEC_CUDA_TRY(cudaMemcpy(grad_host, n.G, n.woff[9] * sizeof(float), cudaMemcpyDeviceToHost));
+  return BEC_OK;
+}
+}  // namespace
+
+bec_status net_loss_grad(bec_problem* p, int B, const int* lams, const double* r, const double* et,
+                         double* loss_out, float* grad_host) {
+  if (B < 1 || B > p->net->Bmax || B > p->mg.K) {   // samples are staged in rows 0..B-1 of K
+    set_error("B must lie in [1, min(32, N/2 + 1)]");
+    return BEC_EINVAL;
+  }
+  return p->net->fp32 ? loss_grad_t<float>(p, B, lams, r, et, loss_out, grad_host)
+                      : loss_grad_t<__nv_bfloat16>(p, B, lams, r, et, loss_out, grad_host);
+}
+
+long long net_fallbacks(bec_problem* p) {
+  if (p->net == nullptr) return -1;
+  int fb = 0;
+  cudaStreamSynchronize(p->stream);
+  cudaMemcpy(&fb, reinterpret_cast<int*>(p->net->part + 2 * p->mg.K), sizeof(int),
+             cudaMemcpyDeviceToHost);
+  return fb;
+}
+
+}  // namespace bec

@@ -1,0 +1,81 @@
+"""Batched solves of independent instances of uneven grid size, N and eps
+(bec_batch_*): every instance reaches its tolerance, each equals the same
+instance solved alone (bit for bit: the same kernels run, replayed from CUDA
+graphs), and small instances equal the oracle's sequential stepping."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from workloads import batch_cases, heat_case_2d
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2002_01108_gb300 import build
+    build.build()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _cases():
+    out = []
+    for i, (m, N, eps) in enumerate([(31, 8, 1e-3), (63, 32, 0.05), (15, 64, 0.1), (31, 16, 1.0),
+                                     (63, 8, 1e-4), (7, 4, 0.5), (31, 32, 0.02)]):
+        out.append(heat_case_2d(seed=40 + i, m=m, N=N, eps=eps))
+    return out
+
+
+@pytest.mark.parametrize("use_graphs,nstreams", [(True, 3), (False, 1)])
+def test_batch_equals_single_solves_and_the_oracle(use_graphs, nstreams):
+    import torch
+    from paper_2002_01108_gb300 import Batch, Problem
+    cases = _cases()
+    specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
+    fs = [dev(O.build_rhs(c.u0, c.fsrc, c.tau)) for c in cases]
+    us = [torch.empty_like(f) for f in fs]
+    with Batch(specs, nstreams=nstreams, use_graphs=use_graphs) as b:
+        for rep in range(2):       # the second solve replays the captured graphs
+            infos = b.solve(fs, us, restart=10, rtol=1e-10)
+            assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-10 for i in infos), infos
+        launches = b.launches
+    assert launches > 0
+    torch.cuda.synchronize()
+    for c, f, u, info in zip(cases, fs, us, infos):
+        with Problem(2, c.m, c.N, precision="fp32", flexible=True, max_restart=10) as p:
+            p.set_eps(c.eps)
+            u1, i1 = p.gmres_solve(f, restart=10, rtol=1e-10, flexible=True)
+            torch.cuda.synchronize()
+            assert i1["iters"] == info["iters"]
+            assert torch.equal(u1, u)
+        K = O.fd_stiffness(2, c.m)
+        uref = O.timestep_solve(O.build_rhs(c.u0, c.fsrc, c.tau), sp.identity(K.shape[0], format="csr"),
+                                K, c.tau)
+        assert np.linalg.norm(u.cpu().numpy() - uref) / np.linalg.norm(uref) <= 1e-8
+
+
+def test_batch_64_uneven_instances():
+    """64 instances, side in {63, 127, 255}, N in {32..512}, ln eps ~ U[ln 1e-4,
+    ln sqrt(tau)]: FP32 preconditioner, FP64 FGMRES(10), every instance to
+    RES <= 1e-8."""
+    import torch
+    from paper_2002_01108_gb300 import Batch
+    cases = batch_cases(seed=4, count=64)
+    specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
+    with Batch(specs, nstreams=8, use_graphs=True) as b:
+        fs, us = [], []
+        for i, c in enumerate(cases):
+            f = torch.empty(c.fsrc.shape, dtype=torch.float64, device="cuda")
+            b.build_rhs(i, dev(c.u0), dev(c.fsrc), f)
+            fs.append(f)
+            us.append(torch.empty_like(f))
+        infos = b.solve(fs, us, restart=10, rtol=1e-8)
+        assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-8 for i in infos)
+        assert b.unknowns == sum(c.U for c in cases)
