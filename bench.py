@@ -58,10 +58,37 @@ BYTES_PER_UNIT = {"fp64": {"dst_rows_kernel": 16.0, "dst_cols_kernel": 16.0, "ti
                            "apply_L_kernel": 16.0},
                   "fp32": {"dst_rows_kernel": 12.0, "dst_cols_kernel": 8.0, "time_pass_kernel": 8.0,
                            "apply_L_kernel": 16.0}}
+# Multigrid route (variable coefficient): algorithmic bytes per unit, a unit
+# being one (grid point, frequency) pair of the level the kernel runs on, in
+# complex words V (8 B in FP32, 16 B in FP64): smoothing from zero reads b and
+# writes x (2V), a smoothing sweep and the residual read x, b and write one
+# array (3V), restriction reads the fine array and writes a quarter (1.25V),
+# prolongation reads a quarter and updates the fine array (2.25V).  The time
+# transforms move one real 8-byte word per space-time unknown plus the half
+# spectrum (0.5V per unknown).
+MG_WORDS = {"mg_smooth0_kernel": 2.0, "mg_smooth_kernel": 3.0, "mg_residual_kernel": 3.0,
+            "mg_restrict_kernel": 1.25, "mg_prolong_add_kernel": 2.25}
+MG_FLOPS = {"mg_smooth0_kernel": 14.0, "mg_smooth_kernel": 98.0, "mg_residual_kernel": 84.0,
+            "mg_restrict_kernel": 36.0, "mg_prolong_add_kernel": 10.0}
+
 # FP64 FMA peak of GB300 from unit counts: 2 FP64 FMA / clock / SM x 152 SMs x
 # 2.07 GHz x 2 flops = 1.26 TFLOP/s (a throughput probe measured 1.20 TFLOP/s
 # at 1.99 GHz).  FP32: 128 lanes / SM -> 80.5 TFLOP/s.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+# FP32 FMA peak from unit counts: 128 FP32 lanes / SM x 152 SMs x 2.07 GHz x 2
+FP32_PEAK_TFLOPS = 128 * 152 * 2.07e9 * 2 / 1e12
+# the learned correction's network: 9 convolutions (c_in, c_out, level) on the
+# grid of spacing 2h and three below it, C = 32 channels
+NET_LAYERS = [(5, 32, 0), (32, 32, 0), (32, 32, 1), (32, 32, 2), (32, 32, 3), (32, 32, 2),
+              (32, 32, 1), (32, 32, 0), (32, 2, 0)]
+
+
+def net_fwd_flops(m: int) -> float:
+    """FLOPs of one forward pass of the network for one frequency (2 per MAC)."""
+    sz = [(m - 1) // 2]
+    for _ in range(3):
+        sz.append((sz[-1] - 1) // 2)
+    return sum(2.0 * 9 * ci * co * sz[l] ** 2 for ci, co, l in NET_LAYERS)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of each kernel at this workload (see profiles/); None = not captured for the
 # current build of the kernel.
@@ -317,6 +344,146 @@ def roofline(form, kernels, U):
     return roof
 
 
+def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16):
+    """The variable-coefficient workload (255^2, N = 256, a = exp(GRF)) solved
+    with one multigrid V-cycle per shifted system inside FGMRES(30); with
+    route="learned" the V-cycle is followed by the learned correction, whose
+    network is first trained on the GPU (timed apart from the solves)."""
+    import torch
+
+    from paper_2002_01108_gb300 import Problem
+    from workloads import grf_log_coefficient, heat_case_2d
+    m, N = M_SIDE, N_STEPS
+    eps = math.sqrt(1.0 / N) / 2
+    import numpy as np
+    a = np.exp(grf_log_coefficient(seed=5, m=m))
+    case = heat_case_2d(seed=6, m=m, N=N, eps=eps)
+    prob = Problem(2, m, N, route=route, a_nodes=a, precision=precision, flexible=True,
+                   max_restart=RESTART)
+    prob.set_eps(eps)
+    training = None
+    if train_steps:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = prob.learned_train(steps=train_steps, batch=train_batch, lr=2e-3, seed=3)
+        dt = time.perf_counter() - t0
+        training = {"steps": train_steps, "batch": train_batch, "s": dt,
+                    "ms_per_step": dt * 1e3 / train_steps,
+                    "loss_first5": float(np.mean(hist[:5])), "loss_last20": float(np.mean(hist[-20:])),
+                    "note": "Adam on pairs (V-cycle residual of a Gaussian right-hand side, 12 defect-"
+                            "correction V-cycles for its solution), fresh pairs every "
+                            "ceil((N/2+1)/batch) steps; includes their generation"}
+    f = prob.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
+    u = torch.empty_like(f)
+    kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=True)
+    for _ in range(max(1, args.warmup)):
+        prob.gmres_solve(f, u, **kw)
+    torch.cuda.synchronize()
+    prob.profile_start(1 << 16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(prob.stream)
+    launches0 = prob.launches
+    for _ in range(args.steps):
+        _, info = prob.gmres_solve(f, u, **kw)
+    ev1.record(prob.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    kernels = prob.profile_stop()
+    launches = prob.launches - launches0
+    U = prob.U
+    K = N // 2 + 1
+    ratios = prob.learned_residual_ratios() if route == "learned" else None
+    prob.close()
+    # roofline of the dominant kernel
+    dom = max(kernels.items(), key=lambda kv: kv[1][1])[0]
+    n, tot = kernels[dom]
+    avg = tot / n
+    word = 8 if precision == "fp32" else 16
+    base = dom.split("[")[0]
+    if base == "net_conv_fwd_kernel":
+        # all 9 layers share the name: FLOPs of whole forward passes over their time
+        applies = n / len(NET_LAYERS)
+        ach = applies * K * net_fwd_flops(m) / (tot / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "algorithmic_per_unit": f"{net_fwd_flops(m) / 1e6:.1f} MFLOP per frequency per apply",
+                "units_per_launch": "one layer of 129 or fewer frequencies (batches of 32)",
+                "avg_launch_ms": avg}
+    elif base in MG_WORDS:
+        lvl = int(dom.split("[l")[1].rstrip("]"))
+        ml = m
+        for _ in range(lvl):
+            ml = (ml - 1) // 2
+        units = K * ml * ml
+        bpu, fpu = MG_WORDS[base] * word, MG_FLOPS[base]
+    else:
+        units = U
+        bpu, fpu = 8 + 0.5 * word, 5.0 * LOG2T / 2
+    if base != "net_conv_fwd_kernel":
+        peaks, src = measured_peaks()
+        if precision == "fp64":
+            ach = fpu * units / (avg / 1e3) / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "algorithmic_per_unit": f"{fpu:.0f} flop", "units_per_launch": units}
+        else:
+            ach = bpu * units / (avg / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                    "algorithmic_per_unit": f"{bpu:.1f} B", "units_per_launch": units}
+        roof["avg_launch_ms"] = avg
+    out = {"value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iters"],
+           "true_relres": info["true_relres"], "gpu_launches": launches, "roofline": roof,
+           "kernels": kernel_table(kernels)}
+    if route == "learned":
+        out["training"] = training
+        out["residual_ratio_last_apply"] = {"mean": float(np.mean(ratios)), "min": float(np.min(ratios)),
+                                            "max": float(np.max(ratios))}
+    return out
+
+
+def measure_batch(args):
+    """The uneven batch: 64 instances, side in {63, 127, 255}, N in {32, ..., 512},
+    ln eps ~ U[ln 1e-4, ln sqrt(tau)], FP32 preconditioner in FP64 FGMRES(10)
+    to RES 1e-8.  Timed as one bec_batch_solve (rounds over 8 streams, Arnoldi
+    iterations replayed from CUDA graphs) and, for comparison, as the same
+    instances solved one after another by bec_gmres_solve."""
+    import torch
+    from paper_2002_01108_gb300 import Batch
+    from workloads import batch_cases
+    cases = batch_cases(seed=4, count=64)
+    specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
+    out = {"workload": "64 instances of 2D heat: side in {63,127,255}, N in {32,...,512}, "
+                       "ln eps ~ U[ln 1e-4, ln sqrt(tau)] (seed 4); FP32 sine-transform P_eps^-1 "
+                       "in FP64 FGMRES(10) to RES 1e-8"}
+    for label, graphs, nstreams in (("batched_graphs_8_streams", True, 8),
+                                    ("batched_no_graphs_1_stream", False, 1)):
+        with Batch(specs, nstreams=nstreams, use_graphs=graphs) as b:
+            fs, us = [], []
+            for i, c in enumerate(cases):
+                f = torch.empty(c.fsrc.shape, dtype=torch.float64, device="cuda")
+                b.build_rhs(i, torch.from_numpy(c.u0).cuda(), torch.from_numpy(c.fsrc).cuda(), f)
+                fs.append(f)
+                us.append(torch.empty_like(f))
+            torch.cuda.synchronize()
+            for _ in range(max(2, args.warmup)):        # the second call captures the graphs
+                b.solve(fs, us, restart=10, rtol=RTOL)
+            torch.cuda.synchronize()
+            l0 = b.launches
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                infos = b.solve(fs, us, restart=10, rtol=RTOL)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / args.steps
+            out[label] = {"value": b.unknowns / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+                          "gpu_launches": (b.launches - l0) // args.steps,
+                          "iterations_total": sum(i["iters"] for i in infos),
+                          "max_true_relres": max(i["true_relres"] for i in infos)}
+            out["unknowns"] = b.unknowns
+            del fs, us
+    return out
+
+
 def kernel_table(kernels):
     total_ms = sum(ms for _, ms in kernels.values())
     return {name: {"launches": n, "ms": round(ms, 4),
@@ -374,6 +541,17 @@ def run_gpu(args):
             "roofline": roofline(other, o["kernels"], U), "kernels": kernel_table(o["kernels"]),
             "note": "same workload and tolerance; FP32/complex64 P_eps^-1 inside FP64 FGMRES"
                     if other == "fp32" else "same workload; plain FP64 form"}}
+    if not args.no_other_form:
+        line["variable_coefficient_multigrid"] = {
+            "workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, a=exp(g), g a Gaussian random field "
+                        "(squared-exponential kernel, length 0.1, sigma 1), eps=sqrt(tau)/2, one V-cycle "
+                        "per shifted system (damped Jacobi 1+1, Galerkin coarse grids), FGMRES(30) "
+                        "to RES 1e-8",
+            "fp32": measure_mg("fp32", args), "fp64": measure_mg("fp64", args),
+            "learned_fp32_bf16": measure_mg("fp32", args, route="learned", train_steps=300),
+            "learned_note": "the V-cycle, then the trained network's correction (BF16 activations, "
+                            "FP32 accumulation), one smoothing sweep and the minimal-residual judge"}
+        line["batch"] = measure_batch(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(case)
     if rank == 0:

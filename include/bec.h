@@ -57,9 +57,12 @@ enum {
                           the grid of spacing 2h (BF16 activations, FP32
                           accumulation), trained on the GPU by
                           bec_learned_train on pairs the multigrid generates;
-                          per frequency, the correction is kept only if it
-                          lowers ||b - B x|| (the V-cycle is the fallback and
-                          the judge).  Needs BEC_PC_FP32 and nx >= 31. */
+                          per frequency the corrected iterate gets one
+                          damped-Jacobi sweep and the judge then takes the
+                          complex step from the V-cycle's iterate towards it
+                          that minimises ||b - B x||, so the residual never
+                          grows (the V-cycle is the fallback).  Needs
+                          BEC_PC_FP32 and nx >= 31. */
   BEC_ROUTE_MG = 1     /* one geometric multigrid V-cycle per shifted system,
                           any positive a (Sec. 4; Example 2 of Sec. 5): bilinear
                           prolongation, full-weighting restriction, Galerkin
@@ -240,8 +243,15 @@ bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx,
                                  double* loss, float* grad);
 
 /* Frequencies at which the last bec_apply_Pinv kept the V-cycle result
- * because the correction did not lower the residual (-1: not learned). */
+ * because the judged step was 0 (B d = 0 or not finite; -1: not learned).
+ * Synchronises. */
 long long bec_learned_fallbacks(bec_problem* p);
+
+/* ||b_k - B_k x_k|| after the judged correction divided by the V-cycle's
+ * ||b_k - B_k x_k||, for every frequency k = 0..N/2 of the last
+ * bec_apply_Pinv (host array of N/2+1 doubles; a value of 1 means the
+ * correction gained nothing there).  Synchronises. */
+bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
 
 /* ---- Batches of independent problems of uneven size ---------------------
  * Not a construct of the paper: many independent instances (different grid,

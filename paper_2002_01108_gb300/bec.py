@@ -28,7 +28,7 @@ EXPORTED = (
     "bec_batch_create", "bec_batch_problem", "bec_batch_solve", "bec_batch_unknowns",
     "bec_batch_kernel_launches", "bec_batch_free", "bec_learned_num_weights",
     "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
-    "bec_learned_loss_grad", "bec_learned_fallbacks",
+    "bec_learned_loss_grad", "bec_learned_fallbacks", "bec_learned_residual_ratios",
 )
 
 
@@ -113,6 +113,7 @@ def _lib():
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)],
                                   ctypes.c_int),
         "bec_learned_fallbacks": ([P], ctypes.c_longlong),
+        "bec_learned_residual_ratios": ([P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bec_relres_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, D, D, D, P], ctypes.c_int),
         "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
@@ -337,6 +338,14 @@ class Problem:
     @property
     def learned_fallbacks(self) -> int:
         return int(_lib().bec_learned_fallbacks(self._p))
+
+    def learned_residual_ratios(self):
+        """Per frequency k <= N/2 of the last apply: the residual after the judged
+        correction over the V-cycle's residual."""
+        out = np.empty(self.N // 2 + 1)
+        _check(_lib().bec_learned_residual_ratios(self._p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "bec_learned_residual_ratios")
+        return out
 
     def true_relres(self, f, u) -> float:
         out = ctypes.c_double()

@@ -149,6 +149,10 @@ bec_status bec_batch_solve(bec_batch* b, const double* const* f, double* const* 
   for (int i = 0; i < n; ++i) {
     if (infos) bec::gmres_run_info(runs[i], &infos[i]);
     all_conv = all_conv && runs[i].converged;
+    if (b->probs[i]->net) {
+      const bec_status st = bec::net_check(b->probs[i]);
+      if (st != BEC_OK && first_error == BEC_OK) first_error = st;
+    }
   }
   if (first_error != BEC_OK) return first_error;
   return all_conv ? BEC_OK : BEC_ENOTCONV;

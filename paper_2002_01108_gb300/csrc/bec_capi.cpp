@@ -106,7 +106,7 @@ void free_all(bec_problem* p) {
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
                   p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
-                  p->sn, p->g, p->ycoef, p->sigma, p->scal, p->io_f, p->io_u};
+                  p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->host_scal) cudaFreeHost(p->host_scal);
@@ -272,6 +272,7 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&p->g, (size_t)R + 1));
   chain(dmalloc(&p->ycoef, (size_t)R));
   chain(dmalloc(&p->sigma, (size_t)R + 1));
+  chain(dmalloc(&p->flag, (size_t)1));
   chain(dmalloc(&p->scal, (size_t)kScalSlots));
   if (d->host_io) {
     chain(dmalloc(&p->io_f, (size_t)U));
@@ -542,6 +543,12 @@ bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx, cons
 long long bec_learned_fallbacks(bec_problem* p) {
   if (p == nullptr || p->net == nullptr) return -1;
   return net_fallbacks(p);
+}
+
+bec_status bec_learned_residual_ratios(bec_problem* p, double* host) {
+  BEC_TRY(need_net(p));
+  if (host == nullptr) return einval("null host pointer");
+  return net_residual_ratios(p, host);
 }
 
 const char* bec_status_string(bec_status s) {

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(rows_warps<T>() * 32)
 dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
   constexpr int n = 1 << LOGN;
-  constexpr int LSC = n + 1;                 // complex slots per line (odd: fewer conflicts)
+  constexpr int LSC = line_slots(LOGN);      // complex slots per line
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(cols_warps<T>() * 32)
 dst_cols_kernel(T* data, int m, long long J, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
   constexpr int n = 1 << LOGN;
-  constexpr int LSC = n + 1;
+  constexpr int LSC = line_slots(LOGN);
   constexpr int WARPS = cols_warps<T>();
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
@@ -89,7 +89,7 @@ bec_status rows_launch(bec_problem* p, const void* in, void* out, long long rows
                        const T* sin2, const v2_t<T>* tw) {
   constexpr int n = 1 << LOGN;
   const int warps = rows_warps<T>();
-  const size_t smem = (size_t)warps * 2 * (n + 1) * sizeof(T);
+  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
   auto k = dst_rows_kernel<T, TI, TO, LOGN>;
   BEC_CUDA_TRY(prepare(k, smem));
   const long long pairs = (rows + 1) / 2;
@@ -105,7 +105,7 @@ template <typename T, int LOGN>
 bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>* tw) {
   constexpr int n = 1 << LOGN;
   constexpr int warps = cols_warps<T>();
-  const size_t smem = (size_t)warps * 2 * (n + 1) * sizeof(T);
+  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
   auto k = dst_cols_kernel<T, LOGN>;
   BEC_CUDA_TRY(prepare(k, smem));
   dim3 grid((unsigned)((p->m + 2 * warps - 1) / (2 * warps)), (unsigned)p->N);

@@ -26,25 +26,66 @@ __device__ __forceinline__ V cmulc(V a, V b) {
   return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+// Complex slots a warp's line of n = 2^LOGN values occupies in shared memory:
+// n plus one pad slot per 16 (the padded layout of the intermediate passes),
+// made odd so that a block's lines also start on different banks.
+__host__ __device__ constexpr int line_slots(int logn) {
+  return ((1 << logn) + ((1 << logn) >> 4) + 1) | 1;
+}
+
+// position of element i in the padded layout: one slot skipped every 16
+template <bool PAD>
+__device__ __forceinline__ int pidx(int i) {
+  return PAD ? i + (i >> 4) : i;
+}
+
+template <typename V>
+__device__ __forceinline__ V cadd(V a, V b) { return {a.x + b.x, a.y + b.y}; }
+template <typename V>
+__device__ __forceinline__ V csub(V a, V b) { return {a.x - b.x, a.y - b.y}; }
+// SIGN * i * a
+template <int SIGN, typename V>
+__device__ __forceinline__ V cmul_si(V a) { return SIGN < 0 ? V{a.y, -a.x} : V{-a.y, a.x}; }
+
 // In-register DFT of length R with kernel e^{SIGN 2 pi i r k / R}.
 template <int R, int SIGN, typename V>
 __device__ __forceinline__ void radix_dft(V (&v)[R]) {
   if constexpr (R == 2) {
     V a = v[0], b = v[1];
-    v[0] = {a.x + b.x, a.y + b.y};
-    v[1] = {a.x - b.x, a.y - b.y};
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const V a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    const V c = cadd(v[1], v[3]);
+    const V wd = cmul_si<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, wd);
+    v[3] = csub(b, wd);
   } else {
-    static_assert(R == 4, "radix 2 or 4");
-    V a = {v[0].x + v[2].x, v[0].y + v[2].y};
-    V b = {v[0].x - v[2].x, v[0].y - v[2].y};
-    V c = {v[1].x + v[3].x, v[1].y + v[3].y};
-    V d = {v[1].x - v[3].x, v[1].y - v[3].y};
-    // w d with w = SIGN * i
-    V wd = SIGN < 0 ? V{d.y, -d.x} : V{-d.y, d.x};
-    v[0] = {a.x + c.x, a.y + c.y};
-    v[2] = {a.x - c.x, a.y - c.y};
-    v[1] = {b.x + wd.x, b.y + wd.y};
-    v[3] = {b.x - wd.x, b.y - wd.y};
+    static_assert(R == 8, "radix 2, 4 or 8");
+    // X_k = E_k + w^k O_k, X_{k+4} = E_k - w^k O_k with E, O the 4-point DFTs
+    // of the even and odd samples and w = e^{SIGN 2 pi i / 8}
+    using T = decltype(v[0].x);
+    V e[4] = {v[0], v[2], v[4], v[6]};
+    V o[4] = {v[1], v[3], v[5], v[7]};
+    radix_dft<4, SIGN>(e);
+    radix_dft<4, SIGN>(o);
+    const T h = T(0.70710678118654752440);
+    // w o1 = h (1 + SIGN i) o1, w^2 o2 = SIGN i o2, w^3 o3 = h (-1 + SIGN i) o3
+    const V s1 = cmul_si<SIGN>(o[1]);
+    const V t1 = {h * (o[1].x + s1.x), h * (o[1].y + s1.y)};
+    const V t2 = cmul_si<SIGN>(o[2]);
+    const V s3 = cmul_si<SIGN>(o[3]);
+    const V t3 = {h * (s3.x - o[3].x), h * (s3.y - o[3].y)};
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
   }
 }
 
@@ -52,8 +93,11 @@ __device__ __forceinline__ void radix_dft(V (&v)[R]) {
 // line of n = 2^LOGN complex values.  Butterfly j reads x[j + r n/R], applies
 // the twiddles e^{SIGN 2 pi i (j mod Ns) r / (Ns R)}, does the radix-R DFT and
 // writes x[(j div Ns) Ns R + (j mod Ns) + r Ns].  All reads finish before any
-// write, so the pass works in place.  tw[t] = e^{-2 pi i t / n}.
-template <typename T, int SIGN, int LOGN, int LOGNS, int LOGR>
+// write, so the pass works in place; PIN / POUT select the padded layout for
+// the reads / writes.  tw[t] = e^{-2 pi i t / n}.  In FP32 one twiddle is read
+// per butterfly and its powers are formed by multiplication; in FP64, whose
+// arithmetic is the scarce resource, every power is read from the table.
+template <typename T, int SIGN, int LOGN, int LOGNS, int LOGR, bool PIN, bool POUT>
 __device__ __forceinline__ void fft_pass(v2_t<T>* buf, const v2_t<T>* __restrict__ tw,
                                          int lane) {
   using V = v2_t<T>;
@@ -67,7 +111,7 @@ __device__ __forceinline__ void fft_pass(v2_t<T>* buf, const v2_t<T>* __restrict
     const int j = lane + 32 * t;
     if (NB % 32 == 0 || j < NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[t][r] = buf[j + r * NB];
+      for (int r = 0; r < R; ++r) v[t][r] = buf[pidx<PIN>(j + r * NB)];
     }
   }
   __syncwarp();
@@ -77,42 +121,56 @@ __device__ __forceinline__ void fft_pass(v2_t<T>* buf, const v2_t<T>* __restrict
     if (NB % 32 == 0 || j < NB) {
       const int k = j & (Ns - 1);
       if constexpr (Ns > 1) {
+        if constexpr (sizeof(T) == 4) {
+          V w = tw[k * TWSTEP];
+          if (SIGN > 0) w.y = -w.y;
+          V wr = w;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const V w = tw[k * r * TWSTEP];
-          v[t][r] = SIGN < 0 ? cmul(v[t][r], w) : cmulc(v[t][r], w);
+          for (int r = 1; r < R; ++r) {
+            v[t][r] = cmul(v[t][r], wr);
+            if (r + 1 < R) wr = cmul(wr, w);
+          }
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            const V w = tw[k * r * TWSTEP];
+            v[t][r] = SIGN < 0 ? cmul(v[t][r], w) : cmulc(v[t][r], w);
+          }
         }
       }
       radix_dft<R, SIGN>(v[t]);
       const int base = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[t][r];
+      for (int r = 0; r < R; ++r) buf[pidx<POUT>(base + r * Ns)] = v[t][r];
     }
   }
   __syncwarp();
 }
 
+// radix of the pass that starts at span 2^LOGNS: 8 while at least 3 bits
+// remain (but not 8 then 2: 4 + 4 instead), else what remains
+__host__ __device__ constexpr int pass_logr(int logn, int logns) {
+  return (logn - logns >= 3 && logn - logns != 4) ? 3 : (logn - logns >= 2 ? 2 : 1);
+}
+
 template <typename T, int SIGN, int LOGN, int LOGNS>
-__device__ __forceinline__ void fft_radix4_passes(v2_t<T>* buf, const v2_t<T>* __restrict__ tw,
-                                                  int lane) {
-  if constexpr (LOGNS + 2 <= LOGN) {
-    fft_pass<T, SIGN, LOGN, LOGNS, 2>(buf, tw, lane);
-    fft_radix4_passes<T, SIGN, LOGN, LOGNS + 2>(buf, tw, lane);
+__device__ __forceinline__ void fft_passes(v2_t<T>* buf, const v2_t<T>* __restrict__ tw,
+                                           int lane) {
+  if constexpr (LOGNS < LOGN) {
+    constexpr int LOGR = pass_logr(LOGN, LOGNS);
+    constexpr bool first = LOGNS == 0, last = LOGNS + LOGR == LOGN;
+    fft_pass<T, SIGN, LOGN, LOGNS, LOGR, !first, !last>(buf, tw, lane);
+    fft_passes<T, SIGN, LOGN, LOGNS + LOGR>(buf, tw, lane);
   }
 }
 
 // Complex FFT of length 2^LOGN in place in shared memory, natural order in
-// and out, by one warp.  SIGN = -1: X_k = sum_j x_j e^{-2 pi i jk/n};
-// SIGN = +1: the unnormalised inverse.  A radix-2 pass (with trivial
-// twiddles) comes first when LOGN is odd, radix-4 passes follow.
+// and out, by one warp; the buffer holds line_slots(LOGN) complex values.
+// SIGN = -1: X_k = sum_j x_j e^{-2 pi i jk/n}; SIGN = +1: the unnormalised
+// inverse.  Radix-8 passes, then radix 4 or 2 for the remaining bits.
 template <typename T, int SIGN, int LOGN>
 __device__ __forceinline__ void warp_fft(v2_t<T>* buf, const v2_t<T>* __restrict__ tw, int lane) {
-  if constexpr (LOGN & 1) {
-    fft_pass<T, SIGN, LOGN, 0, 1>(buf, tw, lane);
-    fft_radix4_passes<T, SIGN, LOGN, 1>(buf, tw, lane);
-  } else {
-    fft_radix4_passes<T, SIGN, LOGN, 0>(buf, tw, lane);
-  }
+  fft_passes<T, SIGN, LOGN, 0>(buf, tw, lane);
 }
 
 // DST-I of two real lines at once, by one warp.  With n = 2^LOGN, each line
@@ -122,7 +180,8 @@ __device__ __forceinline__ void warp_fft(v2_t<T>* buf, const v2_t<T>* __restrict
 // Method: y_j = 2 sin(j pi / n)(x_j + x_{n-j}) + (x_j - x_{n-j}) makes the odd
 // outputs the running sums of the real parts and the even outputs the
 // imaginary parts of one length-n real DFT; both lines share one complex FFT
-// (y^a + i y^b).  `raw` must hold 2n reals (it doubles as the complex line).
+// (y^a + i y^b).  `raw` must hold 2 line_slots(LOGN) reals (it doubles as the
+// complex line).
 // sin2[j] = 2 sin(j pi / n), tw[t] = e^{-2 pi i t / n}.
 template <typename T, int LOGN>
 __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restrict__ sin2,

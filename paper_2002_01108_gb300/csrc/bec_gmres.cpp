@@ -17,7 +17,7 @@
 namespace bec {
 
 namespace {
-constexpr int S_REF = 0, S_BETA = 1, S_W = 2, S_RES = 3, S_TRUE = 4, S_ONE = 15;
+constexpr int S_REF = 0, S_BETA = 1, S_W = 2, S_RES = 3, S_TRUE = 4, S_WB = 6, S_ONE = 15;
 
 #define BEC_TRY(expr)            \
   do {                           \
@@ -88,20 +88,31 @@ bec_status iteration_body(GmresRun& r) {
   double* sigma = p->sigma;
   double* h1 = p->hcol;
   double* h2 = p->hcol + (p->max_restart + 2);
+  double* vnext = p->V + (long long)(j + 1) * p->U;
   if (r.o.left_pc) {
     BEC_TRY(launch_apply_L(p, r.Vp[j], p->t, 0.0, sigma + j));
     BEC_TRY(apply_pinv(p, p->t, p->w, nullptr));
     BEC_TRY(launch_dots(p, p->w, r.Vp.data(), j + 1, sigma, h1));
-  } else {
-    double* z = r.o.flexible ? p->Z + (long long)j * p->U : p->t;
-    BEC_TRY(apply_pinv(p, r.Vp[j], z, sigma + j));
-    BEC_TRY(launch_stencil_dots(p, z, p->w, r.Vp.data(), j + 1, sigma, h1));
+    // classical Gram-Schmidt, second pass fused with the first update
+    BEC_TRY(launch_update_dots(p, p->w, r.Vp.data(), j + 1, sigma, h1, h2));
+    BEC_TRY(launch_combine(p, vnext, p->w, r.Vp.data(), j + 1, sigma, h2, -1.0, S_W));
+    BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES));
+    return enqueue_scalar_read(p);
   }
-  // classical Gram-Schmidt, second pass fused with the first update
-  BEC_TRY(launch_update_dots(p, p->w, r.Vp.data(), j + 1, sigma, h1, h2));
-  double* vnext = p->V + (long long)(j + 1) * p->U;
-  BEC_TRY(launch_combine(p, vnext, p->w, r.Vp.data(), j + 1, sigma, h2, -1.0, S_W));
-  BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES));
+  // Right preconditioning: Arnoldi on A - I with A = L P^{-1} (same Krylov
+  // space, H(A) = H(A - I) + I).  w = L z_j - v_j no longer carries the
+  // dominant v_j component of a near-identity A, so one classical
+  // Gram-Schmidt pass is kept unless the test of Daniel, Gragg, Kaufman and
+  // Stewart (||w after|| < ||w before|| / sqrt 2) asks for a second one; that
+  // decision is taken on the device.
+  double* z = r.o.flexible ? p->Z + (long long)j * p->U : p->t;
+  BEC_TRY(apply_pinv(p, r.Vp[j], z, sigma + j));
+  BEC_TRY(launch_stencil_dots(p, z, p->w, r.Vp.data(), j + 1, sigma, h1, r.Vp[j], sigma + j, S_WB));
+  BEC_TRY(launch_combine(p, vnext, p->w, r.Vp.data(), j + 1, sigma, h1, -1.0, S_W));
+  BEC_TRY(launch_reorth_flag(p, S_WB, S_W));
+  BEC_TRY(launch_dots(p, vnext, r.Vp.data(), j + 1, sigma, h2, p->flag));
+  BEC_TRY(launch_combine(p, vnext, vnext, r.Vp.data(), j + 1, sigma, h2, -1.0, S_W, p->flag));
+  BEC_TRY(launch_hessenberg(p, j, h1, h2, S_W, S_RES, 1.0));
   return enqueue_scalar_read(p);
 }
 
@@ -321,6 +332,7 @@ bec_status gmres_solve_one(bec_problem* p, const double* f, double* u, const bec
     if (enq) BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
   }
   gmres_run_info(r, info);
+  if (p->net) BEC_TRY(net_check(p));
   return gmres_run_result(r);
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libbec.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -101,6 +102,7 @@ struct bec_problem {
   double* g = nullptr;          // rotated right-hand side (max_restart + 1)
   double* ycoef = nullptr;      // least-squares solution (max_restart)
   double* sigma = nullptr;      // 1 / ||stored V_i||: V_i is kept unnormalised (max_restart + 1)
+  int* flag = nullptr;          // device flag: second Gram-Schmidt pass needed
   double* scal = nullptr;       // device scalars (norms, residual estimate)
   double* host_scal = nullptr;  // pinned mirror of scal
   double* io_f = nullptr;       // host_io staging
@@ -197,6 +199,8 @@ void mg_free(bec_problem* p);
 bec_status mg_vcycle(bec_problem* p);
 // r = b - B x on the finest level for every frequency ([K][J] complex arrays)
 bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void* b);
+// xo = x + omega D^{-1} (b - B x) on the finest grid, every frequency (xo != x)
+bec_status mg_smooth_level0(bec_problem* p, void* xo, const void* x, const void* b);
 // spec[k][q] = sum_j e^{-2 pi i jk/N} eps^{j/N} (s y)[j][q], k <= N/2 (s = *scale_dev or 1)
 bec_status launch_time_fwd(bec_problem* p, const double* y, void* spec, int fp64,
                            const double* scale_dev);
@@ -215,6 +219,20 @@ bec_status net_set_weights(bec_problem* p, const float* host);
 bec_status net_loss_grad(bec_problem* p, int B, const int* lams, const double* r, const double* et,
                          double* loss_out, float* grad_host);
 long long net_fallbacks(bec_problem* p);
+// BEC_ETIMEOUT (and clears the flag) when a bounded device wait of the
+// network's kernels ran out since the last check; synchronises.
+bec_status net_check(bec_problem* p);
+
+// ---- tensor-core convolution (bec_conv_tc.cu): 3 x 3, 32 -> 32 channels,
+// BF16 NHWC activations, tcgen05 MMA with TMA-staged operands
+bool tc_conv_supported();
+// wt[l][tap][co][ci] (BF16) from the FP32 weights [l][tap][ci][co] of nlayers layers
+bec_status tc_convert_weights(bec_problem* p, const float* W_first, int nlayers,
+                              __nv_bfloat16* wt);
+bec_status tc_conv3x3(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat16* wt,
+                      int nlayers, int layer, __nv_bfloat16* out, int m, int B, int bmax,
+                      bool relu, int* err);
+bec_status net_residual_ratios(bec_problem* p, double* host);
 
 // ---- stencils (bec_stencil.cu)
 // number of blocks (partial sums) the residual-norm kernel writes
@@ -223,10 +241,14 @@ long long stencil_blocks(const bec_problem* p);
 // with out_scale != null the result is multiplied by the device scalar.
 bec_status launch_apply_L(bec_problem* p, const double* v, double* y,
                           double corner, const double* out_scale = nullptr);
-// w = L z and hout[i] = sigma_i <V_i, w> for i < nv in one pass over z, w, V.
+// w = L z - s vshift (s = *sshift; no shift if vshift is null) and
+// hout[i] = sigma_i <V_i, w> for i < nv in one pass over z, w, V; with
+// norm_slot >= 0 also scal[norm_slot] = ||w||.
 bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
                                const double* const* V, int nv,
-                               const double* sigma, double* hout);
+                               const double* sigma, double* hout,
+                               const double* vshift = nullptr,
+                               const double* sshift = nullptr, int norm_slot = -1);
 bec_status launch_build_rhs(bec_problem* p, const double* u0,
                             const double* fsrc, double* f);
 // partials[b] = sum over block b of (f - L u)^2, partials[B + b] = sum f^2;
@@ -239,9 +261,17 @@ bec_status launch_residual(bec_problem* p, const double* f, const double* u,
 
 // ---- Krylov BLAS (bec_krylov.cu).  V is a host array of nv device
 // pointers; sigma (device, may be null = all ones) scales V_i.
-// hout[i] = sigma_i <V_i, w>
+// hout[i] = sigma_i <V_i, w>; with flag != null and *flag == 0 on the
+// device, nothing is computed and hout = 0 (a skipped reorthogonalisation).
 bec_status launch_dots(bec_problem* p, const double* w, const double* const* V,
-                       int nv, const double* sigma, double* hout);
+                       int nv, const double* sigma, double* hout,
+                       const int* flag = nullptr);
+// scal[slot] = sqrt(sum of nb partials) (skipped when flag && !*flag)
+bec_status launch_finish_sqrt(bec_problem* p, const double* parts, int nb, int slot,
+                              const int* flag);
+// *flag = (scal[after] < scal[before] / sqrt(2)): the second Gram-Schmidt pass
+// is needed (the test of Daniel, Gragg, Kaufman and Stewart)
+bec_status launch_reorth_flag(bec_problem* p, int before_slot, int after_slot);
 // w -= sum_i coef_i sigma_i V_i, then hout[i] = sigma_i <V_i, w>
 bec_status launch_update_dots(bec_problem* p, double* w,
                               const double* const* V, int nv,
@@ -251,10 +281,12 @@ bec_status launch_update_dots(bec_problem* p, double* w,
 // if norm_slot >= 0 also scal[norm_slot] = ||out||.
 bec_status launch_combine(bec_problem* p, double* out, const double* w,
                           const double* const* V, int nv, const double* sigma,
-                          const double* coef, double sign, int norm_slot);
+                          const double* coef, double sign, int norm_slot,
+                          const int* flag = nullptr);
 // dots of a finished partial array: hout[i] = sigma_i sum_b partials[i nb + b]
 bec_status launch_finish_dots(bec_problem* p, int nv, int nb,
-                              const double* sigma, double* hout);
+                              const double* sigma, double* hout,
+                              const int* flag = nullptr);
 // scal[slot] = ||x||
 bec_status launch_norm(bec_problem* p, const double* x, int slot);
 // Hessenberg column j: H(0:j, j) = h1 + h2 (the two Gram-Schmidt passes),
@@ -262,7 +294,8 @@ bec_status launch_norm(bec_problem* p, const double* x, int slot);
 // previous rotations, makes rotation j, updates g and writes |g[j+1]| to
 // scal[res_slot].
 bec_status launch_hessenberg(bec_problem* p, int j, const double* h1,
-                             const double* h2, int norm_slot, int res_slot);
+                             const double* h2, int norm_slot, int res_slot,
+                             double shift = 0.0);
 // g = (scal[slot], 0, ...), sigma[0] = 1 / scal[slot].
 bec_status launch_gmres_start(bec_problem* p, int slot);
 // ycoef = H(0:k,0:k)^{-1} g(0:k)

@@ -61,7 +61,9 @@ __device__ __forceinline__ void block_store_sum(double v, double* __restrict__ p
 // vector is 16-byte aligned, so double2 loads are used.
 template <int NV>
 __global__ void __launch_bounds__(kThreads)
-dots_kernel(const double* __restrict__ w, VecList V, long long U, double* __restrict__ partials) {
+dots_kernel(const double* __restrict__ w, VecList V, long long U, double* __restrict__ partials,
+            const int* __restrict__ flag) {
+  if (flag && *flag == 0) return;
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
@@ -114,7 +116,8 @@ update_dots_kernel(double* __restrict__ w, VecList V, long long U, const double*
 __global__ void __launch_bounds__(kThreads)
 combine_kernel(double* out, const double* w, VecList V, int nv, long long U,
                const double* __restrict__ coef, const double* __restrict__ sigma, double sign,
-               double* __restrict__ partials) {
+               double* __restrict__ partials, const int* __restrict__ flag) {
+  if (flag && *flag == 0) return;
   __shared__ double c[kMaxVec];
   for (int v = threadIdx.x; v < nv; v += kThreads) c[v] = sign * coef[v] * (sigma ? sigma[v] : 1.0);
   __syncthreads();
@@ -152,7 +155,11 @@ sumsq_kernel(const double* __restrict__ x, long long U, double* __restrict__ par
 // hout[v] = sigma_v * sum_b partials[v * nb + b]   (block v, fixed tree order)
 __global__ void __launch_bounds__(kThreads)
 finish_dots_kernel(const double* __restrict__ partials, int nb, const double* __restrict__ sigma,
-                   double* __restrict__ hout) {
+                   double* __restrict__ hout, const int* __restrict__ flag) {
+  if (flag && *flag == 0) {
+    if (threadIdx.x == 0) hout[blockIdx.x] = 0.0;
+    return;
+  }
   __shared__ double s[kThreads];
   double a = 0.0;
   for (int b = threadIdx.x; b < nb; b += kThreads) a += partials[(long long)blockIdx.x * nb + b];
@@ -168,7 +175,8 @@ finish_dots_kernel(const double* __restrict__ partials, int nb, const double* __
 // scal[slot] = sqrt(sum partials)
 __global__ void __launch_bounds__(kThreads)
 finish_sqrt_kernel(const double* __restrict__ partials, int nb, double* __restrict__ scal,
-                   int slot) {
+                   int slot, const int* __restrict__ flag) {
+  if (flag && *flag == 0) return;
   __shared__ double s[kThreads];
   double a = 0.0;
   for (int b = threadIdx.x; b < nb; b += kThreads) a += partials[b];
@@ -188,10 +196,12 @@ __global__ void hessenberg_kernel(double* __restrict__ H, int ldh, int j,
                                   const double* __restrict__ h1, const double* __restrict__ h2,
                                   double* __restrict__ scal, int norm_slot, int res_slot,
                                   double* __restrict__ cs, double* __restrict__ sn,
-                                  double* __restrict__ g, double* __restrict__ sigma) {
+                                  double* __restrict__ g, double* __restrict__ sigma,
+                                  double shift) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + (long long)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  col[j] += shift;   // Arnoldi on (A - shift I): H(A) = H(A - shift I) + shift I
   const double hn = scal[norm_slot];
   col[j + 1] = hn;
   sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
@@ -215,6 +225,11 @@ __global__ void hessenberg_kernel(double* __restrict__ H, int ldh, int j,
   g[j] = c * gj;
   g[j + 1] = -s * gj;
   scal[res_slot] = fabs(g[j + 1]);
+}
+
+__global__ void reorth_flag_kernel(const double* __restrict__ scal, int before, int after,
+                                   int* __restrict__ flag) {
+  if (threadIdx.x == 0) flag[0] = scal[after] * scal[after] < 0.5 * scal[before] * scal[before];
 }
 
 __global__ void gmres_start_kernel(double* __restrict__ g, int len, const double* __restrict__ scal,
@@ -245,11 +260,11 @@ VecList pack(const double* const* V, int n) {
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)   \
   X(31) X(32)
 
-bec_status launch_dots_chunk(bec_problem* p, const double* w, VecList L, int n) {
+bec_status launch_dots_chunk(bec_problem* p, const double* w, VecList L, int n, const int* flag) {
   BEC_LAUNCH_BEGIN(p);
   switch (n) {
 #define BEC_DOTS_CASE(NV) \
-  case NV: dots_kernel<NV><<<kReduceBlocks, kThreads, 0, p->stream>>>(w, L, p->U, p->partials); break;
+  case NV: dots_kernel<NV><<<kReduceBlocks, kThreads, 0, p->stream>>>(w, L, p->U, p->partials, flag); break;
     BEC_NV_CASES(BEC_DOTS_CASE)
 #undef BEC_DOTS_CASE
     default: return BEC_EINVAL;
@@ -260,20 +275,36 @@ bec_status launch_dots_chunk(bec_problem* p, const double* w, VecList L, int n) 
 
 }  // namespace
 
-bec_status launch_finish_dots(bec_problem* p, int nv, int nb, const double* sigma, double* hout) {
+bec_status launch_finish_dots(bec_problem* p, int nv, int nb, const double* sigma, double* hout,
+                              const int* flag) {
   BEC_LAUNCH_BEGIN(p);
-  finish_dots_kernel<<<nv, kThreads, 0, p->stream>>>(p->partials, nb, sigma, hout);
+  finish_dots_kernel<<<nv, kThreads, 0, p->stream>>>(p->partials, nb, sigma, hout, flag);
   BEC_LAUNCH_CHECK(p, "finish_dots_kernel");
   return BEC_OK;
 }
 
+bec_status launch_finish_sqrt(bec_problem* p, const double* parts, int nb, int slot,
+                              const int* flag) {
+  BEC_LAUNCH_BEGIN(p);
+  finish_sqrt_kernel<<<1, kThreads, 0, p->stream>>>(parts, nb, p->scal, slot, flag);
+  BEC_LAUNCH_CHECK(p, "finish_sqrt_kernel");
+  return BEC_OK;
+}
+
+bec_status launch_reorth_flag(bec_problem* p, int before_slot, int after_slot) {
+  BEC_LAUNCH_BEGIN(p);
+  reorth_flag_kernel<<<1, 32, 0, p->stream>>>(p->scal, before_slot, after_slot, p->flag);
+  BEC_LAUNCH_CHECK(p, "reorth_flag_kernel");
+  return BEC_OK;
+}
+
 bec_status launch_dots(bec_problem* p, const double* w, const double* const* V, int nv,
-                       const double* sigma, double* hout) {
+                       const double* sigma, double* hout, const int* flag) {
   for (int v0 = 0; v0 < nv; v0 += kMaxVec) {
     const int n = nv - v0 < kMaxVec ? nv - v0 : kMaxVec;
-    bec_status s = launch_dots_chunk(p, w, pack(V + v0, n), n);
+    bec_status s = launch_dots_chunk(p, w, pack(V + v0, n), n, flag);
     if (s != BEC_OK) return s;
-    s = launch_finish_dots(p, n, kReduceBlocks, sigma ? sigma + v0 : nullptr, hout + v0);
+    s = launch_finish_dots(p, n, kReduceBlocks, sigma ? sigma + v0 : nullptr, hout + v0, flag);
     if (s != BEC_OK) return s;
   }
   return BEC_OK;
@@ -304,7 +335,7 @@ bec_status launch_update_dots(bec_problem* p, double* w, const double* const* V,
 
 bec_status launch_combine(bec_problem* p, double* out, const double* w, const double* const* V,
                           int nv, const double* sigma, const double* coef, double sign,
-                          int norm_slot) {
+                          int norm_slot, const int* flag) {
   // chunks of kMaxVec vectors; the norm comes from the last chunk
   int v0 = 0;
   do {
@@ -315,16 +346,11 @@ bec_status launch_combine(bec_problem* p, double* out, const double* w, const do
     BEC_LAUNCH_BEGIN(p);
     combine_kernel<<<kReduceBlocks, kThreads, 0, p->stream>>>(
         out, src, pack(V + v0, n > 0 ? n : 1), n, p->U, coef + v0, sigma ? sigma + v0 : nullptr,
-        sign, part);
+        sign, part, flag);
     BEC_LAUNCH_CHECK(p, "combine_kernel");
     v0 += kMaxVec;
   } while (v0 < nv);
-  if (norm_slot >= 0) {
-    BEC_LAUNCH_BEGIN(p);
-    finish_sqrt_kernel<<<1, kThreads, 0, p->stream>>>(p->partials, kReduceBlocks, p->scal,
-                                                       norm_slot);
-    BEC_LAUNCH_CHECK(p, "finish_sqrt_kernel");
-  }
+  if (norm_slot >= 0) return launch_finish_sqrt(p, p->partials, kReduceBlocks, norm_slot, flag);
   return BEC_OK;
 }
 
@@ -332,17 +358,15 @@ bec_status launch_norm(bec_problem* p, const double* x, int slot) {
   BEC_LAUNCH_BEGIN(p);
   sumsq_kernel<<<kReduceBlocks, kThreads, 0, p->stream>>>(x, p->U, p->partials);
   BEC_LAUNCH_CHECK(p, "sumsq_kernel");
-  BEC_LAUNCH_BEGIN(p);
-  finish_sqrt_kernel<<<1, kThreads, 0, p->stream>>>(p->partials, kReduceBlocks, p->scal, slot);
-  BEC_LAUNCH_CHECK(p, "finish_sqrt_kernel");
-  return BEC_OK;
+  return launch_finish_sqrt(p, p->partials, kReduceBlocks, slot, nullptr);
 }
 
 bec_status launch_hessenberg(bec_problem* p, int j, const double* h1, const double* h2,
-                             int norm_slot, int res_slot) {
+                             int norm_slot, int res_slot, double shift) {
   BEC_LAUNCH_BEGIN(p);
   hessenberg_kernel<<<1, 32, 0, p->stream>>>(p->H, p->max_restart + 1, j, h1, h2, p->scal,
-                                             norm_slot, res_slot, p->cs, p->sn, p->g, p->sigma);
+                                             norm_slot, res_slot, p->cs, p->sn, p->g, p->sigma,
+                                             shift);
   BEC_LAUNCH_CHECK(p, "hessenberg_kernel");
   return BEC_OK;
 }

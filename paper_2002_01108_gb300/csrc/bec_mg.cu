@@ -467,6 +467,23 @@ bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void
   return BEC_OK;
 }
 
+bec_status mg_smooth_level0(bec_problem* p, void* xo, const void* x, const void* b) {
+  const MgLevel& L = p->mg.lv[0];
+  if (p->desc.precision == BEC_PC_FP64) {
+    BEC_LAUNCH_BEGIN(p);
+    mg_smooth_kernel<double, false><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+        static_cast<double2*>(xo), static_cast<const double2*>(x), static_cast<const double2*>(b),
+        level_args<double>(p, L));
+  } else {
+    BEC_LAUNCH_BEGIN(p);
+    mg_smooth_kernel<float, false><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+        static_cast<float2*>(xo), static_cast<const float2*>(x), static_cast<const float2*>(b),
+        level_args<float>(p, L));
+  }
+  BEC_LAUNCH_CHECK(p, "mg_smooth_kernel[l0]");
+  return BEC_OK;
+}
+
 bec_status mg_vcycle(bec_problem* p) {
   if (p->desc.precision == BEC_PC_FP64) return vcycle_t<double>(p);
   return vcycle_t<float>(p);

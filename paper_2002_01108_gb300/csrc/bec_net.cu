@@ -1,9 +1,11 @@
 // Learned route of P_eps^{-1} (BEC_ROUTE_LEARNED): one multigrid V-cycle per
 // shifted system, then a learned correction of what the V-cycle left,
-//     x_k <- x_k + P_0 (s c_k Net(R_0 (b_k - B_k x_k) / s, log a, lambda'_k)),
-// judged per frequency by the residual ||b_k - B_k x||: a frequency whose
-// residual the network does not reduce keeps the V-cycle result (the
-// multigrid is the fallback and the judge).  The network (see
+//     x1 = x_k + P_0 (s c_k Net(R_0 (b_k - B_k x_k) / s, log a, lambda'_k)),
+// one damped-Jacobi sweep x2 = x1 + omega D^{-1} (b_k - B_k x1) (the
+// post-smoothing that follows a prolonged correction), and the judge: the
+// complex step x_k <- x_k + alpha_k (x2 - x_k) that minimises ||b_k - B_k x||,
+// so the residual never grows (alpha_k = 0 keeps the V-cycle's iterate; the
+// multigrid is the fallback).  The network (see
 // bec_net_kernels.cuh) runs on the grid of spacing 2h with 4 levels and C
 // channels and is trained on the GPU, by these kernels, on pairs
 // (r, e* = B_k^{-1} r) that the multigrid itself generates: r is the residual
@@ -75,8 +77,10 @@ struct NetState {
   double* part = nullptr;        // per-sample / per-frequency partial sums
   double* h_part = nullptr;      // pinned mirror
   int adam_t = 0;
-  long long fallbacks = 0;       // frequencies the judge kept at the V-cycle (last apply)
   unsigned long long rng_ctr = 0;
+  bool tc = false;               // 32 -> 32 layers on the tensor cores (BF16, C = 32)
+  __nv_bfloat16* wt = nullptr;   // BF16 weights of layers 1..7, [l][tap][co][ci]
+  int* err = nullptr;            // set by a device wait that ran out
 };
 
 namespace {
@@ -279,35 +283,57 @@ __global__ void add_corr_kernel(float2* __restrict__ out, const float2* __restri
   out[o] = make_float2(a.x + e.x, a.y + e.y);
 }
 
-// one block per frequency: part[k] = ||r_k||^2
-__global__ void freq_sumsq_kernel(const float2* __restrict__ r, double* __restrict__ part,
-                                  long long mff) {
-  __shared__ double red[256];
+// One block per frequency k: with res = b - B x (the V-cycle's residual) and
+// r2 = b - B x2 (the corrected and smoothed iterate), B d = res - r2 for the
+// step d = x2 - x.  part[4k..4k+3] = Re, Im <B d, res>, ||B d||^2, ||res||^2
+// (<u, v> = u^H v), summed in FP64 in a fixed order.
+__global__ void mr_dots_kernel(const float2* __restrict__ res, const float2* __restrict__ r2,
+                               double* __restrict__ part, long long mff) {
+  __shared__ double red[4][256];
   const int k = blockIdx.x;
-  double s = 0.0;
+  double cr = 0.0, ci = 0.0, dd = 0.0, rr = 0.0;
   for (long long f = threadIdx.x; f < mff; f += blockDim.x) {
-    const float2 v = r[(long long)k * mff + f];
-    s += (double)v.x * v.x + (double)v.y * v.y;
+    const float2 r = res[(long long)k * mff + f];
+    const float2 q = r2[(long long)k * mff + f];
+    const double bx = (double)r.x - q.x, by = (double)r.y - q.y;
+    cr += bx * r.x + by * r.y;
+    ci += bx * r.y - by * r.x;
+    dd += bx * bx + by * by;
+    rr += (double)r.x * r.x + (double)r.y * r.y;
   }
-  red[threadIdx.x] = s;
+  red[0][threadIdx.x] = cr;
+  red[1][threadIdx.x] = ci;
+  red[2][threadIdx.x] = dd;
+  red[3][threadIdx.x] = rr;
   __syncthreads();
   for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
-    if ((int)threadIdx.x < st2) red[threadIdx.x] += red[threadIdx.x + st2];
+    if ((int)threadIdx.x < st2)
+      for (int i = 0; i < 4; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st2];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[k] = red[0];
+  if (threadIdx.x < 4) part[4 * k + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// keep the corrected iterate where it lowered the residual, else the V-cycle's
-__global__ void judge_select_kernel(float2* __restrict__ x, const float2* __restrict__ xnew,
-                                    const double* __restrict__ before, const double* __restrict__ after,
-                                    long long mff, int K, int* __restrict__ fallbacks) {
+// x <- x + alpha_k (x2 - x), alpha_k = <B d, res> / ||B d||^2: the complex step
+// that minimises ||b - B (x + alpha d)|| (0 when B d = 0: the V-cycle's
+// iterate is kept).  ratio[k] = ||b - B x_new|| / ||res||.
+__global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restrict__ x2,
+                                 const double* __restrict__ part, long long mff, int K,
+                                 double* __restrict__ ratio, int* __restrict__ fallbacks) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)K * mff) return;
   const int k = (int)(g / mff);
-  const bool take = after[k] < before[k];
-  if (take) x[g] = xnew[g];
-  if (g - (long long)k * mff == 0 && !take) atomicAdd(fallbacks, 1);
+  const double cr = part[4 * k], ci = part[4 * k + 1], dd = part[4 * k + 2], rr = part[4 * k + 3];
+  const bool ok = dd > 0.0 && isfinite(dd) && isfinite(cr) && isfinite(ci);
+  const float ar = ok ? (float)(cr / dd) : 0.f, ai = ok ? (float)(ci / dd) : 0.f;
+  const float2 a = x[g], c = x2[g];
+  const float dx = c.x - a.x, dy = c.y - a.y;
+  x[g] = make_float2(a.x + ar * dx - ai * dy, a.y + ar * dy + ai * dx);
+  if (g - (long long)k * mff == 0) {
+    const double after = ok ? fmax(rr - (cr * cr + ci * ci) / dd, 0.0) : rr;
+    ratio[k] = rr > 0.0 ? sqrt(after / rr) : 0.0;
+    if (!ok) atomicAdd(fallbacks, 1);
+  }
 }
 
 // ------------------------------------------------------------ dispatch helpers
@@ -320,6 +346,11 @@ bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m,
   const int ci = n.cin[layer], co = n.cout[layer];
   const AT* a = static_cast<const AT*>(in);
   AT* o = static_cast<AT*>(out);
+  if constexpr (sizeof(AT) == 2) {
+    if (n.tc && ci == 32 && co == 32 && m >= 16)
+      return tc_conv3x3(p, reinterpret_cast<const __nv_bfloat16*>(a), n.wt, 7, layer - 1,
+                        reinterpret_cast<__nv_bfloat16*>(o), m, B, n.Bmax, relu, n.err);
+  }
   BEC_LAUNCH_BEGIN(p);
 #define BEC_CF(CI, CO)                                                                            \
   if (ci == CI && co == CO) {                                                                     \
@@ -460,6 +491,7 @@ template <typename AT>
 bec_status forward(bec_problem* p, int B) {
   NetState& n = *p->net;
   void** a = n.act;
+  if (sizeof(AT) == 2 && n.tc) BEC_TRY(tc_convert_weights(p, n.W + n.woff[1], 7, n.wt));
   BEC_TRY(conv_fwd<AT>(p, a[A_X], 0, a[A_H0], n.sz[0], B, true));
   BEC_TRY(conv_fwd<AT>(p, a[A_H0], 1, a[A_S0], n.sz[0], B, true));
   BEC_TRY(restrict_ch<AT>(p, a[A_S0], a[A_R0], 0, B, 1.f, false));
@@ -622,7 +654,7 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
     }
   }
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  return BEC_OK;
+  return net_check(p);
 }
 
 template <typename AT>
@@ -631,11 +663,9 @@ bec_status correct_t(bec_problem* p) {
   MgLevel& L0 = p->mg.lv[0];
   const int K = p->mg.K;
   const long long mff = (long long)n.mf * n.mf;
-  // residual the V-cycle left, and its norm per frequency
+  // residual the V-cycle left
   BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
-  BEC_LAUNCH_BEGIN(p);
-  freq_sumsq_kernel<<<K, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.res), n.part, mff);
-  BEC_LAUNCH_CHECK(p, "net_freq_norm_kernel");
+  // x1 = x + P_0 (s c_k Net(...)), in batches of Bmax frequencies
   for (int k0 = 0; k0 < K; k0 += n.Bmax) {
     const int B = K - k0 < n.Bmax ? K - k0 : n.Bmax;
     n.cur_row = n.iota + k0;
@@ -648,18 +678,22 @@ bec_status correct_t(bec_problem* p) {
         reinterpret_cast<const float2*>(n.efine), mff, k0, B);
     BEC_LAUNCH_CHECK(p, "net_add_correction_kernel");
   }
-  // judge: keep the correction only where it lowered the residual
-  BEC_TRY(mg_residual_level0(p, L0.r, n.xnew, L0.b));
+  // x2 = one damped-Jacobi sweep on x1 (the post-smoothing of a prolonged
+  // correction), into L0.r (V-cycle scratch); its residual into xnew
+  BEC_TRY(mg_smooth_level0(p, L0.r, n.xnew, L0.b));
+  BEC_TRY(mg_residual_level0(p, n.xnew, L0.r, L0.b));
+  // the judge: the minimal-residual step along x2 - x, per frequency
   BEC_LAUNCH_BEGIN(p);
-  freq_sumsq_kernel<<<K, 256, 0, p->stream>>>(static_cast<const float2*>(L0.r), n.part + K, mff);
-  BEC_LAUNCH_CHECK(p, "net_freq_norm_kernel");
-  int* fb = reinterpret_cast<int*>(n.part + 2 * K);
+  mr_dots_kernel<<<K, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.res),
+                                           reinterpret_cast<const float2*>(n.xnew), n.part, mff);
+  BEC_LAUNCH_CHECK(p, "net_judge_dots_kernel");
+  int* fb = reinterpret_cast<int*>(n.part + 5 * K);
   BEC_CUDA_TRY(cudaMemsetAsync(fb, 0, sizeof(int), p->stream));
   BEC_LAUNCH_BEGIN(p);
-  judge_select_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
-      static_cast<float2*>(L0.x), reinterpret_cast<const float2*>(n.xnew), n.part, n.part + K, mff,
-      K, fb);
-  BEC_LAUNCH_CHECK(p, "net_judge_kernel");
+  mr_update_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
+      static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.part, mff, K, n.part + 4 * K,
+      fb);
+  BEC_LAUNCH_CHECK(p, "net_judge_update_kernel");
   return BEC_OK;
 }
 
@@ -730,10 +764,13 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   chain(dalloc(reinterpret_cast<void**>(&n->etgt), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->ework), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->xnew), (size_t)K * mff * sizeof(float2)));
-  chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(2 * K + 2 * bmax + 2) * sizeof(double)));
+  chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
+  chain(dalloc(reinterpret_cast<void**>(&n->err), sizeof(int)));
+  n->tc = !n->fp32 && C == 32 && tc_conv_supported();
+  if (n->tc) chain(dalloc(reinterpret_cast<void**>(&n->wt), 7 * 9 * 32 * 32 * sizeof(__nv_bfloat16)));
   if (s == BEC_OK) {
     if (cudaMallocHost(reinterpret_cast<void**>(&n->h_idx), 2 * bmax * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&n->h_part), (2 * K + 2 * bmax + 2) * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(reinterpret_cast<void**>(&n->h_part), (5 * K + 2 * bmax + 2) * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       s = BEC_ENOMEM;
     }
@@ -775,6 +812,7 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   BEC_CUDA_TRY(cudaMemcpy(n->W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice));
   BEC_CUDA_TRY(cudaMemset(n->Mo, 0, nw * sizeof(float)));
   BEC_CUDA_TRY(cudaMemset(n->Ve, 0, nw * sizeof(float)));
+  BEC_CUDA_TRY(cudaMemset(n->err, 0, sizeof(int)));
   return BEC_OK;
 }
 
@@ -782,7 +820,8 @@ void net_free(bec_problem* p) {
   NetState* n = p->net;
   if (n == nullptr) return;
   void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->la_c, n->rc, n->sinv, n->cfac, n->row,
-                  n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part};
+                  n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part,
+                  n->err, n->wt};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int a = 0; a < NACT; ++a) {
@@ -859,7 +898,7 @@ bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, 
   *loss_out = l / B;
   if (grad_host)
     BEC_CUDA_TRY(cudaMemcpy(grad_host, n.G, n.woff[9] * sizeof(float), cudaMemcpyDeviceToHost));
-  return BEC_OK;
+  return net_check(p);
 }
 }  // namespace
 
@@ -877,9 +916,27 @@ long long net_fallbacks(bec_problem* p) {
   if (p->net == nullptr) return -1;
   int fb = 0;
   cudaStreamSynchronize(p->stream);
-  cudaMemcpy(&fb, reinterpret_cast<int*>(p->net->part + 2 * p->mg.K), sizeof(int),
+  cudaMemcpy(&fb, reinterpret_cast<int*>(p->net->part + 5 * p->mg.K), sizeof(int),
              cudaMemcpyDeviceToHost);
   return fb;
+}
+
+bec_status net_check(bec_problem* p) {
+  if (p->net == nullptr || p->net->err == nullptr) return BEC_OK;
+  int v = 0;
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(&v, p->net->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v == 0) return BEC_OK;
+  BEC_CUDA_TRY(cudaMemset(p->net->err, 0, sizeof(int)));
+  set_error("a bounded wait in the tensor-core convolution ran out");
+  return BEC_ETIMEOUT;
+}
+
+bec_status net_residual_ratios(bec_problem* p, double* host) {
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(host, p->net->part + 4 * p->mg.K, p->mg.K * sizeof(double),
+                          cudaMemcpyDeviceToHost));
+  return BEC_OK;
 }
 
 }  // namespace bec

@@ -71,10 +71,13 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
 template <int NV>
 __global__ void __launch_bounds__(kStencilThreads)
 stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, StencilGeom g, VecList V,
+                    const double* __restrict__ vshift, const double* __restrict__ sshift,
                     double* __restrict__ partials) {
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  double accn = 0.0;
+  const double ss = vshift ? sshift[0] : 0.0;
   const long long jt = (g.J + kStencilThreads - 1) / kStencilThreads;
   const long long tiles = jt * ((g.N + kTimeChunk - 1) / kTimeChunk);
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -89,14 +92,16 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
       const double* zs = z + (long long)n * g.J;
       const double center = zs[q];
       const long long o = (long long)n * g.J + q;
-      const double y = apply_row(zs, q, ix, iy, g, center, prev);
+      double y = apply_row(zs, q, ix, iy, g, center, prev);
+      if (vshift) y = fma(-ss, vshift[o], y);
       w[o] = y;
       prev = center;
+      accn = fma(y, y, accn);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = fma(V.v[v][o], y, acc[v]);
     }
   }
-  __shared__ double red[kStencilThreads / 32][NV];
+  __shared__ double red[kStencilThreads / 32][NV + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -104,12 +109,14 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) red[warp][v] = s;
   }
+  for (int off = 16; off > 0; off >>= 1) accn += __shfl_down_sync(0xffffffffu, accn, off);
+  if (lane == 0) red[warp][NV] = accn;
   __syncthreads();
-  if ((int)threadIdx.x < NV) {
+  if ((int)threadIdx.x <= NV) {
     double s = 0.0;
 #pragma unroll
     for (int wi = 0; wi < kStencilThreads / 32; ++wi) s += red[wi][threadIdx.x];
-    partials[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    partials[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;   // row NV: sum of w^2
   }
 }
 
@@ -254,7 +261,8 @@ bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double cor
 
 bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
                                const double* const* V, int nv, const double* sigma,
-                               double* hout) {
+                               double* hout, const double* vshift, const double* sshift,
+                               int norm_slot) {
   const int n = nv < kMaxVec ? nv : kMaxVec;
   VecList L;
   for (int i = 0; i < kMaxVec; ++i) L.v[i] = i < n ? V[i] : V[0];
@@ -263,7 +271,7 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
 #define BEC_SD_CASE(NV)                                                                     \
   case NV:                                                                                  \
     stencil_dots_kernel<NV><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(          \
-        z, w, geom(p), L, p->partials);                                                     \
+        z, w, geom(p), L, vshift, sshift, p->partials);                                     \
     break;
     BEC_SD_CASE(1) BEC_SD_CASE(2) BEC_SD_CASE(3) BEC_SD_CASE(4) BEC_SD_CASE(5) BEC_SD_CASE(6)
     BEC_SD_CASE(7) BEC_SD_CASE(8) BEC_SD_CASE(9) BEC_SD_CASE(10) BEC_SD_CASE(11) BEC_SD_CASE(12)
@@ -275,7 +283,13 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
     default: return BEC_EINVAL;
   }
   BEC_LAUNCH_CHECK(p, "stencil_dots_kernel");
-  bec_status s = launch_finish_dots(p, n, kStencilDotBlocks, sigma, hout);
+  bec_status s = BEC_OK;
+  if (norm_slot >= 0) {
+    s = launch_finish_sqrt(p, p->partials + (long long)n * kStencilDotBlocks, kStencilDotBlocks,
+                           norm_slot, nullptr);
+    if (s != BEC_OK) return s;
+  }
+  s = launch_finish_dots(p, n, kStencilDotBlocks, sigma, hout);
   if (s != BEC_OK || nv <= kMaxVec) return s;
   // more vectors than one fused launch holds: the rest as plain dots
   return launch_dots(p, w, V + kMaxVec, nv - kMaxVec, sigma ? sigma + kMaxVec : nullptr,

@@ -41,7 +41,7 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   using V = v2_t<T>;
   const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
   constexpr int N = 1 << LOGN;
-  constexpr int LSC = N + 1;
+  constexpr int LSC = line_slots(LOGN);
   constexpr int WARPS = time_warps<T>();
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
@@ -103,7 +103,7 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
                        const v2_t<T>* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int warps = time_warps<T>();
-  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T);
+  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
   auto k = time_pass_kernel<T, LOGN>;
   if (smem > 48 * 1024)
     BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -144,7 +144,7 @@ time_fwd_kernel(const double* __restrict__ y, v2_t<T>* __restrict__ spec, long l
                 const v2_t<T>* __restrict__ tw) {
   using V = v2_t<T>;
   constexpr int N = 1 << LOGN;
-  constexpr int LSC = N + 1;
+  constexpr int LSC = line_slots(LOGN);
   constexpr int WARPS = time_warps<T>();
   constexpr int W = 2 * WARPS;
   constexpr int NK = N / 2 + 1;
@@ -177,14 +177,15 @@ time_fwd_kernel(const double* __restrict__ y, v2_t<T>* __restrict__ spec, long l
 }
 
 // Step 3 alone (multigrid route): z[j][q] = scale eps^{-j/N} sum_k Z_k
-// e^{+2 pi i jk/N} with Z_{N-k} = conj(Z_k), from the half spectrum.
+// e^{+2 pi i jk/N} with Z_{N-k} = conj(Z_k), from the half spectrum; the
+// imaginary parts of Z_0 and Z_{N/2} are ignored (complex-to-real inverse).
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(time_warps<T>() * 32)
 time_inv_kernel(const v2_t<T>* __restrict__ spec, double* __restrict__ z, long long J,
                 const T* __restrict__ eis, T scale, const v2_t<T>* __restrict__ tw) {
   using V = v2_t<T>;
   constexpr int N = 1 << LOGN;
-  constexpr int LSC = N + 1;
+  constexpr int LSC = line_slots(LOGN);
   constexpr int WARPS = time_warps<T>();
   constexpr int W = 2 * WARPS;
   constexpr int NK = N / 2 + 1;
@@ -202,8 +203,14 @@ time_inv_kernel(const v2_t<T>* __restrict__ spec, double* __restrict__ z, long l
   V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
   for (int k = lane; k < NK; k += 32) {
     const V A = in[k * W + 2 * warp], B = in[k * W + 2 * warp + 1];
-    line[k] = {A.x - B.y, A.y + B.x};                    // A + i B
-    if (k > 0 && k < N / 2) line[N - k] = {A.x + B.y, B.x - A.y};   // conj(A) + i conj(B)
+    if (k > 0 && k < N / 2) {
+      line[k] = {A.x - B.y, A.y + B.x};                  // A + i B
+      line[N - k] = {A.x + B.y, B.x - A.y};              // conj(A) + i conj(B)
+    } else {
+      // k = 0 and N/2 of a real signal are real: their imaginary parts are
+      // dropped (a complex-to-real inverse), not mixed into the other line
+      line[k] = {A.x, B.x};
+    }
   }
   __syncwarp();
   warp_fft<T, +1, LOGN>(line, tw, lane);
@@ -221,7 +228,7 @@ bec_status time_fwd_launch(bec_problem* p, const double* y, void* spec, double s
                            const double* scale_dev, const T* es, const v2_t<T>* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int warps = time_warps<T>();
-  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T) +
+  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T) +
                       (size_t)(N / 2 + 1) * 2 * warps * sizeof(v2_t<T>);
   auto k = time_fwd_kernel<T, LOGN>;
   if (smem > 48 * 1024)
@@ -239,7 +246,7 @@ bec_status time_inv_launch(bec_problem* p, const void* spec, double* z, double s
                            const T* eis, const v2_t<T>* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int warps = time_warps<T>();
-  const size_t smem = (size_t)warps * 2 * (N + 1) * sizeof(T) +
+  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T) +
                       (size_t)(N / 2 + 1) * 2 * warps * sizeof(v2_t<T>);
   auto k = time_inv_kernel<T, LOGN>;
   if (smem > 48 * 1024)
