@@ -83,12 +83,25 @@ NET_LAYERS = [(5, 32, 0), (32, 32, 0), (32, 32, 1), (32, 32, 2), (32, 32, 3), (3
               (32, 32, 1), (32, 32, 0), (32, 2, 0)]
 
 
-def net_fwd_flops(m: int) -> float:
-    """FLOPs of one forward pass of the network for one frequency (2 per MAC)."""
+def net_levels(m: int):
     sz = [(m - 1) // 2]
     for _ in range(3):
         sz.append((sz[-1] - 1) // 2)
+    return sz
+
+
+def net_fwd_flops(m: int) -> float:
+    """FLOPs of one forward pass of the network for one frequency (2 per MAC)."""
+    sz = net_levels(m)
     return sum(2.0 * 9 * ci * co * sz[l] ** 2 for ci, co, l in NET_LAYERS)
+
+
+def net_tc_flops(m: int) -> float:
+    """The part of net_fwd_flops the tensor-core kernel runs: the 32 -> 32
+    layers on grids of side >= 16."""
+    sz = net_levels(m)
+    return sum(2.0 * 9 * ci * co * sz[l] ** 2 for ci, co, l in NET_LAYERS
+               if ci == 32 and co == 32 and sz[l] >= 16)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of each kernel at this workload (see profiles/); None = not captured for the
 # current build of the kernel.
@@ -106,7 +119,8 @@ def parse():
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip measuring the other preconditioner form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32"), default=None,
+    ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32", "learned_bf16"),
+                    default=None,
                     help="run a small bounded case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -265,6 +279,7 @@ def measure_form(form, case, args, ws, local, dist):
     prob = Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=RESTART, flexible=True,
                    host_io=True)
     prob.set_eps(EPS)
+    tiles = prob.autotune()          # block widths of the P_eps^-1 passes, before any timing
     f = prob.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
     u = torch.empty_like(f)
     solve_kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=True)
@@ -319,7 +334,8 @@ def measure_form(form, case, args, ws, local, dist):
     prob.close()
     return {"U": U, "ms_step": ms_step, "kernels": kernels, "launches": launches,
             "clocks": clocks, "info": infos[-1], "e2e_s": e2e_s,
-            "e2e_samples_ms": [round(x * 1e3, 3) for x in e2e]}
+            "e2e_samples_ms": [round(x * 1e3, 3) for x in e2e],
+            "tiles": {k: tiles[k] for k in ("rows_warps", "cols_warps", "time_warps")}}
 
 
 def roofline(form, kernels, U):
@@ -400,15 +416,23 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16):
     avg = tot / n
     word = 8 if precision == "fp32" else 16
     base = dom.split("[")[0]
-    if base == "net_conv_fwd_kernel":
-        # all 9 layers share the name: FLOPs of whole forward passes over their time
-        applies = n / len(NET_LAYERS)
-        ach = applies * K * net_fwd_flops(m) / (tot / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "algorithmic_per_unit": f"{net_fwd_flops(m) / 1e6:.1f} MFLOP per frequency per apply",
-                "units_per_launch": "one layer of 129 or fewer frequencies (batches of 32)",
-                "avg_launch_ms": avg}
+    if route == "learned":
+        # the network's tensor-core convolution (row a5): its FLOPs over its
+        # own time; timed inside a long solve, so against the sustained peak
+        dom = "net_conv_tc_kernel"
+        n, tot = kernels[dom]
+        avg = tot / n
+        applies = kernels["mg_coarsest_kernel"][0]   # one V-cycle per P_eps^{-1} apply
+        peaks, src = measured_peaks()
+        pk = peaks.get("bf16_tflops_sustained", 1698.3)
+        ach = applies * K * net_tc_flops(m) / (tot / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "peak_source": "bf16_tflops_sustained " + src,
+                "algorithmic_per_unit": f"{2 * 9 * 32 * 32} FLOP per output pixel (3x3, 32 -> 32)",
+                "units_per_launch": "B x side^2 pixels, B <= 32 frequencies",
+                "flops_per_apply": K * net_tc_flops(m), "avg_launch_ms": avg,
+                "other_network_kernels_ms": {k: round(v[1], 3) for k, v in kernels.items()
+                                             if k.startswith("net_") and k != dom}}
     elif base in MG_WORDS:
         lvl = int(dom.split("[l")[1].rstrip("]"))
         ml = m
@@ -419,7 +443,7 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16):
     else:
         units = U
         bpu, fpu = 8 + 0.5 * word, 5.0 * LOG2T / 2
-    if base != "net_conv_fwd_kernel":
+    if route != "learned":
         peaks, src = measured_peaks()
         if precision == "fp64":
             ach = fpu * units / (avg / 1e3) / 1e12
@@ -519,7 +543,7 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded U[-1,1] source, 8x8 random sine-series u0)",
         "config": dict(workload_config(form), iterations=r["info"]["iters"],
-                       true_relres=r["info"]["true_relres"],
+                       true_relres=r["info"]["true_relres"], autotuned_warps_per_block=r["tiles"],
                        parallelism=f"{ws} independent replicas"),
         "roofline": roofline(form, r["kernels"], U),
         "e2e": {"value": ws * U / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": U * 8,
@@ -538,6 +562,7 @@ def run_gpu(args):
             "value": ws * U / (o["ms_step"] / 1e3), "unit": UNIT, "ms_per_step": o["ms_step"],
             "iterations": o["info"]["iters"], "true_relres": o["info"]["true_relres"],
             "e2e_value": ws * U / o["e2e_s"], "gpu_launches": o["launches"], "clocks": o["clocks"],
+            "autotuned_warps_per_block": o["tiles"],
             "roofline": roofline(other, o["kernels"], U), "kernels": kernel_table(o["kernels"]),
             "note": "same workload and tolerance; FP32/complex64 P_eps^-1 inside FP64 FGMRES"
                     if other == "fp32" else "same workload; plain FP64 form"}}
@@ -564,13 +589,29 @@ def run_gpu(args):
 def run_ncu_case(which: str):
     """A bounded workload for profiler captures: the benchmark problem with a
     two-vector Krylov basis (under 1 GB on the device), three P_eps^{-1}
-    applies and two stencil applies, or one short FGMRES solve."""
+    applies and two stencil applies, or one short FGMRES solve; or three
+    learned-route P_eps^{-1} applies at 255^2 x 64."""
     import torch
     torch.cuda.set_device(0)
     from paper_2002_01108_gb300 import Problem
     from paper_2002_01108_gb300 import build as bec_build
     from workloads import heat_case_2d
     bec_build.build()
+    if which == "learned_bf16":
+        # the learned route at 255^2 with N = 64 (33 frequencies: one batch of
+        # 32 and one of 1), untrained weights, three P_eps^{-1} applies
+        import numpy as np
+        from workloads import grf_log_coefficient
+        a = np.exp(grf_log_coefficient(seed=5, m=M_SIDE))
+        y = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (64, M_SIDE, M_SIDE))).cuda()
+        with Problem(2, M_SIDE, 64, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
+            p.set_eps(1.0 / 16)
+            z = torch.empty_like(y)
+            for _ in range(3):
+                p.apply_Pinv(y, z)
+            torch.cuda.synchronize()
+        print(f"ncu case {which} done")
+        return 0
     case = heat_case_2d(seed=2, m=M_SIDE, N=N_STEPS, eps=EPS)
     form = "fp64" if which == "pinv_fp64" else "fp32"
     with Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=2, flexible=form == "fp32") as p:

@@ -253,6 +253,40 @@ long long bec_learned_fallbacks(bec_problem* p);
  * correction gained nothing there).  Synchronises. */
 bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
 
+/* ---- Tile shapes of the P_eps^{-1} passes --------------------------------
+ * Not a construct of the paper.  The x-DST, y-DST and time passes group
+ * their lines into blocks of 4, 8 or 16 warps (one line pair per warp).
+ * bec_autotune times each width on this GPU with the problem's own
+ * workspace (it overwrites the Krylov basis and scratch, so it must not
+ * overlap a solve on the same problem), keeps the fastest per pass, and
+ * caches the choice for the process per (precision, dim, nx, N); force = 1
+ * re-times a cached shape.  The width only regroups lines, so every choice
+ * gives the same result bit for bit.  Transforms shorter than 32 and the
+ * multigrid and learned routes have nothing to tune (the report is zero).
+ * bec_batch_create tunes each instance.  Synchronises. */
+typedef struct {
+  int rows_warps, cols_warps, time_warps; /* chosen widths (warps per block) */
+  float rows_ms[3], cols_ms[3], time_ms[3]; /* ms per launch at 4, 8, 16 warps; 0 = not tried */
+  int cached;                              /* 1: taken from an earlier tuning of the shape */
+} bec_tune_report;
+bec_status bec_autotune(bec_problem* p, int force, bec_tune_report* report /* may be NULL */);
+/* Sets the widths by hand: 0 (the default), 4, 8 or 16 warps per pass.
+ * BEC_EINVAL for other values, for a non-zero width of a transform shorter
+ * than 32, or for a width whose shared memory does not fit a block. */
+bec_status bec_set_tiles(bec_problem* p, int rows_warps, int cols_warps, int time_warps);
+
+/* ---- Precision conversions ---------------------------------------------
+ * Not a construct of the paper.  The conversions the FP32 preconditioner
+ * applies where it reads y and writes z: n doubles to floats (IEEE round to
+ * nearest, ties to even) and n floats to doubles (exact).  They are done in
+ * integer arithmetic, because the hardware conversion runs on the FP64 pipe,
+ * and they agree with the hardware conversion bit for bit.  x and y are device
+ * arrays that must not overlap; the calls are asynchronous on `stream` (a
+ * cudaStream_t, NULL = the default stream).  BEC_EINVAL for n < 0 or a null
+ * pointer with n > 0. */
+bec_status bec_convert_to_float(const double* x, float* y, long long n, void* stream);
+bec_status bec_convert_to_double(const float* x, double* y, long long n, void* stream);
+
 /* ---- Batches of independent problems of uneven size ---------------------
  * Not a construct of the paper: many independent instances (different grid,
  * N and eps) solved together.  Each instance is a bec_problem (own

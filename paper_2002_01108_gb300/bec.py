@@ -29,6 +29,7 @@ EXPORTED = (
     "bec_batch_kernel_launches", "bec_batch_free", "bec_learned_num_weights",
     "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
     "bec_learned_loss_grad", "bec_learned_fallbacks", "bec_learned_residual_ratios",
+    "bec_convert_to_float", "bec_convert_to_double", "bec_autotune", "bec_set_tiles",
 )
 
 
@@ -57,6 +58,13 @@ class GmresInfo(ctypes.Structure):
 
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("rows_warps", ctypes.c_int), ("cols_warps", ctypes.c_int),
+                ("time_warps", ctypes.c_int), ("rows_ms", ctypes.c_float * 3),
+                ("cols_ms", ctypes.c_float * 3), ("time_ms", ctypes.c_float * 3),
+                ("cached", ctypes.c_int)]
 
 
 class BecError(RuntimeError):
@@ -114,6 +122,10 @@ def _lib():
                                   ctypes.c_int),
         "bec_learned_fallbacks": ([P], ctypes.c_longlong),
         "bec_learned_residual_ratios": ([P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bec_autotune": ([P, ctypes.c_int, ctypes.POINTER(TuneReport)], ctypes.c_int),
+        "bec_set_tiles": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "bec_convert_to_float": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
+        "bec_convert_to_double": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
         "bec_relres_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, D, D, D, P], ctypes.c_int),
         "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
@@ -149,6 +161,29 @@ def _dptr(t, U: int, name: str):
     if t.numel() != U:
         raise ValueError(f"{name} has {t.numel()} elements, expected {U}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def convert(x, out=None):
+    """The library's FP64 <-> FP32 conversion of a contiguous CUDA tensor
+    (float64 -> float32 rounds to nearest even, float32 -> float64 is exact),
+    on the current torch stream."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or not x.is_contiguous():
+        raise TypeError("x must be a contiguous CUDA tensor")
+    if x.dtype == torch.float64:
+        to, fn = torch.float32, "bec_convert_to_float"
+    elif x.dtype == torch.float32:
+        to, fn = torch.float64, "bec_convert_to_double"
+    else:
+        raise TypeError("x must be float32 or float64")
+    if out is None:
+        out = torch.empty(x.shape, dtype=to, device=x.device)
+    if out.dtype != to or not out.is_contiguous() or out.numel() != x.numel():
+        raise ValueError("out must be a contiguous tensor of the other precision and the same size")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(getattr(_lib(), fn)(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                               x.numel(), st), fn)
+    return out
 
 
 class Problem:
@@ -299,6 +334,18 @@ class Problem:
         _check(_lib().bec_profile_stop(self._p, buf, cap, ctypes.byref(n)), "bec_profile_stop")
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms))
                 for i in range(min(n.value, cap))}
+
+    # -- tile shapes of the preconditioner passes
+    def autotune(self, force: bool = False) -> dict:
+        """Times 4, 8 and 16 warps per block for each pass and keeps the fastest."""
+        r = TuneReport()
+        _check(_lib().bec_autotune(self._p, int(force), ctypes.byref(r)), "bec_autotune")
+        return {"rows_warps": r.rows_warps, "cols_warps": r.cols_warps, "time_warps": r.time_warps,
+                "rows_ms": list(r.rows_ms), "cols_ms": list(r.cols_ms), "time_ms": list(r.time_ms),
+                "cached": bool(r.cached)}
+
+    def set_tiles(self, rows: int = 0, cols: int = 0, time: int = 0):
+        _check(_lib().bec_set_tiles(self._p, int(rows), int(cols), int(time)), "bec_set_tiles")
 
     # -- learned correction
     def learned_weights(self):

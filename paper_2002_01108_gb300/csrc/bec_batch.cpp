@@ -69,6 +69,7 @@ bec_status bec_batch_create(const bec_problem_desc* descs, const double* eps, in
     const int si = i % ns;
     bec_status st = bec_allocate_problem(&descs[i], b->streams[si], &p);
     if (st == BEC_OK) st = bec_set_eps(p, eps[i]);
+    if (st == BEC_OK) st = bec_autotune(p, 0, nullptr);   // once per distinct shape (cached)
     if (st != BEC_OK) {
       if (p) bec_free_problem(p);
       const std::string msg = "instance " + std::to_string(i) + ": " + bec_last_error();

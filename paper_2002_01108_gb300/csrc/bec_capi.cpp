@@ -105,7 +105,7 @@ void free_all(bec_problem* p) {
   PcTables& t = p->tab;
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
-                  p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
+                  t.rinv64, p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
                   p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -246,6 +246,8 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&t.eis32, N));
   chain(dmalloc(&t.lamf64, N / 2 + 1));
   chain(dmalloc(&t.lamf32, N / 2 + 1));
+  if (d->precision == BEC_PC_FP64 && d->route == BEC_ROUTE_FST)
+    chain(dmalloc(&t.rinv64, (size_t)p->J * (N / 2 + 1)));
   if (mgroute && s == BEC_OK) {
     p->mg.pre = d->mg_pre == 0 ? 1 : d->mg_pre;
     p->mg.post = (d->mg_pre == 0 && d->mg_post == 0) ? 1 : d->mg_post;
@@ -370,6 +372,7 @@ bec_status bec_set_eps(bec_problem* p, double eps) {
   BEC_TRY(upload(t.eis32, eis32, p->stream));
   BEC_TRY(upload(t.lamf64, lam, p->stream));
   BEC_TRY(upload(t.lamf32, lam32, p->stream));
+  if (t.rinv64) BEC_TRY(launch_rinv_table(p));
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
   p->eps = eps;
   return BEC_OK;
@@ -549,6 +552,28 @@ bec_status bec_learned_residual_ratios(bec_problem* p, double* host) {
   BEC_TRY(need_net(p));
   if (host == nullptr) return einval("null host pointer");
   return net_residual_ratios(p, host);
+}
+
+bec_status bec_autotune(bec_problem* p, int force, bec_tune_report* report) {
+  if (p == nullptr) return einval("null problem");
+  return autotune(p, force, report);
+}
+
+bec_status bec_set_tiles(bec_problem* p, int rows_warps, int cols_warps, int time_warps) {
+  if (p == nullptr) return einval("null problem");
+  return set_tiles(p, rows_warps, cols_warps, time_warps);
+}
+
+bec_status bec_convert_to_float(const double* x, float* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (x == nullptr || y == nullptr))) return einval("bad conversion arguments");
+  const cudaError_t e = launch_convert(x, y, n, 1, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BEC_OK : cuda_fail(e, "convert_kernel_f32");
+}
+
+bec_status bec_convert_to_double(const float* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (x == nullptr || y == nullptr))) return einval("bad conversion arguments");
+  const cudaError_t e = launch_convert(x, y, n, 0, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BEC_OK : cuda_fail(e, "convert_kernel_f64");
 }
 
 const char* bec_status_string(bec_status s) {

@@ -10,51 +10,76 @@
 namespace bec {
 namespace {
 
-template <typename T>
-constexpr int rows_warps() { return 8; }
-template <typename T>
-constexpr int cols_warps() { return sizeof(T) == 8 ? 8 : 16; }
 
 // DST along x: one warp per pair of contiguous rows of length m = n - 1.
 // `in` and `out` may be the same array (each warp reads its rows before
 // writing them); in that case TI == TO.
-template <typename T, typename TI, typename TO, int LOGN>
-__global__ void __launch_bounds__(rows_warps<T>() * 32)
+template <typename T, typename TI, typename TO, int LOGN, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
-  constexpr int n = 1 << LOGN;
   constexpr int LSC = line_slots(LOGN);      // complex slots per line
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* raw = sm + (size_t)warp * 2 * LSC;
-  const long long r0 = 2 * ((long long)blockIdx.x * rows_warps<T>() + warp);
+  const long long r0 = 2 * ((long long)blockIdx.x * WARPS + warp);
   if (r0 >= rows) return;                    // whole warp leaves; no block barrier below
   const bool hasb = r0 + 1 < rows;
   const TI* ia = in + r0 * m;
-  for (int j = lane; j < m; j += 32) {
-    raw[j] = (T)ia[j];
-    raw[LSC + j] = hasb ? (T)ia[m + j] : T(0);
+  // loads in groups of G per row, all issued before the group's conversions
+  // (m = n - 1 < 32 PER)
+  constexpr int PER = (1 << LOGN) / 32 > 0 ? (1 << LOGN) / 32 : 1;
+  constexpr int G = PER < 8 ? PER : 8;
+#pragma unroll
+  for (int t0 = 0; t0 < PER; t0 += G) {
+    TI va[G], vb[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int j = lane + 32 * (t0 + t);
+      va[t] = j < m ? ia[j] : TI(0);
+      vb[t] = (j < m && hasb) ? ia[m + j] : TI(0);
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int j = lane + 32 * (t0 + t);
+      if (j < m) {
+        raw[j] = convert<T>(va[t]);
+        raw[LSC + j] = convert<T>(vb[t]);
+      }
+    }
   }
   __syncwarp();
   warp_dst_pair<T, LOGN>(raw, LSC, sin2, tw, lane);
   TO* oa = out + r0 * m;
-  for (int j = lane; j < m; j += 32) {
-    oa[j] = (TO)raw[j];
-    if (hasb) oa[m + j] = (TO)raw[LSC + j];
+#pragma unroll
+  for (int t0 = 0; t0 < PER; t0 += G) {
+    TO wa[G], wb[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int j = lane + 32 * (t0 + t);
+      wa[t] = j < m ? convert<TO>(raw[j]) : TO(0);
+      wb[t] = j < m ? convert<TO>(raw[LSC + j]) : TO(0);
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int j = lane + 32 * (t0 + t);
+      if (j < m) {
+        oa[j] = wa[t];
+        if (hasb) oa[m + j] = wb[t];
+      }
+    }
   }
 }
 
 // DST along y, in place, for every slice of `nslices` [m][m] slices: a block
 // owns W = 2 x warps adjacent columns of one slice; the tile is loaded and
 // stored with coalesced row segments, each warp transforms one column pair.
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(cols_warps<T>() * 32)
+template <typename T, int LOGN, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 dst_cols_kernel(T* data, int m, long long J, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
-  constexpr int n = 1 << LOGN;
   constexpr int LSC = line_slots(LOGN);
-  constexpr int WARPS = cols_warps<T>();
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
@@ -62,6 +87,7 @@ dst_cols_kernel(T* data, int m, long long J, const T* __restrict__ sin2,
   const int x0 = blockIdx.x * W;
   T* base = data + (long long)blockIdx.y * J;
   const int total = m * W;
+#pragma unroll 4
   for (int e = threadIdx.x; e < total; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const int x = x0 + c;
@@ -70,6 +96,7 @@ dst_cols_kernel(T* data, int m, long long J, const T* __restrict__ sin2,
   __syncthreads();
   warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * LSC, LSC, sin2, tw, lane);
   __syncthreads();
+#pragma unroll 4
   for (int e = threadIdx.x; e < total; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const int x = x0 + c;
@@ -84,35 +111,53 @@ cudaError_t prepare(Kern k, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename T, typename TI, typename TO, int LOGN>
+template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 bec_status rows_launch(bec_problem* p, const void* in, void* out, long long rows,
                        const T* sin2, const v2_t<T>* tw) {
-  constexpr int n = 1 << LOGN;
-  const int warps = rows_warps<T>();
-  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
-  auto k = dst_rows_kernel<T, TI, TO, LOGN>;
+  const size_t smem = (size_t)WARPS * 2 * line_slots(LOGN) * sizeof(T);
+  auto k = dst_rows_kernel<T, TI, TO, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
   const long long pairs = (rows + 1) / 2;
-  const unsigned grid = (unsigned)((pairs + warps - 1) / warps);
+  const unsigned grid = (unsigned)((pairs + WARPS - 1) / WARPS);
   BEC_LAUNCH_BEGIN(p);
-  k<<<grid, warps * 32, smem, p->stream>>>(static_cast<const TI*>(in), static_cast<TO*>(out), rows,
+  k<<<grid, WARPS * 32, smem, p->stream>>>(static_cast<const TI*>(in), static_cast<TO*>(out), rows,
                                            p->m, sin2, tw);
   BEC_LAUNCH_CHECK(p, "dst_rows_kernel");
   return BEC_OK;
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int WARPS>
 bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>* tw) {
-  constexpr int n = 1 << LOGN;
-  constexpr int warps = cols_warps<T>();
-  const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
-  auto k = dst_cols_kernel<T, LOGN>;
+  const size_t smem = (size_t)WARPS * 2 * line_slots(LOGN) * sizeof(T);
+  auto k = dst_cols_kernel<T, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
-  dim3 grid((unsigned)((p->m + 2 * warps - 1) / (2 * warps)), (unsigned)p->N);
+  dim3 grid((unsigned)((p->m + 2 * WARPS - 1) / (2 * WARPS)), (unsigned)p->N);
   BEC_LAUNCH_BEGIN(p);
-  k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->m, p->J, sin2, tw);
+  k<<<grid, WARPS * 32, smem, p->stream>>>(static_cast<T*>(data), p->m, p->J, sin2, tw);
   BEC_LAUNCH_CHECK(p, "dst_cols_kernel");
   return BEC_OK;
+}
+
+// The block width w (warps per block) is tunable for n >= 32; shorter
+// transforms always use the default.
+template <typename T, typename TI, typename TO, int LOGN>
+bec_status rows_w(bec_problem* p, int w, const void* in, void* out, long long rows, const T* sin2,
+                  const v2_t<T>* tw) {
+  if constexpr (LOGN >= 5) {
+    if (w == 4) return rows_launch<T, TI, TO, LOGN, 4>(p, in, out, rows, sin2, tw);
+    if (w == 16) return rows_launch<T, TI, TO, LOGN, 16>(p, in, out, rows, sin2, tw);
+  }
+  return rows_launch<T, TI, TO, LOGN, kRowsWarps>(p, in, out, rows, sin2, tw);
+}
+
+template <typename T, int LOGN>
+bec_status cols_w(bec_problem* p, int w, void* data, const T* sin2, const v2_t<T>* tw) {
+  if constexpr (LOGN >= 5) {
+    if (w == 4) return cols_launch<T, LOGN, 4>(p, data, sin2, tw);
+    if (w == 8) return cols_launch<T, LOGN, 8>(p, data, sin2, tw);
+    if (w == 16) return cols_launch<T, LOGN, 16>(p, data, sin2, tw);
+  }
+  return cols_launch<T, LOGN, default_cols_warps(sizeof(T))>(p, data, sin2, tw);
 }
 
 #define BEC_LOGN_SWITCH(logn, CALL)         \
@@ -130,9 +175,9 @@ bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>*
   }
 
 template <typename T, typename TI, typename TO>
-bec_status rows_dispatch(bec_problem* p, const void* in, void* out, long long rows,
+bec_status rows_dispatch(bec_problem* p, int w, const void* in, void* out, long long rows,
                          const T* sin2, const v2_t<T>* tw) {
-#define BEC_ROWS_CALL(L) rows_launch<T, TI, TO, L>(p, in, out, rows, sin2, tw)
+#define BEC_ROWS_CALL(L) rows_w<T, TI, TO, L>(p, w, in, out, rows, sin2, tw)
   BEC_LOGN_SWITCH(p->tab.space.logn, BEC_ROWS_CALL)
 #undef BEC_ROWS_CALL
   set_error("unsupported spatial transform length");
@@ -140,35 +185,64 @@ bec_status rows_dispatch(bec_problem* p, const void* in, void* out, long long ro
 }
 
 template <typename T>
-bec_status cols_dispatch(bec_problem* p, void* data, const T* sin2, const v2_t<T>* tw) {
-#define BEC_COLS_CALL(L) cols_launch<T, L>(p, data, sin2, tw)
+bec_status cols_dispatch(bec_problem* p, int w, void* data, const T* sin2, const v2_t<T>* tw) {
+#define BEC_COLS_CALL(L) cols_w<T, L>(p, w, data, sin2, tw)
   BEC_LOGN_SWITCH(p->tab.space.logn, BEC_COLS_CALL)
 #undef BEC_COLS_CALL
   set_error("unsupported spatial transform length");
   return BEC_EUNSUPPORTED;
 }
 
+__global__ void convert_kernel_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y[g] = f64_to_f32(x[g]);
+}
+
+__global__ void convert_kernel_f64(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y[g] = f32_to_f64(x[g]);
+}
+
 }  // namespace
 
-bec_status launch_dst_rows(bec_problem* p, const void* in, int in_fp64, void* out, int out_fp64,
-                           long long rows, int fp64) {
+cudaError_t launch_convert(const void* x, void* y, long long n, int to_float, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (to_float)
+    convert_kernel_f32<<<grid, 256, 0, st>>>(static_cast<const double*>(x), static_cast<float*>(y), n);
+  else
+    convert_kernel_f64<<<grid, 256, 0, st>>>(static_cast<const float*>(x), static_cast<double*>(y), n);
+  return cudaGetLastError();
+}
+
+bec_status launch_dst_rows_w(bec_problem* p, const void* in, int in_fp64, void* out, int out_fp64,
+                             long long rows, int fp64, int w) {
   if (fp64) {
     if (!in_fp64 || !out_fp64) return BEC_EINVAL;
-    return rows_dispatch<double, double, double>(p, in, out, rows, p->tab.sin2_64,
+    return rows_dispatch<double, double, double>(p, w, in, out, rows, p->tab.sin2_64,
                                                  p->tab.space.tw64);
   }
   const float* s = p->tab.sin2_32;
   const float2* tw = p->tab.space.tw32;
-  if (in_fp64 && !out_fp64) return rows_dispatch<float, double, float>(p, in, out, rows, s, tw);
-  if (!in_fp64 && out_fp64) return rows_dispatch<float, float, double>(p, in, out, rows, s, tw);
-  if (!in_fp64 && !out_fp64) return rows_dispatch<float, float, float>(p, in, out, rows, s, tw);
+  if (in_fp64 && !out_fp64) return rows_dispatch<float, double, float>(p, w, in, out, rows, s, tw);
+  if (!in_fp64 && out_fp64) return rows_dispatch<float, float, double>(p, w, in, out, rows, s, tw);
+  if (!in_fp64 && !out_fp64) return rows_dispatch<float, float, float>(p, w, in, out, rows, s, tw);
   set_error("FP32 row pass needs a float input or a float output");
   return BEC_EINVAL;
 }
 
+bec_status launch_dst_cols_w(bec_problem* p, void* data, int fp64, int w) {
+  if (fp64) return cols_dispatch<double>(p, w, data, p->tab.sin2_64, p->tab.space.tw64);
+  return cols_dispatch<float>(p, w, data, p->tab.sin2_32, p->tab.space.tw32);
+}
+
+bec_status launch_dst_rows(bec_problem* p, const void* in, int in_fp64, void* out, int out_fp64,
+                           long long rows, int fp64) {
+  return launch_dst_rows_w(p, in, in_fp64, out, out_fp64, rows, fp64, p->tile.rows);
+}
+
 bec_status launch_dst_cols(bec_problem* p, void* data, int fp64) {
-  if (fp64) return cols_dispatch<double>(p, data, p->tab.sin2_64, p->tab.space.tw64);
-  return cols_dispatch<float>(p, data, p->tab.sin2_32, p->tab.space.tw32);
+  return launch_dst_cols_w(p, data, fp64, p->tile.cols);
 }
 
 }  // namespace bec

@@ -26,6 +26,50 @@ __device__ __forceinline__ V cmulc(V a, V b) {
   return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+// IEEE 754 binary64 <-> binary32 conversions in integer arithmetic.  On this
+// GPU the hardware conversion runs on the FP64 pipe (2 per clock per SM),
+// which made it the bottleneck of the FP32 passes that read or write the
+// FP64 vectors.  Normal results are formed from the bit fields: the float
+// exponent is the double's minus 896, and the 29 dropped mantissa bits round
+// to nearest, ties to even (a carry into the exponent is the correct
+// result, up to infinity).  Zero, subnormal, overflowing, infinite and NaN
+// inputs take the hardware conversion.
+// the rare cases, out of line so that the hardware conversion is not
+// executed (and its result discarded) on the common path
+static __device__ __noinline__ float f64_to_f32_slow(double x) { return (float)x; }
+static __device__ __noinline__ double f32_to_f64_slow(float x) { return (double)x; }
+
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e - 897u <= 253u) {                                  // float exponent 1..254
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned r = ((e - 896u) << 23) | m;
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | r);
+  }
+  return f64_to_f32_slow(x);
+}
+
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e - 1u <= 253u) {                                    // normal float
+    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+  }
+  return f32_to_f64_slow(x);
+}
+
+// value conversion between the preconditioner's storage types
+template <typename TO, typename TI>
+__device__ __forceinline__ TO convert(TI x) {
+  if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8) return f64_to_f32(x);
+  else if constexpr (sizeof(TO) == 8 && sizeof(TI) == 4) return f32_to_f64(x);
+  else return (TO)x;
+}
+
 // Complex slots a warp's line of n = 2^LOGN values occupies in shared memory:
 // n plus one pad slot per 16 (the padded layout of the intermediate passes),
 // made odd so that a block's lines also start on different banks.
@@ -219,59 +263,115 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
   // sum of the odd outputs, e_k is the even output S_{2k}.
   constexpr int H = n / 2;
   constexpr int CH = H >= 32 ? H / 32 : 1;
-  const int k0 = lane * CH;
-  const bool act = k0 < H;
-  T ra[CH], rb[CH], ea[CH], eb[CH];
-  T sa = 0, sb = 0;
-#pragma unroll
-  for (int i = 0; i < CH; ++i) {
-    ra[i] = rb[i] = ea[i] = eb[i] = 0;
-    if (act) {
-      const int k = k0 + i;
-      const V C = line[k];
-      if (k == 0) {
-        ra[i] = C.x;
-        rb[i] = C.y;
-      } else {
-        const V Cn = line[n - k];
-        ra[i] = C.x + Cn.x;
-        rb[i] = C.y + Cn.y;
-        ea[i] = Cn.y - C.y;
-        eb[i] = C.x - Cn.x;
-      }
-    }
-    sa += ra[i];
-    ra[i] = sa;
-    sb += rb[i];
-    rb[i] = sb;
-  }
-  // exclusive prefix of the per-lane totals across the warp
-  T ta = sa, tb = sb;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const T va = __shfl_up_sync(0xffffffffu, ta, off);
-    const T vb = __shfl_up_sync(0xffffffffu, tb, off);
-    if (lane >= off) {
-      ta += va;
-      tb += vb;
-    }
-  }
-  ta -= sa;
-  tb -= sb;
-  __syncwarp();
-  if (act) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32: lane owns k = lane + 32 i, so the reads of line[k] and line[n-k]
+    // are conflict-free and the writes at most 2-way; the running sum is one
+    // warp scan per row i plus the carry of the rows before.
+    T oa[CH], ob[CH], ea[CH], eb[CH];
+    T ca = 0, cb = 0;
 #pragma unroll
     for (int i = 0; i < CH; ++i) {
-      const int k = k0 + i;
-      raw[2 * k] = ra[i] + ta;           // 4 S_{2k+1}
-      raw[rs + 2 * k] = rb[i] + tb;
-      if (k > 0) {
-        raw[2 * k - 1] = ea[i];          // 4 S_{2k}
-        raw[rs + 2 * k - 1] = eb[i];
+      const int k = lane + 32 * i;
+      T ra = 0, rb = 0;
+      ea[i] = eb[i] = 0;
+      if (k < H) {
+        const V C = line[k];
+        if (k == 0) {
+          ra = C.x;
+          rb = C.y;
+        } else {
+          const V Cn = line[n - k];
+          ra = C.x + Cn.x;
+          rb = C.y + Cn.y;
+          ea[i] = Cn.y - C.y;
+          eb[i] = C.x - Cn.x;
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const T va = __shfl_up_sync(0xffffffffu, ra, off);
+        const T vb = __shfl_up_sync(0xffffffffu, rb, off);
+        if (lane >= off) {
+          ra += va;
+          rb += vb;
+        }
+      }
+      oa[i] = ra + ca;
+      ob[i] = rb + cb;
+      ca += __shfl_sync(0xffffffffu, ra, 31);
+      cb += __shfl_sync(0xffffffffu, rb, 31);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int k = lane + 32 * i;
+      if (k < H) {
+        raw[2 * k] = oa[i];                // 4 S_{2k+1}
+        raw[rs + 2 * k] = ob[i];
+        if (k > 0) {
+          raw[2 * k - 1] = ea[i];          // 4 S_{2k}
+          raw[rs + 2 * k - 1] = eb[i];
+        }
       }
     }
+    __syncwarp();
+  } else {
+    // FP64: lane owns the CH consecutive k from lane * CH: a serial running
+    // sum and one warp scan of the lane totals, the fewest FP64 additions
+    const int k0 = lane * CH;
+    const bool act = k0 < H;
+    T ra[CH], rb[CH], ea[CH], eb[CH];
+    T sa = 0, sb = 0;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      ra[i] = rb[i] = ea[i] = eb[i] = 0;
+      if (act) {
+        const int k = k0 + i;
+        const V C = line[k];
+        if (k == 0) {
+          ra[i] = C.x;
+          rb[i] = C.y;
+        } else {
+          const V Cn = line[n - k];
+          ra[i] = C.x + Cn.x;
+          rb[i] = C.y + Cn.y;
+          ea[i] = Cn.y - C.y;
+          eb[i] = C.x - Cn.x;
+        }
+      }
+      sa += ra[i];
+      ra[i] = sa;
+      sb += rb[i];
+      rb[i] = sb;
+    }
+    // exclusive prefix of the per-lane totals across the warp
+    T ta = sa, tb = sb;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const T va = __shfl_up_sync(0xffffffffu, ta, off);
+      const T vb = __shfl_up_sync(0xffffffffu, tb, off);
+      if (lane >= off) {
+        ta += va;
+        tb += vb;
+      }
+    }
+    ta -= sa;
+    tb -= sb;
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int k = k0 + i;
+        raw[2 * k] = ra[i] + ta;           // 4 S_{2k+1}
+        raw[rs + 2 * k] = rb[i] + tb;
+        if (k > 0) {
+          raw[2 * k - 1] = ea[i];          // 4 S_{2k}
+          raw[rs + 2 * k - 1] = eb[i];
+        }
+      }
+    }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 }  // namespace bec

@@ -19,6 +19,15 @@ struct FftTables {
   float2* tw32 = nullptr;
 };
 
+// Block widths (warps per block) of the P_eps^{-1} passes: the defaults, and
+// a problem's tuned choice (0 = the default; see bec_autotune).
+constexpr int kRowsWarps = 8;
+constexpr int default_cols_warps(int tsize) { return tsize == 8 ? 8 : 16; }
+constexpr int default_time_warps(int tsize) { return tsize == 8 ? 8 : 16; }
+struct TileChoice {
+  int rows = 0, cols = 0, time = 0;
+};
+
 // Everything the preconditioner kernels read besides the vectors.
 struct PcTables {
   FftTables space;           // n = nx + 1
@@ -33,6 +42,9 @@ struct PcTables {
   float* eis32 = nullptr;
   double2* lamf64 = nullptr; // 1 - eps^{1/N} e^{-2 pi i k / N}, k = 0..N/2
   float2* lamf32 = nullptr;
+  // [J][N/2+1]: 1 / |lambda'_k + tau mu_q|^2, FP64 sine-transform route only
+  // (replaces a division per mode and frequency in the ALU-bound time pass)
+  double* rinv64 = nullptr;
 };
 
 // Event pairs around kernel launches (bec_profile_start / bec_profile_stop).
@@ -87,6 +99,7 @@ struct bec_problem {
   long long launches = 0;
 
   bec::PcTables tab;
+  bec::TileChoice tile;         // block widths of the P_eps^{-1} passes
   void* pc_scratch = nullptr;   // U elements of the preconditioner's type
 
   // Krylov workspace (FP64)
@@ -180,16 +193,34 @@ void prof_end(bec_problem* p, const char* name);
   } while (0)
 
 // ---- preconditioner passes (bec_dst.cu, bec_time.cu)
+// Each pass runs with the problem's tuned block width (p->tile); the _w
+// variants take an explicit width (4, 8 or 16 warps; 0 = the default).
 // DST-I (unnormalised, times 4) along x of `rows` contiguous rows of length m.
 bec_status launch_dst_rows(bec_problem* p, const void* in, int in_fp64,
                            void* out, int out_fp64, long long rows, int fp64);
+bec_status launch_dst_rows_w(bec_problem* p, const void* in, int in_fp64, void* out,
+                             int out_fp64, long long rows, int fp64, int w);
 // DST-I (same scaling) along y of every [ny][nx] slice, in place.
 bec_status launch_dst_cols(bec_problem* p, void* data, int fp64);
+bec_status launch_dst_cols_w(bec_problem* p, void* data, int fp64, int w);
 // Time pass: scale, FFT over N, divide by the shifted eigenvalues, inverse
 // FFT, unscale, for every spatial mode, in place.  The divide is multiplied by
 // `scale` and, when scale_dev is not null, by the device scalar *scale_dev.
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
                             const double* scale_dev);
+bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale,
+                              const double* scale_dev, int w);
+// rinv64[q][k] = 1 / |lambda'_k + tau mu_q|^2 from the current lambda' table
+bec_status launch_rinv_table(bec_problem* p);
+// y = x converted between FP64 and FP32 (to_float: double -> float) by the
+// integer conversions of the FP32 passes
+cudaError_t launch_convert(const void* x, void* y, long long n, int to_float, cudaStream_t st);
+// the shared memory pass `which` (0 x-DST, 1 y-DST, 2 time pass) needs at
+// block width w (0 = the default)
+size_t pass_smem_bytes(int which, int logn, int fp64, int w);
+// bec_autotune / bec_set_tiles (bec_tune.cu)
+bec_status autotune(bec_problem* p, int force, bec_tune_report* rep);
+bec_status set_tiles(bec_problem* p, int rows, int cols, int time);
 
 // ---- multigrid route (bec_mg.cu, bec_time.cu)
 // Builds the coefficient rows, the Galerkin hierarchy and its buffers.

@@ -19,7 +19,7 @@ namespace bec {
 namespace {
 
 template <typename T>
-constexpr int time_warps() { return sizeof(T) == 8 ? 8 : 16; }
+constexpr int time_warps() { return default_time_warps(sizeof(T)); }
 
 template <typename T>
 __device__ __forceinline__ T mode_mu(long long q, long long J, int m, int dim,
@@ -30,19 +30,34 @@ __device__ __forceinline__ T mode_mu(long long q, long long J, int m, int dim,
   return mu1[i] + mu1[l];
 }
 
+// rinv[q][k] = 1 / |lambda'_k + tau mu_q|^2 (same arithmetic as the division
+// it replaces in time_pass_kernel)
+__global__ void rinv_table_kernel(double* __restrict__ rinv, long long J, int NK, int m, int dim,
+                                  const double2* __restrict__ lamf,
+                                  const double* __restrict__ mu1, double tau) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= J * NK) return;
+  const long long q = g / NK;
+  const int k = (int)(g - q * NK);
+  const double2 L = lamf[k];
+  const double dr = L.x + tau * mode_mu(q, J, m, dim, mu1);
+  rinv[g] = 1.0 / (dr * dr + L.y * L.y);
+}
+
 // data: [N][J] in place.  A block owns W = 2 x warps adjacent modes; warp w
 // transforms modes (q0 + 2w, q0 + 2w + 1) packed as real + i imaginary.
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(time_warps<T>() * 32)
+// registers: 128 per thread in FP64 and 64 in FP32 for N <= 256 (the block
+// count the bound asks for fills the 64K-register file), free above
+template <typename T, int LOGN, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, LOGN <= 8 ? (sizeof(T) == 8 ? 16 : 32) / WARPS : 1)
 time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
                  const T* __restrict__ mu1, T tau, T scale_h, const double* __restrict__ scale_dev,
-                 const v2_t<T>* __restrict__ tw) {
+                 const v2_t<T>* __restrict__ tw, const T* __restrict__ rinv) {
   using V = v2_t<T>;
   const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
   constexpr int N = 1 << LOGN;
   constexpr int LSC = line_slots(LOGN);
-  constexpr int WARPS = time_warps<T>();
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
@@ -50,6 +65,7 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   const long long q0 = (long long)blockIdx.x * W;
 
   // load + D_eps scaling: mode c of the tile -> line c/2, real (c even) or imaginary part
+#pragma unroll 4
   for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const long long q = q0 + c;
@@ -77,8 +93,14 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
       const V A2 = {C.y + Cn.y, Cn.x - C.x};
       const V L = lamf[k];
       const T d1r = L.x + tau * mua, d2r = L.x + tau * mub;
-      const T s1 = scale / (d1r * d1r + L.y * L.y);
-      const T s2 = scale / (d2r * d2r + L.y * L.y);
+      T s1, s2;
+      if (rinv != nullptr) {           // 1 / |d|^2 from the table ([q][k], coalesced in k)
+        s1 = qa < J ? scale * rinv[qa * NK + k] : T(0);
+        s2 = qa + 1 < J ? scale * rinv[(qa + 1) * NK + k] : s1;
+      } else {
+        s1 = scale / (d1r * d1r + L.y * L.y);
+        s2 = scale / (d2r * d2r + L.y * L.y);
+      }
       const V q1 = {d1r * s1, -L.y * s1};           // scale / d1
       const V q2 = {d2r * s2, -L.y * s2};
       const V B1 = cmul(A1, q1), B2 = cmul(A2, q2);
@@ -90,6 +112,7 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   warp_fft<T, +1, LOGN>(line, tw, lane);
   __syncthreads();
 
+#pragma unroll 4
   for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const long long q = q0 + c;
@@ -97,32 +120,46 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   }
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int WARPS>
 bec_status time_launch(bec_problem* p, void* data, double scale, const double* scale_dev,
                        const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
-                       const v2_t<T>* tw) {
-  constexpr int N = 1 << LOGN;
-  constexpr int warps = time_warps<T>();
+                       const v2_t<T>* tw, const T* rinv) {
+  constexpr int warps = WARPS;
   const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
-  auto k = time_pass_kernel<T, LOGN>;
+  auto k = time_pass_kernel<T, LOGN, WARPS>;
   if (smem > 48 * 1024)
     BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const long long W = 2 * warps;
   const unsigned grid = (unsigned)((p->J + W - 1) / W);
   BEC_LAUNCH_BEGIN(p);
   k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->J, p->m, p->dim, es, eis,
-                                           lamf, mu1, (T)p->tau, (T)scale, scale_dev, tw);
+                                           lamf, mu1, (T)p->tau, (T)scale, scale_dev, tw, rinv);
   BEC_LAUNCH_CHECK(p, "time_pass_kernel");
   return BEC_OK;
 }
 
+// The block width w (warps per block) is tunable for N >= 32; shorter
+// transforms always use the default.
+template <typename T, int LOGN>
+bec_status time_w(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
+                  const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                  const v2_t<T>* tw, const T* rinv) {
+  if constexpr (LOGN >= 5) {
+    if (w == 4) return time_launch<T, LOGN, 4>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
+    if (w == 8) return time_launch<T, LOGN, 8>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
+    if (w == 16) return time_launch<T, LOGN, 16>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
+  }
+  return time_launch<T, LOGN, time_warps<T>()>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw,
+                                                rinv);
+}
+
 template <typename T>
-bec_status time_dispatch(bec_problem* p, void* data, double scale, const double* scale_dev,
+bec_status time_dispatch(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
                          const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
-                         const v2_t<T>* tw) {
+                         const v2_t<T>* tw, const T* rinv) {
   switch (p->tab.time.logn) {
 #define BEC_TIME_CASE(L) \
-  case L: return time_launch<T, L>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw);
+  case L: return time_w<T, L>(p, w, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
     BEC_TIME_CASE(1) BEC_TIME_CASE(2) BEC_TIME_CASE(3) BEC_TIME_CASE(4) BEC_TIME_CASE(5)
     BEC_TIME_CASE(6) BEC_TIME_CASE(7) BEC_TIME_CASE(8) BEC_TIME_CASE(9) BEC_TIME_CASE(10)
 #undef BEC_TIME_CASE
@@ -154,10 +191,11 @@ time_fwd_kernel(const double* __restrict__ y, v2_t<T>* __restrict__ spec, long l
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long q0 = (long long)blockIdx.x * W;
   const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
+#pragma unroll 4
   for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const long long q = q0 + c;
-    sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] = q < J ? (T)y[(long long)j * J + q] * es[j] : T(0);
+    sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] = q < J ? convert<T>(y[(long long)j * J + q]) * es[j] : T(0);
   }
   __syncthreads();
   V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
@@ -169,6 +207,7 @@ time_fwd_kernel(const double* __restrict__ y, v2_t<T>* __restrict__ spec, long l
     out[k * W + 2 * warp + 1] = {(C.y + Cn.y) * half, (Cn.x - C.x) * half};
   }
   __syncthreads();
+#pragma unroll 4
   for (int e = threadIdx.x; e < NK * W; e += WARPS * 32) {
     const int k = e / W, c = e % W;
     const long long q = q0 + c;
@@ -194,6 +233,7 @@ time_inv_kernel(const v2_t<T>* __restrict__ spec, double* __restrict__ z, long l
   V* in = reinterpret_cast<V*>(sm + (size_t)WARPS * 2 * LSC);    // [NK][W]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long q0 = (long long)blockIdx.x * W;
+#pragma unroll 4
   for (int e = threadIdx.x; e < NK * W; e += WARPS * 32) {
     const int k = e / W, c = e % W;
     const long long q = q0 + c;
@@ -215,11 +255,12 @@ time_inv_kernel(const v2_t<T>* __restrict__ spec, double* __restrict__ z, long l
   __syncwarp();
   warp_fft<T, +1, LOGN>(line, tw, lane);
   __syncthreads();
+#pragma unroll 4
   for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
     const int j = e / W, c = e % W;
     const long long q = q0 + c;
     if (q < J)
-      z[(long long)j * J + q] = (double)(sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] * eis[j] * scale);
+      z[(long long)j * J + q] = convert<double>(sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] * eis[j] * scale);
   }
 }
 
@@ -307,14 +348,28 @@ bec_status launch_time_inv(bec_problem* p, const void* spec, double* z, int fp64
   return BEC_EUNSUPPORTED;
 }
 
-bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
-                            const double* scale_dev) {
+bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale,
+                              const double* scale_dev, int w) {
   const PcTables& t = p->tab;
   if (fp64)
-    return time_dispatch<double>(p, data, scale, scale_dev, t.es64, t.eis64, t.lamf64, t.mu64,
-                                 t.time.tw64);
-  return time_dispatch<float>(p, data, scale, scale_dev, t.es32, t.eis32, t.lamf32, t.mu32,
-                              t.time.tw32);
+    return time_dispatch<double>(p, w, data, scale, scale_dev, t.es64, t.eis64, t.lamf64, t.mu64,
+                                 t.time.tw64, t.rinv64);
+  return time_dispatch<float>(p, w, data, scale, scale_dev, t.es32, t.eis32, t.lamf32, t.mu32,
+                              t.time.tw32, nullptr);
+}
+
+bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
+                            const double* scale_dev) {
+  return launch_time_pass_w(p, data, fp64, scale, scale_dev, p->tile.time);
+}
+
+bec_status launch_rinv_table(bec_problem* p) {
+  const long long total = p->J * (long long)(p->N / 2 + 1);
+  BEC_LAUNCH_BEGIN(p);
+  rinv_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, p->stream>>>(
+      p->tab.rinv64, p->J, p->N / 2 + 1, p->m, p->dim, p->tab.lamf64, p->tab.mu64, p->tau);
+  BEC_LAUNCH_CHECK(p, "rinv_table_kernel");
+  return BEC_OK;
 }
 
 }  // namespace bec
