@@ -1,26 +1,33 @@
-// 3 x 3 convolution with 32 input and 32 output channels on the 5th-generation
-// tensor cores (tcgen05), BF16 operands, FP32 accumulation in tensor memory:
-// the hot layers of the learned correction's network (7 of its 9 layers).
+// 3 x 3 convolutions of the learned correction's network on the 5th-generation
+// tensor cores (tcgen05): BF16 operands, FP32 accumulation in tensor memory,
+// all 9 layers (C_in in {16, 32}: the 5 input planes are padded to 16; C_out
+// in {16, 32}: the 2 output planes are computed as 16 and 2 are stored).
 //
-// Implicit GEMM.  One tile is 8 x 16 output pixels of one image = the MMA's
-// M = 128 rows; N = 32 output channels; K = 9 taps x 32 input channels, issued
-// as 9 x 2 MMAs of K = 16.  For tap (dy, dx) the A operand is the input box
-// shifted by (dy, dx): TMA loads it from the NHWC activation (channels
-// innermost, 64 bytes per pixel) with the 64-byte swizzle, and the tensor
-// map's out-of-range fill supplies the zero padding at the borders.  The B
-// operand (the weights of all taps, [tap][c_out][c_in]) is loaded once per
-// CTA by TMA with the same swizzle.  Both operands are K-major, so the shared
-// memory descriptors describe rows of 64 bytes in 8-row swizzle atoms
-// (stride 512 bytes), the second K-step starting 32 bytes into the row.
+// Implicit GEMM on halo tiles.  A tile is 8 rows x 14 columns of output
+// pixels of one image.  Its input halo, 10 rows x 16 columns of C_in
+// channels, is loaded once by TMA as C_in/8 chunks of 8 channels, each chunk
+// [10][16] pixels x 16 bytes; the tensor map's out-of-range fill supplies the
+// zero padding at the borders.  The MMA's M = 128 rows are the 8 x 16 pixels
+// (ty, tx) of the tile; for tap (dy, dx) row (ty, tx) reads halo pixel
+// (ty + dy, tx + dx), so each tap's A operand is the same K-major,
+// non-swizzled layout shifted by (16 dy + dx) x 16 bytes: 8-row core
+// matrices of 16-byte rows, 128 bytes apart along M (SBO), the chunk size
+// apart along K (LBO).  Rows tx = 14, 15 read past the tile and are dropped.
+// K = 9 taps x C_in, issued as 9 x C_in/16 MMAs of K = 16; N = C_out.  The
+// weights of all taps ([tap][chunk][c_out][8 c_in], the same layout) are
+// copied once per CTA by a bulk copy.
 //
-// The CTA is persistent over tiles: while the epilogue of tile t reads the
-// accumulator from tensor memory (tcgen05.ld), applies ReLU and stores BF16,
-// the loads of tile t + grid are already in flight.  Two CTAs share an SM.
+// Warp roles in a persistent CTA: warp 4 issues the TMA loads into a 4-stage
+// ring, warp 5 issues the MMAs into one of two tensor-memory accumulators,
+// warps 0-3 (tensor-memory lanes 0-127) read an accumulator back with
+// tcgen05.ld, apply ReLU, convert to BF16 and store.  Loads, MMAs and the
+// epilogue of different tiles overlap.
 //
-// Every wait is bounded (about 0.2 s of SM clock); a wait that runs
-// out sets *err, every thread leaves the tile loop at the next CTA barrier,
-// the CTA waits (bounded) for its copies and MMAs in flight, frees its
-// tensor memory and returns.
+// Every wait is bounded (about 0.2 s of SM clock).  A wait that runs out
+// sets *err and the CTA's abort flag; every role leaves its loop, the CTA
+// waits (bounded) for its copies and MMAs in flight, frees its tensor memory
+// and returns.  The shared-memory allocation keeps 48 KB beyond the
+// operands, more than any reading of the descriptors' two strides can reach.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,21 +40,34 @@
 namespace bec {
 namespace {
 
-constexpr int kTileX = 16, kTileY = 8;             // 128 output pixels
-constexpr int kC = 32;                             // channels in and out
-constexpr int kTaps = 9;
-constexpr int kABytes = kTileX * kTileY * kC * 2;  // 8192 per tap
-constexpr int kBBytes = kC * kC * 2;               // 2048 per tap
-constexpr int kSmemBytes = kTaps * (kABytes + kBBytes) + 1024 + 64;
-constexpr int kThreads = 128;
+constexpr int kTileX = 14, kTileY = 8;             // valid output pixels of a tile
+constexpr int kHaloX = 16, kHaloY = 10;            // input halo (one MMA row per halo column)
+constexpr int kChunkBytes = 2688;                  // 168 pixels x 16 B (162 reachable)
+constexpr int kStages = 4;
+constexpr int kThreads = 192;                      // warps 0-3 epilogue, 4 TMA, 5 MMA
+constexpr int kSlack = 48 * 1024;
 constexpr long long kSpinCycles = 400000000LL;     // ~0.2 s at 2 GHz
-constexpr uint32_t kTmemCols = 32;
+constexpr int kNetLayers = 9;
 
-// instruction descriptor of tcgen05.mma kind::f16: D F32 (bits 4-5 = 1),
-// A and B BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
-                            ((uint32_t)(128 >> 4) << 24);
+template <int CIN, int COUT>
+struct Cfg {
+  static constexpr int NCH = CIN / 8;                          // K chunks
+  static constexpr int kStageBytes = NCH * kChunkBytes;
+  static constexpr int kWBytes = 9 * NCH * COUT * 16;
+  static constexpr int kSmem = 1024 + kWBytes + kStages * kStageBytes + 256 + kSlack;
+  static constexpr uint32_t kTmemCols = 2 * COUT < 32 ? 32 : 2 * COUT;
+  // instruction descriptor (kind::f16): D F32, A and B BF16, K-major, N, M = 128
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                     ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+};
+
+// BF16 elements of each layer's converted weights and their offsets
+__host__ __device__ constexpr int layer_wt_elems(int l) {
+  return l == 0 ? 9 * 2 * 32 * 8 : (l == 8 ? 9 * 4 * 16 * 8 : 9 * 4 * 32 * 8);
+}
+__host__ __device__ constexpr int layer_wt_offset(int l) {
+  return l == 0 ? 0 : layer_wt_elems(0) + (l - 1) * layer_wt_elems(1);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -62,8 +82,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-// Waits for the phase of parity ph; false when it ran out or another thread
-// of the CTA gave up (*abort).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Waits for the phase of parity ph; false when it ran out or the CTA is
+// aborting (*abort).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t ph, volatile int* abort) {
   const long long t0 = clock64();
   while (true) {
@@ -90,33 +114,33 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint32_t bar) {
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
-// shared memory descriptor: K-major, 64-byte swizzle, 8-row atoms 512 bytes
-// apart (SBO); LBO is not used by swizzled K-major layouts (set to 1);
-// bits 46-48 hold the fixed value 0b001; swizzle mode 4 = 64 bytes.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+// shared memory descriptor, K-major without swizzle: LBO = stride between
+// core matrices along K, SBO = stride between 8-row groups along M/N; bits
+// 46-48 hold the fixed value 0b001; swizzle mode 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)4 << 61;
   return d;
 }
 
+template <uint32_t IDESC>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
       : "memory");
 }
 
@@ -133,23 +157,36 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32 columns of FP32 from tensor memory: thread t of the warp gets
-// row (lane base + t), columns col .. col + 31.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+// COUT columns of FP32 from tensor memory: thread t of the warp gets row
+// (lane base + t), columns col .. col + COUT - 1.
+template <int COUT>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[COUT]) {
+  uint32_t r[COUT];
+  if constexpr (COUT == 32) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+  } else {
+    static_assert(COUT == 16, "C_out 16 or 32");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  }
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < COUT; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 struct TileCoord {
@@ -166,44 +203,47 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_im
   return c;
 }
 
-__device__ __forceinline__ void issue_tile(const CUtensorMap* in_map, uint32_t sA, uint32_t bar,
-                                           TileCoord c) {
-  mbar_expect_tx(bar, kTaps * kABytes);
-#pragma unroll 1
-  for (int tap = 0; tap < kTaps; ++tap) {
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    tma_load_4d(sA + tap * kABytes, in_map, 0, c.x0 + dx, c.y0 + dy, c.img, bar);
-  }
-}
-
+// out[img][y][x][0 .. STORE_C) = act(conv(in)), act = ReLU when RELU
+template <int CIN, int COUT, int STORE_C, bool RELU>
 __global__ void __launch_bounds__(kThreads, 2)
-conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map,
-                  const __grid_constant__ CUtensorMap w_map, int layer,
+conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16* __restrict__ wt,
                   __nv_bfloat16* __restrict__ out, int m, int tiles_x, int tiles_img, int ntiles,
-                  int relu, int* __restrict__ err) {
+                  int* __restrict__ err) {
+  using C = Cfg<CIN, COUT>;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const uint32_t sA = smem_u32(base);
-  const uint32_t sB = sA + kTaps * kABytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTaps * (kABytes + kBBytes));
-  const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]),
-                 bar_w = smem_u32(&bars[2]);
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const uint32_t sB = smem_u32(base);
+  const uint32_t sA = sB + C::kWBytes;                        // stage s at sA + s * kStageBytes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kWBytes + kStages * C::kStageBytes);
+  // bars: full[4], empty[4], tfull[2], tempty[2], weights
+  const uint32_t b0 = smem_u32(bars);
+  auto full = [&](int s) { return b0 + 8u * s; };
+  auto empty = [&](int s) { return b0 + 8u * (kStages + s); };
+  auto tfull = [&](int a) { return b0 + 8u * (2 * kStages + a); };
+  auto tempty = [&](int a) { return b0 + 8u * (2 * kStages + 2 + a); };
+  const uint32_t wbar = b0 + 8u * (2 * kStages + 4);
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    mbar_init(bar_ld, 1);
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_w, 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull(a), 1);
+      mbar_init(tempty(a), 4);                                // one arrival per epilogue warp
+    }
+    mbar_init(wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(C::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -212,103 +252,160 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map,
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  int t = blockIdx.x;
-  bool pending_ld = false;   // a tile's loads were issued and not yet waited for
-  bool pending_mma = false;  // MMAs were committed and not yet waited for
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(bar_w, kTaps * kBBytes);
-    tma_load_3d(sB, &w_map, 0, 0, layer * kTaps, bar_w);
-    if (t < ntiles) {
-      issue_tile(&in_map, sA, bar_ld, tile_coord(t, tiles_x, tiles_img));
-      pending_ld = true;
-    }
-    if (!mbar_wait(bar_w, 0, &abort_flag)) abort_flag = 1;
-  }
-  uint32_t ph = 0;
-  bool failed = false;
-  for (; t < ntiles; t += gridDim.x) {
-    if (threadIdx.x == 0 && !abort_flag) {
-      if (mbar_wait(bar_ld, ph, &abort_flag)) {
-        pending_ld = false;
-        fence_after();
-#pragma unroll 1
-        for (int tap = 0; tap < kTaps; ++tap) {
+  // what each role has in flight when it stops (waited for on an abort)
+  int issued_ld = 0;                      // producer: tiles whose loads were issued
+  bool mma_pending = false;
+  int last_acc = 0;
+  uint32_t last_ph = 0;
+
+  if (warp == 4) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      mbar_expect_tx(wbar, C::kWBytes);
+      bulk_load(sB, wt, C::kWBytes, wbar);
+      int i = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages;
+        if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        const TileCoord c = tile_coord(t, tiles_x, tiles_img);
+        const uint32_t dst = sA + s * C::kStageBytes;
+        mbar_expect_tx(full(s), C::NCH * (kHaloX * kHaloY * 16));
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t off = ks * 32;
-            mma_bf16(tmem, sdesc(sA + tap * kABytes + off), sdesc(sB + tap * kBBytes + off),
-                     (tap | ks) != 0);
+        for (int ch = 0; ch < C::NCH; ++ch)
+          tma_load_4d(dst + ch * kChunkBytes, &in_map, 8 * ch, c.x0 - 1, c.y0 - 1, c.img, full(s));
+        issued_ld = i + 1;
+      }
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      bool ok = mbar_wait(wbar, 0, &abort_flag);
+      int i = 0;
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages, acc = i & 1;
+        if (!mbar_wait(full(s), (i / kStages) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        if (i >= 2 && !mbar_wait(tempty(acc), ((i >> 1) - 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = sA + s * C::kStageBytes;
+        const uint32_t d = tmem + acc * COUT;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t shift = (uint32_t)((tap / 3) * kHaloX + (tap % 3)) * 16u;
+#pragma unroll
+          for (int ks = 0; ks < CIN / 16; ++ks) {
+            const uint64_t ad = sdesc(a0 + 2 * ks * kChunkBytes + shift, kChunkBytes, 128);
+            const uint64_t bd = sdesc(sB + (tap * C::NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
+            mma_bf16<C::kIdesc>(d, ad, bd, (tap | ks) != 0);
           }
         }
-        mma_commit(bar_mma);
-        pending_mma = true;
-      } else {
+        mma_commit(empty(s));
+        mma_commit(tfull(acc));
+        mma_pending = true;
+        last_acc = acc;
+        last_ph = (i >> 1) & 1;
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int acc = i & 1;
+      if (!mbar_wait(tfull(acc), (i >> 1) & 1, &abort_flag)) {
         abort_flag = 1;
+        break;
       }
-    }
-    const bool ok = mbar_wait(bar_mma, ph, &abort_flag);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    pending_mma = false;
-    fence_after();
-    const int tn = t + gridDim.x;
-    if (threadIdx.x == 0 && tn < ntiles) {
-      issue_tile(&in_map, sA, bar_ld, tile_coord(tn, tiles_x, tiles_img));
-      pending_ld = true;
-    }
-    // epilogue: row 32 warp + lane of the accumulator = tile pixel
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-    const TileCoord c = tile_coord(t, tiles_x, tiles_img);
-    const int row = 32 * warp + lane;
-    const int y = c.y0 + row / kTileX, x = c.x0 + row % kTileX;
-    if (y < m && x < m) {
-      uint4 pk[4];
-      uint32_t* w32 = reinterpret_cast<uint32_t*>(pk);
+      fence_after();
+      float v[COUT];
+      tmem_ld<COUT>(tmem + acc * COUT + ((uint32_t)(32 * warp) << 16), v);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
+      const TileCoord c = tile_coord(t, tiles_x, tiles_img);
+      const int row = 32 * warp + lane;
+      const int tx = row % kHaloX, ty = row / kHaloX;
+      const int x = c.x0 + tx, y = c.y0 + ty;
+      if (tx < kTileX && x < m && y < m) {
+        __nv_bfloat16* dst = out + (((long long)c.img * m + y) * m + x) * STORE_C;
+        if constexpr (STORE_C % 8 == 0) {
+          uint4 pk[STORE_C / 8];
+          uint32_t* w32 = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float a = v[2 * i], b = v[2 * i + 1];
-        if (relu) {
-          a = fmaxf(a, 0.f);
-          b = fmaxf(b, 0.f);
+          for (int k = 0; k < STORE_C / 2; ++k) {
+            float a = v[2 * k], b = v[2 * k + 1];
+            if (RELU) {
+              a = fmaxf(a, 0.f);
+              b = fmaxf(b, 0.f);
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            w32[k] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+#pragma unroll
+          for (int k = 0; k < STORE_C / 8; ++k) reinterpret_cast<uint4*>(dst)[k] = pk[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < STORE_C; ++k)
+            dst[k] = __float2bfloat16(RELU ? fmaxf(v[k], 0.f) : v[k]);
         }
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        w32[i] = *reinterpret_cast<const uint32_t*>(&h);
       }
-      uint4* dst = reinterpret_cast<uint4*>(out + (((long long)c.img * m + y) * m + x) * kC);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) dst[i] = pk[i];
     }
-    fence_before();
-    __syncthreads();
-    ph ^= 1;
   }
-  if (failed && threadIdx.x == 0) {
-    atomicExch(err, 1);
-    // let copies and MMAs in flight land before the shared and tensor memory
-    // are released (bounded again)
+
+  // ------------------------------------------------------------- teardown
+  __syncthreads();
+  if (abort_flag) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
     volatile int never = 0;
-    if (pending_ld) mbar_wait(bar_ld, ph, &never);
-    if (pending_mma) mbar_wait(bar_mma, ph, &never);
+    // let copies and MMAs in flight land before the memory is released: each
+    // stage has at most one load outstanding, the latest one issued into it
+    // (a completed phase passes the parity wait at once)
+    if (warp == 4 && lane == 0)
+      for (int i = issued_ld > kStages ? issued_ld - kStages : 0; i < issued_ld; ++i)
+        mbar_wait(full(i % kStages), (i / kStages) & 1, &never);
+    if (warp == 5 && lane == 0 && mma_pending) mbar_wait(tfull(last_acc), last_ph, &never);
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0)
+  if (warp == 5)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
+                 "r"(C::kTmemCols)
                  : "memory");
 }
 
-// wt[l][tap][co][ci] = bf16(W[l][tap][ci][co]) for the 32 -> 32 layers
-__global__ void tc_weights_kernel(const float* __restrict__ W, __nv_bfloat16* __restrict__ wt,
-                                  int nlayers) {
+// Converted weights of all 9 layers in the operand layout
+// wt_l[tap][chunk][c_out][8 c_in] (BF16), zero where a padded channel has no
+// weight: layer 0 has 5 of its 16 input channels, layer 8 2 of its 16
+// outputs.  W holds the FP32 master weights [tap][c_in][c_out] of all layers.
+struct LayerOffsets {
+  long long o[kNetLayers];
+};
+
+__global__ void tc_weights_kernel(const float* __restrict__ W, LayerOffsets woff,
+                                  __nv_bfloat16* __restrict__ wt) {
+  const int total = layer_wt_offset(kNetLayers - 1) + layer_wt_elems(kNetLayers - 1);
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nlayers * kTaps * kC * kC) return;
-  const int ci = g % kC, co = (g / kC) % kC, lt = g / (kC * kC);
-  wt[g] = __float2bfloat16(W[(long long)lt * kC * kC + ci * kC + co]);
+  if (g >= total) return;
+  int l = 0;
+  while (l + 1 < kNetLayers && g >= layer_wt_offset(l + 1)) ++l;
+  const int cin_pad = l == 0 ? 16 : 32, cout_pad = l == 8 ? 16 : 32;
+  const int cin = l == 0 ? 5 : 32, cout = l == 8 ? 2 : 32;
+  const int e = g - layer_wt_offset(l);
+  const int j = e % 8, co = (e / 8) % cout_pad, ch = (e / (8 * cout_pad)) % (cin_pad / 8),
+            tap = e / (8 * cout_pad * (cin_pad / 8));
+  const int ci = ch * 8 + j;
+  const float v =
+      (ci < cin && co < cout) ? W[woff.o[l] + ((long long)tap * cin + ci) * cout + co] : 0.f;
+  wt[g] = __float2bfloat16(v);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -328,63 +425,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-}  // namespace
-
-bool tc_conv_supported() {
-  int dev = 0, major = 0, minor = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  return major == 10 && minor == 3 && encode_fn() != nullptr;
-}
-
-bec_status tc_convert_weights(bec_problem* p, const float* W_first, int nlayers,
-                              __nv_bfloat16* wt) {
-  const int n = nlayers * kTaps * kC * kC;
-  BEC_LAUNCH_BEGIN(p);
-  tc_weights_kernel<<<(n + 255) / 256, 256, 0, p->stream>>>(W_first, wt, nlayers);
-  BEC_LAUNCH_CHECK(p, "net_tc_weights_kernel");
-  return BEC_OK;
-}
-
-bec_status tc_conv3x3(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat16* wt,
-                      int nlayers, int layer, __nv_bfloat16* out, int m, int B, int bmax, bool relu,
-                      int* err) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (enc == nullptr || m < kTileX || B < 1 || B > bmax || layer < 0 || layer >= nlayers) {
-    set_error("tensor-core convolution: unsupported request");
-    return BEC_EUNSUPPORTED;
+template <int CIN, int COUT, int STORE_C, bool RELU>
+bec_status launch_tc(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat16* wt,
+                     __nv_bfloat16* out, int m, int B, int bmax, int* err) {
+  using C = Cfg<CIN, COUT>;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)bmax};
+  const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)CIN * 2 * m,
+                                 (cuuint64_t)CIN * 2 * m * m};
+  const cuuint32_t box[4] = {8, kHaloX, kHaloY, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (activations)");
+    return BEC_ECUDA;
   }
-  alignas(64) CUtensorMap in_map, w_map;
-  {
-    const cuuint64_t dims[4] = {(cuuint64_t)kC, (cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)bmax};
-    const cuuint64_t strides[3] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * 2 * m,
-                                   (cuuint64_t)kC * 2 * m * m};
-    const cuuint32_t box[4] = {(cuuint32_t)kC, kTileX, kTileY, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(&in_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in), dims,
-            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-      set_error("cuTensorMapEncodeTiled (activations)");
-      return BEC_ECUDA;
-    }
-  }
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kC, (cuuint64_t)kC, (cuuint64_t)nlayers * kTaps};
-    const cuuint64_t strides[2] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * kC * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kC, (cuuint32_t)kC, (cuuint32_t)kTaps};
-    const cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&w_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(wt), dims,
-            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-      set_error("cuTensorMapEncodeTiled (weights)");
-      return BEC_ECUDA;
-    }
-  }
+  auto k = conv3x3_tc_kernel<CIN, COUT, STORE_C, RELU>;
   static bool attr_set = false;
   if (!attr_set) {
-    BEC_CUDA_TRY(cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmemBytes));
+    BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
     attr_set = true;
   }
   int dev = 0, sms = 0;
@@ -395,10 +456,44 @@ bec_status tc_conv3x3(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat
   const int ntiles = tiles_img * B;
   const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
   BEC_LAUNCH_BEGIN(p);
-  conv3x3_tc_kernel<<<grid, kThreads, kSmemBytes, p->stream>>>(
-      in_map, w_map, layer, out, m, tiles_x, tiles_img, ntiles, relu ? 1 : 0, err);
+  k<<<grid, kThreads, C::kSmem, p->stream>>>(map, wt, out, m, tiles_x, tiles_img, ntiles, err);
   BEC_LAUNCH_CHECK(p, "net_conv_tc_kernel");
   return BEC_OK;
+}
+
+}  // namespace
+
+int tc_weights_elems() { return layer_wt_offset(kNetLayers - 1) + layer_wt_elems(kNetLayers - 1); }
+
+bool tc_conv_supported() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* woff,
+                              __nv_bfloat16* wt) {
+  const int n = tc_weights_elems();
+  LayerOffsets o;
+  for (int l = 0; l < kNetLayers; ++l) o.o[l] = woff[l];
+  BEC_LAUNCH_BEGIN(p);
+  tc_weights_kernel<<<(n + 255) / 256, 256, 0, p->stream>>>(W, o, wt);
+  BEC_LAUNCH_CHECK(p, "net_tc_weights_kernel");
+  return BEC_OK;
+}
+
+bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
+                      __nv_bfloat16* out, int m, int B, int bmax, int* err) {
+  if (encode_fn() == nullptr || B < 1 || B > bmax || m < 1 || layer < 0 || layer >= kNetLayers) {
+    set_error("tensor-core convolution: unsupported request");
+    return BEC_EUNSUPPORTED;
+  }
+  const __nv_bfloat16* w = wt + layer_wt_offset(layer);
+  if (layer == 0) return launch_tc<16, 32, 32, true>(p, in, w, out, m, B, bmax, err);
+  if (layer == 8) return launch_tc<32, 16, 2, false>(p, in, w, out, m, B, bmax, err);
+  return launch_tc<32, 32, 32, true>(p, in, w, out, m, B, bmax, err);
 }
 
 }  // namespace bec

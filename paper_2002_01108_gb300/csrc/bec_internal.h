@@ -254,15 +254,19 @@ long long net_fallbacks(bec_problem* p);
 // network's kernels ran out since the last check; synchronises.
 bec_status net_check(bec_problem* p);
 
-// ---- tensor-core convolution (bec_conv_tc.cu): 3 x 3, 32 -> 32 channels,
-// BF16 NHWC activations, tcgen05 MMA with TMA-staged operands
+// ---- tensor-core convolutions (bec_conv_tc.cu): every layer of the network,
+// BF16 NHWC activations, tcgen05 MMA with TMA-staged halo tiles
 bool tc_conv_supported();
-// wt[l][tap][co][ci] (BF16) from the FP32 weights [l][tap][ci][co] of nlayers layers
-bec_status tc_convert_weights(bec_problem* p, const float* W_first, int nlayers,
+// BF16 elements of the converted weights of all 9 layers
+int tc_weights_elems();
+// the operand layout of every layer from the FP32 master weights W (layer l
+// at W + woff[l], [tap][c_in][c_out]); host array woff of 9 offsets
+bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* woff,
                               __nv_bfloat16* wt);
-bec_status tc_conv3x3(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat16* wt,
-                      int nlayers, int layer, __nv_bfloat16* out, int m, int B, int bmax,
-                      bool relu, int* err);
+// out = act(conv3x3(in)) of layer l: l = 0 reads the 16-channel padded
+// input planes, l = 8 stores its 2 output channels, ReLU except for l = 8
+bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
+                      __nv_bfloat16* out, int m, int B, int bmax, int* err);
 bec_status net_residual_ratios(bec_problem* p, double* host);
 
 // ---- stencils (bec_stencil.cu)

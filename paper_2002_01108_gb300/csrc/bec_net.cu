@@ -78,8 +78,9 @@ struct NetState {
   double* h_part = nullptr;      // pinned mirror
   int adam_t = 0;
   unsigned long long rng_ctr = 0;
-  bool tc = false;               // 32 -> 32 layers on the tensor cores (BF16, C = 32)
-  __nv_bfloat16* wt = nullptr;   // BF16 weights of layers 1..7, [l][tap][co][ci]
+  bool tc = false;               // every layer on the tensor cores (BF16, C = 32)
+  __nv_bfloat16* wt = nullptr;   // BF16 weights of all layers in the operand layout
+  __nv_bfloat16* x16 = nullptr;  // input planes padded to 16 channels (tensor-core layer 0)
   int* err = nullptr;            // set by a device wait that ran out
 };
 
@@ -136,11 +137,13 @@ __global__ void feat_scale_kernel(const float2* __restrict__ rc, const int* __re
 }
 
 // X[b][q] = (Re rc / s, Im rc / s, log a, Re lambda', Im lambda')
+// (and, when X16 is not null, the same planes padded with zeros to 16 BF16
+// channels: the input of the tensor-core layer 0)
 template <typename AT>
 __global__ void feat_fill_kernel(const float2* __restrict__ rc, const float* __restrict__ sinv,
                                  const float* __restrict__ la_c, const int* __restrict__ lam,
-                                 const float2* __restrict__ lamf, AT* __restrict__ X, long long mcc,
-                                 int B) {
+                                 const float2* __restrict__ lamf, AT* __restrict__ X,
+                                 __nv_bfloat16* __restrict__ X16, long long mcc, int B) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= B * mcc) return;
   const int b = (int)(g / mcc);
@@ -148,12 +151,23 @@ __global__ void feat_fill_kernel(const float2* __restrict__ rc, const float* __r
   const float2 v = rc[g];
   const float si = sinv[b];
   const float2 L = lamf[lam[b]];
+  const float f[5] = {v.x * si, v.y * si, la_c[q], L.x, L.y};
   AT* d = X + g * 5;
-  d[0] = net::st<AT>(v.x * si);
-  d[1] = net::st<AT>(v.y * si);
-  d[2] = net::st<AT>(la_c[q]);
-  d[3] = net::st<AT>(L.x);
-  d[4] = net::st<AT>(L.y);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) d[c] = net::st<AT>(f[c]);
+  if (X16 != nullptr) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(f[0], f[1]);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(f[2], f[3]);
+    const __nv_bfloat162 h4 = __floats2bfloat162_rn(f[4], 0.f);
+    uint4 lo;
+    lo.x = *reinterpret_cast<const unsigned*>(&h01);
+    lo.y = *reinterpret_cast<const unsigned*>(&h23);
+    lo.z = *reinterpret_cast<const unsigned*>(&h4);
+    lo.w = 0u;
+    uint4* d16 = reinterpret_cast<uint4*>(X16 + g * 16);
+    d16[0] = lo;
+    d16[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 // efine[b][f] = P_0 (cfac_b (y0 + i y1)) at fine node f
@@ -347,9 +361,12 @@ bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m,
   const AT* a = static_cast<const AT*>(in);
   AT* o = static_cast<AT*>(out);
   if constexpr (sizeof(AT) == 2) {
-    if (n.tc && ci == 32 && co == 32 && m >= 16)
-      return tc_conv3x3(p, reinterpret_cast<const __nv_bfloat16*>(a), n.wt, 7, layer - 1,
-                        reinterpret_cast<__nv_bfloat16*>(o), m, B, n.Bmax, relu, n.err);
+    if (n.tc) {   // every layer (layer 0 reads the 16-channel padded planes)
+      const __nv_bfloat16* src =
+          layer == 0 ? n.x16 : reinterpret_cast<const __nv_bfloat16*>(a);
+      return tc_conv3x3(p, layer, src, n.wt, reinterpret_cast<__nv_bfloat16*>(o), m, B, n.Bmax,
+                        n.err);
+    }
   }
   BEC_LAUNCH_BEGIN(p);
 #define BEC_CF(CI, CO)                                                                            \
@@ -482,7 +499,7 @@ bec_status features(bec_problem* p, int B) {
   BEC_LAUNCH_BEGIN(p);
   feat_fill_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
       reinterpret_cast<const float2*>(n.rc), n.sinv, n.la_c, n.cur_lam, lamf,
-      static_cast<AT*>(n.act[A_X]), mcc, B);
+      static_cast<AT*>(n.act[A_X]), (sizeof(AT) == 2 && n.tc) ? n.x16 : nullptr, mcc, B);
   BEC_LAUNCH_CHECK(p, "net_feat_fill_kernel");
   return BEC_OK;
 }
@@ -491,7 +508,7 @@ template <typename AT>
 bec_status forward(bec_problem* p, int B) {
   NetState& n = *p->net;
   void** a = n.act;
-  if (sizeof(AT) == 2 && n.tc) BEC_TRY(tc_convert_weights(p, n.W + n.woff[1], 7, n.wt));
+  if (sizeof(AT) == 2 && n.tc) BEC_TRY(tc_convert_weights(p, n.W, n.woff, n.wt));
   BEC_TRY(conv_fwd<AT>(p, a[A_X], 0, a[A_H0], n.sz[0], B, true));
   BEC_TRY(conv_fwd<AT>(p, a[A_H0], 1, a[A_S0], n.sz[0], B, true));
   BEC_TRY(restrict_ch<AT>(p, a[A_S0], a[A_R0], 0, B, 1.f, false));
@@ -767,7 +784,11 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->err), sizeof(int)));
   n->tc = !n->fp32 && C == 32 && tc_conv_supported();
-  if (n->tc) chain(dalloc(reinterpret_cast<void**>(&n->wt), 7 * 9 * 32 * 32 * sizeof(__nv_bfloat16)));
+  if (n->tc) {
+    chain(dalloc(reinterpret_cast<void**>(&n->wt), (size_t)tc_weights_elems() * sizeof(__nv_bfloat16)));
+    chain(dalloc(reinterpret_cast<void**>(&n->x16),
+                 (size_t)bmax * n->sz[0] * n->sz[0] * 16 * sizeof(__nv_bfloat16)));
+  }
   if (s == BEC_OK) {
     if (cudaMallocHost(reinterpret_cast<void**>(&n->h_idx), 2 * bmax * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&n->h_part), (5 * K + 2 * bmax + 2) * sizeof(double)) != cudaSuccess) {
@@ -821,7 +842,7 @@ void net_free(bec_problem* p) {
   if (n == nullptr) return;
   void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->la_c, n->rc, n->sinv, n->cfac, n->row,
                   n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part,
-                  n->err, n->wt};
+                  n->err, n->wt, n->x16};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int a = 0; a < NACT; ++a) {
