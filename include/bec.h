@@ -81,9 +81,10 @@ enum {
 };
 
 typedef struct {
-  int dim;             /* 1 or 2 */
+  int dim;             /* 1, 2 or 3 (the unit interval, square or cube) */
   int nx, ny;          /* interior points per side (h = 1/(nx+1)); ny must
-                          equal nx for dim 2 and is ignored for dim 1.
+                          equal nx for dim 2 and 3 (the cube has nx points
+                          along z too) and is ignored for dim 1.
                           nx + 1 must be a power of two in [4, 1024]. */
   int N;               /* time steps; a power of two in [2, 1024] */
   double T;            /* final time, tau = T / N */
@@ -106,7 +107,15 @@ typedef struct {
   int net_channels;      /* BEC_ROUTE_LEARNED: channels (4 or 32; 0 selects 32) */
   int net_fp32;          /* BEC_ROUTE_LEARNED: nonzero keeps activations in FP32
                             (used to check gradients); default BF16 */
+  int space;             /* spatial discretisation: BEC_SPACE_FD (0, M = I and
+                            the 3- or 5-point K) or BEC_SPACE_Q1 (linear / bilinear
+                            finite elements on the uniform mesh, Sec. 5 Example
+                            1: M = M1 (x) M1, K = a (M1 (x) K1 + K1 (x) M1) in 2D,
+                            M1 = h/6 tridiag(1, 4, 1), K1 = 1/h tridiag(-1, 2, -1);
+                            needs BEC_ROUTE_FST) */
 } bec_problem_desc;
+
+enum { BEC_SPACE_FD = 0, BEC_SPACE_Q1 = 1 };
 
 /* Validates desc, allocates the workspace (Krylov basis (max_restart+1) x U
  * doubles, Z when flexible, one U-vector of preconditioner scratch, tables)
@@ -139,8 +148,9 @@ bec_status bec_apply_P(bec_problem* p, const double* v, double* y);
  * Needs bec_set_eps first (else BEC_EINVAL). */
 bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z);
 
-/* f = (tau f^1 + u^0; tau f^2; ...; tau f^N) (Sec. 2).  u0: J doubles,
- * fsrc: U doubles (the source at t_1..t_N), f: U doubles. */
+/* f = (tau f^1 + M u^0; tau f^2; ...; tau f^N) (Sec. 2; M = I for finite
+ * differences).  u0: J doubles, fsrc: U doubles (the source at t_1..t_N, taken
+ * as given: with Q1 elements pass the load vector), f: U doubles. */
 bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc,
                          double* f);
 

@@ -55,12 +55,17 @@ def fd_stiffness_1d(m: int, a: float = 1.0) -> sp.csr_matrix:
 
 
 def fd_stiffness(dim: int, m: int, a: float = 1.0) -> sp.csr_matrix:
-    """5-point (2D) or 3-point (1D) FD Laplacian times a; 2D ordering [ny][nx]."""
+    """3-point (1D), 5-point (2D) or 7-point (3D) FD Laplacian times a on the
+    unit interval, square or cube (the domain of eq. heateq is in R^2 or R^3);
+    ordering [ny][nx] and [nz][ny][nx], x fastest."""
     K1 = fd_stiffness_1d(m, a)
     if dim == 1:
         return K1
     I = sp.identity(m, format="csr")
-    return (sp.kron(I, K1) + sp.kron(K1, I)).tocsr()
+    if dim == 2:
+        return (sp.kron(I, K1) + sp.kron(K1, I)).tocsr()
+    return (sp.kron(sp.kron(I, I), K1) + sp.kron(sp.kron(I, K1), I)
+            + sp.kron(sp.kron(K1, I), I)).tocsr()
 
 
 def fd_stiffness_varcoef(a_nodes: np.ndarray) -> sp.csr_matrix:
@@ -302,7 +307,7 @@ def apply_Pinv_woodbury(y: np.ndarray, M, K, tau: float, eps: float) -> np.ndarr
 
 def _dst_spatial(x: np.ndarray, dim: int) -> np.ndarray:
     """Orthonormal DST-I over the spatial axes of [N][...] data (S is its own inverse)."""
-    axes = (1,) if dim == 1 else (1, 2)
+    axes = tuple(range(1, dim + 1))
     if np.iscomplexobj(x):
         return (sfft.dstn(x.real, type=1, axes=axes, norm="ortho")
                 + 1j * sfft.dstn(x.imag, type=1, axes=axes, norm="ortho"))
@@ -313,15 +318,21 @@ def apply_Pinv_fst(y: np.ndarray, dim: int, a: float, tau: float, eps: float,
                    r=BDF1) -> np.ndarray:
     """z = P_eps^{-1} y for the FD Laplacian with constant a (M = I): the three
     steps of Sec. 4 where every B_k = lambda_k I + tau K is diagonalised by the
-    2D sine transform (remark after eq. zcompt): B_k^{-1} = S diag(1/(lambda_k +
-    tau mu)) S with mu the FD eigenvalues.  All N frequencies are solved."""
+    1D, 2D or 3D sine transform (remark after eq. zcompt): B_k^{-1} = S
+    diag(1/(lambda_k + tau mu)) S with mu the FD eigenvalues (sums of the 1D
+    ones over the axes).  All N frequencies are solved."""
     N = y.shape[0]
     m = y.shape[1]
     d = eps_scaling(N, eps)
     shape_b = (N,) + (1,) * dim
     yt = math.sqrt(N) * np.fft.ifft(d.reshape(shape_b) * y, axis=0)  # Step 1
     mu1 = fd_dst_eigs(m, a)
-    mu = mu1 if dim == 1 else (mu1[:, None] + mu1[None, :])
+    if dim == 1:
+        mu = mu1
+    elif dim == 2:
+        mu = mu1[:, None] + mu1[None, :]
+    else:
+        mu = mu1[:, None, None] + mu1[None, :, None] + mu1[None, None, :]
     lam = eps_circulant_eigs(N, eps, r)
     yh = _dst_spatial(yt, dim)                                         # Step 2
     zh = yh / (lam.reshape(shape_b) + tau * mu[None, ...])

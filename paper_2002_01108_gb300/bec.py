@@ -40,7 +40,8 @@ class ProblemDesc(ctypes.Structure):
                 ("max_restart", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("host_io", ctypes.c_int), ("a_nodes", ctypes.c_void_p),
                 ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("net_channels", ctypes.c_int), ("net_fp32", ctypes.c_int)]
+                ("net_channels", ctypes.c_int), ("net_fp32", ctypes.c_int),
+                ("space", ctypes.c_int)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -193,7 +194,7 @@ class Problem:
                  precision: str = "fp64", max_restart: int = 30, flexible: bool = False,
                  host_io: bool = False, stream=None, route: str = "fst", a_nodes=None,
                  mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0,
-                 net_channels: int = 0, net_fp32: bool = False):
+                 net_channels: int = 0, net_fp32: bool = False, space: str = "fd"):
         import torch
         self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
         self.precision = precision
@@ -205,11 +206,11 @@ class Problem:
                 raise ValueError("a_nodes must hold (nx+2)^2 values")
             a_ptr = self._a_nodes.ctypes.data
         routes = {"fst": BEC_ROUTE_FST, "mg": BEC_ROUTE_MG, "learned": BEC_ROUTE_LEARNED}
-        desc = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, T, a, routes[route],
+        desc = ProblemDesc(dim, nx, nx if dim >= 2 else 1, N, T, a, routes[route],
                            BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
                            max_restart, int(flexible), int(host_io), a_ptr,
                            int(mg_pre), int(mg_post), float(mg_omega), int(net_channels),
-                           int(net_fp32))
+                           int(net_fp32), {"fd": 0, "q1": 1}[space])
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -220,7 +221,7 @@ class Problem:
         self._p = out
         self.U = int(_lib().bec_problem_size(self._p))
         self.J = self.U // N
-        self.shape = (N, nx, nx) if dim == 2 else (N, nx)
+        self.shape = (N,) + (nx,) * dim
 
     # -- lifetime
     def close(self):
@@ -419,12 +420,13 @@ class Batch:
                 self._keep.append(arr)
                 a_ptr = arr.ctypes.data
             dim, nx, N = sp["dim"], sp["nx"], sp["N"]
-            descs[i] = ProblemDesc(dim, nx, nx if dim == 2 else 1, N, sp.get("T", 1.0), sp.get("a", 1.0),
+            descs[i] = ProblemDesc(dim, nx, nx if dim >= 2 else 1, N, sp.get("T", 1.0), sp.get("a", 1.0),
                                    BEC_ROUTE_MG if sp.get("route") == "mg" else BEC_ROUTE_FST,
                                    BEC_PC_FP32 if sp.get("precision", "fp32") == "fp32" else BEC_PC_FP64,
-                                   sp.get("max_restart", 10), int(flexible), 0, a_ptr, 0, 0, 0.0)
+                                   sp.get("max_restart", 10), int(flexible), 0, a_ptr, 0, 0, 0.0,
+                                   0, 0, {"fd": 0, "q1": 1}[sp.get("space", "fd")])
             eps[i] = sp["eps"]
-            self.shapes.append((N, nx, nx) if dim == 2 else (N, nx))
+            self.shapes.append((N,) + (nx,) * dim)
         out = ctypes.c_void_p()
         _check(_lib().bec_batch_create(descs, eps, n, int(nstreams), int(use_graphs), ctypes.byref(out)),
                "bec_batch_create")

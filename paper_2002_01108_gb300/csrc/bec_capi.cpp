@@ -104,8 +104,8 @@ void free_all(bec_problem* p) {
   p->graphs.clear();
   PcTables& t = p->tab;
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
-                  t.mu64, t.mu32, t.es64, t.eis64, t.es32, t.eis32, t.lamf64, t.lamf32,
-                  t.rinv64, p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
+                  t.mu64, t.mu32, t.mum64, t.mum32, t.es64, t.eis64, t.es32, t.eis32,
+                  t.lamf64, t.lamf32, t.rinv64, p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
                   p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -174,10 +174,10 @@ extern "C" {
 bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_problem** out) {
   if (d == nullptr || out == nullptr) return einval("null argument");
   *out = nullptr;
-  if (d->dim != 1 && d->dim != 2) return einval("dim must be 1 or 2");
+  if (d->dim < 1 || d->dim > 3) return einval("dim must be 1, 2 or 3");
   if (!is_pow2((long long)d->nx + 1) || d->nx + 1 < 4 || d->nx + 1 > 1024)
     return einval("nx + 1 must be a power of two in [4, 1024]");
-  if (d->dim == 2 && d->ny != d->nx) return einval("dim 2 needs ny == nx");
+  if (d->dim >= 2 && d->ny != d->nx) return einval("dim 2 and 3 need ny == nx");
   if (!is_pow2(d->N) || d->N < 2 || d->N > 1024)
     return einval("N must be a power of two in [2, 1024]");
   if (!(d->T > 0.0) || !std::isfinite(d->T)) return einval("T must be finite and > 0");
@@ -202,6 +202,11 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     return einval("precision must be BEC_PC_FP64 or BEC_PC_FP32");
   if (d->max_restart < 0 || d->max_restart > kMaxRestart)
     return einval("max_restart must be in [0, 60]");
+  if (d->space != BEC_SPACE_FD && d->space != BEC_SPACE_Q1)
+    return einval("space must be BEC_SPACE_FD or BEC_SPACE_Q1");
+  if (d->space == BEC_SPACE_Q1 && d->route != BEC_ROUTE_FST)
+    return einval("Q1 elements need BEC_ROUTE_FST");
+  if (d->space == BEC_SPACE_Q1 && d->dim == 3) return einval("Q1 elements are 1D or 2D");
 
   bec_problem* p = new (std::nothrow) bec_problem();
   if (p == nullptr) return BEC_ENOMEM;
@@ -209,7 +214,8 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   p->dim = d->dim;
   p->m = d->nx;
   p->N = d->N;
-  p->J = d->dim == 2 ? (long long)d->nx * d->nx : d->nx;
+  p->J = d->nx;
+  for (int k = 1; k < d->dim; ++k) p->J *= d->nx;
   p->U = p->J * d->N;
   p->tau = d->T / d->N;
   p->h = 1.0 / (d->nx + 1);
@@ -240,6 +246,10 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   chain(dmalloc(&t.sin2_32, n));
   chain(dmalloc(&t.mu64, p->m));
   chain(dmalloc(&t.mu32, p->m));
+  if (d->space == BEC_SPACE_Q1) {
+    chain(dmalloc(&t.mum64, p->m));
+    chain(dmalloc(&t.mum32, p->m));
+  }
   chain(dmalloc(&t.es64, N));
   chain(dmalloc(&t.eis64, N));
   chain(dmalloc(&t.es32, N));
@@ -313,16 +323,27 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     s64[j] = 2.0 * std::sin(j * kPi / n);
     s32[j] = (float)s64[j];
   }
-  // 1D FD eigenvalues (4a/h^2) sin^2(k pi h / 2), k = 1..m
+  // 1D eigenvalues on the sine basis, k = 1..m: FD stiffness (4a/h^2)
+  // sin^2(k pi h / 2); Q1 stiffness a (4/h) sin^2(k pi h / 2) and mass
+  // (h/3)(2 + cos(k pi h)) (the tridiagonal Toeplitz K1 and M1)
+  const bool q1 = d->space == BEC_SPACE_Q1;
+  std::vector<double> mum64(p->m);
+  std::vector<float> mum32(p->m);
   for (int k = 1; k <= p->m; ++k) {
     const double sk = std::sin(k * kPi * p->h / 2.0);
-    mu64[k - 1] = 4.0 * p->a / (p->h * p->h) * sk * sk;
+    mu64[k - 1] = (q1 ? 4.0 * p->a / p->h : 4.0 * p->a / (p->h * p->h)) * sk * sk;
     mu32[k - 1] = (float)mu64[k - 1];
+    mum64[k - 1] = p->h / 3.0 * (2.0 + std::cos(k * kPi * p->h));
+    mum32[k - 1] = (float)mum64[k - 1];
   }
   chain(upload(t.sin2_64, s64, p->stream));
   chain(upload(t.sin2_32, s32, p->stream));
   chain(upload(t.mu64, mu64, p->stream));
   chain(upload(t.mu32, mu32, p->stream));
+  if (q1) {
+    chain(upload(t.mum64, mum64, p->stream));
+    chain(upload(t.mum32, mum32, p->stream));
+  }
   std::vector<double> scal0(kScalSlots, 0.0);
   scal0[S_ONE] = 1.0;
   chain(upload(p->scal, scal0, p->stream));

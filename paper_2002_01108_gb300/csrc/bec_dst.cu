@@ -72,35 +72,42 @@ dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restric
   }
 }
 
-// DST along y, in place, for every slice of `nslices` [m][m] slices: a block
-// owns W = 2 x warps adjacent columns of one slice; the tile is loaded and
-// stored with coalesced row segments, each warp transforms one column pair.
+// DST along the rows of every slice, in place: slice s (s < nslices, at
+// data + s * slice_stride) holds m rows of ncols values, row j at j *
+// row_stride, and the transform runs down each column (along j).  A block
+// owns W = 2 x warps adjacent columns; the tile is loaded and stored with
+// coalesced row segments, each warp transforms one column pair.  2D: the
+// y-DST of [ny][nx] slices; 3D: the y-DST of every [ny][nx] plane and the
+// z-DST of [nz][ny nx] slices.
 template <typename T, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-dst_cols_kernel(T* data, int m, long long J, const T* __restrict__ sin2,
-                const v2_t<T>* __restrict__ tw) {
+dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice_stride,
+                long long nslices, const T* __restrict__ sin2, const v2_t<T>* __restrict__ tw) {
   constexpr int LSC = line_slots(LOGN);
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = blockIdx.x * W;
-  T* base = data + (long long)blockIdx.y * J;
   const int total = m * W;
+  for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y) {
+    T* base = data + sl * slice_stride;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < total; e += WARPS * 32) {
-    const int j = e / W, c = e % W;
-    const int x = x0 + c;
-    sm[c * LSC + j] = x < m ? base[(long long)j * m + x] : T(0);
-  }
-  __syncthreads();
-  warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * LSC, LSC, sin2, tw, lane);
-  __syncthreads();
+    for (int e = threadIdx.x; e < total; e += WARPS * 32) {
+      const int j = e / W, c = e % W;
+      const int x = x0 + c;
+      sm[c * LSC + j] = x < ncols ? base[(long long)j * row_stride + x] : T(0);
+    }
+    __syncthreads();
+    warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * LSC, LSC, sin2, tw, lane);
+    __syncthreads();
 #pragma unroll 4
-  for (int e = threadIdx.x; e < total; e += WARPS * 32) {
-    const int j = e / W, c = e % W;
-    const int x = x0 + c;
-    if (x < m) base[(long long)j * m + x] = sm[c * LSC + j];
+    for (int e = threadIdx.x; e < total; e += WARPS * 32) {
+      const int j = e / W, c = e % W;
+      const int x = x0 + c;
+      if (x < ncols) base[(long long)j * row_stride + x] = sm[c * LSC + j];
+    }
+    __syncthreads();
   }
 }
 
@@ -131,10 +138,23 @@ bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>*
   const size_t smem = (size_t)WARPS * 2 * line_slots(LOGN) * sizeof(T);
   auto k = dst_cols_kernel<T, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
-  dim3 grid((unsigned)((p->m + 2 * WARPS - 1) / (2 * WARPS)), (unsigned)p->N);
-  BEC_LAUNCH_BEGIN(p);
-  k<<<grid, WARPS * 32, smem, p->stream>>>(static_cast<T*>(data), p->m, p->J, sin2, tw);
-  BEC_LAUNCH_CHECK(p, "dst_cols_kernel");
+  const long long m = p->m, m2 = m * m;
+  // 2D: y over [ny][nx] slices; 3D: y over every [ny][nx] plane, then z over
+  // [nz][ny nx] slices
+  const int passes = p->dim == 3 ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
+    const bool zpass = pass == 1;
+    const int ncols = (int)(zpass ? m2 : m);
+    const long long row_stride = zpass ? m2 : m;
+    const long long slice_stride = zpass ? p->J : m2;
+    const long long nslices = zpass ? (long long)p->N : (long long)p->N * (p->dim == 3 ? m : 1);
+    dim3 grid((unsigned)((ncols + 2 * WARPS - 1) / (2 * WARPS)),
+              (unsigned)(nslices < 65535 ? nslices : 65535));
+    BEC_LAUNCH_BEGIN(p);
+    k<<<grid, WARPS * 32, smem, p->stream>>>(static_cast<T*>(data), p->m, ncols, row_stride,
+                                             slice_stride, nslices, sin2, tw);
+    BEC_LAUNCH_CHECK(p, "dst_cols_kernel");
+  }
   return BEC_OK;
 }
 

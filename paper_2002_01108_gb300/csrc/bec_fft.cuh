@@ -16,14 +16,16 @@ template <> struct V2T<double> { using type = double2; };
 template <> struct V2T<float> { using type = float2; };
 template <typename T> using v2_t = typename V2T<T>::type;
 
+// Complex products with the fused multiply-adds written out, so that every
+// compilation of a kernel (e.g. each block width) rounds them the same way.
 template <typename V>
 __device__ __forceinline__ V cmul(V a, V b) {
-  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+  return {fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x)};
 }
 // a * conj(b)
 template <typename V>
 __device__ __forceinline__ V cmulc(V a, V b) {
-  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+  return {fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -(a.x * b.y))};
 }
 
 // IEEE 754 binary64 <-> binary32 conversions in integer arithmetic.  On this

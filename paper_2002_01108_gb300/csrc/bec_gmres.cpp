@@ -43,20 +43,21 @@ bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* 
   }
   const double n = (double)(p->m + 1);
   const double per_axis = (2.0 / n) / 16.0;   // (orthonormal / raw)^2 for one forward+inverse pair
-  const double scale = 0.5 / p->N * (p->dim == 2 ? per_axis * per_axis : per_axis);
-  const long long rows = p->dim == 2 ? (long long)p->N * p->m : p->N;
+  double scale = 0.5 / p->N;
+  for (int d = 0; d < p->dim; ++d) scale *= per_axis;
+  const long long rows = p->J / p->m * p->N;    // lines along x
   if (fp64) {
     BEC_TRY(launch_dst_rows(p, y, 1, z, 1, rows, 1));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
+    if (p->dim >= 2) BEC_TRY(launch_dst_cols(p, z, 1));
     BEC_TRY(launch_time_pass(p, z, 1, scale, scale_dev));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, z, 1));
+    if (p->dim >= 2) BEC_TRY(launch_dst_cols(p, z, 1));
     BEC_TRY(launch_dst_rows(p, z, 1, z, 1, rows, 1));
   } else {
     void* s = p->pc_scratch;
     BEC_TRY(launch_dst_rows(p, y, 1, s, 0, rows, 0));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
+    if (p->dim >= 2) BEC_TRY(launch_dst_cols(p, s, 0));
     BEC_TRY(launch_time_pass(p, s, 0, scale, scale_dev));
-    if (p->dim == 2) BEC_TRY(launch_dst_cols(p, s, 0));
+    if (p->dim >= 2) BEC_TRY(launch_dst_cols(p, s, 0));
     BEC_TRY(launch_dst_rows(p, s, 0, z, 1, rows, 0));
   }
   return BEC_OK;

@@ -34,8 +34,10 @@ struct PcTables {
   FftTables time;            // n = N
   double* sin2_64 = nullptr; // 2 sin(j pi / n), j < n   (DST-I pre-pass)
   float* sin2_32 = nullptr;
-  double* mu64 = nullptr;    // 1D FD eigenvalues mu_i, i = 1..m
+  double* mu64 = nullptr;    // 1D stiffness eigenvalues mu_i, i = 1..m (times a)
   float* mu32 = nullptr;
+  double* mum64 = nullptr;   // 1D mass eigenvalues (Q1 elements only; null: M = I)
+  float* mum32 = nullptr;
   double* es64 = nullptr;    // eps^{j/N}, j < N
   double* eis64 = nullptr;   // eps^{-j/N}
   float* es32 = nullptr;

@@ -3,7 +3,9 @@
 //
 // With M = I and K = (a/h^2) x (3- or 5-point Laplacian), block row n of L is
 //     (L v)^n = (1 + 2 dim c) v^n - c (sum of the 2 dim neighbours of v^n) - v^{n-1},
-// c = tau a / h^2, with no v^0 term; P_eps adds -eps v^N to block row 1.
+// c = tau a / h^2, with no v^0 term; P_eps adds -eps v^N to block row 1.  With
+// Q1 elements (Example 1 of Sec. 5) it is (M + tau K) v^n - M v^{n-1}, with the
+// 9-point stencils of M and K, and P_eps adds -eps M v^N.
 // A thread owns one spatial point and walks a chunk of time slices, keeping
 // v^{n-1} in a register, so v is read from memory once.
 #include <cuda_runtime.h>
@@ -22,12 +24,78 @@ struct StencilGeom {
   double c;       // tau a / h^2 (constant a)
   double alpha;   // (1 + 2 dim c) / c
   const double* __restrict__ kc;   // variable a: tau K row [centre, W, E, S, N] x J, or null
+  // Q1 elements (q1 != 0): the 9-point (2D) or 3-point (1D) stencils of
+  // M + tau K and of M, as centre / edge / corner weights
+  int q1;
+  double ac, ae, ak, mc, me, mk;
 };
 
+// sums of the 4 edge and 4 corner neighbours of point q of slice s (zero
+// outside the interior; 1D: the 2 neighbours, no corners)
+__device__ __forceinline__ void neighbour_sums(const double* __restrict__ s, long long q, int ix,
+                                               int iy, const StencilGeom& g, double& edge,
+                                               double& corner) {
+  const int m = g.m;
+  const bool w = ix > 0, e = ix < m - 1;
+  edge = (w ? s[q - 1] : 0.0) + (e ? s[q + 1] : 0.0);
+  corner = 0.0;
+  if (g.dim == 2) {
+    const bool so = iy > 0, no = iy < m - 1;
+    edge += (so ? s[q - m] : 0.0) + (no ? s[q + m] : 0.0);
+    corner = ((so && w) ? s[q - m - 1] : 0.0) + ((so && e) ? s[q - m + 1] : 0.0) +
+             ((no && w) ? s[q + m - 1] : 0.0) + ((no && e) ? s[q + m + 1] : 0.0);
+  }
+}
+
+// Q1 elements: (M + tau K) v^n - ps_scale M ps at one point (ps = the slice
+// before, or the wrapped last slice of P_eps, or null).
+__device__ __forceinline__ double apply_row_q1(const double* __restrict__ vs,
+                                               const double* __restrict__ ps, double ps_scale,
+                                               long long q, int ix, int iy, const StencilGeom& g,
+                                               double center) {
+  double e, k;
+  neighbour_sums(vs, q, ix, iy, g, e, k);
+  double y = fma(g.ac, center, fma(g.ae, e, g.ak * k));
+  if (ps != nullptr) {
+    double pe, pk;
+    neighbour_sums(ps, q, ix, iy, g, pe, pk);
+    y = fma(-ps_scale, fma(g.mc, ps[q], fma(g.me, pe, g.mk * pk)), y);
+  }
+  return y;
+}
+
+// M u at one point (Q1 elements)
+__device__ __forceinline__ double mass_row_q1(const double* __restrict__ us, long long q, int ix,
+                                              int iy, const StencilGeom& g) {
+  double e, k;
+  neighbour_sums(us, q, ix, iy, g, e, k);
+  return fma(g.mc, us[q], fma(g.me, e, g.mk * k));
+}
+
+// The operator a kernel instantiation applies: finite differences in 1D or
+// 2D (constant or variable a), Q1 elements (1D or 2D), finite differences in 3D.
+enum { kFD = 0, kQ1 = 1, kFD3 = 2 };
+
+// point q of a slice as (ix, iy, iz): x fastest, rows of m points
+template <int KIND>
+__device__ __forceinline__ void decompose(long long q, const StencilGeom& g, int& ix, int& iy,
+                                          int& iz) {
+  if constexpr (KIND == kFD3) {
+    const long long r = q / g.m;
+    ix = (int)(q - r * g.m);
+    iz = (int)(r / g.m);
+    iy = (int)(r - (long long)iz * g.m);
+  } else {
+    iy = g.dim == 2 ? (int)(q / g.m) : 0;
+    ix = (int)(q - (long long)iy * g.m);
+    iz = 0;
+  }
+}
+
 // (L v)^n at one point: c (alpha v - sum of neighbours) - v^{n-1}, which is
-// (1 + 2 dim c) v - c (sum) - v^{n-1} in 3 FP64 adds and 2 FMAs.
+// (1 + 2 dim c) v - c (sum) - v^{n-1} in 3 FP64 adds and 2 FMAs (2D).
 __device__ __forceinline__ double apply_row(const double* __restrict__ vs, long long q, int ix,
-                                            int iy, const StencilGeom& g, double center,
+                                            int iy, int iz, const StencilGeom& g, double center,
                                             double prev) {
   if (g.kc != nullptr) {   // variable coefficient: v + tau K v - v^{n-1}
     const long long J = g.J;
@@ -43,7 +111,31 @@ __device__ __forceinline__ double apply_row(const double* __restrict__ vs, long 
   return fma(g.c, fma(g.alpha, center, -nb), -prev);
 }
 
+// 3D finite differences (7-point): (1 + 6c) v - c (sum of the 6 neighbours) - v^{n-1}
+__device__ __forceinline__ double apply_row3(const double* __restrict__ vs, long long q, int ix,
+                                             int iy, int iz, const StencilGeom& g, double center,
+                                             double prev) {
+  const long long m2 = (long long)g.m * g.m;
+  const double nb = (ix > 0 ? vs[q - 1] : 0.0) + (ix < g.m - 1 ? vs[q + 1] : 0.0) +
+                    (iy > 0 ? vs[q - g.m] : 0.0) + (iy < g.m - 1 ? vs[q + g.m] : 0.0) +
+                    (iz > 0 ? vs[q - m2] : 0.0) + (iz < g.m - 1 ? vs[q + m2] : 0.0);
+  return fma(g.c, fma(g.alpha, center, -nb), -prev);
+}
+
+// the row of L (or P_eps without the wrap) of kernel kind KIND at one point;
+// ps = the slice before (Q1 only; null for the first slice)
+template <int KIND>
+__device__ __forceinline__ double row_of(const double* __restrict__ vs,
+                                         const double* __restrict__ ps, long long q, int ix,
+                                         int iy, int iz, const StencilGeom& g, double center,
+                                         double prev) {
+  if constexpr (KIND == kQ1) return apply_row_q1(vs, ps, 1.0, q, ix, iy, g, center);
+  else if constexpr (KIND == kFD3) return apply_row3(vs, q, ix, iy, iz, g, center, prev);
+  else return apply_row(vs, q, ix, iy, iz, g, center, prev);
+}
+
 // y = L v (corner = 0) or y = P_eps v (corner = eps), times *out_scale if given.
+template <int KIND>
 __global__ void __launch_bounds__(kStencilThreads)
 apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom g,
                double corner, const double* __restrict__ out_scale) {
@@ -51,15 +143,21 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
   if (q >= g.J) return;
   const int n0 = blockIdx.y * kTimeChunk;
   const int n1 = min(g.N, n0 + kTimeChunk);
-  const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
-  const int ix = (int)(q - (long long)iy * g.m);
+  int ix, iy, iz;
+  decompose<KIND>(q, g, ix, iy, iz);
   double prev = n0 > 0 ? v[(long long)(n0 - 1) * g.J + q]
                        : (corner != 0.0 ? corner * v[(long long)(g.N - 1) * g.J + q] : 0.0);
   const double sc = out_scale ? out_scale[0] : 1.0;
   for (int n = n0; n < n1; ++n) {
     const double* vs = v + (long long)n * g.J;
     const double center = vs[q];
-    const double r = apply_row(vs, q, ix, iy, g, center, prev);
+    double r;
+    if constexpr (KIND == kQ1) {
+      const double* ps = n > 0 ? vs - g.J : (corner != 0.0 ? v + (long long)(g.N - 1) * g.J : nullptr);
+      r = apply_row_q1(vs, ps, n > 0 ? 1.0 : corner, q, ix, iy, g, center);
+    } else {
+      r = row_of<KIND>(vs, nullptr, q, ix, iy, iz, g, center, prev);
+    }
     y[(long long)n * g.J + q] = out_scale ? sc * r : r;
     prev = center;
   }
@@ -68,7 +166,7 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
 // w = L z and, for v < NV, the block sums of V_v . w: the first Gram-Schmidt
 // pass fused with the operator.  A fixed grid walks the (256-point tile, time
 // chunk) pairs in a fixed order, so the partial sums are reproducible.
-template <int NV>
+template <int NV, int KIND>
 __global__ void __launch_bounds__(kStencilThreads)
 stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, StencilGeom g, VecList V,
                     const double* __restrict__ vshift, const double* __restrict__ sshift,
@@ -85,14 +183,14 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
     if (q >= g.J) continue;
     const int n0 = (int)(t / jt) * kTimeChunk;
     const int n1 = min(g.N, n0 + kTimeChunk);
-    const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
-    const int ix = (int)(q - (long long)iy * g.m);
+    int ix, iy, iz;
+    decompose<KIND>(q, g, ix, iy, iz);
     double prev = n0 > 0 ? z[(long long)(n0 - 1) * g.J + q] : 0.0;
     for (int n = n0; n < n1; ++n) {
       const double* zs = z + (long long)n * g.J;
       const double center = zs[q];
       const long long o = (long long)n * g.J + q;
-      double y = apply_row(zs, q, ix, iy, g, center, prev);
+      double y = row_of<KIND>(zs, n > 0 ? zs - g.J : nullptr, q, ix, iy, iz, g, center, prev);
       if (vshift) y = fma(-ss, vshift[o], y);
       w[o] = y;
       prev = center;
@@ -121,6 +219,7 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
 }
 
 // r = f - L u (u == nullptr: r = f)
+template <int KIND>
 __global__ void __launch_bounds__(kStencilThreads)
 residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
                 double* __restrict__ r, StencilGeom g) {
@@ -128,8 +227,8 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
   if (q >= g.J) return;
   const int n0 = blockIdx.y * kTimeChunk;
   const int n1 = min(g.N, n0 + kTimeChunk);
-  const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
-  const int ix = (int)(q - (long long)iy * g.m);
+  int ix, iy, iz;
+  decompose<KIND>(q, g, ix, iy, iz);
   if (u == nullptr) {
     for (int n = n0; n < n1; ++n) r[(long long)n * g.J + q] = f[(long long)n * g.J + q];
     return;
@@ -139,13 +238,14 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
     const double* us = u + (long long)n * g.J;
     const double center = us[q];
     const long long o = (long long)n * g.J + q;
-    r[o] = f[o] - apply_row(us, q, ix, iy, g, center, prev);
+    r[o] = f[o] - row_of<KIND>(us, n > 0 ? us - g.J : nullptr, q, ix, iy, iz, g, center, prev);
     prev = center;
   }
 }
 
 // Block sums of (f - L u)^2 and f^2 for RES (Sec. 5).  One partial pair per
 // block, reduced in a fixed order by finish_norms_kernel: deterministic.
+template <int KIND>
 __global__ void __launch_bounds__(kStencilThreads)
 residual_norms_kernel(const double* __restrict__ f, const double* __restrict__ u,
                       double* __restrict__ partials, StencilGeom g) {
@@ -154,15 +254,16 @@ residual_norms_kernel(const double* __restrict__ f, const double* __restrict__ u
   if (q < g.J) {
     const int n0 = blockIdx.y * kTimeChunk;
     const int n1 = min(g.N, n0 + kTimeChunk);
-    const int iy = g.dim == 2 ? (int)(q / g.m) : 0;
-    const int ix = (int)(q - (long long)iy * g.m);
+    int ix, iy, iz;
+    decompose<KIND>(q, g, ix, iy, iz);
     double prev = n0 > 0 ? u[(long long)(n0 - 1) * g.J + q] : 0.0;
     for (int n = n0; n < n1; ++n) {
       const double* us = u + (long long)n * g.J;
       const double center = us[q];
       const long long o = (long long)n * g.J + q;
       const double fo = f[o];
-      const double r = fo - apply_row(us, q, ix, iy, g, center, prev);
+      const double r =
+          fo - row_of<KIND>(us, n > 0 ? us - g.J : nullptr, q, ix, iy, iz, g, center, prev);
       rr += r * r;
       ff += fo * fo;
       prev = center;
@@ -215,13 +316,22 @@ __global__ void finish_norms_kernel(const double* __restrict__ partials, long lo
   }
 }
 
-// f = tau fsrc, plus u0 in slice 1 (Sec. 2).
+// f = tau fsrc, plus M u0 in slice 1 (Sec. 2; M = I for finite differences).
 __global__ void build_rhs_kernel(const double* __restrict__ u0, const double* __restrict__ fsrc,
-                                 double* __restrict__ f, long long J, long long U, double tau) {
+                                 double* __restrict__ f, StencilGeom g, double tau) {
+  const long long U = g.J * g.N;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < U;
        i += (long long)gridDim.x * blockDim.x) {
     double v = tau * fsrc[i];
-    if (i < J) v += u0[i];
+    if (i < g.J) {
+      if (g.q1) {
+        int ix, iy, iz;
+        decompose<kQ1>(i, g, ix, iy, iz);
+        v += mass_row_q1(u0, i, ix, iy, g);
+      } else {
+        v += u0[i];
+      }
+    }
     f[i] = v;
   }
 }
@@ -235,7 +345,36 @@ StencilGeom geom(const bec_problem* p) {
   g.c = p->tau * p->a / (p->h * p->h);
   g.alpha = (1.0 + 2.0 * p->dim * g.c) / g.c;
   g.kc = p->kcoef;
+  g.q1 = p->desc.space == BEC_SPACE_Q1;
+  g.ac = g.ae = g.ak = g.mc = g.me = g.mk = 0.0;
+  if (g.q1) {
+    const double h = p->h, a = p->a, tau = p->tau;
+    double kc, ke, kk;
+    if (p->dim == 2) {   // M = h^2/36 [1 4 1; 4 16 4; 1 4 1], K = a/3 [-1 -1 -1; -1 8 -1; -1 -1 -1]
+      g.mc = 16.0 * h * h / 36.0;
+      g.me = 4.0 * h * h / 36.0;
+      g.mk = h * h / 36.0;
+      kc = 8.0 * a / 3.0;
+      ke = -a / 3.0;
+      kk = -a / 3.0;
+    } else {             // M = h/6 [1 4 1], K = a/h [-1 2 -1]
+      g.mc = 4.0 * h / 6.0;
+      g.me = h / 6.0;
+      g.mk = 0.0;
+      kc = 2.0 * a / h;
+      ke = -a / h;
+      kk = 0.0;
+    }
+    g.ac = g.mc + tau * kc;
+    g.ae = g.me + tau * ke;
+    g.ak = g.mk + tau * kk;
+  }
   return g;
+}
+
+int kind_of(const bec_problem* p) {
+  if (p->desc.space == BEC_SPACE_Q1) return kQ1;
+  return p->dim == 3 ? kFD3 : kFD;
 }
 
 dim3 stencil_grid(const bec_problem* p) {
@@ -253,8 +392,19 @@ long long stencil_blocks(const bec_problem* p) {
 bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double corner,
                           const double* out_scale) {
   BEC_LAUNCH_BEGIN(p);
-  apply_L_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
-                                                                     out_scale);
+  switch (kind_of(p)) {
+    case kQ1:
+      apply_L_kernel<kQ1><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
+                                                                            out_scale);
+      break;
+    case kFD3:
+      apply_L_kernel<kFD3><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
+                                                                             out_scale);
+      break;
+    default:
+      apply_L_kernel<kFD><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
+                                                                            out_scale);
+  }
   BEC_LAUNCH_CHECK(p, "apply_L_kernel");
   return BEC_OK;
 }
@@ -266,12 +416,20 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
   const int n = nv < kMaxVec ? nv : kMaxVec;
   VecList L;
   for (int i = 0; i < kMaxVec; ++i) L.v[i] = i < n ? V[i] : V[0];
+  const int kind = kind_of(p);
   BEC_LAUNCH_BEGIN(p);
   switch (n) {
 #define BEC_SD_CASE(NV)                                                                     \
   case NV:                                                                                  \
-    stencil_dots_kernel<NV><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(          \
-        z, w, geom(p), L, vshift, sshift, p->partials);                                     \
+    if (kind == kQ1)                                                                        \
+      stencil_dots_kernel<NV, kQ1><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(   \
+          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
+    else if (kind == kFD3)                                                                  \
+      stencil_dots_kernel<NV, kFD3><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(  \
+          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
+    else                                                                                    \
+      stencil_dots_kernel<NV, kFD><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(   \
+          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
     break;
     BEC_SD_CASE(1) BEC_SD_CASE(2) BEC_SD_CASE(3) BEC_SD_CASE(4) BEC_SD_CASE(5) BEC_SD_CASE(6)
     BEC_SD_CASE(7) BEC_SD_CASE(8) BEC_SD_CASE(9) BEC_SD_CASE(10) BEC_SD_CASE(11) BEC_SD_CASE(12)
@@ -298,7 +456,16 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
 
 bec_status launch_residual(bec_problem* p, const double* f, const double* u, double* r) {
   BEC_LAUNCH_BEGIN(p);
-  residual_kernel<<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
+  switch (kind_of(p)) {
+    case kQ1:
+      residual_kernel<kQ1><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
+      break;
+    case kFD3:
+      residual_kernel<kFD3><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
+      break;
+    default:
+      residual_kernel<kFD><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
+  }
   BEC_LAUNCH_CHECK(p, "residual_kernel");
   return BEC_OK;
 }
@@ -306,7 +473,16 @@ bec_status launch_residual(bec_problem* p, const double* f, const double* u, dou
 bec_status launch_residual_norms(bec_problem* p, const double* f, const double* u, int slot) {
   const dim3 grid = stencil_grid(p);
   BEC_LAUNCH_BEGIN(p);
-  residual_norms_kernel<<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
+  switch (kind_of(p)) {
+    case kQ1:
+      residual_norms_kernel<kQ1><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
+      break;
+    case kFD3:
+      residual_norms_kernel<kFD3><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
+      break;
+    default:
+      residual_norms_kernel<kFD><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
+  }
   BEC_LAUNCH_CHECK(p, "residual_norms_kernel");
   BEC_LAUNCH_BEGIN(p);
   finish_norms_kernel<<<1, 256, 0, p->stream>>>(p->partials, (long long)grid.x * grid.y, p->scal,
@@ -317,7 +493,7 @@ bec_status launch_residual_norms(bec_problem* p, const double* f, const double* 
 
 bec_status launch_build_rhs(bec_problem* p, const double* u0, const double* fsrc, double* f) {
   BEC_LAUNCH_BEGIN(p);
-  build_rhs_kernel<<<4 * 152, 256, 0, p->stream>>>(u0, fsrc, f, p->J, p->U, p->tau);
+  build_rhs_kernel<<<4 * 152, 256, 0, p->stream>>>(u0, fsrc, f, geom(p), p->tau);
   BEC_LAUNCH_CHECK(p, "build_rhs_kernel");
   return BEC_OK;
 }

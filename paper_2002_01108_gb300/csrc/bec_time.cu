@@ -21,27 +21,63 @@ namespace {
 template <typename T>
 constexpr int time_warps() { return default_time_warps(sizeof(T)); }
 
+// The 1D eigenvalue tables of the spatial operators on the sine basis:
+// stiffness k (times a) and mass m (null: M = I, finite differences).
 template <typename T>
-__device__ __forceinline__ T mode_mu(long long q, long long J, int m, int dim,
-                                     const T* __restrict__ mu1) {
-  if (q >= J) return T(1);                     // padding column: any positive value
-  if (dim == 1) return mu1[q];
+struct ModeEigs {
+  const T* __restrict__ k;
+  const T* __restrict__ m;
+};
+
+// Mass and stiffness eigenvalues of spatial mode q: FD (1, k_i + k_l); Q1
+// (m_i m_l, m_i k_l + k_i m_l) in 2D, (m_q, k_q) in 1D.
+template <typename T>
+__device__ __forceinline__ void mode_eigs(long long q, long long J, int m, int dim,
+                                          ModeEigs<T> e, T& muM, T& muK) {
+  if (q >= J) {                                  // padding column: any positive value
+    muM = T(1);
+    muK = T(1);
+    return;
+  }
+  if (dim == 1) {
+    muM = e.m ? e.m[q] : T(1);
+    muK = e.k[q];
+    return;
+  }
+  if (dim == 3) {                                // FD only: k_i + k_l + k_s
+    const long long m2 = (long long)m * m;
+    const int s = (int)(q / m2);
+    const long long r = q - (long long)s * m2;
+    const int l = (int)(r / m), i = (int)(r - (long long)l * m);
+    muM = T(1);
+    muK = e.k[i] + e.k[l] + e.k[s];
+    return;
+  }
   const int l = (int)(q / m), i = (int)(q - (long long)l * m);
-  return mu1[i] + mu1[l];
+  if (e.m == nullptr) {
+    muM = T(1);
+    muK = e.k[i] + e.k[l];
+  } else {
+    muM = e.m[i] * e.m[l];
+    muK = fma(e.m[i], e.k[l], e.k[i] * e.m[l]);
+  }
 }
 
 // rinv[q][k] = 1 / |lambda'_k + tau mu_q|^2 (same arithmetic as the division
 // it replaces in time_pass_kernel)
 __global__ void rinv_table_kernel(double* __restrict__ rinv, long long J, int NK, int m, int dim,
-                                  const double2* __restrict__ lamf,
-                                  const double* __restrict__ mu1, double tau) {
+                                  const double2* __restrict__ lamf, ModeEigs<double> me,
+                                  double tau) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= J * NK) return;
   const long long q = g / NK;
   const int k = (int)(g - q * NK);
   const double2 L = lamf[k];
-  const double dr = L.x + tau * mode_mu(q, J, m, dim, mu1);
-  rinv[g] = 1.0 / (dr * dr + L.y * L.y);
+  double muM, muK;
+  mode_eigs(q, J, m, dim, me, muM, muK);
+  const bool fe = me.m != nullptr;
+  const double dr = fe ? fma(L.x, muM, tau * muK) : L.x + tau * muK, di = fe ? L.y * muM : L.y;
+  rinv[g] = 1.0 / fma(dr, dr, di * di);
 }
 
 // data: [N][J] in place.  A block owns W = 2 x warps adjacent modes; warp w
@@ -52,7 +88,7 @@ template <typename T, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, LOGN <= 8 ? (sizeof(T) == 8 ? 16 : 32) / WARPS : 1)
 time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
-                 const T* __restrict__ mu1, T tau, T scale_h, const double* __restrict__ scale_dev,
+                 ModeEigs<T> me, T tau, T scale_h, const double* __restrict__ scale_dev,
                  const v2_t<T>* __restrict__ tw, const T* __restrict__ rinv) {
   using V = v2_t<T>;
   const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
@@ -78,8 +114,14 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   warp_fft<T, -1, LOGN>(line, tw, lane);
 
   const long long qa = q0 + 2 * warp;
-  const T mua = mode_mu(qa, J, m, dim, mu1);
-  const T mub = qa + 1 < J ? mode_mu(qa + 1, J, m, dim, mu1) : mua;
+  T ma, mua, mb, mub;                 // mass and stiffness eigenvalues of modes a, b
+  mode_eigs(qa, J, m, dim, me, ma, mua);
+  if (qa + 1 < J) {
+    mode_eigs(qa + 1, J, m, dim, me, mb, mub);
+  } else {
+    mb = ma;
+    mub = mua;
+  }
   constexpr int NK = N / 2 + 1;
   constexpr int PERK = (NK + 31) / 32;
 #pragma unroll
@@ -92,17 +134,21 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
       const V A1 = {C.x + Cn.x, C.y - Cn.y};
       const V A2 = {C.y + Cn.y, Cn.x - C.x};
       const V L = lamf[k];
-      const T d1r = L.x + tau * mua, d2r = L.x + tau * mub;
+      // d = lambda'_k mu^M + tau mu^K for each mode (mu^M = 1 with FD)
+      const bool fe = me.m != nullptr;
+      const T d1r = fe ? fma(L.x, ma, tau * mua) : L.x + tau * mua;
+      const T d2r = fe ? fma(L.x, mb, tau * mub) : L.x + tau * mub;
+      const T d1i = fe ? L.y * ma : L.y, d2i = fe ? L.y * mb : L.y;
       T s1, s2;
       if (rinv != nullptr) {           // 1 / |d|^2 from the table ([q][k], coalesced in k)
         s1 = qa < J ? scale * rinv[qa * NK + k] : T(0);
         s2 = qa + 1 < J ? scale * rinv[(qa + 1) * NK + k] : s1;
       } else {
-        s1 = scale / (d1r * d1r + L.y * L.y);
-        s2 = scale / (d2r * d2r + L.y * L.y);
+        s1 = scale / fma(d1r, d1r, d1i * d1i);
+        s2 = scale / fma(d2r, d2r, d2i * d2i);
       }
-      const V q1 = {d1r * s1, -L.y * s1};           // scale / d1
-      const V q2 = {d2r * s2, -L.y * s2};
+      const V q1 = {d1r * s1, -d1i * s1};           // scale / d1
+      const V q2 = {d2r * s2, -d2i * s2};
       const V B1 = cmul(A1, q1), B2 = cmul(A2, q2);
       line[k] = {B1.x - B2.y, B1.y + B2.x};         // B1 + i B2
       line[kk] = {B1.x + B2.y, B2.x - B1.y};        // conj(B1) + i conj(B2)
@@ -122,7 +168,7 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
 
 template <typename T, int LOGN, int WARPS>
 bec_status time_launch(bec_problem* p, void* data, double scale, const double* scale_dev,
-                       const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                       const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
                        const v2_t<T>* tw, const T* rinv) {
   constexpr int warps = WARPS;
   const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
@@ -133,7 +179,7 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
   const unsigned grid = (unsigned)((p->J + W - 1) / W);
   BEC_LAUNCH_BEGIN(p);
   k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->J, p->m, p->dim, es, eis,
-                                           lamf, mu1, (T)p->tau, (T)scale, scale_dev, tw, rinv);
+                                           lamf, me, (T)p->tau, (T)scale, scale_dev, tw, rinv);
   BEC_LAUNCH_CHECK(p, "time_pass_kernel");
   return BEC_OK;
 }
@@ -142,24 +188,24 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
 // transforms always use the default.
 template <typename T, int LOGN>
 bec_status time_w(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
-                  const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                  const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
                   const v2_t<T>* tw, const T* rinv) {
   if constexpr (LOGN >= 5) {
-    if (w == 4) return time_launch<T, LOGN, 4>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
-    if (w == 8) return time_launch<T, LOGN, 8>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
-    if (w == 16) return time_launch<T, LOGN, 16>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
+    if (w == 4) return time_launch<T, LOGN, 4>(p, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
+    if (w == 8) return time_launch<T, LOGN, 8>(p, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
+    if (w == 16) return time_launch<T, LOGN, 16>(p, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
   }
-  return time_launch<T, LOGN, time_warps<T>()>(p, data, scale, scale_dev, es, eis, lamf, mu1, tw,
+  return time_launch<T, LOGN, time_warps<T>()>(p, data, scale, scale_dev, es, eis, lamf, me, tw,
                                                 rinv);
 }
 
 template <typename T>
 bec_status time_dispatch(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
-                         const T* es, const T* eis, const v2_t<T>* lamf, const T* mu1,
+                         const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
                          const v2_t<T>* tw, const T* rinv) {
   switch (p->tab.time.logn) {
 #define BEC_TIME_CASE(L) \
-  case L: return time_w<T, L>(p, w, data, scale, scale_dev, es, eis, lamf, mu1, tw, rinv);
+  case L: return time_w<T, L>(p, w, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
     BEC_TIME_CASE(1) BEC_TIME_CASE(2) BEC_TIME_CASE(3) BEC_TIME_CASE(4) BEC_TIME_CASE(5)
     BEC_TIME_CASE(6) BEC_TIME_CASE(7) BEC_TIME_CASE(8) BEC_TIME_CASE(9) BEC_TIME_CASE(10)
 #undef BEC_TIME_CASE
@@ -352,10 +398,10 @@ bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale
                               const double* scale_dev, int w) {
   const PcTables& t = p->tab;
   if (fp64)
-    return time_dispatch<double>(p, w, data, scale, scale_dev, t.es64, t.eis64, t.lamf64, t.mu64,
-                                 t.time.tw64, t.rinv64);
-  return time_dispatch<float>(p, w, data, scale, scale_dev, t.es32, t.eis32, t.lamf32, t.mu32,
-                              t.time.tw32, nullptr);
+    return time_dispatch<double>(p, w, data, scale, scale_dev, t.es64, t.eis64, t.lamf64,
+                                 ModeEigs<double>{t.mu64, t.mum64}, t.time.tw64, t.rinv64);
+  return time_dispatch<float>(p, w, data, scale, scale_dev, t.es32, t.eis32, t.lamf32,
+                              ModeEigs<float>{t.mu32, t.mum32}, t.time.tw32, nullptr);
 }
 
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
@@ -367,7 +413,8 @@ bec_status launch_rinv_table(bec_problem* p) {
   const long long total = p->J * (long long)(p->N / 2 + 1);
   BEC_LAUNCH_BEGIN(p);
   rinv_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, p->stream>>>(
-      p->tab.rinv64, p->J, p->N / 2 + 1, p->m, p->dim, p->tab.lamf64, p->tab.mu64, p->tau);
+      p->tab.rinv64, p->J, p->N / 2 + 1, p->m, p->dim, p->tab.lamf64,
+      ModeEigs<double>{p->tab.mu64, p->tab.mum64}, p->tau);
   BEC_LAUNCH_CHECK(p, "rinv_table_kernel");
   return BEC_OK;
 }

@@ -80,13 +80,13 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
     cudaEventDestroy(e0);
     return cuda_fail(cudaGetLastError(), "cudaEventCreate");
   }
-  const long long rows = p->dim == 2 ? (long long)p->N * p->m : p->N;
+  const long long rows = p->J / p->m * p->N;
   const int cand[3] = {4, 8, 16};
   float* out_ms[3] = {r.rows_ms, r.cols_ms, r.time_ms};
   int best[3] = {0, 0, 0};
   bec_status st = BEC_OK;
   for (int which = 0; which < 3 && st == BEC_OK; ++which) {
-    if (which == 1 && p->dim != 2) continue;
+    if (which == 1 && p->dim < 2) continue;
     const int logn = which == 2 ? p->tab.time.logn : p->tab.space.logn;
     if (logn < 5) continue;                       // short transforms: default width only
     float best_ms = -1.f;

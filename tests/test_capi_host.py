@@ -47,7 +47,7 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("dim", 3), ("nx", 254), ("nx", 2), ("nx", 2047), ("N", 100), ("N", 1), ("N", 2048),
+    ("dim", 4), ("nx", 254), ("nx", 2), ("nx", 2047), ("N", 100), ("N", 1), ("N", 2048),
     ("T", 0.0), ("T", float("nan")), ("a", -1.0), ("precision", 7), ("max_restart", 61),
 ])
 def test_allocate_rejects_invalid_descriptions(lib, field, value):
@@ -82,6 +82,17 @@ def test_allocate_rejects_invalid_multigrid_requests(lib):
     for dim, N, pre, omega in ((1, 64, 0, 0.0), (2, 1024, 0, 0.0), (2, 64, 9, 0.0), (2, 64, 0, 2.5)):
         d = ProblemDesc(dim, 63, 63, N, 1.0, 1.0, 1, 0, 10, 0, 0, None, pre, 0, omega)
         assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (dim, N, pre, omega)
+
+
+def test_allocate_rejects_invalid_space_requests(lib):
+    from paper_2002_01108_gb300.bec import ProblemDesc
+    out = ctypes.c_void_p()
+    # an unknown discretisation, and Q1 elements off the sine-transform route
+    for route, space in ((0, 2), (0, -1), (1, 1), (2, 1)):
+        d = ProblemDesc(2, 63, 63, 64, 1.0, 1.0, route, 1 if route == 2 else 0, 10, 0, 0, None,
+                        0, 0, 0.0, 0, 0, space)
+        assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (route, space)
+        assert out.value is None
 
 
 def test_null_arguments_are_rejected(lib):
