@@ -37,7 +37,7 @@ N_STEPS = 256
 EPS = 1.0 / 16.0                     # sqrt(tau)
 RTOL = 1e-8
 RESTART = 30
-METRIC = "space-time unknowns/s solved to 1e-8 rel. residual"
+METRIC = "space-time unknowns/s solved to 1e-8 rel. residual; apply_Pinv HBM GB/s vs peak"
 UNIT = "unknowns/s"
 
 # Algorithmic work per space-time unknown of each kernel at this workload
@@ -97,9 +97,30 @@ def net_fwd_flops(m: int) -> float:
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of each kernel at this workload (see profiles/); None = not captured for the
-# current build of the kernel.
-NCU_TRAFFIC = {}
+# of each kernel at this workload (profiles/dram_traffic_heat2d_255x255_N256.md;
+# the P_eps^-1 passes of the second of three applies, the Krylov kernels of a
+# two-iteration FP32-form solve); absent = not captured for the current build
+# of the kernel.  The writes are what left L2 while the kernel ran.
+NCU_TRAFFIC = {
+    ("dst_rows_kernel", "fp64"): 133235200 + 81506048,
+    ("dst_cols_kernel", "fp64"): 133211648 + 73886720,
+    ("time_pass_kernel", "fp64"): 200390144 + 75095040,
+    ("dst_rows_kernel", "fp32"): 133203712 + 32083712,
+    ("dst_cols_kernel", "fp32"): 66619904 + 8134144,
+    ("time_pass_kernel", "fp32"): 66635520 + 7955200,
+    ("stencil_dots_kernel", "fp32"): 272325632 + 104049664,
+    ("combine_kernel", "fp32"): 266389760 + 100883200,
+}
+# DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
+NCU_PINV_BYTES = {
+    "fp64": (133235200 + 81506048) + (133211648 + 73886720) + (200390144 + 75095040)
+            + (133308160 + 74059008) + (133211648 + 70091776),
+    "fp32": (133203712 + 32083712) + (66619904 + 8134144) + (66635520 + 7955200)
+            + (66605056 + 8205312) + (66615808 + 68916224),
+}
+# Algorithmic bytes per unit of one P_eps^-1 apply with five streaming passes:
+# FP64 16 B per pass; FP32 8 B (x-DST in and out: 12 B, one side FP64).
+PINV_BYTES_PER_UNIT = {"fp64": 80.0, "fp32": 48.0}
 
 
 def parse():
@@ -310,40 +331,86 @@ def measure_form(form, case, args, ws, local, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
 
-    # end to end through the host-buffer entry point: H2D of f, solve, D2H of u
-    f_host = f.cpu().pin_memory()
-    u_host = torch.empty_like(f_host).pin_memory()
-    prob.gmres_solve_host(f_host, u_host, **solve_kw)
-    e2e = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        prob.gmres_solve_host(f_host, u_host, **solve_kw)
-        e2e.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e) / len(e2e)
+    # P_eps^-1 alone (Steps 1-3 of Sec. 4) on f, 4K applies after 3 warm-ups;
+    # the 133 MB input and output exceed L2.  One more apply under per-launch
+    # events gives the passes.
+    z = torch.empty_like(f)
+    for _ in range(3):
+        prob.apply_Pinv(f, z)
+    torch.cuda.synchronize()
+    reps = 4 * args.steps
+    ev0.record(stream)
+    for _ in range(reps):
+        prob.apply_Pinv(f, z)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    pinv_ms = ev0.elapsed_time(ev1) / reps
+    prob.profile_start(1 << 10)
+    prob.apply_Pinv(f, z)
+    pinv_passes = prob.profile_stop()
+    del z
+
+    # End to end through the host-buffer entry points: every step copies its
+    # f from pinned host memory and its u back.  The headline form pipelines
+    # the K steps (bec_gmres_solve_host_many: the copies of one step overlap
+    # the compute of its neighbours); the single-call form runs them one
+    # after another (H2D, solve, D2H, synchronise).  Four distinct input and
+    # output buffers are used in turn.
+    nbuf = min(4, args.steps)
+    f_hosts = [(f * (1.0 + 0.01 * i)).cpu().pin_memory() for i in range(nbuf)]
+    u_hosts = [torch.empty_like(f_hosts[0]).pin_memory() for _ in range(nbuf)]
+    prob.gmres_solve_host_many(f_hosts[:2], u_hosts[:2], **solve_kw)
     if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
+        dist.barrier()
+    t0 = time.perf_counter()
+    _, e2e_infos = prob.gmres_solve_host_many([f_hosts[i % nbuf] for i in range(args.steps)],
+                                              [u_hosts[i % nbuf] for i in range(args.steps)],
+                                              **solve_kw)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_single = []
+    for i in range(args.steps):
+        t1 = time.perf_counter()
+        prob.gmres_solve_host(f_hosts[i % nbuf], u_hosts[i % nbuf], **solve_kw)
+        e2e_single.append(time.perf_counter() - t1)
+    e2e_single_s = sum(e2e_single) / len(e2e_single)
+    if ws > 1:
+        t = torch.tensor([e2e_s, e2e_single_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s, e2e_single_s = (float(x) for x in t.tolist())
     U = prob.U
     prob.close()
     return {"U": U, "ms_step": ms_step, "kernels": kernels, "launches": launches,
             "clocks": clocks, "info": infos[-1], "e2e_s": e2e_s,
-            "e2e_samples_ms": [round(x * 1e3, 3) for x in e2e],
+            "e2e_iters": [i["iters"] for i in e2e_infos],
+            "e2e_single_s": e2e_single_s, "pinv_ms": pinv_ms, "pinv_passes": pinv_passes,
+            "e2e_samples_ms": [round(x * 1e3, 3) for x in e2e_single],
             "tiles": {k: tiles[k] for k in ("rows_warps", "cols_warps", "time_warps")}}
 
 
-def roofline(form, kernels, U):
+def roofline(form, kernels, U, iters=2):
     dom = max(kernels.items(), key=lambda kv: kv[1][1])[0]
     dom_n, dom_ms = kernels[dom]
     avg_ms = dom_ms / max(dom_n, 1)
     peaks, peak_src = measured_peaks()
-    if form == "fp64" and dom in ALGO:
+    if dom == "stencil_dots_kernel":
+        # FP64 arithmetic bounds it (2 FP64 FMA per clock per SM): per unit the
+        # stencil (3 adds, 2 FMAs: 7 flops), the shift by v_j and the norm of w
+        # (2 FMAs) and one FMA per basis vector, j + 1 of them at iteration j
+        nv = (iters + 1) / 2.0
+        flops = 7.0 + 4.0 + 2.0 * nv
+        achieved = flops * U / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 FMA units x clock (2/clk/SM x 152 SMs x 2.07 GHz)",
+                "algorithmic_per_unit": f"{flops:.1f} flop (mean over the {iters} Arnoldi steps)",
+                "units_per_launch": U}
+    elif form == "fp64" and dom in ALGO:
         achieved = ALGO[dom]["flops"] * U / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA units x clock (2/clk/SM x 152 SMs x 2.07 GHz)",
                 "algorithmic_per_unit": f"{ALGO[dom]['flops']:.1f} flop", "units_per_launch": U}
-    else:
+    if dom != "stencil_dots_kernel" and not (form == "fp64" and dom in ALGO):
         bpu = BYTES_PER_UNIT[form].get(dom, 16.0)
         achieved = bpu * U / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -352,6 +419,27 @@ def roofline(form, kernels, U):
     roof["avg_launch_ms"] = avg_ms
     roof["traffic"] = NCU_TRAFFIC.get((dom, form))
     return roof
+
+
+def pinv_report(form, r, U):
+    """Bandwidth of one P_eps^-1 apply: algorithmic bytes of the five
+    streaming passes, the 16 B/U minimum (read y, write z) and the DRAM bytes
+    ncu counted, each over the CUDA-event time of an apply."""
+    peaks, peak_src = measured_peaks()
+    t = r["pinv_ms"] / 1e3
+    bpu = PINV_BYTES_PER_UNIT[form]
+    design = bpu * U / t / 1e9
+    dram = NCU_PINV_BYTES.get(form)
+    return {
+        "ms_per_apply": r["pinv_ms"], "unknowns_per_s": U / t,
+        "algorithmic_bytes_per_unit": bpu, "achieved_gbs": design, "peak_gbs": peaks["hbm_gbs"],
+        "frac": design / peaks["hbm_gbs"], "peak_source": peak_src,
+        "min_bytes_gbs": 16.0 * U / t / 1e9,
+        "dram_bytes_per_apply": dram, "dram_gbs": dram / t / 1e9 if dram else None,
+        "passes_ms": {k: round(ms, 4) for k, (n, ms) in
+                      sorted(r["pinv_passes"].items(), key=lambda kv: -kv[1][1])},
+        "bound": "FP64 pipe (2 FMA/clk/SM)" if form == "fp64" else
+                 "instruction issue and shared memory (the FP32 intermediate stays in L2)"}
 
 
 def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1, post=1):
@@ -587,10 +675,17 @@ def run_gpu(args):
         "config": dict(workload_config(form), iterations=r["info"]["iters"],
                        true_relres=r["info"]["true_relres"], autotuned_warps_per_block=r["tiles"],
                        parallelism=f"{ws} independent replicas"),
-        "roofline": roofline(form, r["kernels"], U),
+        "roofline": roofline(form, r["kernels"], U, r["info"]["iters"]),
+        "apply_pinv": pinv_report(form, r, U),
         "e2e": {"value": ws * U / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": U * 8,
                 "d2h_bytes_per_step": U * 8, "ms_per_step": r["e2e_s"] * 1e3,
-                "samples_ms": r["e2e_samples_ms"]},
+                "api": "bec_gmres_solve_host_many (K steps, copies overlapped with the "
+                       "neighbouring solves; pinned host buffers)",
+                "iterations": r["e2e_iters"],
+                "single_call": {"value": ws * U / r["e2e_single_s"], "unit": UNIT,
+                                "ms_per_step": r["e2e_single_s"] * 1e3,
+                                "api": "bec_gmres_solve_host (H2D, solve, D2H, synchronise)",
+                                "samples_ms": r["e2e_samples_ms"]}},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "kernels": kernel_table(r["kernels"]),
@@ -603,9 +698,12 @@ def run_gpu(args):
         line["forms"] = {other + "_preconditioner": {
             "value": ws * U / (o["ms_step"] / 1e3), "unit": UNIT, "ms_per_step": o["ms_step"],
             "iterations": o["info"]["iters"], "true_relres": o["info"]["true_relres"],
-            "e2e_value": ws * U / o["e2e_s"], "gpu_launches": o["launches"], "clocks": o["clocks"],
+            "e2e_value": ws * U / o["e2e_s"], "e2e_single_call_value": ws * U / o["e2e_single_s"],
+            "gpu_launches": o["launches"], "clocks": o["clocks"],
             "autotuned_warps_per_block": o["tiles"],
-            "roofline": roofline(other, o["kernels"], U), "kernels": kernel_table(o["kernels"]),
+            "roofline": roofline(other, o["kernels"], U, o["info"]["iters"]),
+            "apply_pinv": pinv_report(other, o, U),
+            "kernels": kernel_table(o["kernels"]),
             "note": "same workload and tolerance; FP32/complex64 P_eps^-1 inside FP64 FGMRES"
                     if other == "fp32" else "same workload; plain FP64 form"}}
     if not args.no_other_form:

@@ -191,6 +191,19 @@ bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host,
                                 double* u_host, const bec_gmres_opts* opts,
                                 bec_gmres_info* info);
 
+/* Solves `count` systems with the same problem, one after another, from host
+ * buffers (f_host[i] -> u_host[i], U doubles each; pinned memory gives the
+ * fastest copies).  Not a construct of the paper: a serving form.  Two
+ * device buffer pairs and a copy stream (allocated with desc.host_io) let
+ * the host-to-device copy of f for solve i + 1 and the device-to-host copy
+ * of u from solve i - 1 run while solve i computes.  Every solve starts from
+ * zero (opts->use_x0 must be 0); infos (may be NULL) receives count records.
+ * Returns BEC_ENOTCONV if any solve did not converge (all results are still
+ * written), or the first hard error.  Synchronises. */
+bec_status bec_gmres_solve_host_many(bec_problem* p, const double* const* f_host,
+                                     double* const* u_host, int count,
+                                     const bec_gmres_opts* opts, bec_gmres_info* infos);
+
 /* RES = ||f - L u||_2 / ||f||_2 (Sec. 5) computed on the device; writes the
  * value to *out (host) after synchronising the stream. */
 bec_status bec_true_relres(bec_problem* p, const double* f, const double* u,
@@ -263,6 +276,18 @@ long long bec_learned_fallbacks(bec_problem* p);
  * correction gained nothing there).  Synchronises. */
 bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
 
+/* ---- Failure detection (test hook) ---------------------------------------
+ * Not a construct of the paper.  Every device wait of the library's kernels
+ * is bounded; one that runs out sets an error word and the kernel returns
+ * (freeing what it holds), and the next synchronising call on the problem
+ * (bec_gmres_solve, the learned-route calls) returns BEC_ETIMEOUT.
+ * bec_inject_fault(BEC_FAULT_TC_WITHHOLD_LOADS) makes the next tensor-core
+ * convolution withhold its tile loads, so that its waits run out (about
+ * 0.2 s): a host-side injection that faults, traps and hangs nothing.  The
+ * injection is one-shot; BEC_FAULT_NONE does nothing. */
+enum { BEC_FAULT_NONE = 0, BEC_FAULT_TC_WITHHOLD_LOADS = 1 };
+bec_status bec_inject_fault(int kind);
+
 /* ---- Tile shapes of the P_eps^{-1} passes --------------------------------
  * Not a construct of the paper.  The x-DST, y-DST and time passes group
  * their lines into blocks of 4, 8 or 16 warps (one line pair per warp).
@@ -273,7 +298,9 @@ bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
  * re-times a cached shape.  The width only regroups lines, so every choice
  * gives the same result bit for bit.  Transforms shorter than 32 and the
  * multigrid and learned routes have nothing to tune (the report is zero).
- * bec_batch_create tunes each instance.  Synchronises. */
+ * bec_batch_create tunes each instance.  When the environment variable
+ * BEC_TUNE_CACHE names a file, choices are also read from and appended to
+ * it, so that later processes skip the timing.  Synchronises. */
 typedef struct {
   int rows_warps, cols_warps, time_warps; /* chosen widths (warps per block) */
   float rows_ms[3], cols_ms[3], time_ms[3]; /* ms per launch at 4, 8, 16 warps; 0 = not tried */

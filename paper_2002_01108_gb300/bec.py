@@ -22,7 +22,8 @@ BEC_PC_FP64, BEC_PC_FP32 = 0, 1
 #: every symbol include/bec.h declares
 EXPORTED = (
     "bec_allocate_problem", "bec_set_eps", "bec_apply_A", "bec_apply_P", "bec_apply_Pinv",
-    "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_true_relres",
+    "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_gmres_solve_host_many",
+    "bec_true_relres",
     "bec_free_problem", "bec_problem_size", "bec_kernel_launches", "bec_status_string",
     "bec_last_error", "bec_profile_start", "bec_profile_stop", "bec_relres_noalloc",
     "bec_batch_create", "bec_batch_problem", "bec_batch_solve", "bec_batch_unknowns",
@@ -30,6 +31,7 @@ EXPORTED = (
     "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
     "bec_learned_loss_grad", "bec_learned_fallbacks", "bec_learned_residual_ratios",
     "bec_convert_to_float", "bec_convert_to_double", "bec_autotune", "bec_set_tiles",
+    "bec_inject_fault",
 )
 
 
@@ -97,6 +99,9 @@ def _lib():
                             ctypes.c_int),
         "bec_gmres_solve_host": ([P, D, D, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
                                  ctypes.c_int),
+        "bec_gmres_solve_host_many": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
+                                       ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+                                      ctypes.c_int),
         "bec_true_relres": ([P, D, D, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bec_free_problem": ([P], ctypes.c_int),
         "bec_problem_size": ([P], ctypes.c_longlong),
@@ -124,6 +129,7 @@ def _lib():
         "bec_learned_fallbacks": ([P], ctypes.c_longlong),
         "bec_learned_residual_ratios": ([P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bec_autotune": ([P, ctypes.c_int, ctypes.POINTER(TuneReport)], ctypes.c_int),
+        "bec_inject_fault": ([ctypes.c_int], ctypes.c_int),
         "bec_set_tiles": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "bec_convert_to_float": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
         "bec_convert_to_double": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
@@ -303,6 +309,32 @@ class Problem:
                                            ctypes.byref(info)),
                "bec_gmres_solve_host", allow=(BEC_OK, BEC_ENOTCONV))
         return u_out, info.as_dict()
+
+    def gmres_solve_host_many(self, f_list, u_list=None, restart: int = 30, maxit: int = 300,
+                              rtol: float = 1e-8, flexible: bool = False, left_pc: bool = False):
+        """Solves len(f_list) systems from host buffers, with the copies of
+        one solve overlapping the compute of its neighbours
+        (bec_gmres_solve_host_many).  Returns (u_list, list of info dicts)."""
+        if len(f_list) == 0:
+            raise ValueError("f_list is empty")
+        if u_list is None:
+            u_list = [None] * len(f_list)
+        if len(u_list) != len(f_list):
+            raise ValueError("u_list and f_list differ in length")
+        fp, up, outs = [], [], []
+        for f_host, u_host in zip(f_list, u_list):
+            a, b, c = self._host_ptrs(f_host, u_host)
+            fp.append(a)
+            up.append(b)
+            outs.append(c)
+        count = len(fp)
+        farr = (ctypes.c_void_p * count)(*fp)
+        uarr = (ctypes.c_void_p * count)(*up)
+        opts = self._opts(restart, maxit, rtol, flexible, left_pc, False)
+        infos = (GmresInfo * count)()
+        _check(_lib().bec_gmres_solve_host_many(self._p, farr, uarr, count, ctypes.byref(opts), infos),
+               "bec_gmres_solve_host_many", allow=(BEC_OK, BEC_ENOTCONV))
+        return outs, [i.as_dict() for i in infos]
 
     def _host_ptrs(self, f_host, u_host):
         import torch

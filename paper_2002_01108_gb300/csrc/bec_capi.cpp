@@ -106,10 +106,14 @@ void free_all(bec_problem* p) {
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.mum64, t.mum32, t.es64, t.eis64, t.es32, t.eis32,
                   t.lamf64, t.lamf32, t.rinv64, p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
-                  p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u};
+                  p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u,
+                  p->io_f2, p->io_u2};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->host_scal) cudaFreeHost(p->host_scal);
+  for (cudaEvent_t& e : p->io_ev)
+    if (e) cudaEventDestroy(e);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
 }
 
 // e^{-2 pi i j / n}, j < n
@@ -124,8 +128,8 @@ void twiddles(int n, std::vector<double2>& t64, std::vector<float2>& t32) {
 }
 
 bec_status read_scalars(bec_problem* p) {
-  BEC_CUDA_TRY(cudaMemcpyAsync(p->host_scal, p->scal, kScalSlots * sizeof(double),
-                               cudaMemcpyDeviceToHost, p->stream));
+  const bec_status s = launch_publish_scalars(p);
+  if (s != BEC_OK) return s;
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
   return BEC_OK;
 }
@@ -289,14 +293,25 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   if (d->host_io) {
     chain(dmalloc(&p->io_f, (size_t)U));
     chain(dmalloc(&p->io_u, (size_t)U));
+    chain(dmalloc(&p->io_f2, (size_t)U));
+    chain(dmalloc(&p->io_u2, (size_t)U));
+    if (s == BEC_OK) {
+      cudaError_t e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+      for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&p->io_ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) s = cuda_fail(e, "copy stream / events");
+    }
   }
   if (s == BEC_OK) {
-    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&p->host_scal),
-                                   kScalSlots * sizeof(double));
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&p->host_scal),
+                                  kScalSlots * sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess)
+      e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->host_scal_dev), p->host_scal, 0);
     if (e != cudaSuccess) {
+      if (p->host_scal) cudaFreeHost(p->host_scal);
       cudaGetLastError();
       p->host_scal = nullptr;
-      set_error("cudaMallocHost failed");
+      set_error("cudaHostAlloc of the scalar mirror failed");
       s = BEC_ENOMEM;
     }
   }
@@ -460,6 +475,51 @@ bec_status bec_gmres_solve_host(bec_problem* p, const double* f_host, double* u_
   return s;
 }
 
+bec_status bec_gmres_solve_host_many(bec_problem* p, const double* const* f_host,
+                                     double* const* u_host, int count, const bec_gmres_opts* opts,
+                                     bec_gmres_info* infos) {
+  if (p == nullptr) return einval("null problem");
+  if (p->io_f2 == nullptr) return einval("bec_gmres_solve_host_many needs desc.host_io");
+  BEC_TRY(check_gmres_opts(p, opts));
+  if (opts->use_x0) return einval("bec_gmres_solve_host_many starts every solve from zero");
+  if (count < 1 || f_host == nullptr || u_host == nullptr) return einval("bad right-hand side list");
+  for (int i = 0; i < count; ++i)
+    if (f_host[i] == nullptr || u_host[i] == nullptr) return einval("null host pointer");
+  const size_t bytes = (size_t)p->U * sizeof(double);
+  double* F[2] = {p->io_f, p->io_f2};
+  double* Ub[2] = {p->io_u, p->io_u2};
+  cudaEvent_t* loaded = p->io_ev;
+  cudaEvent_t* solved = p->io_ev + 2;
+  cudaStream_t cs = p->copy_stream;
+  // Solve i uses buffer pair i % 2.  The copy stream loads f of solve i + 1
+  // while solve i runs, and reads u of solve i back while solve i + 1 runs.
+  for (int i = 0; i < count && i < 2; ++i) {
+    BEC_CUDA_TRY(cudaMemcpyAsync(F[i], f_host[i], bytes, cudaMemcpyHostToDevice, cs));
+    BEC_CUDA_TRY(cudaEventRecord(loaded[i], cs));
+  }
+  bec_status worst = BEC_OK;
+  for (int i = 0; i < count; ++i) {
+    const int b = i & 1;
+    BEC_CUDA_TRY(cudaStreamWaitEvent(p->stream, loaded[b], 0));
+    bec_gmres_info local;
+    const bec_status s = gmres_solve_one(p, F[b], Ub[b], opts, infos ? &infos[i] : &local);
+    if (s != BEC_OK && s != BEC_ENOTCONV) {
+      cudaStreamSynchronize(cs);
+      return s;
+    }
+    if (s == BEC_ENOTCONV) worst = s;
+    BEC_CUDA_TRY(cudaEventRecord(solved[b], p->stream));
+    BEC_CUDA_TRY(cudaStreamWaitEvent(cs, solved[b], 0));
+    BEC_CUDA_TRY(cudaMemcpyAsync(u_host[i], Ub[b], bytes, cudaMemcpyDeviceToHost, cs));
+    if (i + 2 < count) {
+      BEC_CUDA_TRY(cudaMemcpyAsync(F[b], f_host[i + 2], bytes, cudaMemcpyHostToDevice, cs));
+      BEC_CUDA_TRY(cudaEventRecord(loaded[b], cs));
+    }
+  }
+  BEC_CUDA_TRY(cudaStreamSynchronize(cs));
+  return worst;
+}
+
 bec_status bec_true_relres(bec_problem* p, const double* f, const double* u, double* out) {
   if (p == nullptr || out == nullptr) return einval("null argument");
   BEC_TRY(check_vec(f));
@@ -573,6 +633,15 @@ bec_status bec_learned_residual_ratios(bec_problem* p, double* host) {
   BEC_TRY(need_net(p));
   if (host == nullptr) return einval("null host pointer");
   return net_residual_ratios(p, host);
+}
+
+bec_status bec_inject_fault(int kind) {
+  if (kind == BEC_FAULT_NONE) return BEC_OK;
+  if (kind == BEC_FAULT_TC_WITHHOLD_LOADS) {
+    tc_withhold_next_loads();
+    return BEC_OK;
+  }
+  return einval("unknown fault kind");
 }
 
 bec_status bec_autotune(bec_problem* p, int force, bec_tune_report* report) {

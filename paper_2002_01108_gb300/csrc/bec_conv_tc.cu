@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "bec_internal.h"
@@ -208,7 +209,7 @@ template <int CIN, int COUT, int STORE_C, bool RELU>
 __global__ void __launch_bounds__(kThreads, 2)
 conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16* __restrict__ wt,
                   __nv_bfloat16* __restrict__ out, int m, int tiles_x, int tiles_img, int ntiles,
-                  int* __restrict__ err) {
+                  int withhold, int* __restrict__ err) {
   using C = Cfg<CIN, COUT>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -264,7 +265,9 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
       mbar_expect_tx(wbar, C::kWBytes);
       bulk_load(sB, wt, C::kWBytes, wbar);
       int i = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      // withhold (a test of the bounded waits): issue no tile load, so that the
+      // MMA warp's wait runs out and the CTA aborts with nothing in flight
+      for (int t = blockIdx.x; !withhold && t < ntiles; t += gridDim.x, ++i) {
         const int s = i % kStages;
         if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, &abort_flag)) {
           abort_flag = 1;
@@ -408,6 +411,9 @@ __global__ void tc_weights_kernel(const float* __restrict__ W, LayerOffsets woff
   wt[g] = __float2bfloat16(v);
 }
 
+// set by bec_inject_fault: the next launch withholds its tile loads
+std::atomic<int> g_withhold_loads{0};
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
@@ -456,12 +462,16 @@ bec_status launch_tc(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat1
   const int ntiles = tiles_img * B;
   const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
   BEC_LAUNCH_BEGIN(p);
-  k<<<grid, kThreads, C::kSmem, p->stream>>>(map, wt, out, m, tiles_x, tiles_img, ntiles, err);
+  const int withhold = g_withhold_loads.exchange(0);   // one-shot test hook
+  k<<<grid, kThreads, C::kSmem, p->stream>>>(map, wt, out, m, tiles_x, tiles_img, ntiles, withhold,
+                                             err);
   BEC_LAUNCH_CHECK(p, "net_conv_tc_kernel");
   return BEC_OK;
 }
 
 }  // namespace
+
+void tc_withhold_next_loads() { g_withhold_loads.store(1); }
 
 int tc_weights_elems() { return layer_wt_offset(kNetLayers - 1) + layer_wt_elems(kNetLayers - 1); }
 

@@ -26,14 +26,14 @@ constexpr int S_REF = 0, S_BETA = 1, S_W = 2, S_RES = 3, S_TRUE = 4, S_WB = 6, S
   } while (0)
 
 bec_status enqueue_scalar_read(bec_problem* p) {
-  BEC_CUDA_TRY(cudaMemcpyAsync(p->host_scal, p->scal, kScalSlots * sizeof(double),
-                               cudaMemcpyDeviceToHost, p->stream));
+  BEC_TRY(launch_publish_scalars(p));
   return BEC_OK;
 }
 }  // namespace
 
 // z = P_eps^{-1} (s y), s = *scale_dev (1 if null)
 bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* scale_dev) {
+  NvtxRange range("bec P_eps^-1");
   const int fp64 = p->desc.precision == BEC_PC_FP64;
   if (p->desc.route == BEC_ROUTE_MG || p->desc.route == BEC_ROUTE_LEARNED) {
     BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));
@@ -119,6 +119,7 @@ bec_status iteration_body(GmresRun& r) {
 
 // Enqueue iteration j, from the problem's graph cache when graphs are used.
 bec_status enqueue_iteration(GmresRun& r) {
+  NvtxRange range("bec Arnoldi iteration");
   bec_problem* p = r.p;
   if (!r.use_graphs) return iteration_body(r);
   const int mode = (r.o.left_pc ? 1 : 0) | (r.o.flexible ? 2 : 0);

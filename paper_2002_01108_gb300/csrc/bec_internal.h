@@ -9,8 +9,18 @@
 #include <vector>
 
 #include "bec.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace bec {
+
+// NVTX range for the duration of a scope (host thread; visible in Nsight
+// timelines, a no-op without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Tables for one transform length n: twiddles e^{-2 pi i j / n}, j < n.
 struct FftTables {
@@ -119,9 +129,14 @@ struct bec_problem {
   double* sigma = nullptr;      // 1 / ||stored V_i||: V_i is kept unnormalised (max_restart + 1)
   int* flag = nullptr;          // device flag: second Gram-Schmidt pass needed
   double* scal = nullptr;       // device scalars (norms, residual estimate)
-  double* host_scal = nullptr;  // pinned mirror of scal
+  double* host_scal = nullptr;  // mapped pinned mirror of scal (host address)
+  double* host_scal_dev = nullptr;   // its device address
   double* io_f = nullptr;       // host_io staging
   double* io_u = nullptr;
+  double* io_f2 = nullptr;      // second staging pair (bec_gmres_solve_host_many)
+  double* io_u2 = nullptr;
+  cudaStream_t copy_stream = nullptr;   // host <-> device copies of the pipelined solves
+  cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // loaded[2], solved[2]
   bec::Profiler prof;
   double* kcoef = nullptr;      // variable a: tau K row [centre, W, E, S, N] x J
   bec::MgState mg;              // BEC_ROUTE_MG hierarchy
@@ -259,6 +274,8 @@ bec_status net_check(bec_problem* p);
 // ---- tensor-core convolutions (bec_conv_tc.cu): every layer of the network,
 // BF16 NHWC activations, tcgen05 MMA with TMA-staged halo tiles
 bool tc_conv_supported();
+// test hook: the next tensor-core convolution withholds its tile loads
+void tc_withhold_next_loads();
 // BF16 elements of the converted weights of all 9 layers
 int tc_weights_elems();
 // the operand layout of every layer from the FP32 master weights W (layer l
@@ -338,6 +355,9 @@ bec_status launch_gmres_start(bec_problem* p, int slot);
 // ycoef = H(0:k,0:k)^{-1} g(0:k)
 bec_status launch_least_squares(bec_problem* p, int k);
 bec_status launch_copy(bec_problem* p, const double* x, double* y);
+// copies the kScalSlots scalars to the mapped host mirror with a kernel, so
+// that the read never queues behind a large copy on a copy engine
+bec_status launch_publish_scalars(bec_problem* p);
 bec_status launch_zero(bec_problem* p, double* x);
 
 }  // namespace bec

@@ -260,6 +260,11 @@ VecList pack(const double* const* V, int n) {
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)   \
   X(31) X(32)
 
+__global__ void publish_scalars_kernel(const double* __restrict__ scal, double* __restrict__ host,
+                                       int n) {
+  if ((int)threadIdx.x < n) host[threadIdx.x] = scal[threadIdx.x];
+}
+
 bec_status launch_dots_chunk(bec_problem* p, const double* w, VecList L, int n, const int* flag) {
   BEC_LAUNCH_BEGIN(p);
   switch (n) {
@@ -382,6 +387,13 @@ bec_status launch_least_squares(bec_problem* p, int k) {
   BEC_LAUNCH_BEGIN(p);
   least_squares_kernel<<<1, 32, 0, p->stream>>>(p->H, p->max_restart + 1, k, p->g, p->ycoef);
   BEC_LAUNCH_CHECK(p, "least_squares_kernel");
+  return BEC_OK;
+}
+
+bec_status launch_publish_scalars(bec_problem* p) {
+  BEC_LAUNCH_BEGIN(p);
+  publish_scalars_kernel<<<1, 32, 0, p->stream>>>(p->scal, p->host_scal_dev, kScalSlots);
+  BEC_LAUNCH_CHECK(p, "publish_scalars_kernel");
   return BEC_OK;
 }
 

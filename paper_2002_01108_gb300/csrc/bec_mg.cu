@@ -485,6 +485,7 @@ bec_status mg_smooth_level0(bec_problem* p, void* xo, const void* x, const void*
 }
 
 bec_status mg_vcycle(bec_problem* p) {
+  NvtxRange range("bec V-cycle");
   if (p->desc.precision == BEC_PC_FP64) return vcycle_t<double>(p);
   return vcycle_t<float>(p);
 }

@@ -644,6 +644,7 @@ bec_status make_pairs(bec_problem* p, int sweeps) {
 template <typename AT>
 bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                    double* loss_hist) {
+  NvtxRange range("bec learned training");
   NetState& n = *p->net;
   const int K = p->mg.K;
   unsigned long long st = seed * 6364136223846793005ull + 1442695040888963407ull;
@@ -676,6 +677,7 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
 
 template <typename AT>
 bec_status correct_t(bec_problem* p) {
+  NvtxRange range("bec learned correction");
   NetState& n = *p->net;
   MgLevel& L0 = p->mg.lv[0];
   const int K = p->mg.K;

@@ -8,9 +8,14 @@
 // changes how lines are grouped into blocks, not what each warp computes, so
 // every choice gives the same result bit for bit.  Choices are cached per
 // (precision, dim, nx, N) for the process, so the instances of a batch that
-// share a shape are tuned once.
+// share a shape are tuned once.  When the environment variable
+// BEC_TUNE_CACHE names a file, earlier choices are read from it once per
+// process and every new choice is appended to it ("fp64 dim nx N rows cols
+// time" per line), so other processes reuse them without timing again.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -33,6 +38,42 @@ std::map<Key, TileChoice>& cache() {
   return c;
 }
 
+const char* cache_file() {
+  const char* f = std::getenv("BEC_TUNE_CACHE");
+  return (f != nullptr && f[0] != '\0') ? f : nullptr;
+}
+
+bool valid_width(int w) { return w == 0 || w == 4 || w == 8 || w == 16; }
+
+// reads the cache file into the process cache (once; under cache_mutex)
+void load_cache_file() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = cache_file();
+  if (path == nullptr) return;
+  FILE* fh = std::fopen(path, "r");
+  if (fh == nullptr) return;
+  char line[256];
+  while (std::fgets(line, sizeof line, fh) != nullptr) {   // a malformed line is skipped
+    int f64, dim, m, N, r, c, t;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d", &f64, &dim, &m, &N, &r, &c, &t) == 7 &&
+        valid_width(r) && valid_width(c) && valid_width(t))
+      cache()[Key{f64, dim, m, N}] = TileChoice{r, c, t};
+  }
+  std::fclose(fh);
+}
+
+void append_cache_file(const Key& k, const TileChoice& t) {
+  const char* path = cache_file();
+  if (path == nullptr) return;
+  FILE* fh = std::fopen(path, "a");
+  if (fh == nullptr) return;
+  std::fprintf(fh, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+               std::get<3>(k), t.rows, t.cols, t.time);
+  std::fclose(fh);
+}
+
 int default_width(int which, int tsize) {
   return which == 0 ? kRowsWarps : which == 1 ? default_cols_warps(tsize) : default_time_warps(tsize);
 }
@@ -46,6 +87,7 @@ size_t pass_smem_bytes(int which, int logn, int fp64, int w) {
 }
 
 bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
+  NvtxRange range("bec autotune");
   bec_tune_report r = {};
   const int fp64 = p->desc.precision == BEC_PC_FP64;
   const int tsize = fp64 ? 8 : 4;
@@ -56,6 +98,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   }
   if (!force) {
     std::lock_guard<std::mutex> g(cache_mutex());
+    load_cache_file();
     auto it = cache().find(key);
     if (it != cache().end()) {
       p->tile = it->second;
@@ -128,6 +171,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   {
     std::lock_guard<std::mutex> g(cache_mutex());
     cache()[key] = p->tile;
+    append_cache_file(key, p->tile);
   }
   r.rows_warps = best[0] ? best[0] : default_width(0, tsize);
   r.cols_warps = best[1] ? best[1] : default_width(1, tsize);

@@ -131,6 +131,31 @@ def test_host_buffer_solve_equals_device_solve():
         assert np.array_equal(uh.numpy(), host(ud))
 
 
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_pipelined_host_solves_equal_single_solves(count):
+    """bec_gmres_solve_host_many: every result and record equals the one
+    bec_gmres_solve_host gives for the same right-hand side, bit for bit,
+    whichever of the two buffer pairs it ran in; pinned and pageable host
+    buffers may be mixed."""
+    import torch
+    from paper_2002_01108_gb300 import BecError
+    case = heat_case_2d(seed=8, m=63, N=32, eps=0.1)
+    f, _, _, _ = oracle_solution(case)
+    rng = np.random.default_rng(80 + count)
+    fs = [f * (1.0 + 0.5 * i) + 1e-3 * rng.standard_normal(f.shape) for i in range(count)]
+    with problem(case, host_io=True) as p:
+        single = [p.gmres_solve_host(torch.from_numpy(x.copy()), rtol=1e-10) for x in fs]
+        fl = [torch.from_numpy(x.copy()).pin_memory() if i % 2 == 0 else torch.from_numpy(x.copy())
+              for i, x in enumerate(fs)]
+        us, infos = p.gmres_solve_host_many(fl, rtol=1e-10)
+        for (u1, i1), u2, i2 in zip(single, us, infos):
+            assert np.array_equal(u1.numpy(), u2.numpy())
+            assert i1 == i2 and i2["converged"] == 1
+    with problem(case) as p:
+        with pytest.raises(BecError):
+            p.gmres_solve_host_many([torch.from_numpy(f.copy())])
+
+
 def test_restarts_maxit_and_initial_guess():
     case = heat_case_2d(seed=7, m=31, N=16, eps=0.5)
     f, u_ref, _, _ = oracle_solution(case)

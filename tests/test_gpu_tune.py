@@ -65,3 +65,31 @@ def test_invalid_widths_are_refused():
         with pytest.raises(BecError):
             p.set_tiles(0, 0, 16)
         p.set_tiles(0, 0, 8)
+
+
+def test_tune_cache_file_is_written_and_read(tmp_path):
+    """BEC_TUNE_CACHE: a forced tuning appends the shape's choice to the file,
+    and a process that starts with the file takes the choice from it,
+    skipping lines it cannot use."""
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    code = (
+        "import torch, sys\n"
+        "from paper_2002_01108_gb300 import Problem\n"
+        "with Problem(2, 63, 32, precision='fp32', flexible=True) as p:\n"
+        "    p.set_eps(0.1)\n"
+        "    r = p.autotune(force=len(sys.argv) > 1)\n"
+        "    print(int(r['cached']), r['rows_warps'], r['cols_warps'], r['time_warps'])\n")
+    env = dict(os.environ, BEC_TUNE_CACHE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    first = subprocess.run([sys.executable, "-c", code, "force"], env=env, cwd=root,
+                           capture_output=True, text=True, check=True).stdout.split()
+    text = path.read_text()
+    assert text.split()[:4] == ["0", "2", "63", "32"]
+    # a malformed line and a line with invalid widths for the same shape are skipped
+    path.write_text("not a tuning line\n" + text + "0 2 63 32 3 3 3\n")
+    second = subprocess.run([sys.executable, "-c", code], env=env, cwd=root,
+                            capture_output=True, text=True, check=True).stdout.split()
+    assert first[0] == "0" and second[0] == "1" and second[1:] == first[1:]
