@@ -30,7 +30,7 @@ __all__ = [
     "BDF1", "BDF2",
     "fd_stiffness_1d", "fd_stiffness", "fd_stiffness_varcoef", "q1_mass_stiffness",
     "time_toeplitz", "time_eps_circulant", "assemble_L", "assemble_P",
-    "build_rhs", "timestep_solve",
+    "build_rhs", "timestep_solve", "build_rhs_pstep", "timestep_solve_pstep",
     "fourier_matrix", "eps_scaling", "eps_circulant_eigs", "dst_matrix", "fd_dst_eigs",
     "apply_Pinv_dense", "apply_Pinv_lu", "apply_Pinv_woodbury", "apply_Pinv_fst",
     "gmres", "fgmres", "relative_residual",
@@ -177,6 +177,41 @@ def timestep_solve(f: np.ndarray, M, K, tau: float) -> np.ndarray:
         rhs = F[n] if prev is None else F[n] + M @ prev
         u[n] = lu.solve(rhs)
         prev = u[n]
+    return u.reshape(f.shape)
+
+
+def build_rhs_pstep(u0: np.ndarray, fsrc: np.ndarray, tau: float, r=BDF1, M=None) -> np.ndarray:
+    """Right-hand side of the p-step all-at-once system L u = f with
+    L = R (x) M + tau I_N (x) K (eq. pstepscheme).  Block row n of R u reaches
+    back to u^{n-p}; the terms r_j M u^{n-j} with n - j <= 0 are known and move
+    to the right: f^n = tau f^n - sum_{j=n}^{p} r_j M u^{n-j}, n = 1..p.
+    The paper does not state the values before u^0; this reading takes them
+    all equal to u^0, so f^n = tau f^n - (r_n + ... + r_p) M u^0.  For BDF1
+    it is build_rhs."""
+    f = tau * np.asarray(fsrc, dtype=np.float64)
+    flat0 = np.asarray(u0, dtype=np.float64).reshape(-1)
+    mu0 = (flat0 if M is None else M @ flat0).reshape(f[0].shape)
+    p = len(r) - 1
+    for n in range(1, min(p, f.shape[0]) + 1):     # 1-based block row n
+        f[n - 1] -= sum(r[n:]) * mu0
+    return f
+
+
+def timestep_solve_pstep(f: np.ndarray, M, K, tau: float, r=BDF1) -> np.ndarray:
+    """u = L^{-1} f for L = R (x) M + tau I_N (x) K (eq. pstepscheme) by
+    stepping block row after block row of the lower-triangular Toeplitz R:
+    (r_0 M + tau K) u^n = f^n - sum_{j=1}^{min(p, n-1)} r_j M u^{n-j},
+    one sparse LU of r_0 M + tau K."""
+    N = f.shape[0]
+    F = f.reshape(N, -1)
+    lu = spla.splu((r[0] * M + tau * K).tocsc())
+    u = np.empty_like(F)
+    for n in range(N):
+        rhs = F[n].copy()
+        for j in range(1, len(r)):
+            if n - j >= 0:
+                rhs -= r[j] * (M @ u[n - j])
+        u[n] = lu.solve(rhs)
     return u.reshape(f.shape)
 
 

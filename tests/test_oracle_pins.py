@@ -227,6 +227,70 @@ def test_timestep_solve_single_mode_closed_form():
         np.testing.assert_allclose(u[n], (1 + tau * mu) ** (-(n + 1)) * u0, rtol=1e-12, atol=1e-15)
 
 
+# ---------------------------------------------------------------- p-step (BDF2) system
+@pytest.mark.parametrize("dim,m,N,space", [(1, 9, 7, "fd"), (2, 5, 6, "fd"), (2, 4, 5, "q1")])
+def test_pstep_stepping_equals_direct_solve_of_L(dim, m, N, space):
+    """Stepping the BDF2 rows one after another gives the solution of the
+    assembled all-at-once matrix R (x) M + tau I (x) K (eq. pstepscheme)."""
+    if space == "fd":
+        M, K, tau = _fd_problem(dim, m, N)
+    else:
+        M, K = O.q1_mass_stiffness(m, 0.3)
+        tau = 1.0 / N
+    f = np.random.default_rng(31).standard_normal((N,) + (m,) * dim)
+    u = O.timestep_solve_pstep(f, M, K, tau, O.BDF2)
+    ud = spla.spsolve(O.assemble_L(N, M, K, tau, O.BDF2).tocsc(), f.reshape(-1))
+    np.testing.assert_allclose(u.reshape(-1), ud, rtol=1e-11, atol=1e-13)
+
+
+def test_pstep_with_bdf1_is_backward_euler():
+    M, K, tau = _fd_problem(2, 5, 6)
+    rng = np.random.default_rng(32)
+    u0, fs = rng.standard_normal((5, 5)), rng.standard_normal((6, 5, 5))
+    np.testing.assert_array_equal(O.build_rhs_pstep(u0, fs, tau, O.BDF1), O.build_rhs(u0, fs, tau))
+    f = O.build_rhs(u0, fs, tau)
+    np.testing.assert_allclose(O.timestep_solve_pstep(f, M, K, tau, O.BDF1),
+                               O.timestep_solve(f, M, K, tau), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 4, 15])
+def test_bdf2_single_mode_closed_form(k):
+    """One DST mode, zero source, pre-start value u^{-1} = u^0: u^n = a_n u^0
+    with (r0 + tau mu) a_n + r1 a_{n-1} + r2 a_{n-2} = 0, a_0 = a_{-1} = 1,
+    i.e. a_n = A z1^n + B z2^n over the roots of (r0 + tau mu) z^2 + r1 z + r2."""
+    m, N = 15, 12
+    M, K, tau = _fd_problem(1, m, N)
+    S = O.dst_matrix(m)
+    u0 = S[:, k - 1]
+    f = O.build_rhs_pstep(u0, np.zeros((N, m)), tau, O.BDF2)
+    u = O.timestep_solve_pstep(f, M, K, tau, O.BDF2)
+    mu = (4.0 * (m + 1) ** 2) * math.sin(k * math.pi / (2 * (m + 1))) ** 2
+    r0, r1, r2 = O.BDF2
+    z1, z2 = np.roots([r0 + tau * mu, r1, r2]).astype(complex)
+    # A + B = 1 and A / z1 + B / z2 = 1
+    A, B = np.linalg.solve(np.array([[1, 1], [1 / z1, 1 / z2]]), np.array([1, 1], dtype=complex))
+    for n in range(1, N + 1):
+        an = (A * z1 ** n + B * z2 ** n).real
+        np.testing.assert_allclose(u[n - 1], an * u0, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("space", ["fd", "q1"])
+def test_pstep_steady_state_with_constant_pre_history(space):
+    """With every pre-start value equal to u^0 and the source K w, the constant
+    trajectory u^n = w solves L u = f: the rows of R sum to zero."""
+    m, N = 5, 6
+    if space == "fd":
+        M, K, tau = _fd_problem(2, m, N)
+    else:
+        M, K = O.q1_mass_stiffness(m, 0.2)
+        tau = 1.0 / N
+    w = np.random.default_rng(33).standard_normal(m * m)
+    fs = np.tile((K @ w).reshape(m, m), (N, 1, 1))
+    f = O.build_rhs_pstep(w.reshape(m, m), fs, tau, O.BDF2, M=None if space == "fd" else M)
+    L = O.assemble_L(N, M, K, tau, O.BDF2)
+    np.testing.assert_allclose(L @ np.tile(w, N), f.reshape(-1), rtol=1e-12, atol=1e-13)
+
+
 # ---------------------------------------------------------------- diagonalisation
 def test_fourier_matrix_is_unitary_and_an_inverse_dft():
     N = 8
@@ -276,6 +340,19 @@ def test_apply_Pinv_routes_agree_with_dense_inverse(dim, m, N, eps):
     zf = O.apply_Pinv_fst(y, dim, 1.0, tau, eps)
     Ps = O.assemble_P(N, M, K, tau, eps)
     assert np.linalg.norm(Ps @ zf.reshape(-1) - y.reshape(-1)) / np.linalg.norm(y) < tol
+
+
+@pytest.mark.parametrize("dim,m,N,eps", [(1, 7, 8, 0.05), (2, 5, 4, 1e-3), (2, 3, 6, 1.0)])
+def test_apply_Pinv_fst_bdf2_agrees_with_dense_inverse(dim, m, N, eps):
+    """The sine-transform route with the BDF2 eigenvalues
+    lambda_k = r0 + r1 eps^{1/N} theta^k + r2 eps^{2/N} theta^{2k} inverts
+    R_eps (x) I + tau I (x) K (eq. pstepbecpreconditioner)."""
+    M, K, tau = _fd_problem(dim, m, N)
+    y = np.random.default_rng(34).standard_normal((N,) + (m,) * dim)
+    P = O.assemble_P(N, M, K, tau, eps, O.BDF2).toarray()
+    zd = np.linalg.solve(P, y.reshape(-1))
+    z = O.apply_Pinv_fst(y, dim, 1.0, tau, eps, O.BDF2).reshape(-1)
+    assert np.linalg.norm(z - zd) / np.linalg.norm(zd) < 1e-11
 
 
 def test_apply_Pinv_lu_with_q1_and_bdf2():
