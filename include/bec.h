@@ -113,9 +113,14 @@ typedef struct {
                             1: M = M1 (x) M1, K = a (M1 (x) K1 + K1 (x) M1) in 2D,
                             M1 = h/6 tridiag(1, 4, 1), K1 = 1/h tridiag(-1, 2, -1);
                             needs BEC_ROUTE_FST) */
+  int time_scheme;       /* BEC_TIME_BDF1 (0, backward Euler, Sec. 2) or
+                            BEC_TIME_BDF2 (the two-step backward difference
+                            r = (3/2, -2, 1/2) of Sec. 4 eq. pstepscheme and
+                            Sec. 5; needs BEC_ROUTE_FST, dim 1 or 2, N >= 4) */
 } bec_problem_desc;
 
 enum { BEC_SPACE_FD = 0, BEC_SPACE_Q1 = 1 };
+enum { BEC_TIME_BDF1 = 0, BEC_TIME_BDF2 = 1 };
 
 /* Validates desc, allocates the workspace (Krylov basis (max_restart+1) x U
  * doubles, Z when flexible, one U-vector of preconditioner scratch, tables)
@@ -125,17 +130,24 @@ bec_status bec_allocate_problem(const bec_problem_desc* desc, void* stream,
                                 bec_problem** out);
 
 /* Sets eps in (0, 1] (Theorem pinvertibility) and recomputes the tables of
- * Sec. 4: D_eps = diag(eps^{(k-1)/N}) and lambda_k = 1 - eps^{1/N} theta^k
- * (eq. repsdiagform with r = (1, -1)).  eps = 1 is the block circulant
- * preconditioner of McDonald, Pestana and Wathen.  Else BEC_EINVAL. */
+ * Sec. 4: D_eps = diag(eps^{(k-1)/N}) and lambda_k = sum_j r_j eps^{j/N}
+ * theta^{jk} (eq. repsdiagform): 1 - eps^{1/N} theta^k for BDF1, and
+ * 3/2 - 2 eps^{1/N} theta^k + 1/2 eps^{2/N} theta^{2k} for BDF2 (the
+ * eigenvalues of R_eps of eq. pstepbecpreconditioner).  eps = 1 is the block
+ * circulant preconditioner of McDonald, Pestana and Wathen.  Else
+ * BEC_EINVAL. */
 bec_status bec_set_eps(bec_problem* p, double eps);
 
 /* y = L v (Sec. 2, eq. allatoncesystem): y^n = (I + tau K) v^n - v^{n-1},
- * with no v^0 term.  v and y must not overlap. */
+ * with no v^0 term.  With BEC_TIME_BDF2 it is L = R (x) M + tau I (x) K of
+ * eq. pstepscheme: y^n = (3/2 M + tau K) v^n - 2 M v^{n-1} + 1/2 M v^{n-2},
+ * terms before v^1 absent.  v and y must not overlap. */
 bec_status bec_apply_A(bec_problem* p, const double* v, double* y);
 
-/* y = P_eps v (start of Sec. 3); as bec_apply_A plus -eps v^N into slice 1.
- * A check of bec_apply_Pinv, not part of the solve.  v, y must not overlap. */
+/* y = P_eps v (start of Sec. 3); as bec_apply_A plus -eps v^N into slice 1
+ * (BDF2: the wrapped terms eps r_j M v^{N+n-j} of eq. pstepbecpreconditioner
+ * in slices 1 and 2).  A check of bec_apply_Pinv, not part of the solve.
+ * v, y must not overlap. */
 bec_status bec_apply_P(bec_problem* p, const double* v, double* y);
 
 /* z = P_eps^{-1} y by the three steps of Sec. 4 (eqs. ytild, blockdiaginv,
@@ -150,7 +162,10 @@ bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z);
 
 /* f = (tau f^1 + M u^0; tau f^2; ...; tau f^N) (Sec. 2; M = I for finite
  * differences).  u0: J doubles, fsrc: U doubles (the source at t_1..t_N, taken
- * as given: with Q1 elements pass the load vector), f: U doubles. */
+ * as given: with Q1 elements pass the load vector), f: U doubles.  BDF2: the
+ * known terms of the first two block rows move to the right, with the value
+ * before u^0 taken equal to u^0 (the paper does not state it):
+ * f^1 = tau f^1 + 3/2 M u^0, f^2 = tau f^2 - 1/2 M u^0. */
 bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc,
                          double* f);
 

@@ -43,7 +43,7 @@ class ProblemDesc(ctypes.Structure):
                 ("host_io", ctypes.c_int), ("a_nodes", ctypes.c_void_p),
                 ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double),
                 ("net_channels", ctypes.c_int), ("net_fp32", ctypes.c_int),
-                ("space", ctypes.c_int)]
+                ("space", ctypes.c_int), ("time_scheme", ctypes.c_int)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -200,7 +200,8 @@ class Problem:
                  precision: str = "fp64", max_restart: int = 30, flexible: bool = False,
                  host_io: bool = False, stream=None, route: str = "fst", a_nodes=None,
                  mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0,
-                 net_channels: int = 0, net_fp32: bool = False, space: str = "fd"):
+                 net_channels: int = 0, net_fp32: bool = False, space: str = "fd",
+                 scheme: str = "bdf1"):
         import torch
         self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
         self.precision = precision
@@ -216,7 +217,8 @@ class Problem:
                            BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
                            max_restart, int(flexible), int(host_io), a_ptr,
                            int(mg_pre), int(mg_post), float(mg_omega), int(net_channels),
-                           int(net_fp32), {"fd": 0, "q1": 1}[space])
+                           int(net_fp32), {"fd": 0, "q1": 1}[space],
+                           {"bdf1": 0, "bdf2": 1}[scheme])
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -456,7 +458,8 @@ class Batch:
                                    BEC_ROUTE_MG if sp.get("route") == "mg" else BEC_ROUTE_FST,
                                    BEC_PC_FP32 if sp.get("precision", "fp32") == "fp32" else BEC_PC_FP64,
                                    sp.get("max_restart", 10), int(flexible), 0, a_ptr, 0, 0, 0.0,
-                                   0, 0, {"fd": 0, "q1": 1}[sp.get("space", "fd")])
+                                   0, 0, {"fd": 0, "q1": 1}[sp.get("space", "fd")],
+                                   {"bdf1": 0, "bdf2": 1}[sp.get("scheme", "bdf1")])
             eps[i] = sp["eps"]
             self.shapes.append((N,) + (nx,) * dim)
         out = ctypes.c_void_p()

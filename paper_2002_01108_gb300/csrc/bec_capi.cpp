@@ -211,6 +211,10 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   if (d->space == BEC_SPACE_Q1 && d->route != BEC_ROUTE_FST)
     return einval("Q1 elements need BEC_ROUTE_FST");
   if (d->space == BEC_SPACE_Q1 && d->dim == 3) return einval("Q1 elements are 1D or 2D");
+  if (d->time_scheme != BEC_TIME_BDF1 && d->time_scheme != BEC_TIME_BDF2)
+    return einval("time_scheme must be BEC_TIME_BDF1 or BEC_TIME_BDF2");
+  if (d->time_scheme == BEC_TIME_BDF2 && (d->route != BEC_ROUTE_FST || d->dim == 3 || d->N < 4))
+    return einval("BDF2 needs BEC_ROUTE_FST, dim 1 or 2 and N >= 4");
 
   bec_problem* p = new (std::nothrow) bec_problem();
   if (p == nullptr) return BEC_ENOMEM;
@@ -388,16 +392,29 @@ bec_status bec_set_eps(bec_problem* p, double eps) {
     es32[j] = (float)es[j];
     eis32[j] = (float)eis[j];
   }
-  // lambda'_k = 1 - eps^{1/N} e^{-2 pi i k / N}, the eigenvalue that pairs with
-  // the forward-sign FFT (lambda_{N-k} of eq. repsdiagform, r = (1, -1))
+  // lambda'_k = sum_j r_j eps^{j/N} e^{-2 pi i j k / N}, the eigenvalue that
+  // pairs with the forward-sign FFT (lambda_{N-k} of eq. repsdiagform):
+  // 1 - eps^{1/N} e^{-2 pi i k/N} for BDF1 (r = (1, -1)), and for BDF2
+  // (r = (3/2, -2, 1/2)) the same sum over j = 0, 1, 2
   const double e1 = std::exp(le / N);
+  const bool bdf2 = p->desc.time_scheme == BEC_TIME_BDF2;
   std::vector<double2> lam(N / 2 + 1);
   std::vector<float2> lam32(N / 2 + 1);
   for (int k = 0; k <= N / 2; ++k) {
     const double a = 2.0 * kPi * k / N;
-    double re = 1.0 - e1 * std::cos(a), im = e1 * std::sin(a);
-    if (k == 0) re = 1.0 - e1, im = 0.0;
-    if (2 * k == N) re = 1.0 + e1, im = 0.0;
+    double re, im;
+    if (!bdf2) {
+      re = 1.0 - e1 * std::cos(a);
+      im = e1 * std::sin(a);
+      if (k == 0) re = 1.0 - e1, im = 0.0;
+      if (2 * k == N) re = 1.0 + e1, im = 0.0;
+    } else {
+      const double e2 = std::exp(2.0 * le / N);
+      re = 1.5 - 2.0 * e1 * std::cos(a) + 0.5 * e2 * std::cos(2.0 * a);
+      im = 2.0 * e1 * std::sin(a) - 0.5 * e2 * std::sin(2.0 * a);
+      if (k == 0) re = 1.5 - 2.0 * e1 + 0.5 * e2, im = 0.0;
+      if (2 * k == N) re = 1.5 + 2.0 * e1 + 0.5 * e2, im = 0.0;
+    }
     lam[k] = make_double2(re, im);
     lam32[k] = make_float2((float)re, (float)im);
   }

@@ -5,7 +5,11 @@
 //     (L v)^n = (1 + 2 dim c) v^n - c (sum of the 2 dim neighbours of v^n) - v^{n-1},
 // c = tau a / h^2, with no v^0 term; P_eps adds -eps v^N to block row 1.  With
 // Q1 elements (Example 1 of Sec. 5) it is (M + tau K) v^n - M v^{n-1}, with the
-// 9-point stencils of M and K, and P_eps adds -eps M v^N.
+// 9-point stencils of M and K, and P_eps adds -eps M v^N.  The two-step
+// scheme (eq. pstepscheme with r = (3/2, -2, 1/2), template parameter P = 2)
+// has block rows (r0 M + tau K) v^n + r1 M v^{n-1} + r2 M v^{n-2}, and P_eps
+// wraps the missing terms around with the factor eps (eq.
+// pstepbecpreconditioner).
 // A thread owns one spatial point and walks a chunk of time slices, keeping
 // v^{n-1} in a register, so v is read from memory once.
 #include <cuda_runtime.h>
@@ -28,6 +32,9 @@ struct StencilGeom {
   // M + tau K and of M, as centre / edge / corner weights
   int q1;
   double ac, ae, ak, mc, me, mk;
+  // two-step scheme: r1, r2 of the rows; rhs1, rhs2 = the multiples of M u^0
+  // that the right-hand side adds to slices 1 and 2 (BDF1: 1 and 0)
+  double r1, r2, rhs1, rhs2;
 };
 
 // sums of the 4 edge and 4 corner neighbours of point q of slice s (zero
@@ -60,6 +67,29 @@ __device__ __forceinline__ double apply_row_q1(const double* __restrict__ vs,
     double pe, pk;
     neighbour_sums(ps, q, ix, iy, g, pe, pk);
     y = fma(-ps_scale, fma(g.mc, ps[q], fma(g.me, pe, g.mk * pk)), y);
+  }
+  return y;
+}
+
+// Q1 elements, two-step scheme: (r0 M + tau K) v^n + s1 M ps + s2 M ps2 at one
+// point (ps, ps2 = the slices one and two back, wrapped or null).
+__device__ __forceinline__ double apply_row_q1_p2(const double* __restrict__ vs,
+                                                  const double* __restrict__ ps, double s1,
+                                                  const double* __restrict__ ps2, double s2,
+                                                  long long q, int ix, int iy, const StencilGeom& g,
+                                                  double center) {
+  double e, k;
+  neighbour_sums(vs, q, ix, iy, g, e, k);
+  double y = fma(g.ac, center, fma(g.ae, e, g.ak * k));
+  if (ps != nullptr) {
+    double pe, pk;
+    neighbour_sums(ps, q, ix, iy, g, pe, pk);
+    y = fma(s1, fma(g.mc, ps[q], fma(g.me, pe, g.mk * pk)), y);
+  }
+  if (ps2 != nullptr) {
+    double pe, pk;
+    neighbour_sums(ps2, q, ix, iy, g, pe, pk);
+    y = fma(s2, fma(g.mc, ps2[q], fma(g.me, pe, g.mk * pk)), y);
   }
   return y;
 }
@@ -122,20 +152,46 @@ __device__ __forceinline__ double apply_row3(const double* __restrict__ vs, long
   return fma(g.c, fma(g.alpha, center, -nb), -prev);
 }
 
-// the row of L (or P_eps without the wrap) of kernel kind KIND at one point;
-// ps = the slice before (Q1 only; null for the first slice)
-template <int KIND>
+// the row of L (or P_eps without the wrap) of kernel kind KIND and P-step
+// scheme at one point; ps, ps2 = the slices one and two back (Q1 only; null
+// before the first slice); prev, prev2 = v^{n-1}, v^{n-2} at the point (FD)
+template <int KIND, int P>
 __device__ __forceinline__ double row_of(const double* __restrict__ vs,
-                                         const double* __restrict__ ps, long long q, int ix,
+                                         const double* __restrict__ ps,
+                                         const double* __restrict__ ps2, long long q, int ix,
                                          int iy, int iz, const StencilGeom& g, double center,
-                                         double prev) {
-  if constexpr (KIND == kQ1) return apply_row_q1(vs, ps, 1.0, q, ix, iy, g, center);
-  else if constexpr (KIND == kFD3) return apply_row3(vs, q, ix, iy, iz, g, center, prev);
-  else return apply_row(vs, q, ix, iy, iz, g, center, prev);
+                                         double prev, double prev2) {
+  if constexpr (P == 2) {
+    static_assert(KIND != kFD3, "the two-step scheme is 1D or 2D");
+    if constexpr (KIND == kQ1) {
+      return apply_row_q1_p2(vs, ps, g.r1, ps2, g.r2, q, ix, iy, g, center);
+    } else {
+      double nb = (ix > 0 ? vs[q - 1] : 0.0) + (ix < g.m - 1 ? vs[q + 1] : 0.0);
+      if (g.dim == 2) nb += (iy > 0 ? vs[q - g.m] : 0.0) + (iy < g.m - 1 ? vs[q + g.m] : 0.0);
+      return fma(g.c, fma(g.alpha, center, -nb), fma(g.r1, prev, g.r2 * prev2));
+    }
+  } else if constexpr (KIND == kQ1) {
+    return apply_row_q1(vs, ps, 1.0, q, ix, iy, g, center);
+  } else if constexpr (KIND == kFD3) {
+    return apply_row3(vs, q, ix, iy, iz, g, center, prev);
+  } else {
+    return apply_row(vs, q, ix, iy, iz, g, center, prev);
+  }
+}
+
+// slice n - j of v for row n, or the slice wrapped around by P_eps (corner
+// != 0) with *scale multiplied by corner; null when there is none
+__device__ __forceinline__ const double* back_slice(const double* __restrict__ v, int n, int j,
+                                                    const StencilGeom& g, double corner,
+                                                    double& scale) {
+  if (n - j >= 0) return v + (long long)(n - j) * g.J;
+  if (corner == 0.0) return nullptr;
+  scale *= corner;
+  return v + (long long)(n - j + g.N) * g.J;
 }
 
 // y = L v (corner = 0) or y = P_eps v (corner = eps), times *out_scale if given.
-template <int KIND>
+template <int KIND, int P>
 __global__ void __launch_bounds__(kStencilThreads)
 apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom g,
                double corner, const double* __restrict__ out_scale) {
@@ -145,20 +201,32 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
   const int n1 = min(g.N, n0 + kTimeChunk);
   int ix, iy, iz;
   decompose<KIND>(q, g, ix, iy, iz);
+  // v^{n0-1} and v^{n0-2} at this point, wrapped around (times corner) by P_eps
   double prev = n0 > 0 ? v[(long long)(n0 - 1) * g.J + q]
                        : (corner != 0.0 ? corner * v[(long long)(g.N - 1) * g.J + q] : 0.0);
+  double prev2 = 0.0;
+  if constexpr (P == 2) {
+    prev2 = n0 > 1 ? v[(long long)(n0 - 2) * g.J + q]
+                   : (corner != 0.0 ? corner * v[(long long)(n0 - 2 + g.N) * g.J + q] : 0.0);
+  }
   const double sc = out_scale ? out_scale[0] : 1.0;
   for (int n = n0; n < n1; ++n) {
     const double* vs = v + (long long)n * g.J;
     const double center = vs[q];
     double r;
-    if constexpr (KIND == kQ1) {
+    if constexpr (KIND == kQ1 && P == 2) {
+      double s1 = g.r1, s2 = g.r2;
+      const double* ps = back_slice(v, n, 1, g, corner, s1);
+      const double* ps2 = back_slice(v, n, 2, g, corner, s2);
+      r = apply_row_q1_p2(vs, ps, s1, ps2, s2, q, ix, iy, g, center);
+    } else if constexpr (KIND == kQ1) {
       const double* ps = n > 0 ? vs - g.J : (corner != 0.0 ? v + (long long)(g.N - 1) * g.J : nullptr);
       r = apply_row_q1(vs, ps, n > 0 ? 1.0 : corner, q, ix, iy, g, center);
     } else {
-      r = row_of<KIND>(vs, nullptr, q, ix, iy, iz, g, center, prev);
+      r = row_of<KIND, P>(vs, nullptr, nullptr, q, ix, iy, iz, g, center, prev, prev2);
     }
     y[(long long)n * g.J + q] = out_scale ? sc * r : r;
+    prev2 = prev;
     prev = center;
   }
 }
@@ -166,7 +234,7 @@ apply_L_kernel(const double* __restrict__ v, double* __restrict__ y, StencilGeom
 // w = L z and, for v < NV, the block sums of V_v . w: the first Gram-Schmidt
 // pass fused with the operator.  A fixed grid walks the (256-point tile, time
 // chunk) pairs in a fixed order, so the partial sums are reproducible.
-template <int NV, int KIND>
+template <int NV, int KIND, int P>
 __global__ void __launch_bounds__(kStencilThreads)
 stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, StencilGeom g, VecList V,
                     const double* __restrict__ vshift, const double* __restrict__ sshift,
@@ -186,13 +254,16 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
     int ix, iy, iz;
     decompose<KIND>(q, g, ix, iy, iz);
     double prev = n0 > 0 ? z[(long long)(n0 - 1) * g.J + q] : 0.0;
+    double prev2 = (P == 2 && n0 > 1) ? z[(long long)(n0 - 2) * g.J + q] : 0.0;
     for (int n = n0; n < n1; ++n) {
       const double* zs = z + (long long)n * g.J;
       const double center = zs[q];
       const long long o = (long long)n * g.J + q;
-      double y = row_of<KIND>(zs, n > 0 ? zs - g.J : nullptr, q, ix, iy, iz, g, center, prev);
+      double y = row_of<KIND, P>(zs, n > 0 ? zs - g.J : nullptr, n > 1 ? zs - 2 * g.J : nullptr, q,
+                                 ix, iy, iz, g, center, prev, prev2);
       if (vshift) y = fma(-ss, vshift[o], y);
       w[o] = y;
+      prev2 = prev;
       prev = center;
       accn = fma(y, y, accn);
 #pragma unroll
@@ -219,7 +290,7 @@ stencil_dots_kernel(const double* __restrict__ z, double* __restrict__ w, Stenci
 }
 
 // r = f - L u (u == nullptr: r = f)
-template <int KIND>
+template <int KIND, int P>
 __global__ void __launch_bounds__(kStencilThreads)
 residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
                 double* __restrict__ r, StencilGeom g) {
@@ -234,18 +305,21 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u,
     return;
   }
   double prev = n0 > 0 ? u[(long long)(n0 - 1) * g.J + q] : 0.0;
+  double prev2 = (P == 2 && n0 > 1) ? u[(long long)(n0 - 2) * g.J + q] : 0.0;
   for (int n = n0; n < n1; ++n) {
     const double* us = u + (long long)n * g.J;
     const double center = us[q];
     const long long o = (long long)n * g.J + q;
-    r[o] = f[o] - row_of<KIND>(us, n > 0 ? us - g.J : nullptr, q, ix, iy, iz, g, center, prev);
+    r[o] = f[o] - row_of<KIND, P>(us, n > 0 ? us - g.J : nullptr, n > 1 ? us - 2 * g.J : nullptr,
+                                  q, ix, iy, iz, g, center, prev, prev2);
+    prev2 = prev;
     prev = center;
   }
 }
 
 // Block sums of (f - L u)^2 and f^2 for RES (Sec. 5).  One partial pair per
 // block, reduced in a fixed order by finish_norms_kernel: deterministic.
-template <int KIND>
+template <int KIND, int P>
 __global__ void __launch_bounds__(kStencilThreads)
 residual_norms_kernel(const double* __restrict__ f, const double* __restrict__ u,
                       double* __restrict__ partials, StencilGeom g) {
@@ -257,15 +331,18 @@ residual_norms_kernel(const double* __restrict__ f, const double* __restrict__ u
     int ix, iy, iz;
     decompose<KIND>(q, g, ix, iy, iz);
     double prev = n0 > 0 ? u[(long long)(n0 - 1) * g.J + q] : 0.0;
+    double prev2 = (P == 2 && n0 > 1) ? u[(long long)(n0 - 2) * g.J + q] : 0.0;
     for (int n = n0; n < n1; ++n) {
       const double* us = u + (long long)n * g.J;
       const double center = us[q];
       const long long o = (long long)n * g.J + q;
       const double fo = f[o];
-      const double r =
-          fo - row_of<KIND>(us, n > 0 ? us - g.J : nullptr, q, ix, iy, iz, g, center, prev);
+      const double r = fo - row_of<KIND, P>(us, n > 0 ? us - g.J : nullptr,
+                                            n > 1 ? us - 2 * g.J : nullptr, q, ix, iy, iz, g,
+                                            center, prev, prev2);
       rr += r * r;
       ff += fo * fo;
+      prev2 = prev;
       prev = center;
     }
   }
@@ -316,21 +393,26 @@ __global__ void finish_norms_kernel(const double* __restrict__ partials, long lo
   }
 }
 
-// f = tau fsrc, plus M u0 in slice 1 (Sec. 2; M = I for finite differences).
+// f = tau fsrc, plus M u0 in slice 1 (Sec. 2; M = I for finite differences);
+// two-step scheme: plus rhs1 M u0 in slice 1 and rhs2 M u0 in slice 2.
 __global__ void build_rhs_kernel(const double* __restrict__ u0, const double* __restrict__ fsrc,
                                  double* __restrict__ f, StencilGeom g, double tau) {
   const long long U = g.J * g.N;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < U;
        i += (long long)gridDim.x * blockDim.x) {
     double v = tau * fsrc[i];
-    if (i < g.J) {
+    const double coef = i < g.J ? g.rhs1 : (i < 2 * g.J ? g.rhs2 : 0.0);
+    if (coef != 0.0) {
+      const long long q = i < g.J ? i : i - g.J;
+      double mu;
       if (g.q1) {
         int ix, iy, iz;
-        decompose<kQ1>(i, g, ix, iy, iz);
-        v += mass_row_q1(u0, i, ix, iy, g);
+        decompose<kQ1>(q, g, ix, iy, iz);
+        mu = mass_row_q1(u0, q, ix, iy, g);
       } else {
-        v += u0[i];
+        mu = u0[q];
       }
+      v = coef == 1.0 ? v + mu : fma(coef, mu, v);
     }
     f[i] = v;
   }
@@ -342,8 +424,16 @@ StencilGeom geom(const bec_problem* p) {
   g.m = p->m;
   g.N = p->N;
   g.dim = p->dim;
+  // r0, r1, r2 of the time scheme (BDF1: 1, -1, 0; BDF2: 3/2, -2, 1/2)
+  const bool bdf2 = p->desc.time_scheme == BEC_TIME_BDF2;
+  const double r0 = bdf2 ? 1.5 : 1.0;
+  g.r1 = bdf2 ? -2.0 : -1.0;
+  g.r2 = bdf2 ? 0.5 : 0.0;
+  // pre-start values taken equal to u^0: slice n gains -(r_n + ... + r_p) M u^0
+  g.rhs1 = -(g.r1 + g.r2);
+  g.rhs2 = -g.r2;
   g.c = p->tau * p->a / (p->h * p->h);
-  g.alpha = (1.0 + 2.0 * p->dim * g.c) / g.c;
+  g.alpha = (r0 + 2.0 * p->dim * g.c) / g.c;
   g.kc = p->kcoef;
   g.q1 = p->desc.space == BEC_SPACE_Q1;
   g.ac = g.ae = g.ak = g.mc = g.me = g.mk = 0.0;
@@ -365,9 +455,9 @@ StencilGeom geom(const bec_problem* p) {
       ke = -a / h;
       kk = 0.0;
     }
-    g.ac = g.mc + tau * kc;
-    g.ae = g.me + tau * ke;
-    g.ak = g.mk + tau * kk;
+    g.ac = r0 * g.mc + tau * kc;
+    g.ae = r0 * g.me + tau * ke;
+    g.ak = r0 * g.mk + tau * kk;
   }
   return g;
 }
@@ -375,6 +465,35 @@ StencilGeom geom(const bec_problem* p) {
 int kind_of(const bec_problem* p) {
   if (p->desc.space == BEC_SPACE_Q1) return kQ1;
   return p->dim == 3 ? kFD3 : kFD;
+}
+
+// the kernel instantiation a problem uses: operator kind and time-scheme steps
+enum { kVarFD = 0, kVarQ1, kVarFD3, kVarFD2, kVarQ12 };
+int variant_of(const bec_problem* p) {
+  const int k = kind_of(p);
+  if (p->desc.time_scheme == BEC_TIME_BDF2) return k == kQ1 ? kVarQ12 : kVarFD2;
+  return k == kQ1 ? kVarQ1 : (k == kFD3 ? kVarFD3 : kVarFD);
+}
+
+// LAUNCH(KIND, P) for the problem's variant
+#define BEC_STENCIL_SWITCH(var, LAUNCH) \
+  switch (var) {                         \
+    case kVarQ1: LAUNCH(kQ1, 1); break;  \
+    case kVarFD3: LAUNCH(kFD3, 1); break; \
+    case kVarFD2: LAUNCH(kFD, 2); break; \
+    case kVarQ12: LAUNCH(kQ1, 2); break; \
+    default: LAUNCH(kFD, 1);             \
+  }
+
+template <int NV>
+void stencil_dots_launch(int var, cudaStream_t st, const double* z, double* w,
+                         const StencilGeom& g, const VecList& L, const double* vshift,
+                         const double* sshift, double* partials) {
+#define BEC_SD_LAUNCH(K, P)                                                      \
+  stencil_dots_kernel<NV, K, P><<<kStencilDotBlocks, kStencilThreads, 0, st>>>( \
+      z, w, g, L, vshift, sshift, partials)
+  BEC_STENCIL_SWITCH(var, BEC_SD_LAUNCH)
+#undef BEC_SD_LAUNCH
 }
 
 dim3 stencil_grid(const bec_problem* p) {
@@ -391,20 +510,13 @@ long long stencil_blocks(const bec_problem* p) {
 
 bec_status launch_apply_L(bec_problem* p, const double* v, double* y, double corner,
                           const double* out_scale) {
+  const StencilGeom g = geom(p);
   BEC_LAUNCH_BEGIN(p);
-  switch (kind_of(p)) {
-    case kQ1:
-      apply_L_kernel<kQ1><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
-                                                                            out_scale);
-      break;
-    case kFD3:
-      apply_L_kernel<kFD3><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
-                                                                             out_scale);
-      break;
-    default:
-      apply_L_kernel<kFD><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(v, y, geom(p), corner,
-                                                                            out_scale);
-  }
+#define BEC_L_LAUNCH(K, P)                                                \
+  apply_L_kernel<K, P><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>( \
+      v, y, g, corner, out_scale)
+  BEC_STENCIL_SWITCH(variant_of(p), BEC_L_LAUNCH)
+#undef BEC_L_LAUNCH
   BEC_LAUNCH_CHECK(p, "apply_L_kernel");
   return BEC_OK;
 }
@@ -416,20 +528,13 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
   const int n = nv < kMaxVec ? nv : kMaxVec;
   VecList L;
   for (int i = 0; i < kMaxVec; ++i) L.v[i] = i < n ? V[i] : V[0];
-  const int kind = kind_of(p);
+  const int var = variant_of(p);
+  const StencilGeom g = geom(p);
   BEC_LAUNCH_BEGIN(p);
   switch (n) {
-#define BEC_SD_CASE(NV)                                                                     \
-  case NV:                                                                                  \
-    if (kind == kQ1)                                                                        \
-      stencil_dots_kernel<NV, kQ1><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(   \
-          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
-    else if (kind == kFD3)                                                                  \
-      stencil_dots_kernel<NV, kFD3><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(  \
-          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
-    else                                                                                    \
-      stencil_dots_kernel<NV, kFD><<<kStencilDotBlocks, kStencilThreads, 0, p->stream>>>(   \
-          z, w, geom(p), L, vshift, sshift, p->partials);                                   \
+#define BEC_SD_CASE(NV)                                                                  \
+  case NV:                                                                               \
+    stencil_dots_launch<NV>(var, p->stream, z, w, g, L, vshift, sshift, p->partials);   \
     break;
     BEC_SD_CASE(1) BEC_SD_CASE(2) BEC_SD_CASE(3) BEC_SD_CASE(4) BEC_SD_CASE(5) BEC_SD_CASE(6)
     BEC_SD_CASE(7) BEC_SD_CASE(8) BEC_SD_CASE(9) BEC_SD_CASE(10) BEC_SD_CASE(11) BEC_SD_CASE(12)
@@ -455,34 +560,24 @@ bec_status launch_stencil_dots(bec_problem* p, const double* z, double* w,
 }
 
 bec_status launch_residual(bec_problem* p, const double* f, const double* u, double* r) {
+  const StencilGeom g = geom(p);
   BEC_LAUNCH_BEGIN(p);
-  switch (kind_of(p)) {
-    case kQ1:
-      residual_kernel<kQ1><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
-      break;
-    case kFD3:
-      residual_kernel<kFD3><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
-      break;
-    default:
-      residual_kernel<kFD><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, geom(p));
-  }
+#define BEC_R_LAUNCH(K, P) \
+  residual_kernel<K, P><<<stencil_grid(p), kStencilThreads, 0, p->stream>>>(f, u, r, g)
+  BEC_STENCIL_SWITCH(variant_of(p), BEC_R_LAUNCH)
+#undef BEC_R_LAUNCH
   BEC_LAUNCH_CHECK(p, "residual_kernel");
   return BEC_OK;
 }
 
 bec_status launch_residual_norms(bec_problem* p, const double* f, const double* u, int slot) {
   const dim3 grid = stencil_grid(p);
+  const StencilGeom g = geom(p);
   BEC_LAUNCH_BEGIN(p);
-  switch (kind_of(p)) {
-    case kQ1:
-      residual_norms_kernel<kQ1><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
-      break;
-    case kFD3:
-      residual_norms_kernel<kFD3><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
-      break;
-    default:
-      residual_norms_kernel<kFD><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, geom(p));
-  }
+#define BEC_RN_LAUNCH(K, P) \
+  residual_norms_kernel<K, P><<<grid, kStencilThreads, 0, p->stream>>>(f, u, p->partials, g)
+  BEC_STENCIL_SWITCH(variant_of(p), BEC_RN_LAUNCH)
+#undef BEC_RN_LAUNCH
   BEC_LAUNCH_CHECK(p, "residual_norms_kernel");
   BEC_LAUNCH_BEGIN(p);
   finish_norms_kernel<<<1, 256, 0, p->stream>>>(p->partials, (long long)grid.x * grid.y, p->scal,

@@ -95,6 +95,19 @@ def test_allocate_rejects_invalid_space_requests(lib):
         assert out.value is None
 
 
+def test_allocate_rejects_invalid_time_schemes(lib):
+    from paper_2002_01108_gb300.bec import ProblemDesc
+    out = ctypes.c_void_p()
+    # an unknown scheme; BDF2 off the sine-transform route, in 3D, or with N < 4
+    for dim, N, route, scheme in ((2, 64, 0, 2), (2, 64, 0, -1), (2, 64, 1, 1), (3, 64, 0, 1),
+                                  (2, 2, 0, 1)):
+        d = ProblemDesc(dim, 63, 63, N, 1.0, 1.0, route, 0, 10, 0, 0, None,
+                        0, 0, 0.0, 0, 0, 0, scheme)
+        assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (dim, N, scheme)
+        assert out.value is None
+        assert b"BDF2" in lib.bec_last_error() or b"time_scheme" in lib.bec_last_error()
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.bec_set_eps(None, 0.5) == 1
     assert lib.bec_apply_A(None, None, None) == 1
