@@ -29,12 +29,14 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "BDF1", "BDF2",
     "fd_stiffness_1d", "fd_stiffness", "fd_stiffness_varcoef", "q1_mass_stiffness",
+    "fd_convection_diffusion", "build_rhs_dirichlet",
     "time_toeplitz", "time_eps_circulant", "assemble_L", "assemble_P",
     "build_rhs", "timestep_solve", "build_rhs_pstep", "timestep_solve_pstep",
     "fourier_matrix", "eps_scaling", "eps_circulant_eigs", "dst_matrix", "fd_dst_eigs",
     "apply_Pinv_dense", "apply_Pinv_lu", "apply_Pinv_woodbury", "apply_Pinv_fst",
     "gmres", "fgmres", "relative_residual",
     "mg_prolongation", "MGHierarchy", "mg_vcycle", "apply_Pinv_mg", "node_coefficient",
+    "dilu_diagonal", "dilu_solve",
 ]
 
 #: backward Euler, r_0 = 1, r_1 = -1 (Sec. 4, remark after eq. pstepscheme)
@@ -98,6 +100,68 @@ def fd_stiffness_varcoef(a_nodes: np.ndarray) -> sp.csr_matrix:
             cols.append(idx(iy, ix))
             vals.append(diag / h ** 2)
     return sp.csr_matrix((vals, (rows, cols)), shape=(m * m, m * m))
+
+
+def fd_convection_diffusion(nu: float, wind: np.ndarray, side: float = 2.0):
+    """5-point FD for -nu Lap u + w . grad u on a square of side ``side``
+    (Example 3 of Sec. 5: nu = 1/200 on (-1, 1)^2 with the circulating wind),
+    m interior points per direction, h = side/(m+1).  The diffusion takes
+    central second differences; the convection takes first-order upwind
+    differences, w_x (u_i - u_{i-1})/h where w_x > 0 and w_x (u_{i+1} - u_i)/h
+    where w_x < 0 (likewise in y).  This stands in for the paper's SUPG Q1
+    elements: both stabilise the convection, and upwinding keeps every
+    off-diagonal entry <= 0.  ``wind`` holds (w_x, w_y) on all nodes,
+    [2][m+2][m+2] ([iy][ix]), evaluated at the node of the row.
+
+    Returns (K, Kb): K (J x J) acts on the interior unknowns [ny][nx], Kb
+    (J x (m+2)^2) on the values at all nodes of which only the boundary ones
+    are used, so that a row of the operator is (K u + Kb g) with g the
+    Dirichlet data."""
+    n2 = wind.shape[1]
+    m = n2 - 2
+    h = side / (m + 1)
+    rows, cols, vals = [], [], []
+    brows, bcols, bvals = [], [], []
+    for iy in range(m):
+        for ix in range(m):
+            gy, gx = iy + 1, ix + 1
+            wx, wy = wind[0, gy, gx], wind[1, gy, gx]
+            row = iy * m + ix
+            # (dy, dx): diffusion -nu/h^2 plus the upwind convection weight
+            nbrs = {(0, -1): -nu / h ** 2 - max(wx, 0.0) / h,
+                    (0, 1): -nu / h ** 2 + min(wx, 0.0) / h,
+                    (-1, 0): -nu / h ** 2 - max(wy, 0.0) / h,
+                    (1, 0): -nu / h ** 2 + min(wy, 0.0) / h}
+            diag = 4.0 * nu / h ** 2 + (abs(wx) + abs(wy)) / h
+            rows.append(row)
+            cols.append(row)
+            vals.append(diag)
+            for (dy, dx), v in nbrs.items():
+                ny, nx = iy + dy, ix + dx
+                if 0 <= ny < m and 0 <= nx < m:
+                    rows.append(row)
+                    cols.append(ny * m + nx)
+                    vals.append(v)
+                else:
+                    brows.append(row)
+                    bcols.append((gy + dy) * n2 + (gx + dx))
+                    bvals.append(v)
+    K = sp.csr_matrix((vals, (rows, cols)), shape=(m * m, m * m))
+    Kb = sp.csr_matrix((bvals, (brows, bcols)), shape=(m * m, n2 * n2))
+    return K, Kb
+
+
+def build_rhs_dirichlet(u0: np.ndarray, fsrc: np.ndarray, g: np.ndarray, tau: float,
+                        Kb) -> np.ndarray:
+    """f of the all-at-once system (Sec. 2, M = I) when the boundary values
+    are prescribed: f^n = tau (fsrc^n - Kb g^n) plus u^0 in slice 1, with g^n
+    the node values [m+2][m+2] at t_n (only the boundary ones enter)."""
+    N = fsrc.shape[0]
+    f = tau * np.asarray(fsrc, dtype=np.float64).reshape(N, -1).copy()
+    for n in range(N):
+        f[n] -= tau * (Kb @ np.asarray(g[n], dtype=np.float64).reshape(-1))
+    f[0] += np.asarray(u0, dtype=np.float64).reshape(-1)
+    return f.reshape(fsrc.shape)
 
 
 def q1_mass_stiffness(m: int, a: float = 1.0):
@@ -568,30 +632,96 @@ class MGHierarchy:
         return (lam * self.M[l] + tau * self.K[l]).tocsr()
 
 
+def dilu_diagonal(A) -> np.ndarray:
+    """The diagonal D of the incomplete factorisation M = (D + L) D^{-1} (D + U)
+    of A = L + diag(A) + U (L, U its strictly lower and upper parts) that
+    makes diag(M) = diag(A): d_i = a_ii - sum_{j < i} a_ij a_ji / d_j over the
+    neighbours j of i.  On a 5-point matrix this M is ILU(0) (M = A on the
+    pattern of A).  This is the ILU smoother of the multigrid route (Example 2
+    and 3 of Sec. 5 smooth with ILU); the sum runs row by row in order."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    d = np.array(A.diagonal(), dtype=np.complex128)
+    for i in range(n):
+        acc = 0.0 + 0.0j
+        for p in range(A.indptr[i], A.indptr[i + 1]):
+            j = A.indices[p]
+            if j < i:
+                aji = A[j, i]
+                if aji != 0:
+                    acc += A.data[p] * aji / d[j]
+        d[i] = d[i] - acc
+    return d
+
+
+def dilu_solve(A, d: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """z = M^{-1} r for M = (D + L) D^{-1} (D + U): forward (D + L) y = r, then
+    backward (D + U) z = D y, both by plain row loops."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    y = np.zeros(n, dtype=np.complex128)
+    for i in range(n):
+        acc = r[i]
+        for p in range(A.indptr[i], A.indptr[i + 1]):
+            j = A.indices[p]
+            if j < i:
+                acc -= A.data[p] * y[j]
+        y[i] = acc / d[i]
+    z = np.zeros(n, dtype=np.complex128)
+    for i in range(n - 1, -1, -1):
+        acc = 0.0 + 0.0j
+        for p in range(A.indptr[i], A.indptr[i + 1]):
+            j = A.indices[p]
+            if j > i:
+                acc += A.data[p] * z[j]
+        z[i] = y[i] - acc / d[i]
+    return z
+
+
 def mg_vcycle(h: MGHierarchy, lam: complex, tau: float, b: np.ndarray, omega: float = 0.8,
-              nu1: int = 1, nu2: int = 1, l: int = 0, x0=None) -> np.ndarray:
+              nu1: int = 1, nu2: int = 1, l: int = 0, x0=None, smoother: str = "jacobi",
+              dcache=None) -> np.ndarray:
     """One V-cycle for (lam M_l + tau K_l) x = b from x0 (zero if None): nu1
-    damped-Jacobi sweeps, residual, restriction, recursive coarse correction,
-    prolongation, nu2 sweeps.  The 1 x 1 coarsest grid is solved exactly."""
+    smoothing sweeps, residual, restriction, recursive coarse correction,
+    prolongation, nu2 sweeps.  The 1 x 1 coarsest grid is solved exactly.
+    smoother="jacobi": x <- x + omega D^{-1} (b - A x); smoother="ilu":
+    x <- x + M^{-1} (b - A x) with M the incomplete factorisation of
+    dilu_diagonal (``dcache`` may hold its diagonals per level)."""
     A = h.op(l, lam, tau)
     if h.sizes[l] == 1:
         return b / A.toarray()[0, 0]
-    dinv = 1.0 / A.diagonal()
+    if smoother == "ilu":
+        if dcache is None:
+            dcache = {}
+        if l not in dcache:
+            dcache[l] = dilu_diagonal(A)
+        dl = dcache[l]
+
+        def sweep(v, rr):
+            return v + dilu_solve(A, dl, rr)
+    else:
+        dinv = 1.0 / A.diagonal()
+
+        def sweep(v, rr):
+            return v + omega * dinv * rr
     x = np.zeros_like(b, dtype=np.complex128) if x0 is None else x0.astype(np.complex128)
     for _ in range(nu1):
-        x = x + omega * dinv * (b - A @ x)
+        x = sweep(x, b - A @ x)
     r = b - A @ x
-    ec = mg_vcycle(h, lam, tau, h.R[l] @ r, omega, nu1, nu2, l + 1)
+    ec = mg_vcycle(h, lam, tau, h.R[l] @ r, omega, nu1, nu2, l + 1, smoother=smoother,
+                   dcache=dcache)
     x = x + h.P[l] @ ec
     for _ in range(nu2):
-        x = x + omega * dinv * (b - A @ x)
+        x = sweep(x, b - A @ x)
     return x
 
 
 def apply_Pinv_mg(y: np.ndarray, h: MGHierarchy, tau: float, eps: float, r=BDF1,
-                  omega: float = 0.8, nu1: int = 1, nu2: int = 1) -> np.ndarray:
+                  omega: float = 0.8, nu1: int = 1, nu2: int = 1, smoother: str = "jacobi",
+                  dcaches=None) -> np.ndarray:
     """Approximate P_eps^{-1} y by the three steps of Sec. 4 with Step 2 done
-    by one V-cycle per shifted system (all N frequencies)."""
+    by one V-cycle per shifted system (all N frequencies).  ``dcaches`` (a
+    dict, optional) keeps the ILU diagonals per frequency across calls."""
     N = y.shape[0]
     Y = y.reshape(N, -1).astype(np.float64)
     d = eps_scaling(N, eps)
@@ -599,7 +729,8 @@ def apply_Pinv_mg(y: np.ndarray, h: MGHierarchy, tau: float, eps: float, r=BDF1,
     lam = eps_circulant_eigs(N, eps, r)
     zt = np.empty_like(yt)
     for k in range(N):                                                # Step 2
-        zt[k] = mg_vcycle(h, lam[k], tau, yt[k], omega, nu1, nu2)
+        dc = None if dcaches is None else dcaches.setdefault(k, {})
+        zt[k] = mg_vcycle(h, lam[k], tau, yt[k], omega, nu1, nu2, smoother=smoother, dcache=dc)
     z = (np.fft.fft(zt, axis=0) / math.sqrt(N)) / d[:, None]           # Step 3
     return z.real.reshape(y.shape)
 

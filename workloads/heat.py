@@ -131,3 +131,20 @@ def grf_log_coefficient(seed: int = 5, m: int = 255, ell: float = 0.1,
     A = Q * np.sqrt(np.maximum(d, 0.0))
     Z = rng.standard_normal((m + 2, m + 2))
     return sigma * (A @ Z @ A.T)
+
+
+def circulating_wind_case(m: int = 255, N: int = 256, T: float = 1.0):
+    """The data of Example 3 of Sec. 5 on the nodes of (-1, 1)^2 with m
+    interior points per side (h = 2/(m+1)): the circulating wind
+    w = (2y(1 - x^2), -2x(1 - y^2)) as [2][m+2][m+2] node values ([iy][ix]),
+    the hot-wall boundary data g(x, y, t_n) = (1 - exp(-10 t_n)) phi(x, y)
+    with phi = 1 on the wall x = 1 and 0 elsewhere, as [N][m+2][m+2] (interior
+    entries zero), u0 = 0 and no source.  Returns (wind, g, u0, fsrc)."""
+    s = -1.0 + 2.0 * np.arange(m + 2, dtype=np.float64) / (m + 1)
+    X, Y = np.meshgrid(s, s)              # X[iy, ix] = x_ix, Y[iy, ix] = y_iy
+    wind = np.stack([2.0 * Y * (1.0 - X * X), -2.0 * X * (1.0 - Y * Y)])
+    phi = np.zeros((m + 2, m + 2))
+    phi[:, m + 1] = 1.0                   # the wall x = 1
+    t = T * np.arange(1, N + 1) / N
+    g = (1.0 - np.exp(-10.0 * t))[:, None, None] * phi[None, :, :]
+    return wind, g, np.zeros((m, m)), np.zeros((N, m, m))
