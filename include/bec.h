@@ -117,7 +117,22 @@ typedef struct {
                             BEC_TIME_BDF2 (the two-step backward difference
                             r = (3/2, -2, 1/2) of Sec. 4 eq. pstepscheme and
                             Sec. 5; needs BEC_ROUTE_FST, dim 1 or 2, N >= 4) */
+  const double* wind;    /* HOST array of 2*(nx+2)*(nx+2) values, the velocity
+                            (w_x then w_y, each [iy][ix] on all nodes), copied;
+                            NULL: no convection.  Adds w . grad u to K with
+                            first-order upwind differences (Example 3 of Sec. 5
+                            with the upwind stencil in place of SUPG elements).
+                            Needs BEC_ROUTE_MG. */
+  double side;           /* side length of the square domain (0 selects 1);
+                            h = side / (nx + 1).  Needs BEC_ROUTE_MG. */
+  int mg_smoother;       /* BEC_MG_JACOBI (0, damped Jacobi) or BEC_MG_ILU (the
+                            incomplete factorisation (D + L) D^{-1} (D + U) of
+                            each shifted system, diag kept, ILU(0) on the
+                            5-point finest grid: the ILU smoothing of Examples 2
+                            and 3 of Sec. 5).  BEC_MG_ILU needs BEC_ROUTE_MG. */
 } bec_problem_desc;
+
+enum { BEC_MG_JACOBI = 0, BEC_MG_ILU = 1 };
 
 enum { BEC_SPACE_FD = 0, BEC_SPACE_Q1 = 1 };
 enum { BEC_TIME_BDF1 = 0, BEC_TIME_BDF2 = 1 };
@@ -168,6 +183,15 @@ bec_status bec_apply_Pinv(bec_problem* p, const double* y, double* z);
  * f^1 = tau f^1 + 3/2 M u^0, f^2 = tau f^2 - 1/2 M u^0. */
 bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc,
                          double* f);
+
+/* As bec_build_rhs, with Dirichlet values on the boundary (Example 3 of
+ * Sec. 5: the hot wall): f^n = tau (fsrc^n - K_b g^n) (+ u^0 in slice 1),
+ * K_b the couplings of the boundary-adjacent points to the boundary nodes.
+ * g: device array of N * (nx+2)^2 doubles, the node values at t_1..t_N
+ * ([n][iy][ix]; only the boundary nodes are read).  Needs BEC_ROUTE_MG
+ * (finite differences with M = I, 2D); else BEC_EINVAL. */
+bec_status bec_build_rhs_dirichlet(bec_problem* p, const double* u0, const double* fsrc,
+                                   const double* g, double* f);
 
 typedef struct {
   int restart;         /* GMRES(restart); 1 <= restart <= max_restart */

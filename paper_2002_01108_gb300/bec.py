@@ -22,7 +22,8 @@ BEC_PC_FP64, BEC_PC_FP32 = 0, 1
 #: every symbol include/bec.h declares
 EXPORTED = (
     "bec_allocate_problem", "bec_set_eps", "bec_apply_A", "bec_apply_P", "bec_apply_Pinv",
-    "bec_build_rhs", "bec_gmres_solve", "bec_gmres_solve_host", "bec_gmres_solve_host_many",
+    "bec_build_rhs", "bec_build_rhs_dirichlet", "bec_gmres_solve", "bec_gmres_solve_host",
+    "bec_gmres_solve_host_many",
     "bec_true_relres",
     "bec_free_problem", "bec_problem_size", "bec_kernel_launches", "bec_status_string",
     "bec_last_error", "bec_profile_start", "bec_profile_stop", "bec_relres_noalloc",
@@ -43,7 +44,8 @@ class ProblemDesc(ctypes.Structure):
                 ("host_io", ctypes.c_int), ("a_nodes", ctypes.c_void_p),
                 ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int), ("mg_omega", ctypes.c_double),
                 ("net_channels", ctypes.c_int), ("net_fp32", ctypes.c_int),
-                ("space", ctypes.c_int), ("time_scheme", ctypes.c_int)]
+                ("space", ctypes.c_int), ("time_scheme", ctypes.c_int),
+                ("wind", ctypes.c_void_p), ("side", ctypes.c_double), ("mg_smoother", ctypes.c_int)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -95,6 +97,7 @@ def _lib():
         "bec_apply_P": ([P, D, D], ctypes.c_int),
         "bec_apply_Pinv": ([P, D, D], ctypes.c_int),
         "bec_build_rhs": ([P, D, D, D], ctypes.c_int),
+        "bec_build_rhs_dirichlet": ([P, D, D, D, D], ctypes.c_int),
         "bec_gmres_solve": ([P, D, D, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
                             ctypes.c_int),
         "bec_gmres_solve_host": ([P, D, D, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
@@ -201,7 +204,7 @@ class Problem:
                  host_io: bool = False, stream=None, route: str = "fst", a_nodes=None,
                  mg_pre: int = 0, mg_post: int = 0, mg_omega: float = 0.0,
                  net_channels: int = 0, net_fp32: bool = False, space: str = "fd",
-                 scheme: str = "bdf1"):
+                 scheme: str = "bdf1", wind=None, side: float = 0.0, mg_smoother: str = "jacobi"):
         import torch
         self.dim, self.nx, self.N, self.T, self.a = dim, nx, N, T, a
         self.precision = precision
@@ -212,13 +215,21 @@ class Problem:
             if self._a_nodes.size != (nx + 2) ** 2:
                 raise ValueError("a_nodes must hold (nx+2)^2 values")
             a_ptr = self._a_nodes.ctypes.data
+        self._wind = None
+        w_ptr = None
+        if wind is not None:
+            self._wind = np.ascontiguousarray(wind, dtype=np.float64)
+            if self._wind.size != 2 * (nx + 2) ** 2:
+                raise ValueError("wind must hold 2 (nx+2)^2 values")
+            w_ptr = self._wind.ctypes.data
         routes = {"fst": BEC_ROUTE_FST, "mg": BEC_ROUTE_MG, "learned": BEC_ROUTE_LEARNED}
         desc = ProblemDesc(dim, nx, nx if dim >= 2 else 1, N, T, a, routes[route],
                            BEC_PC_FP32 if precision == "fp32" else BEC_PC_FP64,
                            max_restart, int(flexible), int(host_io), a_ptr,
                            int(mg_pre), int(mg_post), float(mg_omega), int(net_channels),
                            int(net_fp32), {"fd": 0, "q1": 1}[space],
-                           {"bdf1": 0, "bdf2": 1}[scheme])
+                           {"bdf1": 0, "bdf2": 1}[scheme], w_ptr, float(side),
+                           {"jacobi": 0, "ilu": 1}[mg_smoother])
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -282,6 +293,15 @@ class Problem:
         f = self._new() if f is None else f
         _check(_lib().bec_build_rhs(self._p, _dptr(u0, self.J, "u0"), _dptr(fsrc, self.U, "fsrc"),
                                     _dptr(f, self.U, "f")), "bec_build_rhs")
+        return f
+
+    def build_rhs_dirichlet(self, u0, fsrc, g, f=None):
+        """f with Dirichlet node values g ([N][nx+2][nx+2] on the device)."""
+        f = self._new() if f is None else f
+        _check(_lib().bec_build_rhs_dirichlet(self._p, _dptr(u0, self.J, "u0"),
+                                              _dptr(fsrc, self.U, "fsrc"),
+                                              _dptr(g, self.N * (self.nx + 2) ** 2, "g"),
+                                              _dptr(f, self.U, "f")), "bec_build_rhs_dirichlet")
         return f
 
     @staticmethod

@@ -211,6 +211,13 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   if (d->space == BEC_SPACE_Q1 && d->route != BEC_ROUTE_FST)
     return einval("Q1 elements need BEC_ROUTE_FST");
   if (d->space == BEC_SPACE_Q1 && d->dim == 3) return einval("Q1 elements are 1D or 2D");
+  if (d->route != BEC_ROUTE_MG && (d->wind != nullptr || (d->side != 0.0 && d->side != 1.0)))
+    return einval("wind and side need BEC_ROUTE_MG");
+  if (!(d->side >= 0.0) || !std::isfinite(d->side)) return einval("side must be finite and >= 0");
+  if (d->mg_smoother != BEC_MG_JACOBI && d->mg_smoother != BEC_MG_ILU)
+    return einval("mg_smoother must be BEC_MG_JACOBI or BEC_MG_ILU");
+  if (d->mg_smoother == BEC_MG_ILU && d->route != BEC_ROUTE_MG)
+    return einval("the ILU smoother needs BEC_ROUTE_MG");
   if (d->time_scheme != BEC_TIME_BDF1 && d->time_scheme != BEC_TIME_BDF2)
     return einval("time_scheme must be BEC_TIME_BDF1 or BEC_TIME_BDF2");
   if (d->time_scheme == BEC_TIME_BDF2 && (d->route != BEC_ROUTE_FST || d->dim == 3 || d->N < 4))
@@ -270,11 +277,13 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     p->mg.pre = d->mg_pre == 0 ? 1 : d->mg_pre;
     p->mg.post = (d->mg_pre == 0 && d->mg_post == 0) ? 1 : d->mg_post;
     p->mg.omega = d->mg_omega == 0.0 ? 0.8 : d->mg_omega;
-    chain(mg_setup(p, d->a_nodes));
+    p->mg.ilu = d->mg_smoother == BEC_MG_ILU;
+    chain(mg_setup(p, d->a_nodes, d->wind));
     if (d->route == BEC_ROUTE_LEARNED && s == BEC_OK)
       chain(net_setup(p, d->a_nodes, d->net_channels == 0 ? 32 : d->net_channels, d->net_fp32, 32));
   }
   p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
+  p->desc.wind = nullptr;
   if (d->precision == BEC_PC_FP32 && d->route == BEC_ROUTE_FST) {
     float* sc = nullptr;
     chain(dmalloc(&sc, (size_t)U));
@@ -426,6 +435,7 @@ bec_status bec_set_eps(bec_problem* p, double eps) {
   BEC_TRY(upload(t.lamf64, lam, p->stream));
   BEC_TRY(upload(t.lamf32, lam32, p->stream));
   if (t.rinv64) BEC_TRY(launch_rinv_table(p));
+  if (p->mg.ilu) BEC_TRY(mg_ilu_setup(p));
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
   p->eps = eps;
   return BEC_OK;
@@ -463,6 +473,17 @@ bec_status bec_build_rhs(bec_problem* p, const double* u0, const double* fsrc, d
   BEC_TRY(check_vec(fsrc));
   BEC_TRY(check_vec(f));
   return launch_build_rhs(p, u0, fsrc, f);
+}
+
+bec_status bec_build_rhs_dirichlet(bec_problem* p, const double* u0, const double* fsrc,
+                                   const double* g, double* f) {
+  if (p == nullptr) return einval("null problem");
+  if (p->bcoef == nullptr) return einval("bec_build_rhs_dirichlet needs BEC_ROUTE_MG");
+  BEC_TRY(check_vec(u0));
+  BEC_TRY(check_vec(fsrc));
+  BEC_TRY(check_vec(g));
+  BEC_TRY(check_vec(f));
+  return launch_build_rhs_dirichlet(p, u0, fsrc, g, f);
 }
 
 bec_status bec_gmres_solve(bec_problem* p, const double* f, double* u, const bec_gmres_opts* opts,

@@ -79,11 +79,13 @@ struct MgLevel {
   void* x = nullptr;    // [K][J] complex
   void* b = nullptr;
   void* r = nullptr;
+  void* dinv = nullptr; // [K][J] complex: 1 / D of the ILU smoother (BEC_MG_ILU)
 };
 
 struct MgState {
   int pre = 1, post = 1;
   double omega = 0.8;
+  int ilu = 0;          // smoother: 0 damped Jacobi, 1 ILU
   int K = 0;            // N/2 + 1 frequencies
   std::vector<MgLevel> lv;
 };
@@ -139,6 +141,8 @@ struct bec_problem {
   cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // loaded[2], solved[2]
   bec::Profiler prof;
   double* kcoef = nullptr;      // variable a: tau K row [centre, W, E, S, N] x J
+  double* bcoef = nullptr;      // multigrid route: -tau x the couplings of each point to
+                                // its W, E, S, N boundary nodes, [4][J] (0 if interior)
   bec::MgState mg;              // BEC_ROUTE_MG hierarchy
   bec::NetState* net = nullptr;  // BEC_ROUTE_LEARNED network
   std::vector<bec::IterGraph> graphs;   // per Arnoldi index j (batched solves)
@@ -241,7 +245,12 @@ bec_status set_tiles(bec_problem* p, int rows, int cols, int time);
 
 // ---- multigrid route (bec_mg.cu, bec_time.cu)
 // Builds the coefficient rows, the Galerkin hierarchy and its buffers.
-bec_status mg_setup(bec_problem* p, const double* a_nodes);
+bec_status mg_setup(bec_problem* p, const double* a_nodes, const double* wind);
+// the ILU smoother's 1 / D for every level and frequency (after the eps tables)
+bec_status mg_ilu_setup(bec_problem* p);
+// f = tau (fsrc - K_b g) + u0 in slice 1 (multigrid route)
+bec_status launch_build_rhs_dirichlet(bec_problem* p, const double* u0, const double* fsrc,
+                                      const double* g, double* f);
 void mg_free(bec_problem* p);
 // One V-cycle for every frequency: level-0 b -> level-0 x.
 bec_status mg_vcycle(bec_problem* p);

@@ -7,14 +7,20 @@
 //   * M_0 = I and K_0 = the conservative 5-point -div(a grad) / h^2;
 //   * P_l bilinear interpolation, R_l = P_l^T / 4 (full weighting);
 //   * M_{l+1} = R_l M_l P_l and K_{l+1} = R_l K_l P_l (Galerkin, 9-point);
-//   * damped Jacobi, x <- x + omega D^{-1} (b - B x), D = diag(B);
+//   * damped Jacobi, x <- x + omega D^{-1} (b - B x), D = diag(B), or the ILU
+//     smoother x <- x + M^{-1} (b - B x), M = (D + L) D^{-1} (D + U) with L, U
+//     the strictly lower and upper parts of B and D chosen so that diag(M) =
+//     diag(B) (ILU(0) on the 5-point finest grid);
 //   * the 1 x 1 level is solved exactly.
+// K_0 may also carry a convection term w . grad u by first-order upwind
+// differences (Example 3 of Sec. 5, whose multigrid smooths with ILU).
 // The Galerkin stencils are real and do not depend on k; they are built once
 // on the host and read by every frequency.  Each thread owns one grid point
 // and walks a chunk of frequencies with its 18 stencil coefficients in
 // registers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -211,6 +217,174 @@ __global__ void mg_coarsest_kernel(v2_t<T>* __restrict__ x, const v2_t<T>* __res
   x[k] = {c.x * inv, c.y * inv};
 }
 
+// ---------------------------------------------------------------- ILU smoother
+// The triangular recurrences of M run over the wavefronts t = x + 2y of a
+// level's grid (x fastest): every lower neighbour of (x, y) (W, SE on t - 1;
+// S on t - 2; SW on t - 3) lies on an earlier wavefront, every upper one (E,
+// NW on t + 1; N on t + 2; NE on t + 3) on a later one.  One block per
+// frequency walks the 3 (m - 1) + 1 wavefronts; a thread owns the points of
+// a wavefront by their row y, and the values of the last three wavefronts
+// stay in a shared-memory ring indexed by [t mod 4][y].
+constexpr int kIluThreads = 128;
+
+// entry s (stencil slot (dy+1)*3 + dx+1) of row q of lambda M + tau K
+template <typename T>
+__device__ __forceinline__ v2_t<T> ilu_coef(const MgArgs<T>& a, int s, long long q, v2_t<T> lam) {
+  const T sm = a.SM[(long long)s * a.J + q], sk = a.SK[(long long)s * a.J + q];
+  return {lam.x * sm + a.tau * sk, lam.y * sm};
+}
+
+template <typename T>
+__device__ __forceinline__ v2_t<T> cinv(v2_t<T> d) {
+  const T s = T(1) / (d.x * d.x + d.y * d.y);
+  return {d.x * s, -d.y * s};
+}
+
+// 1/d_i, d_i = b_ii - sum over the lower neighbours j of b_ij b_ji / d_j
+template <typename T>
+__global__ void __launch_bounds__(kIluThreads)
+ilu_setup_kernel(v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
+  using V = v2_t<T>;
+  extern __shared__ __align__(16) unsigned char ilu_smem[];
+  V* ring = reinterpret_cast<V*>(ilu_smem);     // [4][m]
+  const int k = blockIdx.x, m = a.m;
+  const V lam = a.lam[k];
+  V* dk = dinv + (long long)k * a.J;
+  for (int t = 0; t <= 3 * (m - 1); ++t) {
+    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
+    const int yhi = min(m - 1, t / 2);
+    for (int y = ylo + (int)threadIdx.x; y <= yhi; y += blockDim.x) {
+      const int x = t - 2 * y;
+      const long long q = (long long)y * m + x;
+      V d = ilu_coef(a, 4, q, lam);
+      // (slot at i, slot at j, neighbour offset, ring wavefront, ring row)
+      if (x > 0) {                                   // W
+        const V p = cmul(ilu_coef(a, 3, q, lam), ilu_coef(a, 5, q - 1, lam));
+        const V e = cmul(p, ring[((t - 1) & 3) * m + y]);
+        d.x -= e.x;
+        d.y -= e.y;
+      }
+      if (y > 0) {
+        const V p = cmul(ilu_coef(a, 1, q, lam), ilu_coef(a, 7, q - m, lam));   // S
+        const V e = cmul(p, ring[((t - 2) & 3) * m + y - 1]);
+        d.x -= e.x;
+        d.y -= e.y;
+        if (x + 1 < m) {                             // SE
+          const V p2 = cmul(ilu_coef(a, 2, q, lam), ilu_coef(a, 6, q - m + 1, lam));
+          const V e2 = cmul(p2, ring[((t - 1) & 3) * m + y - 1]);
+          d.x -= e2.x;
+          d.y -= e2.y;
+        }
+        if (x > 0) {                                 // SW
+          const V p3 = cmul(ilu_coef(a, 0, q, lam), ilu_coef(a, 8, q - m - 1, lam));
+          const V e3 = cmul(p3, ring[((t - 3) & 3) * m + y - 1]);
+          d.x -= e3.x;
+          d.y -= e3.y;
+        }
+      }
+      const V di = cinv<T>(d);
+      ring[(t & 3) * m + y] = di;
+      dk[q] = di;
+    }
+    __syncthreads();
+  }
+}
+
+// One ILU smoothing step for every frequency: z = M^{-1} rin, then
+// x = z (ACC false) or x += z (ACC true).  rin may alias work; work holds the
+// forward result y between the two sweeps.
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(kIluThreads)
+ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
+                 const v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
+  using V = v2_t<T>;
+  extern __shared__ __align__(16) unsigned char ilu_smem[];
+  V* ring = reinterpret_cast<V*>(ilu_smem);     // [4][m]
+  const int k = blockIdx.x, m = a.m;
+  const V lam = a.lam[k];
+  const long long base = (long long)k * a.J;
+  const V* dk = dinv + base;
+  const V* rk = rin + base;
+  V* wk = work + base;
+  V* xk = x + base;
+  const int tmax = 3 * (m - 1);
+  // forward: (D + L) y = rin
+  for (int t = 0; t <= tmax; ++t) {
+    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
+    const int yhi = min(m - 1, t / 2);
+    for (int y = ylo + (int)threadIdx.x; y <= yhi; y += blockDim.x) {
+      const int xx = t - 2 * y;
+      const long long q = (long long)y * m + xx;
+      V acc = rk[q];
+      if (xx > 0) {
+        const V e = cmul(ilu_coef(a, 3, q, lam), ring[((t - 1) & 3) * m + y]);
+        acc.x -= e.x;
+        acc.y -= e.y;
+      }
+      if (y > 0) {
+        const V e = cmul(ilu_coef(a, 1, q, lam), ring[((t - 2) & 3) * m + y - 1]);
+        acc.x -= e.x;
+        acc.y -= e.y;
+        if (xx + 1 < m) {
+          const V e2 = cmul(ilu_coef(a, 2, q, lam), ring[((t - 1) & 3) * m + y - 1]);
+          acc.x -= e2.x;
+          acc.y -= e2.y;
+        }
+        if (xx > 0) {
+          const V e3 = cmul(ilu_coef(a, 0, q, lam), ring[((t - 3) & 3) * m + y - 1]);
+          acc.x -= e3.x;
+          acc.y -= e3.y;
+        }
+      }
+      const V yv = cmul(acc, dk[q]);
+      ring[(t & 3) * m + y] = yv;
+      wk[q] = yv;
+    }
+    __syncthreads();
+  }
+  // backward: (D + U) z = D y, i.e. z = y - D^{-1} U z
+  for (int t = tmax; t >= 0; --t) {
+    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
+    const int yhi = min(m - 1, t / 2);
+    for (int y = ylo + (int)threadIdx.x; y <= yhi; y += blockDim.x) {
+      const int xx = t - 2 * y;
+      const long long q = (long long)y * m + xx;
+      V acc = {0, 0};
+      if (xx + 1 < m) {                               // E
+        const V e = cmul(ilu_coef(a, 5, q, lam), ring[((t + 1) & 3) * m + y]);
+        acc.x += e.x;
+        acc.y += e.y;
+      }
+      if (y + 1 < m) {
+        const V e = cmul(ilu_coef(a, 7, q, lam), ring[((t + 2) & 3) * m + y + 1]);   // N
+        acc.x += e.x;
+        acc.y += e.y;
+        if (xx > 0) {                                 // NW
+          const V e2 = cmul(ilu_coef(a, 6, q, lam), ring[((t + 1) & 3) * m + y + 1]);
+          acc.x += e2.x;
+          acc.y += e2.y;
+        }
+        if (xx + 1 < m) {                             // NE
+          const V e3 = cmul(ilu_coef(a, 8, q, lam), ring[((t + 3) & 3) * m + y + 1]);
+          acc.x += e3.x;
+          acc.y += e3.y;
+        }
+      }
+      const V c = cmul(acc, dk[q]);
+      const V yv = wk[q];
+      const V z = {yv.x - c.x, yv.y - c.y};
+      ring[(t & 3) * m + y] = z;
+      if (ACC) {
+        const V xo = xk[q];
+        xk[q] = {xo.x + z.x, xo.y + z.y};
+      } else {
+        xk[q] = z;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- host side
 // Coarse 9-point stencil Ac = R Af P with R = P^T / 4 (layout [s][J], s =
 // (dy+1)*3 + (dx+1)).  Fine point f of a 1D grid of mf points belongs to
@@ -287,11 +461,88 @@ const char* const kSmoothNames[] = BEC_LV_NAMES("mg_smooth_kernel");
 const char* const kResidNames[] = BEC_LV_NAMES("mg_residual_kernel");
 const char* const kRestrictNames[] = BEC_LV_NAMES("mg_restrict_kernel");
 const char* const kProlongNames[] = BEC_LV_NAMES("mg_prolong_add_kernel");
+const char* const kIluSweepNames[] = BEC_LV_NAMES("ilu_sweep_kernel");
+const char* const kIluSetupNames[] = BEC_LV_NAMES("ilu_setup_kernel");
 #undef BEC_LV_NAMES
 
 dim3 mg_grid(long long J, int K) {
   return dim3((unsigned)((J + kMgThreads - 1) / kMgThreads),
               (unsigned)((K + kFreqChunk - 1) / kFreqChunk));
+}
+
+#define BEC_TRY_MG(expr)         \
+  do {                           \
+    bec_status _s = (expr);      \
+    if (_s != BEC_OK) return _s; \
+  } while (0)
+
+size_t ilu_smem_bytes(int m, size_t vsize) { return 4 * (size_t)m * vsize; }
+
+// one ILU smoothing step on level l: x = M^{-1} rin (acc false) or x += M^{-1} rin;
+// r is the work array (rin may be r)
+template <typename T>
+bec_status ilu_sweep(bec_problem* p, MgLevel& c, int l, const void* rin, bool acc) {
+  using V = v2_t<T>;
+  const MgArgs<T> a = level_args<T>(p, c);
+  const size_t smem = ilu_smem_bytes(c.m, sizeof(V));
+  BEC_LAUNCH_BEGIN(p);
+  if (acc)
+    ilu_sweep_kernel<T, true><<<p->mg.K, kIluThreads, smem, p->stream>>>(
+        static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
+        static_cast<const V*>(c.dinv), a);
+  else
+    ilu_sweep_kernel<T, false><<<p->mg.K, kIluThreads, smem, p->stream>>>(
+        static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
+        static_cast<const V*>(c.dinv), a);
+  BEC_LAUNCH_CHECK(p, kIluSweepNames[l]);
+  return BEC_OK;
+}
+
+template <typename T>
+bec_status ilu_setup_t(bec_problem* p) {
+  using V = v2_t<T>;
+  // the ring of the largest grid may exceed the default 48 KB
+  const int big = (int)ilu_smem_bytes(p->mg.lv[0].m, sizeof(V));
+  if (big > 48 * 1024) {
+    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_setup_kernel<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_kernel<T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_kernel<T, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  }
+  for (size_t l = 0; l + 1 < p->mg.lv.size(); ++l) {
+    MgLevel& c = p->mg.lv[l];
+    BEC_LAUNCH_BEGIN(p);
+    ilu_setup_kernel<T><<<p->mg.K, kIluThreads, ilu_smem_bytes(c.m, sizeof(V)), p->stream>>>(
+        static_cast<V*>(c.dinv), level_args<T>(p, c));
+    BEC_LAUNCH_CHECK(p, kIluSetupNames[l]);
+  }
+  return BEC_OK;
+}
+
+// f = tau fsrc + sum over the W, E, S, N boundary nodes of bcoef g (+ u0 in slice 1)
+__global__ void build_rhs_dirichlet_kernel(const double* __restrict__ u0,
+                                           const double* __restrict__ fsrc,
+                                           const double* __restrict__ g,
+                                           const double* __restrict__ bcoef,
+                                           double* __restrict__ f, int m, int N, double tau) {
+  const long long J = (long long)m * m, U = J * N;
+  const long long n2 = (long long)(m + 2) * (m + 2);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < U;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long n = i / J, q = i - n * J;
+    const int iy = (int)(q / m), ix = (int)(q - (long long)iy * m);
+    const double* gn = g + n * n2;
+    const long long node = (long long)(iy + 1) * (m + 2) + (ix + 1);
+    double v = tau * fsrc[i];
+    if (ix == 0) v = fma(bcoef[q], gn[node - 1], v);
+    if (ix == m - 1) v = fma(bcoef[J + q], gn[node + 1], v);
+    if (iy == 0) v = fma(bcoef[2 * J + q], gn[node - (m + 2)], v);
+    if (iy == m - 1) v = fma(bcoef[3 * J + q], gn[node + (m + 2)], v);
+    if (n == 0) v += u0[q];
+    f[i] = v;
+  }
 }
 
 template <typename T>
@@ -304,16 +555,27 @@ bec_status vcycle_t(bec_problem* p) {
     MgLevel& c = lv[l];
     const MgArgs<T> a = level_args<T>(p, c);
     const dim3 g = mg_grid(c.J, K);
-    BEC_LAUNCH_BEGIN(p);
-    mg_smooth_kernel<T, true><<<g, kMgThreads, 0, p->stream>>>(
-        static_cast<V*>(c.x), nullptr, static_cast<const V*>(c.b), a);
-    BEC_LAUNCH_CHECK(p, kSmooth0Names[l]);
-    for (int s = 1; s < p->mg.pre; ++s) {
+    if (p->mg.ilu) {
+      BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.b, false));        // x = M^{-1} b
+      for (int s = 1; s < p->mg.pre; ++s) {
+        BEC_LAUNCH_BEGIN(p);
+        mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
+            static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
+        BEC_LAUNCH_CHECK(p, kResidNames[l]);
+        BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.r, true));
+      }
+    } else {
       BEC_LAUNCH_BEGIN(p);
-      mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
-          static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
-      BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
-      std::swap(c.x, c.r);
+      mg_smooth_kernel<T, true><<<g, kMgThreads, 0, p->stream>>>(
+          static_cast<V*>(c.x), nullptr, static_cast<const V*>(c.b), a);
+      BEC_LAUNCH_CHECK(p, kSmooth0Names[l]);
+      for (int s = 1; s < p->mg.pre; ++s) {
+        BEC_LAUNCH_BEGIN(p);
+        mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
+            static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
+        BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
+        std::swap(c.x, c.r);
+      }
     }
     BEC_LAUNCH_BEGIN(p);
     mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
@@ -342,6 +604,14 @@ bec_status vcycle_t(bec_problem* p) {
     BEC_LAUNCH_CHECK(p, kProlongNames[l]);
     const MgArgs<T> a = level_args<T>(p, c);
     for (int s = 0; s < p->mg.post; ++s) {
+      if (p->mg.ilu) {
+        BEC_LAUNCH_BEGIN(p);
+        mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
+            static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
+        BEC_LAUNCH_CHECK(p, kResidNames[l]);
+        BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.r, true));
+        continue;
+      }
       BEC_LAUNCH_BEGIN(p);
       mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
           static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
@@ -354,9 +624,11 @@ bec_status vcycle_t(bec_problem* p) {
 
 }  // namespace
 
-bec_status mg_setup(bec_problem* p, const double* a_nodes) {
+bec_status mg_setup(bec_problem* p, const double* a_nodes, const double* wind) {
   const int m = p->m;
-  const double h2 = p->h * p->h;
+  const double side = p->desc.side == 0.0 ? 1.0 : p->desc.side;
+  const double hp = side / (m + 1);   // physical spacing
+  const double h2 = hp * hp;
   // node coefficients (constant a when a_nodes is null)
   const int n2 = m + 2;
   std::vector<double> an((size_t)n2 * n2, p->a);
@@ -367,39 +639,65 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes) {
       set_error("a_nodes must be finite and > 0");
       return BEC_EINVAL;
     }
-  // level 0: M = I, K = conservative 5-point with face means; also the tau K
-  // row for the stencil kernels: [centre, W, E, S, N] x J
+  if (wind != nullptr)
+    for (size_t i = 0; i < 2 * an.size(); ++i)
+      if (!std::isfinite(wind[i])) {
+        set_error("wind must be finite");
+        return BEC_EINVAL;
+      }
+  // level 0: M = I, K = conservative 5-point with face means, plus the upwind
+  // convection w_x (u - u_W)/h where w_x > 0, w_x (u_E - u)/h where w_x < 0
+  // (likewise in y) when a wind is given; also the tau K row for the stencil
+  // kernels, [centre, W, E, S, N] x J (off-diagonals negated), and -tau x the
+  // couplings to boundary nodes for the Dirichlet right-hand side
   const long long J = (long long)m * m;
-  std::vector<double> SM0(9 * J, 0.0), SK0(9 * J, 0.0), kc(5 * J, 0.0);
+  std::vector<double> SM0(9 * J, 0.0), SK0(9 * J, 0.0), kc(5 * J, 0.0), bc(4 * J, 0.0);
   for (int iy = 0; iy < m; ++iy)
     for (int ix = 0; ix < m; ++ix) {
       const long long q = (long long)iy * m + ix;
       const int gy = iy + 1, gx = ix + 1;
-      const double ac = an[(size_t)gy * n2 + gx];
-      const double aw = 0.5 * (ac + an[(size_t)gy * n2 + gx - 1]);
-      const double ae = 0.5 * (ac + an[(size_t)gy * n2 + gx + 1]);
-      const double as = 0.5 * (ac + an[(size_t)(gy - 1) * n2 + gx]);
-      const double anf = 0.5 * (ac + an[(size_t)(gy + 1) * n2 + gx]);
+      const size_t node = (size_t)gy * n2 + gx;
+      const double ac = an[node];
+      const double aw = 0.5 * (ac + an[node - 1]);
+      const double ae = 0.5 * (ac + an[node + 1]);
+      const double as = 0.5 * (ac + an[node - n2]);
+      const double anf = 0.5 * (ac + an[node + n2]);
+      const double wx = wind ? wind[node] : 0.0;
+      const double wy = wind ? wind[an.size() + node] : 0.0;
+      // row entries: centre, W, E, S, N
+      const double cW = -aw / h2 - std::max(wx, 0.0) / hp;
+      const double cE = -ae / h2 + std::min(wx, 0.0) / hp;
+      const double cS = -as / h2 - std::max(wy, 0.0) / hp;
+      const double cN = -anf / h2 + std::min(wy, 0.0) / hp;
+      const double cC = (aw + ae + as + anf) / h2 + (std::fabs(wx) + std::fabs(wy)) / hp;
       SM0[4 * J + q] = 1.0;
-      SK0[4 * J + q] = (aw + ae + as + anf) / h2;
-      if (ix > 0) SK0[3 * J + q] = -aw / h2;
-      if (ix < m - 1) SK0[5 * J + q] = -ae / h2;
-      if (iy > 0) SK0[1 * J + q] = -as / h2;
-      if (iy < m - 1) SK0[7 * J + q] = -anf / h2;
-      kc[0 * J + q] = p->tau * (aw + ae + as + anf) / h2;
-      kc[1 * J + q] = ix > 0 ? p->tau * aw / h2 : 0.0;
-      kc[2 * J + q] = ix < m - 1 ? p->tau * ae / h2 : 0.0;
-      kc[3 * J + q] = iy > 0 ? p->tau * as / h2 : 0.0;
-      kc[4 * J + q] = iy < m - 1 ? p->tau * anf / h2 : 0.0;
+      SK0[4 * J + q] = cC;
+      if (ix > 0) SK0[3 * J + q] = cW;
+      if (ix < m - 1) SK0[5 * J + q] = cE;
+      if (iy > 0) SK0[1 * J + q] = cS;
+      if (iy < m - 1) SK0[7 * J + q] = cN;
+      kc[0 * J + q] = p->tau * cC;
+      kc[1 * J + q] = ix > 0 ? -p->tau * cW : 0.0;
+      kc[2 * J + q] = ix < m - 1 ? -p->tau * cE : 0.0;
+      kc[3 * J + q] = iy > 0 ? -p->tau * cS : 0.0;
+      kc[4 * J + q] = iy < m - 1 ? -p->tau * cN : 0.0;
+      bc[0 * J + q] = ix == 0 ? -p->tau * cW : 0.0;
+      bc[1 * J + q] = ix == m - 1 ? -p->tau * cE : 0.0;
+      bc[2 * J + q] = iy == 0 ? -p->tau * cS : 0.0;
+      bc[3 * J + q] = iy == m - 1 ? -p->tau * cN : 0.0;
     }
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->kcoef), kc.size() * sizeof(double));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    p->kcoef = nullptr;
-    set_error("cudaMalloc (coefficients)");
-    return BEC_ENOMEM;
+  for (int which = 0; which < 2; ++which) {
+    double** dst = which == 0 ? &p->kcoef : &p->bcoef;
+    const std::vector<double>& src = which == 0 ? kc : bc;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *dst = nullptr;
+      set_error("cudaMalloc (coefficients)");
+      return BEC_ENOMEM;
+    }
+    BEC_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
-  BEC_CUDA_TRY(cudaMemcpy(p->kcoef, kc.data(), kc.size() * sizeof(double), cudaMemcpyHostToDevice));
 
   const bool fp64 = p->desc.precision == BEC_PC_FP64;
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
@@ -414,8 +712,9 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes) {
     bec_status s = fp64 ? upload_stencil<double>(&L.SM, SM) : upload_stencil<float>(&L.SM, SM);
     if (s == BEC_OK) s = fp64 ? upload_stencil<double>(&L.SK, SK) : upload_stencil<float>(&L.SK, SK);
     const size_t bytes = (size_t)p->mg.K * L.J * csz;
-    void* bufs[3] = {nullptr, nullptr, nullptr};
-    for (int i = 0; i < 3 && s == BEC_OK; ++i) {
+    void* bufs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const int nbuf = (p->mg.ilu && ml > 1) ? 4 : 3;   // + 1/D of the ILU smoother
+    for (int i = 0; i < nbuf && s == BEC_OK; ++i) {
       if (cudaMalloc(&bufs[i], bytes) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc (multigrid levels)");
@@ -425,6 +724,7 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes) {
     L.x = bufs[0];
     L.b = bufs[1];
     L.r = bufs[2];
+    L.dinv = bufs[3];
     p->mg.lv.push_back(L);
     if (s != BEC_OK) return s;
     if (ml == 1) break;
@@ -441,13 +741,15 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes) {
 
 void mg_free(bec_problem* p) {
   for (MgLevel& L : p->mg.lv) {
-    void* ptrs[] = {L.SM, L.SK, L.x, L.b, L.r};
+    void* ptrs[] = {L.SM, L.SK, L.x, L.b, L.r, L.dinv};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
   p->mg.lv.clear();
   if (p->kcoef) cudaFree(p->kcoef);
   p->kcoef = nullptr;
+  if (p->bcoef) cudaFree(p->bcoef);
+  p->bcoef = nullptr;
 }
 
 bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void* b) {
@@ -481,6 +783,20 @@ bec_status mg_smooth_level0(bec_problem* p, void* xo, const void* x, const void*
         level_args<float>(p, L));
   }
   BEC_LAUNCH_CHECK(p, "mg_smooth_kernel[l0]");
+  return BEC_OK;
+}
+
+bec_status mg_ilu_setup(bec_problem* p) {
+  if (p->desc.precision == BEC_PC_FP64) return ilu_setup_t<double>(p);
+  return ilu_setup_t<float>(p);
+}
+
+bec_status launch_build_rhs_dirichlet(bec_problem* p, const double* u0, const double* fsrc,
+                                      const double* g, double* f) {
+  BEC_LAUNCH_BEGIN(p);
+  build_rhs_dirichlet_kernel<<<4 * 152, 256, 0, p->stream>>>(u0, fsrc, g, p->bcoef, f, p->m, p->N,
+                                                             p->tau);
+  BEC_LAUNCH_CHECK(p, "build_rhs_dirichlet_kernel");
   return BEC_OK;
 }
 

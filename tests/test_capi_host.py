@@ -108,8 +108,25 @@ def test_allocate_rejects_invalid_time_schemes(lib):
         assert b"BDF2" in lib.bec_last_error() or b"time_scheme" in lib.bec_last_error()
 
 
+def test_allocate_rejects_invalid_convection_requests(lib):
+    import numpy as np
+    from paper_2002_01108_gb300.bec import ProblemDesc
+    out = ctypes.c_void_p()
+    w = np.zeros(2 * 65 * 65)
+    # a wind, a side length or the ILU smoother off the multigrid route; an
+    # unknown smoother; a negative side
+    for route, wind, side, smoother in ((0, w.ctypes.data, 0.0, 0), (0, None, 2.0, 0),
+                                        (0, None, 0.0, 1), (1, None, 0.0, 5), (1, None, -1.0, 0),
+                                        (2, None, 0.0, 1)):
+        d = ProblemDesc(2, 63, 63, 64, 1.0, 1.0, route, 1 if route == 2 else 0, 10, 0, 0, None,
+                        0, 0, 0.0, 0, 0, 0, 0, wind, side, smoother)
+        assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (route, side)
+        assert out.value is None
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.bec_set_eps(None, 0.5) == 1
+    assert lib.bec_build_rhs_dirichlet(None, None, None, None, None) == 1
     assert lib.bec_apply_A(None, None, None) == 1
     assert lib.bec_apply_Pinv(None, None, None) == 1
     assert lib.bec_gmres_solve(None, None, None, None, None) == 1
