@@ -134,7 +134,8 @@ def parse():
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip measuring the other preconditioner form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32", "learned_bf16"),
+    ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32", "learned_bf16",
+                                           "ilu_fp32"),
                     default=None,
                     help="run a small bounded case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -521,6 +522,9 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
                 "flops_per_apply": K * net_fwd_flops(m), "avg_launch_ms": avg,
                 "other_network_kernels_ms": {k: round(v[1], 3) for k, v in kernels.items()
                                              if k.startswith("net_") and k != dom}}
+    elif dom == "stencil_dots_kernel":
+        # the FP64 Krylov operator dominates: bound by the FP64 pipe
+        roof = roofline(precision, kernels, U, info["iters"])
     elif base in MG_WORDS:
         lvl = int(dom.split("[l")[1].rstrip("]"))
         ml = m
@@ -531,7 +535,7 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
     else:
         units = U
         bpu, fpu = 8 + 0.5 * word, 5.0 * LOG2T / 2
-    if route != "learned":
+    if route != "learned" and dom != "stencil_dots_kernel":
         peaks, src = measured_peaks()
         if precision == "fp64":
             ach = fpu * units / (avg / 1e3) / 1e12
@@ -620,12 +624,11 @@ def measure_convection(args, form):
     f = prob.build_rhs_dirichlet(torch.from_numpy(u0).cuda(), torch.from_numpy(fs).cuda(),
                                  torch.from_numpy(g).cuda())
     u = torch.empty_like(f)
-    kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=True)
-    for _ in range(max(1, min(args.warmup, 2))):
-        prob.gmres_solve(f, u, **kw)
+    kw = dict(restart=RESTART, rtol=RTOL, maxit=100, flexible=True)
+    prob.gmres_solve(f, u, **kw)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 2))
     ev0.record(prob.stream)
     for _ in range(steps):
         _, info = prob.gmres_solve(f, u, **kw)
@@ -638,7 +641,8 @@ def measure_convection(args, form):
     U = prob.U
     prob.close()
     return {"value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iters"],
-            "true_relres": info["true_relres"], "timed_solves": steps,
+            "true_relres": info["true_relres"], "converged": info["converged"],
+            "timed_solves": steps,
             "kernels": dict(list(kernel_table(kernels).items())[:6])}
 
 
@@ -833,6 +837,22 @@ def run_ncu_case(which: str):
     from paper_2002_01108_gb300 import build as bec_build
     from workloads import heat_case_2d
     bec_build.build()
+    if which == "ilu_fp32":
+        # Example 3 at 255^2 x 256 on the ILU multigrid route, two-vector
+        # Krylov basis, three P_eps^{-1} applies
+        from workloads import circulating_wind_case
+        wind, g, u0, fs = circulating_wind_case(M_SIDE, N_STEPS)
+        with Problem(2, M_SIDE, N_STEPS, a=1.0 / 200.0, route="mg", precision="fp32", wind=wind,
+                     side=2.0, mg_smoother="ilu", flexible=True, max_restart=2) as p:
+            p.set_eps(min(0.5, 0.5 / N_STEPS))
+            f = p.build_rhs_dirichlet(torch.from_numpy(u0).cuda(), torch.from_numpy(fs).cuda(),
+                                      torch.from_numpy(g).cuda())
+            z = torch.empty_like(f)
+            for _ in range(3):
+                p.apply_Pinv(f, z)
+            torch.cuda.synchronize()
+        print(f"ncu case {which} done")
+        return 0
     if which == "learned_bf16":
         # the learned route at 255^2 with N = 64 (33 frequencies: one batch of
         # 32 and one of 1), untrained weights, three P_eps^{-1} applies

@@ -290,11 +290,52 @@ ilu_setup_kernel(v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
   }
 }
 
+// The independent operands of one point of a wavefront: its row y (thread
+// tid owns y = ylo(t) + tid, one point per thread: the block has at least
+// ceil(m / 2) threads), the right-hand side or forward value, 1/d, and the
+// real M and K entries towards its four lower (forward) or upper (backward)
+// neighbours.  They are loaded three wavefronts ahead, so that their latency
+// (the [K][J] arrays exceed L2) overlaps the dependent work and barriers of
+// the wavefronts before.
+template <typename T>
+struct IluPoint {
+  v2_t<T> v, d, xo;
+  T sm[4], sk[4];
+  int x, y;
+  bool ok;
+};
+
+template <typename T, bool FWD, bool ACC>
+__device__ __forceinline__ void ilu_load(IluPoint<T>& P, int t, const MgArgs<T>& a,
+                                         const v2_t<T>* __restrict__ src,
+                                         const v2_t<T>* __restrict__ dk,
+                                         const v2_t<T>* __restrict__ xk) {
+  const int m = a.m;
+  const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
+  const int yhi = min(m - 1, t / 2);
+  P.y = ylo + (int)threadIdx.x;
+  P.ok = t >= 0 && t <= 3 * (m - 1) && P.y <= yhi;
+  if (!P.ok) return;
+  P.x = t - 2 * P.y;
+  const long long q = (long long)P.y * m + P.x;
+  // forward: W, S, SE, SW; backward: E, N, NW, NE
+  constexpr int s0 = FWD ? 3 : 5, s1 = FWD ? 1 : 7, s2 = FWD ? 2 : 6, s3 = FWD ? 0 : 8;
+  const int sl[4] = {s0, s1, s2, s3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    P.sm[i] = a.SM[(long long)sl[i] * a.J + q];
+    P.sk[i] = a.SK[(long long)sl[i] * a.J + q];
+  }
+  P.v = src[q];
+  P.d = dk[q];
+  if (!FWD && ACC) P.xo = xk[q];
+}
+
 // One ILU smoothing step for every frequency: z = M^{-1} rin, then
 // x = z (ACC false) or x += z (ACC true).  rin may alias work; work holds the
 // forward result y between the two sweeps.
 template <typename T, bool ACC>
-__global__ void __launch_bounds__(kIluThreads)
+__global__ void __launch_bounds__(512)
 ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
                  const v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
   using V = v2_t<T>;
@@ -308,78 +349,84 @@ ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
   V* wk = work + base;
   V* xk = x + base;
   const int tmax = 3 * (m - 1);
+  auto coefv = [&](T sm, T sk) -> V { return {lam.x * sm + a.tau * sk, lam.y * sm}; };
   // forward: (D + L) y = rin
+  IluPoint<T> p0, p1, p2, cur;
+  ilu_load<T, true, ACC>(p0, 0, a, rk, dk, xk);
+  ilu_load<T, true, ACC>(p1, 1, a, rk, dk, xk);
+  ilu_load<T, true, ACC>(p2, 2, a, rk, dk, xk);
   for (int t = 0; t <= tmax; ++t) {
-    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
-    const int yhi = min(m - 1, t / 2);
-    for (int y = ylo + (int)threadIdx.x; y <= yhi; y += blockDim.x) {
-      const int xx = t - 2 * y;
-      const long long q = (long long)y * m + xx;
-      V acc = rk[q];
-      if (xx > 0) {
-        const V e = cmul(ilu_coef(a, 3, q, lam), ring[((t - 1) & 3) * m + y]);
+    cur = p0;
+    p0 = p1;
+    p1 = p2;
+    ilu_load<T, true, ACC>(p2, t + 3, a, rk, dk, xk);
+    if (cur.ok) {
+      const int y = cur.y, xx = cur.x;
+      V acc = cur.v;
+      if (xx > 0) {                                   // W
+        const V e = cmul(coefv(cur.sm[0], cur.sk[0]), ring[((t - 1) & 3) * m + y]);
         acc.x -= e.x;
         acc.y -= e.y;
       }
       if (y > 0) {
-        const V e = cmul(ilu_coef(a, 1, q, lam), ring[((t - 2) & 3) * m + y - 1]);
+        const V e = cmul(coefv(cur.sm[1], cur.sk[1]), ring[((t - 2) & 3) * m + y - 1]);   // S
         acc.x -= e.x;
         acc.y -= e.y;
-        if (xx + 1 < m) {
-          const V e2 = cmul(ilu_coef(a, 2, q, lam), ring[((t - 1) & 3) * m + y - 1]);
+        if (xx + 1 < m) {                             // SE
+          const V e2 = cmul(coefv(cur.sm[2], cur.sk[2]), ring[((t - 1) & 3) * m + y - 1]);
           acc.x -= e2.x;
           acc.y -= e2.y;
         }
-        if (xx > 0) {
-          const V e3 = cmul(ilu_coef(a, 0, q, lam), ring[((t - 3) & 3) * m + y - 1]);
+        if (xx > 0) {                                 // SW
+          const V e3 = cmul(coefv(cur.sm[3], cur.sk[3]), ring[((t - 3) & 3) * m + y - 1]);
           acc.x -= e3.x;
           acc.y -= e3.y;
         }
       }
-      const V yv = cmul(acc, dk[q]);
+      const V yv = cmul(acc, cur.d);
       ring[(t & 3) * m + y] = yv;
-      wk[q] = yv;
+      wk[(long long)y * m + xx] = yv;
     }
     __syncthreads();
   }
   // backward: (D + U) z = D y, i.e. z = y - D^{-1} U z
+  ilu_load<T, false, ACC>(p0, tmax, a, wk, dk, xk);
+  ilu_load<T, false, ACC>(p1, tmax - 1, a, wk, dk, xk);
+  ilu_load<T, false, ACC>(p2, tmax - 2, a, wk, dk, xk);
   for (int t = tmax; t >= 0; --t) {
-    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
-    const int yhi = min(m - 1, t / 2);
-    for (int y = ylo + (int)threadIdx.x; y <= yhi; y += blockDim.x) {
-      const int xx = t - 2 * y;
-      const long long q = (long long)y * m + xx;
+    cur = p0;
+    p0 = p1;
+    p1 = p2;
+    ilu_load<T, false, ACC>(p2, t - 3, a, wk, dk, xk);
+    if (cur.ok) {
+      const int y = cur.y, xx = cur.x;
       V acc = {0, 0};
       if (xx + 1 < m) {                               // E
-        const V e = cmul(ilu_coef(a, 5, q, lam), ring[((t + 1) & 3) * m + y]);
+        const V e = cmul(coefv(cur.sm[0], cur.sk[0]), ring[((t + 1) & 3) * m + y]);
         acc.x += e.x;
         acc.y += e.y;
       }
       if (y + 1 < m) {
-        const V e = cmul(ilu_coef(a, 7, q, lam), ring[((t + 2) & 3) * m + y + 1]);   // N
+        const V e = cmul(coefv(cur.sm[1], cur.sk[1]), ring[((t + 2) & 3) * m + y + 1]);   // N
         acc.x += e.x;
         acc.y += e.y;
         if (xx > 0) {                                 // NW
-          const V e2 = cmul(ilu_coef(a, 6, q, lam), ring[((t + 1) & 3) * m + y + 1]);
+          const V e2 = cmul(coefv(cur.sm[2], cur.sk[2]), ring[((t + 1) & 3) * m + y + 1]);
           acc.x += e2.x;
           acc.y += e2.y;
         }
         if (xx + 1 < m) {                             // NE
-          const V e3 = cmul(ilu_coef(a, 8, q, lam), ring[((t + 3) & 3) * m + y + 1]);
+          const V e3 = cmul(coefv(cur.sm[3], cur.sk[3]), ring[((t + 3) & 3) * m + y + 1]);
           acc.x += e3.x;
           acc.y += e3.y;
         }
       }
-      const V c = cmul(acc, dk[q]);
-      const V yv = wk[q];
-      const V z = {yv.x - c.x, yv.y - c.y};
+      const V c = cmul(acc, cur.d);
+      const V z = {cur.v.x - c.x, cur.v.y - c.y};
       ring[(t & 3) * m + y] = z;
-      if (ACC) {
-        const V xo = xk[q];
-        xk[q] = {xo.x + z.x, xo.y + z.y};
-      } else {
-        xk[q] = z;
-      }
+      const long long q = (long long)y * m + xx;
+      if (ACC) xk[q] = {cur.xo.x + z.x, cur.xo.y + z.y};
+      else xk[q] = z;
     }
     __syncthreads();
   }
@@ -478,6 +525,9 @@ dim3 mg_grid(long long J, int K) {
 
 size_t ilu_smem_bytes(int m, size_t vsize) { return 4 * (size_t)m * vsize; }
 
+// a thread per point of the longest wavefront ((m + 1) / 2 points), in warps
+int ilu_threads(int m) { return (((m + 1) / 2 + 31) / 32) * 32; }
+
 // one ILU smoothing step on level l: x = M^{-1} rin (acc false) or x += M^{-1} rin;
 // r is the work array (rin may be r)
 template <typename T>
@@ -485,13 +535,14 @@ bec_status ilu_sweep(bec_problem* p, MgLevel& c, int l, const void* rin, bool ac
   using V = v2_t<T>;
   const MgArgs<T> a = level_args<T>(p, c);
   const size_t smem = ilu_smem_bytes(c.m, sizeof(V));
+  const int threads = ilu_threads(c.m);
   BEC_LAUNCH_BEGIN(p);
   if (acc)
-    ilu_sweep_kernel<T, true><<<p->mg.K, kIluThreads, smem, p->stream>>>(
+    ilu_sweep_kernel<T, true><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
         static_cast<const V*>(c.dinv), a);
   else
-    ilu_sweep_kernel<T, false><<<p->mg.K, kIluThreads, smem, p->stream>>>(
+    ilu_sweep_kernel<T, false><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
         static_cast<const V*>(c.dinv), a);
   BEC_LAUNCH_CHECK(p, kIluSweepNames[l]);
