@@ -75,6 +75,8 @@ struct NetState {
   float* ework = nullptr;        // [K][J] complex defect-correction iterate
   float* xnew = nullptr;         // [K][J] complex corrected iterate
   double* part = nullptr;        // per-sample / per-frequency partial sums
+  double* jpart = nullptr;       // the judge's block sums, [K][kMrSplit][4]
+  float2* alpha = nullptr;       // the judge's step per frequency
   double* h_part = nullptr;      // pinned mirror
   int adam_t = 0;
   unsigned long long rng_ctr = 0;
@@ -109,17 +111,22 @@ __global__ void feat_restrict_kernel(const float2* __restrict__ res, const int* 
   rc[g] = acc;
 }
 
-// one block per sample: s = rms(rc[b]); sinv = 1/s; cfac = s / |lambda'_k + tau a_mean 2 pi^2|
-__global__ void feat_scale_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
-                                  const float2* __restrict__ lamf, float* __restrict__ sinv,
-                                  float* __restrict__ cfac, long long mcc, float tau_a_2pi2) {
-  __shared__ double red[256];
+// one block of kScaleThreads per sample: s = rms(rc[b]); sinv = 1/s;
+// cfac = s / |lambda'_k + tau a_mean 2 pi^2|.  Each thread sums its points in
+// FP32, the block adds the threads' sums in FP64 in a fixed order.
+constexpr int kScaleThreads = 1024;
+__global__ void __launch_bounds__(kScaleThreads)
+feat_scale_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
+                  const float2* __restrict__ lamf, float* __restrict__ sinv,
+                  float* __restrict__ cfac, long long mcc, float tau_a_2pi2) {
+  __shared__ double red[kScaleThreads];
   const int b = blockIdx.x;
-  double s = 0.0;
+  float sf = 0.f;
   for (long long q = threadIdx.x; q < mcc; q += blockDim.x) {
     const float2 v = rc[b * mcc + q];
-    s += (double)v.x * v.x + (double)v.y * v.y;
+    sf = fmaf(v.x, v.x, fmaf(v.y, v.y, sf));
   }
+  const double s = sf;
   red[threadIdx.x] = s;
   __syncthreads();
   for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
@@ -297,23 +304,28 @@ __global__ void add_corr_kernel(float2* __restrict__ out, const float2* __restri
   out[o] = make_float2(a.x + e.x, a.y + e.y);
 }
 
-// One block per frequency k: with res = b - B x (the V-cycle's residual) and
-// r2 = b - B x2 (the corrected and smoothed iterate), B d = res - r2 for the
-// step d = x2 - x.  part[4k..4k+3] = Re, Im <B d, res>, ||B d||^2, ||res||^2
-// (<u, v> = u^H v), summed in FP64 in a fixed order.
-__global__ void mr_dots_kernel(const float2* __restrict__ res, const float2* __restrict__ r2,
-                               double* __restrict__ part, long long mff) {
+// kMrSplit blocks per frequency k: with res = b - B x (the V-cycle's
+// residual) and r2 = b - B x2 (the corrected and smoothed iterate),
+// B d = res - r2 for the step d = x2 - x.  jpart[(k kMrSplit + s) 4 + i] =
+// the block's Re, Im <B d, res>, ||B d||^2, ||res||^2 (<u, v> = u^H v): each
+// thread sums its points (mff / (kMrSplit 256) of them) in FP32, the block
+// adds the threads' sums in FP64 in a fixed order.
+constexpr int kMrSplit = 8;
+__global__ void __launch_bounds__(256)
+mr_dots_kernel(const float2* __restrict__ res, const float2* __restrict__ r2,
+               double* __restrict__ jpart, long long mff) {
   __shared__ double red[4][256];
-  const int k = blockIdx.x;
-  double cr = 0.0, ci = 0.0, dd = 0.0, rr = 0.0;
-  for (long long f = threadIdx.x; f < mff; f += blockDim.x) {
+  const int k = blockIdx.x, sblk = blockIdx.y;
+  float cr = 0.f, ci = 0.f, dd = 0.f, rr = 0.f;
+  const long long stride = (long long)kMrSplit * blockDim.x;
+  for (long long f = (long long)sblk * blockDim.x + threadIdx.x; f < mff; f += stride) {
     const float2 r = res[(long long)k * mff + f];
     const float2 q = r2[(long long)k * mff + f];
-    const double bx = (double)r.x - q.x, by = (double)r.y - q.y;
-    cr += bx * r.x + by * r.y;
-    ci += bx * r.y - by * r.x;
-    dd += bx * bx + by * by;
-    rr += (double)r.x * r.x + (double)r.y * r.y;
+    const float bx = r.x - q.x, by = r.y - q.y;
+    cr = fmaf(bx, r.x, fmaf(by, r.y, cr));
+    ci = fmaf(bx, r.y, fmaf(-by, r.x, ci));
+    dd = fmaf(bx, bx, fmaf(by, by, dd));
+    rr = fmaf(r.x, r.x, fmaf(r.y, r.y, rr));
   }
   red[0][threadIdx.x] = cr;
   red[1][threadIdx.x] = ci;
@@ -325,29 +337,41 @@ __global__ void mr_dots_kernel(const float2* __restrict__ res, const float2* __r
       for (int i = 0; i < 4; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st2];
     __syncthreads();
   }
-  if (threadIdx.x < 4) part[4 * k + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 4)
+    jpart[((long long)k * kMrSplit + sblk) * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// x <- x + alpha_k (x2 - x), alpha_k = <B d, res> / ||B d||^2: the complex step
-// that minimises ||b - B (x + alpha d)|| (0 when B d = 0: the V-cycle's
-// iterate is kept).  ratio[k] = ||b - B x_new|| / ||res||.
-__global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restrict__ x2,
-                                 const double* __restrict__ part, long long mff, int K,
-                                 double* __restrict__ ratio, int* __restrict__ fallbacks) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)K * mff) return;
-  const int k = (int)(g / mff);
-  const double cr = part[4 * k], ci = part[4 * k + 1], dd = part[4 * k + 2], rr = part[4 * k + 3];
-  const bool ok = dd > 0.0 && isfinite(dd) && isfinite(cr) && isfinite(ci);
-  const float ar = ok ? (float)(cr / dd) : 0.f, ai = ok ? (float)(ci / dd) : 0.f;
-  const float2 a = x[g], c = x2[g];
-  const float dx = c.x - a.x, dy = c.y - a.y;
-  x[g] = make_float2(a.x + ar * dx - ai * dy, a.y + ar * dy + ai * dx);
-  if (g - (long long)k * mff == 0) {
+// Per frequency: the sums over the kMrSplit blocks (in order) into part[4k..],
+// the step alpha_k = <B d, res> / ||B d||^2 (0 when B d = 0: the V-cycle's
+// iterate is kept), ratio[k] = ||b - B x_new|| / ||res||, fallback count.
+__global__ void mr_alpha_kernel(const double* __restrict__ jpart, double* __restrict__ part,
+                                float2* __restrict__ alpha, int K, double* __restrict__ ratio,
+                                int* __restrict__ fallbacks) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double sm[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < kMrSplit; ++b)
+      for (int i = 0; i < 4; ++i) sm[i] += jpart[((long long)k * kMrSplit + b) * 4 + i];
+    for (int i = 0; i < 4; ++i) part[4 * k + i] = sm[i];
+    const double cr = sm[0], ci = sm[1], dd = sm[2], rr = sm[3];
+    const bool ok = dd > 0.0 && isfinite(dd) && isfinite(cr) && isfinite(ci);
+    alpha[k] = ok ? make_float2((float)(cr / dd), (float)(ci / dd)) : make_float2(0.f, 0.f);
     const double after = ok ? fmax(rr - (cr * cr + ci * ci) / dd, 0.0) : rr;
     ratio[k] = rr > 0.0 ? sqrt(after / rr) : 0.0;
     if (!ok) atomicAdd(fallbacks, 1);
   }
+}
+
+// x <- x + alpha_k (x2 - x): the complex step that minimises
+// ||b - B (x + alpha d)|| (alpha from mr_alpha_kernel).
+__global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restrict__ x2,
+                                 const float2* __restrict__ alpha, long long mff, int K) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)K * mff) return;
+  const int k = (int)(g / mff);
+  const float2 al = alpha[k];
+  const float2 a = x[g], c = x2[g];
+  const float dx = c.x - a.x, dy = c.y - a.y;
+  x[g] = make_float2(a.x + al.x * dx - al.y * dy, a.y + al.x * dy + al.y * dx);
 }
 
 // ------------------------------------------------------------ dispatch helpers
@@ -421,12 +445,27 @@ bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer,
   return BEC_OK;
 }
 
+bool aligned16p(const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
 template <typename AT>
 bec_status restrict_ch(bec_problem* p, const void* in, void* out, int lf, int B, float scale,
                        bool add) {
   NetState& n = *p->net;
   const int mf = n.sz[lf], mc = n.sz[lf + 1];
   const long long cnt = (long long)B * mc * mc * n.C;
+  constexpr int V = net::ChVec<AT>::V;
+  if (n.C % V == 0 && aligned16p(in) && aligned16p(out)) {   // 16-byte channel groups
+    const long long cv = cnt / V;
+    BEC_LAUNCH_BEGIN(p);
+    if (add)
+      net::restrict_ch_vec_kernel<AT, true><<<grid_for(cv), kT, 0, p->stream>>>(
+          static_cast<const AT*>(in), static_cast<AT*>(out), mf, mc, n.C, cv, scale);
+    else
+      net::restrict_ch_vec_kernel<AT, false><<<grid_for(cv), kT, 0, p->stream>>>(
+          static_cast<const AT*>(in), static_cast<AT*>(out), mf, mc, n.C, cv, scale);
+    BEC_LAUNCH_CHECK(p, "net_restrict_kernel");
+    return BEC_OK;
+  }
   BEC_LAUNCH_BEGIN(p);
   if (add)
     net::restrict_ch_kernel<AT, true><<<grid_for(cnt), kT, 0, p->stream>>>(
@@ -444,6 +483,16 @@ bec_status prolong_ch(bec_problem* p, const void* in, const void* add_src, void*
   NetState& n = *p->net;
   const int mf = n.sz[lf], mc = n.sz[lf + 1];
   const long long cnt = (long long)B * mf * mf * n.C;
+  constexpr int V = net::ChVec<AT>::V;
+  if (n.C % V == 0 && aligned16p(in) && aligned16p(add_src) && aligned16p(out)) {
+    const long long cv = cnt / V;
+    BEC_LAUNCH_BEGIN(p);
+    net::prolong_ch_vec_kernel<AT><<<grid_for(cv), kT, 0, p->stream>>>(
+        static_cast<const AT*>(in), static_cast<const AT*>(add_src), static_cast<AT*>(out), mc, mf,
+        n.C, cv, scale);
+    BEC_LAUNCH_CHECK(p, "net_prolong_kernel");
+    return BEC_OK;
+  }
   BEC_LAUNCH_BEGIN(p);
   net::prolong_ch_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
       static_cast<const AT*>(in), static_cast<const AT*>(add_src), static_cast<AT*>(out), mc, mf,
@@ -492,7 +541,7 @@ bec_status features(bec_problem* p, int B) {
       reinterpret_cast<const float2*>(n.res), n.cur_row, reinterpret_cast<float2*>(n.rc), n.mf, mc, B);
   BEC_LAUNCH_CHECK(p, "net_feat_restrict_kernel");
   BEC_LAUNCH_BEGIN(p);
-  feat_scale_kernel<<<B, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.rc), n.cur_lam, lamf,
+  feat_scale_kernel<<<B, kScaleThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(n.rc), n.cur_lam, lamf,
                                               n.sinv, n.cfac, mcc,
                                               (float)(p->tau * n.a_mean * 2.0 * M_PI * M_PI));
   BEC_LAUNCH_CHECK(p, "net_feat_scale_kernel");
@@ -703,15 +752,17 @@ bec_status correct_t(bec_problem* p) {
   BEC_TRY(mg_residual_level0(p, n.xnew, L0.r, L0.b));
   // the judge: the minimal-residual step along x2 - x, per frequency
   BEC_LAUNCH_BEGIN(p);
-  mr_dots_kernel<<<K, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.res),
-                                           reinterpret_cast<const float2*>(n.xnew), n.part, mff);
+  mr_dots_kernel<<<dim3(K, kMrSplit), 256, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.res), reinterpret_cast<const float2*>(n.xnew), n.jpart, mff);
   BEC_LAUNCH_CHECK(p, "net_judge_dots_kernel");
   int* fb = reinterpret_cast<int*>(n.part + 5 * K);
   BEC_CUDA_TRY(cudaMemsetAsync(fb, 0, sizeof(int), p->stream));
   BEC_LAUNCH_BEGIN(p);
+  mr_alpha_kernel<<<1, 256, 0, p->stream>>>(n.jpart, n.part, n.alpha, K, n.part + 4 * K, fb);
+  BEC_LAUNCH_CHECK(p, "net_judge_alpha_kernel");
+  BEC_LAUNCH_BEGIN(p);
   mr_update_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
-      static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.part, mff, K, n.part + 4 * K,
-      fb);
+      static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.alpha, mff, K);
   BEC_LAUNCH_CHECK(p, "net_judge_update_kernel");
   return BEC_OK;
 }
@@ -784,6 +835,8 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   chain(dalloc(reinterpret_cast<void**>(&n->ework), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->xnew), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
+  chain(dalloc(reinterpret_cast<void**>(&n->jpart), (size_t)K * kMrSplit * 4 * sizeof(double)));
+  chain(dalloc(reinterpret_cast<void**>(&n->alpha), (size_t)K * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->err), sizeof(int)));
   n->tc = !n->fp32 && C == 32 && tc_conv_supported();
   if (n->tc) {
@@ -844,6 +897,7 @@ void net_free(bec_problem* p) {
   if (n == nullptr) return;
   void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->la_c, n->rc, n->sinv, n->cfac, n->row,
                   n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part,
+                  n->jpart, n->alpha,
                   n->err, n->wt, n->x16};
   for (void* q : ptrs)
     if (q) cudaFree(q);

@@ -228,6 +228,141 @@ __global__ void prolong_ch_kernel(const AT* __restrict__ in, const AT* __restric
   out[g] = st<AT>(acc);
 }
 
+// 16-byte groups of channels: V = 16 / sizeof(AT) consecutive channels of one
+// pixel, loaded and stored as one uint4 (the pointer must be 16-byte aligned)
+template <typename AT>
+struct ChVec {
+  static constexpr int V = 16 / (int)sizeof(AT);
+};
+
+template <typename AT>
+__device__ __forceinline__ void ld_vec(const AT* p, float (&v)[ChVec<AT>::V]) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  if constexpr (sizeof(AT) == 4) {
+    v[0] = __uint_as_float(u.x);
+    v[1] = __uint_as_float(u.y);
+    v[2] = __uint_as_float(u.z);
+    v[3] = __uint_as_float(u.w);
+  } else {
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+}
+
+template <typename AT>
+__device__ __forceinline__ void st_vec(AT* p, const float (&v)[ChVec<AT>::V]) {
+  uint4 u;
+  if constexpr (sizeof(AT) == 4) {
+    u = make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]),
+                   __float_as_uint(v[3]));
+  } else {
+    unsigned w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<const unsigned*>(&h);
+    }
+    u = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  *reinterpret_cast<uint4*>(p) = u;
+}
+
+// restrict_ch_kernel with a thread per 16-byte channel group (C a multiple of
+// ChVec<AT>::V): the same FP32 sums in the same order per channel.
+template <typename AT, bool ADD>
+__global__ void restrict_ch_vec_kernel(const AT* __restrict__ in, AT* __restrict__ out, int mf,
+                                       int mc, int C, long long n, float scale) {
+  constexpr int V = ChVec<AT>::V;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;                    // n = B * mc * mc * C / V
+  const int G = C / V;
+  const int c0 = (int)(g % G) * V;
+  const long long pix = g / G;
+  const long long mcc = (long long)mc * mc;
+  const long long b = pix / mcc;
+  const int q = (int)(pix - b * mcc);
+  const int cy = q / mc, cx = q % mc;
+  const AT* src = in + b * (long long)mf * mf * C;
+  float acc[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) acc[i] = 0.f;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const float w = (dy == 0 ? 0.5f : 0.25f) * (dx == 0 ? 0.5f : 0.25f);
+      float v[V];
+      ld_vec<AT>(src + ((long long)(2 * cy + 1 + dy) * mf + (2 * cx + 1 + dx)) * C + c0, v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[i] = fmaf(w, v[i], acc[i]);
+    }
+  AT* dst = out + pix * C + c0;
+  if (ADD) {
+    float o[V];
+    ld_vec<AT>(dst, o);
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc[i] = acc[i] * scale + o[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc[i] *= scale;
+  }
+  st_vec<AT>(dst, acc);
+}
+
+// prolong_ch_kernel with a thread per 16-byte channel group, same sums.
+template <typename AT>
+__global__ void prolong_ch_vec_kernel(const AT* __restrict__ in, const AT* __restrict__ add_src,
+                                      AT* __restrict__ out, int mc, int mf, int C, long long n,
+                                      float scale) {
+  constexpr int V = ChVec<AT>::V;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;                    // n = B * mf * mf * C / V
+  const int G = C / V;
+  const int c0 = (int)(g % G) * V;
+  const long long pix = g / G;
+  const long long mff = (long long)mf * mf;
+  const long long b = pix / mff;
+  const int f = (int)(pix - b * mff);
+  const int fy = f / mf, fx = f % mf;
+  const AT* src = in + b * (long long)mc * mc * C;
+  float acc[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) acc[i] = 0.f;
+  for (int a = 0; a < 2; ++a) {
+    int cy;
+    float wy;
+    if (fy & 1) { if (a) break; cy = (fy - 1) / 2; wy = 1.f; }
+    else { cy = fy / 2 - 1 + a; wy = 0.5f; }
+    if (cy < 0 || cy >= mc) continue;
+    for (int bb = 0; bb < 2; ++bb) {
+      int cx;
+      float wx;
+      if (fx & 1) { if (bb) break; cx = (fx - 1) / 2; wx = 1.f; }
+      else { cx = fx / 2 - 1 + bb; wx = 0.5f; }
+      if (cx < 0 || cx >= mc) continue;
+      float v[V];
+      ld_vec<AT>(src + ((long long)cy * mc + cx) * C + c0, v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[i] = fmaf(wy * wx, v[i], acc[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < V; ++i) acc[i] *= scale;
+  AT* dst = out + pix * C + c0;
+  if (add_src) {
+    float o[V];
+    ld_vec<AT>(add_src + pix * C + c0, o);
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc[i] += o[i];
+  }
+  st_vec<AT>(dst, acc);
+}
+
 // d *= (a > 0), elementwise
 template <typename AT>
 __global__ void relu_mask_kernel(AT* __restrict__ d, const AT* __restrict__ a, long long n) {
