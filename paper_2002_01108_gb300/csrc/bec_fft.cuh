@@ -119,19 +119,20 @@ __device__ __forceinline__ void radix_dft(V (&v)[R]) {
     radix_dft<4, SIGN>(o);
     const T h = T(0.70710678118654752440);
     // w o1 = h (1 + SIGN i) o1, w^2 o2 = SIGN i o2, w^3 o3 = h (-1 + SIGN i) o3
+    // (the factor h is applied inside the final FMAs: e +- h u)
     const V s1 = cmul_si<SIGN>(o[1]);
-    const V t1 = {h * (o[1].x + s1.x), h * (o[1].y + s1.y)};
+    const V u1 = {o[1].x + s1.x, o[1].y + s1.y};
     const V t2 = cmul_si<SIGN>(o[2]);
     const V s3 = cmul_si<SIGN>(o[3]);
-    const V t3 = {h * (s3.x - o[3].x), h * (s3.y - o[3].y)};
+    const V u3 = {s3.x - o[3].x, s3.y - o[3].y};
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], t1);
-    v[5] = csub(e[1], t1);
+    v[1] = {fma(h, u1.x, e[1].x), fma(h, u1.y, e[1].y)};
+    v[5] = {fma(-h, u1.x, e[1].x), fma(-h, u1.y, e[1].y)};
     v[2] = cadd(e[2], t2);
     v[6] = csub(e[2], t2);
-    v[3] = cadd(e[3], t3);
-    v[7] = csub(e[3], t3);
+    v[3] = {fma(h, u3.x, e[3].x), fma(h, u3.y, e[3].y)};
+    v[7] = {fma(-h, u3.x, e[3].x), fma(-h, u3.y, e[3].y)};
   }
 }
 
