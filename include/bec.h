@@ -46,7 +46,7 @@ typedef enum {
   BEC_ENOTCONV = 4,    /* GMRES hit maxit; u and info still hold the best iterate */
   BEC_ENUMERIC = 5,    /* NaN or Inf met in the Krylov recurrences */
   BEC_ETIMEOUT = 6,    /* a bounded device wait ran out */
-  BEC_EUNSUPPORTED = 7 /* valid request that this build does not implement */
+  BEC_EUNSUPPORTED = 7 /* valid request that the library does not implement */
 } bec_status;
 
 /* How P_eps^{-1} solves the shifted spatial systems B_k z = y (Sec. 4, Step 2). */
