@@ -204,6 +204,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def shard(items, rank: int, ws: int):
+    """The instances of a batch that rank `rank` of `ws` solves: rank, rank + ws,
+    ...  The instances are independent problems, so the ranks exchange no data."""
+    return list(items)[rank::ws]
+
+
+def reduce_ranks(values, dist, ws: int, op: str, device: str = "cuda"):
+    """Element-wise "max" or "sum" of a list of floats over the ranks (the
+    values themselves when ws == 1)."""
+    if ws == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()]
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,10 +344,7 @@ def measure_form(form, case, args, ws, local, dist):
     kernels = prob.profile_stop()
     launches = prob.launches - launches0
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_ranks([ms_step], dist, ws, "max")[0]
 
     # P_eps^-1 alone (Steps 1-3 of Sec. 4) on f, 4K applies after 3 warm-ups;
     # the 133 MB input and output exceed L2.  One more apply under per-launch
@@ -381,10 +395,7 @@ def measure_form(form, case, args, ws, local, dist):
         prob.gmres_solve_host(f_hosts[i % nbuf], u_hosts[i % nbuf], **solve_kw)
         e2e_single.append(time.perf_counter() - t1)
     e2e_single_s = sum(e2e_single) / len(e2e_single)
-    if ws > 1:
-        t = torch.tensor([e2e_s, e2e_single_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s, e2e_single_s = (float(x) for x in t.tolist())
+    e2e_s, e2e_single_s = reduce_ranks([e2e_s, e2e_single_s], dist, ws, "max")
     U = prob.U
     prob.close()
     return {"U": U, "ms_step": ms_step, "kernels": kernels, "launches": launches,
@@ -684,16 +695,18 @@ def measure_bdf2_headline(args, form):
             "true_relres": info["true_relres"]}
 
 
-def measure_batch(args):
+def measure_batch(args, ws=1, rank=0, dist=None):
     """The uneven batch: 64 instances, side in {63, 127, 255}, N in {32, ..., 512},
     ln eps ~ U[ln 1e-4, ln sqrt(tau)], FP32 preconditioner in FP64 FGMRES(10)
     to RES 1e-8.  Timed as one bec_batch_solve (rounds over 8 streams, Arnoldi
-    iterations replayed from CUDA graphs) and, for comparison, as the same
-    instances solved one after another by bec_gmres_solve."""
+    iterations replayed from CUDA graphs) and, for comparison, with one stream
+    and no graphs.  With ws > 1 ranks the instances are sharded (instance i to
+    rank i mod ws, no exchange); the job's throughput is all ranks' unknowns
+    over the slowest rank's time."""
     import torch
     from paper_2002_01108_gb300 import Batch
     from workloads import batch_cases
-    cases = batch_cases(seed=4, count=64)
+    cases = shard(batch_cases(seed=4, count=64), rank, ws)
     specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
     out = {"workload": "64 instances of 2D heat: side in {63,127,255}, N in {32,...,512}, "
                        "ln eps ~ U[ln 1e-4, ln sqrt(tau)] (seed 4); FP32 sine-transform P_eps^-1 "
@@ -711,17 +724,24 @@ def measure_batch(args):
             for _ in range(max(2, args.warmup)):        # the second call captures the graphs
                 b.solve(fs, us, restart=10, rtol=RTOL)
             torch.cuda.synchronize()
+            if ws > 1:
+                dist.barrier()
             l0 = b.launches
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 infos = b.solve(fs, us, restart=10, rtol=RTOL)
             torch.cuda.synchronize()
             dt = (time.perf_counter() - t0) / args.steps
-            out[label] = {"value": b.unknowns / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+            dt, = reduce_ranks([dt], dist, ws, "max")
+            unknowns, iters = reduce_ranks([b.unknowns, sum(i["iters"] for i in infos)], dist, ws,
+                                           "sum")
+            worst, = reduce_ranks([max(i["true_relres"] for i in infos)], dist, ws, "max")
+            out[label] = {"value": unknowns / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
                           "gpu_launches": (b.launches - l0) // args.steps,
-                          "iterations_total": sum(i["iters"] for i in infos),
-                          "max_true_relres": max(i["true_relres"] for i in infos)}
-            out["unknowns"] = b.unknowns
+                          "iterations_total": int(iters), "max_true_relres": worst}
+            out["unknowns"] = int(unknowns)
+            if ws > 1:
+                out["sharding"] = f"instance i on rank i mod {ws}"
             del fs, us
     return out
 
@@ -810,7 +830,7 @@ def run_gpu(args):
                            "instead of 12); FP64 fastest at 1+1",
             "learned_note": "the V-cycle, then the trained network's correction (BF16 activations, "
                             "FP32 accumulation), one smoothing sweep and the minimal-residual judge"}
-        line["batch"] = measure_batch(args)
+        line["batch"] = measure_batch(args, ws, rank, dist)
         line["paper_table1_row"] = measure_paper_table1(args)
         line["bdf2"] = {
             "workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, BDF2 (r = 3/2, -2, 1/2; pre-start "
