@@ -80,6 +80,8 @@ struct MgLevel {
   void* b = nullptr;
   void* r = nullptr;
   void* dinv = nullptr; // [K][J] complex: 1 / D of the ILU smoother (BEC_MG_ILU)
+  void* ilu_nb = nullptr;   // [2][J][8] real: the M and K entries towards the lower
+                            // (W, S, SE, SW) and upper (E, N, NW, NE) neighbours
 };
 
 struct MgState {

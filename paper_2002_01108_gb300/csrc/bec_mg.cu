@@ -309,7 +309,8 @@ template <typename T, bool FWD, bool ACC>
 __device__ __forceinline__ void ilu_load(IluPoint<T>& P, int t, const MgArgs<T>& a,
                                          const v2_t<T>* __restrict__ src,
                                          const v2_t<T>* __restrict__ dk,
-                                         const v2_t<T>* __restrict__ xk) {
+                                         const v2_t<T>* __restrict__ xk,
+                                         const T* __restrict__ nb) {
   const int m = a.m;
   const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
   const int yhi = min(m - 1, t / 2);
@@ -318,13 +319,21 @@ __device__ __forceinline__ void ilu_load(IluPoint<T>& P, int t, const MgArgs<T>&
   if (!P.ok) return;
   P.x = t - 2 * P.y;
   const long long q = (long long)P.y * m + P.x;
-  // forward: W, S, SE, SW; backward: E, N, NW, NE
-  constexpr int s0 = FWD ? 3 : 5, s1 = FWD ? 1 : 7, s2 = FWD ? 2 : 6, s3 = FWD ? 0 : 8;
-  const int sl[4] = {s0, s1, s2, s3};
+  // forward: W, S, SE, SW; backward: E, N, NW, NE (packed, 16-byte loads)
+  const T* e = nb + ((FWD ? 0 : a.J) + q) * 8;
+  if constexpr (sizeof(T) == 4) {
+    const float4 u0 = reinterpret_cast<const float4*>(e)[0];
+    const float4 u1 = reinterpret_cast<const float4*>(e)[1];
+    P.sm[0] = u0.x; P.sm[1] = u0.y; P.sm[2] = u0.z; P.sm[3] = u0.w;
+    P.sk[0] = u1.x; P.sk[1] = u1.y; P.sk[2] = u1.z; P.sk[3] = u1.w;
+  } else {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    P.sm[i] = a.SM[(long long)sl[i] * a.J + q];
-    P.sk[i] = a.SK[(long long)sl[i] * a.J + q];
+    for (int i = 0; i < 2; ++i) {
+      const double2 u = reinterpret_cast<const double2*>(e)[i];
+      const double2 w = reinterpret_cast<const double2*>(e)[2 + i];
+      P.sm[2 * i] = u.x; P.sm[2 * i + 1] = u.y;
+      P.sk[2 * i] = w.x; P.sk[2 * i + 1] = w.y;
+    }
   }
   P.v = src[q];
   P.d = dk[q];
@@ -337,7 +346,7 @@ __device__ __forceinline__ void ilu_load(IluPoint<T>& P, int t, const MgArgs<T>&
 template <typename T, bool ACC>
 __global__ void __launch_bounds__(512)
 ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
-                 const v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
+                 const v2_t<T>* __restrict__ dinv, const T* __restrict__ nb, MgArgs<T> a) {
   using V = v2_t<T>;
   extern __shared__ __align__(16) unsigned char ilu_smem[];
   V* ring = reinterpret_cast<V*>(ilu_smem);     // [4][m]
@@ -352,14 +361,14 @@ ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
   auto coefv = [&](T sm, T sk) -> V { return {lam.x * sm + a.tau * sk, lam.y * sm}; };
   // forward: (D + L) y = rin
   IluPoint<T> p0, p1, p2, cur;
-  ilu_load<T, true, ACC>(p0, 0, a, rk, dk, xk);
-  ilu_load<T, true, ACC>(p1, 1, a, rk, dk, xk);
-  ilu_load<T, true, ACC>(p2, 2, a, rk, dk, xk);
+  ilu_load<T, true, ACC>(p0, 0, a, rk, dk, xk, nb);
+  ilu_load<T, true, ACC>(p1, 1, a, rk, dk, xk, nb);
+  ilu_load<T, true, ACC>(p2, 2, a, rk, dk, xk, nb);
   for (int t = 0; t <= tmax; ++t) {
     cur = p0;
     p0 = p1;
     p1 = p2;
-    ilu_load<T, true, ACC>(p2, t + 3, a, rk, dk, xk);
+    ilu_load<T, true, ACC>(p2, t + 3, a, rk, dk, xk, nb);
     if (cur.ok) {
       const int y = cur.y, xx = cur.x;
       V acc = cur.v;
@@ -390,14 +399,14 @@ ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
     __syncthreads();
   }
   // backward: (D + U) z = D y, i.e. z = y - D^{-1} U z
-  ilu_load<T, false, ACC>(p0, tmax, a, wk, dk, xk);
-  ilu_load<T, false, ACC>(p1, tmax - 1, a, wk, dk, xk);
-  ilu_load<T, false, ACC>(p2, tmax - 2, a, wk, dk, xk);
+  ilu_load<T, false, ACC>(p0, tmax, a, wk, dk, xk, nb);
+  ilu_load<T, false, ACC>(p1, tmax - 1, a, wk, dk, xk, nb);
+  ilu_load<T, false, ACC>(p2, tmax - 2, a, wk, dk, xk, nb);
   for (int t = tmax; t >= 0; --t) {
     cur = p0;
     p0 = p1;
     p1 = p2;
-    ilu_load<T, false, ACC>(p2, t - 3, a, wk, dk, xk);
+    ilu_load<T, false, ACC>(p2, t - 3, a, wk, dk, xk, nb);
     if (cur.ok) {
       const int y = cur.y, xx = cur.x;
       V acc = {0, 0};
@@ -540,11 +549,11 @@ bec_status ilu_sweep(bec_problem* p, MgLevel& c, int l, const void* rin, bool ac
   if (acc)
     ilu_sweep_kernel<T, true><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
-        static_cast<const V*>(c.dinv), a);
+        static_cast<const V*>(c.dinv), static_cast<const T*>(c.ilu_nb), a);
   else
     ilu_sweep_kernel<T, false><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
-        static_cast<const V*>(c.dinv), a);
+        static_cast<const V*>(c.dinv), static_cast<const T*>(c.ilu_nb), a);
   BEC_LAUNCH_CHECK(p, kIluSweepNames[l]);
   return BEC_OK;
 }
@@ -762,6 +771,20 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes, const double* wind) {
     L.J = (long long)ml * ml;
     bec_status s = fp64 ? upload_stencil<double>(&L.SM, SM) : upload_stencil<float>(&L.SM, SM);
     if (s == BEC_OK) s = fp64 ? upload_stencil<double>(&L.SK, SK) : upload_stencil<float>(&L.SK, SK);
+    if (s == BEC_OK && p->mg.ilu && ml > 1) {
+      // the ILU sweeps' neighbour entries, [dir][q][M W, S, SE, SW | K same]
+      // (dir 0) and [M E, N, NW, NE | K same] (dir 1)
+      const int lo[4] = {3, 1, 2, 0}, up[4] = {5, 7, 6, 8};
+      std::vector<double> nbv((size_t)16 * L.J);
+      for (long long q = 0; q < L.J; ++q)
+        for (int i = 0; i < 4; ++i) {
+          nbv[(size_t)q * 8 + i] = SM[(size_t)lo[i] * L.J + q];
+          nbv[(size_t)q * 8 + 4 + i] = SK[(size_t)lo[i] * L.J + q];
+          nbv[(size_t)(L.J + q) * 8 + i] = SM[(size_t)up[i] * L.J + q];
+          nbv[(size_t)(L.J + q) * 8 + 4 + i] = SK[(size_t)up[i] * L.J + q];
+        }
+      s = fp64 ? upload_stencil<double>(&L.ilu_nb, nbv) : upload_stencil<float>(&L.ilu_nb, nbv);
+    }
     const size_t bytes = (size_t)p->mg.K * L.J * csz;
     void* bufs[4] = {nullptr, nullptr, nullptr, nullptr};
     const int nbuf = (p->mg.ilu && ml > 1) ? 4 : 3;   // + 1/D of the ILU smoother
@@ -792,7 +815,7 @@ bec_status mg_setup(bec_problem* p, const double* a_nodes, const double* wind) {
 
 void mg_free(bec_problem* p) {
   for (MgLevel& L : p->mg.lv) {
-    void* ptrs[] = {L.SM, L.SK, L.x, L.b, L.r, L.dinv};
+    void* ptrs[] = {L.SM, L.SK, L.x, L.b, L.r, L.dinv, L.ilu_nb};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
