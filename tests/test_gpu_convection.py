@@ -128,3 +128,23 @@ def test_convection_fgmres_reaches_the_stepping_solution(precision):
     assert info["converged"] == 1 and info["true_relres"] <= 1e-10 * (1 + 1e-6)
     assert float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) <= 1e-7
     assert info["iters"] <= 12, info
+
+
+def test_convection_at_the_workload_size():
+    """Example 3 at the size bench.py times (255^2 x 256, FP32 ILU multigrid,
+    FGMRES(30) to RES 1e-8): converged in at most 10 iterations and equal to
+    sequential stepping."""
+    m, N = 255, 256
+    tau = 1.0 / N
+    wind, g, u0, fs = circulating_wind_case(m, N)
+    K, Kb = O.fd_convection_diffusion(NU, wind)
+    f = O.build_rhs_dirichlet(u0, fs, g, tau, Kb)
+    ref = O.timestep_solve(f, sp.identity(m * m, format="csr"), K, tau)
+    with problem(m, N, wind, "fp32") as p:
+        p.set_eps(min(0.5, 0.5 * tau))
+        fd = p.build_rhs_dirichlet(dev(u0), dev(fs), dev(g))
+        assert max_rel(host(fd), f) <= 64 * U64
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
+        u = host(u)
+    assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8 and info["iters"] <= 10, info
+    assert float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) <= 1e-5
