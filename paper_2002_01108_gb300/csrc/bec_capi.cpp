@@ -280,7 +280,10 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     p->mg.ilu = d->mg_smoother == BEC_MG_ILU;
     chain(mg_setup(p, d->a_nodes, d->wind));
     if (d->route == BEC_ROUTE_LEARNED && s == BEC_OK)
-      chain(net_setup(p, d->a_nodes, d->net_channels == 0 ? 32 : d->net_channels, d->net_fp32, 32));
+      // inference runs all N/2 + 1 frequencies in one batch up to 160 of them
+      // (training batches stay at most 32)
+      chain(net_setup(p, d->a_nodes, d->net_channels == 0 ? 32 : d->net_channels, d->net_fp32,
+                      std::max(32, std::min(p->N / 2 + 1, 160))));
   }
   p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
   p->desc.wind = nullptr;
