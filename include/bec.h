@@ -129,7 +129,8 @@ typedef struct {
                             incomplete factorisation (D + L) D^{-1} (D + U) of
                             each shifted system, diag kept, ILU(0) on the
                             5-point finest grid: the ILU smoothing of Examples 2
-                            and 3 of Sec. 5).  BEC_MG_ILU needs BEC_ROUTE_MG. */
+                            and 3 of Sec. 5).  BEC_MG_ILU needs BEC_ROUTE_MG,
+                            and nx <= 511 with BEC_PC_FP64. */
 } bec_problem_desc;
 
 enum { BEC_MG_JACOBI = 0, BEC_MG_ILU = 1 };

@@ -218,6 +218,8 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     return einval("mg_smoother must be BEC_MG_JACOBI or BEC_MG_ILU");
   if (d->mg_smoother == BEC_MG_ILU && d->route != BEC_ROUTE_MG)
     return einval("the ILU smoother needs BEC_ROUTE_MG");
+  if (d->mg_smoother == BEC_MG_ILU && d->precision == BEC_PC_FP64 && d->nx > 511)
+    return einval("the FP64 ILU smoother needs nx <= 511 (its shared-memory staging)");
   if (d->time_scheme != BEC_TIME_BDF1 && d->time_scheme != BEC_TIME_BDF2)
     return einval("time_scheme must be BEC_TIME_BDF1 or BEC_TIME_BDF2");
   if (d->time_scheme == BEC_TIME_BDF2 && (d->route != BEC_ROUTE_FST || d->dim == 3 || d->N < 4))

@@ -290,67 +290,98 @@ ilu_setup_kernel(v2_t<T>* __restrict__ dinv, MgArgs<T> a) {
   }
 }
 
-// The independent operands of one point of a wavefront: its row y (thread
-// tid owns y = ylo(t) + tid, one point per thread: the block has at least
-// ceil(m / 2) threads), the right-hand side or forward value, 1/d, and the
-// real M and K entries towards its four lower (forward) or upper (backward)
-// neighbours.  They are loaded three wavefronts ahead, so that their latency
-// (the [K][J] arrays exceed L2) overlaps the dependent work and barriers of
-// the wavefronts before.
+// One ILU smoothing step for every frequency: z = M^{-1} rin, then x = z
+// (ACC false) or x += z (ACC true); rin may alias work, which holds the
+// forward result y between the two sweeps.  A thread owns one point per
+// wavefront (the block has a thread per point of the longest one).  The
+// operands that do not depend on the recurrence are staged by cp.async: at
+// wavefront t a thread starts the copies of its point on wavefront t + 3
+// (backward: t - 3) into its own slot of a 4-stage buffer in shared memory
+// and waits only for the group of wavefront t.  Slot layout: the 8 neighbour entries, then rhs / forward value,
+// 1/d and (ACC, backward) the old x.
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The slot stride (80 or 144 bytes, an odd number of 16-byte units) puts the
+// slots of 8 consecutive threads on distinct 16-byte bank groups, so the
+// 16-byte reads of a warp are free of bank conflicts.
 template <typename T>
-struct IluPoint {
-  v2_t<T> v, d, xo;
-  T sm[4], sk[4];
-  int x, y;
-  bool ok;
+struct IluSlot {
+  static constexpr int kNb = 0, kV = 8 * (int)sizeof(T), kD = kV + 2 * (int)sizeof(T),
+                       kX = kD + 2 * (int)sizeof(T), kBytes = sizeof(T) == 4 ? 80 : 144;
 };
 
+// starts the copies of the operands of this thread's point on wavefront t
+// (nothing when it has none), then commits one group
 template <typename T, bool FWD, bool ACC>
-__device__ __forceinline__ void ilu_load(IluPoint<T>& P, int t, const MgArgs<T>& a,
-                                         const v2_t<T>* __restrict__ src,
-                                         const v2_t<T>* __restrict__ dk,
-                                         const v2_t<T>* __restrict__ xk,
-                                         const T* __restrict__ nb) {
+__device__ __forceinline__ void ilu_issue(unsigned char* slot, int t, const MgArgs<T>& a,
+                                          const v2_t<T>* src, const v2_t<T>* dk,
+                                          const v2_t<T>* xk, const T* nb) {
+  using S = IluSlot<T>;
   const int m = a.m;
   const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
   const int yhi = min(m - 1, t / 2);
-  P.y = ylo + (int)threadIdx.x;
-  P.ok = t >= 0 && t <= 3 * (m - 1) && P.y <= yhi;
-  if (!P.ok) return;
-  P.x = t - 2 * P.y;
-  const long long q = (long long)P.y * m + P.x;
-  // forward: W, S, SE, SW; backward: E, N, NW, NE (packed, 16-byte loads)
-  const T* e = nb + ((FWD ? 0 : a.J) + q) * 8;
-  if constexpr (sizeof(T) == 4) {
-    const float4 u0 = reinterpret_cast<const float4*>(e)[0];
-    const float4 u1 = reinterpret_cast<const float4*>(e)[1];
-    P.sm[0] = u0.x; P.sm[1] = u0.y; P.sm[2] = u0.z; P.sm[3] = u0.w;
-    P.sk[0] = u1.x; P.sk[1] = u1.y; P.sk[2] = u1.z; P.sk[3] = u1.w;
-  } else {
+  const int y = ylo + (int)threadIdx.x;
+  if (t >= 0 && t <= 3 * (m - 1) && y <= yhi) {
+    const long long q = (long long)y * m + (t - 2 * y);
+    const unsigned char* e = reinterpret_cast<const unsigned char*>(nb + ((FWD ? 0 : a.J) + q) * 8);
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const double2 u = reinterpret_cast<const double2*>(e)[i];
-      const double2 w = reinterpret_cast<const double2*>(e)[2 + i];
-      P.sm[2 * i] = u.x; P.sm[2 * i + 1] = u.y;
-      P.sk[2 * i] = w.x; P.sk[2 * i + 1] = w.y;
-    }
+    for (int i = 0; i < 8 * (int)sizeof(T) / 16; ++i) cp_async(slot + S::kNb + 16 * i, e + 16 * i, 16);
+    cp_async(slot + S::kV, src + q, 2 * (int)sizeof(T));
+    cp_async(slot + S::kD, dk + q, 2 * (int)sizeof(T));
+    if (!FWD && ACC) cp_async(slot + S::kX, xk + q, 2 * (int)sizeof(T));
   }
-  P.v = src[q];
-  P.d = dk[q];
-  if (!FWD && ACC) P.xo = xk[q];
+  cp_async_commit();
 }
 
-// One ILU smoothing step for every frequency: z = M^{-1} rin, then
-// x = z (ACC false) or x += z (ACC true).  rin may alias work; work holds the
-// forward result y between the two sweeps.
+// reads a slot with 16-byte loads: the 8 neighbour entries, the value and 1/d
+template <typename T>
+__device__ __forceinline__ void ilu_read(const unsigned char* sl, T (&e)[8], v2_t<T>& v,
+                                         v2_t<T>& d) {
+  using S = IluSlot<T>;
+  if constexpr (sizeof(T) == 4) {
+    const float4 a = reinterpret_cast<const float4*>(sl + S::kNb)[0];
+    const float4 b = reinterpret_cast<const float4*>(sl + S::kNb)[1];
+    const float4 c = *reinterpret_cast<const float4*>(sl + S::kV);   // v, then d
+    e[0] = a.x; e[1] = a.y; e[2] = a.z; e[3] = a.w;
+    e[4] = b.x; e[5] = b.y; e[6] = b.z; e[7] = b.w;
+    v = make_float2(c.x, c.y);
+    d = make_float2(c.z, c.w);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double2 u = reinterpret_cast<const double2*>(sl + S::kNb)[i];
+      e[2 * i] = u.x;
+      e[2 * i + 1] = u.y;
+    }
+    v = *reinterpret_cast<const double2*>(sl + S::kV);
+    d = *reinterpret_cast<const double2*>(sl + S::kD);
+  }
+}
+
 template <typename T, bool ACC>
 __global__ void __launch_bounds__(512)
-ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
-                 const v2_t<T>* __restrict__ dinv, const T* __restrict__ nb, MgArgs<T> a) {
+ilu_sweep_async_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
+                       const v2_t<T>* __restrict__ dinv, const T* __restrict__ nb, MgArgs<T> a) {
   using V = v2_t<T>;
+  using S = IluSlot<T>;
   extern __shared__ __align__(16) unsigned char ilu_smem[];
-  V* ring = reinterpret_cast<V*>(ilu_smem);     // [4][m]
+  V* ring = reinterpret_cast<V*>(ilu_smem);                       // [4][m]
   const int k = blockIdx.x, m = a.m;
+  unsigned char* stage = ilu_smem + ((4 * (size_t)m * sizeof(V) + 127) & ~(size_t)127);
+  auto slot = [&](int t) { return stage + ((size_t)(t & 3) * blockDim.x + threadIdx.x) * S::kBytes; };
   const V lam = a.lam[k];
   const long long base = (long long)k * a.J;
   const V* dk = dinv + base;
@@ -359,86 +390,97 @@ ilu_sweep_kernel(v2_t<T>* __restrict__ x, v2_t<T>* work, const v2_t<T>* rin,
   V* xk = x + base;
   const int tmax = 3 * (m - 1);
   auto coefv = [&](T sm, T sk) -> V { return {lam.x * sm + a.tau * sk, lam.y * sm}; };
+  auto point = [&](int t, int& y, int& xx) {
+    const int ylo = t > m - 1 ? (t - (m - 1) + 1) / 2 : 0;
+    const int yhi = min(m - 1, t / 2);
+    y = ylo + (int)threadIdx.x;
+    xx = t - 2 * y;
+    return y <= yhi;
+  };
   // forward: (D + L) y = rin
-  IluPoint<T> p0, p1, p2, cur;
-  ilu_load<T, true, ACC>(p0, 0, a, rk, dk, xk, nb);
-  ilu_load<T, true, ACC>(p1, 1, a, rk, dk, xk, nb);
-  ilu_load<T, true, ACC>(p2, 2, a, rk, dk, xk, nb);
+  for (int t = 0; t < 3; ++t) ilu_issue<T, true, ACC>(slot(t), t, a, rk, dk, xk, nb);
   for (int t = 0; t <= tmax; ++t) {
-    cur = p0;
-    p0 = p1;
-    p1 = p2;
-    ilu_load<T, true, ACC>(p2, t + 3, a, rk, dk, xk, nb);
-    if (cur.ok) {
-      const int y = cur.y, xx = cur.x;
-      V acc = cur.v;
+    ilu_issue<T, true, ACC>(slot(t + 3), t + 3, a, rk, dk, xk, nb);
+    cp_async_wait<3>();
+    int y, xx;
+    if (point(t, y, xx)) {
+      const unsigned char* sl = slot(t);
+      T e[8];
+      V acc, dv;
+      ilu_read<T>(sl, e, acc, dv);
       if (xx > 0) {                                   // W
-        const V e = cmul(coefv(cur.sm[0], cur.sk[0]), ring[((t - 1) & 3) * m + y]);
-        acc.x -= e.x;
-        acc.y -= e.y;
+        const V c = cmul(coefv(e[0], e[4]), ring[((t - 1) & 3) * m + y]);
+        acc.x -= c.x;
+        acc.y -= c.y;
       }
       if (y > 0) {
-        const V e = cmul(coefv(cur.sm[1], cur.sk[1]), ring[((t - 2) & 3) * m + y - 1]);   // S
-        acc.x -= e.x;
-        acc.y -= e.y;
+        const V c = cmul(coefv(e[1], e[5]), ring[((t - 2) & 3) * m + y - 1]);   // S
+        acc.x -= c.x;
+        acc.y -= c.y;
         if (xx + 1 < m) {                             // SE
-          const V e2 = cmul(coefv(cur.sm[2], cur.sk[2]), ring[((t - 1) & 3) * m + y - 1]);
-          acc.x -= e2.x;
-          acc.y -= e2.y;
+          const V c2 = cmul(coefv(e[2], e[6]), ring[((t - 1) & 3) * m + y - 1]);
+          acc.x -= c2.x;
+          acc.y -= c2.y;
         }
         if (xx > 0) {                                 // SW
-          const V e3 = cmul(coefv(cur.sm[3], cur.sk[3]), ring[((t - 3) & 3) * m + y - 1]);
-          acc.x -= e3.x;
-          acc.y -= e3.y;
+          const V c3 = cmul(coefv(e[3], e[7]), ring[((t - 3) & 3) * m + y - 1]);
+          acc.x -= c3.x;
+          acc.y -= c3.y;
         }
       }
-      const V yv = cmul(acc, cur.d);
+      const V yv = cmul(acc, dv);
       ring[(t & 3) * m + y] = yv;
       wk[(long long)y * m + xx] = yv;
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
   // backward: (D + U) z = D y, i.e. z = y - D^{-1} U z
-  ilu_load<T, false, ACC>(p0, tmax, a, wk, dk, xk, nb);
-  ilu_load<T, false, ACC>(p1, tmax - 1, a, wk, dk, xk, nb);
-  ilu_load<T, false, ACC>(p2, tmax - 2, a, wk, dk, xk, nb);
+  for (int i = 0; i < 3; ++i) ilu_issue<T, false, ACC>(slot(tmax - i), tmax - i, a, wk, dk, xk, nb);
   for (int t = tmax; t >= 0; --t) {
-    cur = p0;
-    p0 = p1;
-    p1 = p2;
-    ilu_load<T, false, ACC>(p2, t - 3, a, wk, dk, xk, nb);
-    if (cur.ok) {
-      const int y = cur.y, xx = cur.x;
+    ilu_issue<T, false, ACC>(slot(t - 3), t - 3, a, wk, dk, xk, nb);
+    cp_async_wait<3>();
+    int y, xx;
+    if (point(t, y, xx)) {
+      const unsigned char* sl = slot(t);
+      T e[8];
+      V yv, dv;
+      ilu_read<T>(sl, e, yv, dv);
       V acc = {0, 0};
       if (xx + 1 < m) {                               // E
-        const V e = cmul(coefv(cur.sm[0], cur.sk[0]), ring[((t + 1) & 3) * m + y]);
-        acc.x += e.x;
-        acc.y += e.y;
+        const V c = cmul(coefv(e[0], e[4]), ring[((t + 1) & 3) * m + y]);
+        acc.x += c.x;
+        acc.y += c.y;
       }
       if (y + 1 < m) {
-        const V e = cmul(coefv(cur.sm[1], cur.sk[1]), ring[((t + 2) & 3) * m + y + 1]);   // N
-        acc.x += e.x;
-        acc.y += e.y;
+        const V c = cmul(coefv(e[1], e[5]), ring[((t + 2) & 3) * m + y + 1]);   // N
+        acc.x += c.x;
+        acc.y += c.y;
         if (xx > 0) {                                 // NW
-          const V e2 = cmul(coefv(cur.sm[2], cur.sk[2]), ring[((t + 1) & 3) * m + y + 1]);
-          acc.x += e2.x;
-          acc.y += e2.y;
+          const V c2 = cmul(coefv(e[2], e[6]), ring[((t + 1) & 3) * m + y + 1]);
+          acc.x += c2.x;
+          acc.y += c2.y;
         }
         if (xx + 1 < m) {                             // NE
-          const V e3 = cmul(coefv(cur.sm[3], cur.sk[3]), ring[((t + 3) & 3) * m + y + 1]);
-          acc.x += e3.x;
-          acc.y += e3.y;
+          const V c3 = cmul(coefv(e[3], e[7]), ring[((t + 3) & 3) * m + y + 1]);
+          acc.x += c3.x;
+          acc.y += c3.y;
         }
       }
-      const V c = cmul(acc, cur.d);
-      const V z = {cur.v.x - c.x, cur.v.y - c.y};
+      const V cc = cmul(acc, dv);
+      const V z = {yv.x - cc.x, yv.y - cc.y};
       ring[(t & 3) * m + y] = z;
       const long long q = (long long)y * m + xx;
-      if (ACC) xk[q] = {cur.xo.x + z.x, cur.xo.y + z.y};
-      else xk[q] = z;
+      if (ACC) {
+        const V xo = *reinterpret_cast<const V*>(sl + S::kX);
+        xk[q] = {xo.x + z.x, xo.y + z.y};
+      } else {
+        xk[q] = z;
+      }
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- host side
@@ -537,21 +579,27 @@ size_t ilu_smem_bytes(int m, size_t vsize) { return 4 * (size_t)m * vsize; }
 // a thread per point of the longest wavefront ((m + 1) / 2 points), in warps
 int ilu_threads(int m) { return (((m + 1) / 2 + 31) / 32) * 32; }
 
+// the wavefront ring (rounded up to 128 bytes) plus 4 operand slots per thread
+size_t ilu_sweep_smem_bytes(int m, int threads, size_t vsize) {
+  const size_t slot = vsize == 8 ? 80 : 144;
+  return ((4 * (size_t)m * vsize + 127) & ~(size_t)127) + 4 * (size_t)threads * slot;
+}
+
 // one ILU smoothing step on level l: x = M^{-1} rin (acc false) or x += M^{-1} rin;
 // r is the work array (rin may be r)
 template <typename T>
 bec_status ilu_sweep(bec_problem* p, MgLevel& c, int l, const void* rin, bool acc) {
   using V = v2_t<T>;
   const MgArgs<T> a = level_args<T>(p, c);
-  const size_t smem = ilu_smem_bytes(c.m, sizeof(V));
   const int threads = ilu_threads(c.m);
+  const size_t smem = ilu_sweep_smem_bytes(c.m, threads, sizeof(V));
   BEC_LAUNCH_BEGIN(p);
   if (acc)
-    ilu_sweep_kernel<T, true><<<p->mg.K, threads, smem, p->stream>>>(
+    ilu_sweep_async_kernel<T, true><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
         static_cast<const V*>(c.dinv), static_cast<const T*>(c.ilu_nb), a);
   else
-    ilu_sweep_kernel<T, false><<<p->mg.K, threads, smem, p->stream>>>(
+    ilu_sweep_async_kernel<T, false><<<p->mg.K, threads, smem, p->stream>>>(
         static_cast<V*>(c.x), static_cast<V*>(c.r), static_cast<const V*>(rin),
         static_cast<const V*>(c.dinv), static_cast<const T*>(c.ilu_nb), a);
   BEC_LAUNCH_CHECK(p, kIluSweepNames[l]);
@@ -561,15 +609,18 @@ bec_status ilu_sweep(bec_problem* p, MgLevel& c, int l, const void* rin, bool ac
 template <typename T>
 bec_status ilu_setup_t(bec_problem* p) {
   using V = v2_t<T>;
-  // the ring of the largest grid may exceed the default 48 KB
-  const int big = (int)ilu_smem_bytes(p->mg.lv[0].m, sizeof(V));
-  if (big > 48 * 1024) {
+  // the ring and the operand slots of the largest grid may exceed the default 48 KB
+  const int m0 = p->mg.lv[0].m;
+  const int big = (int)ilu_smem_bytes(m0, sizeof(V));
+  if (big > 48 * 1024)
     BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_setup_kernel<T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_kernel<T, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_kernel<T, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  const int bigs = (int)ilu_sweep_smem_bytes(m0, ilu_threads(m0), sizeof(V));
+  if (bigs > 48 * 1024) {
+    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_async_kernel<T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bigs));
+    BEC_CUDA_TRY(cudaFuncSetAttribute(ilu_sweep_async_kernel<T, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bigs));
   }
   for (size_t l = 0; l + 1 < p->mg.lv.size(); ++l) {
     MgLevel& c = p->mg.lv[l];

@@ -122,6 +122,11 @@ def test_allocate_rejects_invalid_convection_requests(lib):
                         0, 0, 0.0, 0, 0, 0, 0, wind, side, smoother)
         assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1, (route, side)
         assert out.value is None
+    # the FP64 ILU smoother stages its operands in shared memory: nx <= 511
+    d = ProblemDesc(2, 1023, 1023, 64, 1.0, 1.0, 1, 0, 10, 0, 0, None,
+                    0, 0, 0.0, 0, 0, 0, 0, None, 0.0, 1)
+    assert lib.bec_allocate_problem(ctypes.byref(d), None, ctypes.byref(out)) == 1
+    assert b"511" in lib.bec_last_error()
 
 
 def test_null_arguments_are_rejected(lib):
