@@ -48,8 +48,13 @@ struct MgArgs {
 template <typename V, typename T>
 __device__ __forceinline__ V cscale(V a, T s) { return {a.x * s, a.y * s}; }
 
+// L0: the finest grid, where M = I and K is a 5-point stencil: the mass
+// product is the centre value and the corner slots are skipped (fewer loads
+// and registers; the same sums, since those entries are zero).
+__host__ __device__ constexpr bool mg_corner(int s) { return s == 0 || s == 2 || s == 6 || s == 8; }
+
 // B x at point q for frequency k with the stencil coefficients in registers.
-template <typename T>
+template <typename T, bool L0>
 __device__ __forceinline__ v2_t<T> apply_b(const v2_t<T>* __restrict__ xk, const T (&sm)[9],
                                            const T (&sk)[9], const int (&off)[9],
                                            const bool (&ok)[9], v2_t<T> lam, T tau) {
@@ -57,10 +62,15 @@ __device__ __forceinline__ v2_t<T> apply_b(const v2_t<T>* __restrict__ xk, const
   V am = {0, 0}, ak = {0, 0};
 #pragma unroll
   for (int s = 0; s < 9; ++s) {
+    if (L0 && mg_corner(s)) continue;
     if (ok[s]) {
       const V xv = xk[off[s]];
-      am.x += sm[s] * xv.x;
-      am.y += sm[s] * xv.y;
+      if (L0) {
+        if (s == 4) am = xv;
+      } else {
+        am.x += sm[s] * xv.x;
+        am.y += sm[s] * xv.y;
+      }
       ak.x += sk[s] * xv.x;
       ak.y += sk[s] * xv.y;
     }
@@ -69,7 +79,7 @@ __device__ __forceinline__ v2_t<T> apply_b(const v2_t<T>* __restrict__ xk, const
   return {lm.x + tau * ak.x, lm.y + tau * ak.y};
 }
 
-template <typename T>
+template <typename T, bool L0>
 __device__ __forceinline__ void load_point(const MgArgs<T>& a, long long q, T (&sm)[9], T (&sk)[9],
                                            int (&off)[9], bool (&ok)[9]) {
   const int iy = (int)(q / a.m), ix = (int)(q - (long long)iy * a.m);
@@ -78,14 +88,14 @@ __device__ __forceinline__ void load_point(const MgArgs<T>& a, long long q, T (&
     const int dy = s / 3 - 1, dx = s % 3 - 1;
     ok[s] = iy + dy >= 0 && iy + dy < a.m && ix + dx >= 0 && ix + dx < a.m;
     off[s] = (int)q + dy * a.m + dx;
-    sm[s] = a.SM[(long long)s * a.J + q];
-    sk[s] = a.SK[(long long)s * a.J + q];
+    sm[s] = (L0 ? (s == 4 ? T(1) : T(0)) : a.SM[(long long)s * a.J + q]);
+    sk[s] = (L0 && mg_corner(s)) ? T(0) : a.SK[(long long)s * a.J + q];
   }
 }
 
 // ZERO: xo = omega D^{-1} b (one sweep from x = 0);
 // else: xo = x + omega D^{-1} (b - B x)      (xo != x)
-template <typename T, bool ZERO>
+template <typename T, bool ZERO, bool L0>
 __global__ void __launch_bounds__(kMgThreads)
 mg_smooth_kernel(v2_t<T>* __restrict__ xo, const v2_t<T>* __restrict__ x,
                  const v2_t<T>* __restrict__ b, MgArgs<T> a) {
@@ -95,7 +105,7 @@ mg_smooth_kernel(v2_t<T>* __restrict__ xo, const v2_t<T>* __restrict__ x,
   T sm[9], sk[9];
   int off[9];
   bool ok[9];
-  load_point(a, q, sm, sk, off, ok);
+  load_point<T, L0>(a, q, sm, sk, off, ok);
   const int k0 = blockIdx.y * kFreqChunk, k1 = min(a.K, k0 + kFreqChunk);
   for (int k = k0; k < k1; ++k) {
     const long long base = (long long)k * a.J;
@@ -106,7 +116,7 @@ mg_smooth_kernel(v2_t<T>* __restrict__ xo, const v2_t<T>* __restrict__ x,
     V x0 = {0, 0};
     if (!ZERO) {
       x0 = x[base + q];
-      const V bx = apply_b<T>(x + base, sm, sk, off, ok, lam, a.tau);
+      const V bx = apply_b<T, L0>(x + base, sm, sk, off, ok, lam, a.tau);
       rr = {rr.x - bx.x, rr.y - bx.y};
     }
     const V c = cmulc(rr, D);     // rr conj(D); times omega / |D|^2 = omega rr / D
@@ -115,7 +125,7 @@ mg_smooth_kernel(v2_t<T>* __restrict__ xo, const v2_t<T>* __restrict__ x,
 }
 
 // r = b - B x
-template <typename T>
+template <typename T, bool L0>
 __global__ void __launch_bounds__(kMgThreads)
 mg_residual_kernel(v2_t<T>* __restrict__ r, const v2_t<T>* __restrict__ x,
                    const v2_t<T>* __restrict__ b, MgArgs<T> a) {
@@ -125,11 +135,11 @@ mg_residual_kernel(v2_t<T>* __restrict__ r, const v2_t<T>* __restrict__ x,
   T sm[9], sk[9];
   int off[9];
   bool ok[9];
-  load_point(a, q, sm, sk, off, ok);
+  load_point<T, L0>(a, q, sm, sk, off, ok);
   const int k0 = blockIdx.y * kFreqChunk, k1 = min(a.K, k0 + kFreqChunk);
   for (int k = k0; k < k1; ++k) {
     const long long base = (long long)k * a.J;
-    const V bx = apply_b<T>(x + base, sm, sk, off, ok, a.lam[k], a.tau);
+    const V bx = apply_b<T, L0>(x + base, sm, sk, off, ok, a.lam[k], a.tau);
     const V bb = b[base + q];
     r[base + q] = {bb.x - bx.x, bb.y - bx.y};
   }
@@ -656,6 +666,21 @@ __global__ void build_rhs_dirichlet_kernel(const double* __restrict__ u0,
   }
 }
 
+// stencil launches of level l (level 0 takes the finest-grid specialisation)
+template <typename T>
+void residual_launch(int l, dim3 g, cudaStream_t st, v2_t<T>* r, const v2_t<T>* x,
+                     const v2_t<T>* b, const MgArgs<T>& a) {
+  if (l == 0) mg_residual_kernel<T, true><<<g, kMgThreads, 0, st>>>(r, x, b, a);
+  else mg_residual_kernel<T, false><<<g, kMgThreads, 0, st>>>(r, x, b, a);
+}
+
+template <typename T, bool ZERO>
+void smooth_launch(int l, dim3 g, cudaStream_t st, v2_t<T>* xo, const v2_t<T>* x,
+                   const v2_t<T>* b, const MgArgs<T>& a) {
+  if (l == 0) mg_smooth_kernel<T, ZERO, true><<<g, kMgThreads, 0, st>>>(xo, x, b, a);
+  else mg_smooth_kernel<T, ZERO, false><<<g, kMgThreads, 0, st>>>(xo, x, b, a);
+}
+
 template <typename T>
 bec_status vcycle_t(bec_problem* p) {
   using V = v2_t<T>;
@@ -670,26 +695,26 @@ bec_status vcycle_t(bec_problem* p) {
       BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.b, false));        // x = M^{-1} b
       for (int s = 1; s < p->mg.pre; ++s) {
         BEC_LAUNCH_BEGIN(p);
-        mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
+        residual_launch<T>(l, g, p->stream, 
             static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
         BEC_LAUNCH_CHECK(p, kResidNames[l]);
         BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.r, true));
       }
     } else {
       BEC_LAUNCH_BEGIN(p);
-      mg_smooth_kernel<T, true><<<g, kMgThreads, 0, p->stream>>>(
+      smooth_launch<T, true>(l, g, p->stream, 
           static_cast<V*>(c.x), nullptr, static_cast<const V*>(c.b), a);
       BEC_LAUNCH_CHECK(p, kSmooth0Names[l]);
       for (int s = 1; s < p->mg.pre; ++s) {
         BEC_LAUNCH_BEGIN(p);
-        mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
+        smooth_launch<T, false>(l, g, p->stream, 
             static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
         BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
         std::swap(c.x, c.r);
       }
     }
     BEC_LAUNCH_BEGIN(p);
-    mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
+    residual_launch<T>(l, g, p->stream, 
         static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
     BEC_LAUNCH_CHECK(p, kResidNames[l]);
     MgLevel& n = lv[l + 1];
@@ -717,14 +742,14 @@ bec_status vcycle_t(bec_problem* p) {
     for (int s = 0; s < p->mg.post; ++s) {
       if (p->mg.ilu) {
         BEC_LAUNCH_BEGIN(p);
-        mg_residual_kernel<T><<<g, kMgThreads, 0, p->stream>>>(
+        residual_launch<T>(l, g, p->stream, 
             static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
         BEC_LAUNCH_CHECK(p, kResidNames[l]);
         BEC_TRY_MG(ilu_sweep<T>(p, c, l, c.r, true));
         continue;
       }
       BEC_LAUNCH_BEGIN(p);
-      mg_smooth_kernel<T, false><<<g, kMgThreads, 0, p->stream>>>(
+      smooth_launch<T, false>(l, g, p->stream, 
           static_cast<V*>(c.r), static_cast<const V*>(c.x), static_cast<const V*>(c.b), a);
       BEC_LAUNCH_CHECK(p, kSmoothNames[l]);
       std::swap(c.x, c.r);
@@ -881,12 +906,12 @@ bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void
   const MgLevel& L = p->mg.lv[0];
   if (p->desc.precision == BEC_PC_FP64) {
     BEC_LAUNCH_BEGIN(p);
-    mg_residual_kernel<double><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+    mg_residual_kernel<double, true><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
         static_cast<double2*>(r), static_cast<const double2*>(x), static_cast<const double2*>(b),
         level_args<double>(p, L));
   } else {
     BEC_LAUNCH_BEGIN(p);
-    mg_residual_kernel<float><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+    mg_residual_kernel<float, true><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
         static_cast<float2*>(r), static_cast<const float2*>(x), static_cast<const float2*>(b),
         level_args<float>(p, L));
   }
@@ -898,12 +923,12 @@ bec_status mg_smooth_level0(bec_problem* p, void* xo, const void* x, const void*
   const MgLevel& L = p->mg.lv[0];
   if (p->desc.precision == BEC_PC_FP64) {
     BEC_LAUNCH_BEGIN(p);
-    mg_smooth_kernel<double, false><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+    mg_smooth_kernel<double, false, true><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
         static_cast<double2*>(xo), static_cast<const double2*>(x), static_cast<const double2*>(b),
         level_args<double>(p, L));
   } else {
     BEC_LAUNCH_BEGIN(p);
-    mg_smooth_kernel<float, false><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
+    mg_smooth_kernel<float, false, true><<<mg_grid(L.J, p->mg.K), kMgThreads, 0, p->stream>>>(
         static_cast<float2*>(xo), static_cast<const float2*>(x), static_cast<const float2*>(b),
         level_args<float>(p, L));
   }
