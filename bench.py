@@ -70,6 +70,9 @@ MG_WORDS = {"mg_smooth0_kernel": 2.0, "mg_smooth_kernel": 3.0, "mg_residual_kern
             "mg_restrict_kernel": 1.25, "mg_prolong_add_kernel": 2.25}
 MG_FLOPS = {"mg_smooth0_kernel": 14.0, "mg_smooth_kernel": 98.0, "mg_residual_kernel": 84.0,
             "mg_restrict_kernel": 36.0, "mg_prolong_add_kernel": 10.0}
+# the finest grid (M = I, 5-point K): B x costs 5 neighbour products and one
+# complex product instead of 9 + 9
+MG_FLOPS_L0 = dict(MG_FLOPS, mg_smooth_kernel=48.0, mg_residual_kernel=32.0)
 
 # FP64 FMA peak of GB300 from unit counts: 2 FP64 FMA / clock / SM x 152 SMs x
 # 2.07 GHz x 2 flops = 1.26 TFLOP/s (a throughput probe measured 1.20 TFLOP/s
@@ -550,7 +553,7 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
         for _ in range(lvl):
             ml = (ml - 1) // 2
         units = K * ml * ml
-        bpu, fpu = MG_WORDS[base] * word, MG_FLOPS[base]
+        bpu, fpu = MG_WORDS[base] * word, (MG_FLOPS_L0 if lvl == 0 else MG_FLOPS)[base]
     else:
         units = U
         bpu, fpu = 8 + 0.5 * word, 5.0 * LOG2T / 2
