@@ -138,7 +138,7 @@ def parse():
                     help="skip measuring the other preconditioner form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32", "learned_bf16",
-                                           "ilu_fp32"),
+                                           "ilu_fp32", "mg_fp32", "mg_fp64"),
                     default=None,
                     help="run a small bounded case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -869,6 +869,22 @@ def run_ncu_case(which: str):
     from paper_2002_01108_gb300 import build as bec_build
     from workloads import heat_case_2d
     bec_build.build()
+    if which in ("mg_fp32", "mg_fp64"):
+        # the variable-coefficient workload (255^2 x 256, a = exp(GRF)) on the
+        # multigrid route, two-vector Krylov basis, three P_eps^{-1} applies
+        import numpy as np
+        from workloads import grf_log_coefficient
+        a = np.exp(grf_log_coefficient(seed=5, m=M_SIDE))
+        y = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (N_STEPS, M_SIDE, M_SIDE))).cuda()
+        with Problem(2, M_SIDE, N_STEPS, route="mg", precision=which[3:], a_nodes=a,
+                     flexible=True, max_restart=2) as p:
+            p.set_eps(math.sqrt(1.0 / N_STEPS) / 2)
+            z = torch.empty_like(y)
+            for _ in range(3):
+                p.apply_Pinv(y, z)
+            torch.cuda.synchronize()
+        print(f"ncu case {which} done")
+        return 0
     if which == "ilu_fp32":
         # Example 3 at 255^2 x 256 on the ILU multigrid route, two-vector
         # Krylov basis, three P_eps^{-1} applies

@@ -364,6 +364,14 @@ bec_status bec_set_tiles(bec_problem* p, int rows_warps, int cols_warps, int tim
 bec_status bec_convert_to_float(const double* x, float* y, long long n, void* stream);
 bec_status bec_convert_to_double(const float* x, double* y, long long n, void* stream);
 
+/* y = 1/x for n doubles, by the reciprocal the FP64 multigrid smoother uses
+ * in place of a division (a float reciprocal refined by two Newton-Raphson
+ * steps; within one unit in the last place; |x| outside [2^-120, 2^120],
+ * zero, infinities and NaN take the IEEE division).  Not a construct of the
+ * paper; exported so that it can be checked.  Same conventions as the
+ * conversions above. */
+bec_status bec_reciprocal_fp64(const double* x, double* y, long long n, void* stream);
+
 /* ---- Batches of independent problems of uneven size ---------------------
  * Not a construct of the paper: many independent instances (different grid,
  * N and eps) solved together.  Each instance is a bec_problem (own

@@ -31,7 +31,8 @@ EXPORTED = (
     "bec_batch_kernel_launches", "bec_batch_free", "bec_learned_num_weights",
     "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
     "bec_learned_loss_grad", "bec_learned_fallbacks", "bec_learned_residual_ratios",
-    "bec_convert_to_float", "bec_convert_to_double", "bec_autotune", "bec_set_tiles",
+    "bec_convert_to_float", "bec_convert_to_double", "bec_reciprocal_fp64", "bec_autotune",
+    "bec_set_tiles",
     "bec_inject_fault",
 )
 
@@ -136,6 +137,7 @@ def _lib():
         "bec_set_tiles": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "bec_convert_to_float": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
         "bec_convert_to_double": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
+        "bec_reciprocal_fp64": ([D, D, ctypes.c_longlong, P], ctypes.c_int),
         "bec_relres_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, D, D, D, P], ctypes.c_int),
         "bec_profile_stop": ([P, ctypes.POINTER(KernelTime), ctypes.c_int,
@@ -171,6 +173,20 @@ def _dptr(t, U: int, name: str):
     if t.numel() != U:
         raise ValueError(f"{name} has {t.numel()} elements, expected {U}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def reciprocal_fp64(x, out=None):
+    """1/x by the FP64 reciprocal of the multigrid smoother (a contiguous
+    float64 CUDA tensor), on the current torch stream."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or not x.is_contiguous() \
+            or x.dtype != torch.float64:
+        raise TypeError("x must be a contiguous float64 CUDA tensor")
+    out = torch.empty_like(x) if out is None else out
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(_lib().bec_reciprocal_fp64(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      x.numel(), st), "bec_reciprocal_fp64")
+    return out
 
 
 def convert(x, out=None):

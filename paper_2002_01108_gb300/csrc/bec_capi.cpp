@@ -709,6 +709,12 @@ bec_status bec_convert_to_double(const float* x, double* y, long long n, void* s
   return e == cudaSuccess ? BEC_OK : cuda_fail(e, "convert_kernel_f64");
 }
 
+bec_status bec_reciprocal_fp64(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (x == nullptr || y == nullptr))) return einval("bad reciprocal arguments");
+  const cudaError_t e = launch_rcp64(x, y, n, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BEC_OK : cuda_fail(e, "rcp64_kernel");
+}
+
 const char* bec_status_string(bec_status s) {
   switch (s) {
     case BEC_OK: return "BEC_OK";

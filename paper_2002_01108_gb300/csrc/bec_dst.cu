@@ -225,6 +225,17 @@ __global__ void convert_kernel_f64(const float* __restrict__ x, double* __restri
 
 }  // namespace
 
+__global__ void rcp64_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y[g] = rcp64(x[g]);
+}
+
+cudaError_t launch_rcp64(const double* x, double* y, long long n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  rcp64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(const void* x, void* y, long long n, int to_float, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = (unsigned)((n + 255) / 256);

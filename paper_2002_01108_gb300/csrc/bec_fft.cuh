@@ -65,6 +65,28 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 }
 
 // value conversion between the preconditioner's storage types
+// 1/x in FP64 with few FP64 instructions (a division is a long sequence on
+// GB300, whose FP64 pipe issues 2 operations per clock per SM): the float
+// reciprocal of the float-rounded x (__frcp_rn, relative error <= 2^-23
+// against 1/x), then two Newton-Raphson steps for f(y) = 1/y - x,
+// y <- y + y (1 - x y), each of which squares the relative error
+// (2^-23 -> 2^-46 -> below the FP64 rounding).  The result is within one
+// unit in the last place of 1/x.  |x| outside [2^-120, 2^120] (and zero,
+// infinities, NaN) take the division.
+static __device__ __noinline__ double rcp64_slow(double x) { return 1.0 / x; }
+
+__device__ __forceinline__ double rcp64(double x) {
+  const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7FFu;
+  if (e - (1023u - 120u) <= 240u) {
+    double y = f32_to_f64(__frcp_rn(f64_to_f32(x)));
+    double r = fma(-x, y, 1.0);
+    y = fma(y, r, y);
+    r = fma(-x, y, 1.0);
+    return fma(y, r, y);
+  }
+  return rcp64_slow(x);
+}
+
 template <typename TO, typename TI>
 __device__ __forceinline__ TO convert(TI x) {
   if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8) return f64_to_f32(x);

@@ -237,6 +237,8 @@ bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale
 bec_status launch_rinv_table(bec_problem* p);
 // y = x converted between FP64 and FP32 (to_float: double -> float) by the
 // integer conversions of the FP32 passes
+// y = 1/x by the FP64 reciprocal of the multigrid smoother (rcp64)
+cudaError_t launch_rcp64(const double* x, double* y, long long n, cudaStream_t st);
 cudaError_t launch_convert(const void* x, void* y, long long n, int to_float, cudaStream_t st);
 // the shared memory pass `which` (0 x-DST, 1 y-DST, 2 time pass) needs at
 // block width w (0 = the default)

@@ -111,7 +111,10 @@ mg_smooth_kernel(v2_t<T>* __restrict__ xo, const v2_t<T>* __restrict__ x,
     const long long base = (long long)k * a.J;
     const V lam = a.lam[k];
     const V D = {lam.x * sm[4] + a.tau * sk[4], lam.y * sm[4]};
-    const T inv = a.omega / (D.x * D.x + D.y * D.y);
+    const T d2 = D.x * D.x + D.y * D.y;
+    T inv;
+    if constexpr (sizeof(T) == 8) inv = a.omega * rcp64(d2);   // no FP64 division
+    else inv = a.omega / d2;
     V rr = b[base + q];
     V x0 = {0, 0};
     if (!ZERO) {

@@ -66,3 +66,27 @@ def test_float_to_double_matches_the_hardware_bit_for_bit():
     nan = np.isnan(ref.cpu().numpy())
     assert np.array_equal(np.isnan(y.cpu().numpy()), nan)
     assert np.array_equal(a[~nan], b[~nan])
+
+
+def test_fp64_reciprocal_of_the_smoother_is_within_one_ulp():
+    """The FP64 multigrid smoother's reciprocal (float reciprocal plus two
+    Newton-Raphson steps) against IEEE division: within one unit in the last
+    place over the fast range [2^-120, 2^120] in magnitude, both signs, exact
+    powers of two and values next to them; the values outside that range,
+    zeros, infinities and NaN take the division and agree exactly."""
+    import torch
+    from paper_2002_01108_gb300 import reciprocal_fp64
+    rng = np.random.default_rng(5)
+    x = rng.uniform(1, 2, 200000) * np.exp2(rng.integers(-119, 119, 200000))
+    x *= np.where(rng.random(200000) < 0.5, -1.0, 1.0)
+    p2 = np.exp2(np.arange(-119, 120, dtype=np.float64))
+    x = np.concatenate([x, p2, np.nextafter(p2, np.inf), np.nextafter(p2, 0.0), -p2])
+    y = reciprocal_fp64(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = 1.0 / x
+    ulp = np.spacing(np.abs(ref))
+    assert np.max(np.abs(y - ref) / ulp) <= 1.0
+    slow = np.array([2.0 ** -125, -2.0 ** 125, 1e-300, 1e300, 0.0, -0.0, np.inf, -np.inf])
+    ys = reciprocal_fp64(torch.from_numpy(slow).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(ys, 1.0 / slow)
+    yn = reciprocal_fp64(torch.tensor([np.nan], dtype=torch.float64).cuda()).cpu().numpy()
+    assert np.isnan(yn[0])
