@@ -87,6 +87,7 @@ def test_fp64_reciprocal_of_the_smoother_is_within_one_ulp():
     assert np.max(np.abs(y - ref) / ulp) <= 1.0
     slow = np.array([2.0 ** -125, -2.0 ** 125, 1e-300, 1e300, 0.0, -0.0, np.inf, -np.inf])
     ys = reciprocal_fp64(torch.from_numpy(slow).cuda()).cpu().numpy()
-    np.testing.assert_array_equal(ys, 1.0 / slow)
+    with np.errstate(divide="ignore"):
+        np.testing.assert_array_equal(ys, 1.0 / slow)
     yn = reciprocal_fp64(torch.tensor([np.nan], dtype=torch.float64).cuda()).cpu().numpy()
     assert np.isnan(yn[0])
