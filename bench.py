@@ -699,6 +699,69 @@ def measure_bdf2_headline(args, form):
             "true_relres": info["true_relres"]}
 
 
+def measure_precision_workload(args):
+    """The large precision workload: 2D heat on a 511^2 grid with N = 512
+    steps (133.7M unknowns), eps = sqrt(tau), seeded source and initial value.
+    The FP32/complex64 P_eps^-1 inside FP64 FGMRES(20) and the plain FP64
+    form, each to RES 1e-8, then the two solutions compared.  The vectors
+    (1.07 GB each) are far larger than L2."""
+    import torch
+    from paper_2002_01108_gb300 import Problem
+    from workloads import heat_case_2d
+    m, N = 511, 512
+    case = heat_case_2d(seed=3, m=m, N=N, eps=math.sqrt(1.0 / N))
+    out = {"workload": f"heat2d {m}x{m}, N={N} ({m * m * N} unknowns), eps=sqrt(tau), "
+                       "FGMRES(20) to RES 1e-8"}
+    sols = {}
+    for form in ("fp32", "fp64"):
+        prob = Problem(2, m, N, precision=form, max_restart=20, flexible=True)
+        prob.set_eps(case.eps)
+        tiles = prob.autotune()
+        f = prob.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
+        u = torch.empty_like(f)
+        kw = dict(restart=20, rtol=RTOL, maxit=200, flexible=True)
+        prob.gmres_solve(f, u, **kw)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(1, min(args.steps, 3))
+        ev0.record(prob.stream)
+        for _ in range(steps):
+            _, info = prob.gmres_solve(f, u, **kw)
+        ev1.record(prob.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        # P_eps^-1 alone, 2 warm-ups and 4 timed applies on f
+        z = torch.empty_like(f)
+        for _ in range(2):
+            prob.apply_Pinv(f, z)
+        ev0.record(prob.stream)
+        for _ in range(4):
+            prob.apply_Pinv(f, z)
+        ev1.record(prob.stream)
+        torch.cuda.synchronize()
+        pinv_ms = ev0.elapsed_time(ev1) / 4
+        del z
+        U = prob.U
+        pinv = pinv_report(form, {"pinv_ms": pinv_ms, "pinv_passes": {}}, U)
+        pinv.pop("dram_bytes_per_apply"), pinv.pop("dram_gbs"), pinv.pop("passes_ms")
+        out[form + "_preconditioner"] = {
+            "value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "timed_solves": steps,
+            "iterations": info["iters"], "true_relres": info["true_relres"],
+            "autotuned_warps_per_block": {k: tiles[k] for k in ("rows_warps", "cols_warps",
+                                                                 "time_warps")},
+            "apply_pinv": pinv}
+        sols[form] = u
+        del f
+        prob.close()
+    d = torch.linalg.vector_norm(sols["fp32"] - sols["fp64"]) / torch.linalg.vector_norm(sols["fp64"])
+    out["rel_diff_fp32_vs_fp64_solution"] = float(d)
+    out["note"] = ("the error of both forms against the oracle's sequential stepping is checked "
+                   "by the precision tests (<= 1e-8 when solved to 1e-10)")
+    del sols
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_batch(args, ws=1, rank=0, dist=None):
     """The uneven batch: 64 instances, side in {63, 127, 255}, N in {32, ..., 512},
     ln eps ~ U[ln 1e-4, ln sqrt(tau)], FP32 preconditioner in FP64 FGMRES(10)
@@ -835,6 +898,7 @@ def run_gpu(args):
             "learned_note": "the V-cycle, then the trained network's correction (BF16 activations, "
                             "FP32 accumulation), one smoothing sweep and the minimal-residual judge"}
         line["batch"] = measure_batch(args, ws, rank, dist)
+        line["precision_workload"] = measure_precision_workload(args)
         line["paper_table1_row"] = measure_paper_table1(args)
         line["bdf2"] = {
             "workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, BDF2 (r = 3/2, -2, 1/2; pre-start "

@@ -72,6 +72,14 @@ dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restric
   }
 }
 
+// Blocks per SM that the register bound of dst_cols_kernel asks for, as warps
+// per SM over the block's warps (at least one block): for n <= 256, 40 warps
+// in FP32 (48 registers a thread) and 24 in FP64 (80 registers); for n = 512,
+// 16 warps in FP32; longer transforms are left free.
+__host__ __device__ constexpr int cols_min_blocks(int bytes, int logn, int warps) {
+  return (bytes == 4 ? (logn <= 8 ? 40 : logn == 9 ? 16 : warps) : (logn <= 8 ? 24 : warps)) / warps;
+}
+
 // DST along the rows of every slice, in place: slice s (s < nslices, at
 // data + s * slice_stride) holds m rows of ncols values, row j at j *
 // row_stride, and the transform runs down each column (along j).  A block
@@ -80,7 +88,7 @@ dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restric
 // y-DST of [ny][nx] slices; 3D: the y-DST of every [ny][nx] plane and the
 // z-DST of [nz][ny nx] slices.
 template <typename T, int LOGN, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, cols_min_blocks(sizeof(T), LOGN, WARPS))
 dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice_stride,
                 long long nslices, const T* __restrict__ sin2, const v2_t<T>* __restrict__ tw) {
   constexpr int LSC = line_slots(LOGN);
@@ -88,24 +96,30 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = blockIdx.x * W;
-  const int total = m * W;
+  // thread t always handles column c = t mod W of the tile and the rows
+  // j = t / W + JS i.  In FP32 the tile arrives by asynchronous copies, which
+  // hold no registers, so all of a thread's loads are in flight together.
+  constexpr int JS = WARPS * 32 / W;
+  const int c = threadIdx.x % W, j0 = threadIdx.x / W;
+  const int x = blockIdx.x * W + c;
+  const bool xin = x < ncols;
+  T* const slot = sm + c * LSC;
   for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y) {
-    T* base = data + sl * slice_stride;
+    T* const col = data + sl * slice_stride + (xin ? x : 0);   // row j at col[j row_stride]
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll 4
-    for (int e = threadIdx.x; e < total; e += WARPS * 32) {
-      const int j = e / W, c = e % W;
-      const int x = x0 + c;
-      sm[c * LSC + j] = x < ncols ? base[(long long)j * row_stride + x] : T(0);
+      for (int j = j0; j < m; j += JS) cp_async4(slot + j, col + (long long)j * row_stride, xin);
+      cp_async_wait_all();
+    } else {                                 // FP64: bound by its arithmetic, not by loads
+#pragma unroll 4
+      for (int j = j0; j < m; j += JS) slot[j] = xin ? col[(long long)j * row_stride] : T(0);
     }
     __syncthreads();
     warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * LSC, LSC, sin2, tw, lane);
     __syncthreads();
+    if (xin) {
 #pragma unroll 4
-    for (int e = threadIdx.x; e < total; e += WARPS * 32) {
-      const int j = e / W, c = e % W;
-      const int x = x0 + c;
-      if (x < ncols) base[(long long)j * row_stride + x] = sm[c * LSC + j];
+      for (int j = j0; j < m; j += JS) col[(long long)j * row_stride] = slot[j];
     }
     __syncthreads();
   }

@@ -87,6 +87,19 @@ __device__ __forceinline__ double rcp64(double x) {
   return rcp64_slow(x);
 }
 
+// Asynchronous 4-byte copy from global to shared memory (no register holds
+// the value, so many can be in flight per thread).  valid = false copies no
+// bytes and writes zero.  cp_async_wait_all() makes the thread's own copies
+// visible to it; a block barrier after it makes them visible to the block.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem),
+               "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 template <typename TO, typename TI>
 __device__ __forceinline__ TO convert(TI x) {
   if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8) return f64_to_f32(x);

@@ -100,13 +100,36 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long q0 = (long long)blockIdx.x * W;
 
-  // load + D_eps scaling: mode c of the tile -> line c/2, real (c even) or imaginary part
+  // load + D_eps scaling: mode c of the tile -> line c/2, real (c even) or
+  // imaginary part.  Thread t always handles mode c = t mod W and the rows
+  // j = t / W + JS i.  In FP32 it issues its loads in groups of up to 16
+  // before the group's stores, so that they are in flight together.
+  constexpr int JS = WARPS * 32 / W;
+  constexpr int NI = (N + JS - 1) / JS;
+  const int c = threadIdx.x % W, j0 = threadIdx.x / W;
+  const bool qin = q0 + c < J;
+  T* const slot = sm + (c >> 1) * 2 * LSC + (c & 1);          // element j at slot[2 j]
+  T* const col = data + (qin ? q0 + c : 0);                    // element j at col[j J]
+  if constexpr (sizeof(T) == 4) {
+    constexpr int GMAX = LOGN <= 8 ? 16 : 8;   // loads in flight per group (registers)
+    constexpr int G = NI < GMAX ? NI : GMAX;
+#pragma unroll
+    for (int g = 0; g < NI; g += G) {
+      T v[G];
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int j = j0 + JS * (g + i);
+        v[i] = (qin && (N % JS == 0 || j < N)) ? col[(long long)j * J] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int j = j0 + JS * (g + i);
+        if (N % JS == 0 || j < N) slot[2 * j] = v[i] * es[j];
+      }
+    }
+  } else {                                   // FP64: bound by its arithmetic, not by loads
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
-    const int j = e / W, c = e % W;
-    const long long q = q0 + c;
-    const T v = q < J ? data[(long long)j * J + q] * es[j] : T(0);
-    sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] = v;
+    for (int j = j0; j < N; j += JS) slot[2 * j] = qin ? col[(long long)j * J] * es[j] : T(0);
   }
   __syncthreads();
 
@@ -143,6 +166,11 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
       if (rinv != nullptr) {           // 1 / |d|^2 from the table ([q][k], coalesced in k)
         s1 = qa < J ? scale * rinv[qa * NK + k] : T(0);
         s2 = qa + 1 < J ? scale * rinv[(qa + 1) * NK + k] : s1;
+      } else if constexpr (sizeof(T) == 4) {
+        // |d|^2 lies far inside the normal range, where the approximate
+        // division is within 2 units in the last place
+        s1 = __fdividef(scale, fma(d1r, d1r, d1i * d1i));
+        s2 = __fdividef(scale, fma(d2r, d2r, d2i * d2i));
       } else {
         s1 = scale / fma(d1r, d1r, d1i * d1i);
         s2 = scale / fma(d2r, d2r, d2i * d2i);
@@ -158,11 +186,9 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
   warp_fft<T, +1, LOGN>(line, tw, lane);
   __syncthreads();
 
+  if (qin) {
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * W; e += WARPS * 32) {
-    const int j = e / W, c = e % W;
-    const long long q = q0 + c;
-    if (q < J) data[(long long)j * J + q] = sm[(c >> 1) * 2 * LSC + 2 * j + (c & 1)] * eis[j];
+    for (int j = j0; j < N; j += JS) col[(long long)j * J] = slot[2 * j] * eis[j];
   }
 }
 
