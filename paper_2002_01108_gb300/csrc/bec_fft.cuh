@@ -187,13 +187,19 @@ __device__ __forceinline__ void fft_pass(v2_t<T>* buf, const v2_t<T>* __restrict
   constexpr int NB = n / R;
   constexpr int PER = (NB + 31) / 32;
   constexpr int TWSTEP = n / (Ns * R);
+  // Padded positions as a per-thread base plus compile-time offsets:
+  // pidx(j + r NB) = pidx(j) + r NB + (r NB) / 16 because j < NB and the
+  // multiples of 16 are multiples of NB (or NB of 16); likewise for the
+  // writes, whose butterfly outputs base + r Ns never straddle a multiple of
+  // 16 except at multiples of 16 from base.
   V v[PER][R];
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int j = lane + 32 * t;
     if (NB % 32 == 0 || j < NB) {
+      const int rb = pidx<PIN>(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[t][r] = buf[pidx<PIN>(j + r * NB)];
+      for (int r = 0; r < R; ++r) v[t][r] = buf[rb + r * NB + (PIN ? (r * NB) >> 4 : 0)];
     }
   }
   __syncwarp();
@@ -221,9 +227,9 @@ __device__ __forceinline__ void fft_pass(v2_t<T>* buf, const v2_t<T>* __restrict
         }
       }
       radix_dft<R, SIGN>(v[t]);
-      const int base = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
+      const int wb = pidx<POUT>(((j >> LOGNS) << (LOGNS + LOGR)) + k);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pidx<POUT>(base + r * Ns)] = v[t][r];
+      for (int r = 0; r < R; ++r) buf[wb + r * Ns + (POUT ? (r * Ns) >> 4 : 0)] = v[t][r];
     }
   }
   __syncwarp();
