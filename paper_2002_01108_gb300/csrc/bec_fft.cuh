@@ -276,32 +276,49 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
                                               const v2_t<T>* __restrict__ tw, int lane) {
   using V = v2_t<T>;
   constexpr int n = 1 << LOGN;
-  constexpr int PERJ = (n + 31) / 32;
-  V c[PERJ];
-#pragma unroll
-  for (int t = 0; t < PERJ; ++t) {
-    const int j = lane + 32 * t;
-    if (n % 32 == 0 || j < n) {
-      T xa = 0, xan = 0, xb = 0, xbn = 0;
-      if (j > 0) {
-        xa = raw[j - 1];
-        xan = raw[n - j - 1];
-        xb = raw[rs + j - 1];
-        xbn = raw[rs + n - j - 1];
-      }
-      const T s = sin2[j];
-      c[t] = {s * (xa + xan) + (xa - xan), s * (xb + xbn) + (xb - xbn)};
-    }
-  }
-  __syncwarp();
   V* line = reinterpret_cast<V*>(raw);
+  // The pre-pass is fused into the first radix pass of the FFT, which reads
+  // its inputs y_j straight from the two real lines (no round trip of y
+  // through shared memory); the first pass has no twiddles.
+  {
+    constexpr int LOGR = pass_logr(LOGN, 0), R = 1 << LOGR;
+    constexpr int NB = n / R;
+    constexpr int PER = (NB + 31) / 32;
+    V v[PER][R];
 #pragma unroll
-  for (int t = 0; t < PERJ; ++t) {
-    const int j = lane + 32 * t;
-    if (n % 32 == 0 || j < n) line[j] = c[t];
+    for (int t = 0; t < PER; ++t) {
+      const int j = lane + 32 * t;
+      if (NB % 32 == 0 || j < NB) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = j + r * NB;
+          T xa = 0, xan = 0, xb = 0, xbn = 0;
+          if (r > 0 || e > 0) {
+            xa = raw[e - 1];
+            xan = raw[n - e - 1];
+            xb = raw[rs + e - 1];
+            xbn = raw[rs + n - e - 1];
+          }
+          const T s = sin2[e];
+          v[t][r] = {s * (xa + xan) + (xa - xan), s * (xb + xbn) + (xb - xbn)};
+        }
+      }
+    }
+    __syncwarp();
+    constexpr bool POUT = LOGR < LOGN;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int j = lane + 32 * t;
+      if (NB % 32 == 0 || j < NB) {
+        radix_dft<R, -1>(v[t]);
+        const int wb = pidx<POUT>(j << LOGR);
+#pragma unroll
+        for (int r = 0; r < R; ++r) line[wb + r + (POUT ? r >> 4 : 0)] = v[t][r];
+      }
+    }
+    __syncwarp();
+    fft_passes<T, -1, LOGN, LOGR>(line, tw, lane);
   }
-  __syncwarp();
-  warp_fft<T, -1, LOGN>(line, tw, lane);
 
   // Separate the two real spectra.  For k in [0, n/2): r_k feeds the running
   // sum of the odd outputs, e_k is the even output S_{2k}.
