@@ -18,11 +18,11 @@ template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
-  constexpr int LSC = line_slots(LOGN);      // complex slots per line
+  constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per line
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* raw = sm + (size_t)warp * 2 * LSC;
+  T* raw = sm + (size_t)warp * 2 * RS;
   const long long r0 = 2 * ((long long)blockIdx.x * WARPS + warp);
   if (r0 >= rows) return;                    // whole warp leaves; no block barrier below
   const bool hasb = r0 + 1 < rows;
@@ -45,12 +45,12 @@ dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restric
       const int j = lane + 32 * (t0 + t);
       if (j < m) {
         raw[j] = convert<T>(va[t]);
-        raw[LSC + j] = convert<T>(vb[t]);
+        raw[RS + j] = convert<T>(vb[t]);
       }
     }
   }
   __syncwarp();
-  warp_dst_pair<T, LOGN>(raw, LSC, sin2, tw, lane);
+  warp_dst_pair<T, LOGN>(raw, RS, sin2, tw, lane);
   TO* oa = out + r0 * m;
 #pragma unroll
   for (int t0 = 0; t0 < PER; t0 += G) {
@@ -58,8 +58,8 @@ dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restric
 #pragma unroll
     for (int t = 0; t < G; ++t) {
       const int j = lane + 32 * (t0 + t);
-      wa[t] = j < m ? convert<TO>(raw[j]) : TO(0);
-      wb[t] = j < m ? convert<TO>(raw[LSC + j]) : TO(0);
+      wa[t] = j < m ? convert<TO>(raw[dst_out<T, LOGN>(j)]) : TO(0);
+      wb[t] = j < m ? convert<TO>(raw[RS + dst_out<T, LOGN>(j)]) : TO(0);
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
@@ -91,7 +91,7 @@ template <typename T, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, cols_min_blocks(sizeof(T), LOGN, WARPS))
 dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice_stride,
                 long long nslices, const T* __restrict__ sin2, const v2_t<T>* __restrict__ tw) {
-  constexpr int LSC = line_slots(LOGN);
+  constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per column
   constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T* sm = reinterpret_cast<T*>(smem_bytes);
@@ -103,7 +103,7 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
   const int c = threadIdx.x % W, j0 = threadIdx.x / W;
   const int x = blockIdx.x * W + c;
   const bool xin = x < ncols;
-  T* const slot = sm + c * LSC;
+  T* const slot = sm + c * RS;
   for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y) {
     T* const col = data + sl * slice_stride + (xin ? x : 0);   // row j at col[j row_stride]
     if constexpr (sizeof(T) == 4) {
@@ -115,11 +115,11 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
       for (int j = j0; j < m; j += JS) slot[j] = xin ? col[(long long)j * row_stride] : T(0);
     }
     __syncthreads();
-    warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * LSC, LSC, sin2, tw, lane);
+    warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * RS, RS, sin2, tw, lane);
     __syncthreads();
     if (xin) {
 #pragma unroll 4
-      for (int j = j0; j < m; j += JS) col[(long long)j * row_stride] = slot[j];
+      for (int j = j0; j < m; j += JS) col[(long long)j * row_stride] = slot[dst_out<T, LOGN>(j)];
     }
     __syncthreads();
   }
@@ -135,7 +135,7 @@ cudaError_t prepare(Kern k, size_t smem) {
 template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 bec_status rows_launch(bec_problem* p, const void* in, void* out, long long rows,
                        const T* sin2, const v2_t<T>* tw) {
-  const size_t smem = (size_t)WARPS * 2 * line_slots(LOGN) * sizeof(T);
+  const size_t smem = (size_t)WARPS * 2 * dst_line_stride(LOGN, sizeof(T)) * sizeof(T);
   auto k = dst_rows_kernel<T, TI, TO, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
   const long long pairs = (rows + 1) / 2;
@@ -149,7 +149,7 @@ bec_status rows_launch(bec_problem* p, const void* in, void* out, long long rows
 
 template <typename T, int LOGN, int WARPS>
 bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>* tw) {
-  const size_t smem = (size_t)WARPS * 2 * line_slots(LOGN) * sizeof(T);
+  const size_t smem = (size_t)WARPS * 2 * dst_line_stride(LOGN, sizeof(T)) * sizeof(T);
   auto k = dst_cols_kernel<T, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
   const long long m = p->m, m2 = m * m;

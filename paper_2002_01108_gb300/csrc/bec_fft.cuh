@@ -241,14 +241,15 @@ __host__ __device__ constexpr int pass_logr(int logn, int logns) {
   return (logn - logns >= 3 && logn - logns != 4) ? 3 : (logn - logns >= 2 ? 2 : 1);
 }
 
-template <typename T, int SIGN, int LOGN, int LOGNS>
+// PLAST: the last pass also writes the padded layout
+template <typename T, int SIGN, int LOGN, int LOGNS, bool PLAST = false>
 __device__ __forceinline__ void fft_passes(v2_t<T>* buf, const v2_t<T>* __restrict__ tw,
                                            int lane) {
   if constexpr (LOGNS < LOGN) {
     constexpr int LOGR = pass_logr(LOGN, LOGNS);
     constexpr bool first = LOGNS == 0, last = LOGNS + LOGR == LOGN;
-    fft_pass<T, SIGN, LOGN, LOGNS, LOGR, !first, !last>(buf, tw, lane);
-    fft_passes<T, SIGN, LOGN, LOGNS + LOGR>(buf, tw, lane);
+    fft_pass<T, SIGN, LOGN, LOGNS, LOGR, !first, !last || PLAST>(buf, tw, lane);
+    fft_passes<T, SIGN, LOGN, LOGNS + LOGR, PLAST>(buf, tw, lane);
   }
 }
 
@@ -261,21 +262,41 @@ __device__ __forceinline__ void warp_fft(v2_t<T>* buf, const v2_t<T>* __restrict
   fft_passes<T, SIGN, LOGN, 0>(buf, tw, lane);
 }
 
+// Output layout of warp_dst_pair.  FP64 writes S_k in natural order.  FP32
+// writes them with one pad slot after every 2 CH reals, where lane l owns
+// the CH = max(1, n/64) consecutive k from CH l: its stores then fall on
+// distinct banks.  dst_out<T, LOGN>(j) is the slot of output j of a line;
+// dst_line_stride(logn, bytes) the real slots from line a to line b (odd, and
+// at least what the padded complex FFT line needs).
+template <typename T, int LOGN>
+__device__ __forceinline__ int dst_out(int j) {
+  if constexpr (sizeof(T) == 8) return j;
+  else return j + (j >> (LOGN >= 6 ? LOGN - 5 : 1));
+}
+__host__ __device__ constexpr int dst_line_stride(int logn, int bytes) {
+  if (bytes == 8) return line_slots(logn);
+  const int n = 1 << logn, shift = logn >= 6 ? logn - 5 : 1;
+  const int need = (n - 2) + ((n - 2) >> shift) + 1;        // last output slot + 1
+  return (need > line_slots(logn) ? need : line_slots(logn)) | 1;
+}
+
 // DST-I of two real lines at once, by one warp.  With n = 2^LOGN, each line
 // holds x_1..x_{n-1} (x_0 = x_n = 0): line a at raw[0 .. n-2], line b at
-// raw[rs .. rs+n-2] (rs >= n+1).  On return the same slots hold
-//     4 S_k = 4 sum_{j=1}^{n-1} x_j sin(pi j k / n),  k = 1..n-1.
+// raw[rs .. rs+n-2] (rs = dst_line_stride(LOGN, sizeof(T))).  On return
+//     4 S_k = 4 sum_{j=1}^{n-1} x_j sin(pi j k / n),  k = 1..n-1,
+// of line a is at raw[dst_out(k - 1)] and that of line b at
+// raw[rs + dst_out(k - 1)].
 // Method: y_j = 2 sin(j pi / n)(x_j + x_{n-j}) + (x_j - x_{n-j}) makes the odd
 // outputs the running sums of the real parts and the even outputs the
 // imaginary parts of one length-n real DFT; both lines share one complex FFT
-// (y^a + i y^b).  `raw` must hold 2 line_slots(LOGN) reals (it doubles as the
-// complex line).
-// sin2[j] = 2 sin(j pi / n), tw[t] = e^{-2 pi i t / n}.
+// (y^a + i y^b).  `raw` must hold 2 rs reals (it doubles as the complex
+// line).  sin2[j] = 2 sin(j pi / n), tw[t] = e^{-2 pi i t / n}.
 template <typename T, int LOGN>
 __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restrict__ sin2,
                                               const v2_t<T>* __restrict__ tw, int lane) {
   using V = v2_t<T>;
   constexpr int n = 1 << LOGN;
+  constexpr bool PAD = sizeof(T) == 4;     // FFT output and S_k in the padded layouts
   V* line = reinterpret_cast<V*>(raw);
   // The pre-pass is fused into the first radix pass of the FFT, which reads
   // its inputs y_j straight from the two real lines (no round trip of y
@@ -305,7 +326,7 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
       }
     }
     __syncwarp();
-    constexpr bool POUT = LOGR < LOGN;
+    constexpr bool POUT = LOGR < LOGN || PAD;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
       const int j = lane + 32 * t;
@@ -317,122 +338,69 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
       }
     }
     __syncwarp();
-    fft_passes<T, -1, LOGN, LOGR>(line, tw, lane);
+    fft_passes<T, -1, LOGN, LOGR, PAD>(line, tw, lane);
   }
 
   // Separate the two real spectra.  For k in [0, n/2): r_k feeds the running
-  // sum of the odd outputs, e_k is the even output S_{2k}.
+  // sum of the odd outputs, e_k is the even output S_{2k}.  Lane l owns the
+  // CH consecutive k from CH l: a serial running sum and one warp scan of
+  // the lane totals.  In FP32 the FFT output and the S_k are in the padded
+  // layouts, so these reads and writes are free of bank conflicts.
   constexpr int H = n / 2;
   constexpr int CH = H >= 32 ? H / 32 : 1;
-  if constexpr (sizeof(T) == 4) {
-    // FP32: lane owns k = lane + 32 i, so the reads of line[k] and line[n-k]
-    // are conflict-free and the writes at most 2-way; the running sum is one
-    // warp scan per row i plus the carry of the rows before.
-    T oa[CH], ob[CH], ea[CH], eb[CH];
-    T ca = 0, cb = 0;
+  const int k0 = lane * CH;
+  const bool act = k0 < H;
+  T ra[CH], rb[CH], ea[CH], eb[CH];
+  T sa = 0, sb = 0;
 #pragma unroll
-    for (int i = 0; i < CH; ++i) {
-      const int k = lane + 32 * i;
-      T ra = 0, rb = 0;
-      ea[i] = eb[i] = 0;
-      if (k < H) {
-        const V C = line[k];
-        if (k == 0) {
-          ra = C.x;
-          rb = C.y;
-        } else {
-          const V Cn = line[n - k];
-          ra = C.x + Cn.x;
-          rb = C.y + Cn.y;
-          ea[i] = Cn.y - C.y;
-          eb[i] = C.x - Cn.x;
-        }
-      }
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const T va = __shfl_up_sync(0xffffffffu, ra, off);
-        const T vb = __shfl_up_sync(0xffffffffu, rb, off);
-        if (lane >= off) {
-          ra += va;
-          rb += vb;
-        }
-      }
-      oa[i] = ra + ca;
-      ob[i] = rb + cb;
-      ca += __shfl_sync(0xffffffffu, ra, 31);
-      cb += __shfl_sync(0xffffffffu, rb, 31);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < CH; ++i) {
-      const int k = lane + 32 * i;
-      if (k < H) {
-        raw[2 * k] = oa[i];                // 4 S_{2k+1}
-        raw[rs + 2 * k] = ob[i];
-        if (k > 0) {
-          raw[2 * k - 1] = ea[i];          // 4 S_{2k}
-          raw[rs + 2 * k - 1] = eb[i];
-        }
-      }
-    }
-    __syncwarp();
-  } else {
-    // FP64: lane owns the CH consecutive k from lane * CH: a serial running
-    // sum and one warp scan of the lane totals, the fewest FP64 additions
-    const int k0 = lane * CH;
-    const bool act = k0 < H;
-    T ra[CH], rb[CH], ea[CH], eb[CH];
-    T sa = 0, sb = 0;
-#pragma unroll
-    for (int i = 0; i < CH; ++i) {
-      ra[i] = rb[i] = ea[i] = eb[i] = 0;
-      if (act) {
-        const int k = k0 + i;
-        const V C = line[k];
-        if (k == 0) {
-          ra[i] = C.x;
-          rb[i] = C.y;
-        } else {
-          const V Cn = line[n - k];
-          ra[i] = C.x + Cn.x;
-          rb[i] = C.y + Cn.y;
-          ea[i] = Cn.y - C.y;
-          eb[i] = C.x - Cn.x;
-        }
-      }
-      sa += ra[i];
-      ra[i] = sa;
-      sb += rb[i];
-      rb[i] = sb;
-    }
-    // exclusive prefix of the per-lane totals across the warp
-    T ta = sa, tb = sb;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const T va = __shfl_up_sync(0xffffffffu, ta, off);
-      const T vb = __shfl_up_sync(0xffffffffu, tb, off);
-      if (lane >= off) {
-        ta += va;
-        tb += vb;
-      }
-    }
-    ta -= sa;
-    tb -= sb;
-    __syncwarp();
+  for (int i = 0; i < CH; ++i) {
+    ra[i] = rb[i] = ea[i] = eb[i] = 0;
     if (act) {
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int k = k0 + i;
-        raw[2 * k] = ra[i] + ta;           // 4 S_{2k+1}
-        raw[rs + 2 * k] = rb[i] + tb;
-        if (k > 0) {
-          raw[2 * k - 1] = ea[i];          // 4 S_{2k}
-          raw[rs + 2 * k - 1] = eb[i];
-        }
+      const int k = k0 + i;
+      const V C = line[pidx<PAD>(k)];
+      if (k == 0) {
+        ra[i] = C.x;
+        rb[i] = C.y;
+      } else {
+        const V Cn = line[pidx<PAD>(n - k)];
+        ra[i] = C.x + Cn.x;
+        rb[i] = C.y + Cn.y;
+        ea[i] = Cn.y - C.y;
+        eb[i] = C.x - Cn.x;
       }
     }
-    __syncwarp();
+    sa += ra[i];
+    ra[i] = sa;
+    sb += rb[i];
+    rb[i] = sb;
   }
+  // exclusive prefix of the per-lane totals across the warp
+  T ta = sa, tb = sb;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T va = __shfl_up_sync(0xffffffffu, ta, off);
+    const T vb = __shfl_up_sync(0xffffffffu, tb, off);
+    if (lane >= off) {
+      ta += va;
+      tb += vb;
+    }
+  }
+  ta -= sa;
+  tb -= sb;
+  __syncwarp();
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int k = k0 + i;
+      raw[dst_out<T, LOGN>(2 * k)] = ra[i] + ta;             // 4 S_{2k+1}
+      raw[rs + dst_out<T, LOGN>(2 * k)] = rb[i] + tb;
+      if (k > 0) {
+        raw[dst_out<T, LOGN>(2 * k - 1)] = ea[i];            // 4 S_{2k}
+        raw[rs + dst_out<T, LOGN>(2 * k - 1)] = eb[i];
+      }
+    }
+  }
+  __syncwarp();
 }
 
 }  // namespace bec

@@ -83,7 +83,8 @@ int default_width(int which, int tsize) {
 size_t pass_smem_bytes(int which, int logn, int fp64, int w) {
   const int tsize = fp64 ? 8 : 4;
   if (w == 0) w = default_width(which, tsize);
-  return (size_t)w * 2 * line_slots(logn) * tsize;
+  const int slots = which == 2 ? line_slots(logn) : dst_line_stride(logn, tsize);
+  return (size_t)w * 2 * slots * tsize;
 }
 
 bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
