@@ -105,21 +105,21 @@ def net_fwd_flops(m: int) -> float:
 # two-iteration FP32-form solve); absent = not captured for the current build
 # of the kernel.  The writes are what left L2 while the kernel ran.
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): 133235200 + 81506048,
-    ("dst_cols_kernel", "fp64"): 133211648 + 73886720,
-    ("time_pass_kernel", "fp64"): 200390144 + 75095040,
-    ("dst_rows_kernel", "fp32"): 133203712 + 32083712,
-    ("dst_cols_kernel", "fp32"): 66619904 + 8134144,
-    ("time_pass_kernel", "fp32"): 66635520 + 7955200,
-    ("stencil_dots_kernel", "fp32"): 272325632 + 104049664,
-    ("combine_kernel", "fp32"): 266389760 + 100883200,
+    ("dst_rows_kernel", "fp64"): 133213696 + 80448000,
+    ("dst_cols_kernel", "fp64"): 133240064 + 73878016,
+    ("time_pass_kernel", "fp64"): 200734208 + 75178752,
+    ("dst_rows_kernel", "fp32"): 133201152 + 31706368,
+    ("dst_cols_kernel", "fp32"): 66602240 + 7988992,
+    ("time_pass_kernel", "fp32"): 66622720 + 7884032,
+    ("stencil_dots_kernel", "fp32"): 272463616 + 104494080,
+    ("combine_kernel", "fp32"): 266401280 + 101237248,
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
 NCU_PINV_BYTES = {
-    "fp64": (133235200 + 81506048) + (133211648 + 73886720) + (200390144 + 75095040)
-            + (133308160 + 74059008) + (133211648 + 70091776),
-    "fp32": (133203712 + 32083712) + (66619904 + 8134144) + (66635520 + 7955200)
-            + (66605056 + 8205312) + (66615808 + 68916224),
+    "fp64": (133213696 + 80448000) + (133240064 + 73878016) + (200734208 + 75178752)
+            + (133211136 + 73814784) + (133242112 + 70327808),
+    "fp32": (133201152 + 31706368) + (66602240 + 7988992) + (66622720 + 7884032)
+            + (66602752 + 8340736) + (66624512 + 69254656),
 }
 # Algorithmic bytes per unit of one P_eps^-1 apply with five streaming passes:
 # FP64 16 B per pass; FP32 8 B (x-DST in and out: 12 B, one side FP64).
