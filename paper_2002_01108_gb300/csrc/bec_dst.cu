@@ -11,11 +11,21 @@ namespace bec {
 namespace {
 
 
+// Blocks per SM that the register bound of dst_rows_kernel asks for, as warps
+// per SM over the block's warps (at least one block): in FP64 32 warps for
+// n <= 256 (64 registers) and 16 for n = 512; in FP32 40 warps for n <= 256,
+// 32 for n = 512 and 16 above; longer FP64 transforms are left free.
+__host__ __device__ constexpr int rows_min_blocks(int bytes, int logn, int warps) {
+  const int w = bytes == 8 ? (logn <= 8 ? 32 : logn == 9 ? 16 : warps)
+                           : (logn <= 8 ? 40 : logn == 9 ? 32 : 16);
+  return w / warps > 0 ? w / warps : 1;
+}
+
 // DST along x: one warp per pair of contiguous rows of length m = n - 1.
 // `in` and `out` may be the same array (each warp reads its rows before
 // writing them); in that case TI == TO.
 template <typename T, typename TI, typename TO, int LOGN, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, rows_min_blocks(sizeof(T), LOGN, WARPS))
 dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
   constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per line

@@ -306,13 +306,20 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
     constexpr int NB = n / R;
     constexpr int PER = (NB + 31) / 32;
     V v[PER][R];
+    if constexpr (sizeof(T) == 8 && NB % 32 == 0 && R >= 4 && PER <= 2) {
+      // FP64, where the additions are the scarce resource: inputs e and n - e
+      // share x_e + x_{n-e} and, with the opposite sign, x_e - x_{n-e}.  A
+      // lane forms them for r <= R/2 and takes those for r > R/2 from the lane
+      // that holds n - e: lane (32 - l) mod 32, slot t' = PER - 1 - t,
+      // r' = R - 1 - r.  Lane 0 holds both ends of its pairs (at t' = PER - t,
+      // or r' = R - r when t = 0).  A third of the pre-pass additions go.
+      constexpr int RH = R / 2;
+      T sa[PER][RH + 1], da[PER][RH + 1], sb[PER][RH + 1], db[PER][RH + 1];
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int j = lane + 32 * t;
-      if (NB % 32 == 0 || j < NB) {
+      for (int t = 0; t < PER; ++t) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int e = j + r * NB;
+        for (int r = 0; r <= RH; ++r) {
+          const int e = lane + 32 * t + r * NB;
           T xa = 0, xan = 0, xb = 0, xbn = 0;
           if (r > 0 || e > 0) {
             xa = raw[e - 1];
@@ -320,8 +327,59 @@ __device__ __forceinline__ void warp_dst_pair(T* raw, int rs, const T* __restric
             xb = raw[rs + e - 1];
             xbn = raw[rs + n - e - 1];
           }
-          const T s = sin2[e];
-          v[t][r] = {s * (xa + xan) + (xa - xan), s * (xb + xbn) + (xb - xbn)};
+          sa[t][r] = xa + xan;
+          da[t][r] = xa - xan;
+          sb[t][r] = xb + xbn;
+          db[t][r] = xb - xbn;
+        }
+      }
+      const int pl = (32 - lane) & 31;
+      const bool l0 = lane == 0;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = lane + 32 * t + r * NB;
+          T s1, d1, s2, d2;
+          if (r <= RH) {
+            s1 = sa[t][r];
+            d1 = da[t][r];
+            s2 = sb[t][r];
+            d2 = db[t][r];
+          } else {
+            const int tp = PER - 1 - t, rp = R - 1 - r;
+            const int t0 = t == 0 ? 0 : PER - t, r0 = t == 0 ? R - r : rp;   // lane 0's own
+            const T qs1 = __shfl_sync(0xffffffffu, sa[tp][rp], pl);
+            const T qd1 = __shfl_sync(0xffffffffu, da[tp][rp], pl);
+            const T qs2 = __shfl_sync(0xffffffffu, sb[tp][rp], pl);
+            const T qd2 = __shfl_sync(0xffffffffu, db[tp][rp], pl);
+            s1 = l0 ? sa[t0][r0] : qs1;
+            d1 = -(l0 ? da[t0][r0] : qd1);
+            s2 = l0 ? sb[t0][r0] : qs2;
+            d2 = -(l0 ? db[t0][r0] : qd2);
+          }
+          const T sv = sin2[e];
+          v[t][r] = {fma(sv, s1, d1), fma(sv, s2, d2)};
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const int j = lane + 32 * t;
+        if (NB % 32 == 0 || j < NB) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int e = j + r * NB;
+            T xa = 0, xan = 0, xb = 0, xbn = 0;
+            if (r > 0 || e > 0) {
+              xa = raw[e - 1];
+              xan = raw[n - e - 1];
+              xb = raw[rs + e - 1];
+              xbn = raw[rs + n - e - 1];
+            }
+            const T s = sin2[e];
+            v[t][r] = {s * (xa + xan) + (xa - xan), s * (xb + xbn) + (xb - xbn)};
+          }
         }
       }
     }
