@@ -84,7 +84,9 @@ __global__ void rinv_table_kernel(double* __restrict__ rinv, long long J, int NK
 // transforms modes (q0 + 2w, q0 + 2w + 1) packed as real + i imaginary.
 // registers: 128 per thread in FP64 and 64 in FP32 for N <= 256 (the block
 // count the bound asks for fills the 64K-register file), free above
-template <typename T, int LOGN, int WARPS>
+// FE: the mass eigenvalues are present (Q1 elements); finite differences
+// (M = I) take the other instantiation, without the products by mu^M.
+template <typename T, int LOGN, int WARPS, bool FE>
 __global__ void __launch_bounds__(WARPS * 32, LOGN <= 8 ? (sizeof(T) == 8 ? 16 : 32) / WARPS : 1)
 time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
@@ -158,7 +160,7 @@ time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __r
       const V A2 = {C.y + Cn.y, Cn.x - C.x};
       const V L = lamf[k];
       // d = lambda'_k mu^M + tau mu^K for each mode (mu^M = 1 with FD)
-      const bool fe = me.m != nullptr;
+      constexpr bool fe = FE;
       const T d1r = fe ? fma(L.x, ma, tau * mua) : L.x + tau * mua;
       const T d2r = fe ? fma(L.x, mb, tau * mub) : L.x + tau * mub;
       const T d1i = fe ? L.y * ma : L.y, d2i = fe ? L.y * mb : L.y;
@@ -198,7 +200,8 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
                        const v2_t<T>* tw, const T* rinv) {
   constexpr int warps = WARPS;
   const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
-  auto k = time_pass_kernel<T, LOGN, WARPS>;
+  auto k = me.m != nullptr ? time_pass_kernel<T, LOGN, WARPS, true>
+                           : time_pass_kernel<T, LOGN, WARPS, false>;
   if (smem > 48 * 1024)
     BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const long long W = 2 * warps;
