@@ -105,9 +105,9 @@ def net_fwd_flops(m: int) -> float:
 # two-iteration FP32-form solve); absent = not captured for the current build
 # of the kernel.  The writes are what left L2 while the kernel ran.
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): 133210112 + 80553984,
-    ("dst_cols_kernel", "fp64"): 133219840 + 76789760,
-    ("time_pass_kernel", "fp64"): 200644352 + 78305280,
+    ("dst_rows_kernel", "fp64"): 133210368 + 80974336,
+    ("dst_cols_kernel", "fp64"): 133284608 + 76462336,
+    ("time_pass_kernel", "fp64"): 200689664 + 78113536,
     ("dst_rows_kernel", "fp32"): 133201152 + 31706368,
     ("dst_cols_kernel", "fp32"): 66602240 + 7988992,
     ("time_pass_kernel", "fp32"): 66622720 + 7884032,
@@ -116,8 +116,8 @@ NCU_TRAFFIC = {
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
 NCU_PINV_BYTES = {
-    "fp64": (133210112 + 80553984) + (133219840 + 76789760) + (200644352 + 78305280)
-            + (133261568 + 76768256) + (133209856 + 73660160),
+    "fp64": (133210368 + 80974336) + (133284608 + 76462336) + (200689664 + 78113536)
+            + (133210112 + 76756480) + (133237248 + 73658368),
     "fp32": (133201152 + 31706368) + (66602240 + 7988992) + (66622720 + 7884032)
             + (66602752 + 8340736) + (66624512 + 69254656),
 }
