@@ -99,28 +99,61 @@ def net_fwd_flops(m: int) -> float:
     return sum(2.0 * 9 * ci * co * sz[l] ** 2 for ci, co, l in NET_LAYERS)
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of each kernel at this workload (profiles/dram_traffic_heat2d_255x255_N256.md;
-# the P_eps^-1 passes of the second of three applies, the Krylov kernels of a
-# two-iteration FP32-form solve); absent = not captured for the current build
-# of the kernel.  The writes are what left L2 while the kernel ran.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture
+# of each kernel at this workload (the P_eps^-1 passes of the second of three
+# applies of `bench.py --ncu-case pinv_fp64`; the command is in the committed
+# DRAM-traffic summary under profiles/).  Each entry carries a SHA-256 prefix
+# of the CUDA sources the kernel is built from, taken when the counters were
+# read: if those sources have changed since, the figure no longer describes
+# the kernel and the bench reports null.  The writes are what left L2 while
+# the kernel ran.
+KERNEL_SOURCES = {
+    "dst_rows_kernel": ("bec_dst.cu", "bec_fft.cuh", "bec_internal.h"),
+    "dst_cols_kernel": ("bec_dst.cu", "bec_fft.cuh", "bec_internal.h"),
+    "time_pass_kernel": ("bec_time.cu", "bec_fft.cuh", "bec_internal.h"),
+    "stencil_dots_kernel": ("bec_krylov.cu", "bec_internal.h"),
+    "combine_kernel": ("bec_krylov.cu", "bec_internal.h"),
+}
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): 133210368 + 80974336,
-    ("dst_cols_kernel", "fp64"): 133284608 + 76462336,
-    ("time_pass_kernel", "fp64"): 200689664 + 78113536,
-    ("dst_rows_kernel", "fp32"): 133201152 + 31706368,
-    ("dst_cols_kernel", "fp32"): 66602240 + 7988992,
-    ("time_pass_kernel", "fp32"): 66622720 + 7884032,
-    ("stencil_dots_kernel", "fp32"): 272463616 + 104494080,
-    ("combine_kernel", "fp32"): 266401280 + 101237248,
+    ("dst_rows_kernel", "fp64"): (133210368 + 80974336, "2732a5622277ca4d"),
+    ("dst_cols_kernel", "fp64"): (133284608 + 76462336, "2732a5622277ca4d"),
+    ("time_pass_kernel", "fp64"): (200689664 + 78113536, "0411d9da891aba72"),
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
 NCU_PINV_BYTES = {
-    "fp64": (133210368 + 80974336) + (133284608 + 76462336) + (200689664 + 78113536)
-            + (133210112 + 76756480) + (133237248 + 73658368),
-    "fp32": (133201152 + 31706368) + (66602240 + 7988992) + (66622720 + 7884032)
-            + (66602752 + 8340736) + (66624512 + 69254656),
+    "fp64": ((133210368 + 80974336) + (133284608 + 76462336) + (200689664 + 78113536)
+             + (133210112 + 76756480) + (133237248 + 73658368),
+             ("2732a5622277ca4d", "0411d9da891aba72")),
 }
+
+
+def source_sha16(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(ROOT, "paper_2002_01108_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, form: str):
+    """The captured DRAM bytes of one launch, or None if there is no capture
+    for the kernel's current sources."""
+    ent = NCU_TRAFFIC.get((kernel, form))
+    if ent is None or kernel not in KERNEL_SOURCES:
+        return None
+    return ent[0] if source_sha16(KERNEL_SOURCES[kernel]) == ent[1] else None
+
+
+def ncu_pinv_bytes(form: str):
+    ent = NCU_PINV_BYTES.get(form)
+    if ent is None:
+        return None
+    now = (source_sha16(KERNEL_SOURCES["dst_rows_kernel"]),
+           source_sha16(KERNEL_SOURCES["time_pass_kernel"]))
+    return ent[0] if now == ent[1] else None
+
+
 # Algorithmic bytes per unit of one P_eps^-1 apply with five streaming passes:
 # FP64 16 B per pass; FP32 8 B (x-DST in and out: 12 B, one side FP64).
 PINV_BYTES_PER_UNIT = {"fp64": 80.0, "fp32": 48.0}
@@ -246,31 +279,95 @@ def workload_config(form: str):
     }
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_method_solve(O, L, f, dim, tau, eps, workers):
+    """The oracle's own form of the paper's method: FGMRES(30) with the
+    sine-transform P_eps^-1 (scipy.fft with `workers` threads), to RES 1e-8.
+    Returns (u, iterations)."""
+    import scipy.fft as sfft
+    shape = f.shape
+    with sfft.set_workers(workers):
+        u, info = O.fgmres(lambda v: L @ v, f.reshape(-1),
+                           lambda v: O.apply_Pinv_fst(v.reshape(shape), dim, 1.0, tau, eps).reshape(-1),
+                           restart=RESTART, tol=RTOL)
+    return u.reshape(shape), info["iters"]
+
+
 def cpu_baseline_sample(case):
-    """The oracle's solver for u (sequential backward-Euler stepping, the
-    definition of the all-at-once solution) timed on the full workload."""
-    import numpy as np
+    """The oracle timed on the host's cores: one full solve of the workload by
+    the oracle's FGMRES with its sine-transform P_eps^-1 (the paper's method in
+    NumPy/SciPy FP64, scipy.fft on every affinity core)."""
     import scipy.sparse as sp
 
     import oracle as O
+    K = O.fd_stiffness(2, case.m)
+    L = O.assemble_L(case.N, sp.identity(K.shape[0], format="csr"), K, case.tau)
+    f = O.build_rhs(case.u0, case.fsrc, case.tau)
+    cores = host_cores()
+    t0 = time.perf_counter()
+    u, iters = oracle_method_solve(O, L, f, 2, case.tau, case.eps, cores)
+    dt = time.perf_counter() - t0
+    res = O.relative_residual(L, u, f)
+    return {"value": case.U / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full solve of the workload ({case.U} unknowns): oracle FGMRES({RESTART}) "
+                      f"with the sine-transform P_eps^-1, {iters} iterations, RES {res:.1e}, "
+                      f"{dt:.2f} s; scipy.fft on {cores} threads, numpy.fft and sparse products on one",
+            "cpu": platform.machine()}
+
+
+def cpu_side_lines(case):
+    """Two more oracle timings, each on its own JSON line: the definition of
+    the solution (sequential backward-Euler stepping, one SuperLU
+    factorisation, inherently serial) on the same workload, and the small 1D
+    configuration (m = 63, N = 64, eps = sqrt(tau)/2, GMRES(30) to 1e-10, the
+    oracle's banded-LU P_eps^-1) in CPU seconds."""
+    import scipy.sparse as sp
+
+    import oracle as O
+    from workloads import heat_case_1d
     K = O.fd_stiffness(2, case.m)
     M = sp.identity(K.shape[0], format="csr")
     f = O.build_rhs(case.u0, case.fsrc, case.tau)
     t0 = time.perf_counter()
     O.timestep_solve(f, M, K, case.tau)
     dt = time.perf_counter() - t0
-    return {"value": case.U / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full solve of the workload ({case.U} unknowns) by the oracle's "
-                      f"sequential backward-Euler stepping (one sparse LU, SuperLU, single thread): "
-                      f"{dt:.2f} s",
-            "host_cores": os.cpu_count(), "cpu": platform.processor() or platform.machine()}
+    print(json.dumps({"line": "cpu_stepping", "value": case.U / dt, "unit": UNIT, "cores": 1,
+                      "kind": "oracle", "s": round(dt, 3),
+                      "sample": "sequential backward-Euler stepping of the full workload "
+                                "(one sparse LU, SuperLU, single thread)"}), flush=True)
+    c1 = heat_case_1d(seed=1, m=63, N=64)
+    K1 = O.fd_stiffness(1, c1.m)
+    M1 = sp.identity(c1.m, format="csr")
+    L1 = O.assemble_L(c1.N, M1, K1, c1.tau)
+    f1 = O.build_rhs(c1.u0, c1.fsrc, c1.tau)
+    t0 = time.perf_counter()
+    u1, info = O.gmres(lambda v: L1 @ v, f1.reshape(-1),
+                       lambda v: O.apply_Pinv_lu(v.reshape(f1.shape), M1, K1, c1.tau, c1.eps).reshape(-1),
+                       restart=30, tol=1e-10, left=True)
+    dt1 = time.perf_counter() - t0
+    print(json.dumps({"line": "cpu_1d_m63_N64", "s": round(dt1, 4), "value": c1.U / dt1, "unit": UNIT,
+                      "iterations": info["iters"],
+                      "RES": O.relative_residual(L1, u1, f1), "cores": 1, "kind": "oracle",
+                      "workload": "1D heat, m=63, N=64, eps=sqrt(tau)/2, left GMRES(30) to 1e-10 with "
+                                  "the banded-LU P_eps^-1 (plain method, CPU seconds)"}), flush=True)
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper's method in NumPy/SciPy FP64,
+    FGMRES with the sine-transform P_eps^-1, scipy.fft on every affinity core)
+    timed on the host.  A step solves the first ns time slices of the
+    workload, an exact sub-problem (L is block lower triangular, so its
+    solution is the first ns slices of the full solution); ns = N unless K + W
+    full solves would take longer than about two and a half minutes."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    import numpy as np
     import scipy.sparse as sp
 
     import oracle as O
@@ -279,24 +376,39 @@ def run_reference(args):
     K = O.fd_stiffness(2, case.m)
     M = sp.identity(K.shape[0], format="csr")
     f = O.build_rhs(case.u0, case.fsrc, case.tau)
-    ns = 64                                            # slices per step: a bounded sample
-    sample = f[:ns]
-    for _ in range(args.warmup):
-        O.timestep_solve(sample, M, K, case.tau)
-    t0 = time.perf_counter()
+    cores = host_cores()
+    Ls = {}
+
+    def step(ns):
+        if ns not in Ls:
+            Ls[ns] = O.assemble_L(ns, M, K, case.tau)
+        t0 = time.perf_counter()
+        _, iters = oracle_method_solve(O, Ls[ns], f[:ns], 2, case.tau, case.eps, cores)
+        return time.perf_counter() - t0, iters
+
+    ns = N_STEPS
+    t_first, _ = step(ns)
+    budget = 150.0
+    while ns > 8 and (args.steps + args.warmup) * t_first * ns / N_STEPS > budget:
+        ns //= 2
+    for _ in range(max(0, args.warmup - 1)):
+        step(ns)
+    tot, iters = 0.0, 0
     for _ in range(args.steps):
-        O.timestep_solve(sample, M, K, case.tau)
-    dt = (time.perf_counter() - t0) / args.steps
+        dt, iters = step(ns)
+        tot += dt
+    dt = tot / args.steps
     value = ns * case.J / dt
+    sample = (f"first {ns} of {N_STEPS} time slices per step (an exact sub-problem of the workload), "
+              f"solved by the oracle's FGMRES({RESTART}) with its sine-transform P_eps^-1 to RES 1e-8 "
+              f"({iters} iterations); scipy.fft on {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded U[-1,1] source, 8x8 random sine-series u0)",
         "config": workload_config("fp64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {ns} of {N_STEPS} time slices per step, solved by the "
-                                   f"oracle's sequential backward-Euler stepping (SuperLU, one thread)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -441,7 +553,11 @@ def roofline(form, kernels, U, iters=2):
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_src,
                 "algorithmic_per_unit": f"{bpu:.0f} B", "units_per_launch": U}
     roof["avg_launch_ms"] = avg_ms
-    roof["traffic"] = NCU_TRAFFIC.get((dom, form))
+    roof["traffic"] = ncu_traffic(dom, form)
+    roof["traffic_source"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu capture "
+                              "of bench.py --ncu-case pinv_fp64 on the kernel's current sources"
+                              if roof["traffic"] is not None else
+                              "no ncu capture of the kernel's current sources")
     return roof
 
 
@@ -453,17 +569,35 @@ def pinv_report(form, r, U):
     t = r["pinv_ms"] / 1e3
     bpu = PINV_BYTES_PER_UNIT[form]
     design = bpu * U / t / 1e9
-    dram = NCU_PINV_BYTES.get(form)
+    dram = ncu_pinv_bytes(form)
     return {
-        "ms_per_apply": r["pinv_ms"], "unknowns_per_s": U / t,
-        "algorithmic_bytes_per_unit": bpu, "achieved_gbs": design, "peak_gbs": peaks["hbm_gbs"],
-        "frac": design / peaks["hbm_gbs"], "peak_source": peak_src,
-        "min_bytes_gbs": 16.0 * U / t / 1e9,
-        "dram_bytes_per_apply": dram, "dram_gbs": dram / t / 1e9 if dram else None,
-        "passes_ms": {k: round(ms, 4) for k, (n, ms) in
-                      sorted(r["pinv_passes"].items(), key=lambda kv: -kv[1][1])},
+        "ms": round(r["pinv_ms"], 4), "bytes_per_unit": bpu, "achieved_gbs": round(design, 1),
+        "peak_gbs": peaks["hbm_gbs"], "frac": round(design / peaks["hbm_gbs"], 4),
+        "peak_source": peak_src, "min_bytes_gbs": round(16.0 * U / t / 1e9, 1),
+        "min_bytes_frac": round(16.0 * U / t / 1e9 / peaks["hbm_gbs"], 4),
+        "dram_gbs": round(dram / t / 1e9, 1) if dram else None,
         "bound": "FP64 pipe (2 FMA/clk/SM)" if form == "fp64" else
                  "instruction issue and shared memory (the FP32 intermediate stays in L2)"}
+
+
+def top_kernels(kernels, n=3):
+    """The n kernels with the largest summed event time: name -> [launches, ms]."""
+    return {k: [c, round(ms, 3)] for k, (c, ms) in
+            sorted(kernels.items(), key=lambda kv: -kv[1][1])[:n]}
+
+
+def emit(name, fn, *a, **kw):
+    """Runs one secondary measurement and prints it as its own JSON line
+    (an error line if it fails, so that the headline still follows)."""
+    import torch
+    try:
+        out = fn(*a, **kw)
+    except Exception as exc:   # noqa: BLE001 - reported, the run goes on
+        out = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    print(json.dumps(dict({"line": name}, **out)), flush=True)
+    return out
 
 
 def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1, post=1):
@@ -542,9 +676,7 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
                 "frac": ach / pk, "peak_source": "bf16_tflops_sustained " + src,
                 "algorithmic_per_unit": "2 x 9 x c_in x c_out FLOP per output pixel and layer",
                 "units_per_launch": "B x side^2 pixels of one layer, B <= 32 frequencies",
-                "flops_per_apply": K * net_fwd_flops(m), "avg_launch_ms": avg,
-                "other_network_kernels_ms": {k: round(v[1], 3) for k, v in kernels.items()
-                                             if k.startswith("net_") and k != dom}}
+                "flops_per_apply": K * net_fwd_flops(m), "avg_launch_ms": avg}
     elif dom == "stencil_dots_kernel":
         # the FP64 Krylov operator dominates: bound by the FP64 pipe
         roof = roofline(precision, kernels, U, info["iters"])
@@ -573,8 +705,8 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
         roof["avg_launch_ms"] = avg
     out = {"value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iters"],
            "true_relres": info["true_relres"], "gpu_launches_per_solve": launches,
-           "smoothing_sweeps": f"{pre}+{post}", "roofline": roof,
-           "kernels_one_profiled_solve": kernel_table(kernels)}
+           "smoothing_sweeps": f"{pre}+{post}", "roofline": compact_roof(roof),
+           "top_kernels": top_kernels(kernels)}
     if route == "learned":
         out["training"] = training
         out["residual_ratio_last_apply"] = {"mean": float(np.mean(ratios)), "min": float(np.min(ratios)),
@@ -666,7 +798,7 @@ def measure_convection(args, form):
     return {"value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iters"],
             "true_relres": info["true_relres"], "converged": info["converged"],
             "timed_solves": steps,
-            "kernels": dict(list(kernel_table(kernels).items())[:6])}
+            "top_kernels": top_kernels(kernels)}
 
 
 def measure_bdf2_headline(args, form):
@@ -743,7 +875,7 @@ def measure_precision_workload(args):
         del z
         U = prob.U
         pinv = pinv_report(form, {"pinv_ms": pinv_ms, "pinv_passes": {}}, U)
-        pinv.pop("dram_bytes_per_apply"), pinv.pop("dram_gbs"), pinv.pop("passes_ms")
+        pinv = {k: pinv[k] for k in ("ms", "achieved_gbs", "frac", "min_bytes_frac")}
         out[form + "_preconditioner"] = {
             "value": U / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "timed_solves": steps,
             "iterations": info["iters"], "true_relres": info["true_relres"],
@@ -813,11 +945,62 @@ def measure_batch(args, ws=1, rank=0, dist=None):
     return out
 
 
-def kernel_table(kernels):
-    total_ms = sum(ms for _, ms in kernels.values())
-    return {name: {"launches": n, "ms": round(ms, 4),
-                   "share": round(ms / total_ms, 4) if total_ms else None}
-            for name, (n, ms) in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
+def compact_roof(roof):
+    """The roofline record with its figures rounded (short JSON lines)."""
+    out = {}
+    for k, v in roof.items():
+        out[k] = round(v, 4) if isinstance(v, float) else v
+    return out
+
+
+def measure_eps_sweep(args):
+    """FGMRES iterations and time against eps on the headline workload
+    (255^2 x 256, FGMRES(30) to RES 1e-8), for the FP64 and the FP32
+    P_eps^-1: the eps-dependence of Theorem preconditionedspectrum, and the
+    FP32 form's rounding amplified by cond(D_eps) ~ 1/eps."""
+    import torch
+    from paper_2002_01108_gb300 import Problem
+    from workloads import heat_case_2d
+    out = {"workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, FGMRES({RESTART}) to RES 1e-8"}
+    case = heat_case_2d(seed=2, m=M_SIDE, N=N_STEPS, eps=EPS)
+    for form in ("fp64", "fp32"):
+        with Problem(2, M_SIDE, N_STEPS, precision=form, max_restart=RESTART, flexible=True) as p:
+            p.set_eps(EPS)
+            p.autotune()
+            f = p.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
+            u = torch.empty_like(f)
+            kw = dict(restart=RESTART, rtol=RTOL, maxit=300, flexible=True)
+            rows = {}
+            for eps in (0.1, EPS, 1e-4):
+                p.set_eps(eps)
+                p.gmres_solve(f, u, **kw)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                steps = max(1, min(args.steps, 3))
+                ev0.record(p.stream)
+                for _ in range(steps):
+                    _, info = p.gmres_solve(f, u, **kw)
+                ev1.record(p.stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / steps
+                rows[f"{eps:g}"] = {"iterations": info["iters"], "ms": round(ms, 3),
+                                    "value": p.U / (ms / 1e3), "RES": info["true_relres"]}
+            out[form] = rows
+            del f, u
+    return out
+
+
+def measure_other_form(other, case, args, ws, local, dist):
+    o = measure_form(other, case, args, ws, local, dist)
+    U = o["U"]
+    return {"value": ws * U / (o["ms_step"] / 1e3), "unit": UNIT, "ms_per_step": round(o["ms_step"], 4),
+            "iterations": o["info"]["iters"], "true_relres": o["info"]["true_relres"],
+            "e2e_value": ws * U / o["e2e_s"], "e2e_single_call_value": ws * U / o["e2e_single_s"],
+            "gpu_launches": o["launches"], "clocks": o["clocks"],
+            "roofline": compact_roof(roofline(other, o["kernels"], U, o["info"]["iters"])),
+            "apply_pinv": pinv_report(other, o, U), "top_kernels": top_kernels(o["kernels"]),
+            "workload": "the headline workload with the "
+                        + ("FP32/complex64 P_eps^-1 inside FP64 FGMRES" if other == "fp32"
+                           else "plain FP64 P_eps^-1")}
 
 
 def run_gpu(args):
@@ -842,82 +1025,60 @@ def run_gpu(args):
     form = args.form
     r = measure_form(form, case, args, ws, local, dist)
     U = r["U"]
-    line = {
-        "metric": METRIC, "value": ws * U / (r["ms_step"] / 1e3), "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded U[-1,1] source, 8x8 random sine-series u0)",
-        "config": dict(workload_config(form), iterations=r["info"]["iters"],
-                       true_relres=r["info"]["true_relres"], autotuned_warps_per_block=r["tiles"],
-                       parallelism=f"{ws} independent replicas"),
-        "roofline": roofline(form, r["kernels"], U, r["info"]["iters"]),
-        "apply_pinv": pinv_report(form, r, U),
-        "e2e": {"value": ws * U / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": U * 8,
-                "d2h_bytes_per_step": U * 8, "ms_per_step": r["e2e_s"] * 1e3,
-                "api": "bec_gmres_solve_host_many (copies overlapped with the neighbouring "
-                       "solves; pinned host buffers); median of 5 calls of max(K, 8) steps",
-                "steps_per_call": r["e2e_steps"], "calls_ms_per_step": r["e2e_reps_ms"],
-                "iterations": r["e2e_iters"],
-                "single_call": {"value": ws * U / r["e2e_single_s"], "unit": UNIT,
-                                "ms_per_step": r["e2e_single_s"] * 1e3,
-                                "api": "bec_gmres_solve_host (H2D, solve, D2H, synchronise)",
-                                "samples_ms": r["e2e_samples_ms"]}},
-        "gpu_launches": r["launches"],
-        "clocks": r["clocks"],
-        "kernels": kernel_table(r["kernels"]),
-        "paper_context": "Table table1 (N=256, 255^2, Q1, a=1e-5): 12.54 s MATLAB on 2x Xeon E5-2690 v4 "
-                         "= 1.33e6 unknowns/s (different discretisation and tolerance)",
-    }
+
+    # every other form and row on its own short line, before the headline
+    say = (lambda name, fn, *a, **kw: emit(name, fn, *a, **kw)) if rank == 0 else \
+          (lambda name, fn, *a, **kw: fn(*a, **kw))
     if not args.no_other_form:
         other = "fp32" if form == "fp64" else "fp64"
-        o = measure_form(other, case, args, ws, local, dist)
-        line["forms"] = {other + "_preconditioner": {
-            "value": ws * U / (o["ms_step"] / 1e3), "unit": UNIT, "ms_per_step": o["ms_step"],
-            "iterations": o["info"]["iters"], "true_relres": o["info"]["true_relres"],
-            "e2e_value": ws * U / o["e2e_s"], "e2e_single_call_value": ws * U / o["e2e_single_s"],
-            "gpu_launches": o["launches"], "clocks": o["clocks"],
-            "autotuned_warps_per_block": o["tiles"],
-            "roofline": roofline(other, o["kernels"], U, o["info"]["iters"]),
-            "apply_pinv": pinv_report(other, o, U),
-            "kernels": kernel_table(o["kernels"]),
-            "note": "same workload and tolerance; FP32/complex64 P_eps^-1 inside FP64 FGMRES"
-                    if other == "fp32" else "same workload; plain FP64 form"}}
-    if not args.no_other_form:
-        line["variable_coefficient_multigrid"] = {
-            "workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, a=exp(g), g a Gaussian random field "
-                        "(squared-exponential kernel, length 0.1, sigma 1), eps=sqrt(tau)/2, one V-cycle "
-                        "per shifted system (damped Jacobi 1+1, Galerkin coarse grids), FGMRES(30) "
-                        "to RES 1e-8",
-            "fp32": measure_mg("fp32", args, pre=3, post=2),
-            "fp32_paper_sweeps": measure_mg("fp32", args),
-            "fp64": measure_mg("fp64", args),
-            "learned_fp32_bf16": measure_mg("fp32", args, route="learned", train_steps=300),
-            "sweeps_note": "damped Jacobi in place of the paper's ILU smoother; 1+1 sweeps as in the "
-                           "paper, 3+2 the fastest FP32 setting of a sweep study (9 iterations "
-                           "instead of 12); FP64 fastest at 1+1",
-            "learned_note": "the V-cycle, then the trained network's correction (BF16 activations, "
-                            "FP32 accumulation), one smoothing sweep and the minimal-residual judge"}
-        line["batch"] = measure_batch(args, ws, rank, dist)
-        line["precision_workload"] = measure_precision_workload(args)
-        line["paper_table1_row"] = measure_paper_table1(args)
-        line["bdf2"] = {
-            "workload": f"heat2d {M_SIDE}x{M_SIDE}, N={N_STEPS}, BDF2 (r = 3/2, -2, 1/2; pre-start "
-                        "value u^-1 = u^0), eps=sqrt(tau), FGMRES(30) to RES 1e-8",
-            "fp64_preconditioner": measure_bdf2_headline(args, "fp64"),
-            "fp32_preconditioner": measure_bdf2_headline(args, "fp32"),
-            "paper_bdf2table_row": measure_paper_table1(args, "bdf2")}
-        line["convection_diffusion"] = {
-            "workload": f"Example 3 of Sec. 5 at {M_SIDE}x{M_SIDE}, N={N_STEPS}: nu=1/200, circulating "
-                        "wind, hot wall, u0=0; upwind FD; eps=min(0.5,0.5 tau); one ILU-smoothed "
-                        "V-cycle (1+1, Galerkin coarse grids) per shifted system; FGMRES(30) to RES 1e-8",
-            "fp32": measure_convection(args, "fp32"),
-            "fp64": measure_convection(args, "fp64"),
-            "paper": {"iterations": 5, "RES": 1.09e-8, "cpu_s": 45.13,
-                      "note": "SUPG Q1 with IFISS ILU multigrid, left GMRES(50) to 1e-7; context only"}}
+        say(other + "_preconditioner", measure_other_form, other, case, args, ws, local, dist)
+        if ws == 1:
+            say("eps_sweep", measure_eps_sweep, args)
+            say("mg_fp32_3+2", measure_mg, "fp32", args, pre=3, post=2)
+            say("mg_fp32_1+1", measure_mg, "fp32", args)
+            say("mg_fp64_1+1", measure_mg, "fp64", args)
+            say("learned_fp32_bf16", measure_mg, "fp32", args, route="learned", train_steps=300)
+        say("batch", measure_batch, args, ws, rank, dist)
+        if ws == 1:
+            say("precision_511x511_N512", measure_precision_workload, args)
+            say("paper_table1_row", measure_paper_table1, args)
+            say("bdf2_fp64", measure_bdf2_headline, args, "fp64")
+            say("bdf2_fp32", measure_bdf2_headline, args, "fp32")
+            say("paper_bdf2table_row", measure_paper_table1, args, "bdf2")
+            say("convection_fp32", measure_convection, args, "fp32")
+            say("convection_fp64", measure_convection, args, "fp64")
+    cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(case)
+        cpu_side_lines(case)
+        cpu = cpu_baseline_sample(case)
+
+    roof = compact_roof(roofline(form, r["kernels"], U, r["info"]["iters"]))
+    pinv = pinv_report(form, r, U)
+    line = {
+        "metric": METRIC, "value": ws * U / (r["ms_step"] / 1e3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_step"], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded U[-1,1] source, 8x8 random sine-series u0)",
+        "config": {"workload": workload_config(form)["workload"], "unknowns": U,
+                   "eps": EPS, "iterations": r["info"]["iters"],
+                   "true_relres": r["info"]["true_relres"], "warps_per_block": r["tiles"],
+                   "l2": "inputs larger than L2 (each vector 133 MB > 129 MB L2)",
+                   "parallelism": f"{ws} independent replicas"},
+        "roofline": roof,
+        "apply_pinv": {k: pinv[k] for k in ("ms", "achieved_gbs", "frac", "min_bytes_frac", "dram_gbs",
+                                            "bytes_per_unit")},
+        "e2e": {"value": ws * U / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": U * 8,
+                "d2h_bytes_per_step": U * 8, "ms_per_step": round(r["e2e_s"] * 1e3, 4),
+                "api": "bec_gmres_solve_host_many (pinned host f in, u out, copies overlapped "
+                       "with the neighbouring solves)",
+                "single_call_value": ws * U / r["e2e_single_s"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0

@@ -249,13 +249,20 @@ bec_status bec_gmres_solve_host_many(bec_problem* p, const double* const* f_host
 bec_status bec_true_relres(bec_problem* p, const double* f, const double* u,
                            double* out);
 
-/* RES = ||f - L u||_2 / ||f||_2 for the problem (dim, nx, N, T, a) of
- * bec_allocate_problem, WITHOUT allocating anything and without a problem
- * object.  The paper has no counterpart: this exists for callers that cannot
- * allocate device memory at the point where they check a solution -- device
- * memory owned by another allocator (a framework's caching pool), a memory
- * budget fixed at start-up, a no-allocation-after-initialisation policy, or
- * a device that is nearly full.
+/* RES = ||f - L u||_2 / ||f||_2 (Sec. 5), WITHOUT allocating anything and
+ * without a problem object.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory at the point where they check a
+ * solution -- device memory owned by another allocator (a framework's caching
+ * pool), a memory budget fixed at start-up, a no-allocation-after-
+ * initialisation policy, or a device that is nearly full.
+ *  - Operator covered: only the finite-difference backward-Euler L of
+ *    bec_allocate_problem with BEC_SPACE_FD, BEC_TIME_BDF1, a constant
+ *    coefficient `a` (no a_nodes, no wind) and the unit side, in dim 1 or 2:
+ *    y^n = (I + tau K) u^n - u^{n-1}, tau = T / N, K the 3- or 5-point
+ *    Laplacian times a with h = 1 / (nx + 1).  For a problem set up with Q1
+ *    elements, BDF2, a variable coefficient, convection, another side or
+ *    dim 3 it would compute the residual of a different operator; use
+ *    bec_true_relres there.  dim 3 is rejected (BEC_EINVAL).
  *  - f, u: device vectors of U = N * J doubles ([N][ny][nx]); res_out: one
  *    device double that receives RES.  All owned by the caller; the result
  *    is written asynchronously on `stream` (a cudaStream_t, NULL = legacy

@@ -371,9 +371,12 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
     // let copies and MMAs in flight land before the memory is released: each
     // stage has at most one load outstanding, the latest one issued into it
     // (a completed phase passes the parity wait at once)
-    if (warp == 4 && lane == 0)
+    if (warp == 4 && lane == 0) {
+      // the weight copy is issued before any tile load, whatever happens later
+      mbar_wait(wbar, 0, &never);
       for (int i = issued_ld > kStages ? issued_ld - kStages : 0; i < issued_ld; ++i)
         mbar_wait(full(i % kStages), (i / kStages) & 1, &never);
+    }
     if (warp == 5 && lane == 0 && mma_pending) mbar_wait(tfull(last_acc), last_ph, &never);
   }
   fence_before();

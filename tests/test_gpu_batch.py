@@ -61,13 +61,32 @@ def test_batch_equals_single_solves_and_the_oracle(use_graphs, nstreams):
         assert np.linalg.norm(u.cpu().numpy() - uref) / np.linalg.norm(uref) <= 1e-8
 
 
+def _chosen(cases):
+    """Indices of the instances compared with the oracle: for every side the
+    smallest and the largest N, and the smallest and the largest eps."""
+    pick = set()
+    for m in sorted({c.m for c in cases}):
+        idx = [i for i, c in enumerate(cases) if c.m == m]
+        pick.add(min(idx, key=lambda i: (cases[i].N, i)))
+        pick.add(max(idx, key=lambda i: (cases[i].N, -i)))
+    pick.add(min(range(len(cases)), key=lambda i: cases[i].eps))
+    pick.add(max(range(len(cases)), key=lambda i: cases[i].eps))
+    return sorted(pick)
+
+
 def test_batch_64_uneven_instances():
     """64 instances, side in {63, 127, 255}, N in {32..512}, ln eps ~ U[ln 1e-4,
     ln sqrt(tau)]: FP32 preconditioner, FP64 FGMRES(10), every instance to
-    RES <= 1e-8."""
+    RES <= 1e-8 (the benchmark's tolerance).  Solved again to 1e-10, the
+    instances that span the batch (every side with its smallest and largest
+    N, the smallest and largest eps) equal the oracle's sequential stepping
+    to 1e-8."""
     import torch
     from paper_2002_01108_gb300 import Batch
     cases = batch_cases(seed=4, count=64)
+    chosen = _chosen(cases)
+    assert len(chosen) >= 8
+    assert {cases[i].m for i in chosen} == {63, 127, 255}
     specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
     with Batch(specs, nstreams=8, use_graphs=True) as b:
         fs, us = [], []
@@ -79,3 +98,15 @@ def test_batch_64_uneven_instances():
         infos = b.solve(fs, us, restart=10, rtol=1e-8)
         assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-8 for i in infos)
         assert b.unknowns == sum(c.U for c in cases)
+        infos = b.solve(fs, us, restart=10, rtol=1e-10)
+        assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-10 for i in infos)
+        torch.cuda.synchronize()
+        for i in chosen:
+            c = cases[i]
+            K = O.fd_stiffness(2, c.m)
+            uref = O.timestep_solve(O.build_rhs(c.u0, c.fsrc, c.tau),
+                                    sp.identity(K.shape[0], format="csr"), K, c.tau)
+            err = np.linalg.norm(us[i].cpu().numpy() - uref) / np.linalg.norm(uref)
+            print(f"instance {i}: m={c.m} N={c.N} eps={c.eps:.2e} iters {infos[i]['iters']} "
+                  f"error {err:.1e}")
+            assert err <= 1e-8, (i, c.m, c.N, c.eps, err)

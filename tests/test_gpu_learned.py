@@ -229,8 +229,9 @@ def test_learned_route_reaches_the_solution_and_never_raises_the_inner_residual(
 
 def test_learned_route_at_the_workload_size():
     """The learned form at the size bench.py times: 255^2 x 256, a = exp(GRF),
-    eps = sqrt(tau)/2, 300 training steps, FGMRES(30) to RES 1e-8; the
-    solution matches sequential stepping and no frequency's residual grows."""
+    eps = sqrt(tau)/2, 300 training steps: FGMRES(30) reaches RES 1e-8 (the
+    benchmark's tolerance), and solved on to RES 1e-10 its solution equals
+    sequential stepping to 1e-8; no frequency's residual grows."""
     import torch
     from paper_2002_01108_gb300 import Problem
     m, N = 255, 256
@@ -243,11 +244,14 @@ def test_learned_route_at_the_workload_size():
     with Problem(2, m, N, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
         p.set_eps(eps)
         p.learned_train(steps=300, batch=16, lr=2e-3, seed=3)
-        u, info = p.gmres_solve(torch.from_numpy(f).cuda(), restart=30, rtol=1e-8, flexible=True)
+        fd = torch.from_numpy(f).cuda()
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
+        assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8, info
+        u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, maxit=400, flexible=True)
         torch.cuda.synchronize()
         ratios = p.learned_residual_ratios()
-    assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8, info
+    assert info["converged"] == 1 and info["true_relres"] <= 1.01e-10, info
     assert np.all(ratios <= 1.0 + 1e-6)
-    # RES <= 1e-8 bounds the error by cond(L) 1e-8; in practice it is far smaller
+    # solved to RES 1e-10 through the FP64 outer FGMRES: the FP64 answer
     err = float(np.linalg.norm(u.cpu().numpy() - u_ref) / np.linalg.norm(u_ref))
-    assert err <= 1e-5, err
+    assert err <= 1e-8, err

@@ -4,6 +4,7 @@ R, the absence of biases (positive homogeneity) and the shapes."""
 import math
 
 import numpy as np
+import pytest
 import scipy.signal as ss
 
 import oracle as O
@@ -173,3 +174,45 @@ def sp_identity(n):
 def sp_diags(d):
     import scipy.sparse as sp
     return sp.diags(d)
+
+
+def test_loss_is_the_mean_of_the_per_sample_relative_errors():
+    """Zero weights give e = 0, so every sample's ||e - e*||^2 / ||e*||^2 is 1;
+    with targets 2e and -e the per-sample values are 1/4 and 4, and the loss is
+    their mean, 2.125 (a ratio of sums, or a norm that is not squared, gives
+    another number)."""
+    m = 15
+    rng = np.random.default_rng(30)
+    lc = LO.LearnedCorrection(m, 0.3 * rng.standard_normal((m + 2, m + 2)), 1 / 16)
+    ps = LO.init_params(4, seed=31)
+    zero = [np.zeros_like(w) for w in ps]
+    r1 = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    r2 = 5.0 * (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m)))
+    l1, l2 = 0.3 - 0.2j, 1.1 + 0.4j
+    e1, e2 = lc(ps, r1, l1), lc(ps, r2, l2)
+    assert np.abs(e1).max() > 0 and np.abs(e2).max() > 0
+    assert LO.loss(zero, [(r1, l1, e1), (r2, l2, 3.0 * e2)], lc) == pytest.approx(1.0, abs=1e-15)
+    assert LO.loss(ps, [(r1, l1, e1)], lc) == pytest.approx(0.0, abs=1e-28)
+    assert LO.loss(ps, [(r1, l1, 2.0 * e1)], lc) == pytest.approx(0.25, rel=1e-13)
+    assert LO.loss(ps, [(r1, l1, 2.0 * e1), (r2, l2, -e2)], lc) == pytest.approx(2.125, rel=1e-13)
+
+
+@pytest.mark.parametrize("a", [0.5, 2.0])
+def test_output_scale_is_the_inverse_shifted_operator_on_its_smoothest_mode(a):
+    """For a constant coefficient, the smallest eigenvalue of the 5-point K(a)
+    (shift-invert Lanczos on the assembled matrix, no formula) is a mu_min,
+    and |lambda + tau a mu_min|^-1 is the size of B_k^{-1} on that mode.
+    output_scale uses the continuum value mu_min -> 2 pi^2, which agrees to
+    O(h^2): here pi^2 h^2 / 12 < 2.5e-4 of mu_min."""
+    import scipy.sparse.linalg as spla
+    m, N, eps = 63, 32, 0.05
+    tau = 1.0 / N
+    K = O.fd_stiffness_varcoef(np.full((m + 2, m + 2), a))
+    mu_min = float(spla.eigsh(K.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0])
+    assert mu_min == pytest.approx(a * 2.0 * math.pi ** 2, rel=2.5e-4)
+    for lam in LO.forward_sign_eigs(N, eps):
+        ref = 1.0 / abs(lam + tau * mu_min)
+        assert LO.output_scale(lam, tau, a) == pytest.approx(ref, rel=2.5e-4)
+    # the route takes a_mean over the node values: constant a gives a itself
+    lc = LO.LearnedCorrection(m, np.full((m + 2, m + 2), math.log(a)), tau)
+    assert lc.a_mean == pytest.approx(a, rel=1e-14)
