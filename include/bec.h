@@ -328,11 +328,15 @@ bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
  * is bounded; one that runs out sets an error word and the kernel returns
  * (freeing what it holds), and the next synchronising call on the problem
  * (bec_gmres_solve, the learned-route calls) returns BEC_ETIMEOUT.
+ * bec_inject_fault(BEC_FAULT_PERSIST_WITHHOLD) makes the next persistent batch
+ * launch (BEC_BATCH_PERSISTENT) never report instance 0's first pass done, so
+ * the blocks that wait for it run out after about 0.2 s and bec_batch_solve
+ * returns BEC_ETIMEOUT.
  * bec_inject_fault(BEC_FAULT_TC_WITHHOLD_LOADS) makes the next tensor-core
  * convolution withhold its tile loads, so that its waits run out (about
  * 0.2 s): a host-side injection that faults, traps and hangs nothing.  The
  * injection is one-shot; BEC_FAULT_NONE does nothing. */
-enum { BEC_FAULT_NONE = 0, BEC_FAULT_TC_WITHHOLD_LOADS = 1 };
+enum { BEC_FAULT_NONE = 0, BEC_FAULT_TC_WITHHOLD_LOADS = 1, BEC_FAULT_PERSIST_WITHHOLD = 2 };
 bec_status bec_inject_fault(int kind);
 
 /* ---- Tile shapes of the P_eps^{-1} passes --------------------------------
@@ -384,15 +388,32 @@ bec_status bec_reciprocal_fp64(const double* x, double* y, long long n, void* st
  * N and eps) solved together.  Each instance is a bec_problem (own
  * workspace, own tables) bound to one of `nstreams` CUDA streams the batch
  * creates.  bec_batch_solve runs every instance's restarted GMRES in rounds:
- * one Arnoldi iteration of every active instance is enqueued on its stream
- * (replayed from a per-iteration CUDA graph when use_graphs != 0), then the
- * host waits once per stream and every instance reads its residual.  Work of
- * instances on different streams overlaps on the GPU. */
+ * one Arnoldi iteration of every active instance is enqueued, then the host
+ * waits once per stream and every instance reads its residual.  Work of
+ * instances on different streams overlaps on the GPU.  The mode:
+ *  - BEC_BATCH_STREAMS: each iteration's kernels are launched one by one on
+ *    the instance's stream;
+ *  - BEC_BATCH_GRAPHS: each iteration is replayed from a per-iteration CUDA
+ *    graph of the instance;
+ *  - BEC_BATCH_PERSISTENT: per stream, the P_eps^{-1} (Sec. 4, Steps 1-3)
+ *    of every instance of the stream that takes an Arnoldi step in the
+ *    round runs in ONE launch (up to 64 instances per launch): a device work
+ *    queue hands out the items (pass, instance, tile) of the five passes in
+ *    order, one per block, and a block waits (bounded, about 0.2 s; then
+ *    BEC_ETIMEOUT) until the previous pass of its instance is complete; the
+ *    rest of each step is replayed from the instance's graph after that
+ *    launch, on the same stream.  Needs FP32
+ *    sine-transform instances in 2D (finite differences, backward Euler)
+ *    with sides 31..255 and N in 4..512, and right preconditioning.  The
+ *    results equal the other modes' bit for bit (the tiles compute exactly
+ *    what the per-instance passes compute). */
 typedef struct bec_batch bec_batch;
+enum { BEC_BATCH_STREAMS = 0, BEC_BATCH_GRAPHS = 1, BEC_BATCH_PERSISTENT = 2 };
 
 /* descs[i] and eps[i] for i < count as in bec_allocate_problem/bec_set_eps;
- * nstreams in [1, 64].  On failure nothing stays allocated and
- * bec_last_error() names the failing instance. */
+ * nstreams in [1, 64]; use_graphs is the mode (BEC_BATCH_*; any other value
+ * is BEC_EINVAL).  On failure nothing stays allocated and bec_last_error()
+ * names the failing instance. */
 bec_status bec_batch_create(const bec_problem_desc* descs, const double* eps,
                             int count, int nstreams, int use_graphs,
                             bec_batch** out);
@@ -409,7 +430,8 @@ bec_status bec_batch_solve(bec_batch* b, const double* const* f,
                            double* const* u, const bec_gmres_opts* opts,
                            bec_gmres_info* infos);
 
-/* Total space-time unknowns of the batch; kernels launched by all instances. */
+/* Total space-time unknowns of the batch; kernels launched by all instances
+ * (in BEC_BATCH_PERSISTENT mode each shared P_eps^{-1} launch counts once). */
 long long bec_batch_unknowns(const bec_batch* b);
 long long bec_batch_kernel_launches(const bec_batch* b);
 

@@ -475,9 +475,13 @@ class Problem:
 class Batch:
     """Independent problems of uneven size solved together (bec_batch_*).
     `specs` is a list of dicts with keys dim, nx, N, eps and optionally T, a,
-    precision, max_restart, route, a_nodes."""
+    precision, max_restart, route, a_nodes.  `mode` is "streams", "graphs" or
+    "persistent" (BEC_BATCH_*); without it, use_graphs picks the first two."""
 
-    def __init__(self, specs, nstreams: int = 8, use_graphs: bool = True, flexible: bool = True):
+    MODES = {"streams": 0, "graphs": 1, "persistent": 2}
+
+    def __init__(self, specs, nstreams: int = 8, use_graphs: bool = True, flexible: bool = True,
+                 mode: str | None = None):
         n = len(specs)
         descs = (ProblemDesc * n)()
         eps = (ctypes.c_double * n)()
@@ -499,7 +503,8 @@ class Batch:
             eps[i] = sp["eps"]
             self.shapes.append((N,) + (nx,) * dim)
         out = ctypes.c_void_p()
-        _check(_lib().bec_batch_create(descs, eps, n, int(nstreams), int(use_graphs), ctypes.byref(out)),
+        m = self.MODES[mode] if mode is not None else int(bool(use_graphs))
+        _check(_lib().bec_batch_create(descs, eps, n, int(nstreams), m, ctypes.byref(out)),
                "bec_batch_create")
         self._b = out
         self.count = n

@@ -684,6 +684,10 @@ bec_status bec_inject_fault(int kind) {
     tc_withhold_next_loads();
     return BEC_OK;
   }
+  if (kind == BEC_FAULT_PERSIST_WITHHOLD) {
+    persist_withhold_next();
+    return BEC_OK;
+  }
   return einval("unknown fault kind");
 }
 

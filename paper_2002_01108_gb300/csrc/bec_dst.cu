@@ -6,6 +6,7 @@
 
 #include "bec_fft.cuh"
 #include "bec_internal.h"
+#include "bec_passes.cuh"
 
 namespace bec {
 namespace {
@@ -21,65 +22,16 @@ __host__ __device__ constexpr int rows_min_blocks(int bytes, int logn, int warps
   return w / warps > 0 ? w / warps : 1;
 }
 
-// DST along x: one warp per pair of contiguous rows of length m = n - 1.
-// `in` and `out` may be the same array (each warp reads its rows before
-// writing them); in that case TI == TO.
+// DST along x: one warp per pair of contiguous rows of length m = n - 1
+// (dst_rows_tile, one tile per block).  `in` and `out` may be the same array;
+// in that case TI == TO.
 template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, rows_min_blocks(sizeof(T), LOGN, WARPS))
 dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
                 const v2_t<T>* __restrict__ tw) {
-  constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per line
   extern __shared__ __align__(16) unsigned char smem_bytes[];
-  T* sm = reinterpret_cast<T*>(smem_bytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* raw = sm + (size_t)warp * 2 * RS;
-  const long long r0 = 2 * ((long long)blockIdx.x * WARPS + warp);
-  if (r0 >= rows) return;                    // whole warp leaves; no block barrier below
-  const bool hasb = r0 + 1 < rows;
-  const TI* ia = in + r0 * m;
-  // loads in groups of G per row, all issued before the group's conversions
-  // (m = n - 1 < 32 PER)
-  constexpr int PER = (1 << LOGN) / 32 > 0 ? (1 << LOGN) / 32 : 1;
-  constexpr int G = PER < 8 ? PER : 8;
-#pragma unroll
-  for (int t0 = 0; t0 < PER; t0 += G) {
-    TI va[G], vb[G];
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int j = lane + 32 * (t0 + t);
-      va[t] = j < m ? ia[j] : TI(0);
-      vb[t] = (j < m && hasb) ? ia[m + j] : TI(0);
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int j = lane + 32 * (t0 + t);
-      if (j < m) {
-        raw[j] = convert<T>(va[t]);
-        raw[RS + j] = convert<T>(vb[t]);
-      }
-    }
-  }
-  __syncwarp();
-  warp_dst_pair<T, LOGN>(raw, RS, sin2, tw, lane);
-  TO* oa = out + r0 * m;
-#pragma unroll
-  for (int t0 = 0; t0 < PER; t0 += G) {
-    TO wa[G], wb[G];
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int j = lane + 32 * (t0 + t);
-      wa[t] = j < m ? convert<TO>(raw[dst_out<T, LOGN>(j)]) : TO(0);
-      wb[t] = j < m ? convert<TO>(raw[RS + dst_out<T, LOGN>(j)]) : TO(0);
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int j = lane + 32 * (t0 + t);
-      if (j < m) {
-        oa[j] = wa[t];
-        if (hasb) oa[m + j] = wb[t];
-      }
-    }
-  }
+  dst_rows_tile<T, TI, TO, LOGN, WARPS>(in, out, rows, m, sin2, tw, blockIdx.x, smem_bytes,
+                                        threadIdx.x);
 }
 
 // Blocks per SM that the register bound of dst_cols_kernel asks for, as warps
@@ -92,47 +44,18 @@ __host__ __device__ constexpr int cols_min_blocks(int bytes, int logn, int warps
 
 // DST along the rows of every slice, in place: slice s (s < nslices, at
 // data + s * slice_stride) holds m rows of ncols values, row j at j *
-// row_stride, and the transform runs down each column (along j).  A block
-// owns W = 2 x warps adjacent columns; the tile is loaded and stored with
-// coalesced row segments, each warp transforms one column pair.  2D: the
-// y-DST of [ny][nx] slices; 3D: the y-DST of every [ny][nx] plane and the
-// z-DST of [nz][ny nx] slices.
+// row_stride, and the transform runs down each column (along j); a block
+// owns W = 2 x warps adjacent columns (dst_cols_tile) and walks the slices.
+// 2D: the y-DST of [ny][nx] slices; 3D: the y-DST of every [ny][nx] plane
+// and the z-DST of [nz][ny nx] slices.
 template <typename T, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, cols_min_blocks(sizeof(T), LOGN, WARPS))
 dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice_stride,
                 long long nslices, const T* __restrict__ sin2, const v2_t<T>* __restrict__ tw) {
-  constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per column
-  constexpr int W = 2 * WARPS;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
-  T* sm = reinterpret_cast<T*>(smem_bytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // thread t always handles column c = t mod W of the tile and the rows
-  // j = t / W + JS i.  In FP32 the tile arrives by asynchronous copies, which
-  // hold no registers, so all of a thread's loads are in flight together.
-  constexpr int JS = WARPS * 32 / W;
-  const int c = threadIdx.x % W, j0 = threadIdx.x / W;
-  const int x = blockIdx.x * W + c;
-  const bool xin = x < ncols;
-  T* const slot = sm + c * RS;
-  for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y) {
-    T* const col = data + sl * slice_stride + (xin ? x : 0);   // row j at col[j row_stride]
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll 4
-      for (int j = j0; j < m; j += JS) cp_async4(slot + j, col + (long long)j * row_stride, xin);
-      cp_async_wait_all();
-    } else {                                 // FP64: bound by its arithmetic, not by loads
-#pragma unroll 4
-      for (int j = j0; j < m; j += JS) slot[j] = xin ? col[(long long)j * row_stride] : T(0);
-    }
-    __syncthreads();
-    warp_dst_pair<T, LOGN>(sm + (size_t)warp * 2 * RS, RS, sin2, tw, lane);
-    __syncthreads();
-    if (xin) {
-#pragma unroll 4
-      for (int j = j0; j < m; j += JS) col[(long long)j * row_stride] = slot[dst_out<T, LOGN>(j)];
-    }
-    __syncthreads();
-  }
+  for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y)
+    dst_cols_tile<T, LOGN, WARPS>(data, m, ncols, row_stride, slice_stride, blockIdx.x, sl, sin2,
+                                  tw, smem_bytes, threadIdx.x);
 }
 
 template <typename Kern>

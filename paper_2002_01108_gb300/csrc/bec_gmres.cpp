@@ -107,7 +107,7 @@ bec_status iteration_body(GmresRun& r) {
   // Stewart (||w after|| < ||w before|| / sqrt 2) asks for a second one; that
   // decision is taken on the device.
   double* z = r.o.flexible ? p->Z + (long long)j * p->U : p->t;
-  BEC_TRY(apply_pinv(p, r.Vp[j], z, sigma + j));
+  if (!r.ext_pinv) BEC_TRY(apply_pinv(p, r.Vp[j], z, sigma + j));
   BEC_TRY(launch_stencil_dots(p, z, p->w, r.Vp.data(), j + 1, sigma, h1, r.Vp[j], sigma + j, S_WB));
   BEC_TRY(launch_combine(p, vnext, p->w, r.Vp.data(), j + 1, sigma, h1, -1.0, S_W));
   BEC_TRY(launch_reorth_flag(p, S_WB, S_W));
@@ -122,7 +122,7 @@ bec_status enqueue_iteration(GmresRun& r) {
   NvtxRange range("bec Arnoldi iteration");
   bec_problem* p = r.p;
   if (!r.use_graphs) return iteration_body(r);
-  const int mode = (r.o.left_pc ? 1 : 0) | (r.o.flexible ? 2 : 0);
+  const int mode = (r.o.left_pc ? 1 : 0) | (r.o.flexible ? 2 : 0) | (r.ext_pinv ? 4 : 0);
   if (p->graph_mode != mode || (int)p->graphs.size() < r.o.restart) {
     for (auto& g : p->graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -306,6 +306,14 @@ bec_status gmres_run_step(GmresRun& r, bool* enqueued) {
       return r.status;
   }
   return BEC_OK;
+}
+
+void gmres_run_pinv_operands(const GmresRun& r, const double** y, double** z,
+                             const double** scale_dev) {
+  bec_problem* p = r.p;
+  *y = r.Vp[r.j];
+  *z = r.o.flexible ? p->Z + (long long)r.j * p->U : p->t;
+  *scale_dev = p->sigma + r.j;
 }
 
 void gmres_run_info(const GmresRun& r, bec_gmres_info* info) {

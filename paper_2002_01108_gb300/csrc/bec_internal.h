@@ -161,6 +161,9 @@ struct GmresRun {
   double* u = nullptr;
   bec_gmres_opts o{};
   bool use_graphs = false;
+  // the P_eps^{-1} of each Arnoldi step is enqueued by the caller (a batch's
+  // persistent launch for all instances), not by the iteration itself
+  bool ext_pinv = false;
   State state = BEGIN;
   bec_status status = BEC_OK;
   double ref = 0.0, monitored = 1.0, true_relres = 0.0;
@@ -171,6 +174,10 @@ struct GmresRun {
 void gmres_run_init(GmresRun& r, bec_problem* p, const double* f, double* u,
                     const bec_gmres_opts& o, bool use_graphs);
 bec_status gmres_run_step(GmresRun& r, bool* enqueued);
+// Operands of the P_eps^{-1} of the coming Arnoldi step (state ITER, right
+// preconditioning): z = P^{-1} (s y) with s = *scale_dev.
+void gmres_run_pinv_operands(const GmresRun& r, const double** y, double** z,
+                             const double** scale_dev);
 void gmres_run_info(const GmresRun& r, bec_gmres_info* info);
 bec_status gmres_run_result(const GmresRun& r);
 bec_status gmres_solve_one(bec_problem* p, const double* f, double* u,
@@ -267,6 +274,48 @@ bec_status launch_time_fwd(bec_problem* p, const double* y, void* spec, int fp64
                            const double* scale_dev);
 // z[j][q] = eps^{-j/N} N^{-1} sum_k spec_k e^{2 pi i jk/N} (Hermitian extension)
 bec_status launch_time_inv(bec_problem* p, const void* spec, double* z, int fp64);
+
+// ---- persistent batched P_eps^{-1} (bec_persist.cu)
+constexpr int kPersistMaxJobs = 64;
+// One instance's FP32 sine-transform P_eps^{-1} of one round: z = P^{-1} (s y).
+struct PersistJob {
+  const double* y;
+  double* z;
+  float* s;                    // the instance's FP32 scratch (U floats)
+  const double* scale_dev;     // s (null: 1)
+  const float* sin2;
+  const float2* tws;           // spatial FFT twiddles
+  const float2* twt;           // time FFT twiddles
+  const float* es;
+  const float* eis;
+  const float2* lamf;
+  const float* mu;
+  long long J;
+  float tau, scale_h;
+  int m, N, logn, logt;
+  int tiles[5];                // tiles (queue items) of the five passes, 8 warps each
+};
+// The work queue of one launch, passed by value.
+struct PersistQueue {
+  int njobs, total;
+  int pass_start[6];                          // first item of each pass
+  int job_start[5 * (kPersistMaxJobs + 1)];   // first item of (pass p, job i) at p (njobs + 1) + i
+  int target[5 * kPersistMaxJobs];            // tiles a pass must report before the next starts
+};
+// FP32, sine transform, 2D, finite differences, backward Euler, sides 31..255, N 4..512
+bool persist_supported(const bec_problem* p);
+void persist_make_job(const bec_problem* p, const double* y, double* z, const double* scale_dev,
+                      PersistJob* j);
+// Enqueues on `st`: the copy of the jobs to jobs_dev, the reset of the
+// counters ctr_dev (4 + 5 njobs ints; ctr_dev[1] is the error word) and one
+// persistent launch.  withhold != 0: a test of the bounded waits (instance
+// 0's first pass never completes, so the launch ends with the error word set).
+bec_status persist_launch(const PersistJob* jobs_host, PersistJob* jobs_dev, int njobs,
+                          PersistQueue* q, int* ctr_dev, int withhold, cudaStream_t st);
+// test hook (bec_inject_fault): the next launch withholds instance 0's first
+// pass; persist_take_withhold returns and clears the request
+void persist_withhold_next();
+int persist_take_withhold();
 
 // ---- learned correction (bec_net.cu)
 bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp32_acts, int bmax);

@@ -14,54 +14,13 @@
 
 #include "bec_fft.cuh"
 #include "bec_internal.h"
+#include "bec_passes.cuh"
 
 namespace bec {
 namespace {
 
 template <typename T>
 constexpr int time_warps() { return default_time_warps(sizeof(T)); }
-
-// The 1D eigenvalue tables of the spatial operators on the sine basis:
-// stiffness k (times a) and mass m (null: M = I, finite differences).
-template <typename T>
-struct ModeEigs {
-  const T* __restrict__ k;
-  const T* __restrict__ m;
-};
-
-// Mass and stiffness eigenvalues of spatial mode q: FD (1, k_i + k_l); Q1
-// (m_i m_l, m_i k_l + k_i m_l) in 2D, (m_q, k_q) in 1D.
-template <typename T>
-__device__ __forceinline__ void mode_eigs(long long q, long long J, int m, int dim,
-                                          ModeEigs<T> e, T& muM, T& muK) {
-  if (q >= J) {                                  // padding column: any positive value
-    muM = T(1);
-    muK = T(1);
-    return;
-  }
-  if (dim == 1) {
-    muM = e.m ? e.m[q] : T(1);
-    muK = e.k[q];
-    return;
-  }
-  if (dim == 3) {                                // FD only: k_i + k_l + k_s
-    const long long m2 = (long long)m * m;
-    const int s = (int)(q / m2);
-    const long long r = q - (long long)s * m2;
-    const int l = (int)(r / m), i = (int)(r - (long long)l * m);
-    muM = T(1);
-    muK = e.k[i] + e.k[l] + e.k[s];
-    return;
-  }
-  const int l = (int)(q / m), i = (int)(q - (long long)l * m);
-  if (e.m == nullptr) {
-    muM = T(1);
-    muK = e.k[i] + e.k[l];
-  } else {
-    muM = e.m[i] * e.m[l];
-    muK = fma(e.m[i], e.k[l], e.k[i] * e.m[l]);
-  }
-}
 
 // rinv[q][k] = 1 / |lambda'_k + tau mu_q|^2 (same arithmetic as the division
 // it replaces in time_pass_kernel)
@@ -80,124 +39,27 @@ __global__ void rinv_table_kernel(double* __restrict__ rinv, long long J, int NK
   rinv[g] = 1.0 / fma(dr, dr, di * di);
 }
 
-// data: [N][J] in place.  A block owns W = 2 x warps adjacent modes; warp w
-// transforms modes (q0 + 2w, q0 + 2w + 1) packed as real + i imaginary.
-// registers: 128 per thread in FP64 and 64 in FP32 for N <= 256 (the block
-// count the bound asks for fills the 64K-register file), free above
-// FE: the mass eigenvalues are present (Q1 elements); finite differences
-// (M = I) take the other instantiation, without the products by mu^M.
+// data: [N][J] in place; a block owns W = 2 x warps adjacent modes
+// (time_pass_tile).  registers: 128 per thread in FP64 and 64 in FP32 for
+// N <= 256 (the block count the bound asks for fills the 64K-register
+// file), free above.  FE: the mass eigenvalues are present (Q1 elements);
+// finite differences (M = I) take the other instantiation, without the
+// products by mu^M.
 template <typename T, int LOGN, int WARPS, bool FE>
 __global__ void __launch_bounds__(WARPS * 32, LOGN <= 8 ? (sizeof(T) == 8 ? 16 : 32) / WARPS : 1)
 time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
                  ModeEigs<T> me, T tau, T scale_h, const double* __restrict__ scale_dev,
-                 const v2_t<T>* __restrict__ tw, const T* __restrict__ rinv) {
-  using V = v2_t<T>;
-  const T scale = scale_dev ? (T)((double)scale_h * scale_dev[0]) : scale_h;
-  constexpr int N = 1 << LOGN;
-  constexpr int LSC = line_slots(LOGN);
-  constexpr int W = 2 * WARPS;
+                 const v2_t<T>* __restrict__ tw, const double* __restrict__ rinv) {
   extern __shared__ __align__(16) unsigned char smem_bytes[];
-  T* sm = reinterpret_cast<T*>(smem_bytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long q0 = (long long)blockIdx.x * W;
-
-  // load + D_eps scaling: mode c of the tile -> line c/2, real (c even) or
-  // imaginary part.  Thread t always handles mode c = t mod W and the rows
-  // j = t / W + JS i.  In FP32 it issues its loads in groups of up to 16
-  // before the group's stores, so that they are in flight together.
-  constexpr int JS = WARPS * 32 / W;
-  constexpr int NI = (N + JS - 1) / JS;
-  const int c = threadIdx.x % W, j0 = threadIdx.x / W;
-  const bool qin = q0 + c < J;
-  T* const slot = sm + (c >> 1) * 2 * LSC + (c & 1);          // element j at slot[2 j]
-  T* const col = data + (qin ? q0 + c : 0);                    // element j at col[j J]
-  if constexpr (sizeof(T) == 4) {
-    constexpr int GMAX = LOGN <= 8 ? 16 : 8;   // loads in flight per group (registers)
-    constexpr int G = NI < GMAX ? NI : GMAX;
-#pragma unroll
-    for (int g = 0; g < NI; g += G) {
-      T v[G];
-#pragma unroll
-      for (int i = 0; i < G; ++i) {
-        const int j = j0 + JS * (g + i);
-        v[i] = (qin && (N % JS == 0 || j < N)) ? col[(long long)j * J] : T(0);
-      }
-#pragma unroll
-      for (int i = 0; i < G; ++i) {
-        const int j = j0 + JS * (g + i);
-        if (N % JS == 0 || j < N) slot[2 * j] = v[i] * es[j];
-      }
-    }
-  } else {                                   // FP64: bound by its arithmetic, not by loads
-#pragma unroll 4
-    for (int j = j0; j < N; j += JS) slot[2 * j] = qin ? col[(long long)j * J] * es[j] : T(0);
-  }
-  __syncthreads();
-
-  V* line = reinterpret_cast<V*>(sm + (size_t)warp * 2 * LSC);
-  warp_fft<T, -1, LOGN>(line, tw, lane);
-
-  const long long qa = q0 + 2 * warp;
-  T ma, mua, mb, mub;                 // mass and stiffness eigenvalues of modes a, b
-  mode_eigs(qa, J, m, dim, me, ma, mua);
-  if (qa + 1 < J) {
-    mode_eigs(qa + 1, J, m, dim, me, mb, mub);
-  } else {
-    mb = ma;
-    mub = mua;
-  }
-  constexpr int NK = N / 2 + 1;
-  constexpr int PERK = (NK + 31) / 32;
-#pragma unroll
-  for (int t = 0; t < PERK; ++t) {
-    const int k = lane + 32 * t;
-    if (k < NK) {
-      const int kk = (N - k) & (N - 1);
-      const V C = line[k], Cn = line[kk];
-      // A1 = spectrum of mode a, A2 = spectrum of mode b (each times 2)
-      const V A1 = {C.x + Cn.x, C.y - Cn.y};
-      const V A2 = {C.y + Cn.y, Cn.x - C.x};
-      const V L = lamf[k];
-      // d = lambda'_k mu^M + tau mu^K for each mode (mu^M = 1 with FD)
-      constexpr bool fe = FE;
-      const T d1r = fe ? fma(L.x, ma, tau * mua) : L.x + tau * mua;
-      const T d2r = fe ? fma(L.x, mb, tau * mub) : L.x + tau * mub;
-      const T d1i = fe ? L.y * ma : L.y, d2i = fe ? L.y * mb : L.y;
-      T s1, s2;
-      if (rinv != nullptr) {           // 1 / |d|^2 from the table ([q][k], coalesced in k)
-        s1 = qa < J ? scale * rinv[qa * NK + k] : T(0);
-        s2 = qa + 1 < J ? scale * rinv[(qa + 1) * NK + k] : s1;
-      } else if constexpr (sizeof(T) == 4) {
-        // |d|^2 lies far inside the normal range, where the approximate
-        // division is within 2 units in the last place
-        s1 = __fdividef(scale, fma(d1r, d1r, d1i * d1i));
-        s2 = __fdividef(scale, fma(d2r, d2r, d2i * d2i));
-      } else {
-        s1 = scale / fma(d1r, d1r, d1i * d1i);
-        s2 = scale / fma(d2r, d2r, d2i * d2i);
-      }
-      const V q1 = {d1r * s1, -d1i * s1};           // scale / d1
-      const V q2 = {d2r * s2, -d2i * s2};
-      const V B1 = cmul(A1, q1), B2 = cmul(A2, q2);
-      line[k] = {B1.x - B2.y, B1.y + B2.x};         // B1 + i B2
-      line[kk] = {B1.x + B2.y, B2.x - B1.y};        // conj(B1) + i conj(B2)
-    }
-  }
-  __syncwarp();
-  warp_fft<T, +1, LOGN>(line, tw, lane);
-  __syncthreads();
-
-  if (qin) {
-#pragma unroll 4
-    for (int j = j0; j < N; j += JS) col[(long long)j * J] = slot[2 * j] * eis[j];
-  }
+  time_pass_tile<T, LOGN, WARPS, FE>(data, J, m, dim, es, eis, lamf, me, tau, scale_h, scale_dev,
+                                     tw, rinv, blockIdx.x, smem_bytes, threadIdx.x);
 }
 
 template <typename T, int LOGN, int WARPS>
 bec_status time_launch(bec_problem* p, void* data, double scale, const double* scale_dev,
                        const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
-                       const v2_t<T>* tw, const T* rinv) {
+                       const v2_t<T>* tw, const double* rinv) {
   constexpr int warps = WARPS;
   const size_t smem = (size_t)warps * 2 * line_slots(LOGN) * sizeof(T);
   auto k = me.m != nullptr ? time_pass_kernel<T, LOGN, WARPS, true>
@@ -218,7 +80,7 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
 template <typename T, int LOGN>
 bec_status time_w(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
                   const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
-                  const v2_t<T>* tw, const T* rinv) {
+                  const v2_t<T>* tw, const double* rinv) {
   if constexpr (LOGN >= 5) {
     if (w == 4) return time_launch<T, LOGN, 4>(p, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
     if (w == 8) return time_launch<T, LOGN, 8>(p, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);
@@ -231,7 +93,7 @@ bec_status time_w(bec_problem* p, int w, void* data, double scale, const double*
 template <typename T>
 bec_status time_dispatch(bec_problem* p, int w, void* data, double scale, const double* scale_dev,
                          const T* es, const T* eis, const v2_t<T>* lamf, ModeEigs<T> me,
-                         const v2_t<T>* tw, const T* rinv) {
+                         const v2_t<T>* tw, const double* rinv) {
   switch (p->tab.time.logn) {
 #define BEC_TIME_CASE(L) \
   case L: return time_w<T, L>(p, w, data, scale, scale_dev, es, eis, lamf, me, tw, rinv);

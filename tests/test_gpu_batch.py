@@ -33,15 +33,27 @@ def _cases():
     return out
 
 
-@pytest.mark.parametrize("use_graphs,nstreams", [(True, 3), (False, 1)])
-def test_batch_equals_single_solves_and_the_oracle(use_graphs, nstreams):
+def _persistent_cases():
+    """Shapes the persistent launch covers: sides 31..255, N 4..512."""
+    out = []
+    for i, (m, N, eps) in enumerate([(31, 8, 1e-3), (63, 32, 0.05), (255, 4, 0.1), (31, 512, 1.0),
+                                     (127, 8, 1e-4), (63, 64, 0.5), (31, 32, 0.02), (255, 16, 0.2)]):
+        out.append(heat_case_2d(seed=60 + i, m=m, N=N, eps=eps))
+    return out
+
+
+@pytest.mark.parametrize("mode,nstreams", [("graphs", 3), ("streams", 1), ("persistent", 3)])
+def test_batch_equals_single_solves_and_the_oracle(mode, nstreams):
+    """Every instance equals the same instance solved alone, bit for bit
+    (the same kernels, or in persistent mode the same tiles taken from the
+    shared work queue), and the oracle's sequential stepping to 1e-8."""
     import torch
     from paper_2002_01108_gb300 import Batch, Problem
-    cases = _cases()
+    cases = _persistent_cases() if mode == "persistent" else _cases()
     specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
     fs = [dev(O.build_rhs(c.u0, c.fsrc, c.tau)) for c in cases]
     us = [torch.empty_like(f) for f in fs]
-    with Batch(specs, nstreams=nstreams, use_graphs=use_graphs) as b:
+    with Batch(specs, nstreams=nstreams, mode=mode) as b:
         for rep in range(2):       # the second solve replays the captured graphs
             infos = b.solve(fs, us, restart=10, rtol=1e-10)
             assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-10 for i in infos), infos
@@ -74,6 +86,41 @@ def _chosen(cases):
     return sorted(pick)
 
 
+def test_persistent_batch_rejects_unsupported_instances():
+    from paper_2002_01108_gb300 import Batch, BecError
+    with pytest.raises(BecError) as e:      # side 15 is below the launch's shapes
+        Batch([dict(dim=2, nx=15, N=8, eps=0.1, precision="fp32")], mode="persistent")
+    assert e.value.status == 1
+    with pytest.raises(BecError):           # FP64 preconditioner
+        Batch([dict(dim=2, nx=31, N=8, eps=0.1, precision="fp64")], mode="persistent")
+
+
+def test_persistent_batch_bounded_wait_runs_out_and_recovers():
+    """bec_inject_fault(BEC_FAULT_PERSIST_WITHHOLD): the next shared launch
+    never reports instance 0's first pass done, so the blocks of its second
+    pass wait until their bound (about 0.2 s) and the solve returns
+    BEC_ETIMEOUT; the next solve on the same batch is again exact."""
+    import torch
+    from paper_2002_01108_gb300 import Batch, BecError, bec
+    lib = bec.load()
+    cases = _persistent_cases()[:3]
+    specs = [dict(dim=2, nx=c.m, N=c.N, eps=c.eps, precision="fp32", max_restart=10) for c in cases]
+    fs = [dev(O.build_rhs(c.u0, c.fsrc, c.tau)) for c in cases]
+    us = [torch.empty_like(f) for f in fs]
+    with Batch(specs, nstreams=2, mode="persistent") as b:
+        ref = b.solve(fs, us, restart=10, rtol=1e-10)
+        u_ref = [u.clone() for u in us]
+        assert lib.bec_inject_fault(2) == 0
+        with pytest.raises(BecError) as e:
+            b.solve(fs, us, restart=10, rtol=1e-10)
+        assert e.value.status == 6
+        assert b"ran out" in lib.bec_last_error()
+        again = b.solve(fs, us, restart=10, rtol=1e-10)
+        torch.cuda.synchronize()
+        assert again == ref
+        assert all(torch.equal(a, r) for a, r in zip(us, u_ref))
+
+
 def test_batch_64_uneven_instances():
     """64 instances, side in {63, 127, 255}, N in {32..512}, ln eps ~ U[ln 1e-4,
     ln sqrt(tau)]: FP32 preconditioner, FP64 FGMRES(10), every instance to
@@ -101,6 +148,13 @@ def test_batch_64_uneven_instances():
         infos = b.solve(fs, us, restart=10, rtol=1e-10)
         assert all(i["converged"] == 1 and i["true_relres"] <= 1.01e-10 for i in infos)
         torch.cuda.synchronize()
+        # the persistent form of the same batch: bit for bit the same results
+        with Batch(specs, nstreams=8, mode="persistent") as bp:
+            us_p = [torch.empty_like(f) for f in fs]
+            infos_p = bp.solve(fs, us_p, restart=10, rtol=1e-10)
+            torch.cuda.synchronize()
+            assert infos_p == infos
+            assert all(torch.equal(a, c) for a, c in zip(us_p, us))
         for i in chosen:
             c = cases[i]
             K = O.fd_stiffness(2, c.m)
