@@ -676,7 +676,8 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
         dom = "net_conv_tc_kernel"
         n, tot = kernels[dom]
         avg = tot / n
-        applies = kernels["mg_coarsest_kernel"][0]   # one V-cycle per P_eps^{-1} apply
+        # one V-cycle per P_eps^{-1} apply, each ending in one coarsest solve
+        applies = (kernels.get("mg_coarse_cycle_kernel") or kernels["mg_coarsest_kernel"])[0]
         peaks, src = measured_peaks()
         pk = peaks.get("bf16_tflops_sustained", 1698.3)
         # every layer runs on the tensor cores; algorithmic FLOPs exclude the

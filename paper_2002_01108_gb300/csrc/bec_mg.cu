@@ -230,6 +230,221 @@ __global__ void mg_coarsest_kernel(v2_t<T>* __restrict__ x, const v2_t<T>* __res
   x[k] = {c.x * inv, c.y * inv};
 }
 
+// ------------------------------------------------- fused coarse-grid cycle
+// The levels from lc down to the 1 x 1 grid of one V-cycle in a single
+// kernel: one block per frequency, every level's x, b and r in shared memory,
+// the steps separated by block barriers.  Each step is the per-point
+// arithmetic of the per-level kernels above (same formulas, same order), so
+// the result is the same bit for bit; it replaces 3 + pre + post launches per
+// level, whose run time on these small grids is mostly launch latency.
+constexpr int kMgCoarseMax = 8;        // fused levels at most
+constexpr int kMgCoarseThreads = 256;
+
+template <typename T>
+struct MgCoarseArgs {
+  const T* SM[kMgCoarseMax];
+  const T* SK[kMgCoarseMax];
+  int m[kMgCoarseMax];
+  int nlev;                      // fused levels (the last is 1 x 1)
+  const v2_t<T>* lam;
+  T tau, omega;
+  int pre, post;
+  const v2_t<T>* b_in;           // [K][J_0] right-hand side of the first fused level
+  v2_t<T>* x_out;                // [K][J_0] its V-cycle result
+};
+
+// xo = x + omega D^{-1} (b - B x) (ZERO: x = 0) at every point of one level
+template <typename T, bool ZERO>
+__device__ __forceinline__ void cc_smooth(v2_t<T>* xo, const v2_t<T>* x, const v2_t<T>* b,
+                                          const T* SMl, const T* SKl, int m, v2_t<T> lam, T tau,
+                                          T omega) {
+  using V = v2_t<T>;
+  MgArgs<T> a;
+  a.SM = SMl;
+  a.SK = SKl;
+  a.m = m;
+  a.J = (long long)m * m;
+  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads) {
+    T sm[9], sk[9];
+    int off[9];
+    bool ok[9];
+    load_point<T, false>(a, q, sm, sk, off, ok);
+    const V D = {lam.x * sm[4] + tau * sk[4], lam.y * sm[4]};
+    const T d2 = D.x * D.x + D.y * D.y;
+    T inv;
+    if constexpr (sizeof(T) == 8) inv = omega * rcp64(d2);
+    else inv = omega / d2;
+    V rr = b[q];
+    V x0 = {0, 0};
+    if (!ZERO) {
+      x0 = x[q];
+      const V bx = apply_b<T, false>(x, sm, sk, off, ok, lam, tau);
+      rr = {rr.x - bx.x, rr.y - bx.y};
+    }
+    const V c = cmulc(rr, D);
+    xo[q] = {x0.x + c.x * inv, x0.y + c.y * inv};
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cc_residual(v2_t<T>* r, const v2_t<T>* x, const v2_t<T>* b,
+                                            const T* SMl, const T* SKl, int m, v2_t<T> lam, T tau) {
+  using V = v2_t<T>;
+  MgArgs<T> a;
+  a.SM = SMl;
+  a.SK = SKl;
+  a.m = m;
+  a.J = (long long)m * m;
+  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads) {
+    T sm[9], sk[9];
+    int off[9];
+    bool ok[9];
+    load_point<T, false>(a, q, sm, sk, off, ok);
+    const V bx = apply_b<T, false>(x, sm, sk, off, ok, lam, tau);
+    const V bb = b[q];
+    r[q] = {bb.x - bx.x, bb.y - bx.y};
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cc_restrict(v2_t<T>* bc, const v2_t<T>* r, int mc, int mf) {
+  using V = v2_t<T>;
+  for (int c = threadIdx.x; c < mc * mc; c += kMgCoarseThreads) {
+    const int cy = c / mc, cx = c - cy * mc;
+    const int f0 = (2 * cy + 1) * mf + (2 * cx + 1);
+    V acc = {0, 0};
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const T w = (dy == 0 ? T(0.5) : T(0.25)) * (dx == 0 ? T(0.5) : T(0.25));
+        const V v = r[f0 + dy * mf + dx];
+        acc.x += w * v.x;
+        acc.y += w * v.y;
+      }
+    }
+    bc[c] = acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cc_prolong_add(v2_t<T>* x, const v2_t<T>* xc, int mf, int mc) {
+  using V = v2_t<T>;
+  for (int f = threadIdx.x; f < mf * mf; f += kMgCoarseThreads) {
+    const int fy = f / mf, fx = f - fy * mf;
+    int cyv[2], cxv[2];
+    T wy[2], wx[2];
+    int ny, nx;
+    if (fy & 1) { ny = 1; cyv[0] = (fy - 1) / 2; wy[0] = 1; } else {
+      ny = 2; cyv[0] = fy / 2 - 1; cyv[1] = fy / 2; wy[0] = wy[1] = T(0.5);
+    }
+    if (fx & 1) { nx = 1; cxv[0] = (fx - 1) / 2; wx[0] = 1; } else {
+      nx = 2; cxv[0] = fx / 2 - 1; cxv[1] = fx / 2; wx[0] = wx[1] = T(0.5);
+    }
+    V acc = x[f];
+    for (int a = 0; a < ny; ++a) {
+      if (cyv[a] < 0 || cyv[a] >= mc) continue;
+      for (int b = 0; b < nx; ++b) {
+        if (cxv[b] < 0 || cxv[b] >= mc) continue;
+        const T w = wy[a] * wx[b];
+        const V v = xc[cyv[a] * mc + cxv[b]];
+        acc.x += w * v.x;
+        acc.y += w * v.y;
+      }
+    }
+    x[f] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMgCoarseThreads)
+mg_coarse_cycle_kernel(const __grid_constant__ MgCoarseArgs<T> a) {
+  using V = v2_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  const int k = blockIdx.x;
+  const V lam = a.lam[k];
+  // per level: x, b, r (J_l complex each), levels one after another
+  V* xs[kMgCoarseMax];
+  V* bs[kMgCoarseMax];
+  V* rs[kMgCoarseMax];
+  {
+    V* p = reinterpret_cast<V*>(smem_bytes);
+#pragma unroll
+    for (int l = 0; l < kMgCoarseMax; ++l) {
+      if (l < a.nlev) {
+        const int J = a.m[l] * a.m[l];
+        xs[l] = p;
+        bs[l] = p + J;
+        rs[l] = p + 2 * J;
+        p += 3 * J;
+      }
+    }
+  }
+  const int J0 = a.m[0] * a.m[0];
+  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads) bs[0][q] = a.b_in[(long long)k * J0 + q];
+  __syncthreads();
+  for (int l = 0; l + 1 < a.nlev; ++l) {
+    cc_smooth<T, true>(xs[l], nullptr, bs[l], a.SM[l], a.SK[l], a.m[l], lam, a.tau, a.omega);
+    __syncthreads();
+    for (int s = 1; s < a.pre; ++s) {
+      cc_smooth<T, false>(rs[l], xs[l], bs[l], a.SM[l], a.SK[l], a.m[l], lam, a.tau, a.omega);
+      __syncthreads();
+      V* t = xs[l];
+      xs[l] = rs[l];
+      rs[l] = t;
+    }
+    cc_residual<T>(rs[l], xs[l], bs[l], a.SM[l], a.SK[l], a.m[l], lam, a.tau);
+    __syncthreads();
+    cc_restrict<T>(bs[l + 1], rs[l], a.m[l + 1], a.m[l]);
+    __syncthreads();
+  }
+  {
+    // the 1 x 1 level: x = b / (lambda'_k M + tau K)
+    const int l = a.nlev - 1;
+    if (threadIdx.x == 0) {
+      const T sm = a.SM[l][4], sk = a.SK[l][4];
+      const V D = {lam.x * sm + a.tau * sk, lam.y * sm};
+      const T inv = T(1) / (D.x * D.x + D.y * D.y);
+      const V c = cmulc(bs[l][0], D);
+      xs[l][0] = {c.x * inv, c.y * inv};
+    }
+    __syncthreads();
+  }
+  for (int l = a.nlev - 2; l >= 0; --l) {
+    cc_prolong_add<T>(xs[l], xs[l + 1], a.m[l], a.m[l + 1]);
+    __syncthreads();
+    for (int s = 0; s < a.post; ++s) {
+      cc_smooth<T, false>(rs[l], xs[l], bs[l], a.SM[l], a.SK[l], a.m[l], lam, a.tau, a.omega);
+      __syncthreads();
+      V* t = xs[l];
+      xs[l] = rs[l];
+      rs[l] = t;
+    }
+  }
+  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads) a.x_out[(long long)k * J0 + q] = xs[0][q];
+}
+
+// shared memory of the fused cycle from level l of the hierarchy down
+size_t coarse_cycle_smem(const std::vector<MgLevel>& lv, int l, size_t vsize) {
+  size_t b = 0;
+  for (size_t i = l; i < lv.size(); ++i) b += 3 * (size_t)lv[i].J * vsize;
+  return b;
+}
+
+// the first level the fused cycle takes: the largest below the finest grid
+// (which keeps its 5-point kernels) whose x, b and r for it and every coarser
+// level fit in kMgCoarseSmem bytes (at least two levels; -1: none, or the
+// ILU smoother)
+constexpr size_t kMgCoarseSmem = 160 * 1024;
+int coarse_cycle_level(const bec_problem* p, size_t vsize) {
+  const std::vector<MgLevel>& lv = p->mg.lv;
+  const int L = (int)lv.size();
+  if (p->mg.ilu || L < 3) return -1;
+  for (int l = 1; l + 1 < L; ++l)
+    if (L - l <= kMgCoarseMax && coarse_cycle_smem(lv, l, vsize) <= kMgCoarseSmem) return l;
+  return -1;
+}
+
 // ---------------------------------------------------------------- ILU smoother
 // The triangular recurrences of M run over the wavefronts t = x + 2y of a
 // level's grid (x fastest): every lower neighbour of (x, y) (W, SE on t - 1;
@@ -690,7 +905,10 @@ bec_status vcycle_t(bec_problem* p) {
   std::vector<MgLevel>& lv = p->mg.lv;
   const int L = (int)lv.size();
   const int K = p->mg.K;
-  for (int l = 0; l + 1 < L; ++l) {
+  // levels >= lc run in one fused kernel (the whole coarse part of the cycle)
+  const int lc = coarse_cycle_level(p, sizeof(V));
+  const int ltop = lc >= 0 ? lc : L - 1;   // levels above it run per level
+  for (int l = 0; l < ltop; ++l) {
     MgLevel& c = lv[l];
     const MgArgs<T> a = level_args<T>(p, c);
     const dim3 g = mg_grid(c.J, K);
@@ -726,14 +944,36 @@ bec_status vcycle_t(bec_problem* p) {
         static_cast<V*>(n.b), static_cast<const V*>(c.r), n.m, c.m, K);
     BEC_LAUNCH_CHECK(p, kRestrictNames[l]);
   }
-  {
+  if (lc >= 0) {
+    MgCoarseArgs<T> ca;
+    ca.nlev = L - lc;
+    for (int i = 0; i < ca.nlev; ++i) {
+      ca.SM[i] = static_cast<const T*>(lv[lc + i].SM);
+      ca.SK[i] = static_cast<const T*>(lv[lc + i].SK);
+      ca.m[i] = lv[lc + i].m;
+    }
+    ca.lam = level_args<T>(p, lv[lc]).lam;
+    ca.tau = (T)p->tau;
+    ca.omega = (T)p->mg.omega;
+    ca.pre = p->mg.pre;
+    ca.post = p->mg.post;
+    ca.b_in = static_cast<const V*>(lv[lc].b);
+    ca.x_out = static_cast<V*>(lv[lc].x);
+    const size_t smem = coarse_cycle_smem(lv, lc, sizeof(V));
+    if (smem > 48 * 1024)
+      BEC_CUDA_TRY(cudaFuncSetAttribute(mg_coarse_cycle_kernel<T>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BEC_LAUNCH_BEGIN(p);
+    mg_coarse_cycle_kernel<T><<<K, kMgCoarseThreads, smem, p->stream>>>(ca);
+    BEC_LAUNCH_CHECK(p, "mg_coarse_cycle_kernel");
+  } else {
     MgLevel& c = lv[L - 1];
     BEC_LAUNCH_BEGIN(p);
     mg_coarsest_kernel<T><<<(K + 127) / 128, 128, 0, p->stream>>>(
         static_cast<V*>(c.x), static_cast<const V*>(c.b), level_args<T>(p, c));
     BEC_LAUNCH_CHECK(p, "mg_coarsest_kernel");
   }
-  for (int l = L - 2; l >= 0; --l) {
+  for (int l = ltop - 1; l >= 0; --l) {
     MgLevel& c = lv[l];
     const MgLevel& n = lv[l + 1];
     const dim3 g = mg_grid(c.J, K);
