@@ -55,13 +55,16 @@ enum {
   BEC_ROUTE_LEARNED = 2, /* BEC_ROUTE_MG plus a learned correction of what each
                           V-cycle leaves: a 4-level convolutional network on
                           the grid of spacing 2h (BF16 activations, FP32
-                          accumulation), trained on the GPU by
-                          bec_learned_train on pairs the multigrid generates;
-                          per frequency the corrected iterate gets one
-                          damped-Jacobi sweep and the judge then takes the
-                          complex step from the V-cycle's iterate towards it
-                          that minimises ||b - B x||, so the residual never
-                          grows (the V-cycle is the fallback).  Needs
+                          accumulation), linear in the residual (its layers
+                          are gated by functions of log a and lambda'_k
+                          only), trained on the GPU by bec_learned_train on
+                          pairs the multigrid generates; per frequency the
+                          corrected iterate gets one damped-Jacobi sweep and
+                          the step from the V-cycle's iterate towards it is
+                          scaled by alpha_k, the minimal-residual step of a
+                          calibration apply on a fixed right-hand side
+                          (alpha_k = 0: the V-cycle is the fallback).  So
+                          P_eps^{-1} stays a fixed linear operator.  Needs
                           BEC_PC_FP32 and nx >= 31. */
   BEC_ROUTE_MG = 1     /* one geometric multigrid V-cycle per shifted system,
                           any positive a (Sec. 4; Example 2 of Sec. 5): bilinear
@@ -287,40 +290,53 @@ bec_status bec_relres_noalloc(int dim, int nx, int N, double T, double a,
 bec_status bec_free_problem(bec_problem* p);
 
 /* ---- Learned correction (BEC_ROUTE_LEARNED) -------------------------------
- * The network's weights: 9 layers of 3 x 3 convolutions, layer i a FP32
- * array [3][3][c_in][c_out] (c = 5 -> C, C -> C x 7, C -> 2), concatenated. */
+ * The network's weights, FP32, concatenated in this order (C channels):
+ *  - the 9 convolutions of the residual path, layer i an array
+ *    [3][3][c_in][c_out] (2 -> C, C -> C x 7, C -> 2);
+ *  - the a-gates' first convolutions A1_0..A1_7, [3][3][1][8] each;
+ *  - their second convolutions A2_0..A2_7, [3][3][8][C] each;
+ *  - the lambda-gates' first layers L1_0..L1_7, [2][16] each;
+ *  - their second layers L2_0..L2_7, [16][C] each.
+ * Gated layer i's output is multiplied point by point by
+ * (1 + tanh(conv(relu(conv(log a, A1_i)), A2_i))) (1 + tanh(relu(lam2 L1_i) L2_i)),
+ * lam2 = (Re, Im) lambda'_k, log a centred on the layer's grid: the network
+ * is linear in the residual it corrects. */
 long long bec_learned_num_weights(const bec_problem* p);
 bec_status bec_learned_get_weights(bec_problem* p, float* host);
 bec_status bec_learned_set_weights(bec_problem* p, const float* host);
 
 /* Trains the network on the GPU: every ceil((N/2+1)/batch) steps a fresh set
- * of pairs (r, B_k^{-1} r) is made for all frequencies (r = what one V-cycle
- * leaves of a random right-hand side; B_k^{-1} r by 12 defect-correction
- * V-cycles); each step draws `batch` frequencies, runs the forward and
- * backward kernels on the relative error ||e - e*||^2 / ||e*||^2 and takes
- * one Adam step with learning rate lr.  loss_history (host, `steps` doubles,
- * may be NULL) receives the mean batch loss of every step.  Synchronises. */
+ * of pairs is made for all frequencies (r = what one V-cycle leaves of a
+ * random right-hand side; target the coarse-grid correction B_{k,1}^{-1} R_0 r
+ * on the grid of spacing 2h, by 12 defect-correction V-cycles from level 1);
+ * each step draws `batch` frequencies, runs the forward and backward kernels
+ * on the relative error ||ec - ec*||^2 / ||ec*||^2 and takes one Adam step
+ * with learning rate lr.  loss_history (host, `steps` doubles, may be NULL)
+ * receives the mean batch loss of every step.  The next apply recalibrates
+ * the steps alpha_k.  Synchronises. */
 bec_status bec_learned_train(bec_problem* p, int steps, int batch, double lr,
                              unsigned long long seed, double* loss_history);
 
 /* Loss and weight gradient for B given samples (a check of the kernels):
- * lam_idx (host, B ints) the frequency index k of each sample, r and e_target
- * DEVICE arrays of B fine-grid complex128 fields [B][ny][nx][2].  loss (host)
- * receives the mean relative error, grad (host, may be NULL) the gradient of
- * every weight.  Synchronises. */
+ * lam_idx (host, B ints) the frequency index k of each sample, r DEVICE
+ * complex128 fine-grid residuals [B][ny][nx][2], e_target DEVICE complex128
+ * coarse targets [B][mc][mc][2], mc = (nx - 1) / 2.  loss (host) receives the
+ * mean relative error, grad (host, may be NULL) the gradient of every weight.
+ * Synchronises. */
 bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx,
                                  const double* r, const double* e_target,
                                  double* loss, float* grad);
 
-/* Frequencies at which the last bec_apply_Pinv kept the V-cycle result
- * because the judged step was 0 (B d = 0 or not finite; -1: not learned).
+/* Frequencies at which the last calibration found no step (alpha_k = 0,
+ * the V-cycle's iterate kept: B d = 0 or not finite; -1: not learned).
  * Synchronises. */
 long long bec_learned_fallbacks(bec_problem* p);
 
-/* ||b_k - B_k x_k|| after the judged correction divided by the V-cycle's
- * ||b_k - B_k x_k||, for every frequency k = 0..N/2 of the last
- * bec_apply_Pinv (host array of N/2+1 doubles; a value of 1 means the
- * correction gained nothing there).  Synchronises. */
+/* ||b_k - B_k x_k|| after the calibrated step divided by the V-cycle's
+ * ||b_k - B_k x_k||, for every frequency k = 0..N/2, on the calibration's
+ * fixed right-hand side (host array of N/2+1 doubles; 1 means the correction
+ * gained nothing there).  The calibration runs at the first apply after the
+ * weights or eps change.  Synchronises. */
 bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
 
 /* ---- Failure detection (test hook) ---------------------------------------

@@ -1,35 +1,48 @@
-"""FP64 NumPy oracle of the learned correction network used as an inner
-preconditioner for the shifted systems B_k = lambda_k I + tau K(a) of Sec. 4
-(variable coefficient, where the sine transform no longer applies).
+"""FP64 NumPy oracle of the learned correction used as an inner preconditioner
+for the shifted systems B_k = lambda_k I + tau K(a) of Sec. 4 (variable
+coefficient, where the sine transform no longer applies).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-The network is a 4-level convolutional correction with the multigrid's own
-grid hierarchy (m_{l+1} = (m_l - 1)/2, bilinear prolongation P and
-full-weighting restriction R = P^T/4 as its fixed up- and down-sampling):
+The correction is applied after one multigrid V-cycle to the residual r it
+left, and it is LINEAR in r: for a fixed coefficient a and frequency k it is
+a fixed real-linear map, so that the preconditioner P_eps^{-1} stays a fixed
+linear operator and the outer Krylov method keeps its acceleration.  It runs
+on the grid of spacing 2h (the multigrid's level 1) with 4 levels, the
+multigrid's own bilinear prolongation P and full-weighting restriction
+R = P^T/4 as its down- and up-sampling:
 
-    level 0:  h0 = relu(conv(x, W0)); s0 = relu(conv(h0, W1))
-    level 1:  s1 = relu(conv(R s0, W2))
-    level 2:  s2 = relu(conv(R s1, W3))
-    level 3:  s3 = relu(conv(R s2, W4))
-    up:       u2 = relu(conv(P s3 + s2, W5))
-              u1 = relu(conv(P u2 + s1, W6))
-              u0 = relu(conv(P u1 + s0, W7))
-    output:   y = conv(u0, W8)           (2 channels: real and imaginary part)
+    rc = R_0 r;   x = c_k [Re rc, Im rc]            (2 channels)
+    h0 = conv(x, W0) G0;           s0 = conv(h0, W1) G1
+    s1 = conv(R s0, W2) G2;        s2 = conv(R s1, W3) G3;   s3 = conv(R s2, W4) G4
+    u2 = conv(P s3 + s2, W5) G5;   u1 = conv(P u2 + s1, W6) G6
+    u0 = conv(P u1 + s0, W7) G7;   y = conv(u0, W8)  (2 channels)
+    ec = y_0 + i y_1 (the coarse correction),   e = P_0 ec
 
 Every conv is a 3 x 3 correlation with zero padding and no bias; a weight
-tensor W has shape [3][3][C_in][C_out] and out[co](y, x) = sum_{dy,dx,ci}
-W[dy+1][dx+1][ci][co] in[ci](y+dy, x+dx).  Activations are [C][m][m].
+tensor W has shape [3][3][C_in][C_out].  c_k = 1 / |lambda_k + tau a_mean
+2 pi^2| (the size of B_k^{-1} on the smoothest mode).  The gates multiply
+each channel of a layer's output point by point:
 
-The network runs one level below the fine grid.  For a fine residual r
-(the residual left by one V-cycle), r_c = R_0 r is restricted to the grid
-of spacing 2h.  The input channels (5) are r_c / s (real and imaginary
-parts), log a at the coarse nodes (centred), and the real and imaginary
-parts of lambda_k as constant planes; s is the root-mean-square of r_c.  The
-correction is e = P_0 (s c_k (y_0 + i y_1)) with c_k = 1 / |lambda_k +
-tau a_mean 2 pi^2|, the size of B_k^{-1} on the smoothest mode.  Training
-minimises the relative error ||e - e*||^2 / ||e*||^2 to pairs
-(r, e* = B_k^{-1} r) that the multigrid generates.
+    G_i = GA_i(x, c) GL_i(c),
+    GA_i = 1 + tanh(conv(relu(conv(la_l, A1_i)), A2_i))   (from log a only)
+    GL_i = 1 + tanh(relu(lam2 L1_i) L2_i)                 (from lambda_k only)
+
+with la_l the centred log a on the layer's level l (levels of the gated
+layers: 0 0 1 2 3 2 1 0) and lam2 = (Re lambda_k, Im lambda_k).  The gates
+depend on a and k but not on r: that is what lets the correction adapt to
+the coefficient field and the frequency while staying linear in r (a ReLU
+network of r, tried first, made the preconditioner non-linear, and the
+outer FGMRES then lost more iterations than the correction saved).
+
+Training target: the exact coarse-grid correction ec* = B_{k,1}^{-1} R_0 r,
+B_{k,1} = lambda_k M_1 + tau K_1 the Galerkin operator of level 1; loss =
+mean over samples of ||ec - ec*||^2 / ||ec*||^2.  After the correction one
+damped-Jacobi sweep follows (the post-smoothing of a prolonged correction),
+and the step from the V-cycle's iterate is scaled by a complex alpha_k fixed
+per frequency by one calibration apply (the minimal-residual step on a
+fixed right-hand side); alpha_k = 0 keeps the V-cycle's result (the
+multigrid is the fallback).
 """
 from __future__ import annotations
 
@@ -40,23 +53,63 @@ import numpy as np
 from .bec_oracle import mg_prolongation
 
 N_LAYERS = 9
-C_IN = 5
+N_GATED = 8
+C_IN = 2
 C_OUT = 2
+NA = 8            # hidden channels of an a-gate
+NL = 16           # hidden units of a lambda-gate
+GATE_LEVEL = (0, 0, 1, 2, 3, 2, 1, 0)
 
 
 def layer_shapes(C: int):
-    """(C_in, C_out) of the 9 convolutions."""
+    """(C_in, C_out) of the 9 convolutions of the residual path."""
     return [(C_IN, C), (C, C), (C, C), (C, C), (C, C), (C, C), (C, C), (C, C), (C, C_OUT)]
 
 
-def init_params(C: int, seed: int = 0):
-    """He-normal initialisation, last layer scaled down."""
+def param_shapes(C: int):
+    """Shapes of every parameter array in the order of the flat weight vector:
+    W0..W8, A1_0..A1_7, A2_0..A2_7, L1_0..L1_7, L2_0..L2_7."""
+    out = [(3, 3, ci, co) for ci, co in layer_shapes(C)]
+    out += [(3, 3, 1, NA)] * N_GATED + [(3, 3, NA, C)] * N_GATED
+    out += [(2, NL)] * N_GATED + [(NL, C)] * N_GATED
+    return out
+
+
+def num_params(C: int) -> int:
+    return sum(int(np.prod(s)) for s in param_shapes(C))
+
+
+def unflatten(w, C: int) -> dict:
+    """The parameter dict {"W", "A1", "A2", "L1", "L2"} of a flat vector."""
+    arrs, off = [], 0
+    for s in param_shapes(C):
+        n = int(np.prod(s))
+        arrs.append(np.asarray(w[off:off + n], dtype=np.float64).reshape(s))
+        off += n
+    g = N_GATED
+    return {"W": arrs[:9], "A1": arrs[9:9 + g], "A2": arrs[9 + g:9 + 2 * g],
+            "L1": arrs[9 + 2 * g:9 + 3 * g], "L2": arrs[9 + 3 * g:9 + 4 * g]}
+
+
+def flatten(params: dict) -> np.ndarray:
+    parts = params["W"] + params["A1"] + params["A2"] + params["L1"] + params["L2"]
+    return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
+
+
+def init_params(C: int, seed: int = 0, gate_scale: float = 0.0) -> dict:
+    """Seeded initialisation: W normal with std sqrt(1 / (9 C_in)) (the last
+    layer scaled by 0.1), A1 std 0.3, L1 std 0.5; A2 and L2 normal with std
+    gate_scale (0: every gate starts at 1)."""
     rng = np.random.default_rng(seed)
-    ps = []
+    W = []
     for i, (ci, co) in enumerate(layer_shapes(C)):
-        std = math.sqrt(2.0 / (9 * ci)) * (0.1 if i == N_LAYERS - 1 else 1.0)
-        ps.append(rng.standard_normal((3, 3, ci, co)) * std)
-    return ps
+        std = math.sqrt(1.0 / (9 * ci)) * (0.1 if i == N_LAYERS - 1 else 1.0)
+        W.append(rng.standard_normal((3, 3, ci, co)) * std)
+    A1 = [rng.standard_normal((3, 3, 1, NA)) * 0.3 for _ in range(N_GATED)]
+    A2 = [rng.standard_normal((3, 3, NA, C)) * gate_scale for _ in range(N_GATED)]
+    L1 = [rng.standard_normal((2, NL)) * 0.5 for _ in range(N_GATED)]
+    L2 = [rng.standard_normal((NL, C)) * gate_scale for _ in range(N_GATED)]
+    return {"W": W, "A1": A1, "A2": A2, "L1": L1, "L2": L2}
 
 
 def conv3x3(x: np.ndarray, W: np.ndarray) -> np.ndarray:
@@ -95,20 +148,6 @@ class Transfers:
         return np.stack([(self.P[l] @ c.reshape(-1)).reshape(mf, mf) for c in x])
 
 
-def forward(params, x: np.ndarray, tr: Transfers) -> np.ndarray:
-    """The network of the module docstring on one input [5][m][m]."""
-    W = params
-    h0 = relu(conv3x3(x, W[0]))
-    s0 = relu(conv3x3(h0, W[1]))
-    s1 = relu(conv3x3(tr.restrict(0, s0), W[2]))
-    s2 = relu(conv3x3(tr.restrict(1, s1), W[3]))
-    s3 = relu(conv3x3(tr.restrict(2, s2), W[4]))
-    u2 = relu(conv3x3(tr.prolong(2, s3) + s2, W[5]))
-    u1 = relu(conv3x3(tr.prolong(1, u2) + s1, W[6]))
-    u0 = relu(conv3x3(tr.prolong(0, u1) + s0, W[7]))
-    return conv3x3(u0, W[8])
-
-
 def coarse_log_a(log_a_nodes: np.ndarray, mc: int) -> np.ndarray:
     """log a at the nodes of the grid of spacing 2h (fine node (2i+2, 2j+2) of
     the (m+2)^2 node array), centred by the mean over all fine nodes."""
@@ -116,18 +155,49 @@ def coarse_log_a(log_a_nodes: np.ndarray, mc: int) -> np.ndarray:
     return la - float(np.mean(log_a_nodes))
 
 
-def features(rc: np.ndarray, la_c: np.ndarray, lam: complex):
-    """Input planes and the residual scale s for one coarse complex residual."""
-    s = math.sqrt(float(np.mean(np.abs(rc) ** 2)))
-    s = s if s > 0 else 1.0
-    mc = rc.shape[0]
-    x = np.stack([rc.real / s, rc.imag / s, la_c, np.full((mc, mc), lam.real),
-                  np.full((mc, mc), lam.imag)])
-    return x, s
+def level_log_a(la0: np.ndarray, tr: Transfers):
+    """The centred log a on the network's 4 levels: level 0 as given, level
+    l + 1 the full-weighting restriction of level l."""
+    out = [la0]
+    for l in range(len(tr.sizes) - 1):
+        out.append(tr.restrict(l, out[-1][None])[0])
+    return out
+
+
+def a_gates(params: dict, la_levels) -> list:
+    """GA_i = 1 + tanh(conv(relu(conv(la_l, A1_i)), A2_i)), [C][m_l][m_l]."""
+    out = []
+    for i in range(N_GATED):
+        la = la_levels[GATE_LEVEL[i]][None]
+        out.append(1.0 + np.tanh(conv3x3(relu(conv3x3(la, params["A1"][i])), params["A2"][i])))
+    return out
+
+
+def lam_gates(params: dict, lam: complex) -> list:
+    """GL_i = 1 + tanh(relu(lam2 L1_i) L2_i), [C], lam2 = (Re lambda, Im lambda)."""
+    lam2 = np.array([lam.real, lam.imag])
+    return [1.0 + np.tanh(relu(lam2 @ params["L1"][i]) @ params["L2"][i]) for i in range(N_GATED)]
 
 
 def output_scale(lam: complex, tau: float, a_mean: float) -> float:
+    """c_k = 1 / |lambda + tau a_mean 2 pi^2|."""
     return 1.0 / abs(lam + tau * a_mean * 2.0 * math.pi ** 2)
+
+
+def forward(params: dict, x: np.ndarray, GA: list, GL: list, tr: Transfers) -> np.ndarray:
+    """The residual path of the module docstring on one input [2][m][m], with
+    the gates GA (list of [C][m_l][m_l]) and GL (list of [C])."""
+    W = params["W"]
+    G = [GA[i] * GL[i][:, None, None] for i in range(N_GATED)]
+    h0 = conv3x3(x, W[0]) * G[0]
+    s0 = conv3x3(h0, W[1]) * G[1]
+    s1 = conv3x3(tr.restrict(0, s0), W[2]) * G[2]
+    s2 = conv3x3(tr.restrict(1, s1), W[3]) * G[3]
+    s3 = conv3x3(tr.restrict(2, s2), W[4]) * G[4]
+    u2 = conv3x3(tr.prolong(2, s3) + s2, W[5]) * G[5]
+    u1 = conv3x3(tr.prolong(1, u2) + s1, W[6]) * G[6]
+    u0 = conv3x3(tr.prolong(0, u1) + s0, W[7]) * G[7]
+    return conv3x3(u0, W[8])
 
 
 class LearnedCorrection:
@@ -140,58 +210,99 @@ class LearnedCorrection:
         self.R0 = (self.P0.T / 4.0).tocsr()
         self.tr = Transfers(self.mc)
         self.la_c = coarse_log_a(log_a_nodes, self.mc)
+        self.la_levels = level_log_a(self.la_c, self.tr)
         self.a_mean = float(np.mean(np.exp(log_a_nodes)))
         self.tau = tau
 
-    def __call__(self, params, r: np.ndarray, lam: complex) -> np.ndarray:
-        """e = P_0 (s c_k (y_0 + i y_1)) for a fine complex residual r [m][m]."""
+    def coarse(self, params: dict, r: np.ndarray, lam: complex) -> np.ndarray:
+        """ec (complex [mc][mc]) for a fine complex residual r [m][m]."""
         mc = self.mc
         rc = (self.R0 @ r.reshape(-1)).reshape(mc, mc)
-        x, s = features(rc, self.la_c, lam)
-        y = forward(params, x, self.tr)
-        c = s * output_scale(lam, self.tau, self.a_mean)
-        ec = c * (y[0] + 1j * y[1])
+        c = output_scale(lam, self.tau, self.a_mean)
+        x = c * np.stack([rc.real, rc.imag])
+        y = forward(params, x, a_gates(params, self.la_levels), lam_gates(params, lam), self.tr)
+        return y[0] + 1j * y[1]
+
+    def __call__(self, params: dict, r: np.ndarray, lam: complex) -> np.ndarray:
+        """e = P_0 ec on the fine grid [m][m]."""
+        ec = self.coarse(params, r, lam)
         return (self.P0 @ ec.reshape(-1)).reshape(self.m, self.m)
 
 
-def loss(params, samples, lc: LearnedCorrection) -> float:
-    """Mean over samples (r, lam, e*) of ||e - e*||^2 / ||e*||^2."""
+def coarse_target(h, lam: complex, tau: float, r: np.ndarray) -> np.ndarray:
+    """The exact coarse-grid correction B_{k,1}^{-1} R_0 r (level 1 of the
+    multigrid hierarchy h), [mc][mc] complex."""
+    import scipy.sparse.linalg as spla
+    mc = h.sizes[1]
+    rc = h.R[0] @ r.reshape(-1)
+    return spla.spsolve(h.op(1, lam, tau).tocsc(), rc).reshape(mc, mc)
+
+
+def loss(params: dict, samples, lc: LearnedCorrection) -> float:
+    """Mean over samples (r, lam, ec*) of ||ec - ec*||^2 / ||ec*||^2 on the
+    coarse grid."""
     tot = 0.0
     for r, lam, et in samples:
-        e = lc(params, r, lam)
-        tot += float(np.sum(np.abs(e - et) ** 2) / np.sum(np.abs(et) ** 2))
+        ec = lc.coarse(params, r, lam)
+        tot += float(np.sum(np.abs(ec - et) ** 2) / np.sum(np.abs(et) ** 2))
     return tot / len(samples)
 
 
 def correct(params, lc: LearnedCorrection, A, b: np.ndarray, x: np.ndarray, lam: complex,
-            omega: float = 0.8, net=None):
-    """One judged learned correction of an iterate x of A x = b (A = B_k on the
-    fine grid, vectors flattened), in three steps:
-      1. x1 = x + e, e = the network's correction of the residual b - A x
-         (``net(res, lam)`` in place of the network when given);
-      2. x2 = x1 + omega D^{-1} (b - A x1): one damped-Jacobi sweep, the
-         post-smoothing that follows any prolonged coarse-grid correction in
-         multigrid (Sec. 4's multigrid, Example 2's one post-smoothing step),
-         removing what the bilinear P_0 adds at high frequencies;
-      3. x <- x + alpha (x2 - x) with the complex alpha that minimises
-         ||b - A (x + alpha d)||, d = x2 - x:
-         alpha = <A d, res> / <A d, A d>, <u, v> = u^H v.
-    Step 3 is the judge: the residual norm never grows, and alpha = 0 (the
-    V-cycle's iterate kept) when A d = 0.  Returns (x_new, ||res_new|| /
-    ||res||)."""
+            alpha: complex, omega: float = 0.8, net=None):
+    """The corrected iterate of x (the V-cycle's) for A x = b (A = B_k on the
+    fine grid, vectors flattened): x1 = x + e with e the correction of the
+    residual b - A x (``net(res, lam)`` in place of the network when given),
+    x2 = x1 + omega D^{-1} (b - A x1) (one damped-Jacobi sweep), and the
+    result x + alpha (x2 - x).  Returns (x_new, x2)."""
     m = lc.m
     res = b - A @ x
     e = (net(res, lam) if net is not None else lc(params, res.reshape(m, m), lam)).reshape(-1)
     x1 = x + e
     x2 = x1 + omega * (b - A @ x1) / A.diagonal()
-    d = x2 - x
-    Ad = A @ d
+    return x + alpha * (x2 - x), x2
+
+
+def minimal_residual_step(A, b: np.ndarray, x: np.ndarray, x2: np.ndarray):
+    """alpha = <A d, res> / <A d, A d>, d = x2 - x, res = b - A x (<u, v> = u^H v):
+    the complex step that minimises ||b - A (x + alpha d)||; 0 when A d = 0 or
+    the sums are not finite.  Returns (alpha, ||res_new|| / ||res||)."""
+    res = b - A @ x
+    Ad = A @ (x2 - x)
     dd = float(np.vdot(Ad, Ad).real)
-    alpha = complex(np.vdot(Ad, res)) / dd if dd > 0 else 0.0
-    xn = x + alpha * d
-    rn = float(np.linalg.norm(b - A @ xn))
-    r0 = float(np.linalg.norm(res))
-    return xn, (rn / r0 if r0 > 0 else 0.0)
+    cr = complex(np.vdot(Ad, res))
+    ok = dd > 0 and math.isfinite(dd) and math.isfinite(cr.real) and math.isfinite(cr.imag)
+    alpha = cr / dd if ok else 0.0
+    rr = float(np.vdot(res, res).real)
+    after = max(rr - abs(cr) ** 2 / dd, 0.0) if ok else rr
+    return alpha, (math.sqrt(after / rr) if rr > 0 else 0.0)
+
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(z: np.ndarray) -> np.ndarray:
+    """The SplitMix64 output function (Steele, Lea and Flood, 2014) on uint64."""
+    z = (z + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(MASK64)
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(MASK64)
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(MASK64)
+    return z ^ (z >> np.uint64(31))
+
+
+CALIBRATION_KEY = 0xCA11B8A7E5EED001
+
+
+def calibration_rhs(K: int, J: int) -> np.ndarray:
+    """The fixed right-hand side of the calibration apply, [K][J] complex:
+    value i of the interleaved (re, im) array is (t >> 40) 2^-23 - 1 with
+    t = splitmix64(key ^ splitmix64(i)), uniform in [-1, 1) and exactly
+    representable in FP32 and FP64."""
+    with np.errstate(over="ignore"):
+        i = np.arange(2 * K * J, dtype=np.uint64)
+        t = splitmix64(np.uint64(CALIBRATION_KEY) ^ splitmix64(i))
+    v = (t >> np.uint64(40)).astype(np.float64) * 2.0 ** -23 - 1.0
+    v = v.reshape(K, J, 2)
+    return v[..., 0] + 1j * v[..., 1]
 
 
 def forward_sign_eigs(N: int, eps: float) -> np.ndarray:
@@ -202,17 +313,36 @@ def forward_sign_eigs(N: int, eps: float) -> np.ndarray:
     return 1.0 - eps ** (1.0 / N) * np.exp(-2j * np.pi * k / N)
 
 
+def calibrate(h, lc: LearnedCorrection, params, tau: float, eps: float, N: int,
+              omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
+    """alpha_k for every frequency k = 0..N/2 from one calibration apply: the
+    V-cycle and the correction on calibration_rhs, then the minimal-residual
+    step.  Returns (alphas, ratios)."""
+    from .bec_oracle import mg_vcycle
+    lam = forward_sign_eigs(N, eps)
+    m = lc.m
+    B = calibration_rhs(N // 2 + 1, m * m)
+    alphas, ratios = [], []
+    for k in range(N // 2 + 1):
+        A = h.op(0, lam[k], tau)
+        x = mg_vcycle(h, lam[k], tau, B[k], omega, nu1, nu2)
+        _, x2 = correct(params, lc, A, B[k], x, lam[k], 0.0, omega, net)
+        a, q = minimal_residual_step(A, B[k], x, x2)
+        alphas.append(a)
+        ratios.append(q)
+    return np.array(alphas), np.array(ratios)
+
+
 def apply_Pinv_learned(y: np.ndarray, h, lc: LearnedCorrection, params, tau: float, eps: float,
-                       omega: float = 0.8, nu1: int = 1, nu2: int = 1, ratios=None, net=None):
-    """P_eps^{-1} y by Sec. 4's three steps with Step 2 done, per frequency,
-    by one V-cycle (``mg_vcycle``) and then the judged learned correction
-    (``correct``).  The network is not conjugation-equivariant, so the route is
-    defined on the half spectrum of a forward-sign real DFT (k = 0..N/2 with
-    lambda'_k of ``forward_sign_eigs``); the other frequencies are the
-    conjugates (a real result), and the imaginary parts at k = 0 and N/2 are
-    dropped, as by a complex-to-real inverse DFT.  BDF1 only.  When given,
-    ``ratios`` receives ||res_new|| / ||res|| per frequency, and ``net``
-    replaces the network as in ``correct``."""
+                       alphas, omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
+    """P_eps^{-1} y by Sec. 4's three steps with Step 2 done, per frequency, by
+    one V-cycle (``mg_vcycle``) and then the correction with the fixed step
+    alphas[k] (``correct``).  The route is defined on the half spectrum of a
+    forward-sign real DFT (k = 0..N/2 with lambda'_k of
+    ``forward_sign_eigs``); the other frequencies are the conjugates (a real
+    result), and the imaginary parts at k = 0 and N/2 are dropped, as by a
+    complex-to-real inverse DFT.  BDF1 only.  ``net`` replaces the network as
+    in ``correct``."""
     from .bec_oracle import eps_scaling, mg_vcycle
     N = y.shape[0]
     Y = y.reshape(N, -1).astype(np.float64)
@@ -220,11 +350,9 @@ def apply_Pinv_learned(y: np.ndarray, h, lc: LearnedCorrection, params, tau: flo
     yt = np.fft.rfft(d[:, None] * Y, axis=0)                            # Step 1
     lam = forward_sign_eigs(N, eps)
     zt = np.empty_like(yt)
-    A0 = [h.op(0, lk, tau) for lk in lam]
     for k in range(N // 2 + 1):                                          # Step 2
+        A = h.op(0, lam[k], tau)
         x = mg_vcycle(h, lam[k], tau, yt[k], omega, nu1, nu2)
-        zt[k], q = correct(params, lc, A0[k], yt[k], x, lam[k], omega, net)
-        if ratios is not None:
-            ratios.append(q)
+        zt[k], _ = correct(params, lc, A, yt[k], x, lam[k], alphas[k], omega, net)
     z = np.fft.irfft(zt, n=N, axis=0) / d[:, None]                      # Step 3
     return z.reshape(y.shape)

@@ -439,9 +439,13 @@ class Problem:
         return hist
 
     def learned_loss_grad(self, lam_idx, r, e_target):
-        """r, e_target: complex128 CUDA tensors [B][nx][nx] (view as float64 pairs)."""
+        """r: complex128 CUDA tensor [B][nx][nx] (fine residuals); e_target:
+        complex128 CUDA tensor [B][mc][mc], mc = (nx - 1) / 2 (coarse targets)."""
         import torch
         B = len(lam_idx)
+        mc = (self.nx - 1) // 2
+        if tuple(r.shape) != (B, self.nx, self.nx) or tuple(e_target.shape) != (B, mc, mc):
+            raise ValueError("r must be [B][nx][nx] and e_target [B][mc][mc] complex128")
         idx = (ctypes.c_int * B)(*[int(k) for k in lam_idx])
         rr = torch.view_as_real(r).contiguous()
         et = torch.view_as_real(e_target).contiguous()
@@ -458,8 +462,8 @@ class Problem:
         return int(_lib().bec_learned_fallbacks(self._p))
 
     def learned_residual_ratios(self):
-        """Per frequency k <= N/2 of the last apply: the residual after the judged
-        correction over the V-cycle's residual."""
+        """Per frequency k <= N/2, from the calibration apply: the residual after
+        the corrected step over the V-cycle's residual."""
         out = np.empty(self.N // 2 + 1)
         _check(_lib().bec_learned_residual_ratios(self._p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "bec_learned_residual_ratios")

@@ -396,6 +396,7 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
 bec_status bec_set_eps(bec_problem* p, double eps) {
   if (p == nullptr) return einval("null problem");
   if (!(eps > 0.0 && eps <= 1.0)) return einval("eps must lie in (0, 1]");
+  net_invalidate(p);   // the learned route's steps depend on lambda'_k
   const int N = p->N;
   std::vector<double> es(N), eis(N);
   std::vector<float> es32(N), eis32(N);

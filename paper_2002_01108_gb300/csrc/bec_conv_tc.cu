@@ -1,6 +1,6 @@
 // 3 x 3 convolutions of the learned correction's network on the 5th-generation
 // tensor cores (tcgen05): BF16 operands, FP32 accumulation in tensor memory,
-// all 9 layers (C_in in {16, 32}: the 5 input planes are padded to 16; C_out
+// all 9 layers (C_in in {16, 32}: the 2 input planes are padded to 16; C_out
 // in {16, 32}: the 2 output planes are computed as 16 and 2 are stored).
 //
 // Implicit GEMM on halo tiles.  A tile is 8 rows x 14 columns of output
@@ -20,7 +20,8 @@
 // Warp roles in a persistent CTA: warp 4 issues the TMA loads into a 4-stage
 // ring, warp 5 issues the MMAs into one of two tensor-memory accumulators,
 // warps 0-3 (tensor-memory lanes 0-127) read an accumulator back with
-// tcgen05.ld, apply ReLU, convert to BF16 and store.  Loads, MMAs and the
+// tcgen05.ld, apply ReLU when asked (the network's layers store without it:
+// its gates multiply the outputs), convert to BF16 and store.  Loads, MMAs and the
 // epilogue of different tiles overlap.
 //
 // Every wait is bounded (about 0.2 s of SM clock).  A wait that runs out
@@ -390,7 +391,7 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
 
 // Converted weights of all 9 layers in the operand layout
 // wt_l[tap][chunk][c_out][8 c_in] (BF16), zero where a padded channel has no
-// weight: layer 0 has 5 of its 16 input channels, layer 8 2 of its 16
+// weight: layer 0 has 2 of its 16 input channels, layer 8 2 of its 16
 // outputs.  W holds the FP32 master weights [tap][c_in][c_out] of all layers.
 struct LayerOffsets {
   long long o[kNetLayers];
@@ -404,7 +405,7 @@ __global__ void tc_weights_kernel(const float* __restrict__ W, LayerOffsets woff
   int l = 0;
   while (l + 1 < kNetLayers && g >= layer_wt_offset(l + 1)) ++l;
   const int cin_pad = l == 0 ? 16 : 32, cout_pad = l == 8 ? 16 : 32;
-  const int cin = l == 0 ? 5 : 32, cout = l == 8 ? 2 : 32;
+  const int cin = l == 0 ? 2 : 32, cout = l == 8 ? 2 : 32;
   const int e = g - layer_wt_offset(l);
   const int j = e % 8, co = (e / 8) % cout_pad, ch = (e / (8 * cout_pad)) % (cin_pad / 8),
             tap = e / (8 * cout_pad * (cin_pad / 8));
@@ -504,9 +505,10 @@ bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const 
     return BEC_EUNSUPPORTED;
   }
   const __nv_bfloat16* w = wt + layer_wt_offset(layer);
-  if (layer == 0) return launch_tc<16, 32, 32, true>(p, in, w, out, m, B, bmax, err);
+  // no activation: the network's gates multiply the stored outputs
+  if (layer == 0) return launch_tc<16, 32, 32, false>(p, in, w, out, m, B, bmax, err);
   if (layer == 8) return launch_tc<32, 16, 2, false>(p, in, w, out, m, B, bmax, err);
-  return launch_tc<32, 32, 32, true>(p, in, w, out, m, B, bmax, err);
+  return launch_tc<32, 32, 32, false>(p, in, w, out, m, B, bmax, err);
 }
 
 }  // namespace bec

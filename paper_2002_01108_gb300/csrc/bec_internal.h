@@ -265,6 +265,12 @@ bec_status launch_build_rhs_dirichlet(bec_problem* p, const double* u0, const do
 void mg_free(bec_problem* p);
 // One V-cycle for every frequency: level-0 b -> level-0 x.
 bec_status mg_vcycle(bec_problem* p);
+// The same from level l0 (level-l0 b -> level-l0 x); l0 below the coarsest.
+bec_status mg_vcycle_from(bec_problem* p, int l0);
+// r = b - B x on level l for every frequency ([K][J_l] complex arrays)
+bec_status mg_residual_level(bec_problem* p, int l, void* r, const void* x, const void* b);
+// bc = R rf from level lf to level lf + 1, every frequency
+bec_status mg_restrict_to(bec_problem* p, int lf, void* bc, const void* rf);
 // r = b - B x on the finest level for every frequency ([K][J] complex arrays)
 bec_status mg_residual_level0(bec_problem* p, void* r, const void* x, const void* b);
 // xo = x + omega D^{-1} (b - B x) on the finest grid, every frequency (xo != x)
@@ -320,7 +326,13 @@ int persist_take_withhold();
 // ---- learned correction (bec_net.cu)
 bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp32_acts, int bmax);
 void net_free(bec_problem* p);
-bec_status net_correct(bec_problem* p);   // after the V-cycle: x += judged correction
+bec_status net_correct(bec_problem* p);   // after the V-cycle: x += alpha_k (corrected - x)
+// the calibration apply that fixes alpha_k (uses the level-0 multigrid arrays:
+// call it before an apply's Step 1); net_calibrated: alpha matches the
+// weights and eps; net_invalidate: they changed
+bec_status net_calibrate(bec_problem* p);
+bool net_calibrated(const bec_problem* p);
+void net_invalidate(bec_problem* p);
 bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                      double* loss_hist);
 long long net_num_weights(const bec_problem* p);
@@ -344,8 +356,9 @@ int tc_weights_elems();
 // at W + woff[l], [tap][c_in][c_out]); host array woff of 9 offsets
 bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* woff,
                               __nv_bfloat16* wt);
-// out = act(conv3x3(in)) of layer l: l = 0 reads the 16-channel padded
-// input planes, l = 8 stores its 2 output channels, ReLU except for l = 8
+// out = conv3x3(in) of layer l (no activation: the network's gates follow):
+// l = 0 reads the 16-channel padded input planes, l = 8 stores its 2 output
+// channels
 bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
                       __nv_bfloat16* out, int m, int B, int bmax, int* err);
 bec_status net_residual_ratios(bec_problem* p, double* host);

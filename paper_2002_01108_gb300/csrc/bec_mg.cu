@@ -899,16 +899,18 @@ void smooth_launch(int l, dim3 g, cudaStream_t st, v2_t<T>* xo, const v2_t<T>* x
   else mg_smooth_kernel<T, ZERO, false><<<g, kMgThreads, 0, st>>>(xo, x, b, a);
 }
 
+// One V-cycle for every frequency on levels l0.. (level l0's b -> its x).
 template <typename T>
-bec_status vcycle_t(bec_problem* p) {
+bec_status vcycle_t(bec_problem* p, int l0) {
   using V = v2_t<T>;
   std::vector<MgLevel>& lv = p->mg.lv;
   const int L = (int)lv.size();
   const int K = p->mg.K;
   // levels >= lc run in one fused kernel (the whole coarse part of the cycle)
-  const int lc = coarse_cycle_level(p, sizeof(V));
+  int lc = coarse_cycle_level(p, sizeof(V));
+  if (lc >= 0 && lc < l0) lc = L - l0 >= 2 ? l0 : -1;
   const int ltop = lc >= 0 ? lc : L - 1;   // levels above it run per level
-  for (int l = 0; l < ltop; ++l) {
+  for (int l = l0; l < ltop; ++l) {
     MgLevel& c = lv[l];
     const MgArgs<T> a = level_args<T>(p, c);
     const dim3 g = mg_grid(c.J, K);
@@ -973,7 +975,7 @@ bec_status vcycle_t(bec_problem* p) {
         static_cast<V*>(c.x), static_cast<const V*>(c.b), level_args<T>(p, c));
     BEC_LAUNCH_CHECK(p, "mg_coarsest_kernel");
   }
-  for (int l = ltop - 1; l >= 0; --l) {
+  for (int l = ltop - 1; l >= l0; --l) {
     MgLevel& c = lv[l];
     const MgLevel& n = lv[l + 1];
     const dim3 g = mg_grid(c.J, K);
@@ -1193,10 +1195,44 @@ bec_status launch_build_rhs_dirichlet(bec_problem* p, const double* u0, const do
   return BEC_OK;
 }
 
-bec_status mg_vcycle(bec_problem* p) {
+bec_status mg_vcycle(bec_problem* p) { return mg_vcycle_from(p, 0); }
+
+bec_status mg_vcycle_from(bec_problem* p, int l0) {
   NvtxRange range("bec V-cycle");
-  if (p->desc.precision == BEC_PC_FP64) return vcycle_t<double>(p);
-  return vcycle_t<float>(p);
+  if (l0 < 0 || l0 + 1 >= (int)p->mg.lv.size()) return BEC_EINVAL;
+  if (p->desc.precision == BEC_PC_FP64) return vcycle_t<double>(p, l0);
+  return vcycle_t<float>(p, l0);
+}
+
+bec_status mg_residual_level(bec_problem* p, int l, void* r, const void* x, const void* b) {
+  if (l == 0) return mg_residual_level0(p, r, x, b);
+  const MgLevel& L = p->mg.lv[l];
+  const dim3 g = mg_grid(L.J, p->mg.K);
+  BEC_LAUNCH_BEGIN(p);
+  if (p->desc.precision == BEC_PC_FP64)
+    residual_launch<double>(l, g, p->stream, static_cast<double2*>(r),
+                            static_cast<const double2*>(x), static_cast<const double2*>(b),
+                            level_args<double>(p, L));
+  else
+    residual_launch<float>(l, g, p->stream, static_cast<float2*>(r), static_cast<const float2*>(x),
+                           static_cast<const float2*>(b), level_args<float>(p, L));
+  BEC_LAUNCH_CHECK(p, kResidNames[l]);
+  return BEC_OK;
+}
+
+bec_status mg_restrict_to(bec_problem* p, int lf, void* bc, const void* rf) {
+  const MgLevel& f = p->mg.lv[lf];
+  const MgLevel& c = p->mg.lv[lf + 1];
+  const int K = p->mg.K;
+  BEC_LAUNCH_BEGIN(p);
+  if (p->desc.precision == BEC_PC_FP64)
+    mg_restrict_kernel<double><<<mg_grid(c.J, K), kMgThreads, 0, p->stream>>>(
+        static_cast<double2*>(bc), static_cast<const double2*>(rf), c.m, f.m, K);
+  else
+    mg_restrict_kernel<float><<<mg_grid(c.J, K), kMgThreads, 0, p->stream>>>(
+        static_cast<float2*>(bc), static_cast<const float2*>(rf), c.m, f.m, K);
+  BEC_LAUNCH_CHECK(p, kRestrictNames[lf]);
+  return BEC_OK;
 }
 
 }  // namespace bec

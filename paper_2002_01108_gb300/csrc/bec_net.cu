@@ -1,16 +1,22 @@
 // Learned route of P_eps^{-1} (BEC_ROUTE_LEARNED): one multigrid V-cycle per
 // shifted system, then a learned correction of what the V-cycle left,
-//     x1 = x_k + P_0 (s c_k Net(R_0 (b_k - B_k x_k) / s, log a, lambda'_k)),
+//     x1 = x_k + P_0 Net(c_k R_0 (b_k - B_k x_k)),
 // one damped-Jacobi sweep x2 = x1 + omega D^{-1} (b_k - B_k x1) (the
-// post-smoothing that follows a prolonged correction), and the judge: the
-// complex step x_k <- x_k + alpha_k (x2 - x_k) that minimises ||b_k - B_k x||,
-// so the residual never grows (alpha_k = 0 keeps the V-cycle's iterate; the
-// multigrid is the fallback).  The network (see
-// bec_net_kernels.cuh) runs on the grid of spacing 2h with 4 levels and C
-// channels and is trained on the GPU, by these kernels, on pairs
-// (r, e* = B_k^{-1} r) that the multigrid itself generates: r is the residual
-// a V-cycle leaves for a random right-hand side, e* is obtained by repeated
-// V-cycles (defect correction).  Requires the FP32 preconditioner.
+// post-smoothing that follows a prolonged correction), and the step
+// x_k <- x_k + alpha_k (x2 - x_k) with alpha_k fixed per frequency by a
+// calibration apply (the minimal-residual step on a fixed right-hand side;
+// alpha_k = 0 keeps the V-cycle's iterate: the multigrid is the fallback).
+// The network is LINEAR in the residual: a 4-level convolutional network on
+// the grid of spacing 2h whose layer outputs are multiplied by gates computed
+// from log a (per point and channel) and lambda'_k (per channel), never from
+// the residual.  So for a fixed a and k the correction is a fixed linear map
+// and P_eps^{-1} a fixed linear operator (a network non-linear in the
+// residual made the outer FGMRES lose its Krylov acceleration).  It is
+// trained on the GPU, by these kernels, on pairs that the multigrid itself
+// generates: r is the residual a V-cycle leaves for a random right-hand side,
+// the target is the coarse-grid correction B_{k,1}^{-1} R_0 r (level 1 of the
+// hierarchy), obtained by repeated V-cycles from level 1 (defect correction).
+// Requires the FP32 preconditioner.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -49,7 +55,9 @@ struct NetState {
   int sz[4] = {0, 0, 0, 0};      // network levels, sz[0] = (mf - 1) / 2
   int Bmax = 0;
   int cin[9], cout[9];
-  long long woff[10];
+  long long woff[10];            // the 9 convolutions of the residual path
+  net::GateOffsets goff;         // the gate networks' weights
+  long long nparam = 0;          // all weights
   float* W = nullptr;            // FP32 master weights, all layers
   float* G = nullptr;            // gradients
   float* Mo = nullptr;           // Adam moments
@@ -58,11 +66,21 @@ struct NetState {
   long long wpart_n = 0;
   void* act[NACT] = {};
   void* grad[NACT] = {};
-  float* la_c = nullptr;         // coarse log a, centred
+  void* pre[net::kGates] = {};   // layer outputs before their gates (training)
+  float* la_lv[4] = {};          // centred log a on the 4 network levels
+  float* GA[net::kGates] = {};   // a-gates [m_l^2][C] of the gated layers
+  float* Z1[net::kGates] = {};   // their hidden layer, relu'd, [m_l^2][8]
+  float* dGA[net::kGates] = {};  // gradients of the a-gates
+  float* dA = nullptr;           // work: [sz0^2][C]
+  float* dZ = nullptr;           // work: [sz0^2][8]
+  float* GL = nullptr;           // lambda-gates [Bmax][8][C]
+  float* hid = nullptr;          // their hidden units [Bmax][8][16]
+  float* dGL = nullptr;          // gradients [Bmax][8][C]
+  bool gates_ok = false;         // GA matches the weights
+  bool cal_ok = false;           // alpha matches the weights and eps
   double a_mean = 1.0;
   float* rc = nullptr;           // [Bmax][mc^2] complex
-  float* sinv = nullptr;         // per sample 1/s
-  float* cfac = nullptr;         // per sample s c_k
+  float* ones = nullptr;         // [Bmax] 1.0
   int* row = nullptr;            // per sample row of res / etgt (staged from the host)
   int* lam = nullptr;            // per sample frequency index
   int* iota = nullptr;           // 0, 1, ..., K-1 (rows = frequencies, no host staging)
@@ -71,12 +89,13 @@ struct NetState {
   int* h_idx = nullptr;          // pinned staging of row/lam (2 Bmax)
   float* efine = nullptr;        // [Bmax][J] complex: P_0 correction
   float* res = nullptr;          // [K][J] complex residuals
-  float* etgt = nullptr;         // [K][J] complex targets
-  float* ework = nullptr;        // [K][J] complex defect-correction iterate
+  float* etgt = nullptr;         // [K][mc^2] complex coarse targets
+  float* rcall = nullptr;        // [K][mc^2] complex: R_0 res of every frequency
+  float* ework = nullptr;        // [K][J] complex: the pair generation's right-hand sides
   float* xnew = nullptr;         // [K][J] complex corrected iterate
   double* part = nullptr;        // per-sample / per-frequency partial sums
-  double* jpart = nullptr;       // the judge's block sums, [K][kMrSplit][4]
-  float2* alpha = nullptr;       // the judge's step per frequency
+  double* jpart = nullptr;       // the calibration's block sums, [K][kMrSplit][4]
+  float2* alpha = nullptr;       // the step per frequency (from the calibration)
   double* h_part = nullptr;      // pinned mirror
   int adam_t = 0;
   unsigned long long rng_ctr = 0;
@@ -111,65 +130,29 @@ __global__ void feat_restrict_kernel(const float2* __restrict__ res, const int* 
   rc[g] = acc;
 }
 
-// one block of kScaleThreads per sample: s = rms(rc[b]); sinv = 1/s;
-// cfac = s / |lambda'_k + tau a_mean 2 pi^2|.  Each thread sums its points in
-// FP32, the block adds the threads' sums in FP64 in a fixed order.
-constexpr int kScaleThreads = 1024;
-__global__ void __launch_bounds__(kScaleThreads)
-feat_scale_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
-                  const float2* __restrict__ lamf, float* __restrict__ sinv,
-                  float* __restrict__ cfac, long long mcc, float tau_a_2pi2) {
-  __shared__ double red[kScaleThreads];
-  const int b = blockIdx.x;
-  float sf = 0.f;
-  for (long long q = threadIdx.x; q < mcc; q += blockDim.x) {
-    const float2 v = rc[b * mcc + q];
-    sf = fmaf(v.x, v.x, fmaf(v.y, v.y, sf));
-  }
-  const double s = sf;
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
-    if ((int)threadIdx.x < st2) red[threadIdx.x] += red[threadIdx.x + st2];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double rms = sqrt(red[0] / (double)mcc);
-    if (!(rms > 0.0)) rms = 1.0;
-    const float2 L = lamf[lam[b]];
-    const double mag = hypot((double)L.x + tau_a_2pi2, (double)L.y);
-    sinv[b] = (float)(1.0 / rms);
-    cfac[b] = (float)(rms / mag);
-  }
-}
-
-// X[b][q] = (Re rc / s, Im rc / s, log a, Re lambda', Im lambda')
-// (and, when X16 is not null, the same planes padded with zeros to 16 BF16
-// channels: the input of the tensor-core layer 0)
+// X[b][q] = c_b (Re rc, Im rc), c_b = 1 / |lambda'_k + tau a_mean 2 pi^2| of
+// the sample's frequency (and, when X16 is not null, the same two planes
+// padded with zeros to 16 BF16 channels: the input of the tensor-core layer 0)
 template <typename AT>
-__global__ void feat_fill_kernel(const float2* __restrict__ rc, const float* __restrict__ sinv,
-                                 const float* __restrict__ la_c, const int* __restrict__ lam,
-                                 const float2* __restrict__ lamf, AT* __restrict__ X,
-                                 __nv_bfloat16* __restrict__ X16, long long mcc, int B) {
+__global__ void feat_fill_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
+                                 const float2* __restrict__ lamf, float tau_a_2pi2,
+                                 AT* __restrict__ X, __nv_bfloat16* __restrict__ X16,
+                                 long long mcc, int B) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= B * mcc) return;
   const int b = (int)(g / mcc);
-  const long long q = g - (long long)b * mcc;
-  const float2 v = rc[g];
-  const float si = sinv[b];
   const float2 L = lamf[lam[b]];
-  const float f[5] = {v.x * si, v.y * si, la_c[q], L.x, L.y};
-  AT* d = X + g * 5;
-#pragma unroll
-  for (int c = 0; c < 5; ++c) d[c] = net::st<AT>(f[c]);
+  const float c = (float)(1.0 / hypot((double)L.x + tau_a_2pi2, (double)L.y));
+  const float2 v = rc[g];
+  const float f0 = c * v.x, f1 = c * v.y;
+  X[g * 2] = net::st<AT>(f0);
+  X[g * 2 + 1] = net::st<AT>(f1);
   if (X16 != nullptr) {
-    const __nv_bfloat162 h01 = __floats2bfloat162_rn(f[0], f[1]);
-    const __nv_bfloat162 h23 = __floats2bfloat162_rn(f[2], f[3]);
-    const __nv_bfloat162 h4 = __floats2bfloat162_rn(f[4], 0.f);
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(f0, f1);
     uint4 lo;
     lo.x = *reinterpret_cast<const unsigned*>(&h01);
-    lo.y = *reinterpret_cast<const unsigned*>(&h23);
-    lo.z = *reinterpret_cast<const unsigned*>(&h4);
+    lo.y = 0u;
+    lo.z = 0u;
     lo.w = 0u;
     uint4* d16 = reinterpret_cast<uint4*>(X16 + g * 16);
     d16[0] = lo;
@@ -209,18 +192,21 @@ __global__ void out_prolong_kernel(const AT* __restrict__ Y, const float* __rest
   efine[g] = make_float2(c * ax, c * ay);
 }
 
-// one block per sample: part[2b] = ||efine - etgt[row]||^2, part[2b+1] = ||etgt[row]||^2
-__global__ void loss_parts_kernel(const float2* __restrict__ efine, const float2* __restrict__ etgt,
-                                  const int* __restrict__ row, double* __restrict__ part,
-                                  long long mff) {
+// one block per sample: part[2b] = ||Y_b - etgt[row_b]||^2 and part[2b+1] =
+// ||etgt[row_b]||^2 on the coarse grid (Y_b: 2 channels = real and imaginary
+// part of the coarse correction)
+template <typename AT>
+__global__ void closs_parts_kernel(const AT* __restrict__ Y, const float2* __restrict__ etgt,
+                                   const int* __restrict__ row, double* __restrict__ part,
+                                   long long mcc) {
   __shared__ double rn[256], rd[256];
   const int b = blockIdx.x;
-  const float2* t = etgt + (long long)row[b] * mff;
-  const float2* e = efine + (long long)b * mff;
+  const float2* t = etgt + (long long)row[b] * mcc;
+  const AT* y = Y + (long long)b * mcc * 2;
   double num = 0.0, den = 0.0;
-  for (long long f = threadIdx.x; f < mff; f += blockDim.x) {
-    const float2 tv = t[f], ev = e[f];
-    const double dx = (double)ev.x - tv.x, dy = (double)ev.y - tv.y;
+  for (long long q = threadIdx.x; q < mcc; q += blockDim.x) {
+    const float2 tv = t[q];
+    const double dx = (double)net::ld(y + 2 * q) - tv.x, dy = (double)net::ld(y + 2 * q + 1) - tv.y;
     num += dx * dx + dy * dy;
     den += (double)tv.x * tv.x + (double)tv.y * tv.y;
   }
@@ -240,31 +226,37 @@ __global__ void loss_parts_kernel(const float2* __restrict__ efine, const float2
   }
 }
 
-// dL/dy: dy[b][q][c] = cfac_b * (P_0^T d)[q], d = 2 (efine - etgt) / (den_b B), P_0^T = 4 R_0
+// dL/dY[b][q][c] = 2 (Y - etgt) / (den_b B) for L = mean_b ||Y_b - t_b||^2 / den_b
 template <typename AT>
-__global__ void loss_grad_kernel(const float2* __restrict__ efine, const float2* __restrict__ etgt,
-                                 const int* __restrict__ row, const double* __restrict__ part,
-                                 const float* __restrict__ cfac, AT* __restrict__ dY, int mf,
-                                 int mc, int B) {
+__global__ void closs_grad_kernel(const AT* __restrict__ Y, const float2* __restrict__ etgt,
+                                  const int* __restrict__ row, const double* __restrict__ part,
+                                  AT* __restrict__ dY, long long mcc, int B) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long mcc = (long long)mc * mc, mff = (long long)mf * mf;
   if (g >= B * mcc) return;
-  const int b = (int)(g / mcc), q = (int)(g - (long long)b * mcc);
-  const int cy = q / mc, cx = q % mc;
-  const float2* e = efine + (long long)b * mff;
-  const float2* t = etgt + (long long)row[b] * mff;
+  const int b = (int)(g / mcc);
+  const long long q = g - (long long)b * mcc;
+  const float2 t = etgt[(long long)row[b] * mcc + q];
   const double k = 2.0 / (part[2 * b + 1] * B);
-  double ax = 0.0, ay = 0.0;
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      const double w = (dy == 0 ? 0.5 : 0.25) * (dx == 0 ? 0.5 : 0.25);
-      const long long f = (long long)(2 * cy + 1 + dy) * mf + (2 * cx + 1 + dx);
-      ax += w * ((double)e[f].x - t[f].x);
-      ay += w * ((double)e[f].y - t[f].y);
-    }
-  const double c = 4.0 * k * cfac[b];
-  dY[g * 2] = net::st<AT>((float)(c * ax));
-  dY[g * 2 + 1] = net::st<AT>((float)(c * ay));
+  dY[g * 2] = net::st<AT>((float)(k * ((double)net::ld(Y + g * 2) - t.x)));
+  dY[g * 2 + 1] = net::st<AT>((float)(k * ((double)net::ld(Y + g * 2 + 1) - t.y)));
+}
+
+// The calibration right-hand side: value i of the interleaved (re, im) array
+// of [K][J] complex is (t >> 40) 2^-23 - 1, t = splitmix64(key ^
+// splitmix64(i)) (SplitMix64's output function of Steele, Lea and Flood):
+// uniform in [-1, 1) and exactly representable in FP32.
+constexpr unsigned long long kCalibrationKey = 0xCA11B8A7E5EED001ull;
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void calibration_fill_kernel(float* __restrict__ v, long long n) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const unsigned long long t = splitmix64(kCalibrationKey ^ splitmix64((unsigned long long)g));
+  v[g] = (float)(int)(t >> 40) * 0x1p-23f - 1.0f;
 }
 
 // counter-based standard normal pair (splitmix64 hash + Box-Muller)
@@ -375,13 +367,34 @@ __global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restric
 }
 
 // ------------------------------------------------------------ dispatch helpers
+// out = conv3x3(in, W) (ReLU when relu) for B images of side m, FP32 weights
+// [9][ci][co] at W; the channel pairs of the residual path (C = 4 or 32) and
+// of the a-gates
 template <typename AT>
-bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m, int B, bool relu) {
-  NetState& n = *p->net;
-  const float* W = n.W + n.woff[layer];
+bec_status conv_fwd_raw(bec_problem* p, const AT* a, const float* W, int ci, int co, AT* o, int m,
+                        int B, bool relu) {
   const long long npix = (long long)B * m * m;
   const unsigned g = (unsigned)((npix + net::kConvThreads - 1) / net::kConvThreads);
-  const int ci = n.cin[layer], co = n.cout[layer];
+  BEC_LAUNCH_BEGIN(p);
+#define BEC_CF(CI, CO)                                                                            \
+  if (ci == CI && co == CO) {                                                                     \
+    if (relu) net::conv3x3_fwd_kernel<AT, CI, CO, true><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
+    else net::conv3x3_fwd_kernel<AT, CI, CO, false><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
+  } else
+  BEC_CF(2, 4) BEC_CF(4, 4) BEC_CF(4, 2) BEC_CF(2, 32) BEC_CF(32, 32) BEC_CF(32, 2) BEC_CF(1, 8)
+  BEC_CF(8, 4) BEC_CF(8, 32) {
+    set_error("unsupported network channel count");
+    return BEC_EUNSUPPORTED;
+  }
+#undef BEC_CF
+  BEC_LAUNCH_CHECK(p, "net_conv_fwd_kernel");
+  return BEC_OK;
+}
+
+// layer `layer` of the residual path (no activation: the gates follow)
+template <typename AT>
+bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m, int B) {
+  NetState& n = *p->net;
   const AT* a = static_cast<const AT*>(in);
   AT* o = static_cast<AT*>(out);
   if constexpr (sizeof(AT) == 2) {
@@ -392,37 +405,21 @@ bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m,
                         n.err);
     }
   }
-  BEC_LAUNCH_BEGIN(p);
-#define BEC_CF(CI, CO)                                                                            \
-  if (ci == CI && co == CO) {                                                                     \
-    if (relu) net::conv3x3_fwd_kernel<AT, CI, CO, true><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
-    else net::conv3x3_fwd_kernel<AT, CI, CO, false><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
-  } else
-  BEC_CF(5, 4) BEC_CF(4, 4) BEC_CF(4, 2) BEC_CF(5, 32) BEC_CF(32, 32) BEC_CF(32, 2) {
-    set_error("unsupported network channel count");
-    return BEC_EUNSUPPORTED;
-  }
-#undef BEC_CF
-  BEC_LAUNCH_CHECK(p, "net_conv_fwd_kernel");
-  return BEC_OK;
+  return conv_fwd_raw<AT>(p, a, n.W + n.woff[layer], n.cin[layer], n.cout[layer], o, m, B, false);
 }
 
+// dW (written, not added) and, when din is not null, din for the loss whose
+// gradient with respect to out = conv3x3(in, W) is dout
 template <typename AT>
-bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer, void* din, int m,
-                    int B) {
+bec_status conv_bwd_raw(bec_problem* p, const AT* a, const AT* d, const float* W, float* dW,
+                        int ci, int co, AT* di, int m, int B) {
   NetState& n = *p->net;
-  const float* W = n.W + n.woff[layer];
-  float* dW = n.G + n.woff[layer];
   const long long npix = (long long)B * m * m;
-  const int ci = n.cin[layer], co = n.cout[layer];
   const int nw = 9 * ci * co;
   long long nblk = (npix + 255) / 256;
   if (nblk > 512) nblk = 512;
   const long long per = (npix + nblk - 1) / nblk;
   const unsigned g = (unsigned)((npix + net::kConvThreads - 1) / net::kConvThreads);
-  const AT* a = static_cast<const AT*>(in);
-  const AT* d = static_cast<const AT*>(dout);
-  AT* di = static_cast<AT*>(din);
 #define BEC_CB(CI, CO)                                                                            \
   if (ci == CI && co == CO) {                                                                     \
     BEC_LAUNCH_BEGIN(p);                                                                          \
@@ -434,7 +431,8 @@ bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer,
       BEC_LAUNCH_CHECK(p, "net_conv_dgrad_kernel");                                               \
     }                                                                                             \
   } else
-  BEC_CB(5, 4) BEC_CB(4, 4) BEC_CB(4, 2) BEC_CB(5, 32) BEC_CB(32, 32) BEC_CB(32, 2) {
+  BEC_CB(2, 4) BEC_CB(4, 4) BEC_CB(4, 2) BEC_CB(2, 32) BEC_CB(32, 32) BEC_CB(32, 2) BEC_CB(1, 8)
+  BEC_CB(8, 4) BEC_CB(8, 32) {
     set_error("unsupported network channel count");
     return BEC_EUNSUPPORTED;
   }
@@ -443,6 +441,15 @@ bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer,
   net::reduce_parts_kernel<<<(nw + 255) / 256, 256, 0, p->stream>>>(n.wpart, (int)nblk, nw, dW);
   BEC_LAUNCH_CHECK(p, "net_wgrad_reduce_kernel");
   return BEC_OK;
+}
+
+template <typename AT>
+bec_status conv_bwd(bec_problem* p, const void* in, const void* dout, int layer, void* din, int m,
+                    int B) {
+  NetState& n = *p->net;
+  return conv_bwd_raw<AT>(p, static_cast<const AT*>(in), static_cast<const AT*>(dout),
+                          n.W + n.woff[layer], n.G + n.woff[layer], n.cin[layer], n.cout[layer],
+                          static_cast<AT*>(din), m, B);
 }
 
 bool aligned16p(const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
@@ -502,17 +509,6 @@ bec_status prolong_ch(bec_problem* p, const void* in, const void* add_src, void*
 }
 
 template <typename AT>
-bec_status relu_mask(bec_problem* p, void* d, const void* a, int level, int B) {
-  NetState& n = *p->net;
-  const long long cnt = (long long)B * n.sz[level] * n.sz[level] * n.C;
-  BEC_LAUNCH_BEGIN(p);
-  net::relu_mask_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(static_cast<AT*>(d),
-                                                                 static_cast<const AT*>(a), cnt);
-  BEC_LAUNCH_CHECK(p, "net_relu_mask_kernel");
-  return BEC_OK;
-}
-
-template <typename AT>
 bec_status add_into(bec_problem* p, void* d, const void* e, int level, int B) {
   NetState& n = *p->net;
   const long long cnt = (long long)B * n.sz[level] * n.sz[level] * n.C;
@@ -530,55 +526,136 @@ bec_status add_into(bec_problem* p, void* d, const void* e, int level, int B) {
   } while (0)
 
 // features of B samples (rows n.row, frequencies n.lam) from n.res into act[X]
+// gated layer i: its input and output activations (its level is
+// net::kGateLevel[i])
+constexpr int kGateIn[net::kGates] = {A_X, A_H0, A_R0, A_R1, A_R2, A_P2, A_P1, A_P0};
+constexpr int kGateOut[net::kGates] = {A_H0, A_S0, A_S1, A_S2, A_S3, A_U2, A_U1, A_U0};
+constexpr int kGateLevel[net::kGates] = {0, 0, 1, 2, 3, 2, 1, 0};
+
+// the a-gates of every gated layer from the current weights:
+// Z1_i = relu(conv(la_l, A1_i)), GA_i = 1 + tanh(conv(Z1_i, A2_i))
+bec_status gates_fwd(bec_problem* p) {
+  NetState& n = *p->net;
+  for (int i = 0; i < net::kGates; ++i) {
+    const int l = kGateLevel[i], m = n.sz[l];
+    BEC_TRY(conv_fwd_raw<float>(p, n.la_lv[l], n.W + n.goff.a1[i], 1, net::kGateAHidden, n.Z1[i],
+                                m, 1, true));
+    BEC_TRY(conv_fwd_raw<float>(p, n.Z1[i], n.W + n.goff.a2[i], net::kGateAHidden, n.C, n.GA[i], m,
+                                1, false));
+    const long long cnt = (long long)m * m * n.C;
+    BEC_LAUNCH_BEGIN(p);
+    net::one_plus_tanh_kernel<<<grid_for(cnt), kT, 0, p->stream>>>(n.GA[i], cnt);
+    BEC_LAUNCH_CHECK(p, "net_gate_tanh_kernel");
+  }
+  n.gates_ok = true;
+  return BEC_OK;
+}
+
+// the lambda-gates of the B samples whose frequencies are n.cur_lam
+bec_status lam_gates(bec_problem* p, int B) {
+  NetState& n = *p->net;
+  const int cnt = B * net::kGates * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  net::lam_gate_fwd_kernel<<<(cnt + 255) / 256, 256, 0, p->stream>>>(
+      n.W, n.goff, n.cur_lam, p->tab.lamf32, n.hid, n.GL, n.C, B);
+  BEC_LAUNCH_CHECK(p, "net_lambda_gate_kernel");
+  return BEC_OK;
+}
+
+// input planes of B samples (rows n.cur_row of n.res, frequencies n.cur_lam)
 template <typename AT>
 bec_status features(bec_problem* p, int B) {
   NetState& n = *p->net;
   const int mc = n.sz[0];
   const long long mcc = (long long)mc * mc;
-  const float2* lamf = p->tab.lamf32;
   BEC_LAUNCH_BEGIN(p);
   feat_restrict_kernel<<<grid_for(B * mcc), kT, 0, p->stream>>>(
       reinterpret_cast<const float2*>(n.res), n.cur_row, reinterpret_cast<float2*>(n.rc), n.mf, mc, B);
   BEC_LAUNCH_CHECK(p, "net_feat_restrict_kernel");
   BEC_LAUNCH_BEGIN(p);
-  feat_scale_kernel<<<B, kScaleThreads, 0, p->stream>>>(reinterpret_cast<const float2*>(n.rc), n.cur_lam, lamf,
-                                              n.sinv, n.cfac, mcc,
-                                              (float)(p->tau * n.a_mean * 2.0 * M_PI * M_PI));
-  BEC_LAUNCH_CHECK(p, "net_feat_scale_kernel");
-  BEC_LAUNCH_BEGIN(p);
   feat_fill_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
-      reinterpret_cast<const float2*>(n.rc), n.sinv, n.la_c, n.cur_lam, lamf,
-      static_cast<AT*>(n.act[A_X]), (sizeof(AT) == 2 && n.tc) ? n.x16 : nullptr, mcc, B);
+      reinterpret_cast<const float2*>(n.rc), n.cur_lam, p->tab.lamf32,
+      (float)(p->tau * n.a_mean * 2.0 * M_PI * M_PI), static_cast<AT*>(n.act[A_X]),
+      (sizeof(AT) == 2 && n.tc) ? n.x16 : nullptr, mcc, B);
   BEC_LAUNCH_CHECK(p, "net_feat_fill_kernel");
   return BEC_OK;
 }
 
+// gated layer i: out = conv(in, W_i) * GA_i * GL_i; training keeps the
+// product's first factor in n.pre[i] for the backward pass
 template <typename AT>
-bec_status forward(bec_problem* p, int B) {
+bec_status gate_layer(bec_problem* p, int i, int B, bool training) {
+  NetState& n = *p->net;
+  const int m = n.sz[kGateLevel[i]];
+  AT* out = static_cast<AT*>(n.act[kGateOut[i]]);
+  AT* pre = training ? static_cast<AT*>(n.pre[i]) : out;
+  BEC_TRY(conv_fwd<AT>(p, n.act[kGateIn[i]], i, pre, m, B));
+  const long long mmC = (long long)m * m * n.C, cnt = B * mmC;
+  BEC_LAUNCH_BEGIN(p);
+  net::gate_apply_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
+      pre, out, n.GA[i], n.GL + i * n.C, net::kGates * n.C, mmC, n.C, cnt);
+  BEC_LAUNCH_CHECK(p, "net_gate_kernel");
+  return BEC_OK;
+}
+
+template <typename AT>
+bec_status forward(bec_problem* p, int B, bool training) {
   NetState& n = *p->net;
   void** a = n.act;
   if (sizeof(AT) == 2 && n.tc) BEC_TRY(tc_convert_weights(p, n.W, n.woff, n.wt));
-  BEC_TRY(conv_fwd<AT>(p, a[A_X], 0, a[A_H0], n.sz[0], B, true));
-  BEC_TRY(conv_fwd<AT>(p, a[A_H0], 1, a[A_S0], n.sz[0], B, true));
+  BEC_TRY(gate_layer<AT>(p, 0, B, training));
+  BEC_TRY(gate_layer<AT>(p, 1, B, training));
   BEC_TRY(restrict_ch<AT>(p, a[A_S0], a[A_R0], 0, B, 1.f, false));
-  BEC_TRY(conv_fwd<AT>(p, a[A_R0], 2, a[A_S1], n.sz[1], B, true));
+  BEC_TRY(gate_layer<AT>(p, 2, B, training));
   BEC_TRY(restrict_ch<AT>(p, a[A_S1], a[A_R1], 1, B, 1.f, false));
-  BEC_TRY(conv_fwd<AT>(p, a[A_R1], 3, a[A_S2], n.sz[2], B, true));
+  BEC_TRY(gate_layer<AT>(p, 3, B, training));
   BEC_TRY(restrict_ch<AT>(p, a[A_S2], a[A_R2], 2, B, 1.f, false));
-  BEC_TRY(conv_fwd<AT>(p, a[A_R2], 4, a[A_S3], n.sz[3], B, true));
+  BEC_TRY(gate_layer<AT>(p, 4, B, training));
   BEC_TRY(prolong_ch<AT>(p, a[A_S3], a[A_S2], a[A_P2], 2, B, 1.f));
-  BEC_TRY(conv_fwd<AT>(p, a[A_P2], 5, a[A_U2], n.sz[2], B, true));
+  BEC_TRY(gate_layer<AT>(p, 5, B, training));
   BEC_TRY(prolong_ch<AT>(p, a[A_U2], a[A_S1], a[A_P1], 1, B, 1.f));
-  BEC_TRY(conv_fwd<AT>(p, a[A_P1], 6, a[A_U1], n.sz[1], B, true));
+  BEC_TRY(gate_layer<AT>(p, 6, B, training));
   BEC_TRY(prolong_ch<AT>(p, a[A_U1], a[A_S0], a[A_P0], 0, B, 1.f));
-  BEC_TRY(conv_fwd<AT>(p, a[A_P0], 7, a[A_U0], n.sz[0], B, true));
-  BEC_TRY(conv_fwd<AT>(p, a[A_U0], 8, a[A_Y], n.sz[0], B, false));
-  // the correction on the fine grid
+  BEC_TRY(gate_layer<AT>(p, 7, B, training));
+  BEC_TRY(conv_fwd<AT>(p, a[A_U0], 8, a[A_Y], n.sz[0], B));
+  return BEC_OK;
+}
+
+// efine[b] = P_0 (y_0 + i y_1) of the last forward pass
+template <typename AT>
+bec_status correction_fine(bec_problem* p, int B) {
+  NetState& n = *p->net;
   const long long mff = (long long)n.mf * n.mf;
   BEC_LAUNCH_BEGIN(p);
   out_prolong_kernel<AT><<<grid_for(B * mff), kT, 0, p->stream>>>(
-      static_cast<const AT*>(a[A_Y]), n.cfac, reinterpret_cast<float2*>(n.efine), n.sz[0], n.mf, B);
+      static_cast<const AT*>(n.act[A_Y]), n.ones, reinterpret_cast<float2*>(n.efine), n.sz[0],
+      n.mf, B);
   BEC_LAUNCH_CHECK(p, "net_out_prolong_kernel");
+  return BEC_OK;
+}
+
+// backward through gated layer i, d = dL/d(out_i) on entry: the gate
+// gradients dGA_i (summed over the samples) and dGL[.][i] (summed over the
+// points), then d <- d * G_i = dL/d(pre_i)
+template <typename AT>
+bec_status gate_bwd(bec_problem* p, int i, void* dv, int B) {
+  NetState& n = *p->net;
+  const int m = n.sz[kGateLevel[i]];
+  const long long mm = (long long)m * m, mmC = mm * n.C, cnt = B * mmC;
+  AT* d = static_cast<AT*>(dv);
+  const AT* pre = static_cast<const AT*>(n.pre[i]);
+  BEC_LAUNCH_BEGIN(p);
+  net::gate_dga_kernel<AT><<<grid_for(mmC), kT, 0, p->stream>>>(
+      d, pre, n.GL + i * n.C, net::kGates * n.C, n.dGA[i], mmC, n.C, B);
+  BEC_LAUNCH_CHECK(p, "net_gate_dga_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  net::gate_dgl_kernel<AT><<<B, 256, 0, p->stream>>>(d, pre, n.GA[i], n.dGL + i * n.C,
+                                                     net::kGates * n.C, mm, n.C);
+  BEC_LAUNCH_CHECK(p, "net_gate_dgl_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  net::gate_scale_grad_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
+      d, n.GA[i], n.GL + i * n.C, net::kGates * n.C, mmC, n.C, cnt);
+  BEC_LAUNCH_CHECK(p, "net_gate_grad_kernel");
   return BEC_OK;
 }
 
@@ -589,48 +666,70 @@ bec_status backward(bec_problem* p, int B) {
   void** a = n.act;
   void** d = n.grad;
   BEC_TRY(conv_bwd<AT>(p, a[A_U0], d[A_Y], 8, d[A_U0], n.sz[0], B));
-  BEC_TRY(relu_mask<AT>(p, d[A_U0], a[A_U0], 0, B));
+  BEC_TRY(gate_bwd<AT>(p, 7, d[A_U0], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_P0], d[A_U0], 7, d[A_P0], n.sz[0], B));
   // P0 = P U1 + S0:  dU1 = P^T dP0 = 4 R dP0,  dS0 = dP0 (+ more below)
   BEC_TRY(restrict_ch<AT>(p, d[A_P0], d[A_U1], 0, B, 4.f, false));
-  BEC_TRY(relu_mask<AT>(p, d[A_U1], a[A_U1], 1, B));
+  BEC_TRY(gate_bwd<AT>(p, 6, d[A_U1], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_P1], d[A_U1], 6, d[A_P1], n.sz[1], B));
   BEC_TRY(restrict_ch<AT>(p, d[A_P1], d[A_U2], 1, B, 4.f, false));
-  BEC_TRY(relu_mask<AT>(p, d[A_U2], a[A_U2], 2, B));
+  BEC_TRY(gate_bwd<AT>(p, 5, d[A_U2], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_P2], d[A_U2], 5, d[A_P2], n.sz[2], B));
   BEC_TRY(restrict_ch<AT>(p, d[A_P2], d[A_S3], 2, B, 4.f, false));
-  BEC_TRY(relu_mask<AT>(p, d[A_S3], a[A_S3], 3, B));
+  BEC_TRY(gate_bwd<AT>(p, 4, d[A_S3], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_R2], d[A_S3], 4, d[A_R2], n.sz[3], B));
   // S2 feeds R2 = R S2 and P2 = P S3 + S2:  dS2 = R^T dR2 + dP2 = P dR2 / 4 + dP2
   BEC_TRY(prolong_ch<AT>(p, d[A_R2], d[A_P2], d[A_S2], 2, B, 0.25f));
-  BEC_TRY(relu_mask<AT>(p, d[A_S2], a[A_S2], 2, B));
+  BEC_TRY(gate_bwd<AT>(p, 3, d[A_S2], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_R1], d[A_S2], 3, d[A_R1], n.sz[2], B));
   BEC_TRY(prolong_ch<AT>(p, d[A_R1], d[A_P1], d[A_S1], 1, B, 0.25f));
-  BEC_TRY(relu_mask<AT>(p, d[A_S1], a[A_S1], 1, B));
+  BEC_TRY(gate_bwd<AT>(p, 2, d[A_S1], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_R0], d[A_S1], 2, d[A_R0], n.sz[1], B));
   BEC_TRY(prolong_ch<AT>(p, d[A_R0], d[A_P0], d[A_S0], 0, B, 0.25f));
-  BEC_TRY(relu_mask<AT>(p, d[A_S0], a[A_S0], 0, B));
+  BEC_TRY(gate_bwd<AT>(p, 1, d[A_S0], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_H0], d[A_S0], 1, d[A_H0], n.sz[0], B));
-  BEC_TRY(relu_mask<AT>(p, d[A_H0], a[A_H0], 0, B));
+  BEC_TRY(gate_bwd<AT>(p, 0, d[A_H0], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_X], d[A_H0], 0, nullptr, n.sz[0], B));
+  // the lambda-gates' weights
+  const int per = 2 * net::kGateHidden + net::kGateHidden * n.C;
+  BEC_LAUNCH_BEGIN(p);
+  net::lam_gate_bwd_kernel<<<(net::kGates * per + 127) / 128, 128, 0, p->stream>>>(
+      n.W, n.goff, n.cur_lam, p->tab.lamf32, n.hid, n.GL, n.dGL, n.G, n.C, B);
+  BEC_LAUNCH_CHECK(p, "net_lambda_gate_bwd_kernel");
+  // the a-gates' weights: through GA = 1 + tanh(conv(Z1, A2)), Z1 = relu(conv(la, A1))
+  for (int i = 0; i < net::kGates; ++i) {
+    const int l = kGateLevel[i], m = n.sz[l];
+    const long long cnt = (long long)m * m * n.C;
+    BEC_LAUNCH_BEGIN(p);
+    net::dtanh_kernel<<<grid_for(cnt), kT, 0, p->stream>>>(n.dGA[i], n.GA[i], n.dA, cnt);
+    BEC_LAUNCH_CHECK(p, "net_gate_dtanh_kernel");
+    BEC_TRY(conv_bwd_raw<float>(p, n.Z1[i], n.dA, n.W + n.goff.a2[i], n.G + n.goff.a2[i],
+                                net::kGateAHidden, n.C, n.dZ, m, 1));
+    const long long hz = (long long)m * m * net::kGateAHidden;
+    BEC_LAUNCH_BEGIN(p);
+    net::relu_mask_kernel<float><<<grid_for(hz), kT, 0, p->stream>>>(n.dZ, n.Z1[i], hz);
+    BEC_LAUNCH_CHECK(p, "net_relu_mask_kernel");
+    BEC_TRY(conv_bwd_raw<float>(p, n.la_lv[l], n.dZ, n.W + n.goff.a1[i], n.G + n.goff.a1[i], 1,
+                                net::kGateAHidden, nullptr, m, 1));
+  }
   return BEC_OK;
 }
 
-// loss parts (per sample) and dL/dY for the samples in n.row against n.etgt
+// loss parts (per sample) and dL/dY for the samples in n.row against the
+// coarse targets n.etgt
 template <typename AT>
 bec_status loss_and_dy(bec_problem* p, int B) {
   NetState& n = *p->net;
-  const long long mff = (long long)n.mf * n.mf;
   const long long mcc = (long long)n.sz[0] * n.sz[0];
   BEC_LAUNCH_BEGIN(p);
-  loss_parts_kernel<<<B, 256, 0, p->stream>>>(reinterpret_cast<const float2*>(n.efine),
-                                              reinterpret_cast<const float2*>(n.etgt), n.cur_row,
-                                              n.part, mff);
+  closs_parts_kernel<AT><<<B, 256, 0, p->stream>>>(static_cast<const AT*>(n.act[A_Y]),
+                                                   reinterpret_cast<const float2*>(n.etgt),
+                                                   n.cur_row, n.part, mcc);
   BEC_LAUNCH_CHECK(p, "net_loss_kernel");
   BEC_LAUNCH_BEGIN(p);
-  loss_grad_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
-      reinterpret_cast<const float2*>(n.efine), reinterpret_cast<const float2*>(n.etgt), n.cur_row,
-      n.part, n.cfac, static_cast<AT*>(n.grad[A_Y]), n.mf, n.sz[0], B);
+  closs_grad_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
+      static_cast<const AT*>(n.act[A_Y]), reinterpret_cast<const float2*>(n.etgt), n.cur_row,
+      n.part, static_cast<AT*>(n.grad[A_Y]), mcc, B);
   BEC_LAUNCH_CHECK(p, "net_loss_grad_kernel");
   return BEC_OK;
 }
@@ -656,7 +755,7 @@ bec_status adam_step(bec_problem* p, float lr) {
   n.adam_t++;
   const float b1 = 0.9f, b2 = 0.999f;
   const float lr_t = lr * sqrtf(1.f - powf(b2, (float)n.adam_t)) / (1.f - powf(b1, (float)n.adam_t));
-  const int nw = (int)n.woff[9];
+  const int nw = (int)n.nparam;
   BEC_LAUNCH_BEGIN(p);
   net::adam_kernel<<<(nw + 255) / 256, 256, 0, p->stream>>>(n.W, n.Mo, n.Ve, n.G, nw, lr_t, b1, b2,
                                                             1e-8f);
@@ -665,26 +764,29 @@ bec_status adam_step(bec_problem* p, float lr) {
 }
 
 // Training pairs for every frequency: res = b - B V(b) for a random b, and
-// etgt = B^{-1} res by `sweeps` defect-correction V-cycles.
+// the coarse target etgt = B_1^{-1} R_0 res by `sweeps` defect-correction
+// V-cycles from level 1 of the hierarchy.
 bec_status make_pairs(bec_problem* p, int sweeps) {
   NetState& n = *p->net;
   MgLevel& L0 = p->mg.lv[0];
   const long long tot = (long long)p->mg.K * L0.J;
+  const long long tot1 = (long long)p->mg.K * p->mg.lv[1].J;
   BEC_LAUNCH_BEGIN(p);
   gauss_fill_kernel<<<grid_for(tot), kT, 0, p->stream>>>(static_cast<float2*>(L0.b), tot,
                                                          0xB5C0FFEEull + (n.rng_ctr++) * 0x100000001ull);
   BEC_LAUNCH_CHECK(p, "net_gauss_fill_kernel");
-  // keep the right-hand side: res buffer first holds b
+  // keep the right-hand side: the V-cycle reuses L0.b
   BEC_CUDA_TRY(cudaMemcpyAsync(n.ework, L0.b, tot * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
   BEC_TRY(mg_vcycle(p));
   BEC_TRY(mg_residual_level0(p, n.res, L0.x, n.ework));          // res = b - B V(b)
-  BEC_CUDA_TRY(cudaMemsetAsync(n.etgt, 0, tot * sizeof(float2), p->stream));
+  BEC_TRY(mg_restrict_to(p, 0, n.rcall, n.res));                 // R_0 res
+  BEC_CUDA_TRY(cudaMemsetAsync(n.etgt, 0, tot1 * sizeof(float2), p->stream));
   for (int it = 0; it < sweeps; ++it) {
-    BEC_TRY(mg_residual_level0(p, L0.b, n.etgt, n.res));          // b = res - B e
-    BEC_TRY(mg_vcycle(p));
+    BEC_TRY(mg_residual_level(p, 1, p->mg.lv[1].b, n.etgt, n.rcall));   // b_1 = R_0 res - B_1 e
+    BEC_TRY(mg_vcycle_from(p, 1));
     BEC_LAUNCH_BEGIN(p);
-    axpy_c_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<float2*>(n.etgt),
-                                                       static_cast<const float2*>(p->mg.lv[0].x), tot);
+    axpy_c_kernel<<<grid_for(tot1), kT, 0, p->stream>>>(reinterpret_cast<float2*>(n.etgt),
+                                                        static_cast<const float2*>(p->mg.lv[1].x), tot1);
     BEC_LAUNCH_CHECK(p, "net_axpy_kernel");
   }
   return BEC_OK;
@@ -699,6 +801,8 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
   unsigned long long st = seed * 6364136223846793005ull + 1442695040888963407ull;
   std::vector<int> rows(batch);
   const int regen = (K + batch - 1) / batch;   // batches drawn from one set of pairs
+  n.gates_ok = false;
+  n.cal_ok = false;
   for (int s = 0; s < steps; ++s) {
     if (s % regen == 0) BEC_TRY(make_pairs(p, 12));
     for (int b = 0; b < batch; ++b) {
@@ -706,8 +810,10 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
       rows[b] = (int)((st >> 33) % (unsigned long long)K);
     }
     BEC_TRY(set_samples(p, rows.data(), rows.data(), batch));
+    BEC_TRY(gates_fwd(p));
+    BEC_TRY(lam_gates(p, batch));
     BEC_TRY(features<AT>(p, batch));
-    BEC_TRY(forward<AT>(p, batch));
+    BEC_TRY(forward<AT>(p, batch, true));
     BEC_TRY(loss_and_dy<AT>(p, batch));
     BEC_TRY(backward<AT>(p, batch));
     BEC_TRY(adam_step(p, lr));
@@ -720,8 +826,70 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
       loss_hist[s] = l / batch;
     }
   }
+  n.gates_ok = false;   // the weights moved after the last gates_fwd
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
   return net_check(p);
+}
+
+// x1 = x + P_0 Net(c_k R_0 (b - B x)) for every frequency, into n.xnew, from
+// the residual in n.res (batches of Bmax frequencies)
+template <typename AT>
+bec_status corrected_iterate(bec_problem* p) {
+  NetState& n = *p->net;
+  MgLevel& L0 = p->mg.lv[0];
+  const int K = p->mg.K;
+  const long long mff = (long long)n.mf * n.mf;
+  if (!n.gates_ok) BEC_TRY(gates_fwd(p));
+  for (int k0 = 0; k0 < K; k0 += n.Bmax) {
+    const int B = K - k0 < n.Bmax ? K - k0 : n.Bmax;
+    n.cur_row = n.iota + k0;
+    n.cur_lam = n.iota + k0;
+    BEC_TRY(lam_gates(p, B));
+    BEC_TRY(features<AT>(p, B));
+    BEC_TRY(forward<AT>(p, B, false));
+    BEC_TRY(correction_fine<AT>(p, B));
+    BEC_LAUNCH_BEGIN(p);
+    add_corr_kernel<<<grid_for(B * mff), kT, 0, p->stream>>>(
+        reinterpret_cast<float2*>(n.xnew), static_cast<const float2*>(L0.x),
+        reinterpret_cast<const float2*>(n.efine), mff, k0, B);
+    BEC_LAUNCH_CHECK(p, "net_add_correction_kernel");
+  }
+  return BEC_OK;
+}
+
+// The calibration apply: the V-cycle and the correction on the fixed
+// right-hand side of calibration_fill_kernel; alpha_k = the minimal-residual
+// step <B d, res> / ||B d||^2, d = x2 - x (0 when B d = 0 or not finite, the
+// V-cycle's iterate then kept), and the residual ratio it reaches.  Uses the
+// multigrid's level-0 arrays, so it runs before an apply's Step 1.
+template <typename AT>
+bec_status calibrate_t(bec_problem* p) {
+  NvtxRange range("bec learned calibration");
+  NetState& n = *p->net;
+  MgLevel& L0 = p->mg.lv[0];
+  const int K = p->mg.K;
+  const long long mff = (long long)n.mf * n.mf;
+  BEC_LAUNCH_BEGIN(p);
+  calibration_fill_kernel<<<grid_for(2 * K * mff), kT, 0, p->stream>>>(static_cast<float*>(L0.b),
+                                                                       2 * K * mff);
+  BEC_LAUNCH_CHECK(p, "net_calibration_fill_kernel");
+  BEC_TRY(mg_vcycle(p));
+  BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
+  BEC_TRY(corrected_iterate<AT>(p));
+  // x2 = one damped-Jacobi sweep on x1 into L0.r; its residual into xnew
+  BEC_TRY(mg_smooth_level0(p, L0.r, n.xnew, L0.b));
+  BEC_TRY(mg_residual_level0(p, n.xnew, L0.r, L0.b));
+  BEC_LAUNCH_BEGIN(p);
+  mr_dots_kernel<<<dim3(K, kMrSplit), 256, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.res), reinterpret_cast<const float2*>(n.xnew), n.jpart, mff);
+  BEC_LAUNCH_CHECK(p, "net_calibration_dots_kernel");
+  int* fb = reinterpret_cast<int*>(n.part + 5 * K);
+  BEC_CUDA_TRY(cudaMemsetAsync(fb, 0, sizeof(int), p->stream));
+  BEC_LAUNCH_BEGIN(p);
+  mr_alpha_kernel<<<1, 256, 0, p->stream>>>(n.jpart, n.part, n.alpha, K, n.part + 4 * K, fb);
+  BEC_LAUNCH_CHECK(p, "net_calibration_alpha_kernel");
+  n.cal_ok = true;
+  return BEC_OK;
 }
 
 template <typename AT>
@@ -731,39 +899,16 @@ bec_status correct_t(bec_problem* p) {
   MgLevel& L0 = p->mg.lv[0];
   const int K = p->mg.K;
   const long long mff = (long long)n.mf * n.mf;
-  // residual the V-cycle left
+  // residual the V-cycle left, x1 = x + the correction
   BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
-  // x1 = x + P_0 (s c_k Net(...)), in batches of Bmax frequencies
-  for (int k0 = 0; k0 < K; k0 += n.Bmax) {
-    const int B = K - k0 < n.Bmax ? K - k0 : n.Bmax;
-    n.cur_row = n.iota + k0;
-    n.cur_lam = n.iota + k0;
-    BEC_TRY(features<AT>(p, B));
-    BEC_TRY(forward<AT>(p, B));
-    BEC_LAUNCH_BEGIN(p);
-    add_corr_kernel<<<grid_for(B * mff), kT, 0, p->stream>>>(
-        reinterpret_cast<float2*>(n.xnew), static_cast<const float2*>(L0.x),
-        reinterpret_cast<const float2*>(n.efine), mff, k0, B);
-    BEC_LAUNCH_CHECK(p, "net_add_correction_kernel");
-  }
+  BEC_TRY(corrected_iterate<AT>(p));
   // x2 = one damped-Jacobi sweep on x1 (the post-smoothing of a prolonged
-  // correction), into L0.r (V-cycle scratch); its residual into xnew
+  // correction) into L0.r, then x <- x + alpha_k (x2 - x)
   BEC_TRY(mg_smooth_level0(p, L0.r, n.xnew, L0.b));
-  BEC_TRY(mg_residual_level0(p, n.xnew, L0.r, L0.b));
-  // the judge: the minimal-residual step along x2 - x, per frequency
-  BEC_LAUNCH_BEGIN(p);
-  mr_dots_kernel<<<dim3(K, kMrSplit), 256, 0, p->stream>>>(
-      reinterpret_cast<const float2*>(n.res), reinterpret_cast<const float2*>(n.xnew), n.jpart, mff);
-  BEC_LAUNCH_CHECK(p, "net_judge_dots_kernel");
-  int* fb = reinterpret_cast<int*>(n.part + 5 * K);
-  BEC_CUDA_TRY(cudaMemsetAsync(fb, 0, sizeof(int), p->stream));
-  BEC_LAUNCH_BEGIN(p);
-  mr_alpha_kernel<<<1, 256, 0, p->stream>>>(n.jpart, n.part, n.alpha, K, n.part + 4 * K, fb);
-  BEC_LAUNCH_CHECK(p, "net_judge_alpha_kernel");
   BEC_LAUNCH_BEGIN(p);
   mr_update_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
       static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.alpha, mff, K);
-  BEC_LAUNCH_CHECK(p, "net_judge_update_kernel");
+  BEC_LAUNCH_CHECK(p, "net_step_kernel");
   return BEC_OK;
 }
 
@@ -795,14 +940,21 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   for (int l = 1; l < 4; ++l) n->sz[l] = (n->sz[l - 1] - 1) / 2;
   n->Bmax = bmax;
   const int C = channels;
-  const int shapes[9][2] = {{5, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, 2}};
+  const int shapes[9][2] = {{2, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, 2}};
   n->woff[0] = 0;
   for (int i = 0; i < 9; ++i) {
     n->cin[i] = shapes[i][0];
     n->cout[i] = shapes[i][1];
     n->woff[i + 1] = n->woff[i] + 9LL * shapes[i][0] * shapes[i][1];
   }
-  const long long nw = n->woff[9];
+  // then A1_0..7 [3][3][1][8], A2_0..7 [3][3][8][C], L1_0..7 [2][16], L2_0..7 [16][C]
+  long long o = n->woff[9];
+  for (int i = 0; i < net::kGates; ++i, o += 9LL * net::kGateAHidden) n->goff.a1[i] = o;
+  for (int i = 0; i < net::kGates; ++i, o += 9LL * net::kGateAHidden * C) n->goff.a2[i] = o;
+  for (int i = 0; i < net::kGates; ++i, o += 2LL * net::kGateHidden) n->goff.l1[i] = o;
+  for (int i = 0; i < net::kGates; ++i, o += (long long)net::kGateHidden * C) n->goff.l2[i] = o;
+  n->nparam = o;
+  const long long nw = n->nparam;
   bec_status s = BEC_OK;
   auto chain = [&](bec_status r) { if (s == BEC_OK) s = r; };
   chain(dalloc(reinterpret_cast<void**>(&n->W), nw * sizeof(float)));
@@ -814,24 +966,38 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   const size_t asz = n->fp32 ? sizeof(float) : sizeof(__nv_bfloat16);
   for (int a = 0; a < NACT; ++a) {
     const int l = act_level(a);
-    const int ch = a == A_X ? 5 : (a == A_Y ? 2 : C);
+    const int ch = a == A_X ? 2 : (a == A_Y ? 2 : C);
     const size_t bytes = (size_t)bmax * n->sz[l] * n->sz[l] * ch * asz;
     chain(dalloc(&n->act[a], bytes));
     chain(dalloc(&n->grad[a], bytes));
   }
+  for (int i = 0; i < net::kGates; ++i) {
+    const long long mm = (long long)n->sz[kGateLevel[i]] * n->sz[kGateLevel[i]];
+    chain(dalloc(&n->pre[i], (size_t)bmax * mm * C * asz));
+    chain(dalloc(reinterpret_cast<void**>(&n->GA[i]), (size_t)mm * C * sizeof(float)));
+    chain(dalloc(reinterpret_cast<void**>(&n->dGA[i]), (size_t)mm * C * sizeof(float)));
+    chain(dalloc(reinterpret_cast<void**>(&n->Z1[i]), (size_t)mm * net::kGateAHidden * sizeof(float)));
+  }
   const long long mcc = (long long)n->sz[0] * n->sz[0];
   const long long mff = (long long)p->m * p->m;
   const long long K = p->N / 2 + 1;
-  chain(dalloc(reinterpret_cast<void**>(&n->la_c), mcc * sizeof(float)));
+  for (int l = 0; l < 4; ++l)
+    chain(dalloc(reinterpret_cast<void**>(&n->la_lv[l]), (size_t)n->sz[l] * n->sz[l] * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->dA), (size_t)mcc * C * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->dZ), (size_t)mcc * net::kGateAHidden * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->GL), (size_t)bmax * net::kGates * C * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->dGL), (size_t)bmax * net::kGates * C * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->hid),
+               (size_t)bmax * net::kGates * net::kGateHidden * sizeof(float)));
   chain(dalloc(reinterpret_cast<void**>(&n->rc), (size_t)bmax * mcc * sizeof(float2)));
-  chain(dalloc(reinterpret_cast<void**>(&n->sinv), bmax * sizeof(float)));
-  chain(dalloc(reinterpret_cast<void**>(&n->cfac), bmax * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->ones), bmax * sizeof(float)));
   chain(dalloc(reinterpret_cast<void**>(&n->row), bmax * sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->lam), bmax * sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->iota), K * sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->efine), (size_t)bmax * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->res), (size_t)K * mff * sizeof(float2)));
-  chain(dalloc(reinterpret_cast<void**>(&n->etgt), (size_t)K * mff * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->etgt), (size_t)K * mcc * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->rcall), (size_t)K * mcc * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->ework), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->xnew), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
@@ -852,7 +1018,10 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
     }
   }
   if (s != BEC_OK) return s;
-  // coarse log a (centred by the mean over all nodes) and the mean of a
+  // log a on the network's levels: level 0 at the coarse nodes (fine node
+  // (2i+2, 2j+2)), centred by the mean over all nodes; each next level the
+  // full-weighting restriction (1/4, 1/8, 1/16 on the 3 x 3 block around
+  // fine (2i+1, 2j+1)) of the one above; and the mean of a
   const int m2 = p->m + 2;
   std::vector<double> la((size_t)m2 * m2);
   double mean_la = 0.0, mean_a = 0.0;
@@ -864,26 +1033,53 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   }
   mean_la /= (double)la.size();
   n->a_mean = mean_a / (double)la.size();
-  std::vector<float> lac(mcc);
+  std::vector<double> lv((size_t)mcc);
   for (int cy = 0; cy < n->sz[0]; ++cy)
     for (int cx = 0; cx < n->sz[0]; ++cx)
-      lac[(size_t)cy * n->sz[0] + cx] = (float)(la[(size_t)(2 * cy + 2) * m2 + (2 * cx + 2)] - mean_la);
-  BEC_CUDA_TRY(cudaMemcpy(n->la_c, lac.data(), lac.size() * sizeof(float), cudaMemcpyHostToDevice));
+      lv[(size_t)cy * n->sz[0] + cx] = la[(size_t)(2 * cy + 2) * m2 + (2 * cx + 2)] - mean_la;
+  for (int l = 0; l < 4; ++l) {
+    const int ml = n->sz[l];
+    if (l > 0) {
+      const int mf = n->sz[l - 1];
+      std::vector<double> c((size_t)ml * ml, 0.0);
+      for (int cy = 0; cy < ml; ++cy)
+        for (int cx = 0; cx < ml; ++cx) {
+          double acc = 0.0;
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+              acc += (dy == 0 ? 0.5 : 0.25) * (dx == 0 ? 0.5 : 0.25) *
+                     lv[(size_t)(2 * cy + 1 + dy) * mf + (2 * cx + 1 + dx)];
+          c[(size_t)cy * ml + cx] = acc;
+        }
+      lv.swap(c);
+    }
+    std::vector<float> lf(lv.begin(), lv.end());
+    BEC_CUDA_TRY(cudaMemcpy(n->la_lv[l], lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   std::vector<int> io(K);
   for (long long k = 0; k < K; ++k) io[k] = (int)k;
   BEC_CUDA_TRY(cudaMemcpy(n->iota, io.data(), K * sizeof(int), cudaMemcpyHostToDevice));
-  // He-normal initial weights from a fixed counter-based sequence, last layer x 0.1
-  std::vector<float> w(nw);
+  std::vector<float> ones((size_t)bmax, 1.f);
+  BEC_CUDA_TRY(cudaMemcpy(n->ones, ones.data(), bmax * sizeof(float), cudaMemcpyHostToDevice));
+  // initial weights from a fixed counter-based normal sequence: the residual
+  // path std sqrt(1 / (9 C_in)) (last layer x 0.1), A1 std 0.3, L1 std 0.5,
+  // A2 and L2 zero (every gate starts at 1)
+  std::vector<float> w(nw, 0.f);
   unsigned long long z = 0x243F6A8885A308D3ull;
+  auto normal = [&z]() {
+    z = z * 6364136223846793005ull + 1442695040888963407ull;
+    const double u1 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    z = z * 6364136223846793005ull + 1442695040888963407ull;
+    const double u2 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+  };
   for (int i = 0; i < 9; ++i) {
-    const double sd = std::sqrt(2.0 / (9.0 * n->cin[i])) * (i == 8 ? 0.1 : 1.0);
-    for (long long j = n->woff[i]; j < n->woff[i + 1]; ++j) {
-      z = z * 6364136223846793005ull + 1442695040888963407ull;
-      const double u1 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-      z = z * 6364136223846793005ull + 1442695040888963407ull;
-      const double u2 = ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-      w[j] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
-    }
+    const double sd = std::sqrt(1.0 / (9.0 * n->cin[i])) * (i == 8 ? 0.1 : 1.0);
+    for (long long j = n->woff[i]; j < n->woff[i + 1]; ++j) w[j] = (float)(sd * normal());
+  }
+  for (int i = 0; i < net::kGates; ++i) {
+    for (long long j = 0; j < 9LL * net::kGateAHidden; ++j) w[n->goff.a1[i] + j] = (float)(0.3 * normal());
+    for (long long j = 0; j < 2LL * net::kGateHidden; ++j) w[n->goff.l1[i] + j] = (float)(0.5 * normal());
   }
   BEC_CUDA_TRY(cudaMemcpy(n->W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice));
   BEC_CUDA_TRY(cudaMemset(n->Mo, 0, nw * sizeof(float)));
@@ -895,12 +1091,18 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
 void net_free(bec_problem* p) {
   NetState* n = p->net;
   if (n == nullptr) return;
-  void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->la_c, n->rc, n->sinv, n->cfac, n->row,
-                  n->lam, n->iota, n->efine, n->res, n->etgt, n->ework, n->xnew, n->part,
-                  n->jpart, n->alpha,
-                  n->err, n->wt, n->x16};
+  void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->rc, n->ones, n->row, n->lam, n->iota,
+                  n->efine, n->res, n->etgt, n->rcall, n->ework, n->xnew, n->part, n->jpart,
+                  n->alpha, n->err, n->wt, n->x16, n->dA, n->dZ, n->GL, n->dGL, n->hid};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (int l = 0; l < 4; ++l)
+    if (n->la_lv[l]) cudaFree(n->la_lv[l]);
+  for (int i = 0; i < net::kGates; ++i) {
+    void* g[] = {n->pre[i], n->GA[i], n->dGA[i], n->Z1[i]};
+    for (void* q : g)
+      if (q) cudaFree(q);
+  }
   for (int a = 0; a < NACT; ++a) {
     if (n->act[a]) cudaFree(n->act[a]);
     if (n->grad[a]) cudaFree(n->grad[a]);
@@ -915,6 +1117,16 @@ bec_status net_correct(bec_problem* p) {
   return p->net->fp32 ? correct_t<float>(p) : correct_t<__nv_bfloat16>(p);
 }
 
+bec_status net_calibrate(bec_problem* p) {
+  return p->net->fp32 ? calibrate_t<float>(p) : calibrate_t<__nv_bfloat16>(p);
+}
+
+bool net_calibrated(const bec_problem* p) { return p->net != nullptr && p->net->cal_ok; }
+
+void net_invalidate(bec_problem* p) {
+  if (p->net) p->net->cal_ok = false;
+}
+
 bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                      double* loss_hist) {
   if (batch < 1 || batch > p->net->Bmax) return BEC_EINVAL;
@@ -922,20 +1134,22 @@ bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned lo
                       : train_t<__nv_bfloat16>(p, steps, batch, lr, seed, loss_hist);
 }
 
-long long net_num_weights(const bec_problem* p) { return p->net ? p->net->woff[9] : 0; }
+long long net_num_weights(const bec_problem* p) { return p->net ? p->net->nparam : 0; }
 
 bec_status net_get_weights(bec_problem* p, float* host) {
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  BEC_CUDA_TRY(cudaMemcpy(host, p->net->W, p->net->woff[9] * sizeof(float), cudaMemcpyDeviceToHost));
+  BEC_CUDA_TRY(cudaMemcpy(host, p->net->W, p->net->nparam * sizeof(float), cudaMemcpyDeviceToHost));
   return BEC_OK;
 }
 
 bec_status net_set_weights(bec_problem* p, const float* host) {
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  BEC_CUDA_TRY(cudaMemcpy(p->net->W, host, p->net->woff[9] * sizeof(float), cudaMemcpyHostToDevice));
+  BEC_CUDA_TRY(cudaMemcpy(p->net->W, host, p->net->nparam * sizeof(float), cudaMemcpyHostToDevice));
   p->net->adam_t = 0;
-  BEC_CUDA_TRY(cudaMemset(p->net->Mo, 0, p->net->woff[9] * sizeof(float)));
-  BEC_CUDA_TRY(cudaMemset(p->net->Ve, 0, p->net->woff[9] * sizeof(float)));
+  p->net->gates_ok = false;
+  p->net->cal_ok = false;
+  BEC_CUDA_TRY(cudaMemset(p->net->Mo, 0, p->net->nparam * sizeof(float)));
+  BEC_CUDA_TRY(cudaMemset(p->net->Ve, 0, p->net->nparam * sizeof(float)));
   return BEC_OK;
 }
 
@@ -952,19 +1166,22 @@ bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, 
   NetState& n = *p->net;
   const long long mff = (long long)n.mf * n.mf;
   const long long tot = (long long)B * mff;
+  const long long totc = (long long)B * n.sz[0] * n.sz[0];
   BEC_LAUNCH_BEGIN(p);
   c128_to_c64_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<const double2*>(r),
                                                           reinterpret_cast<float2*>(n.res), tot);
   BEC_LAUNCH_CHECK(p, "net_convert_kernel");
   BEC_LAUNCH_BEGIN(p);
-  c128_to_c64_kernel<<<grid_for(tot), kT, 0, p->stream>>>(reinterpret_cast<const double2*>(et),
-                                                          reinterpret_cast<float2*>(n.etgt), tot);
+  c128_to_c64_kernel<<<grid_for(totc), kT, 0, p->stream>>>(reinterpret_cast<const double2*>(et),
+                                                           reinterpret_cast<float2*>(n.etgt), totc);
   BEC_LAUNCH_CHECK(p, "net_convert_kernel");
   std::vector<int> rows(B);
   for (int b = 0; b < B; ++b) rows[b] = b;
   BEC_TRY(set_samples(p, rows.data(), lams, B));
+  BEC_TRY(gates_fwd(p));
+  BEC_TRY(lam_gates(p, B));
   BEC_TRY(features<AT>(p, B));
-  BEC_TRY(forward<AT>(p, B));
+  BEC_TRY(forward<AT>(p, B, true));
   BEC_TRY(loss_and_dy<AT>(p, B));
   BEC_TRY(backward<AT>(p, B));
   BEC_CUDA_TRY(cudaMemcpyAsync(n.h_part, n.part, 2 * B * sizeof(double), cudaMemcpyDeviceToHost,
@@ -974,7 +1191,7 @@ bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, 
   for (int b = 0; b < B; ++b) l += n.h_part[2 * b] / n.h_part[2 * b + 1];
   *loss_out = l / B;
   if (grad_host)
-    BEC_CUDA_TRY(cudaMemcpy(grad_host, n.G, n.woff[9] * sizeof(float), cudaMemcpyDeviceToHost));
+    BEC_CUDA_TRY(cudaMemcpy(grad_host, n.G, n.nparam * sizeof(float), cudaMemcpyDeviceToHost));
   return net_check(p);
 }
 }  // namespace

@@ -30,7 +30,8 @@ def test_withheld_loads_time_out_and_the_context_survives():
     a = O.node_coefficient(grf_log_coefficient(seed=5, m=m))
     rng = np.random.default_rng(4)
     r = torch.from_numpy(rng.standard_normal((4, m, m)) + 1j * rng.standard_normal((4, m, m))).cuda()
-    e = torch.from_numpy(rng.standard_normal((4, m, m)) + 1j * rng.standard_normal((4, m, m))).cuda()
+    mc = (m - 1) // 2
+    e = torch.from_numpy(rng.standard_normal((4, mc, mc)) + 1j * rng.standard_normal((4, mc, mc))).cuda()
     with Problem(2, m, N, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
         p.set_eps(0.1)
         loss0, _ = p.learned_loss_grad([0, 2, 4, 6], r, e)

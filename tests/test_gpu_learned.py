@@ -1,10 +1,13 @@
 """The learned correction on the GPU (through the C ABI) against the NumPy
-oracle of the same network: loss and weight gradients (checked by central
-finite differences of the oracle), the whole learned P_eps^{-1} (V-cycle,
-correction, smoothing sweep, minimal-residual judge) element by element,
-BF16 against FP32 activations, training by the GPU's own kernels, and what
-the trained correction gains over the multigrid preconditioner without it
-(the A/B test).
+oracle of the same network (oracle/learned_oracle.py): loss and weight
+gradients (checked by central finite differences of the oracle), the whole
+learned P_eps^{-1} (V-cycle, linear gated correction, smoothing sweep,
+calibrated step) element by element, BF16 against FP32 activations,
+training by the GPU's own kernels, and what the trained correction gains
+over the multigrid preconditioner without it (the A/B/C test).
+
+Weights are seeded in the tests (oracle.init_params) and set on the GPU; no
+oracle input is read back from the GPU.
 
 Tolerance of the P_eps^{-1} parity: the multigrid route's bound 16 u
 (log2(N n^2) + 8 L) / eps plus the network's 9 convolutions, each output a
@@ -30,20 +33,6 @@ def _built():
     build.build()
 
 
-def lam_prime(N, eps, k):
-    """The eigenvalue paired with the forward-sign FFT: 1 - eps^{1/N} e^{-2 pi i k / N}."""
-    return 1.0 - eps ** (1.0 / N) * np.exp(-2j * np.pi * k / N)
-
-
-def unflatten(w, C):
-    out, off = [], 0
-    for ci, co in LO.layer_shapes(C):
-        n = 9 * ci * co
-        out.append(w[off:off + n].astype(np.float64).reshape(3, 3, ci, co))
-        off += n
-    return out
-
-
 def small_problem(net_fp32, C=4, m=31, N=8, eps=0.1, seed=5):
     from paper_2002_01108_gb300 import Problem
     a = O.node_coefficient(grf_log_coefficient(seed=seed, m=m))
@@ -53,45 +42,66 @@ def small_problem(net_fp32, C=4, m=31, N=8, eps=0.1, seed=5):
     return p, a
 
 
+def seeded_weights(C, seed, gate_scale):
+    ps = LO.init_params(C, seed=seed, gate_scale=gate_scale)
+    return ps, LO.flatten(ps).astype(np.float32)
+
+
 def samples(m, B, seed):
+    """Fine residuals [B][m][m] and coarse targets [B][mc][mc], complex."""
     rng = np.random.default_rng(seed)
+    mc = (m - 1) // 2
     r = rng.standard_normal((B, m, m)) + 1j * rng.standard_normal((B, m, m))
-    e = rng.standard_normal((B, m, m)) + 1j * rng.standard_normal((B, m, m))
+    e = rng.standard_normal((B, mc, mc)) + 1j * rng.standard_normal((B, mc, mc))
     return r, e
 
 
+def test_weight_count_matches_the_oracle_layout():
+    p, _ = small_problem(True, 4)
+    with p:
+        assert p.learned_weights().size == LO.num_params(4)
+    p, _ = small_problem(False, 32, m=63, N=8)
+    with p:
+        assert p.learned_weights().size == LO.num_params(32)
+
+
 def test_loss_and_gradients_match_the_oracle():
+    """FP32 activations, C = 4, gates away from 1: the GPU's loss against the
+    oracle's, its gradient against central differences of the oracle's loss
+    along random directions and for single weights of the residual path and
+    of every kind of gate weight."""
     import torch
     m, N, eps, C = 31, 8, 0.1, 4
     p, a = small_problem(True, C, m, N, eps)
+    ps, w = seeded_weights(C, 40, 0.3)
+    w64 = w.astype(np.float64)
+    lam = LO.forward_sign_eigs(N, eps)
     with p:
-        w = p.learned_weights()
-        params = unflatten(w, C)
+        p.set_learned_weights(w)
         lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
         idx = [0, 2, 4]
         r, e = samples(m, 3, 7)
         loss_gpu, g = p.learned_loss_grad(idx, torch.from_numpy(r).cuda(), torch.from_numpy(e).cuda())
-        S = [(r[b], lam_prime(N, eps, idx[b]), e[b]) for b in range(3)]
-        loss_ref = LO.loss(params, S, lc)
-        assert abs(loss_gpu - loss_ref) <= 1e-4 * loss_ref
-        # directional derivatives along random directions, central differences in FP64
+        S = [(r[b], lam[idx[b]], e[b]) for b in range(3)]
+        L = lambda v: LO.loss(LO.unflatten(v, C), S, lc)
+        loss_ref = L(w64)
+        assert abs(loss_gpu - loss_ref) <= 1e-4 * loss_ref, (loss_gpu, loss_ref)
         rng = np.random.default_rng(8)
         h = 1e-4
         for _ in range(4):
             d = rng.standard_normal(w.size)
             d /= np.linalg.norm(d)
-            plus = LO.loss(unflatten(w + h * d, C), S, lc)
-            minus = LO.loss(unflatten(w - h * d, C), S, lc)
-            fd = (plus - minus) / (2 * h)
+            fd = (L(w64 + h * d) - L(w64 - h * d)) / (2 * h)
             assert abs(float(g @ d) - fd) <= 2e-3 * max(abs(fd), 1e-2 * np.linalg.norm(g)), (g @ d, fd)
-        # single weights of the first, a middle and the last layer
-        offs = np.cumsum([0] + [9 * ci * co for ci, co in LO.layer_shapes(C)])
-        for layer in (0, 4, 8):
-            j = int(offs[layer] + rng.integers(offs[layer + 1] - offs[layer]))
+        shapes = LO.param_shapes(C)
+        offs = np.cumsum([0] + [int(np.prod(s)) for s in shapes])
+        # conv 0, 4, 8; A1_2, A2_5, L1_1, L2_6
+        for t in (0, 4, 8, 9 + 2, 17 + 5, 25 + 1, 33 + 6):
+            j = int(offs[t] + rng.integers(offs[t + 1] - offs[t]))
             e_j = np.zeros(w.size)
             e_j[j] = 1.0
-            fd = (LO.loss(unflatten(w + h * e_j, C), S, lc) - LO.loss(unflatten(w - h * e_j, C), S, lc)) / (2 * h)
-            assert abs(g[j] - fd) <= 5e-3 * max(abs(fd), 1e-3 * np.abs(g).max()), (layer, g[j], fd)
+            fd = (L(w64 + h * e_j) - L(w64 - h * e_j)) / (2 * h)
+            assert abs(g[j] - fd) <= 5e-3 * max(abs(fd), 1e-3 * np.abs(g).max()), (t, g[j], fd)
 
 
 def _tol(eps, N, m, C):
@@ -100,18 +110,18 @@ def _tol(eps, N, m, C):
     return 16 * U32 * (math.log2(N * (m + 1) ** 2) + 8 * L + 9 * math.sqrt(9 * C)) / eps
 
 
-@pytest.mark.parametrize("m,N,eps,C,train", [(31, 8, 0.1, 4, 0), (63, 16, 0.0625, 32, 60),
-                                             (127, 4, 0.02, 32, 40)])
-def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, train):
-    """Untrained and trained weights (read back from the GPU) in the oracle's
-    learned P_eps^{-1}; FP32 activations."""
+@pytest.mark.parametrize("m,N,eps,C,gs", [(31, 8, 0.1, 4, 0.0), (63, 16, 0.0625, 32, 0.3),
+                                          (127, 4, 0.02, 32, 0.5)])
+def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, gs):
+    """Seeded weights (gates 1, then gates away from 1) in the oracle's
+    learned P_eps^{-1} with its own calibration; FP32 activations.  The
+    steps and residual ratios of the GPU's calibration match the oracle's."""
     import torch
     p, a = small_problem(True, C, m, N, eps)
+    ps, w = seeded_weights(C, 50 + m, gs)
     y = np.random.default_rng(30 + m).uniform(-1, 1, (N, m, m))
     with p:
-        if train:
-            p.learned_train(steps=train, batch=min(8, N // 2 + 1), lr=2e-3, seed=2)
-        w = p.learned_weights()
+        p.set_learned_weights(w)
         z = p.apply_Pinv(torch.from_numpy(y).cuda())
         torch.cuda.synchronize()
         z = z.cpu().numpy()
@@ -120,27 +130,25 @@ def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, train):
     K = O.fd_stiffness_varcoef(a)
     h = O.MGHierarchy(K, m)
     lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
-    rr = []
-    ref = LO.apply_Pinv_learned(y, h, lc, unflatten(w, C), 1.0 / N, eps, ratios=rr)
+    params = LO.unflatten(w.astype(np.float64), C)
+    alphas, rr = LO.calibrate(h, lc, params, 1.0 / N, eps, N)
+    ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alphas)
     err = float(np.max(np.abs(z - ref)) / np.max(np.abs(ref)))
     assert err <= _tol(eps, N, m, C), (err, _tol(eps, N, m, C))
-    assert np.all(ratios <= 1.0 + 1e-6)
     np.testing.assert_allclose(ratios, rr, atol=1e-3)
-    print(f"learned P^-1 parity m={m} N={N} C={C} train={train}: err {err:.2e}, ratios {np.round(ratios, 3)}")
+    print(f"learned P^-1 parity m={m} N={N} C={C} gates {gs}: err {err:.2e}, ratios {np.round(ratios, 3)}")
 
 
 def test_bf16_activations_track_fp32():
     import torch
     m, N, eps, C = 63, 16, 0.05, 32
     r, e = samples(m, 4, 9)
+    _, w = seeded_weights(C, 60, 0.3)
     losses = []
     for fp32 in (True, False):
         p, _ = small_problem(fp32, C, m, N, eps)
         with p:
-            if fp32:
-                w = p.learned_weights()
-            else:
-                p.set_learned_weights(w)
+            p.set_learned_weights(w)
             loss, g = p.learned_loss_grad([0, 3, 5, 8], torch.from_numpy(r).cuda(), torch.from_numpy(e).cuda())
             losses.append((loss, g))
     (l32, g32), (l16, g16) = losses
@@ -150,24 +158,25 @@ def test_bf16_activations_track_fp32():
 
 @pytest.mark.parametrize("m", [63, 127, 255])
 def test_bf16_tensor_core_network_matches_the_oracle(m):
-    """BF16 activations with C = 32 run the 32 -> 32 convolutions on grids of
-    side >= 16 on the tensor cores (tcgen05, BF16 operands and weights, FP32
-    accumulation).  Their correction, against the FP64 oracle network with the
-    same weights: the loss with e* = the oracle's correction is the squared
-    relative error.  Bound: each of the 9 layers rounds its inputs, weights
-    and outputs to BF16 (u = 2^-9), and the transfers add 3 more roundings of
-    the activations: 24 u relative, worst case."""
+    """BF16 activations with C = 32 run every convolution of the residual
+    path on the tensor cores (tcgen05, BF16 operands and weights, FP32
+    accumulation).  Their coarse correction, against the FP64 oracle network
+    with the same weights: the loss with e* = the oracle's correction is the
+    squared relative error.  Bound: each of the 9 layers rounds its inputs,
+    weights and outputs to BF16 (u = 2^-9), the gates and transfers add a few
+    more roundings of the activations: 24 u relative, worst case."""
     import torch
     N, eps, C = 16, 0.05, 32
     p, a = small_problem(False, C, m, N, eps)
     idx = [0, 3, 5, 8]
     r, _ = samples(m, 4, 11)
+    ps, w = seeded_weights(C, 70, 0.3)
+    lam = LO.forward_sign_eigs(N, eps)
     with p:
-        p.learned_train(steps=20, batch=4, lr=2e-3, seed=4)
-        w = p.learned_weights()
+        p.set_learned_weights(w)
         lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
-        params = unflatten(w, C)
-        e_ref = np.stack([lc(params, r[b], lam_prime(N, eps, idx[b])) for b in range(4)])
+        params = LO.unflatten(w.astype(np.float64), C)
+        e_ref = np.stack([lc.coarse(params, r[b], lam[idx[b]]) for b in range(4)])
         loss, _ = p.learned_loss_grad(idx, torch.from_numpy(r).cuda(), torch.from_numpy(e_ref).cuda())
     print(f"BF16 network m={m}: relative error {math.sqrt(loss):.2e}")
     assert math.sqrt(loss) <= 24 * 2.0 ** -9
@@ -177,21 +186,21 @@ def test_training_lowers_the_loss():
     m, N, eps = 63, 16, 0.05
     p, _ = small_problem(False, 32, m, N, eps)
     with p:
-        hist = p.learned_train(steps=120, batch=8, lr=2e-3, seed=1)
+        hist = p.learned_train(steps=200, batch=8, lr=2e-3, seed=1)
     assert np.all(np.isfinite(hist))
-    assert hist[-20:].mean() < 0.7 * hist[:5].mean(), (hist[:5], hist[-20:])
+    assert hist[-20:].mean() < 0.5 * hist[:5].mean(), (hist[:5], hist[-20:])
 
 
-def test_learned_route_reaches_the_solution_and_never_raises_the_inner_residual():
+TRAIN_STEPS = 1500
+
+
+def test_trained_correction_gains_over_the_vcycle():
     """A/B/C at 127^2 x 64 (a = exp(GRF)): FGMRES with the multigrid
-    preconditioner, with the learned route at zero weights (the V-cycle plus
-    the smoothing sweep and judged step alone) and with trained weights.
-    Every arm reaches the sequential stepping solution, and the judge never
-    lets a frequency's residual grow.  The iteration counts are measured and
-    printed, not asserted: the judged step depends on its input, so the
-    preconditioner is no longer linear, and FGMRES loses part of the Krylov
-    acceleration the fixed V-cycle gets (16 iterations for the V-cycle, 18
-    for both learned arms at 300 training steps)."""
+    preconditioner alone, with the learned route at zero weights (the
+    V-cycle, the smoothing sweep and the calibrated step, without a
+    correction) and with trained weights.  The trained correction must take
+    fewer FGMRES iterations than both; every arm reaches the sequential
+    stepping solution."""
     import torch
     from paper_2002_01108_gb300 import Problem
     m, N = 127, 64
@@ -210,28 +219,30 @@ def test_learned_route_reaches_the_solution_and_never_raises_the_inner_residual(
             if arm == "zero":
                 p.set_learned_weights(np.zeros(p.learned_weights().size, np.float32))
             if arm == "trained":
-                hist = p.learned_train(steps=300, batch=16, lr=2e-3, seed=3)
+                hist = p.learned_train(steps=TRAIN_STEPS, batch=16, lr=2e-3, seed=3)
                 print("training loss", hist[:3], hist[-3:])
-                assert hist[-30:].mean() < hist[:5].mean()
+                assert hist[-50:].mean() < 0.2 * hist[:5].mean()
             u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, flexible=True)
             torch.cuda.synchronize()
             err = float(np.linalg.norm(u.cpu().numpy() - u_ref) / np.linalg.norm(u_ref))
             extra = ()
             if route == "learned":
                 ratios = p.learned_residual_ratios()
-                assert np.all(ratios <= 1.0 + 1e-6), ratios
                 extra = (p.learned_fallbacks, float(np.mean(ratios)))
             res[arm] = (info["iters"], err, info["true_relres"]) + extra
-    print("A/B", res)
+    print("A/B/C", res)
     for arm, (it, err, rr, *_) in res.items():
         assert rr <= 1.01e-10 and err <= 1e-8, (arm, it, err, rr)
+    assert res["trained"][0] < res["mg"][0], res
+    assert res["trained"][0] < res["zero"][0], res
 
 
 def test_learned_route_at_the_workload_size():
     """The learned form at the size bench.py times: 255^2 x 256, a = exp(GRF),
-    eps = sqrt(tau)/2, 300 training steps: FGMRES(30) reaches RES 1e-8 (the
+    eps = sqrt(tau)/2, trained on the GPU: FGMRES(30) reaches RES 1e-8 (the
     benchmark's tolerance), and solved on to RES 1e-10 its solution equals
-    sequential stepping to 1e-8; no frequency's residual grows."""
+    sequential stepping to 1e-8.  Its iteration count against the V-cycle's
+    is printed."""
     import torch
     from paper_2002_01108_gb300 import Problem
     m, N = 255, 256
@@ -241,17 +252,18 @@ def test_learned_route_at_the_workload_size():
     f = O.build_rhs(case.u0, case.fsrc, case.tau)
     K = O.fd_stiffness_varcoef(a)
     u_ref = O.timestep_solve(f, sp.identity(K.shape[0], format="csr"), K, case.tau)
+    fd = torch.from_numpy(f).cuda()
+    with Problem(2, m, N, route="mg", precision="fp32", a_nodes=a, flexible=True) as p:
+        p.set_eps(eps)
+        _, info_mg = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
     with Problem(2, m, N, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
         p.set_eps(eps)
-        p.learned_train(steps=300, batch=16, lr=2e-3, seed=3)
-        fd = torch.from_numpy(f).cuda()
+        p.learned_train(steps=TRAIN_STEPS, batch=16, lr=2e-3, seed=3)
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
         assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8, info
+        print(f"255^2 x 256: V-cycle {info_mg['iters']} iterations, learned {info['iters']}")
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, maxit=400, flexible=True)
         torch.cuda.synchronize()
-        ratios = p.learned_residual_ratios()
     assert info["converged"] == 1 and info["true_relres"] <= 1.01e-10, info
-    assert np.all(ratios <= 1.0 + 1e-6)
-    # solved to RES 1e-10 through the FP64 outer FGMRES: the FP64 answer
     err = float(np.linalg.norm(u.cpu().numpy() - u_ref) / np.linalg.norm(u_ref))
     assert err <= 1e-8, err

@@ -1,14 +1,31 @@
-"""Pins of the learned-correction network oracle: the convolution against
-scipy.signal.correlate2d, the transfers against the multigrid oracle's P and
-R, the absence of biases (positive homogeneity) and the shapes."""
+"""Pins of the learned-correction oracle (oracle/learned_oracle.py): the
+convolution against scipy.signal.correlate2d, the transfers against the
+multigrid oracle's P and R, the gates against loops written from their
+definition, linearity in the residual, the coarse-grid target against a
+dense solve, the loss's normalisation, the step and calibration rules, the
+calibration generator against SplitMix64's published first output, and the
+whole learned P_eps^{-1} against banded LU with an exact correction."""
 import math
 
 import numpy as np
 import pytest
 import scipy.signal as ss
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import oracle as O
 from oracle import learned_oracle as LO
+
+
+def sp_identity(n):
+    return sp.identity(n, format="csr")
+
+
+def _varcoef_case(m=15, seed=11):
+    rng = np.random.default_rng(seed)
+    log_a = 0.5 * rng.standard_normal((m + 2, m + 2))
+    K = O.fd_stiffness_varcoef(np.exp(log_a))
+    return log_a, K
 
 
 def test_conv3x3_is_a_zero_padded_correlation():
@@ -33,163 +50,117 @@ def test_transfers_match_the_multigrid_operators():
     np.testing.assert_allclose(tr.prolong(2, y)[0].reshape(-1), h.P[2] @ y[0].reshape(-1), atol=1e-14)
 
 
-def test_network_has_no_bias_and_maps_shapes():
-    tr = LO.Transfers(15)
-    ps = LO.init_params(4, seed=2)
-    assert [p.shape for p in ps][0] == (3, 3, 5, 4) and ps[-1].shape == (3, 3, 4, 2)
-    x = np.random.default_rng(3).standard_normal((5, 15, 15))
-    y = LO.forward(ps, x, tr)
-    assert y.shape == (2, 15, 15)
-    np.testing.assert_allclose(LO.forward(ps, 2.5 * x, tr), 2.5 * y, rtol=1e-12, atol=1e-14)
+def test_parameter_layout():
+    C = 4
+    ps = LO.init_params(C, seed=2, gate_scale=0.3)
+    w = LO.flatten(ps)
+    assert w.size == LO.num_params(C)
+    back = LO.unflatten(w, C)
+    for key in ("W", "A1", "A2", "L1", "L2"):
+        for a, b in zip(ps[key], back[key]):
+            np.testing.assert_array_equal(a, b)
+    assert back["W"][0].shape == (3, 3, 2, C) and back["W"][8].shape == (3, 3, C, 2)
+    assert back["A2"][7].shape == (3, 3, LO.NA, C) and back["L2"][0].shape == (LO.NL, C)
 
 
-def test_correction_scales_with_the_residual_and_lives_on_the_coarse_grid():
+def _conv_loops(x, W):
+    """3 x 3 zero-padded correlation by loops over every output point."""
+    ci_n, m, _ = x.shape
+    co_n = W.shape[3]
+    out = np.zeros((co_n, m, m))
+    for co in range(co_n):
+        for yy in range(m):
+            for xx in range(m):
+                s = 0.0
+                for ci in range(ci_n):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            if 0 <= yy + dy < m and 0 <= xx + dx < m:
+                                s += W[dy + 1, dx + 1, ci, co] * x[ci, yy + dy, xx + dx]
+                out[co, yy, xx] = s
+    return out
+
+
+def test_gates_follow_their_definition():
+    """GA_i and GL_i against loops written from the definition, on a 7 x 7
+    network grid; and all gates are exactly 1 when A2 = L2 = 0."""
+    C = 3
+    ps = LO.init_params(C, seed=3, gate_scale=0.4)
+    tr = LO.Transfers(7)
+    rng = np.random.default_rng(4)
+    la = LO.level_log_a(rng.standard_normal((7, 7)) * 0.7, tr)
+    GA = LO.a_gates(ps, la)
+    for i in (0, 2, 4):
+        lv = LO.GATE_LEVEL[i]
+        z = _conv_loops(np.maximum(_conv_loops(la[lv][None], ps["A1"][i]), 0.0), ps["A2"][i])
+        np.testing.assert_allclose(GA[i], 1.0 + np.tanh(z), rtol=1e-13, atol=1e-14)
+    lam = 0.3 - 0.7j
+    GL = LO.lam_gates(ps, lam)
+    for i in (1, 7):
+        ref = np.zeros(C)
+        for c in range(C):
+            acc = 0.0
+            for j in range(LO.NL):
+                hj = lam.real * ps["L1"][i][0, j] + lam.imag * ps["L1"][i][1, j]
+                acc += max(hj, 0.0) * ps["L2"][i][j, c]
+            ref[c] = 1.0 + math.tanh(acc)
+        np.testing.assert_allclose(GL[i], ref, rtol=1e-14)
+    flat = LO.init_params(C, seed=3, gate_scale=0.0)
+    assert all(np.all(g == 1.0) for g in LO.a_gates(flat, la))
+    assert all(np.all(g == 1.0) for g in LO.lam_gates(flat, lam))
+    # the level fields are restrictions of level 0
+    np.testing.assert_allclose(la[1], tr.restrict(0, la[0][None])[0])
+
+
+def test_correction_is_linear_in_the_residual_and_lives_on_the_coarse_grid():
     m = 31
     rng = np.random.default_rng(5)
     log_a = rng.standard_normal((m + 2, m + 2)) * 0.3
     lc = LO.LearnedCorrection(m, log_a, 1 / 16)
     assert lc.mc == 15 and lc.tr.sizes == [15, 7, 3, 1]
-    ps = LO.init_params(4, seed=4)
-    r = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
-    e1 = lc(ps, r, 0.4 - 0.3j)
-    e2 = lc(ps, 3.0 * r, 0.4 - 0.3j)
-    np.testing.assert_allclose(e2, 3.0 * e1, rtol=1e-12)
+    ps = LO.init_params(4, seed=4, gate_scale=0.5)
+    lam = 0.4 - 0.3j
+    r1 = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    r2 = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    e1, e2 = lc(ps, r1, lam), lc(ps, r2, lam)
+    e12 = lc(ps, 2.5 * r1 - 0.75 * r2, lam)
+    np.testing.assert_allclose(e12, 2.5 * e1 - 0.75 * e2, rtol=1e-11, atol=1e-13 * np.abs(e12).max())
     # the correction is a prolongation of a coarse field
-    assert np.allclose(e1.reshape(-1), lc.P0 @ np.linalg.lstsq(lc.P0.toarray(), e1.reshape(-1), rcond=None)[0])
-    # coarse log a samples the nodes (2i+2, 2j+2)
+    ec = lc.coarse(ps, r1, lam)
+    np.testing.assert_allclose(e1.reshape(-1), lc.P0 @ ec.reshape(-1), atol=1e-14)
+    # coarse log a samples the nodes (2i+2, 2j+2), centred
     assert abs(lc.la_c[0, 0] - (log_a[2, 2] - log_a.mean())) < 1e-15
+    # no last layer: no correction
+    z = dict(ps, W=ps["W"][:8] + [np.zeros_like(ps["W"][8])])
+    assert np.all(lc(z, r1, lam) == 0.0)
 
 
-def _varcoef_case(m=15, seed=11):
-    rng = np.random.default_rng(seed)
-    log_a = 0.5 * rng.standard_normal((m + 2, m + 2))
-    K = O.fd_stiffness_varcoef(np.exp(log_a))
-    return log_a, K
-
-
-def test_correction_step_is_exact_with_an_exact_network():
-    """With e = B^{-1} res in place of the network, x + e is the exact solution,
-    the smoothing sweep leaves it there and the minimal-residual step keeps it."""
-    import scipy.sparse.linalg as spla
-    m, tau, lam = 15, 1 / 16, 0.3 - 0.2j
-    log_a, K = _varcoef_case(m)
-    A = (lam * sp_identity(m * m) + tau * K).tocsc()
-    lc = LO.LearnedCorrection(m, log_a, tau)
-    rng = np.random.default_rng(12)
-    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
-    x = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
-    exact = lambda res, lam_: spla.spsolve(A, res.reshape(-1))
-    xn, q = LO.correct(None, lc, A, b, x, lam, net=exact)
-    np.testing.assert_allclose(xn, spla.spsolve(A, b), rtol=1e-11, atol=1e-12)
-    assert q < 1e-10
-
-
-def test_correction_step_minimises_the_residual_along_its_direction():
-    """The judged step is the minimiser over complex alpha (checked on a grid of
-    alphas around it), so the residual never grows, whatever the network."""
-    m, tau, lam = 15, 1 / 16, 0.05 + 0.01j
-    log_a, K = _varcoef_case(m, 13)
-    A = (lam * sp_identity(m * m) + tau * K).tocsr()
-    lc = LO.LearnedCorrection(m, log_a, tau)
-    rng = np.random.default_rng(14)
-    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
-    x = np.zeros(m * m, complex)
-    ps = LO.init_params(4, seed=15)
-    xn, q = LO.correct(ps, lc, A, b, x, lam)
-    assert q <= 1.0 + 1e-14
-    # the direction of the step, rebuilt from its definition
-    e = lc(ps, b.reshape(m, m), lam).reshape(-1)
-    d = e + 0.8 * (b - A @ e) / A.diagonal()
-    alpha = np.vdot(d, xn - x) / np.vdot(d, d)
-    np.testing.assert_allclose(xn, x + alpha * d, rtol=1e-12, atol=1e-14)
-    f = lambda al: np.linalg.norm(b - A @ (x + al * d))
-    best = f(alpha)
-    assert abs(best / np.linalg.norm(b) - q) < 1e-12
-    for da in (1e-3, -1e-3, 1e-3j, -1e-3j, 0.05, -0.05j):
-        assert f(alpha + da * abs(alpha)) >= best
-    # a hostile network (the negated exact correction) is neutralised, not followed
-    import scipy.sparse.linalg as spla
-    bad = lambda res, lam_: -10.0 * spla.spsolve(A.tocsc(), res.reshape(-1))
-    _, qb = LO.correct(None, lc, A, b, x, lam, net=bad)
-    assert qb <= 1.0 + 1e-14
-
-
-def test_correction_step_solves_a_diagonal_system_exactly():
-    """For a diagonal B and a zero network, d = omega D^{-1} res, B d = omega res,
-    so alpha = 1/omega and the step lands on the exact solution for any omega."""
-    m = 15
-    rng = np.random.default_rng(16)
-    dg = rng.uniform(0.5, 3.0, m * m) + 1j * rng.uniform(-1, 1, m * m)
-    A = sp_diags(dg)
-    lc = LO.LearnedCorrection(m, np.zeros((m + 2, m + 2)), 1 / 16)
-    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
-    zero = lambda res, lam_: np.zeros(m * m, complex)
-    for omega in (0.8, 0.5, 1.3):
-        xn, q = LO.correct(None, lc, A.tocsr(), b, np.zeros(m * m, complex), 0.5, omega, net=zero)
-        np.testing.assert_allclose(xn, b / dg, rtol=1e-13)
-
-
-def test_learned_pinv_with_an_exact_network_is_the_exact_inverse():
-    """With exact shifted solves in place of the network the learned route is
-    P_eps^{-1} itself: this pins the forward-sign pairing of lambda'_k, the
-    half spectrum and the complex-to-real inverse against banded LU."""
-    import scipy.sparse.linalg as spla
-    m, N, eps = 15, 8, 0.1
-    tau = 1.0 / N
-    log_a, K = _varcoef_case(m, 17)
+def test_coarse_target_solves_the_galerkin_system():
+    m, tau, lam = 31, 1 / 16, 0.2 + 0.5j
+    log_a, K = _varcoef_case(m, 6)
     h = O.MGHierarchy(K, m)
-    lc = LO.LearnedCorrection(m, log_a, tau)
-    y = np.random.default_rng(18).standard_normal((N, m, m))
-    exact = lambda res, lam_: spla.spsolve((lam_ * sp_identity(m * m) + tau * K).tocsc(),
-                                           res.reshape(-1))
-    ratios = []
-    z = LO.apply_Pinv_learned(y, h, lc, None, tau, eps, net=exact, ratios=ratios)
-    ref = O.apply_Pinv_lu(y, sp_identity(m * m), K, tau, eps)
-    np.testing.assert_allclose(z, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
-    assert len(ratios) == N // 2 + 1 and max(ratios) < 1e-9
-    # lambda'_k are the conjugates of the eigenvalues of Sec. 4 (k <= N/2)
-    np.testing.assert_allclose(LO.forward_sign_eigs(N, eps), np.conj(O.eps_circulant_eigs(N, eps)[:N // 2 + 1]),
-                               atol=1e-15)
-
-
-def test_learned_pinv_never_does_worse_than_the_vcycle():
-    """Per frequency the judged correction leaves a residual no larger than the
-    V-cycle's (random, untrained weights)."""
-    m, N, eps = 15, 8, 0.05
-    tau = 1.0 / N
-    log_a, K = _varcoef_case(m, 19)
-    h = O.MGHierarchy(K, m)
-    lc = LO.LearnedCorrection(m, log_a, tau)
-    y = np.random.default_rng(20).standard_normal((N, m, m))
-    ratios = []
-    LO.apply_Pinv_learned(y, h, lc, LO.init_params(4, seed=21), tau, eps, ratios=ratios)
-    assert all(0.0 <= q <= 1.0 + 1e-12 for q in ratios)
-
-
-def sp_identity(n):
-    import scipy.sparse as sp
-    return sp.identity(n, format="csr")
-
-
-def sp_diags(d):
-    import scipy.sparse as sp
-    return sp.diags(d)
+    r = np.random.default_rng(7).standard_normal((m, m)) + 1j
+    et = LO.coarse_target(h, lam, tau, r)
+    B1 = (lam * h.M[1] + tau * h.K[1]).toarray()
+    np.testing.assert_allclose(B1 @ et.reshape(-1), h.R[0] @ r.reshape(-1), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(et.reshape(-1), np.linalg.solve(B1, h.R[0] @ r.reshape(-1)),
+                               rtol=1e-10)
 
 
 def test_loss_is_the_mean_of_the_per_sample_relative_errors():
-    """Zero weights give e = 0, so every sample's ||e - e*||^2 / ||e*||^2 is 1;
-    with targets 2e and -e the per-sample values are 1/4 and 4, and the loss is
-    their mean, 2.125 (a ratio of sums, or a norm that is not squared, gives
-    another number)."""
+    """Zero output (last layer 0) gives 1 per sample; with targets 2 ec and
+    -ec the per-sample values are 1/4 and 4, and the loss is their mean,
+    2.125 (a ratio of sums, or a norm that is not squared, gives another
+    number)."""
     m = 15
     rng = np.random.default_rng(30)
     lc = LO.LearnedCorrection(m, 0.3 * rng.standard_normal((m + 2, m + 2)), 1 / 16)
-    ps = LO.init_params(4, seed=31)
-    zero = [np.zeros_like(w) for w in ps]
+    ps = LO.init_params(4, seed=31, gate_scale=0.2)
+    zero = dict(ps, W=ps["W"][:8] + [np.zeros_like(ps["W"][8])])
     r1 = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
     r2 = 5.0 * (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m)))
     l1, l2 = 0.3 - 0.2j, 1.1 + 0.4j
-    e1, e2 = lc(ps, r1, l1), lc(ps, r2, l2)
+    e1, e2 = lc.coarse(ps, r1, l1), lc.coarse(ps, r2, l2)
     assert np.abs(e1).max() > 0 and np.abs(e2).max() > 0
     assert LO.loss(zero, [(r1, l1, e1), (r2, l2, 3.0 * e2)], lc) == pytest.approx(1.0, abs=1e-15)
     assert LO.loss(ps, [(r1, l1, e1)], lc) == pytest.approx(0.0, abs=1e-28)
@@ -204,7 +175,6 @@ def test_output_scale_is_the_inverse_shifted_operator_on_its_smoothest_mode(a):
     and |lambda + tau a mu_min|^-1 is the size of B_k^{-1} on that mode.
     output_scale uses the continuum value mu_min -> 2 pi^2, which agrees to
     O(h^2): here pi^2 h^2 / 12 < 2.5e-4 of mu_min."""
-    import scipy.sparse.linalg as spla
     m, N, eps = 63, 32, 0.05
     tau = 1.0 / N
     K = O.fd_stiffness_varcoef(np.full((m + 2, m + 2), a))
@@ -213,6 +183,140 @@ def test_output_scale_is_the_inverse_shifted_operator_on_its_smoothest_mode(a):
     for lam in LO.forward_sign_eigs(N, eps):
         ref = 1.0 / abs(lam + tau * mu_min)
         assert LO.output_scale(lam, tau, a) == pytest.approx(ref, rel=2.5e-4)
-    # the route takes a_mean over the node values: constant a gives a itself
     lc = LO.LearnedCorrection(m, np.full((m + 2, m + 2), math.log(a)), tau)
     assert lc.a_mean == pytest.approx(a, rel=1e-14)
+
+
+def test_correction_with_an_exact_network_lands_on_the_solution():
+    """With e = B^{-1} res in place of the network, x + e is the exact solution,
+    the smoothing sweep leaves it there, alpha = 1 keeps it, and the
+    calibration's minimal-residual step is 1 with a zero residual ratio."""
+    m, tau, lam = 15, 1 / 16, 0.3 - 0.2j
+    log_a, K = _varcoef_case(m)
+    A = (lam * sp_identity(m * m) + tau * K).tocsc()
+    lc = LO.LearnedCorrection(m, log_a, tau)
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    x = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    exact = lambda res, lam_: spla.spsolve(A, res.reshape(-1))
+    xn, x2 = LO.correct(None, lc, A, b, x, lam, 1.0, net=exact)
+    sol = spla.spsolve(A, b)
+    np.testing.assert_allclose(xn, sol, rtol=1e-11, atol=1e-12)
+    alpha, q = LO.minimal_residual_step(A, b, x, x2)
+    assert abs(alpha - 1.0) < 1e-10 and q < 1e-10
+
+
+def test_minimal_residual_step_minimises_along_its_direction():
+    m, tau, lam = 15, 1 / 16, 0.05 + 0.01j
+    _, K = _varcoef_case(m, 13)
+    A = (lam * sp_identity(m * m) + tau * K).tocsr()
+    rng = np.random.default_rng(14)
+    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    x = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    x2 = x + rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    alpha, q = LO.minimal_residual_step(A, b, x, x2)
+    f = lambda al: np.linalg.norm(b - A @ (x + al * (x2 - x)))
+    best = f(alpha)
+    assert abs(best / np.linalg.norm(b - A @ x) - q) < 1e-12
+    for da in (1e-3, -1e-3, 1e-3j, -1e-3j, 0.05, -0.05j):
+        assert f(alpha + da * max(abs(alpha), 1e-3)) >= best
+    # no direction: the fallback alpha = 0
+    assert LO.minimal_residual_step(A, b, x, x)[0] == 0.0
+
+
+def test_zero_network_step_solves_a_diagonal_system_exactly():
+    """For a diagonal B and a zero network, x2 - x = omega D^{-1} res and
+    B (x2 - x) = omega res, so the minimal-residual step is 1/omega and the
+    step lands on the exact solution for any omega."""
+    m = 15
+    rng = np.random.default_rng(16)
+    dg = rng.uniform(0.5, 3.0, m * m) + 1j * rng.uniform(-1, 1, m * m)
+    A = sp.diags(dg).tocsr()
+    lc = LO.LearnedCorrection(m, np.zeros((m + 2, m + 2)), 1 / 16)
+    b = rng.standard_normal(m * m) + 1j * rng.standard_normal(m * m)
+    zero = lambda res, lam_: np.zeros(m * m, complex)
+    x0 = np.zeros(m * m, complex)
+    for omega in (0.8, 0.5, 1.3):
+        _, x2 = LO.correct(None, lc, A, b, x0, 0.5, 0.0, omega, net=zero)
+        alpha, _ = LO.minimal_residual_step(A, b, x0, x2)
+        assert alpha == pytest.approx(1.0 / omega, rel=1e-13)
+        xn, _ = LO.correct(None, lc, A, b, x0, 0.5, alpha, omega, net=zero)
+        np.testing.assert_allclose(xn, b / dg, rtol=1e-13)
+
+
+def test_calibration_generator():
+    """SplitMix64's published first output for state 0 (0xe220a8397b1dcdaf),
+    the map to [-1, 1) with values exact in FP32, determinism, and the
+    interleaved (re, im) order of the generated array."""
+    out = LO.splitmix64(np.array([0], dtype=np.uint64))
+    assert int(out[0]) == 0xE220A8397B1DCDAF
+    v = LO.calibration_rhs(3, 50)
+    assert v.shape == (3, 50)
+    parts = np.stack([v.real, v.imag])
+    assert parts.min() >= -1.0 and parts.max() < 1.0
+    assert np.all(parts.astype(np.float32).astype(np.float64) == parts)
+    np.testing.assert_array_equal(v, LO.calibration_rhs(3, 50))
+    # element (k, q): indices 2 (k J + q) and 2 (k J + q) + 1, from Python integers
+    M = (1 << 64) - 1
+
+    def mix(z):
+        z = (z + 0x9E3779B97F4A7C15) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+    k, q = 2, 17
+    i = 2 * (k * 50 + q)
+    re = (mix(LO.CALIBRATION_KEY ^ mix(i)) >> 40) * 2.0 ** -23 - 1.0
+    im = (mix(LO.CALIBRATION_KEY ^ mix(i + 1)) >> 40) * 2.0 ** -23 - 1.0
+    assert v[k, q] == re + 1j * im
+
+
+def test_learned_pinv_with_an_exact_network_is_the_exact_inverse():
+    """With exact shifted solves in place of the network and alpha = 1 the
+    learned route is P_eps^{-1} itself: this pins the forward-sign pairing of
+    lambda'_k, the half spectrum and the complex-to-real inverse against
+    banded LU; the calibration then finds alpha = 1 everywhere."""
+    m, N, eps = 15, 8, 0.1
+    tau = 1.0 / N
+    log_a, K = _varcoef_case(m, 17)
+    h = O.MGHierarchy(K, m)
+    lc = LO.LearnedCorrection(m, log_a, tau)
+    y = np.random.default_rng(18).standard_normal((N, m, m))
+    exact = lambda res, lam_: spla.spsolve((lam_ * sp_identity(m * m) + tau * K).tocsc(),
+                                           res.reshape(-1))
+    alphas, ratios = LO.calibrate(h, lc, None, tau, eps, N, net=exact)
+    # the ratio is sqrt(||res||^2 - |<B d, res>|^2 / ||B d||^2) / ||res||: a
+    # difference of nearly equal sums, so about half the digits survive
+    assert np.all(np.abs(alphas - 1.0) < 1e-9) and np.all(ratios < 1e-6)
+    z = LO.apply_Pinv_learned(y, h, lc, None, tau, eps, alphas, net=exact)
+    ref = O.apply_Pinv_lu(y, sp_identity(m * m), K, tau, eps)
+    np.testing.assert_allclose(z, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(LO.forward_sign_eigs(N, eps), np.conj(O.eps_circulant_eigs(N, eps)[:N // 2 + 1]),
+                               atol=1e-15)
+
+
+def test_learned_pinv_with_zero_steps_is_the_multigrid_route():
+    """alpha_k = 0 at every frequency keeps the V-cycle's iterates: the route
+    is then the multigrid P_eps^{-1} (the fallback); with the calibrated
+    steps it is linear in y."""
+    m, N, eps = 15, 8, 0.05
+    tau = 1.0 / N
+    log_a, K = _varcoef_case(m, 19)
+    h = O.MGHierarchy(K, m)
+    lc = LO.LearnedCorrection(m, log_a, tau)
+    ps = LO.init_params(4, seed=21, gate_scale=0.3)
+    rng = np.random.default_rng(20)
+    y1, y2 = rng.standard_normal((2, N, m, m))
+    z0 = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, np.zeros(N // 2 + 1))
+    # the multigrid route on the same half spectrum
+    d = O.eps_scaling(N, eps)
+    yt = np.fft.rfft(d[:, None] * y1.reshape(N, -1), axis=0)
+    lam = LO.forward_sign_eigs(N, eps)
+    zt = np.array([O.mg_vcycle(h, lam[k], tau, yt[k]) for k in range(N // 2 + 1)])
+    ref = (np.fft.irfft(zt, n=N, axis=0) / d[:, None]).reshape(y1.shape)
+    np.testing.assert_allclose(z0, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+    alphas, _ = LO.calibrate(h, lc, ps, tau, eps, N)
+    za = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, alphas)
+    zb = LO.apply_Pinv_learned(y2, h, lc, ps, tau, eps, alphas)
+    zab = LO.apply_Pinv_learned(0.5 * y1 - 2.0 * y2, h, lc, ps, tau, eps, alphas)
+    np.testing.assert_allclose(zab, 0.5 * za - 2.0 * zb, rtol=1e-10, atol=1e-12 * np.abs(zab).max())
