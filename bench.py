@@ -108,22 +108,26 @@ def net_fwd_flops(m: int) -> float:
 # the kernel and the bench reports null.  The writes are what left L2 while
 # the kernel ran.
 KERNEL_SOURCES = {
-    "dst_rows_kernel": ("bec_dst.cu", "bec_fft.cuh", "bec_internal.h"),
-    "dst_cols_kernel": ("bec_dst.cu", "bec_fft.cuh", "bec_internal.h"),
-    "time_pass_kernel": ("bec_time.cu", "bec_fft.cuh", "bec_internal.h"),
-    "stencil_dots_kernel": ("bec_krylov.cu", "bec_internal.h"),
-    "combine_kernel": ("bec_krylov.cu", "bec_internal.h"),
+    "dst_rows_kernel": ("bec_dst.cu", "bec_passes.cuh", "bec_fft.cuh"),
+    "dst_cols_kernel": ("bec_dst.cu", "bec_passes.cuh", "bec_fft.cuh"),
+    "time_pass_kernel": ("bec_time.cu", "bec_passes.cuh", "bec_fft.cuh"),
 }
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): (133210368 + 80974336, "2732a5622277ca4d"),
-    ("dst_cols_kernel", "fp64"): (133284608 + 76462336, "2732a5622277ca4d"),
-    ("time_pass_kernel", "fp64"): (200689664 + 78113536, "0411d9da891aba72"),
+    ("dst_rows_kernel", "fp64"): (133212928 + 80690944, "ac42ee24b80dc569"),
+    ("dst_cols_kernel", "fp64"): (133255680 + 73828608, "ac42ee24b80dc569"),
+    ("time_pass_kernel", "fp64"): (200413952 + 75095552, "4f4748d01d7ca262"),
+    ("dst_rows_kernel", "fp32"): (133223168 + 31759872, "ac42ee24b80dc569"),
+    ("dst_cols_kernel", "fp32"): (66602496 + 7979008, "ac42ee24b80dc569"),
+    ("time_pass_kernel", "fp32"): (66641408 + 7933696, "4f4748d01d7ca262"),
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
 NCU_PINV_BYTES = {
-    "fp64": ((133210368 + 80974336) + (133284608 + 76462336) + (200689664 + 78113536)
-             + (133210112 + 76756480) + (133237248 + 73658368),
-             ("2732a5622277ca4d", "0411d9da891aba72")),
+    "fp64": ((133212928 + 80690944) + (133255680 + 73828608) + (200413952 + 75095552)
+             + (133209856 + 73769728) + (133210112 + 70222592),
+             ("ac42ee24b80dc569", "4f4748d01d7ca262")),
+    "fp32": ((133223168 + 31759872) + (66602496 + 7979008) + (66641408 + 7933696)
+             + (66602496 + 7978752) + (66630144 + 69404672),
+             ("ac42ee24b80dc569", "4f4748d01d7ca262")),
 }
 
 
@@ -1067,6 +1071,14 @@ def run_gpu(args):
 
     roof = compact_roof(roofline(form, r["kernels"], U, r["info"]["iters"]))
     pinv = pinv_report(form, r, U)
+    if rank == 0:
+        # the live per-kernel event table of the profiled pass (shares to set
+        # beside an ncu launch list of the same command)
+        tot = sum(ms for _, ms in r["kernels"].values()) or 1.0
+        print(json.dumps({"line": "kernels_" + form,
+                          "kernels": {k: [c, round(ms, 3), round(ms / tot, 4)] for k, (c, ms) in
+                                      sorted(r["kernels"].items(), key=lambda kv: -kv[1][1])[:14]}}),
+              flush=True)
     line = {
         "metric": METRIC, "value": ws * U / (r["ms_step"] / 1e3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_step"], 4),
