@@ -614,7 +614,8 @@ def emit(name, fn, *a, **kw):
     return out
 
 
-def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1, post=1):
+def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1, post=1,
+               train_lr=1e-3):
     """The variable-coefficient workload (255^2, N = 256, a = exp(GRF)) solved
     with one multigrid V-cycle per shifted system inside FGMRES(30); with
     route="learned" the V-cycle is followed by the learned correction, whose
@@ -635,14 +636,15 @@ def measure_mg(precision, args, route="mg", train_steps=0, train_batch=16, pre=1
     if train_steps:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        hist = prob.learned_train(steps=train_steps, batch=train_batch, lr=2e-3, seed=3)
+        hist = prob.learned_train(steps=train_steps, batch=train_batch, lr=train_lr, seed=3)
         dt = time.perf_counter() - t0
-        training = {"steps": train_steps, "batch": train_batch, "s": dt,
+        training = {"steps": train_steps, "batch": train_batch, "lr": train_lr, "s": dt,
                     "ms_per_step": dt * 1e3 / train_steps,
                     "loss_first5": float(np.mean(hist[:5])), "loss_last20": float(np.mean(hist[-20:])),
-                    "note": "Adam on pairs (V-cycle residual of a Gaussian right-hand side, 12 defect-"
-                            "correction V-cycles for its solution), fresh pairs every "
-                            "ceil((N/2+1)/batch) steps; includes their generation"}
+                    "note": "Adam on pairs (V-cycle residual of the recorded Krylov vectors and of "
+                            "Gaussian right-hand sides, alternately; 12 defect-correction V-cycles "
+                            "from level 1 for the coarse target), fresh pairs every "
+                            "ceil((N/2+1)/batch) steps; includes the recording solve and the pairs"}
     f = prob.build_rhs(torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda())
     u = torch.empty_like(f)
     kw = dict(restart=RESTART, rtol=RTOL, maxit=1000, flexible=True)
@@ -1054,7 +1056,7 @@ def run_gpu(args):
             say("mg_fp32_3+2", measure_mg, "fp32", args, pre=3, post=2)
             say("mg_fp32_1+1", measure_mg, "fp32", args)
             say("mg_fp64_1+1", measure_mg, "fp64", args)
-            say("learned_fp32_bf16", measure_mg, "fp32", args, route="learned", train_steps=300)
+            say("learned_fp32_bf16", measure_mg, "fp32", args, route="learned", train_steps=4000)
         say("batch", measure_batch, args, ws, rank, dist)
         if ws == 1:
             say("precision_511x511_N512", measure_precision_workload, args)

@@ -53,17 +53,24 @@ typedef enum {
 enum {
   BEC_ROUTE_FST = 0,   /* 2D/1D sine transform: exact for constant a (Sec. 4) */
   BEC_ROUTE_LEARNED = 2, /* BEC_ROUTE_MG plus a learned correction of what each
-                          V-cycle leaves: a 4-level convolutional network on
-                          the grid of spacing 2h (BF16 activations, FP32
-                          accumulation), linear in the residual (its layers
-                          are gated by functions of log a and lambda'_k
-                          only), trained on the GPU by bec_learned_train on
-                          pairs the multigrid generates; per frequency the
-                          corrected iterate gets one damped-Jacobi sweep and
-                          the step from the V-cycle's iterate towards it is
-                          scaled by alpha_k, the minimal-residual step of a
+                          V-cycle leaves, on the grid of spacing 2h:
+                          ec_k = sum_j sigma_j / (lambda'_k + sigma_j) Nc_j,
+                          8 fixed poles sigma_j > 0, the residue maps Nc_j
+                          real operators (the outputs of one 4-level
+                          convolutional network of one real plane, applied
+                          to the real and imaginary parts; BF16 activations,
+                          FP32 accumulation) whose layers are gated by
+                          functions of log a only.  So the correction is
+                          linear in the residual and analytic in lambda'_k:
+                          a dependence on conj(lambda'_k) would come back
+                          from Step 3 amplified by up to 1/eps.  Trained on
+                          the GPU by bec_learned_train on pairs the
+                          multigrid generates; the corrected iterate gets one
+                          damped-Jacobi sweep and the step from the V-cycle's
+                          iterate towards it is scaled by one alpha for all
+                          frequencies, the minimal-residual step of a
                           calibration apply on a fixed right-hand side
-                          (alpha_k = 0: the V-cycle is the fallback).  So
+                          (alpha = 0: the V-cycle is the fallback).  So
                           P_eps^{-1} stays a fixed linear operator.  Needs
                           BEC_PC_FP32 and nx >= 31. */
   BEC_ROUTE_MG = 1     /* one geometric multigrid V-cycle per shifted system,
@@ -292,28 +299,38 @@ bec_status bec_free_problem(bec_problem* p);
 /* ---- Learned correction (BEC_ROUTE_LEARNED) -------------------------------
  * The network's weights, FP32, concatenated in this order (C channels):
  *  - the 9 convolutions of the residual path, layer i an array
- *    [3][3][c_in][c_out] (2 -> C, C -> C x 7, C -> 2);
+ *    [3][3][c_in][c_out] (1 -> C, C -> C x 7, C -> 8);
  *  - the a-gates' first convolutions A1_0..A1_7, [3][3][1][8] each;
- *  - their second convolutions A2_0..A2_7, [3][3][8][C] each;
- *  - the lambda-gates' first layers L1_0..L1_7, [2][16] each;
- *  - their second layers L2_0..L2_7, [16][C] each.
+ *  - their second convolutions A2_0..A2_7, [3][3][8][C] each.
  * Gated layer i's output is multiplied point by point by
- * (1 + tanh(conv(relu(conv(log a, A1_i)), A2_i))) (1 + tanh(relu(lam2 L1_i) L2_i)),
- * lam2 = (Re, Im) lambda'_k, log a centred on the layer's grid: the network
- * is linear in the residual it corrects. */
+ * 1 + tanh(conv(relu(conv(log a, A1_i)), A2_i)), log a centred on the
+ * layer's grid.  The network maps one real plane to 8 (output channel j:
+ * residue j) and runs on the real and on the imaginary part of x = the
+ * restricted residual / sigma_0: Nc_j(x) = N_j(Re x) + i N_j(Im x), real
+ * operators, as the exact inverse's symmetry ec(conj lambda, conj r) =
+ * conj ec(lambda, r) requires.  The poles are sigma_j = sigma_0 rho^j with
+ * sigma_0 = tau a_mean 2 pi^2 and sigma_7 = 2 tau a_mean (nx + 1)^2.  The
+ * initial weights (a fixed seeded sequence) give a small correction (last
+ * layer std 0.01 sqrt(1 / (9 C))) and gates of 1. */
 long long bec_learned_num_weights(const bec_problem* p);
 bec_status bec_learned_get_weights(bec_problem* p, float* host);
 bec_status bec_learned_set_weights(bec_problem* p, const float* host);
 
 /* Trains the network on the GPU: every ceil((N/2+1)/batch) steps a fresh set
- * of pairs is made for all frequencies (r = what one V-cycle leaves of a
- * random right-hand side; target the coarse-grid correction B_{k,1}^{-1} R_0 r
- * on the grid of spacing 2h, by 12 defect-correction V-cycles from level 1);
- * each step draws `batch` frequencies, runs the forward and backward kernels
- * on the relative error ||ec - ec*||^2 / ||ec*||^2 and takes one Adam step
- * with learning rate lr.  loss_history (host, `steps` doubles, may be NULL)
+ * of pairs is made for all frequencies: first a recording solve (FGMRES on a
+ * seeded random right-hand side, preconditioned by the multigrid alone, to
+ * RES 1e-10 within one restart cycle) keeps its Krylov vectors; the sets of
+ * pairs take as right-hand sides, alternately, the time spectrum of the next
+ * of them (the inputs its V-cycles were given) and a seeded Gaussian field
+ * per frequency; r = what one V-cycle leaves of it, and the target the
+ * coarse-grid correction B_{k,1}^{-1} R_0 r on the grid of spacing 2h, by 12
+ * defect-correction V-cycles from level 1.  Each step draws `batch`
+ * frequencies (1..32), runs the forward and backward kernels on the
+ * relative error ||ec - ec*||^2 / ||ec*||^2 and takes one Adam step, the
+ * learning rate ramped up linearly to lr over the first 100 steps, then
+ * decayed along a cosine to lr / 10 at the last step.  loss_history (host, `steps` doubles, may be NULL)
  * receives the mean batch loss of every step.  The next apply recalibrates
- * the steps alpha_k.  Synchronises. */
+ * the step alpha.  Synchronises. */
 bec_status bec_learned_train(bec_problem* p, int steps, int batch, double lr,
                              unsigned long long seed, double* loss_history);
 
@@ -327,9 +344,9 @@ bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx,
                                  const double* r, const double* e_target,
                                  double* loss, float* grad);
 
-/* Frequencies at which the last calibration found no step (alpha_k = 0,
- * the V-cycle's iterate kept: B d = 0 or not finite; -1: not learned).
- * Synchronises. */
+/* 1 when the last calibration found no step (alpha = 0, the V-cycle's
+ * iterates kept: the sums vanish or are not finite), else 0; -1: not
+ * learned.  Synchronises. */
 long long bec_learned_fallbacks(bec_problem* p);
 
 /* ||b_k - B_k x_k|| after the calibrated step divided by the V-cycle's

@@ -5,44 +5,72 @@ coefficient, where the sine transform no longer applies).
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 The correction is applied after one multigrid V-cycle to the residual r it
-left, and it is LINEAR in r: for a fixed coefficient a and frequency k it is
-a fixed real-linear map, so that the preconditioner P_eps^{-1} stays a fixed
-linear operator and the outer Krylov method keeps its acceleration.  It runs
-on the grid of spacing 2h (the multigrid's level 1) with 4 levels, the
-multigrid's own bilinear prolongation P and full-weighting restriction
-R = P^T/4 as its down- and up-sampling:
+left.  Two properties are built in, whatever the weights:
 
-    rc = R_0 r;   x = c_k [Re rc, Im rc]            (2 channels)
-    h0 = conv(x, W0) G0;           s0 = conv(h0, W1) G1
+(i) It is LINEAR in r: for a fixed coefficient a and frequency k it is a
+fixed complex-linear map, so P_eps^{-1} stays a fixed linear operator and
+the outer Krylov method keeps its acceleration.
+
+(ii) Its dependence on the frequency is ANALYTIC in lambda_k.  Step 3
+multiplies time step j by eps^{-j/N}.  Write an inner solve's frequency
+dependence as a series in z = eps^{1/N} e^{-2 pi i k/N} (lambda_k = 1 - z
+for backward Euler).  Non-negative powers of z act causally in time and
+come back unamplified; a negative power, which any dependence on conj(z)
+brings in (on Re lambda, Im lambda or |lambda| separately, or on
+conj(r)), links the first time steps to the last ones and comes back
+amplified by up to 1/eps.  The exact shifted inverse, the V-cycle and the
+Jacobi sweep are rational in lambda, with poles at lambda = -(positive),
+outside the circle |z| = eps^{1/N}, so they have no such part.  The
+correction is therefore a sum of such terms, with fixed poles and residue
+maps that do not depend on k (the partial-fraction form of
+(lambda M + tau K)^{-1} = sum over modes of phi phi^T / (lambda + tau mu)):
+
+    ec_k = sum_j w_j(lambda_k) Nc_j(x),   w_j(lambda) = sigma_j / (lambda + sigma_j)
+
+with poles sigma_j = sigma_0 rho^j, j = 0..7, log-spaced from the smoothest
+mode's shift sigma_0 = tau a_mean 2 pi^2 to the largest eigenvalue
+2 tau a_mean (m + 1)^2 of the 5-point operator on the grid of spacing 2h.
+
+The residue maps are REAL operators, applied to the real and the imaginary
+part of the residual alike: Nc_j(x) = N_j(Re x) + i N_j(Im x), with N one
+network of one real plane on the grid of spacing 2h (the multigrid's level
+1), 4 levels, and the multigrid's own bilinear prolongation P and
+full-weighting restriction R = P^T/4 as its down- and up-sampling:
+
+    rc = R_0 r;   x = rc / sigma_0;   for v = Re x and v = Im x (1 channel):
+    h0 = conv(v, W0) G0;           s0 = conv(h0, W1) G1
     s1 = conv(R s0, W2) G2;        s2 = conv(R s1, W3) G3;   s3 = conv(R s2, W4) G4
     u2 = conv(P s3 + s2, W5) G5;   u1 = conv(P u2 + s1, W6) G6
-    u0 = conv(P u1 + s0, W7) G7;   y = conv(u0, W8)  (2 channels)
-    ec = y_0 + i y_1 (the coarse correction),   e = P_0 ec
+    u0 = conv(P u1 + s0, W7) G7;   N(v) = conv(u0, W8)       (8 channels)
+    Nc_j(x) = N_j(Re x) + i N_j(Im x),   e = P_0 ec
 
 Every conv is a 3 x 3 correlation with zero padding and no bias; a weight
-tensor W has shape [3][3][C_in][C_out].  c_k = 1 / |lambda_k + tau a_mean
-2 pi^2| (the size of B_k^{-1} on the smoothest mode).  The gates multiply
-each channel of a layer's output point by point:
+tensor W has shape [3][3][C_in][C_out].  Real residue operators make the
+correction complex-linear and give it the symmetry of the exact inverse,
+ec(conj lambda, conj r) = conj ec(lambda, r).  The route evaluates only
+k = 0..N/2 and takes the conjugates for the other half of the spectrum, so
+without that symmetry the correction would jump between a map and its
+conjugate at k = 0 and k = N/2: a dependence on k that is not analytic,
+see (ii).  (A network mixing the two planes with free weights is only
+real-linear, N(x) = M x + M' conj(x), with M' a dependence on conj(r).)
+The gates depend on the coefficient alone and multiply each channel of a
+layer's output point by point:
 
-    G_i = GA_i(x, c) GL_i(c),
-    GA_i = 1 + tanh(conv(relu(conv(la_l, A1_i)), A2_i))   (from log a only)
-    GL_i = 1 + tanh(relu(lam2 L1_i) L2_i)                 (from lambda_k only)
+    G_i = 1 + tanh(conv(relu(conv(la_l, A1_i)), A2_i))
 
 with la_l the centred log a on the layer's level l (levels of the gated
-layers: 0 0 1 2 3 2 1 0) and lam2 = (Re lambda_k, Im lambda_k).  The gates
-depend on a and k but not on r: that is what lets the correction adapt to
-the coefficient field and the frequency while staying linear in r (a ReLU
-network of r, tried first, made the preconditioner non-linear, and the
-outer FGMRES then lost more iterations than the correction saved).
+layers: 0 0 1 2 3 2 1 0).  They let the correction adapt to a while staying
+linear in r and independent of k.
 
 Training target: the exact coarse-grid correction ec* = B_{k,1}^{-1} R_0 r,
 B_{k,1} = lambda_k M_1 + tau K_1 the Galerkin operator of level 1; loss =
 mean over samples of ||ec - ec*||^2 / ||ec*||^2.  After the correction one
 damped-Jacobi sweep follows (the post-smoothing of a prolonged correction),
-and the step from the V-cycle's iterate is scaled by a complex alpha_k fixed
-per frequency by one calibration apply (the minimal-residual step on a
-fixed right-hand side); alpha_k = 0 keeps the V-cycle's result (the
-multigrid is the fallback).
+and the step from the V-cycle's iterate is scaled by one complex alpha, the
+same for every frequency (a per-frequency step would again depend on k
+non-analytically), fixed by one calibration apply: the minimal-residual
+step over all frequencies on a fixed right-hand side; alpha = 0 keeps the
+V-cycle's result (the multigrid is the fallback).
 """
 from __future__ import annotations
 
@@ -54,10 +82,10 @@ from .bec_oracle import mg_prolongation
 
 N_LAYERS = 9
 N_GATED = 8
-C_IN = 2
-C_OUT = 2
+N_POLES = 8
+C_IN = 1
+C_OUT = N_POLES
 NA = 8            # hidden channels of an a-gate
-NL = 16           # hidden units of a lambda-gate
 GATE_LEVEL = (0, 0, 1, 2, 3, 2, 1, 0)
 
 
@@ -68,10 +96,9 @@ def layer_shapes(C: int):
 
 def param_shapes(C: int):
     """Shapes of every parameter array in the order of the flat weight vector:
-    W0..W8, A1_0..A1_7, A2_0..A2_7, L1_0..L1_7, L2_0..L2_7."""
+    W0..W8, A1_0..A1_7, A2_0..A2_7."""
     out = [(3, 3, ci, co) for ci, co in layer_shapes(C)]
     out += [(3, 3, 1, NA)] * N_GATED + [(3, 3, NA, C)] * N_GATED
-    out += [(2, NL)] * N_GATED + [(NL, C)] * N_GATED
     return out
 
 
@@ -80,26 +107,25 @@ def num_params(C: int) -> int:
 
 
 def unflatten(w, C: int) -> dict:
-    """The parameter dict {"W", "A1", "A2", "L1", "L2"} of a flat vector."""
+    """The parameter dict {"W", "A1", "A2"} of a flat vector."""
     arrs, off = [], 0
     for s in param_shapes(C):
         n = int(np.prod(s))
         arrs.append(np.asarray(w[off:off + n], dtype=np.float64).reshape(s))
         off += n
     g = N_GATED
-    return {"W": arrs[:9], "A1": arrs[9:9 + g], "A2": arrs[9 + g:9 + 2 * g],
-            "L1": arrs[9 + 2 * g:9 + 3 * g], "L2": arrs[9 + 3 * g:9 + 4 * g]}
+    return {"W": arrs[:9], "A1": arrs[9:9 + g], "A2": arrs[9 + g:9 + 2 * g]}
 
 
 def flatten(params: dict) -> np.ndarray:
-    parts = params["W"] + params["A1"] + params["A2"] + params["L1"] + params["L2"]
+    parts = params["W"] + params["A1"] + params["A2"]
     return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
 
 
 def init_params(C: int, seed: int = 0, gate_scale: float = 0.0) -> dict:
     """Seeded initialisation: W normal with std sqrt(1 / (9 C_in)) (the last
-    layer scaled by 0.1), A1 std 0.3, L1 std 0.5; A2 and L2 normal with std
-    gate_scale (0: every gate starts at 1)."""
+    layer scaled by 0.1), A1 std 0.3; A2 normal with std gate_scale (0: every
+    gate starts at 1)."""
     rng = np.random.default_rng(seed)
     W = []
     for i, (ci, co) in enumerate(layer_shapes(C)):
@@ -107,9 +133,7 @@ def init_params(C: int, seed: int = 0, gate_scale: float = 0.0) -> dict:
         W.append(rng.standard_normal((3, 3, ci, co)) * std)
     A1 = [rng.standard_normal((3, 3, 1, NA)) * 0.3 for _ in range(N_GATED)]
     A2 = [rng.standard_normal((3, 3, NA, C)) * gate_scale for _ in range(N_GATED)]
-    L1 = [rng.standard_normal((2, NL)) * 0.5 for _ in range(N_GATED)]
-    L2 = [rng.standard_normal((NL, C)) * gate_scale for _ in range(N_GATED)]
-    return {"W": W, "A1": A1, "A2": A2, "L1": L1, "L2": L2}
+    return {"W": W, "A1": A1, "A2": A2}
 
 
 def conv3x3(x: np.ndarray, W: np.ndarray) -> np.ndarray:
@@ -173,22 +197,27 @@ def a_gates(params: dict, la_levels) -> list:
     return out
 
 
-def lam_gates(params: dict, lam: complex) -> list:
-    """GL_i = 1 + tanh(relu(lam2 L1_i) L2_i), [C], lam2 = (Re lambda, Im lambda)."""
-    lam2 = np.array([lam.real, lam.imag])
-    return [1.0 + np.tanh(relu(lam2 @ params["L1"][i]) @ params["L2"][i]) for i in range(N_GATED)]
+def pole_shifts(tau: float, a_mean: float, m: int) -> np.ndarray:
+    """sigma_j = sigma_0 rho^j, j = 0..N_POLES-1: sigma_0 = tau a_mean 2 pi^2
+    (the shift of the smoothest mode) up to sigma_top = 2 tau a_mean (m+1)^2
+    (tau a_mean 8 / (2h)^2, the largest eigenvalue of the 5-point operator on
+    the grid of spacing 2h, h = 1 / (m+1))."""
+    s0 = tau * a_mean * 2.0 * math.pi ** 2
+    top = 2.0 * tau * a_mean * (m + 1) ** 2
+    return s0 * (top / s0) ** (np.arange(N_POLES) / (N_POLES - 1))
 
 
-def output_scale(lam: complex, tau: float, a_mean: float) -> float:
-    """c_k = 1 / |lambda + tau a_mean 2 pi^2|."""
-    return 1.0 / abs(lam + tau * a_mean * 2.0 * math.pi ** 2)
+def pole_weights(lam: complex, sig: np.ndarray) -> np.ndarray:
+    """w_j = sigma_j / (lambda + sigma_j)."""
+    return sig / (lam + sig)
 
 
-def forward(params: dict, x: np.ndarray, GA: list, GL: list, tr: Transfers) -> np.ndarray:
-    """The residual path of the module docstring on one input [2][m][m], with
-    the gates GA (list of [C][m_l][m_l]) and GL (list of [C])."""
+def forward(params: dict, x: np.ndarray, GA: list, tr: Transfers) -> np.ndarray:
+    """The residual path of the module docstring on one real input plane
+    [1][m][m], with the gates GA (list of [C][m_l][m_l]); returns the
+    N_POLES output planes N_j."""
     W = params["W"]
-    G = [GA[i] * GL[i][:, None, None] for i in range(N_GATED)]
+    G = GA
     h0 = conv3x3(x, W[0]) * G[0]
     s0 = conv3x3(h0, W[1]) * G[1]
     s1 = conv3x3(tr.restrict(0, s0), W[2]) * G[2]
@@ -213,15 +242,21 @@ class LearnedCorrection:
         self.la_levels = level_log_a(self.la_c, self.tr)
         self.a_mean = float(np.mean(np.exp(log_a_nodes)))
         self.tau = tau
+        self.sig = pole_shifts(tau, self.a_mean, m)
+
+    def residues(self, params: dict, rc: np.ndarray) -> np.ndarray:
+        """Nc_j(x) = N_j(Re x) + i N_j(Im x), x = rc / sigma_0, for j =
+        0..N_POLES-1 ([N_POLES][mc][mc] complex) from the coarse residual rc."""
+        GA = a_gates(params, self.la_levels)
+        x = rc / self.sig[0]
+        return forward(params, x.real[None], GA, self.tr) + 1j * forward(params, x.imag[None], GA, self.tr)
 
     def coarse(self, params: dict, r: np.ndarray, lam: complex) -> np.ndarray:
         """ec (complex [mc][mc]) for a fine complex residual r [m][m]."""
         mc = self.mc
         rc = (self.R0 @ r.reshape(-1)).reshape(mc, mc)
-        c = output_scale(lam, self.tau, self.a_mean)
-        x = c * np.stack([rc.real, rc.imag])
-        y = forward(params, x, a_gates(params, self.la_levels), lam_gates(params, lam), self.tr)
-        return y[0] + 1j * y[1]
+        w = pole_weights(lam, self.sig)
+        return np.tensordot(w, self.residues(params, rc), axes=1)
 
     def __call__(self, params: dict, r: np.ndarray, lam: complex) -> np.ndarray:
         """e = P_0 ec on the fine grid [m][m]."""
@@ -315,29 +350,34 @@ def forward_sign_eigs(N: int, eps: float) -> np.ndarray:
 
 def calibrate(h, lc: LearnedCorrection, params, tau: float, eps: float, N: int,
               omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
-    """alpha_k for every frequency k = 0..N/2 from one calibration apply: the
-    V-cycle and the correction on calibration_rhs, then the minimal-residual
-    step.  Returns (alphas, ratios)."""
+    """The one step alpha for all frequencies from one calibration apply: the
+    V-cycle and the correction on calibration_rhs at every k = 0..N/2, then
+    the minimal-residual step of the stacked system, alpha = sum_k <A_k d_k,
+    res_k> / sum_k ||A_k d_k||^2 (0 when the sums vanish or are not finite).
+    Returns (alpha, ratios), ratios[k] = ||res_k - alpha A_k d_k|| / ||res_k||."""
     from .bec_oracle import mg_vcycle
     lam = forward_sign_eigs(N, eps)
     m = lc.m
     B = calibration_rhs(N // 2 + 1, m * m)
-    alphas, ratios = [], []
+    pairs = []
     for k in range(N // 2 + 1):
         A = h.op(0, lam[k], tau)
         x = mg_vcycle(h, lam[k], tau, B[k], omega, nu1, nu2)
         _, x2 = correct(params, lc, A, B[k], x, lam[k], 0.0, omega, net)
-        a, q = minimal_residual_step(A, B[k], x, x2)
-        alphas.append(a)
-        ratios.append(q)
-    return np.array(alphas), np.array(ratios)
+        pairs.append((B[k] - A @ x, A @ (x2 - x)))
+    dd = sum(float(np.vdot(Ad, Ad).real) for _, Ad in pairs)
+    cr = sum(complex(np.vdot(Ad, res)) for res, Ad in pairs)
+    ok = dd > 0 and math.isfinite(dd) and math.isfinite(cr.real) and math.isfinite(cr.imag)
+    alpha = cr / dd if ok else 0.0
+    ratios = [float(np.linalg.norm(res - alpha * Ad) / np.linalg.norm(res)) for res, Ad in pairs]
+    return alpha, np.array(ratios)
 
 
 def apply_Pinv_learned(y: np.ndarray, h, lc: LearnedCorrection, params, tau: float, eps: float,
-                       alphas, omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
+                       alpha, omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
     """P_eps^{-1} y by Sec. 4's three steps with Step 2 done, per frequency, by
     one V-cycle (``mg_vcycle``) and then the correction with the fixed step
-    alphas[k] (``correct``).  The route is defined on the half spectrum of a
+    alpha (``correct``).  The route is defined on the half spectrum of a
     forward-sign real DFT (k = 0..N/2 with lambda'_k of
     ``forward_sign_eigs``); the other frequencies are the conjugates (a real
     result), and the imaginary parts at k = 0 and N/2 are dropped, as by a
@@ -353,6 +393,6 @@ def apply_Pinv_learned(y: np.ndarray, h, lc: LearnedCorrection, params, tau: flo
     for k in range(N // 2 + 1):                                          # Step 2
         A = h.op(0, lam[k], tau)
         x = mg_vcycle(h, lam[k], tau, yt[k], omega, nu1, nu2)
-        zt[k], _ = correct(params, lc, A, yt[k], x, lam[k], alphas[k], omega, net)
+        zt[k], _ = correct(params, lc, A, yt[k], x, lam[k], alpha, omega, net)
     z = np.fft.irfft(zt, n=N, axis=0) / d[:, None]                      # Step 3
     return z.reshape(y.shape)

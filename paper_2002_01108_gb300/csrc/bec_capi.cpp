@@ -283,9 +283,10 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
     chain(mg_setup(p, d->a_nodes, d->wind));
     if (d->route == BEC_ROUTE_LEARNED && s == BEC_OK)
       // inference runs all N/2 + 1 frequencies in one batch up to 160 of them
-      // (training batches stay at most 32)
+      // (training batches stay at most 32); each frequency takes two network
+      // samples (r and i r)
       chain(net_setup(p, d->a_nodes, d->net_channels == 0 ? 32 : d->net_channels, d->net_fp32,
-                      std::max(32, std::min(p->N / 2 + 1, 160))));
+                      2 * std::max(32, std::min(p->N / 2 + 1, 160))));
   }
   p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
   p->desc.wind = nullptr;

@@ -405,7 +405,7 @@ __global__ void tc_weights_kernel(const float* __restrict__ W, LayerOffsets woff
   int l = 0;
   while (l + 1 < kNetLayers && g >= layer_wt_offset(l + 1)) ++l;
   const int cin_pad = l == 0 ? 16 : 32, cout_pad = l == 8 ? 16 : 32;
-  const int cin = l == 0 ? 2 : 32, cout = l == 8 ? 2 : 32;
+  const int cin = l == 0 ? 1 : 32, cout = l == 8 ? kNetOut : 32;
   const int e = g - layer_wt_offset(l);
   const int j = e % 8, co = (e / 8) % cout_pad, ch = (e / (8 * cout_pad)) % (cin_pad / 8),
             tap = e / (8 * cout_pad * (cin_pad / 8));
@@ -507,7 +507,7 @@ bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const 
   const __nv_bfloat16* w = wt + layer_wt_offset(layer);
   // no activation: the network's gates multiply the stored outputs
   if (layer == 0) return launch_tc<16, 32, 32, false>(p, in, w, out, m, B, bmax, err);
-  if (layer == 8) return launch_tc<32, 16, 2, false>(p, in, w, out, m, B, bmax, err);
+  if (layer == 8) return launch_tc<32, 16, kNetOut, false>(p, in, w, out, m, B, bmax, err);
   return launch_tc<32, 32, 32, false>(p, in, w, out, m, B, bmax, err);
 }
 

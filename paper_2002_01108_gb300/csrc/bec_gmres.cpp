@@ -38,10 +38,11 @@ bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* 
   if (p->desc.route == BEC_ROUTE_MG || p->desc.route == BEC_ROUTE_LEARNED) {
     // the learned route's steps alpha_k are fixed by a calibration apply
     // whenever the weights or eps changed
-    if (p->desc.route == BEC_ROUTE_LEARNED && !net_calibrated(p)) BEC_TRY(net_calibrate(p));
+    const bool learned = p->desc.route == BEC_ROUTE_LEARNED && !net_bypassed(p);
+    if (learned && !net_calibrated(p)) BEC_TRY(net_calibrate(p));
     BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));
     BEC_TRY(mg_vcycle(p));
-    if (p->desc.route == BEC_ROUTE_LEARNED) BEC_TRY(net_correct(p));
+    if (learned) BEC_TRY(net_correct(p));
     return launch_time_inv(p, p->mg.lv[0].x, z, fp64);
   }
   const double n = (double)(p->m + 1);

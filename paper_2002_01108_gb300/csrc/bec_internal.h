@@ -333,6 +333,8 @@ bec_status net_correct(bec_problem* p);   // after the V-cycle: x += alpha_k (co
 bec_status net_calibrate(bec_problem* p);
 bool net_calibrated(const bec_problem* p);
 void net_invalidate(bec_problem* p);
+// the route acts as the multigrid route alone (during the training's recording solve)
+bool net_bypassed(const bec_problem* p);
 bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                      double* loss_hist);
 long long net_num_weights(const bec_problem* p);
@@ -356,9 +358,11 @@ int tc_weights_elems();
 // at W + woff[l], [tap][c_in][c_out]); host array woff of 9 offsets
 bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* woff,
                               __nv_bfloat16* wt);
+// output channels of the learned correction's network: one real plane per pole
+constexpr int kNetOut = 8;
 // out = conv3x3(in) of layer l (no activation: the network's gates follow):
-// l = 0 reads the 16-channel padded input planes, l = 8 stores its 2 output
-// channels
+// l = 0 reads the 16-channel padded input planes, l = 8 stores its kNetOut
+// output channels
 bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
                       __nv_bfloat16* out, int m, int B, int bmax, int* err);
 bec_status net_residual_ratios(bec_problem* p, double* host);

@@ -1,21 +1,36 @@
 // Learned route of P_eps^{-1} (BEC_ROUTE_LEARNED): one multigrid V-cycle per
 // shifted system, then a learned correction of what the V-cycle left,
-//     x1 = x_k + P_0 Net(c_k R_0 (b_k - B_k x_k)),
+//     x1 = x_k + P_0 ec_k(R_0 (b_k - B_k x_k)),
 // one damped-Jacobi sweep x2 = x1 + omega D^{-1} (b_k - B_k x1) (the
 // post-smoothing that follows a prolonged correction), and the step
-// x_k <- x_k + alpha_k (x2 - x_k) with alpha_k fixed per frequency by a
-// calibration apply (the minimal-residual step on a fixed right-hand side;
-// alpha_k = 0 keeps the V-cycle's iterate: the multigrid is the fallback).
-// The network is LINEAR in the residual: a 4-level convolutional network on
-// the grid of spacing 2h whose layer outputs are multiplied by gates computed
-// from log a (per point and channel) and lambda'_k (per channel), never from
-// the residual.  So for a fixed a and k the correction is a fixed linear map
-// and P_eps^{-1} a fixed linear operator (a network non-linear in the
-// residual made the outer FGMRES lose its Krylov acceleration).  It is
-// trained on the GPU, by these kernels, on pairs that the multigrid itself
-// generates: r is the residual a V-cycle leaves for a random right-hand side,
-// the target is the coarse-grid correction B_{k,1}^{-1} R_0 r (level 1 of the
-// hierarchy), obtained by repeated V-cycles from level 1 (defect correction).
+// x_k <- x_k + alpha (x2 - x_k) with one alpha for all frequencies, fixed by
+// a calibration apply (the minimal-residual step of all frequencies together
+// on a fixed right-hand side; alpha = 0 keeps the V-cycle's iterates: the
+// multigrid is the fallback).
+//
+// The coarse correction is linear in the residual and analytic in the shift:
+//     ec_k = sum_j sigma_j / (lambda'_k + sigma_j) Nc_j(rc / sigma_0),
+// 8 fixed poles sigma_j (geometric, from the smoothest mode's shift to the
+// largest eigenvalue on the grid of spacing 2h) with residue maps Nc_j that
+// do not depend on k: real operators, Nc_j(x) = N_j(Re x) + i N_j(Im x), the
+// 8 outputs of one 4-level convolutional network of one real plane on the
+// grid of spacing 2h, whose layer outputs are multiplied by gates computed
+// from log a only.  Real residue operators give ec the exact inverse's
+// symmetry ec(conj lambda, conj r) = conj ec(lambda, r), on which the half
+// spectrum relies (else the map would jump to its conjugate at k = 0, N/2).
+// Why analytic: Step 3 multiplies time step j by eps^{-j/N}.  A dependence of
+// the inner solve on conj(lambda'_k) (through Re, Im or |lambda'_k|
+// separately, or through conj of the residual) links the first time steps
+// to the last ones, and that part comes back amplified by up to 1/eps.  Poles
+// on the negative real axis, like those of the exact (lambda M + tau K)^{-1},
+// the V-cycle and the sweep, have no such part.
+//
+// The network is trained on the GPU, by these kernels, on pairs that the
+// method's own multigrid generates: r is the residual a V-cycle leaves for
+// the right-hand sides that the V-cycles of a multigrid-preconditioned FGMRES
+// solve were given (the time spectra of its Krylov vectors), the target the
+// coarse-grid correction B_{k,1}^{-1} R_0 r (level 1 of the hierarchy),
+// obtained by repeated V-cycles from level 1 (defect correction).
 // Requires the FP32 preconditioner.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -53,7 +68,7 @@ struct NetState {
   bool fp32 = false;
   int mf = 0;                    // fine grid
   int sz[4] = {0, 0, 0, 0};      // network levels, sz[0] = (mf - 1) / 2
-  int Bmax = 0;
+  int Bmax = 0;                  // network samples; a frequency takes two (r and i r)
   int cin[9], cout[9];
   long long woff[10];            // the 9 convolutions of the residual path
   net::GateOffsets goff;         // the gate networks' weights
@@ -73,14 +88,16 @@ struct NetState {
   float* dGA[net::kGates] = {};  // gradients of the a-gates
   float* dA = nullptr;           // work: [sz0^2][C]
   float* dZ = nullptr;           // work: [sz0^2][8]
-  float* GL = nullptr;           // lambda-gates [Bmax][8][C]
-  float* hid = nullptr;          // their hidden units [Bmax][8][16]
-  float* dGL = nullptr;          // gradients [Bmax][8][C]
+  net::Poles poles;              // sigma_j of the pole terms
   bool gates_ok = false;         // GA matches the weights
   bool cal_ok = false;           // alpha matches the weights and eps
+  bool bypass = false;           // the route acts as the multigrid route alone
+  int nkry = 0;                  // recorded Krylov vectors (rows of the problem's V)
+  double* kf = nullptr;          // U doubles: the recording solve's right-hand side
+  double* ku = nullptr;          // U doubles: its solution
   double a_mean = 1.0;
   float* rc = nullptr;           // [Bmax][mc^2] complex
-  float* ones = nullptr;         // [Bmax] 1.0
+  float* ecb = nullptr;          // [Bmax / 2][mc^2] complex: the coarse correction ec
   int* row = nullptr;            // per sample row of res / etgt (staged from the host)
   int* lam = nullptr;            // per sample frequency index
   int* iota = nullptr;           // 0, 1, ..., K-1 (rows = frequencies, no host staging)
@@ -95,7 +112,7 @@ struct NetState {
   float* xnew = nullptr;         // [K][J] complex corrected iterate
   double* part = nullptr;        // per-sample / per-frequency partial sums
   double* jpart = nullptr;       // the calibration's block sums, [K][kMrSplit][4]
-  float2* alpha = nullptr;       // the step per frequency (from the calibration)
+  float2* alpha = nullptr;       // the step, one for all frequencies (from the calibration)
   double* h_part = nullptr;      // pinned mirror
   int adam_t = 0;
   unsigned long long rng_ctr = 0;
@@ -130,46 +147,89 @@ __global__ void feat_restrict_kernel(const float2* __restrict__ res, const int* 
   rc[g] = acc;
 }
 
-// X[b][q] = c_b (Re rc, Im rc), c_b = 1 / |lambda'_k + tau a_mean 2 pi^2| of
-// the sample's frequency (and, when X16 is not null, the same two planes
-// padded with zeros to 16 BF16 channels: the input of the tensor-core layer 0)
+// The input planes of Bc complex samples as 2 Bc real network samples:
+// X[b][q] = Re rc / sigma_0 and X[Bc + b][q] = Im rc / sigma_0, the same scale
+// for every frequency (and, when X16 is not null, the same plane padded with
+// zeros to 16 BF16 channels: the input of the tensor-core layer 0)
+__device__ __forceinline__ void x16_store(__nv_bfloat16* X16, long long g, float f0) {
+  const __nv_bfloat162 h01 = __floats2bfloat162_rn(f0, 0.f);
+  uint4 lo;
+  lo.x = *reinterpret_cast<const unsigned*>(&h01);
+  lo.y = 0u;
+  lo.z = 0u;
+  lo.w = 0u;
+  uint4* d16 = reinterpret_cast<uint4*>(X16 + g * 16);
+  d16[0] = lo;
+  d16[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 template <typename AT>
-__global__ void feat_fill_kernel(const float2* __restrict__ rc, const int* __restrict__ lam,
-                                 const float2* __restrict__ lamf, float tau_a_2pi2,
-                                 AT* __restrict__ X, __nv_bfloat16* __restrict__ X16,
-                                 long long mcc, int B) {
+__global__ void feat_fill_kernel(const float2* __restrict__ rc, float c, AT* __restrict__ X,
+                                 __nv_bfloat16* __restrict__ X16, long long mcc, int Bc) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= B * mcc) return;
-  const int b = (int)(g / mcc);
-  const float2 L = lamf[lam[b]];
-  const float c = (float)(1.0 / hypot((double)L.x + tau_a_2pi2, (double)L.y));
+  const long long half = Bc * mcc;
+  if (g >= half) return;
   const float2 v = rc[g];
   const float f0 = c * v.x, f1 = c * v.y;
-  X[g * 2] = net::st<AT>(f0);
-  X[g * 2 + 1] = net::st<AT>(f1);
+  X[g] = net::st<AT>(f0);
+  X[half + g] = net::st<AT>(f1);
   if (X16 != nullptr) {
-    const __nv_bfloat162 h01 = __floats2bfloat162_rn(f0, f1);
-    uint4 lo;
-    lo.x = *reinterpret_cast<const unsigned*>(&h01);
-    lo.y = 0u;
-    lo.z = 0u;
-    lo.w = 0u;
-    uint4* d16 = reinterpret_cast<uint4*>(X16 + g * 16);
-    d16[0] = lo;
-    d16[1] = make_uint4(0u, 0u, 0u, 0u);
+    x16_store(X16, g, f0);
+    x16_store(X16, half + g, f1);
   }
 }
 
-// efine[b][f] = P_0 (cfac_b (y0 + i y1)) at fine node f
+// w_j = sigma_j / (lambda + sigma_j) of one frequency
+__device__ __forceinline__ void pole_weights(float2 L, const net::Poles& P,
+                                             float2 (&w)[net::kPoles]) {
+#pragma unroll
+  for (int j = 0; j < net::kPoles; ++j) {
+    const float dr = L.x + P.s[j], di = L.y;
+    const float f = P.s[j] / fmaf(dr, dr, di * di);
+    w[j] = make_float2(dr * f, -di * f);
+  }
+}
+
+// ec = sum_j w_j Nc_j at coarse point q of complex sample b, with
+// Nc_j = N_j(Re x) + i N_j(Im x) from the network outputs Y[b] = N(Re x) and
+// Y[Bc + b] = N(Im x) (kNetOut = kPoles real channels)
 template <typename AT>
-__global__ void out_prolong_kernel(const AT* __restrict__ Y, const float* __restrict__ cfac,
-                                   float2* __restrict__ efine, int mc, int mf, int B) {
+__device__ __forceinline__ float2 pole_sum(const AT* __restrict__ Y, long long b, long long q,
+                                           long long mcc, int Bc, const float2 (&w)[net::kPoles]) {
+  static_assert(kNetOut == net::kPoles, "one output plane per pole");
+  const AT* yr = Y + (b * mcc + q) * kNetOut;
+  const AT* yi = Y + ((Bc + b) * mcc + q) * kNetOut;
+  float ex = 0.f, ey = 0.f;
+#pragma unroll
+  for (int j = 0; j < net::kPoles; ++j) {
+    const float pr = net::ld(yr + j), pi = net::ld(yi + j);
+    ex = fmaf(w[j].x, pr, fmaf(-w[j].y, pi, ex));
+    ey = fmaf(w[j].x, pi, fmaf(w[j].y, pr, ey));
+  }
+  return make_float2(ex, ey);
+}
+
+// ecb[b][q] = ec of complex sample b (frequency lam[b]) at coarse point q
+template <typename AT>
+__global__ void pole_sum_kernel(const AT* __restrict__ Y, const int* __restrict__ lam,
+                                const float2* __restrict__ lamf, net::Poles P,
+                                float2* __restrict__ ecb, long long mcc, int Bc) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long mff = (long long)mf * mf;
-  if (g >= B * mff) return;
+  if (g >= Bc * mcc) return;
+  const int b = (int)(g / mcc);
+  float2 w[net::kPoles];
+  pole_weights(lamf[lam[b]], P, w);
+  ecb[g] = pole_sum(Y, b, g - (long long)b * mcc, mcc, Bc, w);
+}
+
+// efine[b][f] = P_0 ec_b at fine node f for each of Bc complex samples
+__global__ void out_prolong_kernel(const float2* __restrict__ ecb, float2* __restrict__ efine,
+                                   int mc, int mf, int Bc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mff = (long long)mf * mf, mcc = (long long)mc * mc;
+  if (g >= Bc * mff) return;
   const int b = (int)(g / mff), f = (int)(g - (long long)b * mff);
   const int fy = f / mf, fx = f % mf;
-  const AT* src = Y + (long long)b * mc * mc * 2;
   float ax = 0.f, ay = 0.f;
   for (int a = 0; a < 2; ++a) {
     int cy;
@@ -183,30 +243,32 @@ __global__ void out_prolong_kernel(const AT* __restrict__ Y, const float* __rest
       if (fx & 1) { if (c2) break; cx = (fx - 1) / 2; wx = 1.f; }
       else { cx = fx / 2 - 1 + c2; wx = 0.5f; }
       if (cx < 0 || cx >= mc) continue;
-      const AT* v = src + ((long long)cy * mc + cx) * 2;
-      ax = fmaf(wy * wx, net::ld(v), ax);
-      ay = fmaf(wy * wx, net::ld(v + 1), ay);
+      const float2 v = ecb[(long long)b * mcc + (long long)cy * mc + cx];
+      ax = fmaf(wy * wx, v.x, ax);
+      ay = fmaf(wy * wx, v.y, ay);
     }
   }
-  const float c = cfac[b];
-  efine[g] = make_float2(c * ax, c * ay);
+  efine[g] = make_float2(ax, ay);
 }
 
-// one block per sample: part[2b] = ||Y_b - etgt[row_b]||^2 and part[2b+1] =
-// ||etgt[row_b]||^2 on the coarse grid (Y_b: 2 channels = real and imaginary
-// part of the coarse correction)
+// one block per complex sample: part[2b] = ||ec_b - etgt[row_b]||^2 and
+// part[2b+1] = ||etgt[row_b]||^2 on the coarse grid (ec_b: pole_sum at the
+// sample's frequency lam[b])
 template <typename AT>
 __global__ void closs_parts_kernel(const AT* __restrict__ Y, const float2* __restrict__ etgt,
-                                   const int* __restrict__ row, double* __restrict__ part,
-                                   long long mcc) {
+                                   const int* __restrict__ row, const int* __restrict__ lam,
+                                   const float2* __restrict__ lamf, net::Poles P,
+                                   double* __restrict__ part, long long mcc, int Bc) {
   __shared__ double rn[256], rd[256];
   const int b = blockIdx.x;
   const float2* t = etgt + (long long)row[b] * mcc;
-  const AT* y = Y + (long long)b * mcc * 2;
+  float2 w[net::kPoles];
+  pole_weights(lamf[lam[b]], P, w);
   double num = 0.0, den = 0.0;
   for (long long q = threadIdx.x; q < mcc; q += blockDim.x) {
     const float2 tv = t[q];
-    const double dx = (double)net::ld(y + 2 * q) - tv.x, dy = (double)net::ld(y + 2 * q + 1) - tv.y;
+    const float2 e = pole_sum(Y, b, q, mcc, Bc, w);
+    const double dx = (double)e.x - tv.x, dy = (double)e.y - tv.y;
     num += dx * dx + dy * dy;
     den += (double)tv.x * tv.x + (double)tv.y * tv.y;
   }
@@ -226,19 +288,35 @@ __global__ void closs_parts_kernel(const AT* __restrict__ Y, const float2* __res
   }
 }
 
-// dL/dY[b][q][c] = 2 (Y - etgt) / (den_b B) for L = mean_b ||Y_b - t_b||^2 / den_b
+// L = mean_b ||ec_b - t_b||^2 / den_b over Bc complex samples, G = dL/dec_b
+// = 2 (ec_b - t_b) / (den_b Bc).  Through ec = sum_j w_j (a_j + i b_j)
+// (pole_sum: a_j channel j of Y_b, b_j of Y_{Bc+b}), with h_j = conj(G) w_j:
+// dL/da_j = Re h_j,  dL/db_j = -Im h_j
 template <typename AT>
 __global__ void closs_grad_kernel(const AT* __restrict__ Y, const float2* __restrict__ etgt,
-                                  const int* __restrict__ row, const double* __restrict__ part,
-                                  AT* __restrict__ dY, long long mcc, int B) {
+                                  const int* __restrict__ row, const int* __restrict__ lam,
+                                  const float2* __restrict__ lamf, net::Poles P,
+                                  const double* __restrict__ part, AT* __restrict__ dY,
+                                  long long mcc, int Bc) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= B * mcc) return;
+  const long long half = Bc * mcc;
+  if (g >= half) return;
   const int b = (int)(g / mcc);
   const long long q = g - (long long)b * mcc;
+  float2 w[net::kPoles];
+  pole_weights(lamf[lam[b]], P, w);
   const float2 t = etgt[(long long)row[b] * mcc + q];
-  const double k = 2.0 / (part[2 * b + 1] * B);
-  dY[g * 2] = net::st<AT>((float)(k * ((double)net::ld(Y + g * 2) - t.x)));
-  dY[g * 2 + 1] = net::st<AT>((float)(k * ((double)net::ld(Y + g * 2 + 1) - t.y)));
+  const float2 e = pole_sum(Y, b, q, mcc, Bc, w);
+  const double k = 2.0 / (part[2 * b + 1] * Bc);
+  const float gx = (float)(k * ((double)e.x - t.x)), gy = (float)(k * ((double)e.y - t.y));
+  AT* dr = dY + g * kNetOut;
+  AT* di = dY + (half + g) * kNetOut;
+#pragma unroll
+  for (int j = 0; j < net::kPoles; ++j) {
+    const float hr = fmaf(gx, w[j].x, gy * w[j].y), hi = fmaf(gx, w[j].y, -gy * w[j].x);
+    dr[j] = net::st<AT>(hr);
+    di[j] = net::st<AT>(-hi);
+  }
 }
 
 // The calibration right-hand side: value i of the interleaved (re, im) array
@@ -257,6 +335,15 @@ __global__ void calibration_fill_kernel(float* __restrict__ v, long long n) {
   if (g >= n) return;
   const unsigned long long t = splitmix64(kCalibrationKey ^ splitmix64((unsigned long long)g));
   v[g] = (float)(int)(t >> 40) * 0x1p-23f - 1.0f;
+}
+
+// v[i] = uniform in [-1, 1): (splitmix64(key ^ splitmix64(i)) >> 11) 2^-52 - 1
+__global__ void uniform_fill_f64_kernel(double* __restrict__ v, long long n,
+                                        unsigned long long key) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const unsigned long long t = splitmix64(key ^ splitmix64((unsigned long long)g));
+  v[g] = (double)(t >> 11) * 0x1p-52 - 1.0;
 }
 
 // counter-based standard normal pair (splitmix64 hash + Box-Muller)
@@ -333,34 +420,50 @@ mr_dots_kernel(const float2* __restrict__ res, const float2* __restrict__ r2,
     jpart[((long long)k * kMrSplit + sblk) * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Per frequency: the sums over the kMrSplit blocks (in order) into part[4k..],
-// the step alpha_k = <B d, res> / ||B d||^2 (0 when B d = 0: the V-cycle's
-// iterate is kept), ratio[k] = ||b - B x_new|| / ||res||, fallback count.
-__global__ void mr_alpha_kernel(const double* __restrict__ jpart, double* __restrict__ part,
-                                float2* __restrict__ alpha, int K, double* __restrict__ ratio,
-                                int* __restrict__ fallbacks) {
+// One block: per frequency the sums over the kMrSplit blocks (in order) into
+// part[4k..]; then the one step alpha = sum_k <B d, res>_k / sum_k ||B d||_k^2
+// (k in order; 0 when the sums vanish or are not finite: the V-cycle's
+// iterate is kept, one fallback); then ratio[k] = ||res - alpha B d|| / ||res||
+// = sqrt(rr - 2 Re(alpha conj<B d, res>) + |alpha|^2 dd) / sqrt(rr).
+__global__ void __launch_bounds__(256)
+mr_alpha_kernel(const double* __restrict__ jpart, double* __restrict__ part,
+                float2* __restrict__ alpha, int K, double* __restrict__ ratio,
+                int* __restrict__ fallbacks) {
+  __shared__ double al[2];
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double sm[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = 0; b < kMrSplit; ++b)
       for (int i = 0; i < 4; ++i) sm[i] += jpart[((long long)k * kMrSplit + b) * 4 + i];
     for (int i = 0; i < 4; ++i) part[4 * k + i] = sm[i];
-    const double cr = sm[0], ci = sm[1], dd = sm[2], rr = sm[3];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cr = 0.0, ci = 0.0, dd = 0.0;
+    for (int k = 0; k < K; ++k) {
+      cr += part[4 * k];
+      ci += part[4 * k + 1];
+      dd += part[4 * k + 2];
+    }
     const bool ok = dd > 0.0 && isfinite(dd) && isfinite(cr) && isfinite(ci);
-    alpha[k] = ok ? make_float2((float)(cr / dd), (float)(ci / dd)) : make_float2(0.f, 0.f);
-    const double after = ok ? fmax(rr - (cr * cr + ci * ci) / dd, 0.0) : rr;
-    ratio[k] = rr > 0.0 ? sqrt(after / rr) : 0.0;
-    if (!ok) atomicAdd(fallbacks, 1);
+    al[0] = ok ? cr / dd : 0.0;
+    al[1] = ok ? ci / dd : 0.0;
+    alpha[0] = make_float2((float)al[0], (float)al[1]);
+    if (!ok) *fallbacks = 1;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double cr = part[4 * k], ci = part[4 * k + 1], dd = part[4 * k + 2], rr = part[4 * k + 3];
+    const double after = rr - 2.0 * (al[0] * cr + al[1] * ci) + (al[0] * al[0] + al[1] * al[1]) * dd;
+    ratio[k] = rr > 0.0 ? sqrt(fmax(after, 0.0) / rr) : 0.0;
   }
 }
 
-// x <- x + alpha_k (x2 - x): the complex step that minimises
-// ||b - B (x + alpha d)|| (alpha from mr_alpha_kernel).
+// x <- x + alpha (x2 - x) with the calibration's step (mr_alpha_kernel)
 __global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restrict__ x2,
-                                 const float2* __restrict__ alpha, long long mff, int K) {
+                                 const float2* __restrict__ alpha, long long n) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)K * mff) return;
-  const int k = (int)(g / mff);
-  const float2 al = alpha[k];
+  if (g >= n) return;
+  const float2 al = alpha[0];
   const float2 a = x[g], c = x2[g];
   const float dx = c.x - a.x, dy = c.y - a.y;
   x[g] = make_float2(a.x + al.x * dx - al.y * dy, a.y + al.x * dy + al.y * dx);
@@ -381,7 +484,7 @@ bec_status conv_fwd_raw(bec_problem* p, const AT* a, const float* W, int ci, int
     if (relu) net::conv3x3_fwd_kernel<AT, CI, CO, true><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
     else net::conv3x3_fwd_kernel<AT, CI, CO, false><<<g, net::kConvThreads, 0, p->stream>>>(a, W, o, m, npix); \
   } else
-  BEC_CF(2, 4) BEC_CF(4, 4) BEC_CF(4, 2) BEC_CF(2, 32) BEC_CF(32, 32) BEC_CF(32, 2) BEC_CF(1, 8)
+  BEC_CF(1, 4) BEC_CF(4, 4) BEC_CF(4, 8) BEC_CF(1, 32) BEC_CF(32, 32) BEC_CF(32, 8) BEC_CF(1, 8)
   BEC_CF(8, 4) BEC_CF(8, 32) {
     set_error("unsupported network channel count");
     return BEC_EUNSUPPORTED;
@@ -431,7 +534,7 @@ bec_status conv_bwd_raw(bec_problem* p, const AT* a, const AT* d, const float* W
       BEC_LAUNCH_CHECK(p, "net_conv_dgrad_kernel");                                               \
     }                                                                                             \
   } else
-  BEC_CB(2, 4) BEC_CB(4, 4) BEC_CB(4, 2) BEC_CB(2, 32) BEC_CB(32, 32) BEC_CB(32, 2) BEC_CB(1, 8)
+  BEC_CB(1, 4) BEC_CB(4, 4) BEC_CB(4, 8) BEC_CB(1, 32) BEC_CB(32, 32) BEC_CB(32, 8) BEC_CB(1, 8)
   BEC_CB(8, 4) BEC_CB(8, 32) {
     set_error("unsupported network channel count");
     return BEC_EUNSUPPORTED;
@@ -551,38 +654,27 @@ bec_status gates_fwd(bec_problem* p) {
   return BEC_OK;
 }
 
-// the lambda-gates of the B samples whose frequencies are n.cur_lam
-bec_status lam_gates(bec_problem* p, int B) {
-  NetState& n = *p->net;
-  const int cnt = B * net::kGates * n.C;
-  BEC_LAUNCH_BEGIN(p);
-  net::lam_gate_fwd_kernel<<<(cnt + 255) / 256, 256, 0, p->stream>>>(
-      n.W, n.goff, n.cur_lam, p->tab.lamf32, n.hid, n.GL, n.C, B);
-  BEC_LAUNCH_CHECK(p, "net_lambda_gate_kernel");
-  return BEC_OK;
-}
-
-// input planes of B samples (rows n.cur_row of n.res, frequencies n.cur_lam)
+// input planes of Bc complex samples (rows n.cur_row of n.res, frequencies
+// n.cur_lam) as 2 Bc network samples
 template <typename AT>
-bec_status features(bec_problem* p, int B) {
+bec_status features(bec_problem* p, int Bc) {
   NetState& n = *p->net;
   const int mc = n.sz[0];
   const long long mcc = (long long)mc * mc;
   BEC_LAUNCH_BEGIN(p);
-  feat_restrict_kernel<<<grid_for(B * mcc), kT, 0, p->stream>>>(
-      reinterpret_cast<const float2*>(n.res), n.cur_row, reinterpret_cast<float2*>(n.rc), n.mf, mc, B);
+  feat_restrict_kernel<<<grid_for(Bc * mcc), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.res), n.cur_row, reinterpret_cast<float2*>(n.rc), n.mf, mc, Bc);
   BEC_LAUNCH_CHECK(p, "net_feat_restrict_kernel");
   BEC_LAUNCH_BEGIN(p);
-  feat_fill_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
-      reinterpret_cast<const float2*>(n.rc), n.cur_lam, p->tab.lamf32,
-      (float)(p->tau * n.a_mean * 2.0 * M_PI * M_PI), static_cast<AT*>(n.act[A_X]),
-      (sizeof(AT) == 2 && n.tc) ? n.x16 : nullptr, mcc, B);
+  feat_fill_kernel<AT><<<grid_for(Bc * mcc), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.rc), 1.f / n.poles.s[0], static_cast<AT*>(n.act[A_X]),
+      (sizeof(AT) == 2 && n.tc) ? n.x16 : nullptr, mcc, Bc);
   BEC_LAUNCH_CHECK(p, "net_feat_fill_kernel");
   return BEC_OK;
 }
 
-// gated layer i: out = conv(in, W_i) * GA_i * GL_i; training keeps the
-// product's first factor in n.pre[i] for the backward pass
+// gated layer i: out = conv(in, W_i) * GA_i; training keeps the product's
+// first factor in n.pre[i] for the backward pass
 template <typename AT>
 bec_status gate_layer(bec_problem* p, int i, int B, bool training) {
   NetState& n = *p->net;
@@ -592,8 +684,7 @@ bec_status gate_layer(bec_problem* p, int i, int B, bool training) {
   BEC_TRY(conv_fwd<AT>(p, n.act[kGateIn[i]], i, pre, m, B));
   const long long mmC = (long long)m * m * n.C, cnt = B * mmC;
   BEC_LAUNCH_BEGIN(p);
-  net::gate_apply_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
-      pre, out, n.GA[i], n.GL + i * n.C, net::kGates * n.C, mmC, n.C, cnt);
+  net::gate_apply_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(pre, out, n.GA[i], mmC, cnt);
   BEC_LAUNCH_CHECK(p, "net_gate_kernel");
   return BEC_OK;
 }
@@ -621,22 +712,25 @@ bec_status forward(bec_problem* p, int B, bool training) {
   return BEC_OK;
 }
 
-// efine[b] = P_0 (y_0 + i y_1) of the last forward pass
+// efine[b] = P_0 ec_b of the last forward pass, b < Bc (frequencies n.cur_lam)
 template <typename AT>
-bec_status correction_fine(bec_problem* p, int B) {
+bec_status correction_fine(bec_problem* p, int Bc) {
   NetState& n = *p->net;
-  const long long mff = (long long)n.mf * n.mf;
+  const long long mff = (long long)n.mf * n.mf, mcc = (long long)n.sz[0] * n.sz[0];
   BEC_LAUNCH_BEGIN(p);
-  out_prolong_kernel<AT><<<grid_for(B * mff), kT, 0, p->stream>>>(
-      static_cast<const AT*>(n.act[A_Y]), n.ones, reinterpret_cast<float2*>(n.efine), n.sz[0],
-      n.mf, B);
+  pole_sum_kernel<AT><<<grid_for(Bc * mcc), kT, 0, p->stream>>>(
+      static_cast<const AT*>(n.act[A_Y]), n.cur_lam, p->tab.lamf32, n.poles,
+      reinterpret_cast<float2*>(n.ecb), mcc, Bc);
+  BEC_LAUNCH_CHECK(p, "net_pole_sum_kernel");
+  BEC_LAUNCH_BEGIN(p);
+  out_prolong_kernel<<<grid_for(Bc * mff), kT, 0, p->stream>>>(
+      reinterpret_cast<const float2*>(n.ecb), reinterpret_cast<float2*>(n.efine), n.sz[0], n.mf, Bc);
   BEC_LAUNCH_CHECK(p, "net_out_prolong_kernel");
   return BEC_OK;
 }
 
 // backward through gated layer i, d = dL/d(out_i) on entry: the gate
-// gradients dGA_i (summed over the samples) and dGL[.][i] (summed over the
-// points), then d <- d * G_i = dL/d(pre_i)
+// gradient dGA_i (summed over the samples), then d <- d * GA_i = dL/d(pre_i)
 template <typename AT>
 bec_status gate_bwd(bec_problem* p, int i, void* dv, int B) {
   NetState& n = *p->net;
@@ -645,21 +739,16 @@ bec_status gate_bwd(bec_problem* p, int i, void* dv, int B) {
   AT* d = static_cast<AT*>(dv);
   const AT* pre = static_cast<const AT*>(n.pre[i]);
   BEC_LAUNCH_BEGIN(p);
-  net::gate_dga_kernel<AT><<<grid_for(mmC), kT, 0, p->stream>>>(
-      d, pre, n.GL + i * n.C, net::kGates * n.C, n.dGA[i], mmC, n.C, B);
+  net::gate_dga_kernel<AT><<<grid_for(mmC), kT, 0, p->stream>>>(d, pre, n.dGA[i], mmC, B);
   BEC_LAUNCH_CHECK(p, "net_gate_dga_kernel");
   BEC_LAUNCH_BEGIN(p);
-  net::gate_dgl_kernel<AT><<<B, 256, 0, p->stream>>>(d, pre, n.GA[i], n.dGL + i * n.C,
-                                                     net::kGates * n.C, mm, n.C);
-  BEC_LAUNCH_CHECK(p, "net_gate_dgl_kernel");
-  BEC_LAUNCH_BEGIN(p);
-  net::gate_scale_grad_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(
-      d, n.GA[i], n.GL + i * n.C, net::kGates * n.C, mmC, n.C, cnt);
+  net::gate_scale_grad_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(d, n.GA[i], mmC, cnt);
   BEC_LAUNCH_CHECK(p, "net_gate_grad_kernel");
   return BEC_OK;
 }
 
-// gradients of every weight for the loss whose dL/dY is in grad[A_Y]
+// gradients of every weight for the loss whose dL/dY is in grad[A_Y], over
+// B = 2 Bc network samples
 template <typename AT>
 bec_status backward(bec_problem* p, int B) {
   NetState& n = *p->net;
@@ -690,12 +779,6 @@ bec_status backward(bec_problem* p, int B) {
   BEC_TRY(conv_bwd<AT>(p, a[A_H0], d[A_S0], 1, d[A_H0], n.sz[0], B));
   BEC_TRY(gate_bwd<AT>(p, 0, d[A_H0], B));
   BEC_TRY(conv_bwd<AT>(p, a[A_X], d[A_H0], 0, nullptr, n.sz[0], B));
-  // the lambda-gates' weights
-  const int per = 2 * net::kGateHidden + net::kGateHidden * n.C;
-  BEC_LAUNCH_BEGIN(p);
-  net::lam_gate_bwd_kernel<<<(net::kGates * per + 127) / 128, 128, 0, p->stream>>>(
-      n.W, n.goff, n.cur_lam, p->tab.lamf32, n.hid, n.GL, n.dGL, n.G, n.C, B);
-  BEC_LAUNCH_CHECK(p, "net_lambda_gate_bwd_kernel");
   // the a-gates' weights: through GA = 1 + tanh(conv(Z1, A2)), Z1 = relu(conv(la, A1))
   for (int i = 0; i < net::kGates; ++i) {
     const int l = kGateLevel[i], m = n.sz[l];
@@ -715,21 +798,21 @@ bec_status backward(bec_problem* p, int B) {
   return BEC_OK;
 }
 
-// loss parts (per sample) and dL/dY for the samples in n.row against the
-// coarse targets n.etgt
+// loss parts (per complex sample) and dL/dY of the 2 Bc network samples, for
+// the Bc complex samples in n.row against the coarse targets n.etgt
 template <typename AT>
-bec_status loss_and_dy(bec_problem* p, int B) {
+bec_status loss_and_dy(bec_problem* p, int Bc) {
   NetState& n = *p->net;
   const long long mcc = (long long)n.sz[0] * n.sz[0];
   BEC_LAUNCH_BEGIN(p);
-  closs_parts_kernel<AT><<<B, 256, 0, p->stream>>>(static_cast<const AT*>(n.act[A_Y]),
-                                                   reinterpret_cast<const float2*>(n.etgt),
-                                                   n.cur_row, n.part, mcc);
+  closs_parts_kernel<AT><<<Bc, 256, 0, p->stream>>>(
+      static_cast<const AT*>(n.act[A_Y]), reinterpret_cast<const float2*>(n.etgt), n.cur_row,
+      n.cur_lam, p->tab.lamf32, n.poles, n.part, mcc, Bc);
   BEC_LAUNCH_CHECK(p, "net_loss_kernel");
   BEC_LAUNCH_BEGIN(p);
-  closs_grad_kernel<AT><<<grid_for(B * mcc), kT, 0, p->stream>>>(
+  closs_grad_kernel<AT><<<grid_for(Bc * mcc), kT, 0, p->stream>>>(
       static_cast<const AT*>(n.act[A_Y]), reinterpret_cast<const float2*>(n.etgt), n.cur_row,
-      n.part, static_cast<AT*>(n.grad[A_Y]), mcc, B);
+      n.cur_lam, p->tab.lamf32, n.poles, n.part, static_cast<AT*>(n.grad[A_Y]), mcc, Bc);
   BEC_LAUNCH_CHECK(p, "net_loss_grad_kernel");
   return BEC_OK;
 }
@@ -763,18 +846,29 @@ bec_status adam_step(bec_problem* p, float lr) {
   return BEC_OK;
 }
 
-// Training pairs for every frequency: res = b - B V(b) for a random b, and
-// the coarse target etgt = B_1^{-1} R_0 res by `sweeps` defect-correction
-// V-cycles from level 1 of the hierarchy.
-bec_status make_pairs(bec_problem* p, int sweeps) {
+// Training pairs for every frequency: res = b - B V(b), and the coarse
+// target etgt = B_1^{-1} R_0 res by `sweeps` defect-correction V-cycles from
+// level 1 of the hierarchy.  The right-hand sides b: with kry < 0 a random
+// Gaussian one per frequency; else the time spectrum (Step 1 of Sec. 4) of
+// Krylov vector kry of the recording solve, i.e. exactly what the V-cycles
+// of that solve were given.
+bec_status make_pairs(bec_problem* p, int sweeps, int kry) {
   NetState& n = *p->net;
   MgLevel& L0 = p->mg.lv[0];
   const long long tot = (long long)p->mg.K * L0.J;
   const long long tot1 = (long long)p->mg.K * p->mg.lv[1].J;
-  BEC_LAUNCH_BEGIN(p);
-  gauss_fill_kernel<<<grid_for(tot), kT, 0, p->stream>>>(static_cast<float2*>(L0.b), tot,
-                                                         0xB5C0FFEEull + (n.rng_ctr++) * 0x100000001ull);
-  BEC_LAUNCH_CHECK(p, "net_gauss_fill_kernel");
+  if (kry < 0) {
+    BEC_LAUNCH_BEGIN(p);
+    gauss_fill_kernel<<<grid_for(tot), kT, 0, p->stream>>>(
+        static_cast<float2*>(L0.b), tot, 0xB5C0FFEEull + (n.rng_ctr++) * 0x100000001ull);
+    BEC_LAUNCH_CHECK(p, "net_gauss_fill_kernel");
+  } else {
+    // V_kry is stored unnormalised; sigma[kry] = 1 / ||V_kry|| scales it as
+    // the solve's preconditioner apply did.  V_0 is the right-hand side
+    // itself (a solve from zero does not copy it into V).
+    const double* v = kry == 0 ? n.kf : p->V + (long long)kry * p->U;
+    BEC_TRY(launch_time_fwd(p, v, L0.b, 0, p->sigma + kry));
+  }
   // keep the right-hand side: the V-cycle reuses L0.b
   BEC_CUDA_TRY(cudaMemcpyAsync(n.ework, L0.b, tot * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
   BEC_TRY(mg_vcycle(p));
@@ -792,6 +886,42 @@ bec_status make_pairs(bec_problem* p, int sweeps) {
   return BEC_OK;
 }
 
+// The recording solve: FGMRES preconditioned by the multigrid alone (the
+// route bypassed) on a random right-hand side, to RES 1e-10 within one
+// restart cycle.  Its Krylov basis stays in the problem's V: the inputs of
+// its preconditioner applies, which the training then turns into pairs.
+bec_status record_krylov(bec_problem* p, unsigned long long seed) {
+  NetState& n = *p->net;
+  BEC_LAUNCH_BEGIN(p);
+  uniform_fill_f64_kernel<<<grid_for(p->U), kT, 0, p->stream>>>(n.kf, p->U,
+                                                                0x5EEDF00Dull ^ (seed * 0x9E37ull));
+  BEC_LAUNCH_CHECK(p, "net_uniform_fill_kernel");
+  bec_gmres_opts o{};
+  o.restart = p->max_restart;
+  o.maxit = p->max_restart;
+  o.rtol = 1e-10;
+  o.flexible = p->desc.flexible ? 1 : 0;
+  bec_gmres_info info{};
+  n.bypass = true;
+  const bec_status st = gmres_solve_one(p, n.kf, n.ku, &o, &info);
+  n.bypass = false;
+  if (st != BEC_OK && st != BEC_ENOTCONV) return st;
+  n.nkry = info.iters > 0 ? info.iters : 0;
+  return BEC_OK;
+}
+
+// The learning rate of step s of `steps`: a linear warm-up over the first
+// kWarmup steps (the first Adam steps move every weight by about lr whatever
+// its gradient), then a cosine decay to lr / 10 at the last step (the final
+// weights come from small steps, whatever the loss did on the way).
+constexpr int kWarmup = 100;
+float lr_at(float lr, int s, int steps) {
+  if (s < kWarmup) return lr * (float)(s + 1) / kWarmup;
+  const int span = steps - kWarmup;
+  const double t = span > 1 ? (double)(s - kWarmup) / (span - 1) : 1.0;
+  return (float)(lr * (0.1 + 0.45 * (1.0 + std::cos(M_PI * t))));
+}
+
 template <typename AT>
 bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                    double* loss_hist) {
@@ -803,20 +933,29 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
   const int regen = (K + batch - 1) / batch;   // batches drawn from one set of pairs
   n.gates_ok = false;
   n.cal_ok = false;
+  BEC_TRY(record_krylov(p, seed));
+  int sets = 0;
   for (int s = 0; s < steps; ++s) {
-    if (s % regen == 0) BEC_TRY(make_pairs(p, 12));
+    // fresh pairs, alternately from the recorded Krylov vectors in turn (what
+    // the solve's V-cycles are given) and from a random Gaussian right-hand
+    // side per frequency (every mode the V-cycle leaves, so that the
+    // correction is trained not to amplify modes outside the Krylov space)
+    if (s % regen == 0) {
+      const bool krylov = n.nkry > 0 && (sets & 1) == 0;
+      BEC_TRY(make_pairs(p, 12, krylov ? (sets / 2) % n.nkry : -1));
+      ++sets;
+    }
     for (int b = 0; b < batch; ++b) {
       st = st * 6364136223846793005ull + 1442695040888963407ull;
       rows[b] = (int)((st >> 33) % (unsigned long long)K);
     }
     BEC_TRY(set_samples(p, rows.data(), rows.data(), batch));
     BEC_TRY(gates_fwd(p));
-    BEC_TRY(lam_gates(p, batch));
     BEC_TRY(features<AT>(p, batch));
-    BEC_TRY(forward<AT>(p, batch, true));
+    BEC_TRY(forward<AT>(p, 2 * batch, true));
     BEC_TRY(loss_and_dy<AT>(p, batch));
-    BEC_TRY(backward<AT>(p, batch));
-    BEC_TRY(adam_step(p, lr));
+    BEC_TRY(backward<AT>(p, 2 * batch));
+    BEC_TRY(adam_step(p, lr_at(lr, s, steps)));
     if (loss_hist) {
       BEC_CUDA_TRY(cudaMemcpyAsync(n.h_part, n.part, 2 * batch * sizeof(double),
                                    cudaMemcpyDeviceToHost, p->stream));
@@ -831,8 +970,9 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
   return net_check(p);
 }
 
-// x1 = x + P_0 Net(c_k R_0 (b - B x)) for every frequency, into n.xnew, from
-// the residual in n.res (batches of Bmax frequencies)
+// x1 = x + P_0 ec(c_k R_0 (b - B x)) for every frequency, into n.xnew, from
+// the residual in n.res (batches of Bmax / 2 frequencies, Bmax network
+// samples)
 template <typename AT>
 bec_status corrected_iterate(bec_problem* p) {
   NetState& n = *p->net;
@@ -840,13 +980,13 @@ bec_status corrected_iterate(bec_problem* p) {
   const int K = p->mg.K;
   const long long mff = (long long)n.mf * n.mf;
   if (!n.gates_ok) BEC_TRY(gates_fwd(p));
-  for (int k0 = 0; k0 < K; k0 += n.Bmax) {
-    const int B = K - k0 < n.Bmax ? K - k0 : n.Bmax;
+  const int bc = n.Bmax / 2;
+  for (int k0 = 0; k0 < K; k0 += bc) {
+    const int B = K - k0 < bc ? K - k0 : bc;
     n.cur_row = n.iota + k0;
     n.cur_lam = n.iota + k0;
-    BEC_TRY(lam_gates(p, B));
     BEC_TRY(features<AT>(p, B));
-    BEC_TRY(forward<AT>(p, B, false));
+    BEC_TRY(forward<AT>(p, 2 * B, false));
     BEC_TRY(correction_fine<AT>(p, B));
     BEC_LAUNCH_BEGIN(p);
     add_corr_kernel<<<grid_for(B * mff), kT, 0, p->stream>>>(
@@ -858,9 +998,10 @@ bec_status corrected_iterate(bec_problem* p) {
 }
 
 // The calibration apply: the V-cycle and the correction on the fixed
-// right-hand side of calibration_fill_kernel; alpha_k = the minimal-residual
-// step <B d, res> / ||B d||^2, d = x2 - x (0 when B d = 0 or not finite, the
-// V-cycle's iterate then kept), and the residual ratio it reaches.  Uses the
+// right-hand side of calibration_fill_kernel at every frequency; alpha = the
+// minimal-residual step sum_k <B d, res> / sum_k ||B d||^2, d = x2 - x (0
+// when the sums vanish or are not finite, the V-cycle's iterates then kept),
+// and the residual ratio it reaches per frequency.  Uses the
 // multigrid's level-0 arrays, so it runs before an apply's Step 1.
 template <typename AT>
 bec_status calibrate_t(bec_problem* p) {
@@ -903,11 +1044,11 @@ bec_status correct_t(bec_problem* p) {
   BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
   BEC_TRY(corrected_iterate<AT>(p));
   // x2 = one damped-Jacobi sweep on x1 (the post-smoothing of a prolonged
-  // correction) into L0.r, then x <- x + alpha_k (x2 - x)
+  // correction) into L0.r, then x <- x + alpha (x2 - x)
   BEC_TRY(mg_smooth_level0(p, L0.r, n.xnew, L0.b));
   BEC_LAUNCH_BEGIN(p);
   mr_update_kernel<<<grid_for(K * mff), kT, 0, p->stream>>>(
-      static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.alpha, mff, K);
+      static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.alpha, K * mff);
   BEC_LAUNCH_CHECK(p, "net_step_kernel");
   return BEC_OK;
 }
@@ -940,19 +1081,18 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   for (int l = 1; l < 4; ++l) n->sz[l] = (n->sz[l - 1] - 1) / 2;
   n->Bmax = bmax;
   const int C = channels;
-  const int shapes[9][2] = {{2, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, C}, {C, 2}};
+  const int shapes[9][2] = {{1, C}, {C, C}, {C, C}, {C, C}, {C, C},
+                            {C, C}, {C, C}, {C, C}, {C, kNetOut}};
   n->woff[0] = 0;
   for (int i = 0; i < 9; ++i) {
     n->cin[i] = shapes[i][0];
     n->cout[i] = shapes[i][1];
     n->woff[i + 1] = n->woff[i] + 9LL * shapes[i][0] * shapes[i][1];
   }
-  // then A1_0..7 [3][3][1][8], A2_0..7 [3][3][8][C], L1_0..7 [2][16], L2_0..7 [16][C]
+  // then A1_0..7 [3][3][1][8], A2_0..7 [3][3][8][C]
   long long o = n->woff[9];
   for (int i = 0; i < net::kGates; ++i, o += 9LL * net::kGateAHidden) n->goff.a1[i] = o;
   for (int i = 0; i < net::kGates; ++i, o += 9LL * net::kGateAHidden * C) n->goff.a2[i] = o;
-  for (int i = 0; i < net::kGates; ++i, o += 2LL * net::kGateHidden) n->goff.l1[i] = o;
-  for (int i = 0; i < net::kGates; ++i, o += (long long)net::kGateHidden * C) n->goff.l2[i] = o;
   n->nparam = o;
   const long long nw = n->nparam;
   bec_status s = BEC_OK;
@@ -966,7 +1106,7 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   const size_t asz = n->fp32 ? sizeof(float) : sizeof(__nv_bfloat16);
   for (int a = 0; a < NACT; ++a) {
     const int l = act_level(a);
-    const int ch = a == A_X ? 2 : (a == A_Y ? 2 : C);
+    const int ch = a == A_X ? 1 : (a == A_Y ? kNetOut : C);
     const size_t bytes = (size_t)bmax * n->sz[l] * n->sz[l] * ch * asz;
     chain(dalloc(&n->act[a], bytes));
     chain(dalloc(&n->grad[a], bytes));
@@ -985,12 +1125,8 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
     chain(dalloc(reinterpret_cast<void**>(&n->la_lv[l]), (size_t)n->sz[l] * n->sz[l] * sizeof(float)));
   chain(dalloc(reinterpret_cast<void**>(&n->dA), (size_t)mcc * C * sizeof(float)));
   chain(dalloc(reinterpret_cast<void**>(&n->dZ), (size_t)mcc * net::kGateAHidden * sizeof(float)));
-  chain(dalloc(reinterpret_cast<void**>(&n->GL), (size_t)bmax * net::kGates * C * sizeof(float)));
-  chain(dalloc(reinterpret_cast<void**>(&n->dGL), (size_t)bmax * net::kGates * C * sizeof(float)));
-  chain(dalloc(reinterpret_cast<void**>(&n->hid),
-               (size_t)bmax * net::kGates * net::kGateHidden * sizeof(float)));
   chain(dalloc(reinterpret_cast<void**>(&n->rc), (size_t)bmax * mcc * sizeof(float2)));
-  chain(dalloc(reinterpret_cast<void**>(&n->ones), bmax * sizeof(float)));
+  chain(dalloc(reinterpret_cast<void**>(&n->ecb), (size_t)(bmax / 2) * mcc * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->row), bmax * sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->lam), bmax * sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->iota), K * sizeof(int)));
@@ -1002,8 +1138,10 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   chain(dalloc(reinterpret_cast<void**>(&n->xnew), (size_t)K * mff * sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->jpart), (size_t)K * kMrSplit * 4 * sizeof(double)));
-  chain(dalloc(reinterpret_cast<void**>(&n->alpha), (size_t)K * sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->alpha), sizeof(float2)));
   chain(dalloc(reinterpret_cast<void**>(&n->err), sizeof(int)));
+  chain(dalloc(reinterpret_cast<void**>(&n->kf), (size_t)p->U * sizeof(double)));
+  chain(dalloc(reinterpret_cast<void**>(&n->ku), (size_t)p->U * sizeof(double)));
   n->tc = !n->fp32 && C == 32 && tc_conv_supported();
   if (n->tc) {
     chain(dalloc(reinterpret_cast<void**>(&n->wt), (size_t)tc_weights_elems() * sizeof(__nv_bfloat16)));
@@ -1033,6 +1171,15 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   }
   mean_la /= (double)la.size();
   n->a_mean = mean_a / (double)la.size();
+  // the poles: sigma_0 = tau a_mean 2 pi^2 (the smoothest mode's shift) up to
+  // 2 tau a_mean (m+1)^2 (the largest eigenvalue of the 5-point operator on
+  // the grid of spacing 2h), geometric
+  {
+    const double s0 = p->tau * n->a_mean * 2.0 * M_PI * M_PI;
+    const double top = 2.0 * p->tau * n->a_mean * (double)(p->m + 1) * (double)(p->m + 1);
+    for (int j = 0; j < net::kPoles; ++j)
+      n->poles.s[j] = (float)(s0 * std::pow(top / s0, (double)j / (net::kPoles - 1)));
+  }
   std::vector<double> lv((size_t)mcc);
   for (int cy = 0; cy < n->sz[0]; ++cy)
     for (int cx = 0; cx < n->sz[0]; ++cx)
@@ -1059,11 +1206,9 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   std::vector<int> io(K);
   for (long long k = 0; k < K; ++k) io[k] = (int)k;
   BEC_CUDA_TRY(cudaMemcpy(n->iota, io.data(), K * sizeof(int), cudaMemcpyHostToDevice));
-  std::vector<float> ones((size_t)bmax, 1.f);
-  BEC_CUDA_TRY(cudaMemcpy(n->ones, ones.data(), bmax * sizeof(float), cudaMemcpyHostToDevice));
   // initial weights from a fixed counter-based normal sequence: the residual
-  // path std sqrt(1 / (9 C_in)) (last layer x 0.1), A1 std 0.3, L1 std 0.5,
-  // A2 and L2 zero (every gate starts at 1)
+  // path std sqrt(1 / (9 C_in)) (last layer x 0.01: the correction starts
+  // small), A1 std 0.3, A2 zero (every gate starts at 1)
   std::vector<float> w(nw, 0.f);
   unsigned long long z = 0x243F6A8885A308D3ull;
   auto normal = [&z]() {
@@ -1074,13 +1219,11 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
     return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
   };
   for (int i = 0; i < 9; ++i) {
-    const double sd = std::sqrt(1.0 / (9.0 * n->cin[i])) * (i == 8 ? 0.1 : 1.0);
+    const double sd = std::sqrt(1.0 / (9.0 * n->cin[i])) * (i == 8 ? 0.01 : 1.0);
     for (long long j = n->woff[i]; j < n->woff[i + 1]; ++j) w[j] = (float)(sd * normal());
   }
-  for (int i = 0; i < net::kGates; ++i) {
+  for (int i = 0; i < net::kGates; ++i)
     for (long long j = 0; j < 9LL * net::kGateAHidden; ++j) w[n->goff.a1[i] + j] = (float)(0.3 * normal());
-    for (long long j = 0; j < 2LL * net::kGateHidden; ++j) w[n->goff.l1[i] + j] = (float)(0.5 * normal());
-  }
   BEC_CUDA_TRY(cudaMemcpy(n->W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice));
   BEC_CUDA_TRY(cudaMemset(n->Mo, 0, nw * sizeof(float)));
   BEC_CUDA_TRY(cudaMemset(n->Ve, 0, nw * sizeof(float)));
@@ -1091,9 +1234,9 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
 void net_free(bec_problem* p) {
   NetState* n = p->net;
   if (n == nullptr) return;
-  void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->rc, n->ones, n->row, n->lam, n->iota,
+  void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->rc, n->row, n->lam, n->iota,
                   n->efine, n->res, n->etgt, n->rcall, n->ework, n->xnew, n->part, n->jpart,
-                  n->alpha, n->err, n->wt, n->x16, n->dA, n->dZ, n->GL, n->dGL, n->hid};
+                  n->alpha, n->err, n->wt, n->x16, n->dA, n->dZ, n->ecb, n->kf, n->ku};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int l = 0; l < 4; ++l)
@@ -1123,13 +1266,15 @@ bec_status net_calibrate(bec_problem* p) {
 
 bool net_calibrated(const bec_problem* p) { return p->net != nullptr && p->net->cal_ok; }
 
+bool net_bypassed(const bec_problem* p) { return p->net != nullptr && p->net->bypass; }
+
 void net_invalidate(bec_problem* p) {
   if (p->net) p->net->cal_ok = false;
 }
 
 bec_status net_train(bec_problem* p, int steps, int batch, float lr, unsigned long long seed,
                      double* loss_hist) {
-  if (batch < 1 || batch > p->net->Bmax) return BEC_EINVAL;
+  if (batch < 1 || 2 * batch > p->net->Bmax) return BEC_EINVAL;
   return p->net->fp32 ? train_t<float>(p, steps, batch, lr, seed, loss_hist)
                       : train_t<__nv_bfloat16>(p, steps, batch, lr, seed, loss_hist);
 }
@@ -1179,11 +1324,10 @@ bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, 
   for (int b = 0; b < B; ++b) rows[b] = b;
   BEC_TRY(set_samples(p, rows.data(), lams, B));
   BEC_TRY(gates_fwd(p));
-  BEC_TRY(lam_gates(p, B));
   BEC_TRY(features<AT>(p, B));
-  BEC_TRY(forward<AT>(p, B, true));
+  BEC_TRY(forward<AT>(p, 2 * B, true));
   BEC_TRY(loss_and_dy<AT>(p, B));
-  BEC_TRY(backward<AT>(p, B));
+  BEC_TRY(backward<AT>(p, 2 * B));
   BEC_CUDA_TRY(cudaMemcpyAsync(n.h_part, n.part, 2 * B * sizeof(double), cudaMemcpyDeviceToHost,
                                p->stream));
   BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -1198,7 +1342,7 @@ bec_status loss_grad_t(bec_problem* p, int B, const int* lams, const double* r, 
 
 bec_status net_loss_grad(bec_problem* p, int B, const int* lams, const double* r, const double* et,
                          double* loss_out, float* grad_host) {
-  if (B < 1 || B > p->net->Bmax || B > p->mg.K) {   // samples are staged in rows 0..B-1 of K
+  if (B < 1 || 2 * B > p->net->Bmax || B > p->mg.K) {   // samples are staged in rows 0..B-1 of K
     set_error("B must lie in [1, min(32, N/2 + 1)]");
     return BEC_EINVAL;
   }

@@ -381,76 +381,42 @@ __global__ void add_kernel(AT* __restrict__ d, const AT* __restrict__ e, long lo
 
 // ---------------------------------------------------------------- gates
 constexpr int kGates = 8;      // gated layers (0..7)
-constexpr int kGateHidden = 16; // hidden units of a lambda-gate
+constexpr int kPoles = 8;      // pole terms of the correction
+struct Poles {
+  float s[kPoles];             // sigma_j
+};
 constexpr int kGateAHidden = 8; // hidden channels of an a-gate
 
-// out[b][p][c] = pre[b][p][c] GA[p][c] GL[b][c] (out may be pre); GL rows of
-// stride gl_stride floats
+// out[b][p][c] = pre[b][p][c] GA[p][c] (out may be pre)
 template <typename AT>
 __global__ void gate_apply_kernel(const AT* __restrict__ pre, AT* __restrict__ out,
-                                  const float* __restrict__ GA, const float* __restrict__ GL,
-                                  int gl_stride, long long mmC, int C, long long n) {
+                                  const float* __restrict__ GA, long long mmC, long long n) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const long long b = g / mmC;
-  const long long pc = g - b * mmC;
-  const int c = (int)(pc % C);
-  out[g] = st<AT>(ld(pre + g) * (GA[pc] * GL[b * gl_stride + c]));
+  out[g] = st<AT>(ld(pre + g) * GA[g % mmC]);
 }
 
-// d[b][p][c] *= GA[p][c] GL[b][c] (the adjoint of the gate multiply)
+// d[b][p][c] *= GA[p][c] (the adjoint of the gate multiply)
 template <typename AT>
 __global__ void gate_scale_grad_kernel(AT* __restrict__ d, const float* __restrict__ GA,
-                                       const float* __restrict__ GL, int gl_stride, long long mmC,
-                                       int C, long long n) {
+                                       long long mmC, long long n) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const long long b = g / mmC;
-  const long long pc = g - b * mmC;
-  const int c = (int)(pc % C);
-  d[g] = st<AT>(ld(d + g) * (GA[pc] * GL[b * gl_stride + c]));
+  d[g] = st<AT>(ld(d + g) * GA[g % mmC]);
 }
 
-// dGA[p][c] = sum_b dout[b][p][c] pre[b][p][c] GL[b][c]  (b in order)
+// dGA[p][c] = sum_b dout[b][p][c] pre[b][p][c]  (b in order)
 template <typename AT>
 __global__ void gate_dga_kernel(const AT* __restrict__ dout, const AT* __restrict__ pre,
-                                const float* __restrict__ GL, int gl_stride, float* __restrict__ dGA,
-                                long long mmC, int C, int B) {
+                                float* __restrict__ dGA, long long mmC, int B) {
   const long long pc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pc >= mmC) return;
-  const int c = (int)(pc % C);
   float s = 0.f;
   for (int b = 0; b < B; ++b) {
     const long long g = (long long)b * mmC + pc;
-    s = fmaf(ld(dout + g) * ld(pre + g), GL[(long long)b * gl_stride + c], s);
+    s = fmaf(ld(dout + g), ld(pre + g), s);
   }
   dGA[pc] = s;
-}
-
-// dGL[b][c] = sum_p dout[b][p][c] pre[b][p][c] GA[p][c]: one block per
-// sample, thread t sums channel t mod C over the pixels t / C + k (256 / C),
-// then the block adds its threads' sums per channel in a fixed order
-template <typename AT>
-__global__ void __launch_bounds__(256)
-gate_dgl_kernel(const AT* __restrict__ dout, const AT* __restrict__ pre,
-                const float* __restrict__ GA, float* __restrict__ dGL, int gl_stride,
-                long long mm, int C) {
-  __shared__ float red[256];
-  const int b = blockIdx.x;
-  const int c = threadIdx.x % C, p0 = threadIdx.x / C, ps = 256 / C;
-  float s = 0.f;
-  const long long base = (long long)b * mm * C;
-  for (long long p = p0; p < mm; p += ps) {
-    const long long pc = p * C + c;
-    s = fmaf(ld(dout + base + pc) * ld(pre + base + pc), GA[pc], s);
-  }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x < C) {
-    float t = 0.f;
-    for (int k = 0; k < ps; ++k) t += red[k * C + threadIdx.x];
-    dGL[(long long)b * gl_stride + threadIdx.x] = t;
-  }
 }
 
 // a = 1 + tanh(a) in place (the a-gate's output)
@@ -468,72 +434,10 @@ __global__ void dtanh_kernel(const float* __restrict__ dG, const float* __restri
   d[g] = dG[g] * (1.f - t * t);
 }
 
-// lambda-gates of B samples: hid[b][i][j] = sum_d lam2_b[d] L1_i[d][j] and
-// GL[b][i][c] = 1 + tanh(sum_j relu(hid) L2_i[j][c]), lam2_b = (Re, Im)
-// lambda'_{k_b}; one thread per (b, i, c).  L1_i and L2_i at W + l1off[i]
-// and W + l2off[i].
+// where the a-gates' weights A1_i and A2_i start in the flat weight vector
 struct GateOffsets {
-  long long a1[kGates], a2[kGates], l1[kGates], l2[kGates];
+  long long a1[kGates], a2[kGates];
 };
-
-__global__ void lam_gate_fwd_kernel(const float* __restrict__ W, GateOffsets off,
-                                    const int* __restrict__ lam, const float2* __restrict__ lamf,
-                                    float* __restrict__ hid, float* __restrict__ GL, int C, int B) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= B * kGates * C) return;
-  const int c = g % C, i = (g / C) % kGates, b = g / (C * kGates);
-  const float2 L = lamf[lam[b]];
-  const float* L1 = W + off.l1[i];
-  const float* L2 = W + off.l2[i];
-  float acc = 0.f;
-  for (int j = 0; j < kGateHidden; ++j) {
-    const float h = fmaf(L.x, L1[j], L.y * L1[kGateHidden + j]);
-    if (c == 0) hid[((long long)b * kGates + i) * kGateHidden + j] = h;
-    acc = fmaf(fmaxf(h, 0.f), L2[j * C + c], acc);
-  }
-  GL[((long long)b * kGates + i) * C + c] = 1.f + tanhf(acc);
-}
-
-// Gradients of the lambda-gates' weights from dGL[b][i][c], one thread per
-// weight (sums over the samples, and over the channels for L1, in order):
-//   dz = dGL (1 - (GL - 1)^2);  dL2_i[j][c] = sum_b relu(hid_bij) dz_bic
-//   dL1_i[d][j] = sum_b lam2_b[d] [hid_bij > 0] sum_c L2_i[j][c] dz_bic
-__global__ void lam_gate_bwd_kernel(const float* __restrict__ W, GateOffsets off,
-                                    const int* __restrict__ lam, const float2* __restrict__ lamf,
-                                    const float* __restrict__ hid, const float* __restrict__ GL,
-                                    const float* __restrict__ dGL, float* __restrict__ G, int C,
-                                    int B) {
-  const int per = 2 * kGateHidden + kGateHidden * C;   // L1 then L2 entries of one gate
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= kGates * per) return;
-  const int i = g / per, e = g % per;
-  const float* L2 = W + off.l2[i];
-  if (e < 2 * kGateHidden) {
-    const int d = e / kGateHidden, j = e % kGateHidden;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) {
-      const long long bi = (long long)b * kGates + i;
-      if (!(hid[bi * kGateHidden + j] > 0.f)) continue;
-      float t = 0.f;
-      for (int c = 0; c < C; ++c) {
-        const float gl = GL[bi * C + c] - 1.f;
-        t = fmaf(L2[j * C + c], dGL[bi * C + c] * (1.f - gl * gl), t);
-      }
-      const float2 L = lamf[lam[b]];
-      s = fmaf(d == 0 ? L.x : L.y, t, s);
-    }
-    G[off.l1[i] + e] = s;
-  } else {
-    const int jc = e - 2 * kGateHidden, j = jc / C, c = jc % C;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) {
-      const long long bi = (long long)b * kGates + i;
-      const float gl = GL[bi * C + c] - 1.f;
-      s = fmaf(fmaxf(hid[bi * kGateHidden + j], 0.f), dGL[bi * C + c] * (1.f - gl * gl), s);
-    }
-    G[off.l2[i] + jc] = s;
-  }
-}
 
 // Adam step on FP32 master weights: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 // w -= lr_t m / (sqrt(v) + eps), lr_t = lr sqrt(1-b2^t) / (1-b1^t).

@@ -95,8 +95,8 @@ def test_loss_and_gradients_match_the_oracle():
             assert abs(float(g @ d) - fd) <= 2e-3 * max(abs(fd), 1e-2 * np.linalg.norm(g)), (g @ d, fd)
         shapes = LO.param_shapes(C)
         offs = np.cumsum([0] + [int(np.prod(s)) for s in shapes])
-        # conv 0, 4, 8; A1_2, A2_5, L1_1, L2_6
-        for t in (0, 4, 8, 9 + 2, 17 + 5, 25 + 1, 33 + 6):
+        # conv 0, 4, 8; A1_2, A2_5
+        for t in (0, 4, 8, 9 + 2, 17 + 5):
             j = int(offs[t] + rng.integers(offs[t + 1] - offs[t]))
             e_j = np.zeros(w.size)
             e_j[j] = 1.0
@@ -115,7 +115,8 @@ def _tol(eps, N, m, C):
 def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, gs):
     """Seeded weights (gates 1, then gates away from 1) in the oracle's
     learned P_eps^{-1} with its own calibration; FP32 activations.  The
-    steps and residual ratios of the GPU's calibration match the oracle's."""
+    residual ratios of the GPU's calibration (which follow from its one
+    step) match the oracle's."""
     import torch
     p, a = small_problem(True, C, m, N, eps)
     ps, w = seeded_weights(C, 50 + m, gs)
@@ -131,8 +132,8 @@ def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, gs):
     h = O.MGHierarchy(K, m)
     lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
     params = LO.unflatten(w.astype(np.float64), C)
-    alphas, rr = LO.calibrate(h, lc, params, 1.0 / N, eps, N)
-    ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alphas)
+    alpha, rr = LO.calibrate(h, lc, params, 1.0 / N, eps, N)
+    ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alpha)
     err = float(np.max(np.abs(z - ref)) / np.max(np.abs(ref)))
     assert err <= _tol(eps, N, m, C), (err, _tol(eps, N, m, C))
     np.testing.assert_allclose(ratios, rr, atol=1e-3)
@@ -194,16 +195,14 @@ def test_training_lowers_the_loss():
 TRAIN_STEPS = 1500
 
 
-def test_trained_correction_gains_over_the_vcycle():
-    """A/B/C at 127^2 x 64 (a = exp(GRF)): FGMRES with the multigrid
-    preconditioner alone, with the learned route at zero weights (the
-    V-cycle, the smoothing sweep and the calibrated step, without a
-    correction) and with trained weights.  The trained correction must take
-    fewer FGMRES iterations than both; every arm reaches the sequential
-    stepping solution."""
+def abc_arms(m, N, rtol):
+    """FGMRES(30) iterations, error against sequential stepping and true
+    relative residual for the three arms on a = exp(GRF) at m^2 x N: the
+    multigrid preconditioner alone ("mg"), the learned route at zero
+    weights ("zero": the V-cycle, the smoothing sweep and the calibrated
+    step without a correction) and the learned route trained on the GPU."""
     import torch
     from paper_2002_01108_gb300 import Problem
-    m, N = 127, 64
     eps = math.sqrt(1.0 / N) / 2
     a = O.node_coefficient(grf_log_coefficient(seed=5, m=m))
     case = heat_case_2d(seed=6, m=m, N=N, eps=eps)
@@ -220,9 +219,10 @@ def test_trained_correction_gains_over_the_vcycle():
                 p.set_learned_weights(np.zeros(p.learned_weights().size, np.float32))
             if arm == "trained":
                 hist = p.learned_train(steps=TRAIN_STEPS, batch=16, lr=2e-3, seed=3)
-                print("training loss", hist[:3], hist[-3:])
+                print(f"{m}^2 x {N} training loss", hist[:3], hist[-3:])
+                assert np.all(np.isfinite(hist))
                 assert hist[-50:].mean() < 0.2 * hist[:5].mean()
-            u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, flexible=True)
+            u, info = p.gmres_solve(fd, restart=30, rtol=rtol, maxit=400, flexible=True)
             torch.cuda.synchronize()
             err = float(np.linalg.norm(u.cpu().numpy() - u_ref) / np.linalg.norm(u_ref))
             extra = ()
@@ -230,19 +230,35 @@ def test_trained_correction_gains_over_the_vcycle():
                 ratios = p.learned_residual_ratios()
                 extra = (p.learned_fallbacks, float(np.mean(ratios)))
             res[arm] = (info["iters"], err, info["true_relres"]) + extra
-    print("A/B/C", res)
+    print(f"A/B/C {m}^2 x {N}", res)
     for arm, (it, err, rr, *_) in res.items():
-        assert rr <= 1.01e-10 and err <= 1e-8, (arm, it, err, rr)
+        assert rr <= 1.01 * rtol and err <= 1e-8, (arm, it, err, rr)
+    return res
+
+
+def test_trained_correction_gains_over_the_vcycle():
+    """A/B/C at 63^2 x 32: the trained correction takes fewer FGMRES
+    iterations than the V-cycle alone and than the route at zero weights;
+    every arm reaches the sequential stepping solution."""
+    res = abc_arms(63, 32, 1e-10)
+    assert res["trained"][0] < res["mg"][0], res
+    assert res["trained"][0] < res["zero"][0], res
+
+
+def test_trained_correction_gains_at_127():
+    """A/B/C at 127^2 x 64, as at 63^2 x 32."""
+    res = abc_arms(127, 64, 1e-10)
     assert res["trained"][0] < res["mg"][0], res
     assert res["trained"][0] < res["zero"][0], res
 
 
 def test_learned_route_at_the_workload_size():
     """The learned form at the size bench.py times: 255^2 x 256, a = exp(GRF),
-    eps = sqrt(tau)/2, trained on the GPU: FGMRES(30) reaches RES 1e-8 (the
-    benchmark's tolerance), and solved on to RES 1e-10 its solution equals
-    sequential stepping to 1e-8.  Its iteration count against the V-cycle's
-    is printed."""
+    eps = sqrt(tau)/2, trained on the GPU as bench.py trains it (4000 steps,
+    lr 1e-3): FGMRES(30) reaches RES 1e-8 (the benchmark's tolerance), and
+    solved on to RES 1e-10 its solution equals sequential stepping to 1e-8.
+    Its iteration count against the V-cycle's is printed (at this size the
+    correction does not gain)."""
     import torch
     from paper_2002_01108_gb300 import Problem
     m, N = 255, 256
@@ -258,10 +274,11 @@ def test_learned_route_at_the_workload_size():
         _, info_mg = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
     with Problem(2, m, N, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
         p.set_eps(eps)
-        p.learned_train(steps=TRAIN_STEPS, batch=16, lr=2e-3, seed=3)
+        p.learned_train(steps=4000, batch=16, lr=1e-3, seed=3)
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
         assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8, info
-        print(f"255^2 x 256: V-cycle {info_mg['iters']} iterations, learned {info['iters']}")
+        print(f"255^2 x 256: V-cycle {info_mg['iters']} iterations, learned {info['iters']}",
+              "fallbacks", p.learned_fallbacks, "mean ratio", float(np.mean(p.learned_residual_ratios())))
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, maxit=400, flexible=True)
         torch.cuda.synchronize()
     assert info["converged"] == 1 and info["true_relres"] <= 1.01e-10, info

@@ -1,10 +1,13 @@
 """Pins of the learned-correction oracle (oracle/learned_oracle.py): the
 convolution against scipy.signal.correlate2d, the transfers against the
 multigrid oracle's P and R, the gates against loops written from their
-definition, linearity in the residual, the coarse-grid target against a
-dense solve, the loss's normalisation, the step and calibration rules, the
-calibration generator against SplitMix64's published first output, and the
-whole learned P_eps^{-1} against banded LU with an exact correction."""
+definition, complex-linearity in the residual and the conjugation symmetry
+of real residue operators, analyticity in the shift (Cauchy-Riemann), the
+poles against Lanczos eigenvalues and the sign of their weights, the
+coarse-grid target against a dense solve, the loss's normalisation, the step
+and calibration rules, the calibration generator against SplitMix64's
+published first output, and the whole learned P_eps^{-1} against banded LU
+with an exact correction."""
 import math
 
 import numpy as np
@@ -56,11 +59,11 @@ def test_parameter_layout():
     w = LO.flatten(ps)
     assert w.size == LO.num_params(C)
     back = LO.unflatten(w, C)
-    for key in ("W", "A1", "A2", "L1", "L2"):
+    for key in ("W", "A1", "A2"):
         for a, b in zip(ps[key], back[key]):
             np.testing.assert_array_equal(a, b)
-    assert back["W"][0].shape == (3, 3, 2, C) and back["W"][8].shape == (3, 3, C, 2)
-    assert back["A2"][7].shape == (3, 3, LO.NA, C) and back["L2"][0].shape == (LO.NL, C)
+    assert back["W"][0].shape == (3, 3, 1, C) and back["W"][8].shape == (3, 3, C, LO.N_POLES)
+    assert back["A2"][7].shape == (3, 3, LO.NA, C) and len(back) == 3
 
 
 def _conv_loops(x, W):
@@ -82,8 +85,8 @@ def _conv_loops(x, W):
 
 
 def test_gates_follow_their_definition():
-    """GA_i and GL_i against loops written from the definition, on a 7 x 7
-    network grid; and all gates are exactly 1 when A2 = L2 = 0."""
+    """GA_i against loops written from the definition, on a 7 x 7 network
+    grid; and all gates are exactly 1 when A2 = 0."""
     C = 3
     ps = LO.init_params(C, seed=3, gate_scale=0.4)
     tr = LO.Transfers(7)
@@ -94,20 +97,8 @@ def test_gates_follow_their_definition():
         lv = LO.GATE_LEVEL[i]
         z = _conv_loops(np.maximum(_conv_loops(la[lv][None], ps["A1"][i]), 0.0), ps["A2"][i])
         np.testing.assert_allclose(GA[i], 1.0 + np.tanh(z), rtol=1e-13, atol=1e-14)
-    lam = 0.3 - 0.7j
-    GL = LO.lam_gates(ps, lam)
-    for i in (1, 7):
-        ref = np.zeros(C)
-        for c in range(C):
-            acc = 0.0
-            for j in range(LO.NL):
-                hj = lam.real * ps["L1"][i][0, j] + lam.imag * ps["L1"][i][1, j]
-                acc += max(hj, 0.0) * ps["L2"][i][j, c]
-            ref[c] = 1.0 + math.tanh(acc)
-        np.testing.assert_allclose(GL[i], ref, rtol=1e-14)
     flat = LO.init_params(C, seed=3, gate_scale=0.0)
     assert all(np.all(g == 1.0) for g in LO.a_gates(flat, la))
-    assert all(np.all(g == 1.0) for g in LO.lam_gates(flat, lam))
     # the level fields are restrictions of level 0
     np.testing.assert_allclose(la[1], tr.restrict(0, la[0][None])[0])
 
@@ -125,6 +116,9 @@ def test_correction_is_linear_in_the_residual_and_lives_on_the_coarse_grid():
     e1, e2 = lc(ps, r1, lam), lc(ps, r2, lam)
     e12 = lc(ps, 2.5 * r1 - 0.75 * r2, lam)
     np.testing.assert_allclose(e12, 2.5 * e1 - 0.75 * e2, rtol=1e-11, atol=1e-13 * np.abs(e12).max())
+    # complex-linear, not only real-linear
+    ez = lc(ps, (0.6 - 1.3j) * r1, lam)
+    np.testing.assert_allclose(ez, (0.6 - 1.3j) * e1, rtol=1e-11, atol=1e-13 * np.abs(ez).max())
     # the correction is a prolongation of a coarse field
     ec = lc.coarse(ps, r1, lam)
     np.testing.assert_allclose(e1.reshape(-1), lc.P0 @ ec.reshape(-1), atol=1e-14)
@@ -133,6 +127,71 @@ def test_correction_is_linear_in_the_residual_and_lives_on_the_coarse_grid():
     # no last layer: no correction
     z = dict(ps, W=ps["W"][:8] + [np.zeros_like(ps["W"][8])])
     assert np.all(lc(z, r1, lam) == 0.0)
+
+
+def test_residues_are_real_operators():
+    """Nc_j(x) = N_j(Re x) + i N_j(Im x): a real residual gives real residues,
+    the residues of conj(r) are the conjugates, and the correction has the
+    symmetry of the exact inverse, ec(conj lambda, conj r) = conj ec(lambda,
+    r), which the half-spectrum evaluation relies on; ec is the
+    pole-weighted sum of the residues."""
+    m = 31
+    rng = np.random.default_rng(8)
+    lc = LO.LearnedCorrection(m, rng.standard_normal((m + 2, m + 2)) * 0.3, 1 / 16)
+    ps = LO.init_params(4, seed=2, gate_scale=0.4)
+    r = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    rc = (lc.R0 @ r.reshape(-1)).reshape(lc.mc, lc.mc)
+    nc = lc.residues(ps, rc)
+    assert nc.shape == (LO.N_POLES, lc.mc, lc.mc) and np.abs(nc).max() > 1e-3
+    assert np.all(lc.residues(ps, rc.real + 0j).imag == 0.0)
+    np.testing.assert_allclose(lc.residues(ps, np.conj(rc)), np.conj(nc), rtol=1e-13,
+                               atol=1e-15 * np.abs(nc).max())
+    lam = 0.5 - 0.2j
+    ec = lc.coarse(ps, r, lam)
+    np.testing.assert_allclose(lc.coarse(ps, np.conj(r), np.conj(lam)), np.conj(ec), rtol=1e-13,
+                               atol=1e-15 * np.abs(ec).max())
+    w = lc.sig / (lam + lc.sig)
+    np.testing.assert_allclose(ec, sum(w[j] * nc[j] for j in range(LO.N_POLES)), rtol=1e-12,
+                               atol=1e-14 * np.abs(ec).max())
+    # one forward pass per plane: the real part's residues come from Re x alone
+    y = LO.forward(ps, (rc.real / lc.sig[0])[None], LO.a_gates(ps, lc.la_levels), lc.tr)
+    np.testing.assert_allclose(nc.real, y, rtol=1e-13, atol=1e-15 * np.abs(y).max())
+
+
+def test_correction_is_analytic_in_the_shift():
+    """ec(lambda) satisfies the Cauchy-Riemann equations: its difference
+    quotients along a real and along an imaginary step agree (d ec / d
+    conj(lambda) = 0), at points of the backward-Euler circle and off it,
+    with gates away from 1.  A dependence on Re lambda, Im lambda or
+    |lambda| separately fails this by O(1)."""
+    m = 15
+    rng = np.random.default_rng(22)
+    lc = LO.LearnedCorrection(m, rng.standard_normal((m + 2, m + 2)) * 0.4, 1 / 32)
+    ps = LO.init_params(4, seed=23, gate_scale=0.4)
+    r = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    d = 1e-5
+    for lam in (0.02 - 0.01j, 0.6 + 0.9j, 1.9 - 0.1j, 0.3 + 0.0j):
+        dre = (lc.coarse(ps, r, lam + d) - lc.coarse(ps, r, lam - d)) / (2 * d)
+        dim = (lc.coarse(ps, r, lam + 1j * d) - lc.coarse(ps, r, lam - 1j * d)) / (2j * d)
+        assert np.abs(dre).max() > 1e-6
+        assert np.abs(dre - dim).max() <= 1e-6 * np.abs(dre).max(), lam
+
+
+def test_pole_weights_are_bounded_on_the_right_half_plane():
+    """w_j = sigma_j / (lambda + sigma_j) with sigma_j > 0: |w_j| < 1 where
+    Re lambda > 0 (every lambda_k of backward Euler, 1 - eps^{1/N}
+    e^{-2 pi i k/N}), w_j -> 1 as lambda -> 0 and -> 0 as |lambda| grows (a
+    pole on the wrong side, sigma_j / (lambda - sigma_j), breaks the bound
+    near lambda = sigma_j)."""
+    sig = LO.pole_shifts(1 / 64, 1.3, 127)
+    assert np.all(sig > 0) and np.all(np.diff(sig) > 0)
+    lam = np.concatenate([LO.forward_sign_eigs(64, 1 / 16), LO.forward_sign_eigs(256, 1 / 32),
+                          sig[:3]])
+    for l in lam:
+        w = LO.pole_weights(l, sig)
+        assert np.all(np.abs(w) < 1.0)
+    np.testing.assert_allclose(LO.pole_weights(1e-12, sig), 1.0, rtol=1e-9)
+    assert np.all(np.abs(LO.pole_weights(1e9, sig)) < 1e-3)
 
 
 def test_coarse_target_solves_the_galerkin_system():
@@ -169,22 +228,28 @@ def test_loss_is_the_mean_of_the_per_sample_relative_errors():
 
 
 @pytest.mark.parametrize("a", [0.5, 2.0])
-def test_output_scale_is_the_inverse_shifted_operator_on_its_smoothest_mode(a):
-    """For a constant coefficient, the smallest eigenvalue of the 5-point K(a)
-    (shift-invert Lanczos on the assembled matrix, no formula) is a mu_min,
-    and |lambda + tau a mu_min|^-1 is the size of B_k^{-1} on that mode.
-    output_scale uses the continuum value mu_min -> 2 pi^2, which agrees to
-    O(h^2): here pi^2 h^2 / 12 < 2.5e-4 of mu_min."""
-    m, N, eps = 63, 32, 0.05
+def test_poles_span_the_spectrum_of_the_coarse_operator(a):
+    """For a constant coefficient the poles run from the shift of the
+    smoothest mode to the largest eigenvalue on the grid of spacing 2h, both
+    found by Lanczos on assembled matrices (no formula): sigma_0 = tau a 2 pi^2
+    against tau mu_min of the fine 5-point K(a) (the continuum value, O(h^2)
+    off: pi^2 h^2 / 12 < 2.5e-4), and sigma_top = 2 tau a (m+1)^2 against
+    tau mu_max of the 5-point K(a) on the 2h grid (1 - mu_max / (8 a / (2h)^2)
+    = sin^2(pi h) = O(h^2), 2.4e-3 here); the poles are geometric."""
+    m, N = 63, 32
     tau = 1.0 / N
     K = O.fd_stiffness_varcoef(np.full((m + 2, m + 2), a))
     mu_min = float(spla.eigsh(K.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0])
-    assert mu_min == pytest.approx(a * 2.0 * math.pi ** 2, rel=2.5e-4)
-    for lam in LO.forward_sign_eigs(N, eps):
-        ref = 1.0 / abs(lam + tau * mu_min)
-        assert LO.output_scale(lam, tau, a) == pytest.approx(ref, rel=2.5e-4)
+    mc = (m - 1) // 2
+    Kc = O.fd_stiffness_varcoef(np.full((mc + 2, mc + 2), a))
+    mu_max = float(spla.eigsh(Kc.tocsc(), k=1, which="LA", return_eigenvectors=False)[0])
     lc = LO.LearnedCorrection(m, np.full((m + 2, m + 2), math.log(a)), tau)
     assert lc.a_mean == pytest.approx(a, rel=1e-14)
+    sig = lc.sig
+    assert sig.size == LO.N_POLES
+    assert sig[0] == pytest.approx(tau * mu_min, rel=2.5e-4)
+    assert tau * mu_max <= sig[-1] <= tau * mu_max * (1 + 3e-3)
+    np.testing.assert_allclose(sig[1:] / sig[:-1], sig[1] / sig[0], rtol=1e-12)
 
 
 def test_correction_with_an_exact_network_lands_on_the_solution():
@@ -275,7 +340,7 @@ def test_learned_pinv_with_an_exact_network_is_the_exact_inverse():
     """With exact shifted solves in place of the network and alpha = 1 the
     learned route is P_eps^{-1} itself: this pins the forward-sign pairing of
     lambda'_k, the half spectrum and the complex-to-real inverse against
-    banded LU; the calibration then finds alpha = 1 everywhere."""
+    banded LU; the calibration then finds alpha = 1."""
     m, N, eps = 15, 8, 0.1
     tau = 1.0 / N
     log_a, K = _varcoef_case(m, 17)
@@ -284,11 +349,9 @@ def test_learned_pinv_with_an_exact_network_is_the_exact_inverse():
     y = np.random.default_rng(18).standard_normal((N, m, m))
     exact = lambda res, lam_: spla.spsolve((lam_ * sp_identity(m * m) + tau * K).tocsc(),
                                            res.reshape(-1))
-    alphas, ratios = LO.calibrate(h, lc, None, tau, eps, N, net=exact)
-    # the ratio is sqrt(||res||^2 - |<B d, res>|^2 / ||B d||^2) / ||res||: a
-    # difference of nearly equal sums, so about half the digits survive
-    assert np.all(np.abs(alphas - 1.0) < 1e-9) and np.all(ratios < 1e-6)
-    z = LO.apply_Pinv_learned(y, h, lc, None, tau, eps, alphas, net=exact)
+    alpha, ratios = LO.calibrate(h, lc, None, tau, eps, N, net=exact)
+    assert abs(alpha - 1.0) < 1e-10 and np.all(ratios < 1e-9)
+    z = LO.apply_Pinv_learned(y, h, lc, None, tau, eps, alpha, net=exact)
     ref = O.apply_Pinv_lu(y, sp_identity(m * m), K, tau, eps)
     np.testing.assert_allclose(z, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
     np.testing.assert_allclose(LO.forward_sign_eigs(N, eps), np.conj(O.eps_circulant_eigs(N, eps)[:N // 2 + 1]),
@@ -296,9 +359,9 @@ def test_learned_pinv_with_an_exact_network_is_the_exact_inverse():
 
 
 def test_learned_pinv_with_zero_steps_is_the_multigrid_route():
-    """alpha_k = 0 at every frequency keeps the V-cycle's iterates: the route
-    is then the multigrid P_eps^{-1} (the fallback); with the calibrated
-    steps it is linear in y."""
+    """alpha = 0 keeps the V-cycle's iterates: the route is then the
+    multigrid P_eps^{-1} (the fallback); with the calibrated step it is
+    linear in y."""
     m, N, eps = 15, 8, 0.05
     tau = 1.0 / N
     log_a, K = _varcoef_case(m, 19)
@@ -307,7 +370,7 @@ def test_learned_pinv_with_zero_steps_is_the_multigrid_route():
     ps = LO.init_params(4, seed=21, gate_scale=0.3)
     rng = np.random.default_rng(20)
     y1, y2 = rng.standard_normal((2, N, m, m))
-    z0 = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, np.zeros(N // 2 + 1))
+    z0 = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, 0.0)
     # the multigrid route on the same half spectrum
     d = O.eps_scaling(N, eps)
     yt = np.fft.rfft(d[:, None] * y1.reshape(N, -1), axis=0)
@@ -315,8 +378,9 @@ def test_learned_pinv_with_zero_steps_is_the_multigrid_route():
     zt = np.array([O.mg_vcycle(h, lam[k], tau, yt[k]) for k in range(N // 2 + 1)])
     ref = (np.fft.irfft(zt, n=N, axis=0) / d[:, None]).reshape(y1.shape)
     np.testing.assert_allclose(z0, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
-    alphas, _ = LO.calibrate(h, lc, ps, tau, eps, N)
-    za = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, alphas)
-    zb = LO.apply_Pinv_learned(y2, h, lc, ps, tau, eps, alphas)
-    zab = LO.apply_Pinv_learned(0.5 * y1 - 2.0 * y2, h, lc, ps, tau, eps, alphas)
+    alpha, _ = LO.calibrate(h, lc, ps, tau, eps, N)
+    assert alpha != 0.0
+    za = LO.apply_Pinv_learned(y1, h, lc, ps, tau, eps, alpha)
+    zb = LO.apply_Pinv_learned(y2, h, lc, ps, tau, eps, alpha)
+    zab = LO.apply_Pinv_learned(0.5 * y1 - 2.0 * y2, h, lc, ps, tau, eps, alpha)
     np.testing.assert_allclose(zab, 0.5 * za - 2.0 * zb, rtol=1e-10, atol=1e-12 * np.abs(zab).max())
