@@ -344,10 +344,30 @@ bec_status bec_learned_loss_grad(bec_problem* p, int B, const int* lam_idx,
                                  const double* r, const double* e_target,
                                  double* loss, float* grad);
 
-/* 1 when the last calibration found no step (alpha = 0, the V-cycle's
- * iterates kept: the sums vanish or are not finite), else 0; -1: not
- * learned.  Synchronises. */
+/* 1 when the last calibration kept the V-cycle's iterates (alpha = 0: the
+ * minimal-residual sums vanish or are not finite, or the judge rejected the
+ * correction), else 0; -1: not learned.  Synchronises. */
 long long bec_learned_fallbacks(bec_problem* p);
+
+/* The judge (on by default; on = 0 turns it off, as for checking the
+ * correction's arithmetic against a reference): after the calibrated step is
+ * found, 10 power iterations per frequency on the error operator
+ * E_k = I - M_k B_k of one apply, from the calibration right-hand side
+ * normalised per frequency, once with M_k the V-cycle alone and once with
+ * the corrected preconditioner.  The last ||E_k v|| (||v|| = 1) estimates
+ * E_k's spectral radius.  The correction is kept only when its largest
+ * estimate over k is below the V-cycle's; otherwise alpha = 0 for all
+ * frequencies and P_eps^{-1} is the multigrid route's.  The multigrid's
+ * work per calibration grows by 20 V-cycles and 10 network applies.
+ * Changing the setting recalibrates at the next apply. */
+bec_status bec_learned_set_judge(bec_problem* p, int on);
+
+/* The judge's estimates of the last calibration, host array of
+ * 2 (N/2+1) + 2 doubles: the V-cycle's radius per frequency k = 0..N/2, the
+ * corrected preconditioner's per frequency, then the two maxima.  NaN when
+ * the judge is off or no calibration ran since the weights, eps or the
+ * setting changed.  Synchronises. */
+bec_status bec_learned_judge_radii(bec_problem* p, double* host);
 
 /* ||b_k - B_k x_k|| after the calibrated step divided by the V-cycle's
  * ||b_k - B_k x_k||, for every frequency k = 0..N/2, on the calibration's

@@ -69,8 +69,12 @@ damped-Jacobi sweep follows (the post-smoothing of a prolonged correction),
 and the step from the V-cycle's iterate is scaled by one complex alpha, the
 same for every frequency (a per-frequency step would again depend on k
 non-analytically), fixed by one calibration apply: the minimal-residual
-step over all frequencies on a fixed right-hand side; alpha = 0 keeps the
-V-cycle's result (the multigrid is the fallback).
+step over all frequencies on a fixed right-hand side.  Then the multigrid
+judges the result: power iterations on the error operator I - M_k A_k of
+the V-cycle alone and of the corrected preconditioner estimate their
+spectral radii, and unless the corrected one's largest radius over k is the
+smaller, alpha = 0, which keeps the V-cycle's result (the multigrid is the
+fallback).
 """
 from __future__ import annotations
 
@@ -348,13 +352,49 @@ def forward_sign_eigs(N: int, eps: float) -> np.ndarray:
     return 1.0 - eps ** (1.0 / N) * np.exp(-2j * np.pi * k / N)
 
 
+JUDGE_ITERS = 10
+
+
+def judge_radii(h, lc: LearnedCorrection, params, tau: float, eps: float, N: int, alpha,
+                omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None, iters: int = JUDGE_ITERS):
+    """The judge's estimates of the spectral radius of E_k = I - M_k A_k per
+    frequency k = 0..N/2: `iters` power iterations v <- E_k v / ||E_k v|| from
+    the calibration right-hand side normalised, the last ||E_k v||; once for
+    M_k the V-cycle alone and once for the corrected preconditioner (V-cycle,
+    correction, sweep, step alpha).  Returns (rho_vcycle, rho_corrected)."""
+    from .bec_oracle import mg_vcycle
+    lam = forward_sign_eigs(N, eps)
+    m = lc.m
+    B = calibration_rhs(N // 2 + 1, m * m)
+    out = np.zeros((2, N // 2 + 1))
+    for k in range(N // 2 + 1):
+        A = h.op(0, lam[k], tau)
+        for arm in (0, 1):
+            v = B[k] / np.linalg.norm(B[k])
+            for _ in range(iters):
+                r = -(A @ v)
+                z = mg_vcycle(h, lam[k], tau, r, omega, nu1, nu2)
+                if arm == 1:
+                    z, _ = correct(params, lc, A, r, z, lam[k], alpha, omega, net)
+                v = v + z
+                rho = float(np.linalg.norm(v))
+                if rho > 0.0:
+                    v = v / rho
+            out[arm, k] = rho
+    return out[0], out[1]
+
+
 def calibrate(h, lc: LearnedCorrection, params, tau: float, eps: float, N: int,
-              omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None):
+              omega: float = 0.8, nu1: int = 1, nu2: int = 1, net=None, judge: bool = True):
     """The one step alpha for all frequencies from one calibration apply: the
     V-cycle and the correction on calibration_rhs at every k = 0..N/2, then
     the minimal-residual step of the stacked system, alpha = sum_k <A_k d_k,
     res_k> / sum_k ||A_k d_k||^2 (0 when the sums vanish or are not finite).
-    Returns (alpha, ratios), ratios[k] = ||res_k - alpha A_k d_k|| / ||res_k||."""
+    With judge, the multigrid then judges the corrected preconditioner
+    (judge_radii): unless its largest radius estimate over k is below the
+    V-cycle's, alpha = 0.  Returns (alpha, ratios, radii): ratios[k] =
+    ||res_k - alpha A_k d_k|| / ||res_k|| for the minimal-residual alpha,
+    radii = judge_radii's pair (None without judge)."""
     from .bec_oracle import mg_vcycle
     lam = forward_sign_eigs(N, eps)
     m = lc.m
@@ -370,7 +410,12 @@ def calibrate(h, lc: LearnedCorrection, params, tau: float, eps: float, N: int,
     ok = dd > 0 and math.isfinite(dd) and math.isfinite(cr.real) and math.isfinite(cr.imag)
     alpha = cr / dd if ok else 0.0
     ratios = [float(np.linalg.norm(res - alpha * Ad) / np.linalg.norm(res)) for res, Ad in pairs]
-    return alpha, np.array(ratios)
+    radii = None
+    if judge:
+        radii = judge_radii(h, lc, params, tau, eps, N, alpha, omega, nu1, nu2, net)
+        if not radii[1].max() < radii[0].max():
+            alpha = 0.0
+    return alpha, np.array(ratios), radii
 
 
 def apply_Pinv_learned(y: np.ndarray, h, lc: LearnedCorrection, params, tau: float, eps: float,

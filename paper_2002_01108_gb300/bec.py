@@ -31,6 +31,7 @@ EXPORTED = (
     "bec_batch_kernel_launches", "bec_batch_free", "bec_learned_num_weights",
     "bec_learned_get_weights", "bec_learned_set_weights", "bec_learned_train",
     "bec_learned_loss_grad", "bec_learned_fallbacks", "bec_learned_residual_ratios",
+    "bec_learned_set_judge", "bec_learned_judge_radii",
     "bec_convert_to_float", "bec_convert_to_double", "bec_reciprocal_fp64", "bec_autotune",
     "bec_set_tiles",
     "bec_inject_fault",
@@ -132,6 +133,8 @@ def _lib():
                                   ctypes.c_int),
         "bec_learned_fallbacks": ([P], ctypes.c_longlong),
         "bec_learned_residual_ratios": ([P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bec_learned_set_judge": ([P, ctypes.c_int], ctypes.c_int),
+        "bec_learned_judge_radii": ([P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bec_autotune": ([P, ctypes.c_int, ctypes.POINTER(TuneReport)], ctypes.c_int),
         "bec_inject_fault": ([ctypes.c_int], ctypes.c_int),
         "bec_set_tiles": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -460,6 +463,18 @@ class Problem:
     @property
     def learned_fallbacks(self) -> int:
         return int(_lib().bec_learned_fallbacks(self._p))
+
+    def set_learned_judge(self, on: bool):
+        _check(_lib().bec_learned_set_judge(self._p, 1 if on else 0), "bec_learned_set_judge")
+
+    def learned_judge_radii(self):
+        """(rho_vcycle[N/2+1], rho_corrected[N/2+1], max_vcycle, max_corrected)
+        of the last calibration (NaN when the judge was off)."""
+        K = self.N // 2 + 1
+        out = np.empty(2 * K + 2)
+        _check(_lib().bec_learned_judge_radii(self._p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "bec_learned_judge_radii")
+        return out[:K], out[K:2 * K], float(out[2 * K]), float(out[2 * K + 1])
 
     def learned_residual_ratios(self):
         """Per frequency k <= N/2, from the calibration apply: the residual after

@@ -163,6 +163,8 @@ bec_status bec_batch_solve(bec_batch* b, const double* const* f, double* const* 
     if (f[i] == nullptr || u[i] == nullptr) return batch_einval("null vector pointer");
     if ((reinterpret_cast<uintptr_t>(f[i]) & 15u) || (reinterpret_cast<uintptr_t>(u[i]) & 15u))
       return batch_einval("f[i] and u[i] must be 16-byte aligned");
+    const bec_status sp = bec::net_prepare(p);
+    if (sp != BEC_OK) return sp;
     bec::gmres_run_init(runs[i], p, f[i], u[i], *opts, b->use_graphs != 0);
   }
   if (b->persistent) {

@@ -674,6 +674,18 @@ long long bec_learned_fallbacks(bec_problem* p) {
   return net_fallbacks(p);
 }
 
+bec_status bec_learned_set_judge(bec_problem* p, int on) {
+  BEC_TRY(need_net(p));
+  net_set_judge(p, on != 0);
+  return BEC_OK;
+}
+
+bec_status bec_learned_judge_radii(bec_problem* p, double* host) {
+  BEC_TRY(need_net(p));
+  if (host == nullptr) return einval("null host pointer");
+  return net_judge_radii(p, host);
+}
+
 bec_status bec_learned_residual_ratios(bec_problem* p, double* host) {
   BEC_TRY(need_net(p));
   if (host == nullptr) return einval("null host pointer");

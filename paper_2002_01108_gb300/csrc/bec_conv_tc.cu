@@ -205,12 +205,14 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_im
   return c;
 }
 
-// out[img][y][x][0 .. STORE_C) = act(conv(in)), act = ReLU when RELU
-template <int CIN, int COUT, int STORE_C, bool RELU>
+// out[img][y][x][0 .. STORE_C) = conv(in) (times gate[y][x][c] when gate is
+// not null: a gated layer's point-by-point gate, applied to the FP32
+// accumulators before the one rounding to BF16)
+template <int CIN, int COUT, int STORE_C>
 __global__ void __launch_bounds__(kThreads, 2)
 conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16* __restrict__ wt,
-                  __nv_bfloat16* __restrict__ out, int m, int tiles_x, int tiles_img, int ntiles,
-                  int withhold, int* __restrict__ err) {
+                  __nv_bfloat16* __restrict__ out, const float* __restrict__ gate, int m,
+                  int tiles_x, int tiles_img, int ntiles, int withhold, int* __restrict__ err) {
   using C = Cfg<CIN, COUT>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -340,17 +342,24 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
       const int x = c.x0 + tx, y = c.y0 + ty;
       if (tx < kTileX && x < m && y < m) {
         __nv_bfloat16* dst = out + (((long long)c.img * m + y) * m + x) * STORE_C;
+        if (gate != nullptr) {
+          static_assert(STORE_C % 4 == 0, "gated layers store whole float4 groups");
+          const float4* g4 = reinterpret_cast<const float4*>(gate + ((long long)y * m + x) * STORE_C);
+#pragma unroll
+          for (int k = 0; k < STORE_C / 4; ++k) {
+            const float4 gv = __ldg(g4 + k);
+            v[4 * k] *= gv.x;
+            v[4 * k + 1] *= gv.y;
+            v[4 * k + 2] *= gv.z;
+            v[4 * k + 3] *= gv.w;
+          }
+        }
         if constexpr (STORE_C % 8 == 0) {
           uint4 pk[STORE_C / 8];
           uint32_t* w32 = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
           for (int k = 0; k < STORE_C / 2; ++k) {
-            float a = v[2 * k], b = v[2 * k + 1];
-            if (RELU) {
-              a = fmaxf(a, 0.f);
-              b = fmaxf(b, 0.f);
-            }
-            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
             w32[k] = *reinterpret_cast<const uint32_t*>(&h);
           }
 #pragma unroll
@@ -358,7 +367,7 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
         } else {
 #pragma unroll
           for (int k = 0; k < STORE_C; ++k)
-            dst[k] = __float2bfloat16(RELU ? fmaxf(v[k], 0.f) : v[k]);
+            dst[k] = __float2bfloat16(v[k]);
         }
       }
     }
@@ -435,9 +444,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int CIN, int COUT, int STORE_C, bool RELU>
+template <int CIN, int COUT, int STORE_C>
 bec_status launch_tc(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat16* wt,
-                     __nv_bfloat16* out, int m, int B, int bmax, int* err) {
+                     __nv_bfloat16* out, const float* gate, int m, int B, int bmax, int* err) {
   using C = Cfg<CIN, COUT>;
   alignas(64) CUtensorMap map;
   const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)bmax};
@@ -452,7 +461,7 @@ bec_status launch_tc(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat1
     set_error("cuTensorMapEncodeTiled (activations)");
     return BEC_ECUDA;
   }
-  auto k = conv3x3_tc_kernel<CIN, COUT, STORE_C, RELU>;
+  auto k = conv3x3_tc_kernel<CIN, COUT, STORE_C>;
   static bool attr_set = false;
   if (!attr_set) {
     BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
@@ -467,8 +476,8 @@ bec_status launch_tc(bec_problem* p, const __nv_bfloat16* in, const __nv_bfloat1
   const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
   BEC_LAUNCH_BEGIN(p);
   const int withhold = g_withhold_loads.exchange(0);   // one-shot test hook
-  k<<<grid, kThreads, C::kSmem, p->stream>>>(map, wt, out, m, tiles_x, tiles_img, ntiles, withhold,
-                                             err);
+  k<<<grid, kThreads, C::kSmem, p->stream>>>(map, wt, out, gate, m, tiles_x, tiles_img, ntiles,
+                                             withhold, err);
   BEC_LAUNCH_CHECK(p, "net_conv_tc_kernel");
   return BEC_OK;
 }
@@ -499,16 +508,22 @@ bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* w
 }
 
 bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
-                      __nv_bfloat16* out, int m, int B, int bmax, int* err) {
+                      __nv_bfloat16* out, const float* gate, int m, int B, int bmax, int* err) {
   if (encode_fn() == nullptr || B < 1 || B > bmax || m < 1 || layer < 0 || layer >= kNetLayers) {
     set_error("tensor-core convolution: unsupported request");
     return BEC_EUNSUPPORTED;
   }
   const __nv_bfloat16* w = wt + layer_wt_offset(layer);
-  // no activation: the network's gates multiply the stored outputs
-  if (layer == 0) return launch_tc<16, 32, 32, false>(p, in, w, out, m, B, bmax, err);
-  if (layer == 8) return launch_tc<32, 16, kNetOut, false>(p, in, w, out, m, B, bmax, err);
-  return launch_tc<32, 32, 32, false>(p, in, w, out, m, B, bmax, err);
+  // no activation; a gated layer's gate is applied here when given
+  if (layer == 0) return launch_tc<16, 32, 32>(p, in, w, out, gate, m, B, bmax, err);
+  if (layer == 8) {
+    if (gate != nullptr) {
+      set_error("tensor-core convolution: the last layer has no gate");
+      return BEC_EUNSUPPORTED;
+    }
+    return launch_tc<32, 16, kNetOut>(p, in, w, out, nullptr, m, B, bmax, err);
+  }
+  return launch_tc<32, 32, 32>(p, in, w, out, gate, m, B, bmax, err);
 }
 
 }  // namespace bec

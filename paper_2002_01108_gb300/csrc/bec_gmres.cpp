@@ -42,7 +42,7 @@ bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* 
     if (learned && !net_calibrated(p)) BEC_TRY(net_calibrate(p));
     BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));
     BEC_TRY(mg_vcycle(p));
-    if (learned) BEC_TRY(net_correct(p));
+    if (learned && !net_rejected(p)) BEC_TRY(net_correct(p));
     return launch_time_inv(p, p->mg.lv[0].x, z, fp64);
   }
   const double n = (double)(p->m + 1);
@@ -337,6 +337,7 @@ bec_status gmres_run_result(const GmresRun& r) {
 
 bec_status gmres_solve_one(bec_problem* p, const double* f, double* u, const bec_gmres_opts* o,
                            bec_gmres_info* info) {
+  BEC_TRY(net_prepare(p));
   GmresRun r;
   gmres_run_init(r, p, f, u, *o, false);
   while (r.state != GmresRun::DONE) {

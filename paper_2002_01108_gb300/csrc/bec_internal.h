@@ -360,12 +360,21 @@ bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* w
                               __nv_bfloat16* wt);
 // output channels of the learned correction's network: one real plane per pole
 constexpr int kNetOut = 8;
-// out = conv3x3(in) of layer l (no activation: the network's gates follow):
-// l = 0 reads the 16-channel padded input planes, l = 8 stores its kNetOut
-// output channels
+// out = conv3x3(in) of layer l (no activation), times the layer's gate
+// [m^2][32] when gate is not null (layers 0..7): l = 0 reads the 16-channel
+// padded input planes, l = 8 stores its kNetOut output channels
 bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
-                      __nv_bfloat16* out, int m, int B, int bmax, int* err);
+                      __nv_bfloat16* out, const float* gate, int m, int B, int bmax, int* err);
 bec_status net_residual_ratios(bec_problem* p, double* host);
+// the calibration's spectral-radius test on (default) or off; recalibrates
+void net_set_judge(bec_problem* p, bool on);
+// the last calibration fell back to the V-cycle's iterates (alpha = 0)
+bool net_rejected(const bec_problem* p);
+// calibrates the learned route now when it is due (before a solve starts,
+// outside any graph capture); a no-op for other routes
+bec_status net_prepare(bec_problem* p);
+// per-frequency radii (V-cycle, corrected) and their maxima, 2K + 2 doubles
+bec_status net_judge_radii(bec_problem* p, double* host);
 
 // ---- stencils (bec_stencil.cu)
 // number of blocks (partial sums) the residual-norm kernel writes

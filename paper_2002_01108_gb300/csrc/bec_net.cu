@@ -92,6 +92,11 @@ struct NetState {
   bool gates_ok = false;         // GA matches the weights
   bool cal_ok = false;           // alpha matches the weights and eps
   bool bypass = false;           // the route acts as the multigrid route alone
+  bool judge = true;             // the calibration's spectral-radius test runs
+  bool rejected = false;         // the last calibration kept the V-cycle's iterates
+                                 // (read on the host: the applies skip the network)
+  double* jrho = nullptr;        // [2K + 2]: the judge's radii per frequency (V-cycle,
+                                 // corrected) and their maxima
   int nkry = 0;                  // recorded Krylov vectors (rows of the problem's V)
   double* kf = nullptr;          // U doubles: the recording solve's right-hand side
   double* ku = nullptr;          // U doubles: its solution
@@ -458,6 +463,67 @@ mr_alpha_kernel(const double* __restrict__ jpart, double* __restrict__ part,
   }
 }
 
+// kMrSplit blocks per frequency k: jpart[k kMrSplit + s] = the block's part
+// of ||v_k||^2 (FP32 per thread, FP64 across the block's threads in a fixed
+// order)
+__global__ void __launch_bounds__(256)
+knorm_parts_kernel(const float2* __restrict__ v, double* __restrict__ jpart, long long mff) {
+  __shared__ double red[256];
+  const int k = blockIdx.x, sblk = blockIdx.y;
+  float acc = 0.f;
+  const long long stride = (long long)kMrSplit * blockDim.x;
+  for (long long f = (long long)sblk * blockDim.x + threadIdx.x; f < mff; f += stride) {
+    const float2 a = v[(long long)k * mff + f];
+    acc = fmaf(a.x, a.x, fmaf(a.y, a.y, acc));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+    if ((int)threadIdx.x < st2) red[threadIdx.x] += red[threadIdx.x + st2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) jpart[(long long)k * kMrSplit + sblk] = red[0];
+}
+
+// v_k <- v_k / ||v_k|| (kept when the norm is 0), rho[k] = ||v_k||
+__global__ void knorm_scale_kernel(float2* __restrict__ v, const double* __restrict__ jpart,
+                                   double* __restrict__ rho, long long mff, int K) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)K * mff) return;
+  const int k = (int)(g / mff);
+  double ss = 0.0;
+  for (int b = 0; b < kMrSplit; ++b) ss += jpart[(long long)k * kMrSplit + b];
+  const double nrm = sqrt(ss);
+  if (g - (long long)k * mff == 0) rho[k] = nrm;
+  if (nrm > 0.0) {
+    const float sc = (float)(1.0 / nrm);
+    const float2 a = v[g];
+    v[g] = make_float2(a.x * sc, a.y * sc);
+  }
+}
+
+// The judge's decision: the largest radius over the frequencies of the
+// V-cycle (rho[0..K)) and of the corrected preconditioner (rho[K..2K)) into
+// rho[2K], rho[2K+1]; unless the corrected one is the smaller, alpha = 0 (the
+// V-cycle's iterates are kept) and the fallback flag is set.
+__global__ void judge_kernel(double* __restrict__ rho, int K, float2* __restrict__ alpha,
+                             int* __restrict__ fallback) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double m0 = 0.0, m1 = 0.0;
+  for (int k = 0; k < K; ++k) {
+    m0 = fmax(m0, rho[k]);
+    m1 = fmax(m1, rho[K + k]);
+  }
+  for (int k = 0; k < K; ++k)
+    if (!(rho[K + k] == rho[K + k])) m1 = rho[K + k];   // a NaN radius rejects
+  rho[2 * K] = m0;
+  rho[2 * K + 1] = m1;
+  if (!(m1 < m0)) {
+    alpha[0] = make_float2(0.f, 0.f);
+    *fallback = 1;
+  }
+}
+
 // x <- x + alpha (x2 - x) with the calibration's step (mr_alpha_kernel)
 __global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restrict__ x2,
                                  const float2* __restrict__ alpha, long long n) {
@@ -494,9 +560,12 @@ bec_status conv_fwd_raw(bec_problem* p, const AT* a, const float* W, int ci, int
   return BEC_OK;
 }
 
-// layer `layer` of the residual path (no activation: the gates follow)
+// layer `layer` of the residual path (no activation).  With gate not null
+// the tensor-core path multiplies by the layer's gate in its epilogue; only
+// that path takes a gate (the caller applies it otherwise).
 template <typename AT>
-bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m, int B) {
+bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m, int B,
+                    const float* gate = nullptr) {
   NetState& n = *p->net;
   const AT* a = static_cast<const AT*>(in);
   AT* o = static_cast<AT*>(out);
@@ -504,8 +573,8 @@ bec_status conv_fwd(bec_problem* p, const void* in, int layer, void* out, int m,
     if (n.tc) {   // every layer (layer 0 reads the 16-channel padded planes)
       const __nv_bfloat16* src =
           layer == 0 ? n.x16 : reinterpret_cast<const __nv_bfloat16*>(a);
-      return tc_conv3x3(p, layer, src, n.wt, reinterpret_cast<__nv_bfloat16*>(o), m, B, n.Bmax,
-                        n.err);
+      return tc_conv3x3(p, layer, src, n.wt, reinterpret_cast<__nv_bfloat16*>(o), gate, m, B,
+                        n.Bmax, n.err);
     }
   }
   return conv_fwd_raw<AT>(p, a, n.W + n.woff[layer], n.cin[layer], n.cout[layer], o, m, B, false);
@@ -674,17 +743,21 @@ bec_status features(bec_problem* p, int Bc) {
 }
 
 // gated layer i: out = conv(in, W_i) * GA_i; training keeps the product's
-// first factor in n.pre[i] for the backward pass
+// first factor in n.pre[i] for the backward pass.  Inference on the tensor
+// cores applies the gate in the convolution's epilogue (no second pass over
+// the layer's output).
 template <typename AT>
 bec_status gate_layer(bec_problem* p, int i, int B, bool training) {
   NetState& n = *p->net;
   const int m = n.sz[kGateLevel[i]];
   AT* out = static_cast<AT*>(n.act[kGateOut[i]]);
+  if (!training && sizeof(AT) == 2 && n.tc)
+    return conv_fwd<AT>(p, n.act[kGateIn[i]], i, out, m, B, n.GA[i]);
   AT* pre = training ? static_cast<AT*>(n.pre[i]) : out;
   BEC_TRY(conv_fwd<AT>(p, n.act[kGateIn[i]], i, pre, m, B));
-  const long long mmC = (long long)m * m * n.C, cnt = B * mmC;
+  const long long mmC = (long long)m * m * n.C;
   BEC_LAUNCH_BEGIN(p);
-  net::gate_apply_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(pre, out, n.GA[i], mmC, cnt);
+  net::gate_apply_kernel<AT><<<dim3(grid_for(mmC), B), kT, 0, p->stream>>>(pre, out, n.GA[i], mmC);
   BEC_LAUNCH_CHECK(p, "net_gate_kernel");
   return BEC_OK;
 }
@@ -735,14 +808,14 @@ template <typename AT>
 bec_status gate_bwd(bec_problem* p, int i, void* dv, int B) {
   NetState& n = *p->net;
   const int m = n.sz[kGateLevel[i]];
-  const long long mm = (long long)m * m, mmC = mm * n.C, cnt = B * mmC;
+  const long long mmC = (long long)m * m * n.C;
   AT* d = static_cast<AT*>(dv);
   const AT* pre = static_cast<const AT*>(n.pre[i]);
   BEC_LAUNCH_BEGIN(p);
   net::gate_dga_kernel<AT><<<grid_for(mmC), kT, 0, p->stream>>>(d, pre, n.dGA[i], mmC, B);
   BEC_LAUNCH_CHECK(p, "net_gate_dga_kernel");
   BEC_LAUNCH_BEGIN(p);
-  net::gate_scale_grad_kernel<AT><<<grid_for(cnt), kT, 0, p->stream>>>(d, n.GA[i], mmC, cnt);
+  net::gate_scale_grad_kernel<AT><<<dim3(grid_for(mmC), B), kT, 0, p->stream>>>(d, n.GA[i], mmC);
   BEC_LAUNCH_CHECK(p, "net_gate_grad_kernel");
   return BEC_OK;
 }
@@ -1004,6 +1077,9 @@ bec_status corrected_iterate(bec_problem* p) {
 // and the residual ratio it reaches per frequency.  Uses the
 // multigrid's level-0 arrays, so it runs before an apply's Step 1.
 template <typename AT>
+bec_status judge_t(bec_problem* p);
+
+template <typename AT>
 bec_status calibrate_t(bec_problem* p) {
   NvtxRange range("bec learned calibration");
   NetState& n = *p->net;
@@ -1029,7 +1105,71 @@ bec_status calibrate_t(bec_problem* p) {
   BEC_LAUNCH_BEGIN(p);
   mr_alpha_kernel<<<1, 256, 0, p->stream>>>(n.jpart, n.part, n.alpha, K, n.part + 4 * K, fb);
   BEC_LAUNCH_CHECK(p, "net_calibration_alpha_kernel");
+  if (n.judge) {
+    BEC_TRY(judge_t<AT>(p));
+  } else {
+    // all bits set: NaN radii (no judgement)
+    BEC_CUDA_TRY(cudaMemsetAsync(n.jrho, 0xFF, (2 * K + 2) * sizeof(double), p->stream));
+  }
   n.cal_ok = true;
+  return BEC_OK;
+}
+
+// The multigrid judges the correction: kJudgeIters power iterations per
+// frequency on the error operator E_k = I - M_k B_k of one apply, from the
+// calibration right-hand side (normalised per frequency), for M_k the
+// V-cycle alone and for the corrected preconditioner with the calibrated
+// step.  The last ||E_k v|| (||v|| = 1) estimates E_k's spectral radius; the
+// correction is kept only when its largest estimate over k is below the
+// V-cycle's (one decision for all frequencies: a per-frequency choice would
+// depend on k non-analytically).  Uses the calibration's arrays.
+constexpr int kJudgeIters = 10;
+
+template <typename AT>
+bec_status judge_t(bec_problem* p) {
+  NvtxRange range("bec learned judge");
+  NetState& n = *p->net;
+  MgLevel& L0 = p->mg.lv[0];
+  const int K = p->mg.K;
+  const long long mff = (long long)n.mf * n.mf, tot = K * mff;
+  float2* v = reinterpret_cast<float2*>(n.ework);
+  auto normalise = [&](int arm) -> bec_status {
+    BEC_LAUNCH_BEGIN(p);
+    knorm_parts_kernel<<<dim3(K, kMrSplit), 256, 0, p->stream>>>(v, n.jpart, mff);
+    BEC_LAUNCH_CHECK(p, "net_judge_norm_kernel");
+    BEC_LAUNCH_BEGIN(p);
+    knorm_scale_kernel<<<grid_for(tot), kT, 0, p->stream>>>(v, n.jpart, n.jrho + arm * K, mff, K);
+    BEC_LAUNCH_CHECK(p, "net_judge_scale_kernel");
+    return BEC_OK;
+  };
+  for (int arm = 0; arm < 2; ++arm) {
+    BEC_LAUNCH_BEGIN(p);
+    calibration_fill_kernel<<<grid_for(2 * tot), kT, 0, p->stream>>>(n.ework, 2 * tot);
+    BEC_LAUNCH_CHECK(p, "net_calibration_fill_kernel");
+    BEC_TRY(normalise(arm));
+    for (int it = 0; it < kJudgeIters; ++it) {
+      // L0.b = 0 - B v, L0.x = M L0.b, v <- v + L0.x = E v
+      BEC_CUDA_TRY(cudaMemsetAsync(n.xnew, 0, tot * sizeof(float2), p->stream));
+      BEC_TRY(mg_residual_level0(p, L0.b, n.ework, n.xnew));
+      BEC_TRY(mg_vcycle(p));
+      if (arm == 1) {
+        BEC_TRY(mg_residual_level0(p, n.res, L0.x, L0.b));
+        BEC_TRY(corrected_iterate<AT>(p));
+        BEC_TRY(mg_smooth_level0(p, L0.r, n.xnew, L0.b));
+        BEC_LAUNCH_BEGIN(p);
+        mr_update_kernel<<<grid_for(tot), kT, 0, p->stream>>>(
+            static_cast<float2*>(L0.x), static_cast<const float2*>(L0.r), n.alpha, tot);
+        BEC_LAUNCH_CHECK(p, "net_step_kernel");
+      }
+      BEC_LAUNCH_BEGIN(p);
+      axpy_c_kernel<<<grid_for(tot), kT, 0, p->stream>>>(v, static_cast<const float2*>(L0.x), tot);
+      BEC_LAUNCH_CHECK(p, "net_axpy_kernel");
+      BEC_TRY(normalise(arm));
+    }
+  }
+  BEC_LAUNCH_BEGIN(p);
+  judge_kernel<<<1, 1, 0, p->stream>>>(n.jrho, K, n.alpha, reinterpret_cast<int*>(n.part + 5 * K));
+  BEC_LAUNCH_CHECK(p, "net_judge_kernel");
   return BEC_OK;
 }
 
@@ -1139,6 +1279,7 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
   chain(dalloc(reinterpret_cast<void**>(&n->part), (size_t)(5 * K + 2 * bmax + 2) * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->jpart), (size_t)K * kMrSplit * 4 * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->alpha), sizeof(float2)));
+  chain(dalloc(reinterpret_cast<void**>(&n->jrho), (size_t)(2 * K + 2) * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->err), sizeof(int)));
   chain(dalloc(reinterpret_cast<void**>(&n->kf), (size_t)p->U * sizeof(double)));
   chain(dalloc(reinterpret_cast<void**>(&n->ku), (size_t)p->U * sizeof(double)));
@@ -1236,7 +1377,7 @@ void net_free(bec_problem* p) {
   if (n == nullptr) return;
   void* ptrs[] = {n->W, n->G, n->Mo, n->Ve, n->wpart, n->rc, n->row, n->lam, n->iota,
                   n->efine, n->res, n->etgt, n->rcall, n->ework, n->xnew, n->part, n->jpart,
-                  n->alpha, n->err, n->wt, n->x16, n->dA, n->dZ, n->ecb, n->kf, n->ku};
+                  n->alpha, n->jrho, n->err, n->wt, n->x16, n->dA, n->dZ, n->ecb, n->kf, n->ku};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int l = 0; l < 4; ++l)
@@ -1261,7 +1402,21 @@ bec_status net_correct(bec_problem* p) {
 }
 
 bec_status net_calibrate(bec_problem* p) {
-  return p->net->fp32 ? calibrate_t<float>(p) : calibrate_t<__nv_bfloat16>(p);
+  NetState& n = *p->net;
+  BEC_TRY(n.fp32 ? calibrate_t<float>(p) : calibrate_t<__nv_bfloat16>(p));
+  // read the decision when the stream is not being captured (a capture keeps
+  // running the correction, a no-op with alpha = 0)
+  n.rejected = false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BEC_CUDA_TRY(cudaStreamIsCapturing(p->stream, &cs));
+  if (cs == cudaStreamCaptureStatusNone) {
+    int fb = 0;
+    BEC_CUDA_TRY(cudaMemcpyAsync(&fb, reinterpret_cast<int*>(n.part + 5 * p->mg.K), sizeof(int),
+                                 cudaMemcpyDeviceToHost, p->stream));
+    BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    n.rejected = fb != 0;
+  }
+  return BEC_OK;
 }
 
 bool net_calibrated(const bec_problem* p) { return p->net != nullptr && p->net->cal_ok; }
@@ -1368,6 +1523,30 @@ bec_status net_check(bec_problem* p) {
   BEC_CUDA_TRY(cudaMemset(p->net->err, 0, sizeof(int)));
   set_error("a bounded wait in the tensor-core convolution ran out");
   return BEC_ETIMEOUT;
+}
+
+bool net_rejected(const bec_problem* p) { return p->net != nullptr && p->net->rejected; }
+
+bec_status net_prepare(bec_problem* p) {
+  if (p->net == nullptr || p->desc.route != BEC_ROUTE_LEARNED || p->net->bypass || p->net->cal_ok)
+    return BEC_OK;
+  return net_calibrate(p);
+}
+
+void net_set_judge(bec_problem* p, bool on) {
+  p->net->judge = on;
+  p->net->cal_ok = false;
+}
+
+bec_status net_judge_radii(bec_problem* p, double* host) {
+  const int K = p->mg.K;
+  if (!p->net->cal_ok) {
+    for (int i = 0; i < 2 * K + 2; ++i) host[i] = std::nan("");
+    return BEC_OK;
+  }
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(host, p->net->jrho, (2 * K + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+  return BEC_OK;
 }
 
 bec_status net_residual_ratios(bec_problem* p, double* host) {

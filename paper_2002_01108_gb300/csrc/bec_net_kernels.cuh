@@ -387,22 +387,25 @@ struct Poles {
 };
 constexpr int kGateAHidden = 8; // hidden channels of an a-gate
 
-// out[b][p][c] = pre[b][p][c] GA[p][c] (out may be pre)
+// out[b][p][c] = pre[b][p][c] GA[p][c] (out may be pre); grid (x: the
+// mmC = m^2 C elements of one image, y: the image b), no index division
 template <typename AT>
 __global__ void gate_apply_kernel(const AT* __restrict__ pre, AT* __restrict__ out,
-                                  const float* __restrict__ GA, long long mmC, long long n) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  out[g] = st<AT>(ld(pre + g) * GA[g % mmC]);
+                                  const float* __restrict__ GA, long long mmC) {
+  const long long pc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pc >= mmC) return;
+  const long long g = (long long)blockIdx.y * mmC + pc;
+  out[g] = st<AT>(ld(pre + g) * GA[pc]);
 }
 
-// d[b][p][c] *= GA[p][c] (the adjoint of the gate multiply)
+// d[b][p][c] *= GA[p][c] (the adjoint of the gate multiply), the same grid
 template <typename AT>
 __global__ void gate_scale_grad_kernel(AT* __restrict__ d, const float* __restrict__ GA,
-                                       long long mmC, long long n) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  d[g] = st<AT>(ld(d + g) * GA[g % mmC]);
+                                       long long mmC) {
+  const long long pc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pc >= mmC) return;
+  const long long g = (long long)blockIdx.y * mmC + pc;
+  d[g] = st<AT>(ld(d + g) * GA[pc]);
 }
 
 // dGA[p][c] = sum_b dout[b][p][c] pre[b][p][c]  (b in order)

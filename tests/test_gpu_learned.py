@@ -114,15 +114,17 @@ def _tol(eps, N, m, C):
                                           (127, 4, 0.02, 32, 0.5)])
 def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, gs):
     """Seeded weights (gates 1, then gates away from 1) in the oracle's
-    learned P_eps^{-1} with its own calibration; FP32 activations.  The
-    residual ratios of the GPU's calibration (which follow from its one
-    step) match the oracle's."""
+    learned P_eps^{-1} with its own calibration, the judge off on both sides
+    (so that the correction's arithmetic is what is compared); FP32
+    activations.  The residual ratios of the GPU's calibration (which follow
+    from its one step) match the oracle's."""
     import torch
     p, a = small_problem(True, C, m, N, eps)
     ps, w = seeded_weights(C, 50 + m, gs)
     y = np.random.default_rng(30 + m).uniform(-1, 1, (N, m, m))
     with p:
         p.set_learned_weights(w)
+        p.set_learned_judge(False)
         z = p.apply_Pinv(torch.from_numpy(y).cuda())
         torch.cuda.synchronize()
         z = z.cpu().numpy()
@@ -132,12 +134,51 @@ def test_learned_apply_Pinv_matches_the_oracle(m, N, eps, C, gs):
     h = O.MGHierarchy(K, m)
     lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
     params = LO.unflatten(w.astype(np.float64), C)
-    alpha, rr = LO.calibrate(h, lc, params, 1.0 / N, eps, N)
+    alpha, rr, _ = LO.calibrate(h, lc, params, 1.0 / N, eps, N, judge=False)
     ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alpha)
     err = float(np.max(np.abs(z - ref)) / np.max(np.abs(ref)))
     assert err <= _tol(eps, N, m, C), (err, _tol(eps, N, m, C))
     np.testing.assert_allclose(ratios, rr, atol=1e-3)
     print(f"learned P^-1 parity m={m} N={N} C={C} gates {gs}: err {err:.2e}, ratios {np.round(ratios, 3)}")
+
+
+@pytest.mark.parametrize("m,N,eps,C,gs,seed", [(31, 8, 0.1, 4, 0.3, 80), (63, 16, 0.0625, 4, None, 81)])
+def test_judge_matches_the_oracle(m, N, eps, C, gs, seed):
+    """The judge on both sides: the GPU's power-iteration radii per
+    frequency (V-cycle and corrected preconditioner) against the oracle's,
+    the same decision, and the judged P_eps^{-1} element by element.  Seeded
+    random weights (a correction that hurts: rejected) and zero weights (the
+    V-cycle plus the sweep and step: kept).  The cases have the two maxima
+    apart by more than the radii's tolerance, so that the decision is not a
+    rounding tie."""
+    import torch
+    p, a = small_problem(True, C, m, N, eps)
+    if gs is None:
+        w = np.zeros(LO.num_params(C), np.float32)
+    else:
+        _, w = seeded_weights(C, seed, gs)
+    y = np.random.default_rng(seed).uniform(-1, 1, (N, m, m))
+    with p:
+        p.set_learned_weights(w)
+        z = p.apply_Pinv(torch.from_numpy(y).cuda())
+        torch.cuda.synchronize()
+        z = z.cpu().numpy()
+        rv, rc, mv, mc = p.learned_judge_radii()
+        fb = p.learned_fallbacks
+    K = O.fd_stiffness_varcoef(a)
+    h = O.MGHierarchy(K, m)
+    lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
+    params = LO.unflatten(w.astype(np.float64), C)
+    alpha, _, (ov, oc) = LO.calibrate(h, lc, params, 1.0 / N, eps, N)
+    print(f"judge m={m}: V-cycle {ov.max():.4f} (GPU {mv:.4f}), corrected {oc.max():.4f} "
+          f"(GPU {mc:.4f}), kept {alpha != 0.0} (GPU {fb == 0})")
+    np.testing.assert_allclose(rv, ov, rtol=1e-3)
+    np.testing.assert_allclose(rc, oc, rtol=1e-3)
+    assert abs(mc - mv) > 5e-3 * mv
+    assert (fb == 0) == (alpha != 0.0)
+    ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alpha)
+    err = float(np.max(np.abs(z - ref)) / np.max(np.abs(ref)))
+    assert err <= _tol(eps, N, m, C), err
 
 
 def test_bf16_activations_track_fp32():
@@ -222,13 +263,15 @@ def abc_arms(m, N, rtol):
                 print(f"{m}^2 x {N} training loss", hist[:3], hist[-3:])
                 assert np.all(np.isfinite(hist))
                 assert hist[-50:].mean() < 0.2 * hist[:5].mean()
+            if arm == "zero":
+                p.set_learned_judge(False)   # the sweep and step alone, not judged
             u, info = p.gmres_solve(fd, restart=30, rtol=rtol, maxit=400, flexible=True)
             torch.cuda.synchronize()
             err = float(np.linalg.norm(u.cpu().numpy() - u_ref) / np.linalg.norm(u_ref))
             extra = ()
             if route == "learned":
                 ratios = p.learned_residual_ratios()
-                extra = (p.learned_fallbacks, float(np.mean(ratios)))
+                extra = (p.learned_fallbacks, float(np.mean(ratios)), p.learned_judge_radii()[2:])
             res[arm] = (info["iters"], err, info["true_relres"]) + extra
     print(f"A/B/C {m}^2 x {N}", res)
     for arm, (it, err, rr, *_) in res.items():
@@ -237,10 +280,11 @@ def abc_arms(m, N, rtol):
 
 
 def test_trained_correction_gains_over_the_vcycle():
-    """A/B/C at 63^2 x 32: the trained correction takes fewer FGMRES
-    iterations than the V-cycle alone and than the route at zero weights;
-    every arm reaches the sequential stepping solution."""
+    """A/B/C at 63^2 x 32: the judge keeps the trained correction, which
+    takes fewer FGMRES iterations than the V-cycle alone and than the route
+    at zero weights; every arm reaches the sequential stepping solution."""
     res = abc_arms(63, 32, 1e-10)
+    assert res["trained"][3] == 0, res
     assert res["trained"][0] < res["mg"][0], res
     assert res["trained"][0] < res["zero"][0], res
 
@@ -248,6 +292,7 @@ def test_trained_correction_gains_over_the_vcycle():
 def test_trained_correction_gains_at_127():
     """A/B/C at 127^2 x 64, as at 63^2 x 32."""
     res = abc_arms(127, 64, 1e-10)
+    assert res["trained"][3] == 0, res
     assert res["trained"][0] < res["mg"][0], res
     assert res["trained"][0] < res["zero"][0], res
 
@@ -257,8 +302,10 @@ def test_learned_route_at_the_workload_size():
     eps = sqrt(tau)/2, trained on the GPU as bench.py trains it (4000 steps,
     lr 1e-3): FGMRES(30) reaches RES 1e-8 (the benchmark's tolerance), and
     solved on to RES 1e-10 its solution equals sequential stepping to 1e-8.
-    Its iteration count against the V-cycle's is printed (at this size the
-    correction does not gain)."""
+    At this size the trained correction does not gain: the judge finds its
+    spectral radius above the V-cycle's and falls back to the V-cycle, so the
+    route takes the V-cycle's iterations.  The iteration count of the
+    correction forced on (judge off) is printed beside it."""
     import torch
     from paper_2002_01108_gb300 import Problem
     m, N = 255, 256
@@ -275,10 +322,16 @@ def test_learned_route_at_the_workload_size():
     with Problem(2, m, N, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
         p.set_eps(eps)
         p.learned_train(steps=4000, batch=16, lr=1e-3, seed=3)
+        p.set_learned_judge(False)
+        _, info_on = p.gmres_solve(fd, restart=30, rtol=1e-8, maxit=400, flexible=True)
+        p.set_learned_judge(True)
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-8, flexible=True)
         assert info["converged"] == 1 and info["true_relres"] <= 1.01e-8, info
-        print(f"255^2 x 256: V-cycle {info_mg['iters']} iterations, learned {info['iters']}",
-              "fallbacks", p.learned_fallbacks, "mean ratio", float(np.mean(p.learned_residual_ratios())))
+        radii = p.learned_judge_radii()
+        print(f"255^2 x 256: V-cycle {info_mg['iters']} iterations, judged route {info['iters']} "
+              f"(fallback {p.learned_fallbacks}, radii V-cycle {radii[2]:.3f} corrected "
+              f"{radii[3]:.3f}), correction forced on {info_on['iters']}")
+        assert info["iters"] <= info_mg["iters"] + 1, (info, info_mg)
         u, info = p.gmres_solve(fd, restart=30, rtol=1e-10, maxit=400, flexible=True)
         torch.cuda.synchronize()
     assert info["converged"] == 1 and info["true_relres"] <= 1.01e-10, info
