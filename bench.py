@@ -1176,14 +1176,16 @@ def run_ncu_case(which: str):
         print(f"ncu case {which} done")
         return 0
     if which == "learned_bf16":
-        # the learned route at 255^2 with N = 64 (33 frequencies: one batch of
-        # 32 and one of 1), untrained weights, three P_eps^{-1} applies
+        # the learned route at 255^2 with N = 64 (33 frequencies, 66 network
+        # images in one batch), untrained weights, the judge off (so that
+        # every apply runs the network), three P_eps^{-1} applies
         import numpy as np
         from workloads import grf_log_coefficient
         a = np.exp(grf_log_coefficient(seed=5, m=M_SIDE))
         y = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (64, M_SIDE, M_SIDE))).cuda()
         with Problem(2, M_SIDE, 64, route="learned", precision="fp32", a_nodes=a, flexible=True) as p:
             p.set_eps(1.0 / 16)
+            p.set_learned_judge(False)
             z = torch.empty_like(y)
             for _ in range(3):
                 p.apply_Pinv(y, z)

@@ -205,9 +205,9 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_im
   return c;
 }
 
-// out[img][y][x][0 .. STORE_C) = conv(in) (times gate[y][x][c] when gate is
-// not null: a gated layer's point-by-point gate, applied to the FP32
-// accumulators before the one rounding to BF16)
+// out[img][y][x][0 .. STORE_C) = conv(in) (times gate[c][y][x] when gate is
+// not null: a gated layer's point-by-point gate, channel-major, applied to
+// the FP32 accumulators before the one rounding to BF16)
 template <int CIN, int COUT, int STORE_C>
 __global__ void __launch_bounds__(kThreads, 2)
 conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16* __restrict__ wt,
@@ -343,16 +343,12 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
       if (tx < kTileX && x < m && y < m) {
         __nv_bfloat16* dst = out + (((long long)c.img * m + y) * m + x) * STORE_C;
         if (gate != nullptr) {
-          static_assert(STORE_C % 4 == 0, "gated layers store whole float4 groups");
-          const float4* g4 = reinterpret_cast<const float4*>(gate + ((long long)y * m + x) * STORE_C);
+          // channel-major gate [STORE_C][m^2]: for each channel the lanes of a
+          // warp (consecutive pixels of the tile's rows) read consecutive floats
+          const long long mm = (long long)m * m;
+          const float* gp = gate + (long long)y * m + x;
 #pragma unroll
-          for (int k = 0; k < STORE_C / 4; ++k) {
-            const float4 gv = __ldg(g4 + k);
-            v[4 * k] *= gv.x;
-            v[4 * k + 1] *= gv.y;
-            v[4 * k + 2] *= gv.z;
-            v[4 * k + 3] *= gv.w;
-          }
+          for (int k = 0; k < STORE_C; ++k) v[k] *= __ldg(gp + k * mm);
         }
         if constexpr (STORE_C % 8 == 0) {
           uint4 pk[STORE_C / 8];

@@ -361,7 +361,7 @@ bec_status tc_convert_weights(bec_problem* p, const float* W, const long long* w
 // output channels of the learned correction's network: one real plane per pole
 constexpr int kNetOut = 8;
 // out = conv3x3(in) of layer l (no activation), times the layer's gate
-// [m^2][32] when gate is not null (layers 0..7): l = 0 reads the 16-channel
+// (channel-major, [32][m^2]) when gate is not null (layers 0..7): l = 0 reads the 16-channel
 // padded input planes, l = 8 stores its kNetOut output channels
 bec_status tc_conv3x3(bec_problem* p, int layer, const __nv_bfloat16* in, const __nv_bfloat16* wt,
                       __nv_bfloat16* out, const float* gate, int m, int B, int bmax, int* err);

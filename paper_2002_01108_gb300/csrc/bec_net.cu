@@ -84,6 +84,8 @@ struct NetState {
   void* pre[net::kGates] = {};   // layer outputs before their gates (training)
   float* la_lv[4] = {};          // centred log a on the 4 network levels
   float* GA[net::kGates] = {};   // a-gates [m_l^2][C] of the gated layers
+  float* GAt[net::kGates] = {};  // the same, channel-major [C][m_l^2] (the tensor-core
+                                 // epilogue's coalesced reads)
   float* Z1[net::kGates] = {};   // their hidden layer, relu'd, [m_l^2][8]
   float* dGA[net::kGates] = {};  // gradients of the a-gates
   float* dA = nullptr;           // work: [sz0^2][C]
@@ -182,6 +184,15 @@ __global__ void feat_fill_kernel(const float2* __restrict__ rc, float c, AT* __r
     x16_store(X16, g, f0);
     x16_store(X16, half + g, f1);
   }
+}
+
+// gt[c][p] = g[p][c] (a gate in channel-major order)
+__global__ void gate_transpose_kernel(const float* __restrict__ g, float* __restrict__ gt,
+                                      long long mm, int C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mm * C) return;
+  const long long c = e / mm, q = e - c * mm;
+  gt[e] = g[q * C + c];
 }
 
 // w_j = sigma_j / (lambda + sigma_j) of one frequency
@@ -718,6 +729,12 @@ bec_status gates_fwd(bec_problem* p) {
     BEC_LAUNCH_BEGIN(p);
     net::one_plus_tanh_kernel<<<grid_for(cnt), kT, 0, p->stream>>>(n.GA[i], cnt);
     BEC_LAUNCH_CHECK(p, "net_gate_tanh_kernel");
+    if (n.GAt[i] != nullptr) {
+      BEC_LAUNCH_BEGIN(p);
+      gate_transpose_kernel<<<grid_for(cnt), kT, 0, p->stream>>>(n.GA[i], n.GAt[i], (long long)m * m,
+                                                                 n.C);
+      BEC_LAUNCH_CHECK(p, "net_gate_transpose_kernel");
+    }
   }
   n.gates_ok = true;
   return BEC_OK;
@@ -752,7 +769,7 @@ bec_status gate_layer(bec_problem* p, int i, int B, bool training) {
   const int m = n.sz[kGateLevel[i]];
   AT* out = static_cast<AT*>(n.act[kGateOut[i]]);
   if (!training && sizeof(AT) == 2 && n.tc)
-    return conv_fwd<AT>(p, n.act[kGateIn[i]], i, out, m, B, n.GA[i]);
+    return conv_fwd<AT>(p, n.act[kGateIn[i]], i, out, m, B, n.GAt[i]);
   AT* pre = training ? static_cast<AT*>(n.pre[i]) : out;
   BEC_TRY(conv_fwd<AT>(p, n.act[kGateIn[i]], i, pre, m, B));
   const long long mmC = (long long)m * m * n.C;
@@ -1255,6 +1272,8 @@ bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp
     const long long mm = (long long)n->sz[kGateLevel[i]] * n->sz[kGateLevel[i]];
     chain(dalloc(&n->pre[i], (size_t)bmax * mm * C * asz));
     chain(dalloc(reinterpret_cast<void**>(&n->GA[i]), (size_t)mm * C * sizeof(float)));
+    if (!n->fp32 && C == 32)   // the tensor-core path (decided below) reads these
+      chain(dalloc(reinterpret_cast<void**>(&n->GAt[i]), (size_t)mm * C * sizeof(float)));
     chain(dalloc(reinterpret_cast<void**>(&n->dGA[i]), (size_t)mm * C * sizeof(float)));
     chain(dalloc(reinterpret_cast<void**>(&n->Z1[i]), (size_t)mm * net::kGateAHidden * sizeof(float)));
   }
@@ -1383,7 +1402,7 @@ void net_free(bec_problem* p) {
   for (int l = 0; l < 4; ++l)
     if (n->la_lv[l]) cudaFree(n->la_lv[l]);
   for (int i = 0; i < net::kGates; ++i) {
-    void* g[] = {n->pre[i], n->GA[i], n->dGA[i], n->Z1[i]};
+    void* g[] = {n->pre[i], n->GA[i], n->GAt[i], n->dGA[i], n->Z1[i]};
     for (void* q : g)
       if (q) cudaFree(q);
   }
