@@ -20,8 +20,8 @@
 // Warp roles in a persistent CTA: warp 4 issues the TMA loads into a 4-stage
 // ring, warp 5 issues the MMAs into one of two tensor-memory accumulators,
 // warps 0-3 (tensor-memory lanes 0-127) read an accumulator back with
-// tcgen05.ld, apply ReLU when asked (the network's layers store without it:
-// its gates multiply the outputs), convert to BF16 and store.  Loads, MMAs and the
+// tcgen05.ld, multiply by the layer's gate when one is given (inference of
+// the gated layers), convert to BF16 and store.  Loads, MMAs and the
 // epilogue of different tiles overlap.
 //
 // Every wait is bounded (about 0.2 s of SM clock).  A wait that runs out

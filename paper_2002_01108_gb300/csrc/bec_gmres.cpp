@@ -36,8 +36,9 @@ bec_status apply_pinv(bec_problem* p, const double* y, double* z, const double* 
   NvtxRange range("bec P_eps^-1");
   const int fp64 = p->desc.precision == BEC_PC_FP64;
   if (p->desc.route == BEC_ROUTE_MG || p->desc.route == BEC_ROUTE_LEARNED) {
-    // the learned route's steps alpha_k are fixed by a calibration apply
-    // whenever the weights or eps changed
+    // the learned route's step alpha is fixed (and the correction judged) by
+    // a calibration apply whenever the weights, eps or the judge setting
+    // changed; a rejected correction is skipped
     const bool learned = p->desc.route == BEC_ROUTE_LEARNED && !net_bypassed(p);
     if (learned && !net_calibrated(p)) BEC_TRY(net_calibrate(p));
     BEC_TRY(launch_time_fwd(p, y, p->mg.lv[0].b, fp64, scale_dev));

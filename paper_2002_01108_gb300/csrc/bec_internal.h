@@ -326,10 +326,11 @@ int persist_take_withhold();
 // ---- learned correction (bec_net.cu)
 bec_status net_setup(bec_problem* p, const double* a_nodes, int channels, int fp32_acts, int bmax);
 void net_free(bec_problem* p);
-bec_status net_correct(bec_problem* p);   // after the V-cycle: x += alpha_k (corrected - x)
-// the calibration apply that fixes alpha_k (uses the level-0 multigrid arrays:
-// call it before an apply's Step 1); net_calibrated: alpha matches the
-// weights and eps; net_invalidate: they changed
+bec_status net_correct(bec_problem* p);   // after the V-cycle: x += alpha (corrected - x)
+// the calibration apply that fixes alpha and judges the correction (it uses
+// the level-0 multigrid arrays: call it before an apply's Step 1);
+// net_calibrated: alpha matches the weights, eps and the judge setting;
+// net_invalidate: they changed
 bec_status net_calibrate(bec_problem* p);
 bool net_calibrated(const bec_problem* p);
 void net_invalidate(bec_problem* p);

@@ -547,7 +547,7 @@ __global__ void mr_update_kernel(float2* __restrict__ x, const float2* __restric
 }
 
 // ------------------------------------------------------------ dispatch helpers
-// out = conv3x3(in, W) (ReLU when relu) for B images of side m, FP32 weights
+// out = conv3x3(in, W) (ReLU when relu: the a-gates' hidden layer) for B images of side m, FP32 weights
 // [9][ci][co] at W; the channel pairs of the residual path (C = 4 or 32) and
 // of the a-gates
 template <typename AT>
@@ -1060,7 +1060,7 @@ bec_status train_t(bec_problem* p, int steps, int batch, float lr, unsigned long
   return net_check(p);
 }
 
-// x1 = x + P_0 ec(c_k R_0 (b - B x)) for every frequency, into n.xnew, from
+// x1 = x + P_0 ec(R_0 (b - B x)) for every frequency, into n.xnew, from
 // the residual in n.res (batches of Bmax / 2 frequencies, Bmax network
 // samples)
 template <typename AT>
