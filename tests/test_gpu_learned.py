@@ -224,6 +224,40 @@ def test_bf16_tensor_core_network_matches_the_oracle(m):
     assert math.sqrt(loss) <= 24 * 2.0 ** -9
 
 
+def test_bf16_tensor_core_apply_matches_the_oracle():
+    """The learned P_eps^{-1} with BF16 activations, C = 32: inference runs
+    every convolution on the tensor cores with each gated layer's gate
+    applied in the epilogue, then the pole sum, the sweep and the calibrated
+    step (judge off on both sides).  Against the FP64 oracle with the same
+    seeded weights, the error is measured against the size of the
+    correction's contribution, ||z_ref - z_mg|| (z_mg: the same route with
+    alpha = 0): BF16 activations (u = 2^-9, 24 u per network as above) plus
+    the step alpha computed from them, 48 u together."""
+    import torch
+    m, N, eps, C = 63, 16, 0.0625, 32
+    p, a = small_problem(False, C, m, N, eps)
+    _, w = seeded_weights(C, 90, 0.3)
+    y = np.random.default_rng(91).uniform(-1, 1, (N, m, m))
+    with p:
+        p.set_learned_weights(w)
+        p.set_learned_judge(False)
+        z = p.apply_Pinv(torch.from_numpy(y).cuda())
+        torch.cuda.synchronize()
+        z = z.cpu().numpy()
+    K = O.fd_stiffness_varcoef(a)
+    h = O.MGHierarchy(K, m)
+    lc = LO.LearnedCorrection(m, np.log(a), 1.0 / N)
+    params = LO.unflatten(w.astype(np.float64), C)
+    alpha, _, _ = LO.calibrate(h, lc, params, 1.0 / N, eps, N, judge=False)
+    ref = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, alpha)
+    mg = LO.apply_Pinv_learned(y, h, lc, params, 1.0 / N, eps, 0.0)
+    corr = float(np.linalg.norm(ref - mg))
+    assert corr > 1e-3 * np.linalg.norm(ref), corr          # the correction is not negligible
+    err = float(np.linalg.norm(z - ref)) / corr
+    print(f"BF16 tensor-core learned P^-1: error {err:.2e} of the correction's contribution")
+    assert err <= 48 * 2.0 ** -9, err
+
+
 def test_training_lowers_the_loss():
     m, N, eps = 63, 16, 0.05
     p, _ = small_problem(False, 32, m, N, eps)
