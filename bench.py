@@ -176,7 +176,7 @@ def parse():
                     help="skip measuring the other preconditioner form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=("pinv_fp64", "pinv_fp32", "solve_fp32", "learned_bf16",
-                                           "ilu_fp32", "mg_fp32", "mg_fp64"),
+                                           "ilu_fp32", "mg_fp32", "mg_fp64", "batch_fp32"),
                     default=None,
                     help="run a small bounded case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -1157,6 +1157,28 @@ def run_ncu_case(which: str):
             for _ in range(3):
                 p.apply_Pinv(y, z)
             torch.cuda.synchronize()
+        print(f"ncu case {which} done")
+        return 0
+    if which == "batch_fp32":
+        # 4 instances of 255^2 x 64 (FP32 sine-transform P_eps^-1, FGMRES(4)),
+        # 2 streams: two solves in the persistent mode (one P_eps^-1 launch per
+        # stream and round over the device work queue), then two in the graph
+        # mode (the per-pass kernels), the second of each replaying its graphs
+        from paper_2002_01108_gb300 import Batch
+        specs = [dict(dim=2, nx=M_SIDE, N=64, eps=0.05 + 0.01 * i, precision="fp32", max_restart=4)
+                 for i in range(4)]
+        for mode in ("persistent", "graphs"):
+            with Batch(specs, nstreams=2, mode=mode) as b:
+                case = heat_case_2d(seed=2, m=M_SIDE, N=64, eps=0.05)
+                fs, us = [], []
+                for i in range(4):
+                    f = torch.empty((64, M_SIDE, M_SIDE), dtype=torch.float64, device="cuda")
+                    b.build_rhs(i, torch.from_numpy(case.u0).cuda(), torch.from_numpy(case.fsrc).cuda(), f)
+                    fs.append(f)
+                    us.append(torch.empty_like(f))
+                for _ in range(2):
+                    b.solve(fs, us, restart=4, maxit=8, rtol=RTOL)
+                torch.cuda.synchronize()
         print(f"ncu case {which} done")
         return 0
     if which == "ilu_fp32":
