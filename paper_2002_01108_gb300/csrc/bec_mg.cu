@@ -238,7 +238,11 @@ __global__ void mg_coarsest_kernel(v2_t<T>* __restrict__ x, const v2_t<T>* __res
 // the result is the same bit for bit; it replaces 3 + pre + post launches per
 // level, whose run time on these small grids is mostly launch latency.
 constexpr int kMgCoarseMax = 8;        // fused levels at most
-constexpr int kMgCoarseThreads = 256;
+// threads of the fused cycle's one block per frequency: the block is alone
+// on its SM (its levels fill the shared memory), so its warps are the SM's
+// only latency hiding; FP32 (64 registers) takes 1024, FP64 (80) 512
+template <typename T>
+constexpr int kMgCoarseThreads = sizeof(T) == 4 ? 1024 : 512;
 
 template <typename T>
 struct MgCoarseArgs {
@@ -264,7 +268,7 @@ __device__ __forceinline__ void cc_smooth(v2_t<T>* xo, const v2_t<T>* x, const v
   a.SK = SKl;
   a.m = m;
   a.J = (long long)m * m;
-  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads) {
+  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads<T>) {
     T sm[9], sk[9];
     int off[9];
     bool ok[9];
@@ -295,7 +299,7 @@ __device__ __forceinline__ void cc_residual(v2_t<T>* r, const v2_t<T>* x, const 
   a.SK = SKl;
   a.m = m;
   a.J = (long long)m * m;
-  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads) {
+  for (long long q = threadIdx.x; q < a.J; q += kMgCoarseThreads<T>) {
     T sm[9], sk[9];
     int off[9];
     bool ok[9];
@@ -309,7 +313,7 @@ __device__ __forceinline__ void cc_residual(v2_t<T>* r, const v2_t<T>* x, const 
 template <typename T>
 __device__ __forceinline__ void cc_restrict(v2_t<T>* bc, const v2_t<T>* r, int mc, int mf) {
   using V = v2_t<T>;
-  for (int c = threadIdx.x; c < mc * mc; c += kMgCoarseThreads) {
+  for (int c = threadIdx.x; c < mc * mc; c += kMgCoarseThreads<T>) {
     const int cy = c / mc, cx = c - cy * mc;
     const int f0 = (2 * cy + 1) * mf + (2 * cx + 1);
     V acc = {0, 0};
@@ -330,7 +334,7 @@ __device__ __forceinline__ void cc_restrict(v2_t<T>* bc, const v2_t<T>* r, int m
 template <typename T>
 __device__ __forceinline__ void cc_prolong_add(v2_t<T>* x, const v2_t<T>* xc, int mf, int mc) {
   using V = v2_t<T>;
-  for (int f = threadIdx.x; f < mf * mf; f += kMgCoarseThreads) {
+  for (int f = threadIdx.x; f < mf * mf; f += kMgCoarseThreads<T>) {
     const int fy = f / mf, fx = f - fy * mf;
     int cyv[2], cxv[2];
     T wy[2], wx[2];
@@ -357,7 +361,7 @@ __device__ __forceinline__ void cc_prolong_add(v2_t<T>* x, const v2_t<T>* xc, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMgCoarseThreads)
+__global__ void __launch_bounds__(kMgCoarseThreads<T>)
 mg_coarse_cycle_kernel(const __grid_constant__ MgCoarseArgs<T> a) {
   using V = v2_t<T>;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
@@ -381,7 +385,7 @@ mg_coarse_cycle_kernel(const __grid_constant__ MgCoarseArgs<T> a) {
     }
   }
   const int J0 = a.m[0] * a.m[0];
-  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads) bs[0][q] = a.b_in[(long long)k * J0 + q];
+  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads<T>) bs[0][q] = a.b_in[(long long)k * J0 + q];
   __syncthreads();
   for (int l = 0; l + 1 < a.nlev; ++l) {
     cc_smooth<T, true>(xs[l], nullptr, bs[l], a.SM[l], a.SK[l], a.m[l], lam, a.tau, a.omega);
@@ -421,7 +425,7 @@ mg_coarse_cycle_kernel(const __grid_constant__ MgCoarseArgs<T> a) {
       rs[l] = t;
     }
   }
-  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads) a.x_out[(long long)k * J0 + q] = xs[0][q];
+  for (int q = threadIdx.x; q < J0; q += kMgCoarseThreads<T>) a.x_out[(long long)k * J0 + q] = xs[0][q];
 }
 
 // shared memory of the fused cycle from level l of the hierarchy down
@@ -966,7 +970,7 @@ bec_status vcycle_t(bec_problem* p, int l0) {
       BEC_CUDA_TRY(cudaFuncSetAttribute(mg_coarse_cycle_kernel<T>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BEC_LAUNCH_BEGIN(p);
-    mg_coarse_cycle_kernel<T><<<K, kMgCoarseThreads, smem, p->stream>>>(ca);
+    mg_coarse_cycle_kernel<T><<<K, kMgCoarseThreads<T>, smem, p->stream>>>(ca);
     BEC_LAUNCH_CHECK(p, "mg_coarse_cycle_kernel");
   } else {
     MgLevel& c = lv[L - 1];
