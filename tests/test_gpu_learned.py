@@ -181,6 +181,37 @@ def test_judge_matches_the_oracle(m, N, eps, C, gs, seed):
     assert err <= _tol(eps, N, m, C), err
 
 
+def test_judge_api():
+    """The judge's entry points: radii are NaN before a calibration and with
+    the judge off; turning it off, on or off again recalibrates at the next
+    apply (the fallback flag follows); a problem of another route has no
+    judge."""
+    import torch
+    from paper_2002_01108_gb300 import BecError, Problem
+    p, _ = small_problem(True, 4)
+    _, w = seeded_weights(4, 80, 0.3)           # a correction the judge rejects (see above)
+    y = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, (8, 31, 31))).cuda()
+    with p:
+        p.set_learned_weights(w)
+        rv, rc, mv, mc = p.learned_judge_radii()
+        assert np.all(np.isnan(rv)) and np.all(np.isnan(rc)) and math.isnan(mv) and math.isnan(mc)
+        p.apply_Pinv(y)
+        _, _, mv, mc = p.learned_judge_radii()
+        assert mc > mv > 0 and p.learned_fallbacks == 1
+        p.set_learned_judge(False)
+        assert math.isnan(p.learned_judge_radii()[2])
+        p.apply_Pinv(y)
+        assert math.isnan(p.learned_judge_radii()[2]) and p.learned_fallbacks == 0
+        p.set_learned_judge(True)
+        p.apply_Pinv(y)
+        _, _, mv2, mc2 = p.learned_judge_radii()
+        assert (mv2, mc2) == (mv, mc) and p.learned_fallbacks == 1
+    with Problem(2, 31, 8, route="mg", precision="fp32") as q:
+        q.set_eps(0.1)
+        with pytest.raises(BecError):
+            q.set_learned_judge(False)
+
+
 def test_bf16_activations_track_fp32():
     import torch
     m, N, eps, C = 63, 16, 0.05, 32
