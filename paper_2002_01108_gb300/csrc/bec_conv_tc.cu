@@ -192,15 +192,18 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[COUT]) {
 }
 
 struct TileCoord {
-  int img, x0, y0;
+  int img, x0, y0, spatial;
 };
 
-__device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_img) {
+// Tiles are numbered image-fastest: t = spatial tile * nimg + image, and a
+// CTA takes a contiguous range of them, so that it walks one spatial tile
+// through many images (its gate values stay in registers).
+__device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int nimg) {
   TileCoord c;
-  c.img = t / tiles_img;
-  const int r = t - c.img * tiles_img;
-  const int ty = r / tiles_x;
-  c.x0 = (r - ty * tiles_x) * kTileX;
+  c.spatial = t / nimg;
+  c.img = t - c.spatial * nimg;
+  const int ty = c.spatial / tiles_x;
+  c.x0 = (c.spatial - ty * tiles_x) * kTileX;
   c.y0 = ty * kTileY;
   return c;
 }
@@ -230,6 +233,10 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nimg = ntiles / tiles_img;
+  const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int t_begin = (int)blockIdx.x * per;
+  const int t_end = t_begin + per < ntiles ? t_begin + per : ntiles;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -270,13 +277,13 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
       int i = 0;
       // withhold (a test of the bounded waits): issue no tile load, so that the
       // MMA warp's wait runs out and the CTA aborts with nothing in flight
-      for (int t = blockIdx.x; !withhold && t < ntiles; t += gridDim.x, ++i) {
+      for (int t = t_begin; !withhold && t < t_end; ++t, ++i) {
         const int s = i % kStages;
         if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, &abort_flag)) {
           abort_flag = 1;
           break;
         }
-        const TileCoord c = tile_coord(t, tiles_x, tiles_img);
+        const TileCoord c = tile_coord(t, tiles_x, nimg);
         const uint32_t dst = sA + s * C::kStageBytes;
         mbar_expect_tx(full(s), C::NCH * (kHaloX * kHaloY * 16));
 #pragma unroll
@@ -290,7 +297,7 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
     if (lane == 0) {
       bool ok = mbar_wait(wbar, 0, &abort_flag);
       int i = 0;
-      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+      for (int t = t_begin; ok && t < t_end; ++t, ++i) {
         const int s = i % kStages, acc = i & 1;
         if (!mbar_wait(full(s), (i / kStages) & 1, &abort_flag)) {
           ok = false;
@@ -324,7 +331,9 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
   } else {
     // -------------------------------------------------------------- epilogue
     int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    int gate_tile = -1;                 // spatial tile whose gate values g holds
+    float g[STORE_C];
+    for (int t = t_begin; t < t_end; ++t, ++i) {
       const int acc = i & 1;
       if (!mbar_wait(tfull(acc), (i >> 1) & 1, &abort_flag)) {
         abort_flag = 1;
@@ -336,7 +345,7 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty(acc));
-      const TileCoord c = tile_coord(t, tiles_x, tiles_img);
+      const TileCoord c = tile_coord(t, tiles_x, nimg);
       const int row = 32 * warp + lane;
       const int tx = row % kHaloX, ty = row / kHaloX;
       const int x = c.x0 + tx, y = c.y0 + ty;
@@ -344,11 +353,17 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat1
         __nv_bfloat16* dst = out + (((long long)c.img * m + y) * m + x) * STORE_C;
         if (gate != nullptr) {
           // channel-major gate [STORE_C][m^2]: for each channel the lanes of a
-          // warp (consecutive pixels of the tile's rows) read consecutive floats
-          const long long mm = (long long)m * m;
-          const float* gp = gate + (long long)y * m + x;
+          // warp (consecutive pixels of the tile's rows) read consecutive
+          // floats; read again only when the spatial tile changes
+          if (c.spatial != gate_tile) {
+            const long long mm = (long long)m * m;
+            const float* gp = gate + (long long)y * m + x;
 #pragma unroll
-          for (int k = 0; k < STORE_C; ++k) v[k] *= __ldg(gp + k * mm);
+            for (int k = 0; k < STORE_C; ++k) g[k] = __ldg(gp + k * mm);
+            gate_tile = c.spatial;
+          }
+#pragma unroll
+          for (int k = 0; k < STORE_C; ++k) v[k] *= g[k];
         }
         if constexpr (STORE_C % 8 == 0) {
           uint4 pk[STORE_C / 8];
