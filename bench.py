@@ -1077,7 +1077,9 @@ def run_gpu(args):
             say("mg_fp32_3+2", measure_mg, "fp32", args, pre=3, post=2)
             say("mg_fp32_1+1", measure_mg, "fp32", args)
             say("mg_fp64_1+1", measure_mg, "fp64", args)
-            say("learned_fp32_bf16", measure_mg, "fp32", args, route="learned", train_steps=4000)
+            # on the best V-cycle of the multigrid lines (3+2)
+            say("learned_fp32_bf16", measure_mg, "fp32", args, route="learned", train_steps=4000,
+                pre=3, post=2)
         say("batch", measure_batch, args, ws, rank, dist)
         if ws == 1:
             say("precision_511x511_N512", measure_precision_workload, args)
