@@ -267,6 +267,8 @@ bec_status bec_batch_solve(bec_batch* b, const double* const* f, double* const* 
       const bec_status st = bec::net_check(b->probs[i]);
       if (st != BEC_OK && first_error == BEC_OK) first_error = st;
     }
+    const bec_status pst = bec::pc_check(b->probs[i]);
+    if (pst != BEC_OK && first_error == BEC_OK) first_error = pst;
   }
   if (first_error != BEC_OK) return first_error;
   return all_conv ? BEC_OK : BEC_ENOTCONV;

@@ -105,7 +105,7 @@ void free_all(bec_problem* p) {
   PcTables& t = p->tab;
   void* ptrs[] = {t.space.tw64, t.space.tw32, t.time.tw64, t.time.tw32, t.sin2_64, t.sin2_32,
                   t.mu64, t.mu32, t.mum64, t.mum32, t.es64, t.eis64, t.es32, t.eis32,
-                  t.lamf64, t.lamf32, t.rinv64, p->pc_scratch, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
+                  t.lamf64, t.lamf32, t.rinv64, p->pc_scratch, p->pc_err, p->V, p->Z, p->w, p->t, p->partials, p->hcol, p->H, p->cs,
                   p->sn, p->g, p->ycoef, p->sigma, p->flag, p->scal, p->io_f, p->io_u,
                   p->io_f2, p->io_u2};
   for (void* q : ptrs)
@@ -290,10 +290,22 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
   }
   p->desc.a_nodes = nullptr;   // copied by mg_setup; the caller keeps its array
   p->desc.wind = nullptr;
+  p->ld = p->m;
+  p->Jp = p->J;
   if (d->precision == BEC_PC_FP32 && d->route == BEC_ROUTE_FST) {
+    // rows of m + 1 slots (the last one zero): 16-byte aligned rows and time
+    // slices for the TMA tiles of the time pass
+    p->ld = p->m + 1;
+    p->Jp = p->J / p->m * p->ld;
     float* sc = nullptr;
-    chain(dmalloc(&sc, (size_t)U));
+    chain(dmalloc(&sc, (size_t)N * p->Jp));
     p->pc_scratch = sc;
+    chain(dmalloc(&p->pc_err, (size_t)1));
+    if (s == BEC_OK) {
+      const cudaError_t e = cudaMemset(p->pc_err, 0, sizeof(int));
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaMemset");
+    }
+    if (s == BEC_OK) s = time16_make_map(p);
   }
   chain(dmalloc(&p->V, (size_t)(R + 1) * U));
   if (d->flexible) chain(dmalloc(&p->Z, (size_t)R * U));

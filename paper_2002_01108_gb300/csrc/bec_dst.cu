@@ -27,11 +27,11 @@ __host__ __device__ constexpr int rows_min_blocks(int bytes, int logn, int warps
 // in that case TI == TO.
 template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, rows_min_blocks(sizeof(T), LOGN, WARPS))
-dst_rows_kernel(const TI* in, TO* out, long long rows, int m, const T* __restrict__ sin2,
-                const v2_t<T>* __restrict__ tw) {
+dst_rows_kernel(const TI* in, TO* out, long long rows, int m, int in_ld, int out_ld,
+                const T* __restrict__ sin2, const v2_t<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_bytes[];
-  dst_rows_tile<T, TI, TO, LOGN, WARPS>(in, out, rows, m, sin2, tw, blockIdx.x, smem_bytes,
-                                        threadIdx.x);
+  dst_rows_tile<T, TI, TO, LOGN, WARPS>(in, out, rows, m, in_ld, out_ld, sin2, tw, blockIdx.x,
+                                        smem_bytes, threadIdx.x);
 }
 
 // Blocks per SM that the register bound of dst_cols_kernel asks for, as warps
@@ -73,9 +73,11 @@ bec_status rows_launch(bec_problem* p, const void* in, void* out, long long rows
   BEC_CUDA_TRY(prepare(k, smem));
   const long long pairs = (rows + 1) / 2;
   const unsigned grid = (unsigned)((pairs + WARPS - 1) / WARPS);
+  // FP32 arrays are the preconditioner's scratch, in its layout (rows of ld)
+  const int in_ld = sizeof(TI) == 4 ? p->ld : p->m, out_ld = sizeof(TO) == 4 ? p->ld : p->m;
   BEC_LAUNCH_BEGIN(p);
   k<<<grid, WARPS * 32, smem, p->stream>>>(static_cast<const TI*>(in), static_cast<TO*>(out), rows,
-                                           p->m, sin2, tw);
+                                           p->m, in_ld, out_ld, sin2, tw);
   BEC_LAUNCH_CHECK(p, "dst_rows_kernel");
   return BEC_OK;
 }
@@ -85,15 +87,17 @@ bec_status cols_launch(bec_problem* p, void* data, const T* sin2, const v2_t<T>*
   const size_t smem = (size_t)WARPS * 2 * dst_line_stride(LOGN, sizeof(T)) * sizeof(T);
   auto k = dst_cols_kernel<T, LOGN, WARPS>;
   BEC_CUDA_TRY(prepare(k, smem));
-  const long long m = p->m, m2 = m * m;
+  // FP32 data is the preconditioner's scratch: rows of ld slots
+  const long long m = p->m, ld = sizeof(T) == 4 ? p->ld : p->m, m2 = m * ld;
+  const long long J = sizeof(T) == 4 ? p->Jp : p->J;
   // 2D: y over [ny][nx] slices; 3D: y over every [ny][nx] plane, then z over
-  // [nz][ny nx] slices
+  // [nz][ny nx] slices (a plane's pad slots are zeros and stay zeros)
   const int passes = p->dim == 3 ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
     const bool zpass = pass == 1;
     const int ncols = (int)(zpass ? m2 : m);
-    const long long row_stride = zpass ? m2 : m;
-    const long long slice_stride = zpass ? p->J : m2;
+    const long long row_stride = zpass ? m2 : ld;
+    const long long slice_stride = zpass ? J : m2;
     const long long nslices = zpass ? (long long)p->N : (long long)p->N * (p->dim == 3 ? m : 1);
     dim3 grid((unsigned)((ncols + 2 * WARPS - 1) / (2 * WARPS)),
               (unsigned)(nslices < 65535 ? nslices : 65535));

@@ -349,6 +349,7 @@ bec_status gmres_solve_one(bec_problem* p, const double* f, double* u, const bec
   }
   gmres_run_info(r, info);
   if (p->net) BEC_TRY(net_check(p));
+  BEC_TRY(pc_check(p));
   return gmres_run_result(r);
 }
 

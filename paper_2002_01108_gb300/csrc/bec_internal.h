@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -116,7 +117,16 @@ struct bec_problem {
 
   bec::PcTables tab;
   bec::TileChoice tile;         // block widths of the P_eps^{-1} passes
-  void* pc_scratch = nullptr;   // U elements of the preconditioner's type
+  void* pc_scratch = nullptr;   // N x Jp elements of the preconditioner's type
+  // Row length and points per time slice of pc_scratch: in FP32 every row
+  // of m values gets one zero pad slot (ld = m + 1), so that rows and time
+  // slices start on 16-byte boundaries (tensor-memory-access tiles); else
+  // ld = m, Jp = J.
+  int ld = 0;
+  long long Jp = 0;
+  int* pc_err = nullptr;        // device word: a bounded wait of the time pass ran out
+  bool time_map_ok = false;     // time_map describes pc_scratch for the N = 256 time pass
+  CUtensorMap time_map;
 
   // Krylov workspace (FP64)
   double* V = nullptr;          // (max_restart + 1) x U
@@ -236,6 +246,15 @@ bec_status launch_dst_cols_w(bec_problem* p, void* data, int fp64, int w);
 // Time pass: scale, FFT over N, divide by the shifted eigenvalues, inverse
 // FFT, unscale, for every spatial mode, in place.  The divide is multiplied by
 // `scale` and, when scale_dev is not null, by the device scalar *scale_dev.
+// true when the FP32 time pass runs as the four-step N = 256 kernel (no
+// tunable block width)
+bool time16_applies(const bec_problem* p);
+// describes pc_scratch to the TMA unit for that kernel (at allocation;
+// leaves time_map_ok false when the layout or the driver does not allow it)
+bec_status time16_make_map(bec_problem* p);
+// BEC_ETIMEOUT (and clears the word) when a bounded wait of the time pass
+// ran out since the last check; synchronises the problem's stream
+bec_status pc_check(bec_problem* p);
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,
                             const double* scale_dev);
 bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale,
@@ -287,7 +306,7 @@ constexpr int kPersistMaxJobs = 64;
 struct PersistJob {
   const double* y;
   double* z;
-  float* s;                    // the instance's FP32 scratch (U floats)
+  float* s;                    // the instance's FP32 scratch (N Jp floats, rows of ld)
   const double* scale_dev;     // s (null: 1)
   const float* sin2;
   const float2* tws;           // spatial FFT twiddles
@@ -296,9 +315,9 @@ struct PersistJob {
   const float* eis;
   const float2* lamf;
   const float* mu;
-  long long J;
+  long long J;                 // points per time slice of s (the problem's Jp)
   float tau, scale_h;
-  int m, N, logn, logt;
+  int m, ld, N, logn, logt;
   int tiles[5];                // tiles (queue items) of the five passes, 8 warps each
 };
 // The work queue of one launch, passed by value.

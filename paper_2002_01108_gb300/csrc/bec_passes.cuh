@@ -15,14 +15,17 @@
 namespace bec {
 namespace {
 
+
 // ---------------------------------------------------------------- x-DST
-// DST along x: one warp per pair of contiguous rows of length m = n - 1, the
-// tile's warps on rows 2 (blk WARPS + warp) and the next.  `in` and `out` may
-// be the same array (each warp reads its rows before writing them); in that
-// case TI == TO.
+// DST along x: one warp per pair of rows of m = n - 1 values, the tile's
+// warps on rows 2 (blk WARPS + warp) and the next; row r of `in` starts at
+// r in_ld, of `out` at r out_ld (in_ld, out_ld = m or m + 1; an output row
+// of m + 1 slots gets a zero in its last one).  `in` and `out` may be the
+// same array (each warp reads its rows before writing them); in that case
+// TI == TO and in_ld == out_ld.
 template <typename T, typename TI, typename TO, int LOGN, int WARPS>
 __device__ __forceinline__ void dst_rows_tile(const TI* in, TO* out, long long rows, int m,
-                                              const T* __restrict__ sin2,
+                                              int in_ld, int out_ld, const T* __restrict__ sin2,
                                               const v2_t<T>* __restrict__ tw, long long blk,
                                               unsigned char* smem_bytes, int tid) {
   constexpr int RS = dst_line_stride(LOGN, sizeof(T));   // real slots per line
@@ -32,7 +35,7 @@ __device__ __forceinline__ void dst_rows_tile(const TI* in, TO* out, long long r
   const long long r0 = 2 * (blk * WARPS + warp);
   if (r0 >= rows) return;                    // whole warp leaves; no block barrier below
   const bool hasb = r0 + 1 < rows;
-  const TI* ia = in + r0 * m;
+  const TI* ia = in + r0 * in_ld;
   // loads in groups of G per row, all issued before the group's conversions
   // (m = n - 1 < 32 PER)
   constexpr int PER = (1 << LOGN) / 32 > 0 ? (1 << LOGN) / 32 : 1;
@@ -44,7 +47,7 @@ __device__ __forceinline__ void dst_rows_tile(const TI* in, TO* out, long long r
     for (int t = 0; t < G; ++t) {
       const int j = lane + 32 * (t0 + t);
       va[t] = j < m ? ia[j] : TI(0);
-      vb[t] = (j < m && hasb) ? ia[m + j] : TI(0);
+      vb[t] = (j < m && hasb) ? ia[in_ld + j] : TI(0);
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
@@ -57,7 +60,7 @@ __device__ __forceinline__ void dst_rows_tile(const TI* in, TO* out, long long r
   }
   __syncwarp();
   warp_dst_pair<T, LOGN>(raw, RS, sin2, tw, lane);
-  TO* oa = out + r0 * m;
+  TO* oa = out + r0 * out_ld;
 #pragma unroll
   for (int t0 = 0; t0 < PER; t0 += G) {
     TO wa[G], wb[G];
@@ -72,7 +75,10 @@ __device__ __forceinline__ void dst_rows_tile(const TI* in, TO* out, long long r
       const int j = lane + 32 * (t0 + t);
       if (j < m) {
         oa[j] = wa[t];
-        if (hasb) oa[m + j] = wb[t];
+        if (hasb) oa[out_ld + j] = wb[t];
+      } else if (j < out_ld) {             // the pad slot (j = m)
+        oa[j] = TO(0);
+        if (hasb) oa[out_ld + j] = TO(0);
       }
     }
   }
@@ -131,30 +137,32 @@ struct ModeEigs {
 };
 
 // Mass and stiffness eigenvalues of spatial mode q: FD (1, k_i + k_l); Q1
-// (m_i m_l, m_i k_l + k_i m_l) in 2D, (m_q, k_q) in 1D.
+// (m_i m_l, m_i k_l + k_i m_l) in 2D, (m_q, k_q) in 1D.  The layout has J
+// points per time slice in rows of ld >= m slots (x index i = q mod ld);
+// slots past the end or with i >= m are padding.
 template <typename T>
-__device__ __forceinline__ void mode_eigs(long long q, long long J, int m, int dim,
+__device__ __forceinline__ void mode_eigs(long long q, long long J, int m, int ld, int dim,
                                           ModeEigs<T> e, T& muM, T& muK) {
-  if (q >= J) {                                  // padding column: any positive value
+  const long long row = q / ld;
+  const int i = (int)(q - row * ld);
+  if (q >= J || i >= m) {                        // padding: any positive value
     muM = T(1);
     muK = T(1);
     return;
   }
   if (dim == 1) {
-    muM = e.m ? e.m[q] : T(1);
-    muK = e.k[q];
+    muM = e.m ? e.m[i] : T(1);
+    muK = e.k[i];
     return;
   }
   if (dim == 3) {                                // FD only: k_i + k_l + k_s
-    const long long m2 = (long long)m * m;
-    const int s = (int)(q / m2);
-    const long long r = q - (long long)s * m2;
-    const int l = (int)(r / m), i = (int)(r - (long long)l * m);
+    const int s = (int)(row / m);
+    const int l = (int)(row - (long long)s * m);
     muM = T(1);
     muK = e.k[i] + e.k[l] + e.k[s];
     return;
   }
-  const int l = (int)(q / m), i = (int)(q - (long long)l * m);
+  const int l = (int)row;
   if (e.m == nullptr) {
     muM = T(1);
     muK = e.k[i] + e.k[l];
@@ -170,7 +178,8 @@ __device__ __forceinline__ void mode_eigs(long long q, long long J, int m, int d
 // divide by lambda'_k mu^M + tau mu^K (Step 2), inverse FFT, unscale (Step
 // 3).  FE: the mass eigenvalues are present (Q1 elements).
 template <typename T, int LOGN, int WARPS, bool FE>
-__device__ __forceinline__ void time_pass_tile(T* __restrict__ data, long long J, int m, int dim,
+__device__ __forceinline__ void time_pass_tile(T* __restrict__ data, long long J, int m, int ld,
+                                               int dim,
                                                const T* __restrict__ es, const T* __restrict__ eis,
                                                const v2_t<T>* __restrict__ lamf, ModeEigs<T> me,
                                                T tau, T scale_h, const double* __restrict__ scale_dev,
@@ -223,9 +232,9 @@ __device__ __forceinline__ void time_pass_tile(T* __restrict__ data, long long J
   warp_fft<T, -1, LOGN>(line, tw, lane);
   const long long qa = q0 + 2 * warp;
   T ma, mua, mb, mub;                 // mass and stiffness eigenvalues of modes a, b
-  mode_eigs(qa, J, m, dim, me, ma, mua);
+  mode_eigs(qa, J, m, ld, dim, me, ma, mua);
   if (qa + 1 < J) {
-    mode_eigs(qa + 1, J, m, dim, me, mb, mub);
+    mode_eigs(qa + 1, J, m, ld, dim, me, mb, mub);
   } else {
     mb = ma;
     mub = mua;
@@ -274,6 +283,212 @@ __device__ __forceinline__ void time_pass_tile(T* __restrict__ data, long long J
   if (qin) {
 #pragma unroll 4
     for (int j = j0; j < N; j += JS) col[(long long)j * J] = slot[2 * j] * eis[j];
+  }
+}
+
+
+// ------------------------------------------------- time pass, FP32, N = 256
+// The same time pass (Steps 1-3 of Sec. 4 on one tile of spatial modes) as a
+// four-step FFT with N = 16 x 16 held in registers: j = j1 + 16 j2 and
+// k = k2 + 16 k1, so that
+//   X_{k2 + 16 k1} = sum_{j1} w16^{j1 k1} [w^{j1 k2} sum_{j2} x_{j1 + 16 j2} w16^{j2 k2}]
+// (w = e^{-2 pi i / N}).  Step A: a thread owns a residue j1 of one line and
+// does the 16-point DFT over j2 in registers, then the twiddles w^{j1 k2}.
+// One shared-memory exchange hands each thread a class k2, step B does the
+// 16-point DFT over j1, the divide, and the inverse DFT over k1; a second
+// exchange and the inverse DFT over k2 finish the line.  The half spectrum
+// pairs k with N - k: class (16 - k2) mod 16, held by another lane of the
+// same half-warp, which passes it by shuffle.  The tile is 16 complex lines
+// (32 adjacent modes, two per line as real + i imaginary); 16 threads per
+// line, 256 per block.
+constexpr int kT16Threads = 256;
+constexpr int kT16Modes = 32;                   // modes per tile
+constexpr int kT16LineSlots = 16 * 17 + 1;      // complex slots per line: 16 rows of 17, odd
+constexpr size_t kT16Smem = (size_t)16 * kT16LineSlots * 8;
+
+// In-register DFT of length 16 with kernel e^{SIGN 2 pi i r k / 16}, natural
+// order in and out, as 4 x 4: the 4-point DFTs over the samples a + 4 b
+// (b = 0..3), the twiddles w16^{a kb}, then the 4-point DFTs over a; output
+// kb + 4 ka.
+template <int SIGN, typename V>
+__device__ __forceinline__ void dft16(V (&v)[16]) {
+  using T = decltype(v[0].x);
+  V u[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    V t[4] = {v[a], v[a + 4], v[a + 8], v[a + 12]};
+    radix_dft<4, SIGN>(t);
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) u[a][kb] = t[kb];
+  }
+  // w16^m = cos(m pi / 8) + SIGN i sin(m pi / 8) for m = a kb
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
+  const T h = T(0.70710678118654752440);
+  u[1][1] = cmul(u[1][1], V{c1, SIGN * s1});      // m = 1
+  u[1][2] = cmul(u[1][2], V{h, SIGN * h});        // m = 2
+  u[1][3] = cmul(u[1][3], V{s1, SIGN * c1});      // m = 3
+  u[2][1] = cmul(u[2][1], V{h, SIGN * h});        // m = 2
+  u[2][2] = cmul_si<SIGN>(u[2][2]);               // m = 4
+  u[2][3] = cmul(u[2][3], V{-h, SIGN * h});       // m = 6
+  u[3][1] = cmul(u[3][1], V{s1, SIGN * c1});      // m = 3
+  u[3][2] = cmul(u[3][2], V{-h, SIGN * h});       // m = 6
+  u[3][3] = cmul(u[3][3], V{-c1, -SIGN * s1});    // m = 9
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    V t[4] = {u[0][kb], u[1][kb], u[2][kb], u[3][kb]};
+    radix_dft<4, SIGN>(t);
+#pragma unroll
+    for (int ka = 0; ka < 4; ++ka) v[kb + 4 * ka] = t[ka];
+  }
+}
+
+// B_k / (lambda'_k mu^M + tau mu^K) of the two modes of a line for one k,
+// from the packed spectrum C = X_k and its partner Cn = X_{N-k}: the modes'
+// spectra (times 2) are A1 = C + conj Cn and A2 = -i (C - conj Cn); the
+// result is the packed value B1 + i B2 at k.  lam = lambda'_k.
+template <bool FE>
+__device__ __forceinline__ float2 t16_divide(float2 C, float2 Cn, float2 lam, float ma, float tmua,
+                                             float mb, float tmub, float scale) {
+  const float2 A1 = {C.x + Cn.x, C.y - Cn.y};
+  const float2 A2 = {C.y + Cn.y, Cn.x - C.x};
+  const float d1r = FE ? fmaf(lam.x, ma, tmua) : lam.x + tmua;
+  const float d2r = FE ? fmaf(lam.x, mb, tmub) : lam.x + tmub;
+  const float d1i = FE ? lam.y * ma : lam.y, d2i = FE ? lam.y * mb : lam.y;
+  // |d|^2 lies far inside the normal range, where the approximate division
+  // is within 2 units in the last place
+  const float s1 = __fdividef(scale, fmaf(d1r, d1r, d1i * d1i));
+  const float s2 = __fdividef(scale, fmaf(d2r, d2r, d2i * d2i));
+  const float2 q1 = {d1r * s1, -d1i * s1}, q2 = {d2r * s2, -d2i * s2};
+  const float2 B1 = cmul(A1, q1), B2 = cmul(A2, q2);
+  return {B1.x - B2.y, B1.y + B2.x};
+}
+
+// data: [N][J] in place, N = 256, rows of ld slots (mode_eigs); the tile
+// owns modes q0 .. q0 + 31 from q0 = 32 blk (line L: modes q0 + 2L and
+// q0 + 2L + 1).  STAGED: the tile's values are not in `data` but in a
+// shared-memory tile `stage` of [256][32] floats (time row j at 32 j), which
+// it also returns in; global memory is not touched.  `xbuf` holds kT16Smem
+// bytes.  tw[t] = e^{-2 pi i t / N}; lamf[k] = lambda'_k for k = 0..N/2
+// (lambda'_{N-k} = conj lambda'_k).
+template <bool FE, bool STAGED>
+__device__ __forceinline__ void time_pass16_tile(float* __restrict__ data, float* __restrict__ stage,
+                                                 long long J, int m, int ld, int dim,
+                                                 const float* __restrict__ es,
+                                                 const float* __restrict__ eis,
+                                                 const float2* __restrict__ lamf,
+                                                 ModeEigs<float> me, float tau, float scale_h,
+                                                 const double* __restrict__ scale_dev,
+                                                 const float2* __restrict__ tw, long long blk,
+                                                 unsigned char* xbuf, int tid) {
+  using V = float2;
+  const float scale = scale_dev ? (float)((double)scale_h * scale_dev[0]) : scale_h;
+  V* buf = reinterpret_cast<V*>(xbuf);
+  const long long q0 = blk * kT16Modes;
+  const bool full = q0 + kT16Modes <= J;
+  // Step A layout: line L = tid mod 16, residue r; a warp holds residues w and
+  // w + 8 of 16 lines, so its rows j = r + 16 j2 share their parity.  From
+  // global memory a pair of modes is one 8-byte load when its offset j J + q
+  // is even (J even, or r even; q is even), else two 4-byte loads.
+  const int La = tid & 15;
+  const int r = ((tid >> 4) & 1) * 8 + (tid >> 5);
+  const long long qA = q0 + 2 * La;
+  const bool in0 = qA < J, in1 = qA + 1 < J;
+  const bool vec = full && ((J & 1) == 0 || (r & 1) == 0);
+  float* const colA = STAGED ? stage + 2 * La : data + (in0 ? qA : 0);
+  const long long rstride = STAGED ? (long long)kT16Modes : J;   // floats from time row j to j + 1
+  V* const rowA = buf + La * kT16LineSlots + r;            // element k2 at rowA[17 k2]
+  {
+    V v[16];
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {
+      const float* pp = colA + (long long)(r + 16 * j2) * rstride;
+      if (STAGED || vec) {
+        v[j2] = *reinterpret_cast<const V*>(pp);
+      } else {
+        v[j2].x = in0 ? pp[0] : 0.f;
+        v[j2].y = in1 ? pp[1] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {          // D_eps (Step 1)
+      const float e = es[r + 16 * j2];
+      v[j2].x *= e;
+      v[j2].y *= e;
+    }
+    dft16<-1>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], tw[r * k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) rowA[17 * k2] = v[k2];
+  }
+  __syncthreads();
+  {
+    // Step B layout: line L = tid / 16, class k2 = tid mod 16 (a half-warp
+    // is one line, so the partner class is a lane of the same half-warp)
+    const int lane = tid & 31, k2 = lane & 15, Lb = tid >> 4;
+    V* const rowB = buf + Lb * kT16LineSlots + 17 * k2;    // element j1 at rowB[j1]
+    V y[16];
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) y[j1] = rowB[j1];
+    dft16<-1>(y);                              // y[k1] = X_{k2 + 16 k1}
+    const long long qa = q0 + 2 * Lb;
+    float ma, mua, mb, mub;                    // mass and stiffness eigenvalues of the two modes
+    mode_eigs(qa, J, m, ld, dim, me, ma, mua);
+    mode_eigs(qa + 1, J, m, ld, dim, me, mb, mub);
+    const float tmua = tau * mua, tmub = tau * mub;
+    // X_{N-k} for k = k2 + 16 k1: class (16 - k2) mod 16 at k1' = 15 - k1
+    // (k2 > 0, from lane (16 - k2) of the half-warp) or (16 - k1) mod 16
+    // (k2 = 0, the thread's own).  The new values of k1 < 8 wait in nw until
+    // every partner value has been passed: the second half sends y[7..0].
+    const int src = (lane & 16) | ((16 - k2) & 15);
+    V nw[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+      const V sv = k2 == 0 ? y[(16 - k1) & 15] : y[15 - k1];
+      V Cn;
+      Cn.x = __shfl_sync(0xffffffffu, sv.x, src);
+      Cn.y = __shfl_sync(0xffffffffu, sv.y, src);
+      V lam;
+      if (k1 < 8) {
+        lam = lamf[k2 + 16 * k1];
+      } else {
+        lam = lamf[256 - k2 - 16 * k1];
+        lam.y = -lam.y;
+      }
+      const V z = t16_divide<FE>(y[k1], Cn, lam, ma, tmua, mb, tmub, scale);
+      if (k1 < 8) nw[k1] = z;
+      else y[k1] = z;
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) y[k1] = nw[k1];
+    dft16<+1>(y);                              // y[j1] = sum_k1 Z_{k2 + 16 k1} w16^{-j1 k1}
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) rowB[j1] = y[j1];
+  }
+  __syncthreads();
+  {
+    V v[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) v[k2] = rowA[17 * k2];
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmulc(v[k2], tw[r * k2]);
+    dft16<+1>(v);                              // v[j2] = z_{r + 16 j2} times N e^{...}
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {          // D_eps^{-1} (Step 3)
+      const float e = eis[r + 16 * j2];
+      v[j2].x *= e;
+      v[j2].y *= e;
+    }
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {
+      float* pp = colA + (long long)(r + 16 * j2) * rstride;
+      if (STAGED || vec) {
+        *reinterpret_cast<V*>(pp) = v[j2];
+      } else {
+        if (in0) pp[0] = v[j2].x;
+        if (in1) pp[1] = v[j2].y;
+      }
+    }
   }
 }
 

@@ -18,7 +18,9 @@
 // block needs 64 registers.)
 //
 // The tiles are those of the per-instance pass kernels (bec_passes.cuh) at 8
-// warps per block; sizes: sides 31..255 (n = 32..256) and N = 4..512.
+// warps per block (for N = 256 the time pass takes the four-step tile of
+// 32 modes, as the per-instance FP32 pass does); sizes: sides 31..255
+// (n = 32..256) and N = 4..512.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,21 +72,28 @@ __device__ __forceinline__ void space_pass(const PersistJob& j, int p, long long
   const long long rows = (long long)j.N * j.m;
   const int tid = threadIdx.x;
   if (p == 0) {
-    dst_rows_tile<float, double, float, LOGN, kPWarps>(j.y, j.s, rows, j.m, j.sin2, j.tws, t, sm,
-                                                       tid);
+    dst_rows_tile<float, double, float, LOGN, kPWarps>(j.y, j.s, rows, j.m, j.m, j.ld, j.sin2, j.tws,
+                                                       t, sm, tid);
   } else if (p == 4) {
-    dst_rows_tile<float, float, double, LOGN, kPWarps>(j.s, j.z, rows, j.m, j.sin2, j.tws, t, sm,
-                                                       tid);
+    dst_rows_tile<float, float, double, LOGN, kPWarps>(j.s, j.z, rows, j.m, j.ld, j.m, j.sin2, j.tws,
+                                                       t, sm, tid);
   } else {
     const long long cb = (j.m + 2 * kPWarps - 1) / (2 * kPWarps);
-    dst_cols_tile<float, LOGN, kPWarps>(j.s, j.m, j.m, j.m, j.J, t % cb, t / cb, j.sin2, j.tws, sm,
+    dst_cols_tile<float, LOGN, kPWarps>(j.s, j.m, j.m, j.ld, (long long)j.m * j.ld, t % cb, t / cb,
+                                        j.sin2, j.tws, sm,
                                         tid);
   }
 }
 
 template <int LOGT>
 __device__ __forceinline__ void time_pass(const PersistJob& j, long long t, unsigned char* sm) {
-  time_pass_tile<float, LOGT, kPWarps, false>(j.s, j.J, j.m, 2, j.es, j.eis, j.lamf,
+  if constexpr (LOGT == 8) {       // the four-step tile of the per-instance kernel (256 threads)
+    static_assert(kPThreads == kT16Threads, "the N = 256 time tile takes 256 threads");
+    time_pass16_tile<false, false>(j.s, nullptr, j.J, j.m, j.ld, 2, j.es, j.eis, j.lamf, ModeEigs<float>{j.mu, nullptr},
+                            j.tau, j.scale_h, j.scale_dev, j.twt, t, sm, threadIdx.x);
+    return;
+  }
+  time_pass_tile<float, LOGT, kPWarps, false>(j.s, j.J, j.m, j.ld, 2, j.es, j.eis, j.lamf,
                                               ModeEigs<float>{j.mu, nullptr}, j.tau, j.scale_h,
                                               j.scale_dev, j.twt, nullptr, t, sm, threadIdx.x);
 }
@@ -159,7 +168,7 @@ persist_pinv_kernel(const PersistJob* __restrict__ jobs, const __grid_constant__
 // Dynamic shared memory of one job's largest tile.
 size_t job_smem(int logn, int logt) {
   const size_t sp = (size_t)kPWarps * 2 * dst_line_stride(logn, 4) * sizeof(float);
-  const size_t tm = (size_t)kPWarps * 2 * line_slots(logt) * sizeof(float);
+  const size_t tm = logt == 8 ? kT16Smem : (size_t)kPWarps * 2 * line_slots(logt) * sizeof(float);
   return std::max(sp, tm);
 }
 
@@ -195,7 +204,8 @@ void persist_make_job(const bec_problem* p, const double* y, double* z, const do
   j->eis = p->tab.eis32;
   j->lamf = p->tab.lamf32;
   j->mu = p->tab.mu32;
-  j->J = p->J;
+  j->J = p->Jp;   // the scratch in the layout of the per-instance passes
+  j->ld = p->ld;
   j->tau = (float)p->tau;
   j->scale_h = (float)scale;
   j->m = p->m;
@@ -205,7 +215,8 @@ void persist_make_job(const bec_problem* p, const double* y, double* z, const do
   const long long rows = (long long)p->N * p->m;
   const long long row_tiles = (rows + 2 * kPWarps - 1) / (2 * kPWarps);
   const long long col_tiles = (long long)((p->m + 2 * kPWarps - 1) / (2 * kPWarps)) * p->N;
-  const long long time_tiles = (p->J + 2 * kPWarps - 1) / (2 * kPWarps);
+  const long long time_modes = p->N == 256 ? kT16Modes : 2 * kPWarps;   // modes per time tile
+  const long long time_tiles = (p->Jp + time_modes - 1) / time_modes;
   j->tiles[0] = (int)row_tiles;
   j->tiles[1] = (int)col_tiles;
   j->tiles[2] = (int)time_tiles;
@@ -249,7 +260,7 @@ bec_status persist_launch(const PersistJob* jobs_host, PersistJob* jobs_dev, int
     if (!g_attr_set) {
       BEC_CUDA_TRY(cudaFuncSetAttribute(persist_pinv_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)job_smem(8, 9)));
+                                        (int)std::max(job_smem(8, 9), job_smem(8, 8))));
       g_attr_set = true;
     }
   }

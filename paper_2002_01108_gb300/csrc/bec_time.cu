@@ -15,6 +15,9 @@
 #include "bec_fft.cuh"
 #include "bec_internal.h"
 #include "bec_passes.cuh"
+#include "bec_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace bec {
 namespace {
@@ -33,26 +36,27 @@ __global__ void rinv_table_kernel(double* __restrict__ rinv, long long J, int NK
   const int k = (int)(g - q * NK);
   const double2 L = lamf[k];
   double muM, muK;
-  mode_eigs(q, J, m, dim, me, muM, muK);
+  mode_eigs(q, J, m, m, dim, me, muM, muK);
   const bool fe = me.m != nullptr;
   const double dr = fe ? fma(L.x, muM, tau * muK) : L.x + tau * muK, di = fe ? L.y * muM : L.y;
   rinv[g] = 1.0 / fma(dr, dr, di * di);
 }
 
-// data: [N][J] in place; a block owns W = 2 x warps adjacent modes
-// (time_pass_tile).  registers: 128 per thread in FP64 and 64 in FP32 for
+// data: [N][J] in place, rows of ld slots; a block owns W = 2 x warps
+// adjacent modes (time_pass_tile).  registers: 128 per thread in FP64 and 64 in FP32 for
 // N <= 256 (the block count the bound asks for fills the 64K-register
 // file), free above.  FE: the mass eigenvalues are present (Q1 elements);
 // finite differences (M = I) take the other instantiation, without the
 // products by mu^M.
 template <typename T, int LOGN, int WARPS, bool FE>
 __global__ void __launch_bounds__(WARPS * 32, LOGN <= 8 ? (sizeof(T) == 8 ? 16 : 32) / WARPS : 1)
-time_pass_kernel(T* __restrict__ data, long long J, int m, int dim, const T* __restrict__ es,
+time_pass_kernel(T* __restrict__ data, long long J, int m, int ld, int dim,
+                 const T* __restrict__ es,
                  const T* __restrict__ eis, const v2_t<T>* __restrict__ lamf,
                  ModeEigs<T> me, T tau, T scale_h, const double* __restrict__ scale_dev,
                  const v2_t<T>* __restrict__ tw, const double* __restrict__ rinv) {
   extern __shared__ __align__(16) unsigned char smem_bytes[];
-  time_pass_tile<T, LOGN, WARPS, FE>(data, J, m, dim, es, eis, lamf, me, tau, scale_h, scale_dev,
+  time_pass_tile<T, LOGN, WARPS, FE>(data, J, m, ld, dim, es, eis, lamf, me, tau, scale_h, scale_dev,
                                      tw, rinv, blockIdx.x, smem_bytes, threadIdx.x);
 }
 
@@ -66,13 +70,154 @@ bec_status time_launch(bec_problem* p, void* data, double scale, const double* s
                            : time_pass_kernel<T, LOGN, WARPS, false>;
   if (smem > 48 * 1024)
     BEC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // FP32 data is the preconditioner's scratch, in its layout
+  const long long J = sizeof(T) == 4 ? p->Jp : p->J;
+  const int ld = sizeof(T) == 4 ? p->ld : p->m;
   const long long W = 2 * warps;
-  const unsigned grid = (unsigned)((p->J + W - 1) / W);
+  const unsigned grid = (unsigned)((J + W - 1) / W);
   BEC_LAUNCH_BEGIN(p);
-  k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), p->J, p->m, p->dim, es, eis,
+  k<<<grid, warps * 32, smem, p->stream>>>(static_cast<T*>(data), J, p->m, ld, p->dim, es, eis,
                                            lamf, me, (T)p->tau, (T)scale, scale_dev, tw, rinv);
   BEC_LAUNCH_CHECK(p, "time_pass_kernel");
   return BEC_OK;
+}
+
+// FP32 time pass for N = 256 as a four-step FFT in registers
+// (time_pass16_tile): 256 threads per block, 32 modes per block, the
+// block's values loaded and stored by the threads.  128 registers a thread
+// (two blocks per SM): the 16-point transforms and their twiddles keep many
+// values live; a bound of 80 spilled and ran slower.
+template <bool FE>
+__global__ void __launch_bounds__(kT16Threads, 2)
+time_pass16_kernel(float* __restrict__ data, long long J, int m, int ld, int dim,
+                   const float* __restrict__ es, const float* __restrict__ eis,
+                   const float2* __restrict__ lamf, ModeEigs<float> me, float tau, float scale_h,
+                   const double* __restrict__ scale_dev, const float2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  time_pass16_tile<FE, false>(data, nullptr, J, m, ld, dim, es, eis, lamf, me, tau, scale_h,
+                              scale_dev, tw, blockIdx.x, smem_bytes, threadIdx.x);
+}
+
+// The same pass with the tiles moved by TMA: each block walks tiles blk,
+// blk + grid, ...; while it transforms one tile in shared memory (stage b)
+// the next one arrives in the other stage, and the results leave by a TMA
+// store from the stage they were computed in.  Before a stage is refilled
+// its store must have read it (bulk wait_group.read).  A wait for a tile
+// that runs out (about 0.2 s) sets *err and ends the block.
+constexpr size_t kT16StageBytes = (size_t)kT16Modes * 256 * sizeof(float);   // 32 KB
+constexpr size_t kT16TmaSmem = 2 * kT16StageBytes + kT16Smem + 16;
+
+template <bool FE>
+__global__ void __launch_bounds__(kT16Threads, 2)
+time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int m, int ld,
+                       int dim, const float* __restrict__ es, const float* __restrict__ eis,
+                       const float2* __restrict__ lamf, ModeEigs<float> me, float tau,
+                       float scale_h, const double* __restrict__ scale_dev,
+                       const float2* __restrict__ tw, long long ntiles, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char t16_smem[];
+  float* const stage0 = reinterpret_cast<float*>(t16_smem);
+  float* const stage1 = stage0 + kT16StageBytes / sizeof(float);
+  unsigned char* const xbuf = t16_smem + 2 * kT16StageBytes;
+  const uint32_t bar0 = tma_smem_u32(xbuf + kT16Smem), bar1 = bar0 + 8;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    tma_mbar_init(bar0, 1);
+    tma_mbar_init(bar1, 1);
+    tma_fence_mbar_init();
+  }
+  __syncthreads();
+  long long t = blockIdx.x;
+  if (tid == 0 && t < ntiles) {
+    tma_mbar_expect_tx(bar0, (uint32_t)kT16StageBytes);
+    tma_load_2d(tma_smem_u32(stage0), &map, (int)(t * kT16Modes), 0, bar0);
+  }
+  int it = 0;
+  bool ok = true;
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    float* const st = b ? stage1 : stage0;
+    if (tid == 0 && t + gridDim.x < ntiles) {       // prefetch the next tile into the other stage
+      tma_wait_group_read0();
+      const uint32_t nb = b ? bar0 : bar1;
+      tma_mbar_expect_tx(nb, (uint32_t)kT16StageBytes);
+      tma_load_2d(tma_smem_u32(b ? stage0 : stage1), &map, (int)((t + gridDim.x) * kT16Modes), 0,
+                  nb);
+    }
+    const bool got = tma_mbar_wait(b ? bar1 : bar0, (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    time_pass16_tile<FE, true>(nullptr, st, J, m, ld, dim, es, eis, lamf, me, tau, scale_h,
+                               scale_dev, tw, t, xbuf, tid);
+    tma_fence_proxy_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_2d(&map, (int)(t * kT16Modes), 0, tma_smem_u32(st));
+      tma_commit_group();
+    }
+  }
+  if (tid == 0) {
+    if (!ok) {
+      atomicExch(err, 1);
+      // the prefetch issued in the failed iteration may still be in flight
+      if (t + gridDim.x < ntiles) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
+                                                (uint32_t)(((it + 1) >> 1) & 1));
+    }
+    tma_wait_group0();
+  }
+}
+
+bec_status time16_launch(bec_problem* p, void* data, double scale, const double* scale_dev) {
+  const PcTables& t = p->tab;
+  const ModeEigs<float> me{t.mu32, t.mum32};
+  const long long ntiles = (p->Jp + kT16Modes - 1) / kT16Modes;
+  if (p->time_map_ok && data == p->pc_scratch) {
+    auto k = me.m != nullptr ? time_pass16_tma_kernel<true> : time_pass16_tma_kernel<false>;
+    static bool attr_set = false;
+    if (!attr_set) {
+      BEC_CUDA_TRY(cudaFuncSetAttribute(time_pass16_tma_kernel<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kT16TmaSmem));
+      BEC_CUDA_TRY(cudaFuncSetAttribute(time_pass16_tma_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kT16TmaSmem));
+      attr_set = true;
+    }
+    int sms = 0;
+    BEC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    const long long grid = ntiles < 2LL * sms ? ntiles : 2LL * sms;
+    BEC_LAUNCH_BEGIN(p);
+    k<<<(unsigned)grid, kT16Threads, kT16TmaSmem, p->stream>>>(
+        p->time_map, p->Jp, p->m, p->ld, p->dim, t.es32, t.eis32, t.lamf32, me, (float)p->tau,
+        (float)scale, scale_dev, t.time.tw32, ntiles, p->pc_err);
+    BEC_LAUNCH_CHECK(p, "time_pass16_tma_kernel");
+    return BEC_OK;
+  }
+  auto k = me.m != nullptr ? time_pass16_kernel<true> : time_pass16_kernel<false>;
+  BEC_LAUNCH_BEGIN(p);
+  k<<<(unsigned)ntiles, kT16Threads, kT16Smem, p->stream>>>(
+      static_cast<float*>(data), p->Jp, p->m, p->ld, p->dim, t.es32, t.eis32, t.lamf32, me,
+      (float)p->tau, (float)scale, scale_dev, t.time.tw32);
+  BEC_LAUNCH_CHECK(p, "time_pass16_kernel");
+  return BEC_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 time_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
 }
 
 // The block width w (warps per block) is tunable for N >= 32; shorter
@@ -291,8 +436,44 @@ bec_status launch_time_pass_w(bec_problem* p, void* data, int fp64, double scale
   if (fp64)
     return time_dispatch<double>(p, w, data, scale, scale_dev, t.es64, t.eis64, t.lamf64,
                                  ModeEigs<double>{t.mu64, t.mum64}, t.time.tw64, t.rinv64);
+  if (time16_applies(p)) return time16_launch(p, data, scale, scale_dev);
   return time_dispatch<float>(p, w, data, scale, scale_dev, t.es32, t.eis32, t.lamf32,
                               ModeEigs<float>{t.mu32, t.mum32}, t.time.tw32, nullptr);
+}
+
+bool time16_applies(const bec_problem* p) {
+  return p->desc.precision == BEC_PC_FP32 && p->tab.time.logn == 8;
+}
+
+bec_status time16_make_map(bec_problem* p) {
+  p->time_map_ok = false;
+  // a TMA tile needs 16-byte aligned time slices (Jp a multiple of 4 floats)
+  if (!time16_applies(p) || p->pc_scratch == nullptr || p->Jp % 4 != 0) return BEC_OK;
+  auto fn = time_encode_fn();
+  if (fn == nullptr) return BEC_OK;              // the per-thread-load kernel runs instead
+  const cuuint64_t dims[2] = {(cuuint64_t)p->Jp, (cuuint64_t)p->N};
+  const cuuint64_t strides[1] = {(cuuint64_t)p->Jp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kT16Modes, 256};
+  const cuuint32_t es[2] = {1, 1};
+  if (fn(&p->time_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->pc_scratch, dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (time pass)");
+    return BEC_ECUDA;
+  }
+  p->time_map_ok = true;
+  return BEC_OK;
+}
+
+bec_status pc_check(bec_problem* p) {
+  if (p->pc_err == nullptr) return BEC_OK;
+  int v = 0;
+  BEC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  BEC_CUDA_TRY(cudaMemcpy(&v, p->pc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v == 0) return BEC_OK;
+  BEC_CUDA_TRY(cudaMemset(p->pc_err, 0, sizeof(int)));
+  set_error("a bounded wait for a time-pass tile ran out");
+  return BEC_ETIMEOUT;
 }
 
 bec_status launch_time_pass(bec_problem* p, void* data, int fp64, double scale,

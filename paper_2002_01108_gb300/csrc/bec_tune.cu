@@ -22,6 +22,7 @@
 
 #include "bec_fft.cuh"
 #include "bec_internal.h"
+#include "bec_passes.cuh"
 
 namespace bec {
 namespace {
@@ -105,7 +106,8 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
       p->tile = it->second;
       r.rows_warps = p->tile.rows ? p->tile.rows : default_width(0, tsize);
       r.cols_warps = p->tile.cols ? p->tile.cols : default_width(1, tsize);
-      r.time_warps = p->tile.time ? p->tile.time : default_width(2, tsize);
+      r.time_warps = time16_applies(p) ? kT16Threads / 32
+                     : p->tile.time ? p->tile.time : default_width(2, tsize);
       r.cached = 1;
       if (rep) *rep = r;
       return BEC_OK;
@@ -117,7 +119,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   double* x = p->V;
   void* s = p->pc_scratch;
   BEC_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)p->U * sizeof(double), p->stream));
-  if (!fp64) BEC_CUDA_TRY(cudaMemsetAsync(s, 0, (size_t)p->U * sizeof(float), p->stream));
+  if (!fp64) BEC_CUDA_TRY(cudaMemsetAsync(s, 0, (size_t)p->N * p->Jp * sizeof(float), p->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BEC_CUDA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -131,6 +133,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   bec_status st = BEC_OK;
   for (int which = 0; which < 3 && st == BEC_OK; ++which) {
     if (which == 1 && p->dim < 2) continue;
+    if (which == 2 && time16_applies(p)) continue;   // fixed block of 8 warps
     const int logn = which == 2 ? p->tab.time.logn : p->tab.space.logn;
     if (logn < 5) continue;                       // short transforms: default width only
     float best_ms = -1.f;
@@ -176,7 +179,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   }
   r.rows_warps = best[0] ? best[0] : default_width(0, tsize);
   r.cols_warps = best[1] ? best[1] : default_width(1, tsize);
-  r.time_warps = best[2] ? best[2] : default_width(2, tsize);
+  r.time_warps = time16_applies(p) ? kT16Threads / 32 : best[2] ? best[2] : default_width(2, tsize);
   if (rep) *rep = r;
   return BEC_OK;
 }

@@ -51,7 +51,8 @@ def test_apply_A_3d(m, N, a):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("m,N,eps", [(7, 8, 0.1), (15, 32, 0.0625), (31, 16, 1e-3), (63, 8, 0.5)])
+@pytest.mark.parametrize("m,N,eps", [(7, 8, 0.1), (15, 32, 0.0625), (31, 16, 1e-3), (63, 8, 0.5),
+                                     (15, 256, 0.0625)])
 def test_apply_Pinv_3d_matches_oracle(precision, m, N, eps):
     from paper_2002_01108_gb300 import Problem
     a = 1.0

@@ -37,7 +37,8 @@ def _persistent_cases():
     """Shapes the persistent launch covers: sides 31..255, N 4..512."""
     out = []
     for i, (m, N, eps) in enumerate([(31, 8, 1e-3), (63, 32, 0.05), (255, 4, 0.1), (31, 512, 1.0),
-                                     (127, 8, 1e-4), (63, 64, 0.5), (31, 32, 0.02), (255, 16, 0.2)]):
+                                     (127, 8, 1e-4), (63, 64, 0.5), (31, 32, 0.02), (255, 16, 0.2),
+                                     (63, 256, 0.01)]):
         out.append(heat_case_2d(seed=60 + i, m=m, N=N, eps=eps))
     return out
 

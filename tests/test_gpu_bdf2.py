@@ -128,7 +128,8 @@ def test_bdf2_right_hand_side(space):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("space,dim,m,N,eps,a", [
     ("fd", 1, 63, 64, 0.05, 1.0), ("fd", 2, 63, 32, 1e-4, 1.0), ("fd", 2, 127, 16, 0.0625, 1.0),
-    ("q1", 2, 31, 16, 0.1, 1e-2), ("q1", 2, 63, 8, 0.0625, 1e-5)])
+    ("q1", 2, 31, 16, 0.1, 1e-2), ("q1", 2, 63, 8, 0.0625, 1e-5),
+    ("fd", 2, 31, 256, 0.05, 1.0), ("q1", 2, 15, 256, 0.1, 1e-2)])
 def test_bdf2_apply_Pinv_matches_oracle(precision, space, dim, m, N, eps, a):
     M, K = mats(space, dim, m, a)
     tau = 1.0 / N

@@ -88,7 +88,7 @@ def test_q1_right_hand_side_has_M_u0():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("dim,m,N,eps,a", [(2, 31, 16, 0.1, 1e-2), (2, 63, 8, 0.0625, 1e-5),
-                                           (1, 127, 32, 0.05, 1.0)])
+                                           (1, 127, 32, 0.05, 1.0), (2, 31, 256, 0.1, 1e-2)])
 def test_q1_apply_Pinv_matches_banded_lu(precision, dim, m, N, eps, a):
     from paper_2002_01108_gb300 import Problem
     M, K = mats(dim, m, a)
