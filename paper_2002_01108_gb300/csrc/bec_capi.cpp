@@ -306,6 +306,7 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
       if (e != cudaSuccess) s = cuda_fail(e, "cudaMemset");
     }
     if (s == BEC_OK) s = time16_make_map(p);
+    if (s == BEC_OK) s = cols16_make_map(p);
   }
   chain(dmalloc(&p->V, (size_t)(R + 1) * U));
   if (d->flexible) chain(dmalloc(&p->Z, (size_t)R * U));

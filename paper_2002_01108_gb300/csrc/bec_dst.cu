@@ -7,6 +7,9 @@
 #include "bec_fft.cuh"
 #include "bec_internal.h"
 #include "bec_passes.cuh"
+#include "bec_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace bec {
 namespace {
@@ -56,6 +59,94 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
   for (long long sl = blockIdx.y; sl < nslices; sl += gridDim.y)
     dst_cols_tile<T, LOGN, WARPS>(data, m, ncols, row_stride, slice_stride, blockIdx.x, sl, sin2,
                                   tw, smem_bytes, threadIdx.x);
+}
+
+// FP32 y-DST for n = 256 (2D) on the four-step tile (dst16_cols_core), the
+// tiles moved by TMA: each block walks tiles blk, blk + grid, ... (tile t:
+// columns 32 (t mod tiles_x) .. + 31 of slice t / tiles_x), transforming one
+// in its shared-memory stage while the next arrives in the other stage;
+// results leave by a TMA store from the stage they were computed in, which
+// is refilled only after the store has read it.  A wait that runs out
+// (about 0.2 s) sets *err and ends the block.
+constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16;
+
+__global__ void __launch_bounds__(kD16Threads, 2)
+dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __restrict__ sin2,
+                      const float2* __restrict__ tw, int tiles_x, long long ntiles,
+                      uint32_t tile_bytes, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char d16_smem[];
+  float* const stage0 = reinterpret_cast<float*>(d16_smem);
+  float* const stage1 = stage0 + kD16StageBytes / sizeof(float);
+  float2* const tot = reinterpret_cast<float2*>(d16_smem + 2 * kD16StageBytes);
+  const uint32_t bar0 = tma_smem_u32(d16_smem + 2 * kD16StageBytes + kD16TotBytes), bar1 = bar0 + 8;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    tma_mbar_init(bar0, 1);
+    tma_mbar_init(bar1, 1);
+    tma_fence_mbar_init();
+  }
+  __syncthreads();
+  long long t = blockIdx.x;
+  if (tid == 0 && t < ntiles) {
+    tma_mbar_expect_tx(bar0, tile_bytes);
+    tma_load_3d(tma_smem_u32(stage0), &map, (int)(t % tiles_x) * kD16Cols, 0, (int)(t / tiles_x),
+                bar0);
+  }
+  int it = 0;
+  bool ok = true;
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    float* const st = b ? stage1 : stage0;
+    const long long tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {                 // prefetch the next tile into the other stage
+      tma_wait_group_read0();
+      const uint32_t nb = b ? bar0 : bar1;
+      tma_mbar_expect_tx(nb, tile_bytes);
+      tma_load_3d(tma_smem_u32(b ? stage0 : stage1), &map, (int)(tn % tiles_x) * kD16Cols, 0,
+                  (int)(tn / tiles_x), nb);
+    }
+    const bool got = tma_mbar_wait(b ? bar1 : bar0, (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    dst16_cols_core(st, tot, sin2, tw, tid);
+    tma_fence_proxy_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_3d(&map, (int)(t % tiles_x) * kD16Cols, 0, (int)(t / tiles_x), tma_smem_u32(st));
+      tma_commit_group();
+    }
+  }
+  if (tid == 0) {
+    if (!ok) {
+      atomicExch(err, 1);
+      if (t + gridDim.x < ntiles) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
+                                                (uint32_t)(((it + 1) >> 1) & 1));
+    }
+    tma_wait_group0();
+  }
+}
+
+bec_status cols16_launch(bec_problem* p) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    BEC_CUDA_TRY(cudaFuncSetAttribute(dst_cols16_tma_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kD16TmaSmem));
+    attr_set = true;
+  }
+  const int tiles_x = (p->ld + kD16Cols - 1) / kD16Cols;
+  const long long ntiles = (long long)tiles_x * p->N;
+  int sms = 0;
+  BEC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  const long long grid = ntiles < 2LL * sms ? ntiles : 2LL * sms;
+  const uint32_t tile_bytes = (uint32_t)(kD16Cols * p->m * sizeof(float));
+  BEC_LAUNCH_BEGIN(p);
+  dst_cols16_tma_kernel<<<(unsigned)grid, kD16Threads, kD16TmaSmem, p->stream>>>(
+      p->cols_map, p->tab.sin2_32, p->tab.space.tw32, tiles_x, ntiles, tile_bytes, p->pc_err);
+  BEC_LAUNCH_CHECK(p, "dst_cols16_tma_kernel");
+  return BEC_OK;
 }
 
 template <typename Kern>
@@ -213,7 +304,43 @@ bec_status launch_dst_rows_w(bec_problem* p, const void* in, int in_fp64, void* 
   return BEC_EINVAL;
 }
 
+bool cols16_applies(const bec_problem* p) {
+  return p->desc.precision == BEC_PC_FP32 && p->dim == 2 && p->tab.space.logn == 8 &&
+         p->cols_map_ok;
+}
+
+bec_status cols16_make_map(bec_problem* p) {
+  p->cols_map_ok = false;
+  if (p->desc.precision != BEC_PC_FP32 || p->dim != 2 || p->tab.space.logn != 8 ||
+      p->pc_scratch == nullptr || p->ld % 4 != 0)
+    return BEC_OK;
+  void* ptr = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return BEC_OK;                                  // the per-warp column kernel runs instead
+  }
+  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  // the scratch as [N][m][ld] floats; a box is 32 columns of one slice
+  const cuuint64_t dims[3] = {(cuuint64_t)p->ld, (cuuint64_t)p->m, (cuuint64_t)p->N};
+  const cuuint64_t strides[2] = {(cuuint64_t)p->ld * sizeof(float),
+                                 (cuuint64_t)p->ld * p->m * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kD16Cols, (cuuint32_t)p->m, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (fn(&p->cols_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->pc_scratch, dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (column pass)");
+    return BEC_ECUDA;
+  }
+  p->cols_map_ok = true;
+  return BEC_OK;
+}
+
 bec_status launch_dst_cols_w(bec_problem* p, void* data, int fp64, int w) {
+  if (!fp64 && data == p->pc_scratch && cols16_applies(p)) return cols16_launch(p);
   if (fp64) return cols_dispatch<double>(p, w, data, p->tab.sin2_64, p->tab.space.tw64);
   return cols_dispatch<float>(p, w, data, p->tab.sin2_32, p->tab.space.tw32);
 }

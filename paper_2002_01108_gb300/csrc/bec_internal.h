@@ -127,6 +127,8 @@ struct bec_problem {
   int* pc_err = nullptr;        // device word: a bounded wait of the time pass ran out
   bool time_map_ok = false;     // time_map describes pc_scratch for the N = 256 time pass
   CUtensorMap time_map;
+  bool cols_map_ok = false;     // cols_map describes pc_scratch for the n = 256 column pass
+  CUtensorMap cols_map;
 
   // Krylov workspace (FP64)
   double* V = nullptr;          // (max_restart + 1) x U
@@ -252,6 +254,9 @@ bool time16_applies(const bec_problem* p);
 // describes pc_scratch to the TMA unit for that kernel (at allocation;
 // leaves time_map_ok false when the layout or the driver does not allow it)
 bec_status time16_make_map(bec_problem* p);
+// the same for the FP32 2D column pass with n = 256 (dst_cols16_tma_kernel)
+bec_status cols16_make_map(bec_problem* p);
+bool cols16_applies(const bec_problem* p);
 // BEC_ETIMEOUT (and clears the word) when a bounded wait of the time pass
 // ran out since the last check; synchronises the problem's stream
 bec_status pc_check(bec_problem* p);

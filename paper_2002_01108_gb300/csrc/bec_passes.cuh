@@ -492,5 +492,113 @@ __device__ __forceinline__ void time_pass16_tile(float* __restrict__ data, float
   }
 }
 
+// ------------------------------------------------- y-DST, FP32, n = 256
+// The DST-I down 32 adjacent columns of one slice (n = 256, m = 255 rows),
+// with the same four-step 16 x 16 FFT in registers as the N = 256 time
+// pass.  Column pairs (2L, 2L + 1) are one complex line; the DST of a line
+// is the length-n FFT of y_j = 2 sin(j pi / n)(x_j + x_{n-j}) + (x_j -
+// x_{n-j}), then for k < n/2 the even outputs 4 S_{2k} = e_k and the odd
+// ones 4 S_{2k+1} = sum_{k' <= k} r_{k'} (the method of warp_dst_pair).
+// The tile sits in a shared-memory stage of [256][32] floats (row i holds
+// x_{i+1}; row 255 is not used) and returns there as rows of S (row i holds
+// 4 S_{i+1}).  The exchange buffer of the 16 x 16 steps is the stage itself,
+// XOR-swizzled (line L, class k2, index j1 at 256 L + 16 k2 + (j1 ^ k2 ^ L)),
+// which keeps both of its access patterns free of bank conflicts; `tot`
+// holds 256 float2.  sin2[j] = 2 sin(j pi / n), tw[t] = e^{-2 pi i t / n}.
+constexpr int kD16Threads = 256;
+constexpr int kD16Cols = 32;                                // columns per tile
+constexpr size_t kD16StageBytes = (size_t)256 * kD16Cols * sizeof(float);   // 32 KB
+constexpr size_t kD16TotBytes = 256 * sizeof(float2);
+
+__device__ __forceinline__ int d16_xs(int L, int k2, int j1) {
+  return 256 * L + 16 * k2 + ((j1 ^ k2 ^ L) & 15);
+}
+
+__device__ __forceinline__ void dst16_cols_core(float* __restrict__ stage, float2* __restrict__ tot,
+                                                const float* __restrict__ sin2,
+                                                const float2* __restrict__ tw, int tid) {
+  using V = float2;
+  V* const sv = reinterpret_cast<V*>(stage);              // row i, line L at sv[16 i + L]
+  // Step A layout (as in time_pass16_tile): line L, residue r of j mod 16
+  const int La = tid & 15;
+  const int r = ((tid >> 4) & 1) * 8 + (tid >> 5);
+  V v[16];
+#pragma unroll
+  for (int j2 = 0; j2 < 16; ++j2) {
+    const int j = r + 16 * j2;                            // x_j at row j - 1, x_{n-j} at 255 - j
+    V y = {0.f, 0.f};                                     // y_0 = 0 (x_0 = x_n = 0)
+    if (j2 > 0 || r > 0) {
+      const V xa = sv[16 * (j - 1) + La], xb = sv[16 * (255 - j) + La];
+      const float s = sin2[j];
+      y.x = fmaf(s, xa.x + xb.x, xa.x - xb.x);
+      y.y = fmaf(s, xa.y + xb.y, xa.y - xb.y);
+    }
+    v[j2] = y;
+  }
+  __syncthreads();                                        // the stage becomes the exchange buffer
+  dft16<-1>(v);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], tw[r * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) sv[d16_xs(La, k2, r)] = v[k2];
+  __syncthreads();
+  // Step B layout: line L = tid / 16, class k2 = tid mod 16
+  const int lane = tid & 31, k2 = lane & 15, Lb = tid >> 4;
+  V y[16];
+#pragma unroll
+  for (int j1 = 0; j1 < 16; ++j1) y[j1] = sv[d16_xs(Lb, k2, j1)];
+  __syncthreads();                                        // the stage becomes the r / e buffers
+  dft16<-1>(y);                                           // y[k1] = X_{k2 + 16 k1}
+  // X_{n-k} for k = k2 + 16 k1 < n/2 (k1 < 8): as in time_pass16_tile
+  V* const rb = sv;                                       // r_k of line L at rb[129 L + k]
+  V* const eb = sv + 16 * 129;                            // e_k (k >= 1) at eb[127 L + k - 1]
+  const int src = (lane & 16) | ((16 - k2) & 15);
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    const V s = k2 == 0 ? y[(16 - k1) & 15] : y[15 - k1];
+    V Cn;
+    Cn.x = __shfl_sync(0xffffffffu, s.x, src);
+    Cn.y = __shfl_sync(0xffffffffu, s.y, src);
+    const V C = y[k1];
+    const int k = k2 + 16 * k1;
+    if (k == 0) {
+      rb[129 * Lb] = C;
+    } else {
+      rb[129 * Lb + k] = {C.x + Cn.x, C.y + Cn.y};
+      eb[127 * Lb + k - 1] = {Cn.y - C.y, C.x - Cn.x};
+    }
+  }
+  __syncthreads();
+  // Output layout: chunk c = tid / 16 owns k = 8c .. 8c + 7 of line L = tid
+  // mod 16: a serial running sum, the chunk totals of the lower chunks, and
+  // rows 2k (odd outputs) and 2k - 1 (even outputs) of the stage.
+  const int c = tid >> 4, L = tid & 15;
+  V P[8], E[8];
+  V run = {0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = 8 * c + i;
+    const V rv = rb[129 * L + k];
+    run.x += rv.x;
+    run.y += rv.y;
+    P[i] = run;
+    E[i] = (k > 0) ? eb[127 * L + k - 1] : V{0.f, 0.f};
+  }
+  tot[16 * c + L] = run;
+  __syncthreads();
+  V off = {0.f, 0.f};
+  for (int cc = 0; cc < c; ++cc) {
+    const V t = tot[16 * cc + L];
+    off.x += t.x;
+    off.y += t.y;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = 8 * c + i;
+    sv[16 * (2 * k) + L] = {off.x + P[i].x, off.y + P[i].y};   // 4 S_{2k+1}
+    if (k > 0) sv[16 * (2 * k - 1) + L] = E[i];                // 4 S_{2k}
+  }
+}
+
 }  // namespace
 }  // namespace bec

@@ -18,8 +18,9 @@
 // block needs 64 registers.)
 //
 // The tiles are those of the per-instance pass kernels (bec_passes.cuh) at 8
-// warps per block (for N = 256 the time pass takes the four-step tile of
-// 32 modes, as the per-instance FP32 pass does); sizes: sides 31..255
+// warps per block (for N = 256 the time pass, and for n = 256 the y-DST,
+// take the four-step tiles of 32 modes or columns, as the per-instance FP32
+// passes do); sizes: sides 31..255
 // (n = 32..256) and N = 4..512.
 #include <cuda_runtime.h>
 
@@ -77,6 +78,26 @@ __device__ __forceinline__ void space_pass(const PersistJob& j, int p, long long
   } else if (p == 4) {
     dst_rows_tile<float, float, double, LOGN, kPWarps>(j.s, j.z, rows, j.m, j.ld, j.m, j.sin2, j.tws,
                                                        t, sm, tid);
+  } else if constexpr (LOGN == 8) {
+    // the four-step column tile of the per-instance kernel (32 columns of one
+    // slice), its stage filled and emptied with plain 16-byte copies
+    static_assert(kPThreads == kD16Threads, "the n = 256 column tile takes 256 threads");
+    const int cb = j.ld / kD16Cols;
+    float* const st = reinterpret_cast<float*>(sm);
+    float* const base = j.s + (t / cb) * (long long)j.m * j.ld + (t % cb) * kD16Cols;
+    for (int e = tid; e < j.m * (kD16Cols / 4); e += kPThreads) {
+      const int row = e / (kD16Cols / 4), c4 = e - row * (kD16Cols / 4);
+      reinterpret_cast<float4*>(st)[e] =
+          *reinterpret_cast<const float4*>(base + (long long)row * j.ld + 4 * c4);
+    }
+    __syncthreads();
+    dst16_cols_core(st, reinterpret_cast<float2*>(sm + kD16StageBytes), j.sin2, j.tws, tid);
+    __syncthreads();
+    for (int e = tid; e < j.m * (kD16Cols / 4); e += kPThreads) {
+      const int row = e / (kD16Cols / 4), c4 = e - row * (kD16Cols / 4);
+      *reinterpret_cast<float4*>(base + (long long)row * j.ld + 4 * c4) =
+          reinterpret_cast<const float4*>(st)[e];
+    }
   } else {
     const long long cb = (j.m + 2 * kPWarps - 1) / (2 * kPWarps);
     dst_cols_tile<float, LOGN, kPWarps>(j.s, j.m, j.m, j.ld, (long long)j.m * j.ld, t % cb, t / cb,
@@ -167,7 +188,8 @@ persist_pinv_kernel(const PersistJob* __restrict__ jobs, const __grid_constant__
 
 // Dynamic shared memory of one job's largest tile.
 size_t job_smem(int logn, int logt) {
-  const size_t sp = (size_t)kPWarps * 2 * dst_line_stride(logn, 4) * sizeof(float);
+  const size_t sp = logn == 8 ? kD16StageBytes + kD16TotBytes
+                              : (size_t)kPWarps * 2 * dst_line_stride(logn, 4) * sizeof(float);
   const size_t tm = logt == 8 ? kT16Smem : (size_t)kPWarps * 2 * line_slots(logt) * sizeof(float);
   return std::max(sp, tm);
 }
@@ -214,7 +236,9 @@ void persist_make_job(const bec_problem* p, const double* y, double* z, const do
   j->logt = p->tab.time.logn;
   const long long rows = (long long)p->N * p->m;
   const long long row_tiles = (rows + 2 * kPWarps - 1) / (2 * kPWarps);
-  const long long col_tiles = (long long)((p->m + 2 * kPWarps - 1) / (2 * kPWarps)) * p->N;
+  const long long col_tiles = p->tab.space.logn == 8
+                                  ? (long long)(p->ld / kD16Cols) * p->N
+                                  : (long long)((p->m + 2 * kPWarps - 1) / (2 * kPWarps)) * p->N;
   const long long time_modes = p->N == 256 ? kT16Modes : 2 * kPWarps;   // modes per time tile
   const long long time_tiles = (p->Jp + time_modes - 1) / time_modes;
   j->tiles[0] = (int)row_tiles;

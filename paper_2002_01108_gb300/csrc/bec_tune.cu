@@ -105,7 +105,8 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
     if (it != cache().end()) {
       p->tile = it->second;
       r.rows_warps = p->tile.rows ? p->tile.rows : default_width(0, tsize);
-      r.cols_warps = p->tile.cols ? p->tile.cols : default_width(1, tsize);
+      r.cols_warps = cols16_applies(p) ? kD16Threads / 32
+                     : p->tile.cols ? p->tile.cols : default_width(1, tsize);
       r.time_warps = time16_applies(p) ? kT16Threads / 32
                      : p->tile.time ? p->tile.time : default_width(2, tsize);
       r.cached = 1;
@@ -134,6 +135,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
   for (int which = 0; which < 3 && st == BEC_OK; ++which) {
     if (which == 1 && p->dim < 2) continue;
     if (which == 2 && time16_applies(p)) continue;   // fixed block of 8 warps
+    if (which == 1 && cols16_applies(p)) continue;   // likewise
     const int logn = which == 2 ? p->tab.time.logn : p->tab.space.logn;
     if (logn < 5) continue;                       // short transforms: default width only
     float best_ms = -1.f;
@@ -178,7 +180,7 @@ bec_status autotune(bec_problem* p, int force, bec_tune_report* rep) {
     append_cache_file(key, p->tile);
   }
   r.rows_warps = best[0] ? best[0] : default_width(0, tsize);
-  r.cols_warps = best[1] ? best[1] : default_width(1, tsize);
+  r.cols_warps = cols16_applies(p) ? kD16Threads / 32 : best[1] ? best[1] : default_width(1, tsize);
   r.time_warps = time16_applies(p) ? kT16Threads / 32 : best[2] ? best[2] : default_width(2, tsize);
   if (rep) *rep = r;
   return BEC_OK;

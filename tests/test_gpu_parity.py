@@ -142,7 +142,9 @@ def test_apply_Pinv_fp64_matches_oracle(dim, m, N, eps):
                                          (2, 127, 32, 1e-2), (2, 7, 4, 1e-4),
                                          # N = 256: the four-step time pass, ragged last tiles
                                          (1, 63, 256, 0.0625), (2, 31, 256, 1e-4),
-                                         (2, 255, 256, 0.0625)])
+                                         (2, 255, 256, 0.0625),
+                                         # n = 256: the four-step column pass
+                                         (2, 255, 8, 0.1)])
 def test_apply_Pinv_fp32_within_single_precision_bound(dim, m, N, eps):
     y = np.random.default_rng(2000 + N + m).uniform(-1, 1, (N,) + (m,) * dim)
     with problem(dim, m, N, precision="fp32") as p:
