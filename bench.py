@@ -52,11 +52,14 @@ ALGO = {
     "dst_rows_kernel": {"flops": 2.5 * (LOG2N + 1)},
     "dst_cols_kernel": {"flops": 2.5 * (LOG2N + 1)},
     "time_pass_kernel": {"flops": 5.0 * LOG2T + 8.0},
+    "dst_cols16_tma_kernel": {"flops": 2.5 * (LOG2N + 1)},
+    "time_pass16_tma_kernel": {"flops": 5.0 * LOG2T + 8.0},
     "apply_L_kernel": {"flops": 7.0},
 }
 BYTES_PER_UNIT = {"fp64": {"dst_rows_kernel": 16.0, "dst_cols_kernel": 16.0, "time_pass_kernel": 16.0,
                            "apply_L_kernel": 16.0},
                   "fp32": {"dst_rows_kernel": 12.0, "dst_cols_kernel": 8.0, "time_pass_kernel": 8.0,
+                           "dst_cols16_tma_kernel": 8.0, "time_pass16_tma_kernel": 8.0,
                            "apply_L_kernel": 16.0}}
 # Multigrid route (variable coefficient): algorithmic bytes per unit, a unit
 # being one (grid point, frequency) pair of the level the kernel runs on, in
@@ -112,23 +115,28 @@ KERNEL_SOURCES = {
     "dst_rows_kernel": ("bec_dst.cu", "bec_passes.cuh", "bec_fft.cuh"),
     "dst_cols_kernel": ("bec_dst.cu", "bec_passes.cuh", "bec_fft.cuh"),
     "time_pass_kernel": ("bec_time.cu", "bec_passes.cuh", "bec_fft.cuh"),
+    "dst_cols16_tma_kernel": ("bec_dst.cu", "bec_passes.cuh", "bec_fft.cuh", "bec_tma.cuh"),
+    "time_pass16_tma_kernel": ("bec_time.cu", "bec_passes.cuh", "bec_fft.cuh", "bec_tma.cuh"),
 }
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): (133212928 + 80690944, "ac42ee24b80dc569"),
-    ("dst_cols_kernel", "fp64"): (133255680 + 73828608, "ac42ee24b80dc569"),
-    ("time_pass_kernel", "fp64"): (200413952 + 75095552, "4f4748d01d7ca262"),
-    ("dst_rows_kernel", "fp32"): (133223168 + 31759872, "ac42ee24b80dc569"),
-    ("dst_cols_kernel", "fp32"): (66602496 + 7979008, "ac42ee24b80dc569"),
-    ("time_pass_kernel", "fp32"): (66641408 + 7933696, "4f4748d01d7ca262"),
+    ("dst_rows_kernel", "fp64"): (133214976 + 80398592, "5b5d539621edbefa"),
+    ("dst_cols_kernel", "fp64"): (133254912 + 73801984, "5b5d539621edbefa"),
+    ("time_pass_kernel", "fp64"): (200446464 + 75163648, "eec57d01e995c7fc"),
+    ("dst_rows_kernel", "fp32"): (133205248 + 33935360, "5b5d539621edbefa"),
+    ("dst_cols16_tma_kernel", "fp32"): (66874880 + 3591936, "1d4635b6ce7187ac"),
+    ("time_pass16_tma_kernel", "fp32"): (66899712 + 4049920, "ac59da95e3727d01"),
 }
-# DRAM bytes of one whole P_eps^-1 apply (the five passes of the same capture)
+# DRAM bytes of one whole P_eps^-1 apply (the five passes of the same
+# capture) and the kernels whose sources they were taken on
 NCU_PINV_BYTES = {
-    "fp64": ((133212928 + 80690944) + (133255680 + 73828608) + (200413952 + 75095552)
-             + (133209856 + 73769728) + (133210112 + 70222592),
-             ("ac42ee24b80dc569", "4f4748d01d7ca262")),
-    "fp32": ((133223168 + 31759872) + (66602496 + 7979008) + (66641408 + 7933696)
-             + (66602496 + 7978752) + (66630144 + 69404672),
-             ("ac42ee24b80dc569", "4f4748d01d7ca262")),
+    "fp64": ((133214976 + 80398592) + (133254912 + 73801984) + (200446464 + 75163648)
+             + (133319936 + 73796864) + (133241344 + 70547200),
+             {"dst_rows_kernel": "5b5d539621edbefa", "dst_cols_kernel": "5b5d539621edbefa",
+              "time_pass_kernel": "eec57d01e995c7fc"}),
+    "fp32": ((133205248 + 33935360) + (66874880 + 3591936) + (66899712 + 4049920)
+             + (66874368 + 3675392) + (66876672 + 69580288),
+             {"dst_rows_kernel": "5b5d539621edbefa", "dst_cols16_tma_kernel": "1d4635b6ce7187ac",
+              "time_pass16_tma_kernel": "ac59da95e3727d01"}),
 }
 
 
@@ -154,9 +162,8 @@ def ncu_pinv_bytes(form: str):
     ent = NCU_PINV_BYTES.get(form)
     if ent is None:
         return None
-    now = (source_sha16(KERNEL_SOURCES["dst_rows_kernel"]),
-           source_sha16(KERNEL_SOURCES["time_pass_kernel"]))
-    return ent[0] if now == ent[1] else None
+    same = all(source_sha16(KERNEL_SOURCES[k]) == h for k, h in ent[1].items())
+    return ent[0] if same else None
 
 
 # Algorithmic bytes per unit of one P_eps^-1 apply with five streaming passes:
@@ -592,7 +599,7 @@ def pinv_report(form, r, U):
         "min_bytes_frac": round(16.0 * U / t / 1e9 / peaks["hbm_gbs"], 4),
         "dram_gbs": round(dram / t / 1e9, 1) if dram else None,
         "bound": "FP64 pipe (2 FMA/clk/SM)" if form == "fp64" else
-                 "instruction issue and shared memory (the FP32 intermediate stays in L2)"}
+                 "instruction issue (the FP32 intermediate stays in L2)"}
 
 
 def top_kernels(kernels, n=3):
