@@ -387,9 +387,14 @@ bec_status bec_learned_residual_ratios(bec_problem* p, double* host);
  * returns BEC_ETIMEOUT.
  * bec_inject_fault(BEC_FAULT_TC_WITHHOLD_LOADS) makes the next tensor-core
  * convolution withhold its tile loads, so that its waits run out (about
- * 0.2 s): a host-side injection that faults, traps and hangs nothing.  The
+ * 0.2 s): a host-side injection that faults, traps and hangs nothing.
+ * bec_inject_fault(BEC_FAULT_TMA_WITHHOLD_LOADS) does the same to the next
+ * TMA-staged FP32 preconditioner pass (the N = 256 time pass or the n = 256
+ * column pass): it issues no tile load, its blocks' waits run out and they
+ * return without writing, and bec_gmres_solve returns BEC_ETIMEOUT.  Each
  * injection is one-shot; BEC_FAULT_NONE does nothing. */
-enum { BEC_FAULT_NONE = 0, BEC_FAULT_TC_WITHHOLD_LOADS = 1, BEC_FAULT_PERSIST_WITHHOLD = 2 };
+enum { BEC_FAULT_NONE = 0, BEC_FAULT_TC_WITHHOLD_LOADS = 1, BEC_FAULT_PERSIST_WITHHOLD = 2,
+       BEC_FAULT_TMA_WITHHOLD_LOADS = 3 };
 bec_status bec_inject_fault(int kind);
 
 /* ---- Tile shapes of the P_eps^{-1} passes --------------------------------

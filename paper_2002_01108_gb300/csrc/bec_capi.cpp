@@ -715,6 +715,10 @@ bec_status bec_inject_fault(int kind) {
     persist_withhold_next();
     return BEC_OK;
   }
+  if (kind == BEC_FAULT_TMA_WITHHOLD_LOADS) {
+    tma_withhold_next();
+    return BEC_OK;
+  }
   return einval("unknown fault kind");
 }
 

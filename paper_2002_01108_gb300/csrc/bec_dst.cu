@@ -73,7 +73,7 @@ constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16;
 __global__ void __launch_bounds__(kD16Threads, 2)
 dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __restrict__ sin2,
                       const float2* __restrict__ tw, int tiles_x, long long ntiles,
-                      uint32_t tile_bytes, int* __restrict__ err) {
+                      uint32_t tile_bytes, int withhold, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char d16_smem[];
   float* const stage0 = reinterpret_cast<float*>(d16_smem);
   float* const stage1 = stage0 + kD16StageBytes / sizeof(float);
@@ -87,7 +87,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
   }
   __syncthreads();
   long long t = blockIdx.x;
-  if (tid == 0 && t < ntiles) {
+  if (tid == 0 && t < ntiles && !withhold) {
     tma_mbar_expect_tx(bar0, tile_bytes);
     tma_load_3d(tma_smem_u32(stage0), &map, (int)(t % tiles_x) * kD16Cols, 0, (int)(t / tiles_x),
                 bar0);
@@ -98,7 +98,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
     const int b = it & 1;
     float* const st = b ? stage1 : stage0;
     const long long tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {                 // prefetch the next tile into the other stage
+    if (tid == 0 && tn < ntiles && !withhold) {    // prefetch the next tile into the other stage
       tma_wait_group_read0();
       const uint32_t nb = b ? bar0 : bar1;
       tma_mbar_expect_tx(nb, tile_bytes);
@@ -121,7 +121,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
   if (tid == 0) {
     if (!ok) {
       atomicExch(err, 1);
-      if (t + gridDim.x < ntiles) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
+      if (t + gridDim.x < ntiles && !withhold) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
                                                 (uint32_t)(((it + 1) >> 1) & 1));
     }
     tma_wait_group0();
@@ -144,7 +144,8 @@ bec_status cols16_launch(bec_problem* p) {
   const uint32_t tile_bytes = (uint32_t)(kD16Cols * p->m * sizeof(float));
   BEC_LAUNCH_BEGIN(p);
   dst_cols16_tma_kernel<<<(unsigned)grid, kD16Threads, kD16TmaSmem, p->stream>>>(
-      p->cols_map, p->tab.sin2_32, p->tab.space.tw32, tiles_x, ntiles, tile_bytes, p->pc_err);
+      p->cols_map, p->tab.sin2_32, p->tab.space.tw32, tiles_x, ntiles, tile_bytes,
+      tma_take_withhold(), p->pc_err);
   BEC_LAUNCH_CHECK(p, "dst_cols16_tma_kernel");
   return BEC_OK;
 }

@@ -377,6 +377,10 @@ bec_status net_check(bec_problem* p);
 bool tc_conv_supported();
 // test hook: the next tensor-core convolution withholds its tile loads
 void tc_withhold_next_loads();
+// the next TMA-staged FP32 pass (time or column) issues no tile load (test
+// hook, one-shot); tma_take_withhold returns and clears the request
+void tma_withhold_next();
+int tma_take_withhold();
 // BF16 elements of the converted weights of all 9 layers
 int tc_weights_elems();
 // the operand layout of every layer from the FP32 master weights W (layer l

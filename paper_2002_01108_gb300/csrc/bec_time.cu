@@ -19,6 +19,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 namespace bec {
 namespace {
 
@@ -113,7 +115,8 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
                        int dim, const float* __restrict__ es, const float* __restrict__ eis,
                        const float2* __restrict__ lamf, ModeEigs<float> me, float tau,
                        float scale_h, const double* __restrict__ scale_dev,
-                       const float2* __restrict__ tw, long long ntiles, int* __restrict__ err) {
+                       const float2* __restrict__ tw, long long ntiles, int withhold,
+                       int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char t16_smem[];
   float* const stage0 = reinterpret_cast<float*>(t16_smem);
   float* const stage1 = stage0 + kT16StageBytes / sizeof(float);
@@ -127,7 +130,7 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
   }
   __syncthreads();
   long long t = blockIdx.x;
-  if (tid == 0 && t < ntiles) {
+  if (tid == 0 && t < ntiles && !withhold) {
     tma_mbar_expect_tx(bar0, (uint32_t)kT16StageBytes);
     tma_load_2d(tma_smem_u32(stage0), &map, (int)(t * kT16Modes), 0, bar0);
   }
@@ -136,7 +139,7 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
   for (; t < ntiles; t += gridDim.x, ++it) {
     const int b = it & 1;
     float* const st = b ? stage1 : stage0;
-    if (tid == 0 && t + gridDim.x < ntiles) {       // prefetch the next tile into the other stage
+    if (tid == 0 && t + gridDim.x < ntiles && !withhold) {   // prefetch the next tile
       tma_wait_group_read0();
       const uint32_t nb = b ? bar0 : bar1;
       tma_mbar_expect_tx(nb, (uint32_t)kT16StageBytes);
@@ -161,7 +164,7 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
     if (!ok) {
       atomicExch(err, 1);
       // the prefetch issued in the failed iteration may still be in flight
-      if (t + gridDim.x < ntiles) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
+      if (t + gridDim.x < ntiles && !withhold) tma_mbar_wait(((it + 1) & 1) ? bar1 : bar0,
                                                 (uint32_t)(((it + 1) >> 1) & 1));
     }
     tma_wait_group0();
@@ -190,7 +193,7 @@ bec_status time16_launch(bec_problem* p, void* data, double scale, const double*
     BEC_LAUNCH_BEGIN(p);
     k<<<(unsigned)grid, kT16Threads, kT16TmaSmem, p->stream>>>(
         p->time_map, p->Jp, p->m, p->ld, p->dim, t.es32, t.eis32, t.lamf32, me, (float)p->tau,
-        (float)scale, scale_dev, t.time.tw32, ntiles, p->pc_err);
+        (float)scale, scale_dev, t.time.tw32, ntiles, tma_take_withhold(), p->pc_err);
     BEC_LAUNCH_CHECK(p, "time_pass16_tma_kernel");
     return BEC_OK;
   }
@@ -464,6 +467,13 @@ bec_status time16_make_map(bec_problem* p) {
   p->time_map_ok = true;
   return BEC_OK;
 }
+
+namespace {
+std::atomic<int> g_withhold_tma{0};   // set by bec_inject_fault, taken by the next launch
+}  // namespace
+
+void tma_withhold_next() { g_withhold_tma.store(1); }
+int tma_take_withhold() { return g_withhold_tma.exchange(0); }
 
 bec_status pc_check(bec_problem* p) {
   if (p->pc_err == nullptr) return BEC_OK;
