@@ -62,13 +62,16 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
 }
 
 // FP32 y-DST for n = 256 (2D) on the four-step tile (dst16_cols_core), the
-// tiles moved by TMA: each block walks tiles blk, blk + grid, ... (tile t:
+// tiles moved by TMA: each block copies sin2 and the twiddles to shared
+// memory, then walks tiles blk, blk + grid, ... (tile t:
 // columns 32 (t mod tiles_x) .. + 31 of slice t / tiles_x), transforming one
 // in its shared-memory stage while the next arrives in the other stage;
 // results leave by a TMA store from the stage they were computed in, which
 // is refilled only after the store has read it.  A wait that runs out
 // (about 0.2 s) sets *err and ends the block.
-constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16;
+// sin2 (256 floats) and tw (256 float2) copied to shared memory once per block
+constexpr size_t kD16TabBytes = 256 * sizeof(float) + 256 * sizeof(float2);
+constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16 + kD16TabBytes;
 
 __global__ void __launch_bounds__(kD16Threads, 2)
 dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __restrict__ sin2,
@@ -79,12 +82,16 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
   float* const stage1 = stage0 + kD16StageBytes / sizeof(float);
   float2* const tot = reinterpret_cast<float2*>(d16_smem + 2 * kD16StageBytes);
   const uint32_t bar0 = tma_smem_u32(d16_smem + 2 * kD16StageBytes + kD16TotBytes), bar1 = bar0 + 8;
+  float* const s_sin2 = reinterpret_cast<float*>(d16_smem + 2 * kD16StageBytes + kD16TotBytes + 16);
+  float2* const s_tw = reinterpret_cast<float2*>(s_sin2 + 256);
   const int tid = threadIdx.x;
   if (tid == 0) {
     tma_mbar_init(bar0, 1);
     tma_mbar_init(bar1, 1);
     tma_fence_mbar_init();
   }
+  s_sin2[tid] = sin2[tid];
+  s_tw[tid] = tw[tid];
   __syncthreads();
   long long t = blockIdx.x;
   if (tid == 0 && t < ntiles && !withhold) {
@@ -110,7 +117,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
       ok = false;
       break;
     }
-    dst16_cols_core(st, tot, sin2, tw, tid);
+    dst16_cols_core(st, tot, s_sin2, s_tw, tid);
     tma_fence_proxy_smem();
     __syncthreads();
     if (tid == 0) {

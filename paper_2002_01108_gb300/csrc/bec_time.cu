@@ -100,14 +100,17 @@ time_pass16_kernel(float* __restrict__ data, long long J, int m, int ld, int dim
                               scale_dev, tw, blockIdx.x, smem_bytes, threadIdx.x);
 }
 
-// The same pass with the tiles moved by TMA: each block walks tiles blk,
-// blk + grid, ...; while it transforms one tile in shared memory (stage b)
+// The same pass with the tiles moved by TMA: each block copies the pass's
+// tables to shared memory, then walks tiles blk, blk + grid, ...; while it transforms one tile in shared memory (stage b)
 // the next one arrives in the other stage, and the results leave by a TMA
 // store from the stage they were computed in.  Before a stage is refilled
 // its store must have read it (bulk wait_group.read).  A wait for a tile
 // that runs out (about 0.2 s) sets *err and ends the block.
 constexpr size_t kT16StageBytes = (size_t)kT16Modes * 256 * sizeof(float);   // 32 KB
-constexpr size_t kT16TmaSmem = 2 * kT16StageBytes + kT16Smem + 16;
+// tables copied to shared memory once per block: es, eis (256 floats each),
+// tw (256 float2), lamf (129 float2)
+constexpr size_t kT16TabBytes = 2 * 256 * sizeof(float) + (256 + 129) * sizeof(float2);
+constexpr size_t kT16TmaSmem = 2 * kT16StageBytes + kT16Smem + 16 + kT16TabBytes;
 
 template <bool FE>
 __global__ void __launch_bounds__(kT16Threads, 2)
@@ -122,12 +125,20 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
   float* const stage1 = stage0 + kT16StageBytes / sizeof(float);
   unsigned char* const xbuf = t16_smem + 2 * kT16StageBytes;
   const uint32_t bar0 = tma_smem_u32(xbuf + kT16Smem), bar1 = bar0 + 8;
+  float* const s_es = reinterpret_cast<float*>(xbuf + kT16Smem + 16);
+  float* const s_eis = s_es + 256;
+  float2* const s_tw = reinterpret_cast<float2*>(s_eis + 256);
+  float2* const s_lam = s_tw + 256;
   const int tid = threadIdx.x;
   if (tid == 0) {
     tma_mbar_init(bar0, 1);
     tma_mbar_init(bar1, 1);
     tma_fence_mbar_init();
   }
+  s_es[tid] = es[tid];
+  s_eis[tid] = eis[tid];
+  s_tw[tid] = tw[tid];
+  if (tid <= 128) s_lam[tid] = lamf[tid];
   __syncthreads();
   long long t = blockIdx.x;
   if (tid == 0 && t < ntiles && !withhold) {
@@ -151,8 +162,8 @@ time_pass16_tma_kernel(const __grid_constant__ CUtensorMap map, long long J, int
       ok = false;
       break;
     }
-    time_pass16_tile<FE, true>(nullptr, st, J, m, ld, dim, es, eis, lamf, me, tau, scale_h,
-                               scale_dev, tw, t, xbuf, tid);
+    time_pass16_tile<FE, true>(nullptr, st, J, m, ld, dim, s_es, s_eis, s_lam, me, tau, scale_h,
+                               scale_dev, s_tw, t, xbuf, tid);
     tma_fence_proxy_smem();
     __syncthreads();
     if (tid == 0) {
