@@ -62,8 +62,9 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
 }
 
 // FP32 y-DST for n = 256 (2D) on the four-step tile (dst16_cols_core), the
-// tiles moved by TMA: each block copies sin2 and the twiddles to shared
-// memory, then walks tiles blk, blk + grid, ... (tile t:
+// tiles moved by TMA, with an exchange buffer of its own (four block
+// barriers per tile instead of six): each block copies sin2 and the
+// twiddles to shared memory, then walks tiles blk, blk + grid, ... (tile t:
 // columns 32 (t mod tiles_x) .. + 31 of slice t / tiles_x), transforming one
 // in its shared-memory stage while the next arrives in the other stage;
 // results leave by a TMA store from the stage they were computed in, which
@@ -71,7 +72,8 @@ dst_cols_kernel(T* data, int m, int ncols, long long row_stride, long long slice
 // (about 0.2 s) sets *err and ends the block.
 // sin2 (256 floats) and tw (256 float2) copied to shared memory once per block
 constexpr size_t kD16TabBytes = 256 * sizeof(float) + 256 * sizeof(float2);
-constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16 + kD16TabBytes;
+constexpr size_t kD16XBytes = 16 * 256 * sizeof(float2);   // the exchange buffer (32 KB)
+constexpr size_t kD16TmaSmem = 2 * kD16StageBytes + kD16TotBytes + 16 + kD16TabBytes + kD16XBytes;
 
 __global__ void __launch_bounds__(kD16Threads, 2)
 dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __restrict__ sin2,
@@ -84,6 +86,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
   const uint32_t bar0 = tma_smem_u32(d16_smem + 2 * kD16StageBytes + kD16TotBytes), bar1 = bar0 + 8;
   float* const s_sin2 = reinterpret_cast<float*>(d16_smem + 2 * kD16StageBytes + kD16TotBytes + 16);
   float2* const s_tw = reinterpret_cast<float2*>(s_sin2 + 256);
+  float2* const xbuf = s_tw + 256;
   const int tid = threadIdx.x;
   if (tid == 0) {
     tma_mbar_init(bar0, 1);
@@ -117,7 +120,7 @@ dst_cols16_tma_kernel(const __grid_constant__ CUtensorMap map, const float* __re
       ok = false;
       break;
     }
-    dst16_cols_core(st, tot, s_sin2, s_tw, tid);
+    dst16_cols_core(st, xbuf, tot, s_sin2, s_tw, tid);
     tma_fence_proxy_smem();
     __syncthreads();
     if (tid == 0) {

@@ -501,10 +501,12 @@ __device__ __forceinline__ void time_pass16_tile(float* __restrict__ data, float
 // ones 4 S_{2k+1} = sum_{k' <= k} r_{k'} (the method of warp_dst_pair).
 // The tile sits in a shared-memory stage of [256][32] floats (row i holds
 // x_{i+1}; row 255 is not used) and returns there as rows of S (row i holds
-// 4 S_{i+1}).  The exchange buffer of the 16 x 16 steps is the stage itself,
-// XOR-swizzled (line L, class k2, index j1 at 256 L + 16 k2 + (j1 ^ k2 ^ L)),
-// which keeps both of its access patterns free of bank conflicts; `tot`
-// holds 256 float2.  sin2[j] = 2 sin(j pi / n), tw[t] = e^{-2 pi i t / n}.
+// 4 S_{i+1}).  The exchange buffer of the 16 x 16 steps is `xbuf` (32 KB)
+// or, when xbuf is null, the stage itself (two more block barriers), in
+// either case XOR-swizzled (line L, class k2, index j1 at 256 L + 16 k2 +
+// (j1 ^ k2 ^ L)), which keeps both of its access patterns free of bank
+// conflicts; `tot` holds 256 float2.  sin2[j] = 2 sin(j pi / n), tw[t] =
+// e^{-2 pi i t / n}.
 constexpr int kD16Threads = 256;
 constexpr int kD16Cols = 32;                                // columns per tile
 constexpr size_t kD16StageBytes = (size_t)256 * kD16Cols * sizeof(float);   // 32 KB
@@ -514,11 +516,13 @@ __device__ __forceinline__ int d16_xs(int L, int k2, int j1) {
   return 256 * L + 16 * k2 + ((j1 ^ k2 ^ L) & 15);
 }
 
-__device__ __forceinline__ void dst16_cols_core(float* __restrict__ stage, float2* __restrict__ tot,
+__device__ __forceinline__ void dst16_cols_core(float* __restrict__ stage, float2* xbuf,
+                                                float2* __restrict__ tot,
                                                 const float* __restrict__ sin2,
                                                 const float2* __restrict__ tw, int tid) {
   using V = float2;
   V* const sv = reinterpret_cast<V*>(stage);              // row i, line L at sv[16 i + L]
+  V* const xv = xbuf != nullptr ? xbuf : sv;              // the exchange buffer
   // Step A layout (as in time_pass16_tile): line L, residue r of j mod 16
   const int La = tid & 15;
   const int r = ((tid >> 4) & 1) * 8 + (tid >> 5);
@@ -535,19 +539,19 @@ __device__ __forceinline__ void dst16_cols_core(float* __restrict__ stage, float
     }
     v[j2] = y;
   }
-  __syncthreads();                                        // the stage becomes the exchange buffer
+  if (xbuf == nullptr) __syncthreads();                   // the stage becomes the exchange buffer
   dft16<-1>(v);
 #pragma unroll
   for (int k2 = 1; k2 < 16; ++k2) v[k2] = cmul(v[k2], tw[r * k2]);
 #pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) sv[d16_xs(La, k2, r)] = v[k2];
+  for (int k2 = 0; k2 < 16; ++k2) xv[d16_xs(La, k2, r)] = v[k2];
   __syncthreads();
   // Step B layout: line L = tid / 16, class k2 = tid mod 16
   const int lane = tid & 31, k2 = lane & 15, Lb = tid >> 4;
   V y[16];
 #pragma unroll
-  for (int j1 = 0; j1 < 16; ++j1) y[j1] = sv[d16_xs(Lb, k2, j1)];
-  __syncthreads();                                        // the stage becomes the r / e buffers
+  for (int j1 = 0; j1 < 16; ++j1) y[j1] = xv[d16_xs(Lb, k2, j1)];
+  if (xbuf == nullptr) __syncthreads();                   // the stage becomes the r / e buffers
   dft16<-1>(y);                                           // y[k1] = X_{k2 + 16 k1}
   // X_{n-k} for k = k2 + 16 k1 < n/2 (k1 < 8): as in time_pass16_tile
   V* const rb = sv;                                       // r_k of line L at rb[129 L + k]

@@ -91,7 +91,8 @@ __device__ __forceinline__ void space_pass(const PersistJob& j, int p, long long
           *reinterpret_cast<const float4*>(base + (long long)row * j.ld + 4 * c4);
     }
     __syncthreads();
-    dst16_cols_core(st, reinterpret_cast<float2*>(sm + kD16StageBytes), j.sin2, j.tws, tid);
+    dst16_cols_core(st, nullptr, reinterpret_cast<float2*>(sm + kD16StageBytes), j.sin2, j.tws,
+                    tid);
     __syncthreads();
     for (int e = tid; e < j.m * (kD16Cols / 4); e += kPThreads) {
       const int row = e / (kD16Cols / 4), c4 = e - row * (kD16Cols / 4);
