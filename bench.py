@@ -119,24 +119,24 @@ KERNEL_SOURCES = {
     "time_pass16_tma_kernel": ("bec_time.cu", "bec_passes.cuh", "bec_fft.cuh", "bec_tma.cuh"),
 }
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): (133214976 + 80398592, "5b5d539621edbefa"),
-    ("dst_cols_kernel", "fp64"): (133254912 + 73801984, "5b5d539621edbefa"),
-    ("time_pass_kernel", "fp64"): (200446464 + 75163648, "eec57d01e995c7fc"),
-    ("dst_rows_kernel", "fp32"): (133205248 + 33935360, "5b5d539621edbefa"),
-    ("dst_cols16_tma_kernel", "fp32"): (66874880 + 3591936, "1d4635b6ce7187ac"),
-    ("time_pass16_tma_kernel", "fp32"): (66899712 + 4049920, "ac59da95e3727d01"),
+    ("dst_rows_kernel", "fp64"): (133219584 + 80538624, "e8b4bd3a54be47fa"),
+    ("dst_cols_kernel", "fp64"): (133209088 + 73857280, "e8b4bd3a54be47fa"),
+    ("time_pass_kernel", "fp64"): (200386816 + 75440896, "c01e98a3f389a3be"),
+    ("dst_rows_kernel", "fp32"): (133225984 + 33703168, "e8b4bd3a54be47fa"),
+    ("dst_cols16_tma_kernel", "fp32"): (66873600 + 3945984, "96af20670236ad7b"),
+    ("time_pass16_tma_kernel", "fp32"): (66891520 + 4111872, "e27848999e7baff3"),
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same
 # capture) and the kernels whose sources they were taken on
 NCU_PINV_BYTES = {
-    "fp64": ((133214976 + 80398592) + (133254912 + 73801984) + (200446464 + 75163648)
-             + (133319936 + 73796864) + (133241344 + 70547200),
-             {"dst_rows_kernel": "5b5d539621edbefa", "dst_cols_kernel": "5b5d539621edbefa",
-              "time_pass_kernel": "eec57d01e995c7fc"}),
-    "fp32": ((133205248 + 33935360) + (66874880 + 3591936) + (66899712 + 4049920)
-             + (66874368 + 3675392) + (66876672 + 69580288),
-             {"dst_rows_kernel": "5b5d539621edbefa", "dst_cols16_tma_kernel": "1d4635b6ce7187ac",
-              "time_pass16_tma_kernel": "ac59da95e3727d01"}),
+    "fp64": ((133219584 + 80538624) + (133209088 + 73857280) + (200386816 + 75440896)
+             + (133282304 + 73858816) + (133211392 + 70560000),
+             {"dst_rows_kernel": "e8b4bd3a54be47fa", "dst_cols_kernel": "e8b4bd3a54be47fa",
+              "time_pass_kernel": "c01e98a3f389a3be"}),
+    "fp32": ((133225984 + 33703168) + (66873600 + 3945984) + (66891520 + 4111872)
+             + (66898688 + 3749376) + (66879744 + 69626880),
+             {"dst_rows_kernel": "e8b4bd3a54be47fa", "dst_cols16_tma_kernel": "96af20670236ad7b",
+              "time_pass16_tma_kernel": "e27848999e7baff3"}),
 }
 
 
