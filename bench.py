@@ -119,24 +119,24 @@ KERNEL_SOURCES = {
     "time_pass16_tma_kernel": ("bec_time.cu", "bec_passes.cuh", "bec_fft.cuh", "bec_tma.cuh"),
 }
 NCU_TRAFFIC = {
-    ("dst_rows_kernel", "fp64"): (133219584 + 80538624, "e8b4bd3a54be47fa"),
-    ("dst_cols_kernel", "fp64"): (133209088 + 73857280, "e8b4bd3a54be47fa"),
-    ("time_pass_kernel", "fp64"): (200386816 + 75440896, "c01e98a3f389a3be"),
-    ("dst_rows_kernel", "fp32"): (133225984 + 33703168, "e8b4bd3a54be47fa"),
-    ("dst_cols16_tma_kernel", "fp32"): (66873600 + 3945984, "96af20670236ad7b"),
-    ("time_pass16_tma_kernel", "fp32"): (66891520 + 4111872, "e27848999e7baff3"),
+    ("dst_rows_kernel", "fp64"): (133330688 + 80688896, "d8db73df32f0a703"),
+    ("dst_cols_kernel", "fp64"): (133210368 + 73859840, "d8db73df32f0a703"),
+    ("time_pass_kernel", "fp64"): (200675328 + 75272448, "c598ed99a222731c"),
+    ("dst_rows_kernel", "fp32"): (133208320 + 34398464, "d8db73df32f0a703"),
+    ("dst_cols16_tma_kernel", "fp32"): (66874624 + 4049920, "99e057cadaa803e3"),
+    ("time_pass16_tma_kernel", "fp32"): (66894336 + 4122880, "dac5a038203bb35d"),
 }
 # DRAM bytes of one whole P_eps^-1 apply (the five passes of the same
 # capture) and the kernels whose sources they were taken on
 NCU_PINV_BYTES = {
-    "fp64": ((133219584 + 80538624) + (133209088 + 73857280) + (200386816 + 75440896)
-             + (133282304 + 73858816) + (133211392 + 70560000),
-             {"dst_rows_kernel": "e8b4bd3a54be47fa", "dst_cols_kernel": "e8b4bd3a54be47fa",
-              "time_pass_kernel": "c01e98a3f389a3be"}),
-    "fp32": ((133225984 + 33703168) + (66873600 + 3945984) + (66891520 + 4111872)
-             + (66898688 + 3749376) + (66879744 + 69626880),
-             {"dst_rows_kernel": "e8b4bd3a54be47fa", "dst_cols16_tma_kernel": "96af20670236ad7b",
-              "time_pass16_tma_kernel": "e27848999e7baff3"}),
+    "fp64": ((133330688 + 80688896) + (133210368 + 73859840) + (200675328 + 75272448)
+             + (133211648 + 73844224) + (133211648 + 70523136),
+             {"dst_rows_kernel": "d8db73df32f0a703", "dst_cols_kernel": "d8db73df32f0a703",
+              "time_pass_kernel": "c598ed99a222731c"}),
+    "fp32": ((133208320 + 34398464) + (66874624 + 4049920) + (66894336 + 4122880)
+             + (66874880 + 3893248) + (66878720 + 69490944),
+             {"dst_rows_kernel": "d8db73df32f0a703", "dst_cols16_tma_kernel": "99e057cadaa803e3",
+              "time_pass16_tma_kernel": "dac5a038203bb35d"}),
 }
 
 

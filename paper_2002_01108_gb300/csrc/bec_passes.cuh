@@ -363,6 +363,27 @@ __device__ __forceinline__ float2 t16_divide(float2 C, float2 Cn, float2 lam, fl
   return {B1.x - B2.y, B1.y + B2.x};
 }
 
+// The same for the pair: nc = the packed result at k, nn = at N - k
+// (conj B1 + i conj B2).  nn equals, bit for bit, what t16_divide gives from
+// (Cn, C, conj lam): the modes' spectra, the shifts and the products are then
+// exact conjugates of these.
+template <bool FE>
+__device__ __forceinline__ void t16_divide_pair(float2 C, float2 Cn, float2 lam, float ma,
+                                                float tmua, float mb, float tmub, float scale,
+                                                float2& nc, float2& nn) {
+  const float2 A1 = {C.x + Cn.x, C.y - Cn.y};
+  const float2 A2 = {C.y + Cn.y, Cn.x - C.x};
+  const float d1r = FE ? fmaf(lam.x, ma, tmua) : lam.x + tmua;
+  const float d2r = FE ? fmaf(lam.x, mb, tmub) : lam.x + tmub;
+  const float d1i = FE ? lam.y * ma : lam.y, d2i = FE ? lam.y * mb : lam.y;
+  const float s1 = __fdividef(scale, fmaf(d1r, d1r, d1i * d1i));
+  const float s2 = __fdividef(scale, fmaf(d2r, d2r, d2i * d2i));
+  const float2 q1 = {d1r * s1, -d1i * s1}, q2 = {d2r * s2, -d2i * s2};
+  const float2 B1 = cmul(A1, q1), B2 = cmul(A2, q2);
+  nc = {B1.x - B2.y, B1.y + B2.x};
+  nn = {B1.x + B2.y, B2.x - B1.y};
+}
+
 // data: [N][J] in place, N = 256, rows of ld slots (mode_eigs); the tile
 // owns modes q0 .. q0 + 31 from q0 = 32 blk (line L: modes q0 + 2L and
 // q0 + 2L + 1).  STAGED: the tile's values are not in `data` but in a
@@ -438,29 +459,30 @@ __device__ __forceinline__ void time_pass16_tile(float* __restrict__ data, float
     const float tmua = tau * mua, tmub = tau * mub;
     // X_{N-k} for k = k2 + 16 k1: class (16 - k2) mod 16 at k1' = 15 - k1
     // (k2 > 0, from lane (16 - k2) of the half-warp) or (16 - k1) mod 16
-    // (k2 = 0, the thread's own).  The new values of k1 < 8 wait in nw until
-    // every partner value has been passed: the second half sends y[7..0].
+    // (k2 = 0, the thread's own).  Each pair (k, N - k) with k < N/2 is done
+    // once, by the lane that holds k (k1 < 8); its result at N - k goes back
+    // to the partner by the same shuffle.  Lane k2 = 0 also holds k = N/2.
     const int src = (lane & 16) | ((16 - k2) & 15);
-    V nw[8];
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) {
+    for (int k1 = 0; k1 < 8; ++k1) {
       const V sv = k2 == 0 ? y[(16 - k1) & 15] : y[15 - k1];
       V Cn;
       Cn.x = __shfl_sync(0xffffffffu, sv.x, src);
       Cn.y = __shfl_sync(0xffffffffu, sv.y, src);
-      V lam;
-      if (k1 < 8) {
-        lam = lamf[k2 + 16 * k1];
-      } else {
-        lam = lamf[256 - k2 - 16 * k1];
-        lam.y = -lam.y;
-      }
-      const V z = t16_divide<FE>(y[k1], Cn, lam, ma, tmua, mb, tmub, scale);
-      if (k1 < 8) nw[k1] = z;
-      else y[k1] = z;
+      V nc, nn;
+      t16_divide_pair<FE>(y[k1], Cn, lamf[k2 + 16 * k1], ma, tmua, mb, tmub, scale, nc, nn);
+      V rn;                                    // the partner's result at my N - k'
+      rn.x = __shfl_sync(0xffffffffu, nn.x, src);
+      rn.y = __shfl_sync(0xffffffffu, nn.y, src);
+      y[k1] = nc;
+      if (k2 == 0) y[(16 - k1) & 15] = rn;
+      else y[15 - k1] = rn;
     }
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) y[k1] = nw[k1];
+    if (k2 == 0) {                             // k = N/2, its own partner
+      V lam = lamf[128];
+      lam.y = -lam.y;
+      y[8] = t16_divide<FE>(y[8], y[8], lam, ma, tmua, mb, tmub, scale);
+    }
     dft16<+1>(y);                              // y[j1] = sum_k1 Z_{k2 + 16 k1} w16^{-j1 k1}
 #pragma unroll
     for (int j1 = 0; j1 < 16; ++j1) rowB[j1] = y[j1];
