@@ -305,7 +305,9 @@ bec_status bec_allocate_problem(const bec_problem_desc* d, void* stream, bec_pro
       const cudaError_t e = cudaMemset(p->pc_err, 0, sizeof(int));
       if (e != cudaSuccess) s = cuda_fail(e, "cudaMemset");
     }
-    if (s == BEC_OK) s = time16_make_map(p);
+    // the TMA time pass moves tiles of 32 points of a slice; thinner slices
+    // keep the kernel whose threads load the tile
+    if (s == BEC_OK && p->Jp >= 32) s = time16_make_map(p);
     if (s == BEC_OK) s = cols16_make_map(p);
   }
   chain(dmalloc(&p->V, (size_t)(R + 1) * U));

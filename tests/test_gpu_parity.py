@@ -145,7 +145,10 @@ def test_apply_Pinv_fp64_matches_oracle(dim, m, N, eps):
                                          (2, 255, 256, 0.0625),
                                          # n = 256: the four-step column pass (and 2 x 255
                                          # rows: a half-empty last warp of the row pass)
-                                         (2, 255, 8, 0.1), (2, 255, 2, 0.3), (1, 255, 64, 0.1)])
+                                         (2, 255, 8, 0.1), (2, 255, 2, 0.3), (1, 255, 64, 0.1),
+                                         # N = 256 on slices of 8 and 32 points: the
+                                         # thread-loaded and the TMA time pass
+                                         (1, 7, 256, 0.2), (1, 31, 256, 0.05)])
 def test_apply_Pinv_fp32_within_single_precision_bound(dim, m, N, eps):
     y = np.random.default_rng(2000 + N + m).uniform(-1, 1, (N,) + (m,) * dim)
     with problem(dim, m, N, precision="fp32") as p:
